@@ -1,0 +1,613 @@
+/*
+ * BiPart CPU ORACLE -- test infrastructure only.
+ *
+ * A plain, slow, sequential C restatement of the deterministic multilevel bisection of
+ * Maleki, Agarwal, Burtscher and Pingali, "BiPart: A Parallel and Deterministic Multilevel
+ * Hypergraph Partitioner" (PPoPP'21).  Only tests, the package's smoke check and the benchmark's
+ * CPU-baseline leg may load it; the CUDA path shares no code, header or table with this file.
+ *
+ * Every function follows one algorithm of the paper in its order and notation; where the paper
+ * is silent the fixed reading is stated at the function (the same readings are written out for
+ * the CUDA path as specification, not as shared code):
+ *
+ *   normalise      input hyperedges -> sorted unique pins, drop < 2 pins (reading C10)
+ *   match          Algorithm 1 (Sec. 3.1.1): three min passes; hash = MurmurHash3 fmix32 (C1-C3)
+ *   coarsen        Algorithm 2 (Sec. 3.1.2): merge matched sets, attach singletons, contract
+ *                  (C4-C9)
+ *   gains          Algorithm 4 (Sec. 3.2): move gains from per-hyperedge side counts, weighted
+ *                  by hyperedge weight (weighted cut, Sec. 1.1)
+ *   initial        Algorithm 3 (Sec. 3.2): grow P0 by the top ceil(sqrt n) gains (C14)
+ *   refine         Algorithm 5 (Sec. 3.3): gain >= 0 lists, swap the top l_min (C15)
+ *   rebalance      Algorithm 5's final step, a variant of Algorithm 3 (C13)
+ *   bisect         Sec. 3.4 multilevel driver: levels / stop rule (C11), balance limit (C12)
+ *   partition      Algorithm 6 (Sec. 3.5): nested k-way by recursive bisection (C16)
+ *   cut            Sec. 1.1: sum over hyperedges of w_e (lambda_e - 1) (C17)
+ *
+ * Pins: every function here is checked by the -m "not gpu" tests against brute force, closed
+ * forms and invariants (see tests/test_oracle_*.py).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define ORC_OK 0
+#define ORC_WARN_IMBALANCED 1
+#define ORC_ERR_INVALID_ARG (-1)
+#define ORC_ERR_OOM (-3)
+
+enum { POL_LDH = 0, POL_HDH = 1, POL_LWD = 2, POL_HWD = 3, POL_RAND = 4 };
+
+/* Refinement admits nodes whose gain is at least this value (Algorithm 5 filters gain >= 0). */
+#define REFINE_MIN_GAIN 0
+
+typedef struct orc_hg {
+    int32_t N, E;
+    int32_t *off;   /* E + 1 */
+    int32_t *pin;   /* off[E]; pins of e are sorted ascending and unique */
+    int32_t *nwt;   /* N node weights (>= 1) */
+    int32_t *hwt;   /* E hyperedge weights (>= 1) */
+} orc_hg;
+
+static void *xmalloc(size_t n) { return malloc(n ? n : 1); }
+static void *xcalloc(size_t n, size_t s) { return calloc(n ? n : 1, s ? s : 1); }
+
+void orc_hg_free(orc_hg *g) {
+    if (!g) return;
+    free(g->off); free(g->pin); free(g->nwt); free(g->hwt); free(g);
+}
+
+static orc_hg *hg_alloc(int32_t N, int32_t E, int64_t P) {
+    orc_hg *g = (orc_hg *)xcalloc(1, sizeof(orc_hg));
+    g->N = N; g->E = E;
+    g->off = (int32_t *)xmalloc(sizeof(int32_t) * ((size_t)E + 1));
+    g->pin = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)P);
+    g->nwt = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)N);
+    g->hwt = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)E);
+    return g;
+}
+
+int32_t orc_hg_N(const orc_hg *g) { return g->N; }
+int32_t orc_hg_E(const orc_hg *g) { return g->E; }
+int32_t orc_hg_P(const orc_hg *g) { return g->off[g->E]; }
+
+void orc_hg_copy(const orc_hg *g, int32_t *off, int32_t *pin, int32_t *nwt, int32_t *hwt) {
+    if (off) memcpy(off, g->off, sizeof(int32_t) * ((size_t)g->E + 1));
+    if (pin) memcpy(pin, g->pin, sizeof(int32_t) * (size_t)g->off[g->E]);
+    if (nwt) memcpy(nwt, g->nwt, sizeof(int32_t) * (size_t)g->N);
+    if (hwt) memcpy(hwt, g->hwt, sizeof(int32_t) * (size_t)g->E);
+}
+
+static int cmp_i32(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Sort a pin list ascending and drop repeats; returns the distinct count. */
+static int32_t sort_unique(int32_t *a, int32_t n) {
+    if (n == 0) return 0;
+    qsort(a, (size_t)n, sizeof(int32_t), cmp_i32);
+    int32_t m = 1;
+    for (int32_t i = 1; i < n; i++)
+        if (a[i] != a[m - 1]) a[m++] = a[i];
+    return m;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Reading C10: level 0 is the input with each hyperedge's pins sorted ascending and
+ * deduplicated; hyperedges left with fewer than 2 distinct pins are dropped (they can never be
+ * cut) and the survivors are renumbered in ascending input order, keeping their weights.
+ * NULL weights mean unit weights.  The input is assumed valid (offsets monotone, pins in range).
+ * ------------------------------------------------------------------------------------------ */
+orc_hg *orc_hg_normalise(int32_t N, int32_t E, const int32_t *off, const int32_t *pins,
+                         const int32_t *nwt, const int32_t *hwt) {
+    int64_t P = off[E];
+    orc_hg *g = hg_alloc(N, E, P);
+    for (int32_t v = 0; v < N; v++) g->nwt[v] = nwt ? nwt[v] : 1;
+    int32_t *buf = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(P > 0 ? P : 1));
+    int32_t ne = 0, np = 0;
+    g->off[0] = 0;
+    for (int32_t e = 0; e < E; e++) {
+        int32_t d = off[e + 1] - off[e];
+        memcpy(buf, pins + off[e], sizeof(int32_t) * (size_t)d);
+        int32_t m = sort_unique(buf, d);
+        if (m < 2) continue;
+        memcpy(g->pin + np, buf, sizeof(int32_t) * (size_t)m);
+        np += m;
+        g->hwt[ne] = hwt ? hwt[e] : 1;
+        g->off[++ne] = np;
+    }
+    g->E = ne;
+    free(buf);
+    return g;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Reading C1: the hash of Algorithm 1 is the MurmurHash3 32-bit finaliser (fmix32, Appleby),
+ * applied to the level-local hyperedge id.  It is a bijection of 32-bit integers, so
+ * (priority, hash) is unique per hyperedge.
+ * ------------------------------------------------------------------------------------------ */
+uint32_t orc_hash(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+/* Reading C2/C4 (Table 1): lower value = higher priority; degree = distinct pins at this level. */
+uint32_t orc_priority(const orc_hg *g, int32_t e, int policy) {
+    uint32_t deg = (uint32_t)(g->off[e + 1] - g->off[e]);
+    uint32_t w = (uint32_t)g->hwt[e];
+    switch (policy) {
+        case POL_LDH: return deg;
+        case POL_HDH: return 0xFFFFFFFFu - deg;
+        case POL_LWD: return w;
+        case POL_HWD: return 0xFFFFFFFFu - w;
+        default:      return orc_hash((uint32_t)e);
+    }
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Algorithm 1 (parallel matching policy), sequentially.  Three passes over the hyperedges:
+ *   (1) node.priority = min over incident hyperedges of hedge.priority;
+ *   (2) node.rand     = min hedge.rand over incident hyperedges whose priority equals it;
+ *   (3) node.hedgeid  = min hedge.id over incident hyperedges with that priority and rand.
+ * The third pass also compares the priority (reading C3); with a bijective hash the rand test
+ * alone picks the same hyperedge.  Nodes in no hyperedge keep hedgeid = infinity -> -1 (C6).
+ * ------------------------------------------------------------------------------------------ */
+void orc_match(const orc_hg *g, int policy, int32_t *hedgeid) {
+    const uint64_t INF = UINT64_MAX;
+    uint64_t *npri = (uint64_t *)xmalloc(sizeof(uint64_t) * (size_t)g->N);
+    uint64_t *nrand = (uint64_t *)xmalloc(sizeof(uint64_t) * (size_t)g->N);
+    uint64_t *nid = (uint64_t *)xmalloc(sizeof(uint64_t) * (size_t)g->N);
+    for (int32_t v = 0; v < g->N; v++) { npri[v] = INF; nrand[v] = INF; nid[v] = INF; }
+    for (int32_t e = 0; e < g->E; e++) {
+        uint64_t pr = orc_priority(g, e, policy);
+        for (int32_t i = g->off[e]; i < g->off[e + 1]; i++) {
+            int32_t v = g->pin[i];
+            if (pr < npri[v]) npri[v] = pr;
+        }
+    }
+    for (int32_t e = 0; e < g->E; e++) {
+        uint64_t pr = orc_priority(g, e, policy), rd = orc_hash((uint32_t)e);
+        for (int32_t i = g->off[e]; i < g->off[e + 1]; i++) {
+            int32_t v = g->pin[i];
+            if (pr == npri[v] && rd < nrand[v]) nrand[v] = rd;
+        }
+    }
+    for (int32_t e = 0; e < g->E; e++) {
+        uint64_t pr = orc_priority(g, e, policy), rd = orc_hash((uint32_t)e);
+        for (int32_t i = g->off[e]; i < g->off[e + 1]; i++) {
+            int32_t v = g->pin[i];
+            if (pr == npri[v] && rd == nrand[v] && (uint64_t)e < nid[v]) nid[v] = (uint64_t)e;
+        }
+    }
+    for (int32_t v = 0; v < g->N; v++) hedgeid[v] = nid[v] == INF ? -1 : (int32_t)nid[v];
+    free(npri); free(nrand); free(nid);
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Algorithm 2 (parallel coarsening), sequentially.
+ *   S(e) = { v in e : hedgeid(v) = e }.
+ *   Step 1: every S(e) with |S(e)| > 1 becomes one merged node (group id e).
+ *   Step 2 (reading C7): for S(e) = {u}, the "already merged" nodes of e are those merged in
+ *     step 1 (a snapshot: attachments made in step 2 do not count, weights are not updated);
+ *     u joins the merged node of smallest weight (sum of its step-1 members' weights), ties to
+ *     the smaller group id; with no merged node in e, u stays alone.  Unmatched nodes stay alone.
+ *   Step 3 (readings C8, C9): coarse nodes are numbered in ascending order of their smallest
+ *     fine member; each fine hyperedge whose pins have more than one distinct parent becomes a
+ *     coarse hyperedge (ascending fine id) with sorted unique pins and the same weight.
+ * cmap[v] receives the coarse node of fine node v.  The matching is returned in match (N).
+ * ------------------------------------------------------------------------------------------ */
+orc_hg *orc_coarsen(const orc_hg *g, int policy, int32_t *cmap, int32_t *match_out) {
+    int32_t N = g->N, E = g->E;
+    int32_t *hedgeid = match_out ? match_out : (int32_t *)xmalloc(sizeof(int32_t) * (size_t)N);
+    orc_match(g, policy, hedgeid);
+
+    int32_t *Ssize = (int32_t *)xcalloc((size_t)E, sizeof(int32_t));
+    int64_t *mergedw = (int64_t *)xcalloc((size_t)E, sizeof(int64_t));
+    /* parent: >= 0 -> the merged node formed from S(parent); -1 - v -> node v on its own */
+    int32_t *parent = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)N);
+    for (int32_t v = 0; v < N; v++) parent[v] = -1 - v;
+
+    for (int32_t e = 0; e < E; e++)
+        for (int32_t i = g->off[e]; i < g->off[e + 1]; i++)
+            if (hedgeid[g->pin[i]] == e) Ssize[e]++;
+
+    /* Step 1: merge every S(e) with more than one node. */
+    uint8_t *merged = (uint8_t *)xcalloc((size_t)N, 1);
+    for (int32_t e = 0; e < E; e++) {
+        if (Ssize[e] <= 1) continue;
+        for (int32_t i = g->off[e]; i < g->off[e + 1]; i++) {
+            int32_t v = g->pin[i];
+            if (hedgeid[v] != e) continue;
+            parent[v] = e;
+            merged[v] = 1;
+            mergedw[e] += g->nwt[v];
+        }
+    }
+    /* Step 2: singleton sets join the lightest merged node of their hyperedge. */
+    for (int32_t e = 0; e < E; e++) {
+        if (Ssize[e] != 1) continue;
+        int32_t u = -1, best = -1;
+        for (int32_t i = g->off[e]; i < g->off[e + 1]; i++) {
+            int32_t v = g->pin[i];
+            if (hedgeid[v] == e) u = v;
+        }
+        for (int32_t i = g->off[e]; i < g->off[e + 1]; i++) {
+            int32_t v = g->pin[i];
+            if (!merged[v]) continue;
+            int32_t gv = parent[v];
+            if (best < 0 || mergedw[gv] < mergedw[best] || (mergedw[gv] == mergedw[best] && gv < best))
+                best = gv;
+        }
+        parent[u] = best >= 0 ? best : -1 - u;
+    }
+
+    /* Step 3a: coarse node ids, ascending by smallest fine member. */
+    int32_t *grp_first = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(E > 0 ? E : 1));
+    for (int32_t e = 0; e < E; e++) grp_first[e] = -1;
+    int32_t Nc = 0;
+    for (int32_t v = 0; v < N; v++) {
+        int32_t p = parent[v];
+        if (p < 0) {
+            cmap[v] = Nc++;
+        } else if (grp_first[p] < 0) {
+            grp_first[p] = Nc;
+            cmap[v] = Nc++;
+        } else {
+            cmap[v] = grp_first[p];
+        }
+    }
+    /* Step 3b: coarse hyperedges. */
+    int64_t P = g->off[E];
+    orc_hg *c = hg_alloc(Nc, E, P);
+    for (int32_t k = 0; k < Nc; k++) c->nwt[k] = 0;
+    for (int32_t v = 0; v < N; v++) c->nwt[cmap[v]] += g->nwt[v];
+    int32_t ne = 0, np = 0;
+    c->off[0] = 0;
+    for (int32_t e = 0; e < E; e++) {
+        int32_t d = g->off[e + 1] - g->off[e];
+        int32_t *dst = c->pin + np;
+        for (int32_t i = 0; i < d; i++) dst[i] = cmap[g->pin[g->off[e] + i]];
+        int32_t m = sort_unique(dst, d);
+        if (m < 2) continue;
+        np += m;
+        c->hwt[ne] = g->hwt[e];
+        c->off[++ne] = np;
+    }
+    c->E = ne;
+
+    free(grp_first); free(merged); free(parent); free(mergedw); free(Ssize);
+    if (!match_out) free(hedgeid);
+    return c;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Algorithm 4 (move gains).  For each hyperedge, n0 / n1 count its pins in P0 / P1; a pin u on
+ * side i gains w_e when it is the only pin of e on side i (moving it uncuts e) and loses w_e when
+ * all pins of e are on side i (moving it cuts e).  With unit weights this is Algorithm 4 as
+ * printed; with weights it is the change of the weighted cut.
+ * ------------------------------------------------------------------------------------------ */
+void orc_gains(const orc_hg *g, const uint8_t *side, int32_t *gain) {
+    for (int32_t v = 0; v < g->N; v++) gain[v] = 0;
+    for (int32_t e = 0; e < g->E; e++) {
+        int32_t n[2] = {0, 0}, d = g->off[e + 1] - g->off[e];
+        for (int32_t i = g->off[e]; i < g->off[e + 1]; i++) n[side[g->pin[i]]]++;
+        for (int32_t i = g->off[e]; i < g->off[e + 1]; i++) {
+            int32_t u = g->pin[i];
+            int32_t ni = n[side[u]];
+            if (ni == 1) gain[u] += g->hwt[e];
+            else if (ni == d) gain[u] -= g->hwt[e];
+        }
+    }
+}
+
+/* Node order used by Algorithms 3 and 5: higher gain first, ties to the smaller node id. */
+typedef struct { int32_t gain, id, w; } cand_t;
+static int cmp_cand(const void *a, const void *b) {
+    const cand_t *x = (const cand_t *)a, *y = (const cand_t *)b;
+    if (x->gain != y->gain) return x->gain > y->gain ? -1 : 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+/* ceil(sqrt(n)) in integers (reading C14). */
+int64_t orc_ceil_sqrt(int64_t n) {
+    if (n <= 0) return 0;
+    int64_t r = (int64_t)sqrt((double)n);
+    while (r * r > n) r--;
+    while ((r + 1) * (r + 1) <= n) r++;
+    return r * r == n ? r : r + 1;
+}
+
+static void side_weights(const orc_hg *g, const uint8_t *side, int64_t W[2]) {
+    W[0] = W[1] = 0;
+    for (int32_t v = 0; v < g->N; v++) W[side[v]] += g->nwt[v];
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Algorithm 3 (initial partitioning) on the coarsest level.  P0 = {}, P1 = V; while P0 is
+ * lighter than P1 (by node weight, reading C14), recompute the gains and move the
+ * s = ceil(sqrt(n)) nodes of P1 with the highest gains (ties to the smaller id) to P0; the last
+ * round may overshoot.  Returns the number of rounds.
+ * ------------------------------------------------------------------------------------------ */
+int32_t orc_initial(const orc_hg *g, uint8_t *side) {
+    int32_t n = g->N;
+    int64_t s = orc_ceil_sqrt(n);
+    for (int32_t v = 0; v < n; v++) side[v] = 1;
+    int64_t W[2];
+    side_weights(g, side, W);
+    int32_t *gain = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)n);
+    cand_t *L = (cand_t *)xmalloc(sizeof(cand_t) * (size_t)n);
+    int32_t rounds = 0;
+    while (W[0] < W[1]) {
+        orc_gains(g, side, gain);
+        int32_t m = 0;
+        for (int32_t v = 0; v < n; v++)
+            if (side[v] == 1) { L[m].gain = gain[v]; L[m].id = v; L[m].w = g->nwt[v]; m++; }
+        qsort(L, (size_t)m, sizeof(cand_t), cmp_cand);
+        int64_t take = s < m ? s : m;
+        for (int64_t i = 0; i < take; i++) {
+            side[L[i].id] = 0;
+            W[0] += L[i].w;
+            W[1] -= L[i].w;
+        }
+        rounds++;
+    }
+    free(gain); free(L);
+    return rounds;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Algorithm 5, one refinement iteration: gains; L_i = nodes of P_i with gain >= 0 (reading C15);
+ * both lists in (gain desc, id asc) order; the first l_min = min(|L0|, |L1|) of each list swap
+ * sides at once (gains are not updated in between).  Returns l_min.
+ * ------------------------------------------------------------------------------------------ */
+int32_t orc_refine_iter(const orc_hg *g, uint8_t *side) {
+    int32_t n = g->N;
+    int32_t *gain = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)n);
+    cand_t *L0 = (cand_t *)xmalloc(sizeof(cand_t) * (size_t)n);
+    cand_t *L1 = (cand_t *)xmalloc(sizeof(cand_t) * (size_t)n);
+    orc_gains(g, side, gain);
+    int32_t m0 = 0, m1 = 0;
+    for (int32_t v = 0; v < n; v++) {
+        if (gain[v] < REFINE_MIN_GAIN) continue;
+        cand_t c = {gain[v], v, g->nwt[v]};
+        if (side[v] == 0) L0[m0++] = c; else L1[m1++] = c;
+    }
+    qsort(L0, (size_t)m0, sizeof(cand_t), cmp_cand);
+    qsort(L1, (size_t)m1, sizeof(cand_t), cmp_cand);
+    int32_t lmin = m0 < m1 ? m0 : m1;
+    for (int32_t i = 0; i < lmin; i++) { side[L0[i].id] = 1; side[L1[i].id] = 0; }
+    free(gain); free(L0); free(L1);
+    return lmin;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Reading C12: the weight limit of one side of a bisection with total weight W and imbalance
+ * eps is max(ceil(W/2), floor(W * (10^6 + e) / (2 * 10^6))), e = llround(eps * 10^6).
+ * ------------------------------------------------------------------------------------------ */
+int64_t orc_limit(int64_t W, double eps) {
+    int64_t e6 = llround(eps * 1e6);
+    int64_t a = (W + 1) / 2;
+    int64_t b = (W * (1000000 + e6)) / 2000000;
+    return a > b ? a : b;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Algorithm 5, final step (reading C13, "a variant of Algorithm 3"): while the heavier side H
+ * exceeds the limit, recompute the gains; the candidates are the nodes of H whose weight fits in
+ * room = limit - W(other side), in (gain desc, id asc) order; move the shortest prefix whose
+ * weight reaches need = W(H) - limit, stopping early at s = ceil(sqrt(n)) nodes or when the next
+ * node would exceed room.  Returns ORC_OK when balanced, ORC_WARN_IMBALANCED when no candidate
+ * is left while H is still too heavy.
+ * ------------------------------------------------------------------------------------------ */
+int orc_rebalance(const orc_hg *g, uint8_t *side, int64_t limit, int32_t *rounds_out) {
+    int32_t n = g->N;
+    int64_t s = orc_ceil_sqrt(n);
+    int32_t *gain = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    cand_t *L = (cand_t *)xmalloc(sizeof(cand_t) * (size_t)(n > 0 ? n : 1));
+    int status = ORC_OK, rounds = 0;
+    for (;;) {
+        int64_t W[2];
+        side_weights(g, side, W);
+        int H;
+        if (W[0] > limit) H = 0;
+        else if (W[1] > limit) H = 1;
+        else break;
+        int64_t room = limit - W[1 - H], need = W[H] - limit;
+        orc_gains(g, side, gain);
+        int32_t m = 0;
+        for (int32_t v = 0; v < n; v++)
+            if (side[v] == H && g->nwt[v] <= room) { L[m].gain = gain[v]; L[m].id = v; L[m].w = g->nwt[v]; m++; }
+        if (m == 0) { status = ORC_WARN_IMBALANCED; break; }
+        qsort(L, (size_t)m, sizeof(cand_t), cmp_cand);
+        int64_t moved = 0, cnt = 0;
+        for (int32_t i = 0; i < m && cnt < s; i++) {
+            if (moved + L[i].w > room) break;
+            side[L[i].id] = (uint8_t)(1 - H);
+            moved += L[i].w;
+            cnt++;
+            if (moved >= need) break;
+        }
+        rounds++;
+    }
+    if (rounds_out) *rounds_out = rounds;
+    free(gain); free(L);
+    return status;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Sec. 3.4 multilevel bisection.  Coarsen with Algorithm 2 until `levels` coarse levels exist
+ * or a contraction leaves the node count unchanged (reading C11; that coarse level is
+ * discarded); Algorithm 3 on the coarsest level; then from the coarsest level to the input:
+ * project (Algorithm 5's initialisation, except at the coarsest level), `iters` refinement
+ * iterations, rebalance against the limit of reading C12.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct orc_run {
+    int32_t nlev;          /* number of levels including level 0 */
+    orc_hg **lev;          /* lev[0] is the (borrowed) input */
+    int32_t **cmap;        /* cmap[l]: level l -> level l+1, for l < nlev - 1 */
+    int32_t **match;       /* Algorithm 1 result at level l, for l < nlev - 1 */
+    uint8_t *side;         /* final bisection of level 0 */
+    int32_t init_rounds;
+    int status;            /* ORC_OK or ORC_WARN_IMBALANCED (of the level-0 rebalance) */
+    int64_t limit;
+} orc_run;
+
+orc_run *orc_bisect(const orc_hg *g0, double eps, int policy, int32_t levels, int32_t iters) {
+    orc_run *r = (orc_run *)xcalloc(1, sizeof(orc_run));
+    int32_t cap = levels + 1;
+    r->lev = (orc_hg **)xcalloc((size_t)cap, sizeof(orc_hg *));
+    r->cmap = (int32_t **)xcalloc((size_t)cap, sizeof(int32_t *));
+    r->match = (int32_t **)xcalloc((size_t)cap, sizeof(int32_t *));
+    r->lev[0] = (orc_hg *)g0;
+    r->nlev = 1;
+    while (r->nlev - 1 < levels) {
+        const orc_hg *f = r->lev[r->nlev - 1];
+        int32_t *cm = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(f->N > 0 ? f->N : 1));
+        int32_t *mt = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(f->N > 0 ? f->N : 1));
+        orc_hg *c = orc_coarsen(f, policy, cm, mt);
+        if (c->N == f->N) { orc_hg_free(c); free(cm); free(mt); break; }
+        r->cmap[r->nlev - 1] = cm;
+        r->match[r->nlev - 1] = mt;
+        r->lev[r->nlev++] = c;
+    }
+    int64_t W = 0;
+    for (int32_t v = 0; v < g0->N; v++) W += g0->nwt[v];
+    r->limit = orc_limit(W, eps);
+
+    int32_t L = r->nlev - 1;
+    uint8_t *side = (uint8_t *)xmalloc((size_t)(r->lev[L]->N > 0 ? r->lev[L]->N : 1));
+    r->init_rounds = orc_initial(r->lev[L], side);
+    int status = ORC_OK;
+    for (int32_t l = L; l >= 0; l--) {
+        const orc_hg *g = r->lev[l];
+        if (l < L) {
+            uint8_t *fine = (uint8_t *)xmalloc((size_t)(g->N > 0 ? g->N : 1));
+            for (int32_t v = 0; v < g->N; v++) fine[v] = side[r->cmap[l][v]];
+            free(side);
+            side = fine;
+        }
+        for (int32_t it = 0; it < iters; it++) orc_refine_iter(g, side);
+        status = orc_rebalance(g, side, r->limit, NULL);
+    }
+    r->side = side;
+    r->status = status;
+    return r;
+}
+
+int32_t orc_run_nlev(const orc_run *r) { return r->nlev; }
+const orc_hg *orc_run_level(const orc_run *r, int32_t l) { return r->lev[l]; }
+void orc_run_cmap(const orc_run *r, int32_t l, int32_t *out) {
+    memcpy(out, r->cmap[l], sizeof(int32_t) * (size_t)r->lev[l]->N);
+}
+void orc_run_match(const orc_run *r, int32_t l, int32_t *out) {
+    memcpy(out, r->match[l], sizeof(int32_t) * (size_t)r->lev[l]->N);
+}
+void orc_run_side(const orc_run *r, uint8_t *out) { memcpy(out, r->side, (size_t)r->lev[0]->N); }
+int orc_run_status(const orc_run *r) { return r->status; }
+int32_t orc_run_init_rounds(const orc_run *r) { return r->init_rounds; }
+int64_t orc_run_limit(const orc_run *r) { return r->limit; }
+
+void orc_run_free(orc_run *r) {
+    if (!r) return;
+    for (int32_t l = 1; l < r->nlev; l++) orc_hg_free(r->lev[l]);
+    for (int32_t l = 0; l < r->nlev; l++) { free(r->cmap[l]); free(r->match[l]); }
+    free(r->lev); free(r->cmap); free(r->match); free(r->side); free(r);
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Sec. 1.1 cut: sum over hyperedges of w_e * (lambda_e - 1), lambda_e = number of distinct parts
+ * among e's pins (reading C17: over the hyperedges of the graph given).
+ * ------------------------------------------------------------------------------------------ */
+int64_t orc_cut(const orc_hg *g, const int32_t *part) {
+    int64_t cut = 0;
+    int32_t maxd = 0;
+    for (int32_t e = 0; e < g->E; e++)
+        if (g->off[e + 1] - g->off[e] > maxd) maxd = g->off[e + 1] - g->off[e];
+    int32_t *buf = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(maxd > 0 ? maxd : 1));
+    for (int32_t e = 0; e < g->E; e++) {
+        int32_t d = g->off[e + 1] - g->off[e];
+        for (int32_t i = 0; i < d; i++) buf[i] = part[g->pin[g->off[e] + i]];
+        int32_t lambda = sort_unique(buf, d);
+        cut += (int64_t)g->hwt[e] * (lambda - 1);
+    }
+    free(buf);
+    return cut;
+}
+
+/* Second way for a bisection: a hyperedge counts iff it has pins on both sides. */
+int64_t orc_cut_bisection(const orc_hg *g, const uint8_t *side) {
+    int64_t cut = 0;
+    for (int32_t e = 0; e < g->E; e++) {
+        int32_t n0 = 0, n1 = 0;
+        for (int32_t i = g->off[e]; i < g->off[e + 1]; i++) {
+            if (side[g->pin[i]]) n1++; else n0++;
+        }
+        if (n0 > 0 && n1 > 0) cut += g->hwt[e];
+    }
+    return cut;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Reading C16: the subgraph of part j holds the nodes with part j, renumbered in ascending id,
+ * and every hyperedge restricted to them that keeps at least 2 pins (net splitting), in
+ * ascending hyperedge id, with weights carried.
+ * ------------------------------------------------------------------------------------------ */
+orc_hg *orc_subgraph(const orc_hg *g, const int32_t *part, int32_t j, int32_t *local_to_global) {
+    int32_t *loc = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(g->N > 0 ? g->N : 1));
+    int32_t n = 0;
+    for (int32_t v = 0; v < g->N; v++) {
+        if (part[v] == j) { loc[v] = n; if (local_to_global) local_to_global[n] = v; n++; }
+        else loc[v] = -1;
+    }
+    orc_hg *s = hg_alloc(n, g->E, g->off[g->E]);
+    for (int32_t v = 0; v < g->N; v++) if (loc[v] >= 0) s->nwt[loc[v]] = g->nwt[v];
+    int32_t ne = 0, np = 0;
+    s->off[0] = 0;
+    for (int32_t e = 0; e < g->E; e++) {
+        int32_t m = 0;
+        for (int32_t i = g->off[e]; i < g->off[e + 1]; i++) {
+            int32_t v = g->pin[i];
+            if (loc[v] >= 0) s->pin[np + m++] = loc[v];
+        }
+        if (m < 2) continue;
+        np += m;
+        s->hwt[ne] = g->hwt[e];
+        s->off[++ne] = np;
+    }
+    s->E = ne;
+    free(loc);
+    return s;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Algorithm 6 (nested k-way), sequentially: for tree level l = 1..log2 k, every current part j
+ * is bisected as its own subgraph (reading C16) with the same eps, policy, levels and iters, and
+ * its side-0 / side-1 nodes become parts 2j / 2j+1.  k must be a power of two; k = 1 gives all
+ * zeros.  Returns ORC_WARN_IMBALANCED if any bisection ended above its limit.
+ * ------------------------------------------------------------------------------------------ */
+int orc_partition(const orc_hg *g, int32_t k, double eps, int policy, int32_t levels,
+                  int32_t iters, int32_t *part) {
+    if (k < 1 || (k & (k - 1)) != 0) return ORC_ERR_INVALID_ARG;
+    for (int32_t v = 0; v < g->N; v++) part[v] = 0;
+    int status = ORC_OK;
+    int32_t *l2g = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(g->N > 0 ? g->N : 1));
+    int32_t *next = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(g->N > 0 ? g->N : 1));
+    for (int32_t parts = 1; parts < k; parts *= 2) {
+        for (int32_t j = 0; j < parts; j++) {
+            orc_hg *s = orc_subgraph(g, part, j, l2g);
+            orc_run *r = orc_bisect(s, eps, policy, levels, iters);
+            if (r->status != ORC_OK) status = r->status;
+            for (int32_t i = 0; i < s->N; i++) next[l2g[i]] = 2 * j + r->side[i];
+            orc_run_free(r);
+            orc_hg_free(s);
+        }
+        memcpy(part, next, sizeof(int32_t) * (size_t)g->N);
+    }
+    free(l2g); free(next);
+    return status;
+}
