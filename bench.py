@@ -1,0 +1,322 @@
+"""Benchmark: pins/s of one k = 2 BiPart bisection on the 1M-node netlist-like hypergraph.
+
+One step = one full multilevel bisection (coarsening to 25 levels, initial partition, 2
+refinement iterations + rebalance per level) through the C ABI on a hypergraph already resident
+in HBM.  The L2 (129 MB) is flushed between steps by writing a 512 MB buffer; only the partition
+call is inside the timed region (CUDA events on the handle's stream).
+
+Extra keys:
+  e2e          the same metric through bipart_create + bipart_partition + destroy with HOST
+               buffers (pinned), host<->device copies inside the timed region
+  roofline     the dominant kernel: algorithmic bytes / CUDA-event duration per launch, against
+               the measured HBM copy bandwidth
+  cpu_baseline the CPU oracle (single thread) on one full bisection of the same workload
+  gpu_launches kernels the library launched inside the timed region
+
+--impl reference times the CPU oracle as it stands (the paper ships no code; the oracle is the
+reference arm) on the same workload and prints the same JSON line with "impl": "reference".
+Multi-GPU (--gpus N under torchrun): a single bisection does not shard, so every rank runs an
+independent replica; value = all ranks' pins / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pins/s per k=2 bisection (bit-exact)"
+WORKLOAD = dict(workload="netlist-like hypergraph, 1M nodes (weights U{1..4}), 1.2M nets, k=2",
+                generator="synth.c1_netlist(seed=1)", k=2, epsilon=0.05, policy="LDH",
+                levels=25, refine_iters=2)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def load_workload():
+    import synth
+    g = synth.c1_netlist()
+    return g
+
+
+def cpu_baseline(g, budget_s=12.0):
+    """Times the oracle (single thread, as it stands) on full bisections of the workload."""
+    import oracle
+    h = oracle.Hypergraph.from_dict(g)
+    P = int(g["hoff"][-1])
+    times = []
+    t_all = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        oracle.bisect(h, WORKLOAD["epsilon"], WORKLOAD["policy"], WORKLOAD["levels"],
+                      WORKLOAD["refine_iters"], keep_levels=False)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all > budget_s or len(times) >= 5:
+            break
+    t = statistics.median(times)
+    return {"value": P / t, "unit": "pins/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} full k=2 bisection(s) of the 1M-node netlist, single-threaded "
+                      f"sequential C oracle, median {t:.3f} s; host has {os.cpu_count()} cores"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    # Each step is one full bisection (~3 s); for long runs the instance is scaled down so the
+    # whole reference run stays within a few minutes (stated in the sample string).
+    steps = args.steps + args.warmup
+    N = 1_000_000 if steps <= 40 else max(50_000, int(1_000_000 * 40 / steps))
+    g = synth.c1_netlist(N=N)
+    h = oracle.Hypergraph.from_dict(g)
+    P = int(g["hoff"][-1])
+    for _ in range(args.warmup):
+        oracle.bisect(h, WORKLOAD["epsilon"], WORKLOAD["policy"], WORKLOAD["levels"],
+                      WORKLOAD["refine_iters"], keep_levels=False)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.bisect(h, WORKLOAD["epsilon"], WORKLOAD["policy"], WORKLOAD["levels"],
+                      WORKLOAD["refine_iters"], keep_levels=False)
+        times.append(time.perf_counter() - t0)
+    ms = 1000.0 * sum(times) / len(times)
+    value = P / (ms / 1000.0)
+    sample = (f"{args.steps} timed full k=2 bisections of a {N}-node netlist ({P} pins), "
+              f"single-threaded sequential C oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pins/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": dict(WORKLOAD, nodes=N, pins=P),
+            "cpu_baseline": {"value": value, "unit": "pins/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "pins/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def flush_l2(buf):
+    buf.add_(1)
+
+
+def run_gpu(args):
+    import torch
+    import paper_2012_13618_gb300 as bp
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    bp.use_torch_allocator()
+    g = load_workload()
+    N, E = g["N"], g["E"]
+    P = int(g["hoff"][-1])
+    k, eps, pol, lev, it = (WORKLOAD["k"], WORKLOAD["epsilon"], WORKLOAD["policy"],
+                            WORKLOAD["levels"], WORKLOAD["refine_iters"])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+
+    h = bp.create_from(g)
+    for _ in range(args.warmup):
+        h.partition_device(out, k, eps, pol, lev, it)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---------------- device-resident timed region
+    bp.profile_enable(True)
+    launches0 = bp.kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush_l2(flush)
+            ev[i][0].record(stream)
+            st = h.partition_device(out, k, eps, pol, lev, it)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    launches = bp.kernel_launches() - launches0
+    prof = bp.profile_read()
+    bp.profile_enable(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    ms_max = ms
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = ws * P / (ms_max / 1000.0)
+    parts_dev = out.cpu().numpy()
+
+    # ---------------- end to end through the C ABI with host buffers
+    e2e_steps = max(1, min(args.steps, 5))
+    hoff_p = torch.from_numpy(g["hoff"]).pin_memory()
+    pins_p = torch.from_numpy(g["pins"]).pin_memory()
+    nw_p = torch.from_numpy(g["nw"]).pin_memory() if g["nw"] is not None else None
+    parts_p = torch.empty(N, dtype=torch.int32).pin_memory()
+    lib = bp.load()
+    import ctypes
+    e2e_t = []
+    for i in range(e2e_steps + 1):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        raw = ctypes.c_void_p()
+        rc = lib.bipart_create(N, E, ctypes.c_void_p(hoff_p.data_ptr()),
+                               ctypes.c_void_p(pins_p.data_ptr()),
+                               ctypes.c_void_p(nw_p.data_ptr()) if nw_p is not None else None,
+                               None, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(raw))
+        assert rc == 0, lib.bipart_last_error()
+        rc = lib.bipart_partition(raw, k, eps, bp.POLICIES[pol], lev, it,
+                                  ctypes.c_void_p(parts_p.data_ptr()))
+        assert rc >= 0, lib.bipart_last_error()
+        lib.bipart_destroy(raw)
+        t1 = time.perf_counter()
+        if i > 0:  # first iteration warms the allocator
+            e2e_t.append(t1 - t0)
+    e2e_s = statistics.median(e2e_t)
+    assert np.array_equal(parts_p.numpy(), parts_dev), "host-buffer path differs from device path"
+    h2d = 4 * (E + 1 + P + (N if nw_p is not None else 0))
+    d2h = 4 * N
+
+    # ---------------- roofline of the dominant kernel (live CUDA-event timing)
+    hbm, src = peaks()
+    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = None
+    if top:
+        name, (cnt, tms, tbytes) = top
+        per_launch_s = tms / cnt / 1000.0
+        ach = (tbytes / cnt) / per_launch_s / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": src,
+                "launches": cnt, "share_of_step": tms / (ms * args.steps),
+                "note": "achieved = algorithmic bytes per launch / mean CUDA-event duration per "
+                        "launch over the timed region; peak is the " + src + " HBM copy bandwidth"}
+
+    if rank == 0:
+        cpu = cpu_baseline(g) if (ws == 1 and not args.no_cpu_baseline) else None
+        line = {"metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": "synthetic",
+                "config": dict(WORKLOAD, nodes=N, hyperedges=E, pins=P,
+                               l2="flushed between steps (512 MB write)",
+                               parallelism=f"{ws} independent replica(s)"),
+                "status": int(st),
+                "clocks": clk.summary(),
+                "e2e": {"value": ws * P / e2e_s, "unit": "pins/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+                "gpu_launches": int(launches),
+                "roofline": roof,
+                "cpu_baseline": cpu,
+                "kernels": {k2: {"launches": v[0], "ms": v[1], "GBps": (v[2] / (v[1] / 1000) / 1e9) if v[1] else None}
+                            for k2, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
+        print(json.dumps(line))
+    h.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gpu":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

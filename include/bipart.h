@@ -1,0 +1,133 @@
+/*
+ * bipart.h -- C ABI of the GB300 implementation of BiPart's deterministic multilevel hypergraph
+ * bisection (Maleki, Agarwal, Burtscher, Pingali, PPoPP'21).
+ *
+ * Conventions for every entry point:
+ *   - Hypergraphs are given as hyperedge -> pin CSR in int32: hedge_offsets[num_hedges + 1]
+ *     (offsets[0] = 0, non-decreasing, offsets[E] = P) and hedge_pins[P] with every pin in
+ *     [0, num_nodes).  Node weights and hyperedge weights are int32 >= 1; NULL means unit weights.
+ *     The sum of node weights and the sum of hyperedge weights must each stay below 2^31.
+ *   - "Host" pointers are ordinary CPU memory; "device" pointers are CUDA global memory of the
+ *     current device.  The caller owns every array it passes and every output buffer; the
+ *     library copies what it keeps.
+ *   - Return codes: 0 = BIPART_OK, > 0 = warning (the result is valid), < 0 = error (outputs are
+ *     unspecified).  bipart_last_error() describes the last error of the calling thread.
+ *   - A handle is not thread-safe; distinct handles are independent.  All GPU work of a handle
+ *     runs on its stream (bipart_set_stream); entry points that return host data synchronise it.
+ *   - The result of every call is a deterministic function of its inputs: the same hypergraph and
+ *     parameters always give the same partition, the same cut and the same coarse levels.
+ */
+#ifndef BIPART_H
+#define BIPART_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BIPART_OK 0
+#define BIPART_WARN_IMBALANCED 1      /* rebalancing could not reach the limit; result still valid */
+#define BIPART_ERR_INVALID_ARG (-1)   /* bad k, epsilon, policy, levels, iters, level index, NULL */
+#define BIPART_ERR_INVALID_CSR (-2)   /* malformed offsets, pin out of range, weight < 1, sums >= 2^31 */
+#define BIPART_ERR_OOM (-3)           /* device allocation failed or a size limit was exceeded */
+#define BIPART_ERR_CUDA (-4)          /* a CUDA runtime call failed (including: no usable GPU) */
+#define BIPART_ERR_TIMEOUT (-5)       /* a bounded device-side wait expired */
+
+/* Matching policies of Table 1 (Sec. 3.1.1): which hyperedges nodes prefer to merge along. */
+#define BIPART_POLICY_LDH 0   /* lower degree first (the paper's default) */
+#define BIPART_POLICY_HDH 1   /* higher degree first */
+#define BIPART_POLICY_LWD 2   /* lower hyperedge weight first */
+#define BIPART_POLICY_HWD 3   /* higher hyperedge weight first */
+#define BIPART_POLICY_RAND 4  /* deterministic hash of the hyperedge id */
+
+typedef struct bipart_graph *bipart_handle;
+
+/* Optional device allocator used for every device buffer the library owns (for example the
+ * caching allocator of a framework).  alloc returns NULL on failure; both receive the handle's
+ * stream.  With no allocator set the library uses cudaMallocAsync / cudaFreeAsync on that stream.
+ * Applies to allocations made after the call; pass NULLs to restore the default. */
+typedef void *(*bipart_alloc_fn)(void *ctx, size_t bytes, void *stream);
+typedef void (*bipart_free_fn)(void *ctx, void *ptr, size_t bytes, void *stream);
+int bipart_set_allocator(bipart_alloc_fn alloc, bipart_free_fn free_fn, void *ctx);
+
+/* Creates a handle from host CSR arrays (Sec. 1.1 problem statement: nodes, hyperedges, optional
+ * weights).  Validates the CSR on the host, copies it to the device on `stream` (a cudaStream_t;
+ * NULL = the legacy default stream) and builds level 0 there: each hyperedge's pins sorted and
+ * de-duplicated, hyperedges with fewer than 2 distinct pins dropped (they can never be cut), and
+ * the node -> hyperedge incidence.  Errors: INVALID_ARG (NULL out, negative sizes),
+ * INVALID_CSR, OOM, CUDA. */
+int bipart_create(int32_t num_nodes, int32_t num_hedges, const int32_t *hedge_offsets,
+                  const int32_t *hedge_pins, const int32_t *node_weights,
+                  const int32_t *hedge_weights, void *stream, bipart_handle *out);
+
+/* Same as bipart_create with the four arrays in device memory; validation runs on the device. */
+int bipart_create_device(int32_t num_nodes, int32_t num_hedges, const int32_t *hedge_offsets,
+                         const int32_t *hedge_pins, const int32_t *node_weights,
+                         const int32_t *hedge_weights, void *stream, bipart_handle *out);
+
+/* Changes the stream of a handle (a cudaStream_t; NULL = legacy default stream). */
+int bipart_set_stream(bipart_handle h, void *stream);
+
+/* Partitions the handle's hypergraph into k parts (Sec. 3; k-way by the nested recursive
+ * bisection of Algorithm 6), writing part ids in [0, k) to out_parts[num_nodes] (HOST memory).
+ *   k        power of two >= 1 (k = 1 gives all zeros)
+ *   epsilon  imbalance, 0 <= epsilon <= 1000: each bisection keeps both sides at or below
+ *            max(ceil(W/2), floor(W (1 + epsilon) / 2)) of its total node weight W
+ *   policy   BIPART_POLICY_* (Table 1)
+ *   levels   maximum number of coarsening levels, >= 0 (the paper's default is 25, Sec. 3.4)
+ *   refine_iters  refinement iterations per level, >= 0 (default 2, Sec. 3.4)
+ * Returns OK, WARN_IMBALANCED, or an error. */
+int bipart_partition(bipart_handle h, int32_t k, double epsilon, int32_t policy, int32_t levels,
+                     int32_t refine_iters, int32_t *out_parts);
+
+/* Same as bipart_partition with out_parts in DEVICE memory. */
+int bipart_partition_device(bipart_handle h, int32_t k, double epsilon, int32_t policy,
+                            int32_t levels, int32_t refine_iters, int32_t *d_out_parts);
+
+/* Levels of the hierarchy kept from the last k = 2 call (level 0 = the normalised input). */
+int bipart_num_levels(bipart_handle h, int32_t *num_levels);
+
+/* Copies level `level` of the kept hierarchy to host buffers (any buffer may be NULL):
+ * sizes (N, E, P), hoff[E+1], pins[P] (ascending within each hyperedge), node weights[N],
+ * hyperedge weights[E], cmap[N] (node -> node of level+1; -1 on the coarsest level) and the
+ * matching of Algorithm 1 (hyperedge chosen by each node, -1 if none; -1 on the coarsest level). */
+int bipart_get_level(bipart_handle h, int32_t level, int32_t *N, int32_t *E, int32_t *P,
+                     int32_t *hoff, int32_t *pins, int32_t *node_weights,
+                     int32_t *hedge_weights, int32_t *cmap, int32_t *match);
+
+/* Cut of a partition given on the host (Sec. 1.1): sum over input hyperedges of
+ * w_e * (lambda_e - 1), lambda_e = number of distinct parts among the pins of e.  Computed on
+ * the device over the normalised level 0 (dropped hyperedges never contribute). */
+int bipart_cut(bipart_handle h, const int32_t *parts, int64_t *cut);
+
+/* Number of nodes / hyperedges / pins of the normalised level 0. */
+int bipart_sizes(bipart_handle h, int32_t *N, int32_t *E, int32_t *P);
+
+/* Releases every device buffer of the handle (on its stream). NULL is ignored. */
+void bipart_destroy(bipart_handle h);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char *bipart_last_error(void);
+
+/* ---- Diagnostics (not part of the paper's method) ---------------------------------------- */
+/* Running total of kernels this library has launched in the process (all handles). */
+int64_t bipart_kernel_launches(void);
+
+/* Per-kernel timing: while enabled, the library brackets the launches of its main kernels with
+ * CUDA events on the launching stream and accumulates, per kernel name, the number of launches,
+ * their summed device time and their summed algorithmic bytes (the bytes the algorithm must move:
+ * each array streamed once, gathers at element size).  Enabling or disabling resets the totals. */
+int bipart_profile_enable(int on);
+
+/* Reads entry `idx` of the per-kernel totals (finishes pending timing first).  Returns the number
+ * of entries, or INVALID_ARG for an index out of range (idx = -1 only returns the count).
+ * `name` receives at most name_len bytes including the terminating zero. */
+int bipart_profile_read(int32_t idx, char *name, size_t name_len, int64_t *launches,
+                        double *total_ms, double *total_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BIPART_H */

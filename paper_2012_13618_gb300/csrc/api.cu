@@ -1,0 +1,750 @@
+// C ABI of the library (include/bipart.h): handle life cycle, input validation, the multilevel
+// driver of Sec. 3.4 and the nested k-way recursion of Algorithm 6 (Sec. 3.5).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+#include "scan.cuh"
+
+namespace bp {
+
+namespace {
+thread_local std::string g_last_error;
+bipart_alloc_fn g_alloc = nullptr;
+bipart_free_fn g_free = nullptr;
+void *g_alloc_ctx = nullptr;
+constexpr int kBlock = 256;
+constexpr size_t kSmallBytes = 64 * 1024;
+
+inline int grid_for(int64_t n, int per_block = kBlock, int cap = 152 * 16) {
+    int64_t b = (n + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    return (int)std::min<int64_t>(b, cap);
+}
+}  // namespace
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+void *dev_alloc(size_t bytes, cudaStream_t s) {
+    if (g_alloc) return g_alloc(g_alloc_ctx, bytes, (void *)s);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(void *p, size_t bytes, cudaStream_t s) {
+    if (!p) return;
+    if (g_free) g_free(g_alloc_ctx, p, bytes, (void *)s);
+    else cudaFreeAsync(p, s);
+}
+
+uint32_t *dev_status(bipart_graph *g) { return g->w.status.as<uint32_t>(); }
+
+void sync(bipart_graph *g) { BP_CUDA(cudaStreamSynchronize(g->stream)); }
+
+void check_status(bipart_graph *g) {
+    uint32_t st = 0;
+    BP_CUDA(cudaMemcpy(&st, dev_status(g), sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (st & DEV_TIMEOUT) throw Fail{BIPART_ERR_TIMEOUT, "a bounded device-side wait expired"};
+    if (st & DEV_OVERFLOW) throw Fail{BIPART_ERR_OOM, "a device-side size limit was exceeded"};
+}
+
+// ------------------------------------------------------------------------- validation kernels
+__global__ void k_validate(int N, int E, int P, const int *__restrict__ hoff,
+                           const int *__restrict__ pins, const int *__restrict__ nw,
+                           const int *__restrict__ hw, unsigned *__restrict__ bad,
+                           unsigned long long *__restrict__ sums) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    unsigned b = 0;
+    unsigned long long sn = 0, se = 0;
+    if (tid == 0 && hoff[0] != 0) b |= 1;
+    for (int e = tid; e < E; e += nt) {
+        if (hoff[e + 1] < hoff[e]) b |= 1;
+        if (hw) {
+            if (hw[e] < 1) b |= 4;
+            se += (unsigned)max(hw[e], 0);
+        }
+    }
+    for (int i = tid; i < P; i += nt)
+        if (pins[i] < 0 || pins[i] >= N) b |= 2;
+    for (int v = tid; v < N; v += nt) {
+        if (nw) {
+            if (nw[v] < 1) b |= 4;
+            sn += (unsigned)max(nw[v], 0);
+        } else {
+            sn += 1;
+        }
+    }
+    if (b) atomicOr(bad, b);
+    sn = warp_sum(sn);
+    se = warp_sum(se);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&sums[0], sn);
+        atomicAdd(&sums[1], se);
+    }
+}
+
+__global__ void k_weight_sum(int N, const int *__restrict__ nw, unsigned long long *out) {
+    unsigned long long s = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) s += nw[v];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+__global__ void k_side_to_part(int N, const uint8_t *__restrict__ side, const int *__restrict__ l2g,
+                               int base, int *__restrict__ part) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        int v = l2g ? l2g[i] : i;
+        part[v] = base + side[i];
+    }
+}
+
+// ------------------------------------------------------------------------- subgraph extraction
+// Reading of Algorithm 6's subgraphs (net splitting): nodes of part j renumbered in ascending id;
+// every hyperedge restricted to them kept when it has >= 2 pins, in ascending id, weight carried.
+struct SubNodeIn {
+    const int *part;
+    int j;
+    __device__ uint64_t operator()(int64_t v) const { return part[v] == j ? 1ull : 0ull; }
+};
+struct SubNodeOut {
+    int64_t n;
+    const int *nw;
+    int *loc, *l2g, *sub_nw, *n_out;
+    __device__ void operator()(int64_t v, uint64_t pre, uint64_t val) const {
+        if (val) {
+            loc[v] = (int)pre;
+            l2g[pre] = (int)v;
+            sub_nw[pre] = nw[v];
+        } else {
+            loc[v] = -1;
+        }
+        if (v == n - 1) *n_out = (int)(pre + val);
+    }
+};
+
+__global__ void __launch_bounds__(kBlock)
+k_sub_count(int E, const int *__restrict__ hoff, const int *__restrict__ pins,
+            const int *__restrict__ loc, int *__restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    // hyperedges of degree <= 32: one thread; larger ones: the warp handles them cooperatively
+    for (int e0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; e0 < E; e0 += warps * 32) {
+        int e = e0 + lane;
+        int a = 0, d = 0;
+        if (e < E) { a = hoff[e]; d = hoff[e + 1] - a; }
+        bool small = e < E && d <= 32;
+        if (small) {
+            int c = 0;
+            for (int i = 0; i < d; ++i) c += loc[pins[a + i]] >= 0;
+            cnt[e] = c;
+        }
+        unsigned bigmask = __ballot_sync(0xffffffffu, e < E && !small);
+        while (bigmask) {
+            int src = __ffs(bigmask) - 1;
+            bigmask &= bigmask - 1;
+            int eb = e0 + src;
+            int ab = hoff[eb], db = hoff[eb + 1] - ab;
+            int c = 0;
+            for (int i = lane; i < db; i += 32) c += loc[pins[ab + i]] >= 0;
+            c = warp_sum(c);
+            if (lane == 0) cnt[eb] = c;
+        }
+    }
+}
+
+struct SubEdgeIn {
+    const int *cnt;
+    __device__ uint64_t operator()(int64_t e) const {
+        int c = cnt[e];
+        return c >= 2 ? ((1ull << 31) | (uint64_t)c) : 0ull;
+    }
+};
+struct SubEdgeOut {
+    int64_t n;
+    const int *hw;
+    int *hoff_out, *hw_out, *emap, *sizes;
+    __device__ void operator()(int64_t e, uint64_t pre, uint64_t val) const {
+        if (val) {
+            int ei = (int)(pre >> 31);
+            hoff_out[ei] = (int)(pre & 0x7fffffffu);
+            if (hw_out) hw_out[ei] = hw[e];
+            emap[e] = ei;
+        } else {
+            emap[e] = -1;
+        }
+        if (e == n - 1) {
+            uint64_t t = pre + val;
+            hoff_out[(int)(t >> 31)] = (int)(t & 0x7fffffffu);
+            sizes[0] = (int)(t >> 31);
+            sizes[1] = (int)(t & 0x7fffffffu);
+        }
+    }
+};
+
+__global__ void __launch_bounds__(kBlock)
+k_sub_copy(int E, const int *__restrict__ hoff, const int *__restrict__ pins,
+           const int *__restrict__ loc, const int *__restrict__ emap,
+           const int *__restrict__ hoff_out, int *__restrict__ pins_out) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int e0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; e0 < E; e0 += warps * 32) {
+        int e = e0 + lane;
+        int a = 0, d = 0, ee = -1;
+        if (e < E) { a = hoff[e]; d = hoff[e + 1] - a; ee = emap[e]; }
+        bool small = ee >= 0 && d <= 32;
+        if (small) {
+            int o = hoff_out[ee];
+            for (int i = 0; i < d; ++i) {
+                int x = loc[pins[a + i]];
+                if (x >= 0) pins_out[o++] = x;
+            }
+        }
+        unsigned bigmask = __ballot_sync(0xffffffffu, ee >= 0 && d > 32);
+        while (bigmask) {
+            int src = __ffs(bigmask) - 1;
+            bigmask &= bigmask - 1;
+            int eb = e0 + src;
+            int ab = hoff[eb], db = hoff[eb + 1] - ab;
+            int o = hoff_out[emap[eb]];
+            for (int i0 = 0; i0 < db; i0 += 32) {
+                int i = i0 + lane;
+                int x = i < db ? loc[pins[ab + i]] : -1;
+                unsigned m = __ballot_sync(0xffffffffu, x >= 0);
+                if (x >= 0) pins_out[o + __popc(m & ((1u << lane) - 1))] = x;
+                o += __popc(m);
+            }
+        }
+    }
+}
+
+namespace {
+
+int64_t node_weight_sum(bipart_graph *g, Level &L) {
+    cudaStream_t s = g->stream;
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(g->w.small.as<char>() + 48 * 1024 + 256);
+    BP_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long), s));
+    if (L.N > 0) {
+        k_weight_sum<<<grid_for(L.N), kBlock, 0, s>>>(L.N, L.nw(), d);
+        BP_LAUNCH();
+    }
+    unsigned long long hres = 0;
+    BP_CUDA(cudaMemcpyAsync(g->w.host_small, d, sizeof(hres), cudaMemcpyDeviceToHost, s));
+    sync(g);
+    std::memcpy(&hres, g->w.host_small, sizeof(hres));
+    return (int64_t)hres;
+}
+
+// Builds the subgraph of part j of level 0 into g->sub0; node map into g->l2g.
+void extract_subgraph(bipart_graph *g, const int *d_part, int j) {
+    cudaStream_t s = g->stream;
+    Level &L = g->L0;
+    Level &S = g->sub0;
+    Work &w = g->w;
+    int *loc = (int *)w.n_c.ensure(sizeof(int) * (size_t)std::max(L.N, 1), s);
+    int *l2g = (int *)g->l2g.ensure(sizeof(int) * (size_t)std::max(L.N, 1), s);
+    S.b_nw.ensure(sizeof(int) * (size_t)std::max(L.N, 1), s);
+    int *small = w.small.as<int>();
+    BP_CUDA(cudaMemsetAsync(small, 0, 8 * sizeof(int), s));
+    scan(L.N, SubNodeIn{d_part, j}, SubNodeOut{L.N, L.nw(), loc, l2g, S.nw(), small + 4},
+         w.scan.ensure(scan_state_bytes(L.N), s), dev_status(g), s);
+    int *cnt = (int *)w.e_a.ensure(sizeof(int) * (size_t)std::max(L.E, 1), s);
+    int *emap = (int *)w.e_b.ensure(sizeof(int) * (size_t)std::max(L.E, 1), s);
+    S.unit_hw = L.unit_hw;
+    S.b_hoff.ensure(sizeof(int) * ((size_t)L.E + 1), s);
+    S.b_pins.ensure(sizeof(int) * (size_t)std::max(L.P, 1), s);
+    if (!S.unit_hw) S.b_hw.ensure(sizeof(int) * (size_t)std::max(L.E, 1), s);
+    if (L.E > 0) {
+        int gw = grid_for((int64_t)(L.E + 31) / 32 * 32);
+        k_sub_count<<<gw, kBlock, 0, s>>>(L.E, L.hoff(), L.pins(), loc, cnt);
+        BP_LAUNCH();
+        scan(L.E, SubEdgeIn{cnt}, SubEdgeOut{L.E, L.hw(), S.hoff(), S.unit_hw ? nullptr : S.b_hw.as<int>(), emap, small + 2},
+             w.scan.ensure(scan_state_bytes(L.E), s), dev_status(g), s);
+        k_sub_copy<<<gw, kBlock, 0, s>>>(L.E, L.hoff(), L.pins(), loc, emap, S.hoff(), S.pins());
+        BP_LAUNCH();
+    } else {
+        BP_CUDA(cudaMemsetAsync(S.hoff(), 0, sizeof(int), s));
+    }
+    BP_CUDA(cudaMemcpyAsync(w.host_small, small, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    sync(g);
+    check_status(g);
+    S.N = L.N > 0 ? (int)w.host_small[4] : 0;
+    S.E = L.E > 0 ? (int)w.host_small[2] : 0;
+    S.P = L.E > 0 ? (int)w.host_small[3] : 0;
+    build_incidence(g, S);
+    S.b_cmap.ensure(sizeof(int) * (size_t)std::max(S.N, 1), s);
+    S.b_match.ensure(sizeof(int) * (size_t)std::max(S.N, 1), s);
+}
+
+// Sec. 3.4: coarsen until `levels` levels exist or the node count stops changing (reading C11),
+// then initial partition + refinement back to level 0.  Coarse levels live in g->lev.
+int bisect(bipart_graph *g, Level &L0, const Params &p, int64_t W, uint8_t *d_side, int *nlev) {
+    std::vector<Level *> levels{&L0};
+    while ((int)levels.size() - 1 < p.levels) {
+        Level &f = *levels.back();
+        if (f.E == 0) break;  // with no hyperedge nothing merges: N' == N
+        size_t idx = levels.size() - 1;
+        if (g->lev.size() <= idx) g->lev.emplace_back(new Level);
+        Level &c = *g->lev[idx];
+        coarsen_level(g, f, c, p.policy);
+        if (c.N == f.N) break;
+        levels.push_back(&c);
+    }
+    if (nlev) *nlev = (int)levels.size();
+    const int64_t limit = balance_limit(W, p.eps);
+    return uncoarsen(g, levels, limit, p.iters, d_side);
+}
+
+int partition_device(bipart_graph *g, const Params &p, int *d_parts) {
+    cudaStream_t s = g->stream;
+    Level &L = g->L0;
+    g->hier.valid = false;
+    if (L.N == 0) return BIPART_OK;
+    if (p.k == 1) {
+        BP_CUDA(cudaMemsetAsync(d_parts, 0, sizeof(int) * (size_t)L.N, s));
+        return BIPART_OK;
+    }
+    Buf side_out;
+    uint8_t *d_side = (uint8_t *)side_out.ensure((size_t)L.N, s);
+    int status = BIPART_OK;
+    int nlev = 0;
+    int st = bisect(g, L, p, g->total_node_weight, d_side, &nlev);
+    if (st != BIPART_OK) status = st;
+    k_side_to_part<<<grid_for(L.N), kBlock, 0, s>>>(L.N, d_side, nullptr, 0, d_parts);
+    BP_LAUNCH();
+    if (p.k == 2) {
+        g->hier.nlev = nlev;
+        g->hier.valid = true;
+        sync(g);
+        return status;
+    }
+    // nested k-way (Algorithm 6): tree level by tree level, every part bisected as a subgraph
+    int *pa = (int *)g->part_a.ensure(sizeof(int) * (size_t)L.N, s);
+    BP_CUDA(cudaMemcpyAsync(pa, d_parts, sizeof(int) * (size_t)L.N, cudaMemcpyDeviceToDevice, s));
+    for (int parts = 2; parts < p.k; parts *= 2) {
+        for (int j = 0; j < parts; ++j) {
+            extract_subgraph(g, pa, j);
+            Level &S = g->sub0;
+            if (S.N == 0) continue;
+            int64_t Wj = node_weight_sum(g, S);
+            uint8_t *ds = (uint8_t *)side_out.ensure((size_t)S.N, s);
+            st = bisect(g, S, p, Wj, ds, nullptr);
+            if (st != BIPART_OK) status = st;
+            k_side_to_part<<<grid_for(S.N), kBlock, 0, s>>>(S.N, ds, g->l2g.as<int>(), 2 * j, d_parts);
+            BP_LAUNCH();
+        }
+        BP_CUDA(cudaMemcpyAsync(pa, d_parts, sizeof(int) * (size_t)L.N, cudaMemcpyDeviceToDevice, s));
+    }
+    sync(g);
+    return status;
+}
+
+void validate_params(int32_t k, double eps, int32_t policy, int32_t levels, int32_t iters) {
+    if (k < 1 || (k & (k - 1)) != 0) throw Fail{BIPART_ERR_INVALID_ARG, "k must be a power of two >= 1"};
+    if (!(eps >= 0.0 && eps <= 1000.0)) throw Fail{BIPART_ERR_INVALID_ARG, "epsilon must be in [0, 1000]"};
+    if (policy < BIPART_POLICY_LDH || policy > BIPART_POLICY_RAND) throw Fail{BIPART_ERR_INVALID_ARG, "unknown policy"};
+    if (levels < 0) throw Fail{BIPART_ERR_INVALID_ARG, "levels must be >= 0"};
+    if (iters < 0) throw Fail{BIPART_ERR_INVALID_ARG, "refine_iters must be >= 0"};
+}
+
+void validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t *pins,
+                       const int32_t *nw, const int32_t *hw) {
+    if (N < 0 || E < 0) throw Fail{BIPART_ERR_INVALID_ARG, "negative size"};
+    if (E > 0 && !hoff) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_offsets is NULL"};
+    if (hoff && hoff[0] != 0) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets[0] != 0"};
+    for (int32_t e = 0; e < E; ++e)
+        if (hoff[e + 1] < hoff[e]) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets not non-decreasing at " + std::to_string(e)};
+    const int32_t P = E > 0 ? hoff[E] : 0;
+    if (P > 0 && !pins) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_pins is NULL"};
+    for (int32_t i = 0; i < P; ++i)
+        if (pins[i] < 0 || pins[i] >= N) throw Fail{BIPART_ERR_INVALID_CSR, "pin " + std::to_string(i) + " out of range"};
+    int64_t sn = 0, se = 0;
+    if (nw) {
+        for (int32_t v = 0; v < N; ++v) {
+            if (nw[v] < 1) throw Fail{BIPART_ERR_INVALID_CSR, "node weight < 1"};
+            sn += nw[v];
+        }
+    } else {
+        sn = N;
+    }
+    if (hw) {
+        for (int32_t e = 0; e < E; ++e) {
+            if (hw[e] < 1) throw Fail{BIPART_ERR_INVALID_CSR, "hyperedge weight < 1"};
+            se += hw[e];
+        }
+    }
+    if (sn >= (int64_t(1) << 31) || se >= (int64_t(1) << 31))
+        throw Fail{BIPART_ERR_INVALID_CSR, "weight sum must stay below 2^31"};
+}
+
+bipart_graph *new_graph(cudaStream_t s) {
+    std::unique_ptr<bipart_graph> g(new bipart_graph);
+    BP_CUDA(cudaGetDevice(&g->device));
+    g->stream = s;
+    g->w.status.ensure(64, s);
+    g->w.small.ensure(kSmallBytes, s);
+    BP_CUDA(cudaMemsetAsync(g->w.status.p, 0, 64, s));
+    BP_CUDA(cudaMallocHost(&g->w.host_small, 4096));
+    return g.release();
+}
+
+void finish_create(bipart_graph *g, int32_t N, int32_t E, const int *d_hoff, const int *d_pins,
+                   const int *d_nw, const int *d_hw) {
+    build_level0(g, g->L0, N, E, d_hoff, d_pins, d_nw, d_hw);
+    g->total_node_weight = node_weight_sum(g, g->L0);
+    sync(g);
+    check_status(g);
+}
+
+template <class F>
+int guard(F &&f) {
+    try {
+        return f();
+    } catch (const Fail &e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return BIPART_ERR_OOM;
+    } catch (...) {
+        set_error("unexpected exception");
+        return BIPART_ERR_CUDA;
+    }
+}
+
+}  // namespace
+
+}  // namespace bp
+
+using namespace bp;
+
+extern "C" {
+
+int bipart_set_allocator(bipart_alloc_fn alloc, bipart_free_fn free_fn, void *ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) {
+        set_error("alloc and free must both be set or both be NULL");
+        return BIPART_ERR_INVALID_ARG;
+    }
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_ctx = ctx;
+    return BIPART_OK;
+}
+
+const char *bipart_last_error(void) { return g_last_error.c_str(); }
+
+int bipart_create(int32_t num_nodes, int32_t num_hedges, const int32_t *hedge_offsets,
+                  const int32_t *hedge_pins, const int32_t *node_weights,
+                  const int32_t *hedge_weights, void *stream, bipart_handle *out) {
+    return guard([&]() {
+        if (!out) throw Fail{BIPART_ERR_INVALID_ARG, "out is NULL"};
+        *out = nullptr;
+        validate_host_csr(num_nodes, num_hedges, hedge_offsets, hedge_pins, node_weights, hedge_weights);
+        cudaStream_t s = (cudaStream_t)stream;
+        std::unique_ptr<bipart_graph> g(new_graph(s));
+        const int32_t E = num_hedges, N = num_nodes, P = E > 0 ? hedge_offsets[E] : 0;
+        Buf b_hoff, b_pins, b_nw, b_hw;
+        int *d_hoff = (int *)b_hoff.ensure(sizeof(int) * ((size_t)E + 1), s);
+        int *d_pins = (int *)b_pins.ensure(sizeof(int) * (size_t)std::max(P, 1), s);
+        int *d_nw = node_weights ? (int *)b_nw.ensure(sizeof(int) * (size_t)std::max(N, 1), s) : nullptr;
+        int *d_hw = hedge_weights ? (int *)b_hw.ensure(sizeof(int) * (size_t)std::max(E, 1), s) : nullptr;
+        if (E > 0) BP_CUDA(cudaMemcpyAsync(d_hoff, hedge_offsets, sizeof(int) * ((size_t)E + 1), cudaMemcpyHostToDevice, s));
+        if (P > 0) BP_CUDA(cudaMemcpyAsync(d_pins, hedge_pins, sizeof(int) * (size_t)P, cudaMemcpyHostToDevice, s));
+        if (d_nw && N > 0) BP_CUDA(cudaMemcpyAsync(d_nw, node_weights, sizeof(int) * (size_t)N, cudaMemcpyHostToDevice, s));
+        if (d_hw && E > 0) BP_CUDA(cudaMemcpyAsync(d_hw, hedge_weights, sizeof(int) * (size_t)E, cudaMemcpyHostToDevice, s));
+        finish_create(g.get(), N, E, E > 0 ? d_hoff : nullptr, d_pins, d_nw, d_hw);
+        *out = g.release();
+        return BIPART_OK;
+    });
+}
+
+int bipart_create_device(int32_t num_nodes, int32_t num_hedges, const int32_t *hedge_offsets,
+                         const int32_t *hedge_pins, const int32_t *node_weights,
+                         const int32_t *hedge_weights, void *stream, bipart_handle *out) {
+    return guard([&]() {
+        if (!out) throw Fail{BIPART_ERR_INVALID_ARG, "out is NULL"};
+        *out = nullptr;
+        if (num_nodes < 0 || num_hedges < 0) throw Fail{BIPART_ERR_INVALID_ARG, "negative size"};
+        if (num_hedges > 0 && !hedge_offsets) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_offsets is NULL"};
+        cudaStream_t s = (cudaStream_t)stream;
+        std::unique_ptr<bipart_graph> g(new_graph(s));
+        const int32_t E = num_hedges, N = num_nodes;
+        int32_t P = 0;
+        if (E > 0) {
+            BP_CUDA(cudaMemcpyAsync(g->w.host_small, hedge_offsets + E, sizeof(int), cudaMemcpyDeviceToHost, s));
+            sync(g.get());
+            P = (int32_t)g->w.host_small[0];
+            if (P < 0) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets[E] < 0"};
+            if (P > 0 && !hedge_pins) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_pins is NULL"};
+        }
+        unsigned *bad = reinterpret_cast<unsigned *>(g->w.small.as<char>() + 48 * 1024);
+        unsigned long long *sums = reinterpret_cast<unsigned long long *>(g->w.small.as<char>() + 48 * 1024 + 16);
+        BP_CUDA(cudaMemsetAsync(bad, 0, 64, s));
+        if (E > 0 || N > 0) {
+            k_validate<<<grid_for(std::max<int64_t>({(int64_t)N, (int64_t)E, (int64_t)P})), kBlock, 0, s>>>(
+                N, E, P, hedge_offsets, hedge_pins, node_weights, hedge_weights, bad, sums);
+            BP_LAUNCH();
+        }
+        BP_CUDA(cudaMemcpyAsync(g->w.host_small, bad, 64, cudaMemcpyDeviceToHost, s));
+        sync(g.get());
+        unsigned b = g->w.host_small[0];
+        unsigned long long hs[2];
+        std::memcpy(hs, g->w.host_small + 4, sizeof(hs));
+        if (b & 1) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets malformed"};
+        if (b & 2) throw Fail{BIPART_ERR_INVALID_CSR, "pin out of range"};
+        if (b & 4) throw Fail{BIPART_ERR_INVALID_CSR, "weight < 1"};
+        if (hs[0] >= (1ull << 31) || hs[1] >= (1ull << 31)) throw Fail{BIPART_ERR_INVALID_CSR, "weight sum must stay below 2^31"};
+        finish_create(g.get(), N, E, hedge_offsets, hedge_pins, node_weights, hedge_weights);
+        *out = g.release();
+        return BIPART_OK;
+    });
+}
+
+int bipart_set_stream(bipart_handle h, void *stream) {
+    if (!h) { set_error("handle is NULL"); return BIPART_ERR_INVALID_ARG; }
+    return guard([&]() {
+        BP_CUDA(cudaStreamSynchronize(h->stream));
+        h->stream = (cudaStream_t)stream;
+        return BIPART_OK;
+    });
+}
+
+int bipart_partition_device(bipart_handle h, int32_t k, double epsilon, int32_t policy,
+                            int32_t levels, int32_t refine_iters, int32_t *d_out_parts) {
+    if (!h) { set_error("handle is NULL"); return BIPART_ERR_INVALID_ARG; }
+    return guard([&]() {
+        validate_params(k, epsilon, policy, levels, refine_iters);
+        if (!d_out_parts && h->L0.N > 0) throw Fail{BIPART_ERR_INVALID_ARG, "out_parts is NULL"};
+        Params p{k, epsilon, policy, levels, refine_iters};
+        int st = partition_device(h, p, d_out_parts);
+        check_status(h);
+        return st;
+    });
+}
+
+int bipart_partition(bipart_handle h, int32_t k, double epsilon, int32_t policy, int32_t levels,
+                     int32_t refine_iters, int32_t *out_parts) {
+    if (!h) { set_error("handle is NULL"); return BIPART_ERR_INVALID_ARG; }
+    return guard([&]() {
+        validate_params(k, epsilon, policy, levels, refine_iters);
+        const int32_t N = h->L0.N;
+        if (!out_parts && N > 0) throw Fail{BIPART_ERR_INVALID_ARG, "out_parts is NULL"};
+        Params p{k, epsilon, policy, levels, refine_iters};
+        int *d = (int *)h->part_b.ensure(sizeof(int) * (size_t)std::max(N, 1), h->stream);
+        int st = partition_device(h, p, d);
+        if (N > 0) BP_CUDA(cudaMemcpyAsync(out_parts, d, sizeof(int) * (size_t)N, cudaMemcpyDeviceToHost, h->stream));
+        sync(h);
+        check_status(h);
+        return st;
+    });
+}
+
+int bipart_num_levels(bipart_handle h, int32_t *num_levels) {
+    if (!h || !num_levels) { set_error("NULL argument"); return BIPART_ERR_INVALID_ARG; }
+    if (!h->hier.valid) { set_error("no k = 2 hierarchy kept"); return BIPART_ERR_INVALID_ARG; }
+    *num_levels = h->hier.nlev;
+    return BIPART_OK;
+}
+
+__global__ void k_fill_i32(int n, int val, int *a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = val;
+}
+
+int bipart_get_level(bipart_handle h, int32_t level, int32_t *N, int32_t *E, int32_t *P,
+                     int32_t *hoff, int32_t *pins, int32_t *node_weights, int32_t *hedge_weights,
+                     int32_t *cmap, int32_t *match) {
+    if (!h) { set_error("handle is NULL"); return BIPART_ERR_INVALID_ARG; }
+    return guard([&]() {
+        int nlev = h->hier.valid ? h->hier.nlev : 1;
+        if (level < 0 || level >= nlev) throw Fail{BIPART_ERR_INVALID_ARG, "level out of range"};
+        Level &L = level == 0 ? h->L0 : *h->lev[level - 1];
+        cudaStream_t s = h->stream;
+        if (N) *N = L.N;
+        if (E) *E = L.E;
+        if (P) *P = L.P;
+        if (hoff) BP_CUDA(cudaMemcpyAsync(hoff, L.hoff(), sizeof(int) * ((size_t)L.E + 1), cudaMemcpyDeviceToHost, s));
+        if (pins && L.P > 0) BP_CUDA(cudaMemcpyAsync(pins, L.pins(), sizeof(int) * (size_t)L.P, cudaMemcpyDeviceToHost, s));
+        if (node_weights && L.N > 0) BP_CUDA(cudaMemcpyAsync(node_weights, L.nw(), sizeof(int) * (size_t)L.N, cudaMemcpyDeviceToHost, s));
+        bool coarsest = level == nlev - 1;
+        if (cmap && L.N > 0) {
+            if (coarsest) std::fill(cmap, cmap + L.N, -1);
+            else BP_CUDA(cudaMemcpyAsync(cmap, L.cmap(), sizeof(int) * (size_t)L.N, cudaMemcpyDeviceToHost, s));
+        }
+        if (match && L.N > 0) {
+            if (coarsest) std::fill(match, match + L.N, -1);
+            else BP_CUDA(cudaMemcpyAsync(match, L.match(), sizeof(int) * (size_t)L.N, cudaMemcpyDeviceToHost, s));
+        }
+        if (hedge_weights && L.E > 0) {
+            if (L.unit_hw) std::fill(hedge_weights, hedge_weights + L.E, 1);
+            else BP_CUDA(cudaMemcpyAsync(hedge_weights, L.b_hw.as<int>(), sizeof(int) * (size_t)L.E, cudaMemcpyDeviceToHost, s));
+        }
+        sync(h);
+        return BIPART_OK;
+    });
+}
+
+int bipart_sizes(bipart_handle h, int32_t *N, int32_t *E, int32_t *P) {
+    if (!h) { set_error("handle is NULL"); return BIPART_ERR_INVALID_ARG; }
+    if (N) *N = h->L0.N;
+    if (E) *E = h->L0.E;
+    if (P) *P = h->L0.P;
+    return BIPART_OK;
+}
+
+void bipart_destroy(bipart_handle h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    if (h->w.host_small) cudaFreeHost(h->w.host_small);
+    h->w.host_small = nullptr;
+    delete h;
+}
+
+}  // extern "C"
+
+// Cut evaluation reuses the sorted-unique kernels: lambda_e = number of distinct parts of e.
+namespace bp {
+void distinct_counts(bipart_graph *g, Level &L, const int *d_map, int *cnt);
+}
+
+__global__ void k_cut_sum(int E, const int *__restrict__ cnt, const int *__restrict__ hw,
+                          unsigned long long *out) {
+    unsigned long long s = 0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
+        s += (unsigned long long)(hw ? hw[e] : 1) * (unsigned long long)(cnt[e] - 1);
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+extern "C" int bipart_cut(bipart_handle h, const int32_t *parts, int64_t *cut) {
+    if (!h || !cut || (!parts && h->L0.N > 0)) { set_error("NULL argument"); return BIPART_ERR_INVALID_ARG; }
+    return guard([&]() {
+        Level &L = h->L0;
+        cudaStream_t s = h->stream;
+        *cut = 0;
+        if (L.E == 0) return BIPART_OK;
+        int *d = (int *)h->part_b.ensure(sizeof(int) * (size_t)std::max(L.N, 1), s);
+        BP_CUDA(cudaMemcpyAsync(d, parts, sizeof(int) * (size_t)L.N, cudaMemcpyHostToDevice, s));
+        int *cnt = (int *)h->w.e_a.ensure(sizeof(int) * (size_t)L.E, s);
+        distinct_counts(h, L, d, cnt);
+        unsigned long long *acc = reinterpret_cast<unsigned long long *>(h->w.small.as<char>() + 48 * 1024 + 128);
+        BP_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long), s));
+        k_cut_sum<<<grid_for(L.E), kBlock, 0, s>>>(L.E, cnt, L.hw(), acc);
+        BP_LAUNCH();
+        unsigned long long r = 0;
+        BP_CUDA(cudaMemcpyAsync(h->w.host_small, acc, sizeof(r), cudaMemcpyDeviceToHost, s));
+        sync(h);
+        std::memcpy(&r, h->w.host_small, sizeof(r));
+        *cut = (int64_t)r;
+        return BIPART_OK;
+    });
+}
+
+// ------------------------------------------------------------------------- diagnostics
+#include <atomic>
+#include <map>
+#include <mutex>
+
+namespace bp {
+namespace {
+std::atomic<long long> g_launches{0};
+struct ProfRec {
+    std::string name;
+    double bytes;
+    cudaEvent_t a, b;
+    cudaStream_t s;
+};
+struct ProfTot {
+    long long launches = 0;
+    double ms = 0, bytes = 0;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof_pending;
+std::vector<cudaEvent_t> g_prof_pool;
+std::map<std::string, ProfTot> g_prof_tot;
+
+cudaEvent_t prof_event() {
+    if (!g_prof_pool.empty()) {
+        cudaEvent_t e = g_prof_pool.back();
+        g_prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_drain() {
+    for (ProfRec &r : g_prof_pending) {
+        float ms = 0;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            ProfTot &t = g_prof_tot[r.name];
+            t.launches++;
+            t.ms += ms;
+            t.bytes += r.bytes;
+        }
+        g_prof_pool.push_back(r.a);
+        g_prof_pool.push_back(r.b);
+    }
+    g_prof_pending.clear();
+}
+}  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+ProfScope::ProfScope(const char *name, double bytes, cudaStream_t s) {
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfRec r{name, bytes, prof_event(), prof_event(), s};
+    cudaEventRecord(r.a, s);
+    g_prof_pending.push_back(r);
+    slot = (int)g_prof_pending.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (slot < (int)g_prof_pending.size()) cudaEventRecord(g_prof_pending[slot].b, g_prof_pending[slot].s);
+    if (g_prof_pending.size() > 4096) prof_drain();
+}
+}  // namespace bp
+
+extern "C" int64_t bipart_kernel_launches(void) { return (int64_t)bp::g_launches.load(); }
+
+extern "C" int bipart_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(bp::g_prof_mu);
+    bp::prof_drain();
+    bp::g_prof_tot.clear();
+    bp::g_prof_on = on != 0;
+    return BIPART_OK;
+}
+
+extern "C" int bipart_profile_read(int32_t idx, char *name, size_t name_len, int64_t *launches,
+                                   double *total_ms, double *total_bytes) {
+    std::lock_guard<std::mutex> lk(bp::g_prof_mu);
+    bp::prof_drain();
+    int n = (int)bp::g_prof_tot.size();
+    if (idx < 0) return n;
+    if (idx >= n) { bp::set_error("profile index out of range"); return BIPART_ERR_INVALID_ARG; }
+    auto it = bp::g_prof_tot.begin();
+    std::advance(it, idx);
+    if (name && name_len) {
+        std::strncpy(name, it->first.c_str(), name_len - 1);
+        name[name_len - 1] = 0;
+    }
+    if (launches) *launches = it->second.launches;
+    if (total_ms) *total_ms = it->second.ms;
+    if (total_bytes) *total_bytes = it->second.bytes;
+    return n;
+}

@@ -1,0 +1,159 @@
+// Shared device helpers of the sm_103a path: error plumbing, the matching hash, warp/block
+// reductions and the bounded spin-wait used by every cross-block handshake.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "bipart.h"
+
+namespace bp {
+
+// Status word shared by kernels that can fail at run time (bounded waits, size overflows).
+enum DevErr : uint32_t { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_OVERFLOW = 2 };
+
+// Spin limit of every device-side wait: after this many polls the waiting thread records
+// DEV_TIMEOUT in the status word and carries on with a defined (wrong) value, so the kernel
+// always terminates and the host reports BIPART_ERR_TIMEOUT.
+constexpr int kSpinLimit = 1 << 22;
+
+void set_error(const std::string &msg);
+
+struct Fail {
+    int code;
+    std::string msg;
+};
+
+#define BP_CUDA(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            throw ::bp::Fail{BIPART_ERR_CUDA, std::string(#call) + ": " +                    \
+                                                  cudaGetErrorString(e_)};                  \
+    } while (0)
+
+void note_launch();
+
+#define BP_LAUNCH()                                                                         \
+    do {                                                                                    \
+        ::bp::note_launch();                                                                \
+        cudaError_t e_ = cudaGetLastError();                                                \
+        if (e_ != cudaSuccess)                                                              \
+            throw ::bp::Fail{BIPART_ERR_CUDA, std::string("kernel launch at ") + __FILE__ + \
+                                                  ":" + std::to_string(__LINE__) + ": " +   \
+                                                  cudaGetErrorString(e_)};                  \
+    } while (0)
+
+// Matching hash (reading of Algorithm 1's hash(hedge.id)): the 32-bit finaliser of
+// MurmurHash3 (Appleby), a bijection of 32-bit integers, so (priority, hash) is unique per
+// hyperedge and the three atomicMin passes of Algorithm 1 collapse into one 64-bit minimum.
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x85ebca6bu;
+    x ^= x >> 13;
+    x *= 0xc2b2ae35u;
+    x ^= x >> 16;
+    return x;
+}
+
+// Table 1 priorities as a "smaller is preferred" 32-bit value.
+__host__ __device__ __forceinline__ uint32_t policy_priority(int policy, uint32_t deg,
+                                                             uint32_t w, uint32_t hash) {
+    switch (policy) {
+        case BIPART_POLICY_LDH: return deg;
+        case BIPART_POLICY_HDH: return 0xFFFFFFFFu - deg;
+        case BIPART_POLICY_LWD: return w;
+        case BIPART_POLICY_HWD: return 0xFFFFFFFFu - w;
+        default: return hash;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_min(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        T u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u < v ? u : v;
+    }
+    return v;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        T u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u > v ? u : v;
+    }
+    return v;
+}
+
+// Inclusive warp scan.
+template <class T>
+__device__ __forceinline__ T warp_inclusive_scan(T v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Block-wide sum; `red` must hold >= 32 entries; all threads receive the total.
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    T t = lane < nw ? red[lane] : T(0);
+    if (wid == 0) t = warp_sum(t);
+    if (threadIdx.x == 0) red[0] = t;
+    __syncthreads();
+    T r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// Block-wide exclusive scan; returns this thread's exclusive prefix, total in *total.
+template <class T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T *red, T *total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    T inc = warp_inclusive_scan(v);
+    __syncthreads();
+    if (lane == 31 || threadIdx.x == blockDim.x - 1) red[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        T t = lane < nw ? red[lane] : T(0);
+        T ti = warp_inclusive_scan(t);
+        if (lane < nw) red[lane] = ti - t;
+        if (lane == nw - 1) red[32] = ti;
+    }
+    __syncthreads();
+    T r = red[wid] + inc - v;
+    *total = red[32];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void record_error(uint32_t *status, uint32_t code) {
+    if (status) atomicOr(status, code);
+}
+
+inline int ceil_div_i(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace bp

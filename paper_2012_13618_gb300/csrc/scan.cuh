@@ -1,0 +1,114 @@
+// Single-pass device-wide exclusive scan (decoupled look-back, Merrill & Garland 2016) over
+// 62-bit unsigned values produced on the fly by an input functor and consumed by an output
+// functor.  Callers pack two counters into one value (high field << 31 | low field) when both
+// stay below 2^31; the sum then never carries between fields.
+//
+// Tile states are 64-bit words: bits 62-63 hold the flag (0 = not ready, 1 = tile aggregate,
+// 2 = inclusive prefix) and bits 0-61 the value, so one aligned store publishes both.  Tiles take
+// their index from an atomic counter in launch order, so every tile only waits on tiles that
+// already run; each wait is bounded by kSpinLimit polls and reports DEV_TIMEOUT on expiry.
+#pragma once
+
+#include "common.cuh"
+
+namespace bp {
+
+constexpr int kScanBlock = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanBlock * kScanItems;
+constexpr uint64_t kScanValMask = (1ull << 62) - 1;
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagPre = 2ull << 62;
+
+// `state` points at [tile counter (64-bit slot), tile status words ...], zeroed before launch.
+template <class In, class Out>
+__global__ void __launch_bounds__(kScanBlock)
+k_scan(int64_t n, In in, Out out, unsigned long long *state, uint32_t *status) {
+    __shared__ uint64_t s_val[kScanTile];
+    __shared__ uint64_t s_pre[kScanTile];
+    __shared__ uint64_t red[33];
+    __shared__ uint32_t s_tile;
+    __shared__ uint64_t s_prefix;
+    unsigned long long *counter = state;
+    unsigned long long *tiles = state + 1;
+
+    if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile;
+
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k * kScanBlock + threadIdx.x;
+        s_val[k * kScanBlock + threadIdx.x] = i < n ? (uint64_t)in(i) : 0ull;
+    }
+    __syncthreads();
+    uint64_t loc[kScanItems];
+    uint64_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        loc[k] = s_val[threadIdx.x * kScanItems + k];
+        sum += loc[k];
+    }
+    uint64_t total;
+    uint64_t excl = block_exclusive_scan<uint64_t>(sum, red, &total);
+
+    if (threadIdx.x == 0) {
+        uint64_t prefix = 0;
+        if (tile == 0) {
+            atomicExch(&tiles[0], (unsigned long long)(kFlagPre | (total & kScanValMask)));
+        } else {
+            atomicExch(&tiles[tile], (unsigned long long)(kFlagAgg | (total & kScanValMask)));
+            int64_t j = tile - 1;
+            while (j >= 0) {
+                uint64_t s = 0;
+                int spins = 0;
+                for (;;) {
+                    s = *((volatile unsigned long long *)&tiles[j]);
+                    if ((s >> 62) != 0) break;
+                    if (++spins > kSpinLimit) break;
+                    if (spins > 64) __nanosleep(64);
+                }
+                if ((s >> 62) == 0) {  // predecessor never published: give up, flag the error
+                    record_error(status, DEV_TIMEOUT);
+                    break;
+                }
+                prefix += s & kScanValMask;
+                if ((s >> 62) == 2) break;
+                --j;
+            }
+            atomicExch(&tiles[tile], (unsigned long long)(kFlagPre | ((prefix + total) & kScanValMask)));
+        }
+        s_prefix = prefix;
+    }
+    __syncthreads();
+    uint64_t run = s_prefix + excl;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        s_pre[threadIdx.x * kScanItems + k] = run;
+        run += loc[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k * kScanBlock + threadIdx.x;
+        if (i < n) out(i, s_pre[k * kScanBlock + threadIdx.x], s_val[k * kScanBlock + threadIdx.x]);
+    }
+}
+
+inline size_t scan_state_bytes(int64_t n) {
+    return sizeof(unsigned long long) * (size_t)(2 + (n + kScanTile - 1) / kScanTile);
+}
+
+// Launches the scan on `s`; `state` must hold scan_state_bytes(n).
+template <class In, class Out>
+void scan(int64_t n, In in, Out out, void *state, uint32_t *status, cudaStream_t s) {
+    if (n <= 0) return;
+    int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    BP_CUDA(cudaMemsetAsync(state, 0, scan_state_bytes(n), s));
+    k_scan<In, Out><<<(unsigned)tiles, kScanBlock, 0, s>>>(n, in, out,
+                                                             (unsigned long long *)state, status);
+    BP_LAUNCH();
+}
+
+}  // namespace bp

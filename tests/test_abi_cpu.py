@@ -1,0 +1,75 @@
+"""C ABI checks that need no GPU: the library builds for sm_103a, exports every declared symbol,
+and rejects malformed input on the host before any CUDA call."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2012_13618_gb300 as bp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "bipart.h")).read()
+    return sorted(set(re.findall(r"\b(bipart_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = bp.load()
+    names = declared_symbols()
+    assert "bipart_create" in names and "bipart_partition" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(bp.SYMBOLS), set(names) - set(bp.SYMBOLS)
+
+
+def _create_raw(N, hoff, pins, nw=None, hw=None):
+    lib = bp.load()
+    arr = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.int32)
+    hoff, pins, nw, hw = arr(hoff), arr(pins), arr(nw), arr(hw)
+    ptr = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)
+    out = ctypes.c_void_p()
+    rc = lib.bipart_create(N, hoff.size - 1, ptr(hoff), ptr(pins), ptr(nw), ptr(hw), None,
+                           ctypes.byref(out))
+    return rc, out
+
+
+@pytest.mark.parametrize("case", [
+    dict(N=4, hoff=[1, 2], pins=[0, 1]),                      # offsets[0] != 0
+    dict(N=4, hoff=[0, 3, 2], pins=[0, 1, 2]),                # decreasing offsets
+    dict(N=4, hoff=[0, 2], pins=[0, 4]),                      # pin out of range
+    dict(N=4, hoff=[0, 2], pins=[-1, 2]),                     # negative pin
+    dict(N=3, hoff=[0, 2], pins=[0, 1], nw=[1, 0, 1]),        # node weight < 1
+    dict(N=3, hoff=[0, 2], pins=[0, 1], hw=[0]),              # hyperedge weight < 1
+    dict(N=3, hoff=[0, 2], pins=[0, 1], nw=[2**30, 2**30, 1]),  # node weight sum >= 2^31
+])
+def test_create_rejects_malformed_csr(case):
+    rc, out = _create_raw(case["N"], case["hoff"], case["pins"], case.get("nw"), case.get("hw"))
+    assert rc == bp.ERR_INVALID_CSR
+    assert not out.value
+    assert bp.load().bipart_last_error()
+
+
+def test_null_arguments():
+    lib = bp.load()
+    hoff = np.array([0, 2], np.int32)
+    pins = np.array([0, 1], np.int32)
+    rc = lib.bipart_create(2, 1, ctypes.c_void_p(hoff.ctypes.data), ctypes.c_void_p(pins.ctypes.data),
+                           None, None, None, None)
+    assert rc == bp.ERR_INVALID_ARG
+    rc = lib.bipart_create(-1, 1, None, None, None, None, None, ctypes.byref(ctypes.c_void_p()))
+    assert rc == bp.ERR_INVALID_ARG
+    assert lib.bipart_partition(None, 2, 0.1, 0, 25, 2, None) == bp.ERR_INVALID_ARG
+    assert lib.bipart_cut(None, None, None) == bp.ERR_INVALID_ARG
+    lib.bipart_destroy(None)
+
+
+def test_valid_input_without_gpu_reports_cuda_error():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    rc, out = _create_raw(3, [0, 2, 3], [0, 1, 2])
+    assert rc == bp.ERR_CUDA and not out.value

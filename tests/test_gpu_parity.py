@@ -1,0 +1,175 @@
+"""Parity of the sm_103a path (through the C ABI) with the CPU oracle: every coarse level
+(hyperedge CSR, node and hyperedge weights, cmap, matching), the partition vector, the status and
+the cut must be identical -- the arithmetic is integer, so the tolerance is zero."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2012_13618_gb300 as bp
+    bp.use_torch_allocator()
+    yield
+
+
+def _bp():
+    import paper_2012_13618_gb300 as bp
+    return bp
+
+
+def compare_levels(h, ref):
+    assert h.num_levels() == ref["nlev"]
+    for l in range(ref["nlev"]):
+        a, b = h.get_level(l), ref["levels"][l]
+        assert (a["N"], a["E"], a["P"]) == (b["N"], b["E"], int(b["hoff"][-1])), l
+        for key in ("hoff", "pins", "nw", "hw"):
+            assert np.array_equal(a[key], b[key]), (l, key)
+        if l < ref["nlev"] - 1:
+            assert np.array_equal(a["match"], ref["matches"][l]), (l, "match")
+            assert np.array_equal(a["cmap"], ref["cmaps"][l]), (l, "cmap")
+
+
+def check_bisection(g, eps=0.1, policy="LDH", levels=25, iters=2, levels_too=True):
+    bp = _bp()
+    hr = oracle.Hypergraph.from_dict(g)
+    ref = oracle.bisect(hr, eps, policy, levels, iters, keep_levels=levels_too)
+    with bp.create_from(g) as h:
+        parts, st = h.partition(2, eps, policy, levels, iters)
+        if levels_too:
+            compare_levels(h, ref)
+        assert np.array_equal(parts, ref["side"].astype(np.int32))
+        assert st == ref["status"]
+        assert h.cut(parts) == oracle.cut(hr, parts)
+    return ref
+
+
+def random_graph(seed, N, E, dmax=6, weights=True, hweights=False, dup=True):
+    rng = np.random.default_rng(seed)
+    deg = rng.integers(0, dmax + 1, size=E)
+    hoff = np.zeros(E + 1, np.int32)
+    hoff[1:] = np.cumsum(deg)
+    pins = rng.integers(0, N, size=int(hoff[-1])).astype(np.int32)
+    if not dup:
+        raise NotImplementedError
+    nw = rng.integers(1, 6, size=N).astype(np.int32) if weights else None
+    hw = rng.integers(1, 5, size=E).astype(np.int32) if hweights else None
+    return dict(N=N, E=E, hoff=hoff, pins=pins, nw=nw, hw=hw)
+
+
+def test_smoke_small():
+    check_bisection(synth.uniform(500, 500, 2, 6, seed=1))
+
+
+@pytest.mark.parametrize("policy", ["LDH", "HDH", "LWD", "HWD", "RAND"])
+def test_c0_uniform_10k_all_policies(policy):
+    check_bisection(synth.c0_uniform(), 0.1, policy)
+
+
+@pytest.mark.parametrize("levels,iters", [(0, 2), (1, 0), (3, 1), (25, 5)])
+def test_c0_levels_iters(levels, iters):
+    check_bisection(synth.c0_uniform(), 0.1, "LDH", levels, iters)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_weighted_with_duplicates(seed):
+    g = random_graph(seed, 300 + 50 * seed, 400, dmax=7, weights=True, hweights=(seed % 2 == 1))
+    check_bisection(g, eps=[0.0, 0.05, 0.1, 0.3, 1.0, 0.02][seed], policy=["LDH", "HDH", "RAND",
+                    "LWD", "HWD", "LDH"][seed])
+
+
+def test_degenerate_inputs():
+    bp = _bp()
+    # no hyperedges at all: initial partition by id order, nothing else
+    check_bisection(dict(N=37, E=0, hoff=np.zeros(1, np.int32), pins=np.zeros(0, np.int32),
+                         nw=None, hw=None))
+    # only single-pin and empty hyperedges: all dropped at level 0
+    check_bisection(dict(N=10, E=4, hoff=np.array([0, 1, 1, 2, 3], np.int32),
+                         pins=np.array([3, 3, 9], np.int32), nw=None, hw=None))
+    # one node
+    check_bisection(dict(N=1, E=1, hoff=np.array([0, 1], np.int32), pins=np.array([0], np.int32),
+                         nw=None, hw=None))
+    # zero nodes
+    with bp.create(0, np.zeros(1, np.int32), np.zeros(0, np.int32)) as h:
+        parts, st = h.partition(2)
+        assert parts.size == 0 and st == 0
+    # k = 1
+    g = synth.uniform(100, 100, 2, 4, seed=3)
+    with bp.create_from(g) as h:
+        parts, st = h.partition(1)
+        assert st == 0 and not parts.any()
+
+
+def test_mid_and_big_degree_tiers():
+    # degrees across all tiers (<= 8 thread, 9..1024 warp, > 1024 block bitmap) and hyperedges
+    # whose ids span more than one 262,144-id bitmap window
+    rng = np.random.default_rng(7)
+    N = 700_000
+    degs = [2, 3, 8, 9, 31, 32, 33, 64, 65, 200, 511, 512, 513, 1024, 1025, 3000, 20000, 70000]
+    edges = []
+    for d in degs * 3:
+        edges.append(rng.choice(N, size=d, replace=False))
+    for _ in range(200_000):
+        edges.append(rng.choice(N, size=int(rng.integers(2, 5)), replace=False))
+    hoff = np.zeros(len(edges) + 1, np.int32)
+    hoff[1:] = np.cumsum([len(e) for e in edges])
+    pins = np.concatenate(edges).astype(np.int32)
+    g = dict(N=N, E=len(edges), hoff=hoff, pins=pins, nw=None, hw=None)
+    check_bisection(g, 0.1, "LDH")
+    check_bisection(g, 0.05, "HDH", levels=4)
+
+
+def test_deterministic_ten_runs():
+    bp = _bp()
+    g = synth.c1_netlist(N=50_000)
+    with bp.create_from(g) as h:
+        first, _ = h.partition(2, 0.05, "LDH", 25, 2)
+        for _ in range(9):
+            again, _ = h.partition(2, 0.05, "LDH", 25, 2)
+            assert np.array_equal(first, again)
+    with bp.create_from(g) as h2:
+        assert np.array_equal(first, h2.partition(2, 0.05, "LDH", 25, 2)[0])
+
+
+@pytest.mark.parametrize("k", [4, 8])
+def test_kway_small(k):
+    bp = _bp()
+    g = synth.uniform(3000, 3200, 2, 6, seed=21)
+    hr = oracle.Hypergraph.from_dict(g)
+    ref, rst = oracle.partition(hr, k, 0.1, "LDH", 25, 2)
+    with bp.create_from(g) as h:
+        parts, st = h.partition(k, 0.1, "LDH", 25, 2)
+        assert np.array_equal(parts, ref)
+        assert st == rst
+        assert h.cut(parts) == oracle.cut(hr, parts)
+
+
+def test_netlist_100k_kway16():
+    bp = _bp()
+    g = synth.c1_netlist(N=100_000)
+    hr = oracle.Hypergraph.from_dict(g)
+    ref, rst = oracle.partition(hr, 16, 0.05, "LDH", 25, 2)
+    with bp.create_from(g) as h:
+        parts, st = h.partition(16, 0.05, "LDH", 25, 2)
+        assert np.array_equal(parts, ref) and st == rst
+
+
+def test_c1_netlist_1m_full():
+    check_bisection(synth.c1_netlist(), 0.05, "LDH")
+
+
+def test_c2_rownet_reduced_k8():
+    bp = _bp()
+    g = synth.c2_rownet(rows=300_000)
+    hr = oracle.Hypergraph.from_dict(g)
+    ref, rst = oracle.partition(hr, 8, 0.05, "LDH", 25, 2)
+    with bp.create_from(g) as h:
+        parts, st = h.partition(8, 0.05, "LDH", 25, 2)
+        assert np.array_equal(parts, ref) and st == rst
