@@ -56,30 +56,41 @@ def dist_env():
 
 
 class Clocks:
-    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+    """Samples SM clocks and throttle reasons with nvidia-smi around the timed region.
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    The sampler starts before the timed region; only samples stamped inside it (widened to at
+    least one second around it, so short regions still get samples) are summarised."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.t0 = self.t1 = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
 
-    def __enter__(self):
+    def start(self):
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
-        return self
+        time.sleep(1.0)
 
-    def __exit__(self, *exc):
+    def mark_begin(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self):
         if self.proc:
+            time.sleep(0.5)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -88,23 +99,35 @@ class Clocks:
             self.f.close()
 
     def summary(self):
+        import datetime
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        lo, hi = self.t0, self.t1
+        if hi - lo < 1.0:
+            mid = 0.5 * (lo + hi)
+            lo, hi = mid - 0.5, mid + 0.5
         rows = []
         with open(self.path) as f:
             for line in f:
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    continue
+                if lo <= ts <= hi:
+                    rows.append(parts[1:])
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples in window"]}
+        num = lambda x: x.replace(".", "", 1).isdigit()
+        sm = [float(r[1]) for r in rows if num(r[1])]
+        mx = [float(r[2]) for r in rows if num(r[2])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(rows), "window_s": round(hi - lo, 3)}
 
 
 def load_workload():
@@ -208,16 +231,20 @@ def run_gpu(args):
     launches0 = bp.kernel_launches()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    clk = Clocks(local)
+    clk.start()
     barrier()
     torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        for i in range(args.steps):
-            flush_l2(flush)
-            ev[i][0].record(stream)
-            st = h.partition_device(out, k, eps, pol, lev, it)
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
+    clk.mark_begin()
+    for i in range(args.steps):
+        flush_l2(flush)
+        ev[i][0].record(stream)
+        st = h.partition_device(out, k, eps, pol, lev, it)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk.mark_end()
     barrier()
+    clk.stop()
     launches = bp.kernel_launches() - launches0
     prof = bp.profile_read()
     bp.profile_enable(False)

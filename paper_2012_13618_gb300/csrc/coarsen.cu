@@ -19,6 +19,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "lb.cuh"
 #include "scan.cuh"
 
 namespace bp {
@@ -371,53 +372,73 @@ __global__ void k_hedge_key(int E, int policy, const int *__restrict__ hoff,
 }
 
 // Every node takes the incident hyperedge with the smallest key (lexicographic (priority, hash);
-// the hash is a bijection so the key also identifies the hyperedge).  The sizes and weights of
-// the matched sets are integer sums, independent of the order of the atomics.
+// the hash is a bijection so the key also identifies the hyperedge).  Load-balanced over the
+// incidence array: per-node partial minima are combined with 64-bit atomicMin, whose result does
+// not depend on the order of the atomics.
+__global__ void __launch_bounds__(kLbBlock)
+k_match_min(int N, int P, const int *__restrict__ noff, const int *__restrict__ nadj,
+            const unsigned long long *__restrict__ hkey, unsigned long long *__restrict__ nkey) {
+    lb_for_each<unsigned long long>(
+        noff, N, P, ~0ull,
+        [&](int, int j, unsigned long long acc) {
+            unsigned long long k = __ldg(hkey + __ldg(nadj + j));
+            return k < acc ? k : acc;
+        },
+        [&](int v, unsigned long long acc) {
+            if (acc != ~0ull) atomicMin(nkey + v, acc);
+        });
+}
+
+// match[v] from the winning key; sizes and weights of the matched sets S(e) (integer atomics).
 __global__ void __launch_bounds__(kBlock)
-k_match(int N, const int *__restrict__ noff, const int *__restrict__ nadj,
-        const unsigned long long *__restrict__ hkey, const int *__restrict__ nw,
-        int *__restrict__ match, int *__restrict__ ssize, int *__restrict__ sweight) {
+k_match_set(int N, const unsigned long long *__restrict__ nkey, const int *__restrict__ nw,
+            int *__restrict__ match, int *__restrict__ ssize, int *__restrict__ sweight) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
-        unsigned long long best = ~0ull;
-        int be = -1;
-        for (int j = noff[v], j1 = noff[v + 1]; j < j1; ++j) {
-            int e = nadj[j];
-            unsigned long long k = hkey[e];
-            if (k < best) { best = k; be = e; }
-        }
-        match[v] = be;
-        if (be >= 0) {
-            atomicAdd(&ssize[be], 1);
-            atomicAdd(&sweight[be], nw[v]);
+        unsigned long long k = nkey[v];
+        int m = k == ~0ull ? -1 : (int)unmix32((uint32_t)k);
+        match[v] = m;
+        if (m >= 0) {
+            atomicAdd(&ssize[m], 1);
+            atomicAdd(&sweight[m], nw[v]);
         }
     }
 }
 
-// ------------------------------------------------------------------ Algorithm 2
-// grp[v] = matched hyperedge of v's final group, or -1 when v stays alone.  Singleton sets scan
-// their hyperedge for step-1 merged nodes (|S| >= 2) and pick the smallest (weight, group id).
-// rep[g] receives the smallest member of group g.
+// Algorithm 2, second loop, for every singleton set S(e) = {u}: the lightest step-1 merged node
+// among e's pins, as the key (merged weight << 32 | group id), minimum over e's pins.
+// Load-balanced over all pins; hyperedges that are not singleton sets are skipped.
+__global__ void __launch_bounds__(kLbBlock)
+k_single_best(int E, int P, const int *__restrict__ hoff, const int *__restrict__ pins,
+              const int *__restrict__ match, const int *__restrict__ ssize,
+              const int *__restrict__ sweight, unsigned long long *__restrict__ best) {
+    lb_for_each<unsigned long long>(
+        hoff, E, P, ~0ull,
+        [&](int e, int i, unsigned long long acc) {
+            if (__ldg(ssize + e) != 1) return acc;
+            int mv = __ldg(match + __ldg(pins + i));
+            if (mv >= 0 && __ldg(ssize + mv) >= 2) {
+                unsigned long long k = ((unsigned long long)(unsigned)__ldg(sweight + mv) << 32) | (unsigned)mv;
+                acc = k < acc ? k : acc;
+            }
+            return acc;
+        },
+        [&](int e, unsigned long long acc) {
+            if (acc != ~0ull) atomicMin(best + e, acc);
+        });
+}
+
+// grp[v] = matched hyperedge of v's final group, or -1 when v stays alone; rep[g] receives the
+// smallest member of group g.
 __global__ void __launch_bounds__(kBlock)
-k_group(int N, const int *__restrict__ hoff, const int *__restrict__ pins,
-        const int *__restrict__ match, const int *__restrict__ ssize,
-        const int *__restrict__ sweight, int *__restrict__ grp, unsigned *__restrict__ rep) {
+k_group(int N, const int *__restrict__ match, const int *__restrict__ ssize,
+        const unsigned long long *__restrict__ best, int *__restrict__ grp,
+        unsigned *__restrict__ rep) {
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < N; u += gridDim.x * blockDim.x) {
         int m = match[u];
         int g = -1;
         if (m >= 0) {
-            if (ssize[m] >= 2) {
-                g = m;
-            } else {
-                unsigned long long best = ~0ull;
-                for (int i = hoff[m], i1 = hoff[m + 1]; i < i1; ++i) {
-                    int mv = match[pins[i]];
-                    if (mv >= 0 && ssize[mv] >= 2) {
-                        unsigned long long k = ((unsigned long long)(unsigned)sweight[mv] << 32) | (unsigned)mv;
-                        if (k < best) best = k;
-                    }
-                }
-                if (best != ~0ull) g = (int)(best & 0xffffffffu);
-            }
+            if (ssize[m] >= 2) g = m;
+            else if (best[m] != ~0ull) g = (int)(best[m] & 0xffffffffu);
         }
         grp[u] = g;
         if (g >= 0) atomicMin(&rep[g], (unsigned)u);
@@ -604,15 +625,29 @@ void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy) {
         BP_CUDA(cudaMemsetAsync(rep, 0xff, sizeof(int) * (size_t)E, s));
     }
     if (N > 0) {
-        {
-            // noff, nadj, 8-byte key gather per pin, weights, match, two atomics per node
-            ProfScope ps("match", 20.0 * N + 12.0 * f.P, s);
-            k_match<<<grid_for(N), kBlock, 0, s>>>(N, f.noff(), f.nadj(), hkey, f.nw(), f.match(), ssize, sweight);
+        unsigned long long *nkey = (unsigned long long *)w.n_key.ensure(sizeof(uint64_t) * (size_t)N, s);
+        BP_CUDA(cudaMemsetAsync(nkey, 0xff, sizeof(uint64_t) * (size_t)N, s));
+        if (f.P > 0) {
+            // noff, nadj, 8-byte key gather per incidence, one 8-byte atomic per node run
+            ProfScope ps("match_min", 4.0 * N + 12.0 * f.P + 8.0 * N, s);
+            k_match_min<<<lb_grid(f.P), kLbBlock, 0, s>>>(N, f.P, f.noff(), f.nadj(), hkey, nkey);
             BP_LAUNCH();
         }
         {
-            ProfScope ps("group", 16.0 * N, s);
-            k_group<<<grid_for(N), kBlock, 0, s>>>(N, f.hoff(), f.pins(), f.match(), ssize, sweight, grp, rep);
+            ProfScope ps("match_set", 24.0 * N, s);
+            k_match_set<<<grid_for(N), kBlock, 0, s>>>(N, nkey, f.nw(), f.match(), ssize, sweight);
+            BP_LAUNCH();
+        }
+        unsigned long long *best = hkey;  // the hyperedge keys are no longer needed
+        BP_CUDA(cudaMemsetAsync(best, 0xff, sizeof(uint64_t) * (size_t)E, s));
+        if (f.P > 0) {
+            ProfScope ps("single_best", 4.0 * E + 4.0 * f.P, s);
+            k_single_best<<<lb_grid(f.P), kLbBlock, 0, s>>>(E, f.P, f.hoff(), f.pins(), f.match(), ssize, sweight, best);
+            BP_LAUNCH();
+        }
+        {
+            ProfScope ps("group", 20.0 * N, s);
+            k_group<<<grid_for(N), kBlock, 0, s>>>(N, f.match(), ssize, best, grp, rep);
             BP_LAUNCH();
         }
         {

@@ -59,6 +59,25 @@ __host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
     return x;
 }
 
+// Multiplicative inverse of an odd 32-bit constant modulo 2^32 (Newton iteration).
+constexpr uint32_t inv_odd32(uint32_t c) {
+    uint32_t x = c;  // correct to 3 bits for odd c; each step doubles the correct bits
+    for (int i = 0; i < 5; ++i) x *= 2u - c * x;
+    return x;
+}
+
+// Inverse of mix32: undoes each xorshift and multiplication in reverse order, so the matched
+// hyperedge can be read back from the low half of a winning (priority, hash) key.
+__host__ __device__ __forceinline__ uint32_t unmix32(uint32_t x) {
+    constexpr uint32_t i2 = inv_odd32(0xc2b2ae35u), i1 = inv_odd32(0x85ebca6bu);
+    x ^= x >> 16;
+    x *= i2;
+    x ^= (x >> 13) ^ (x >> 26);
+    x *= i1;
+    x ^= x >> 16;
+    return x;
+}
+
 // Table 1 priorities as a "smaller is preferred" 32-bit value.
 __host__ __device__ __forceinline__ uint32_t policy_priority(int policy, uint32_t deg,
                                                              uint32_t w, uint32_t hash) {

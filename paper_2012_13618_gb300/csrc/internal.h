@@ -88,6 +88,7 @@ struct Work {
     Buf e_a, e_b, e_c, e_d;  // per-hyperedge int32 scratch
     Buf e_key;       // per-hyperedge uint64 keys
     Buf n_a, n_b, n_c;       // per-node int32 scratch
+    Buf n_key;       // per-node uint64 keys
     Buf p_a;         // per-pin int32 scratch
     Buf side_a, side_b;      // uint8 sides (ping-pong across levels)
     Buf gain;        // int32 gains

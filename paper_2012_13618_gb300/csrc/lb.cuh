@@ -1,0 +1,67 @@
+// Load-balanced segmented reductions over a CSR (offsets off[0..nseg], items [0, total)).
+//
+// A block owns kLbTile consecutive items; each thread owns kLbItems consecutive items of that
+// tile, finds the segment of its first item by binary search inside the block's segment range
+// and walks forward.  Per-segment partial results are flushed with one atomic per segment run,
+// so a segment with 100,000 items costs the same per item as one with 2 items, and the result
+// does not depend on the schedule when the combining operation is an integer sum or minimum.
+#pragma once
+
+#include "common.cuh"
+
+namespace bp {
+
+constexpr int kLbBlock = 256;
+constexpr int kLbItems = 8;
+constexpr int kLbTile = kLbBlock * kLbItems;
+
+// Largest s in [lo, hi] with off[s] <= j (the non-empty segment holding item j).
+__device__ __forceinline__ int lb_seg(const int *__restrict__ off, int j, int lo, int hi) {
+    while (lo < hi) {
+        int m = (lo + hi + 1) >> 1;
+        if (__ldg(off + m) <= j) lo = m;
+        else hi = m - 1;
+    }
+    return lo;
+}
+
+// Visits the items of this thread in order as (segment, item index) and calls
+// flush(segment, acc) whenever the segment changes and at the end.  `init` is the identity of
+// the combine operation; visit(seg, item, acc) folds one item into acc.
+template <class Acc, class Visit, class Flush>
+__device__ __forceinline__ void lb_for_each(const int *__restrict__ off, int nseg, int total,
+                                            Acc init, Visit visit, Flush flush) {
+    __shared__ int s_rng[2];
+    for (int64_t t0 = (int64_t)blockIdx.x * kLbTile; t0 < total; t0 += (int64_t)gridDim.x * kLbTile) {
+        const int j0 = (int)t0;
+        const int j1 = (int)(t0 + kLbTile < total ? t0 + kLbTile : total);
+        __syncthreads();
+        if (threadIdx.x == 0) s_rng[0] = lb_seg(off, j0, 0, nseg - 1);
+        if (threadIdx.x == 32) s_rng[1] = lb_seg(off, j1 - 1, 0, nseg - 1);
+        __syncthreads();
+        int j = j0 + threadIdx.x * kLbItems;
+        if (j >= j1) continue;
+        const int je = j + kLbItems < j1 ? j + kLbItems : j1;
+        int s = lb_seg(off, j, s_rng[0], s_rng[1]);
+        int send = __ldg(off + s + 1);
+        Acc acc = init;
+        for (; j < je; ++j) {
+            while (j >= send) {  // next non-empty segment
+                flush(s, acc);
+                acc = init;
+                ++s;
+                send = __ldg(off + s + 1);
+            }
+            acc = visit(s, j, acc);
+        }
+        flush(s, acc);
+    }
+}
+
+inline int lb_grid(int64_t total, int cap = 152 * 8) {
+    int64_t b = (total + kLbTile - 1) / kLbTile;
+    if (b < 1) b = 1;
+    return (int)(b < cap ? b : cap);
+}
+
+}  // namespace bp

@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "lb.cuh"
 #include "scan.cuh"
 
 namespace bp {
@@ -115,17 +116,20 @@ __global__ void k_big_list(int E, const int *__restrict__ hoff, int *__restrict_
         if (hoff[e + 1] - hoff[e] > kWarpDeg) list[atomicAdd(count, 1)] = e;
 }
 
-__global__ void __launch_bounds__(kBlock)
-k_node_gain(int N, const int *__restrict__ noff, const int *__restrict__ nadj,
+// gain[v] = sum over v's hyperedges of the contribution for v's side; load-balanced over the
+// incidence array, per-node partial sums combined with integer atomicAdd (gain zeroed first).
+__global__ void __launch_bounds__(kLbBlock)
+k_node_gain(int N, int P, const int *__restrict__ noff, const int *__restrict__ nadj,
             const int2 *__restrict__ hc, const uint8_t *__restrict__ side, int *__restrict__ gain) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
-        int s = side[v], g = 0;
-        for (int j = noff[v], j1 = noff[v + 1]; j < j1; ++j) {
-            int2 c = hc[nadj[j]];
-            g += s ? c.y : c.x;
-        }
-        gain[v] = g;
-    }
+    lb_for_each<int>(
+        noff, N, P, 0,
+        [&](int v, int j, int acc) {
+            int2 c = __ldg(hc + __ldg(nadj + j));
+            return acc + (__ldg(side + v) ? c.y : c.x);
+        },
+        [&](int v, int acc) {
+            if (acc) atomicAdd(gain + v, acc);
+        });
 }
 
 // ------------------------------------------------------------------------ selection
@@ -439,10 +443,11 @@ void compute_gains(bipart_graph *g, const LevelCtx &lc, const uint8_t *side, int
             L.hoff(), L.pins(), L.hw(), side, lc.big_list, lc.big_count, hc);
         BP_LAUNCH();
     }
-    if (L.N > 0) {
-        // noff, nadj, 8-byte contribution gather per pin, side, gain
+    if (L.N > 0) BP_CUDA(cudaMemsetAsync(gain, 0, sizeof(int) * (size_t)L.N, s));
+    if (L.P > 0) {
+        // noff, nadj, 8-byte contribution gather per incidence, side, gain
         ProfScope ps("node_gain", 9.0 * L.N + 12.0 * L.P, s);
-        k_node_gain<<<grid_for(L.N), kBlock, 0, s>>>(L.N, L.noff(), L.nadj(), hc, side, gain);
+        k_node_gain<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.N, L.P, L.noff(), L.nadj(), hc, side, gain);
         BP_LAUNCH();
     }
 }
