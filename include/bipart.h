@@ -111,6 +111,26 @@ void bipart_destroy(bipart_handle h);
 /* Text of the last error on the calling thread ("" if none). */
 const char *bipart_last_error(void);
 
+/* Cut of a k-way partition computed without allocating any device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc when they need
+ * the cut -- a host application that gives all of HBM to its own memory pool up front (so an
+ * allocation by a library fails or breaks the pool's accounting), or a latency-critical loop that
+ * cannot afford the synchronisation an allocation may imply.
+ *   All arrays are DEVICE memory owned by the caller: a valid hyperedge -> pin CSR
+ *   (d_hedge_offsets[num_hedges + 1], d_hedge_pins), optional d_hedge_weights (NULL = unit),
+ *   d_parts[num_nodes] with values in [0, k), and the output d_cut (one int64).  Duplicate pins
+ *   and single-pin hyperedges are allowed (they do not change the cut).
+ *   Result: *d_cut = sum over hyperedges of w_e * (lambda_e - 1), written asynchronously on
+ *   `stream`; -1 if a pin or a part is out of range.
+ *   Limits: num_hedges <= 4,194,304 and 1 <= k <= 64, else BIPART_ERR_INVALID_ARG before any GPU
+ *   work.  Scratch is a fixed 16 MiB array inside the library's device image on every GPU that
+ *   loads it (kept until exit).  The first call on each device looks up that array's address
+ *   (make it before any stream capture).  All calls share the array: calls that overlap on the GPU
+ *   race and must be serialised by the caller. */
+int bipart_cut_noalloc(int32_t num_nodes, int32_t num_hedges, const int32_t *d_hedge_offsets,
+                       const int32_t *d_hedge_pins, const int32_t *d_hedge_weights,
+                       const int32_t *d_parts, int32_t k, int64_t *d_cut, void *stream);
+
 /* ---- Diagnostics (not part of the paper's method) ---------------------------------------- */
 /* Running total of kernels this library has launched in the process (all handles). */
 int64_t bipart_kernel_launches(void);

@@ -54,6 +54,7 @@ SYMBOLS = {
     "bipart_sizes": (ctypes.c_int, [_vp, _p32, _p32, _p32]),
     "bipart_destroy": (None, [_vp]),
     "bipart_last_error": (ctypes.c_char_p, []),
+    "bipart_cut_noalloc": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp, _vp, _i32, _vp, _vp]),
     "bipart_kernel_launches": (ctypes.c_int64, []),
     "bipart_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "bipart_profile_read": (ctypes.c_int, [_i32, ctypes.c_char_p, ctypes.c_size_t,
@@ -257,6 +258,17 @@ def create_device(N, hoff, pins, nw=None, hw=None, stream=None) -> Handle:
     _check(L.bipart_create_device(int(N), int(hoff.numel() - 1), dp(hoff), dp(pins), dp(nw), dp(hw),
                                   _stream_ptr(stream), ctypes.byref(out)))
     return Handle(out)
+
+
+def cut_noalloc(N, hoff, pins, hw, parts, k, out, stream=None) -> int:
+    """bipart_cut_noalloc on CUDA tensors: writes the cut into the int64 tensor `out` (one element)
+    without any device allocation by the library; returns the status code."""
+
+    def dp(t):
+        return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+    return _check(load().bipart_cut_noalloc(int(N), int(hoff.numel() - 1), dp(hoff), dp(pins),
+                                            dp(hw), dp(parts), int(k), dp(out), _stream_ptr(stream)))
 
 
 def create_from(g: dict, stream=None) -> Handle:
