@@ -33,7 +33,22 @@ inline int grid_for(int64_t n, int per_block = kBlock, int cap = 152 * 16) {
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
+thread_local bipart_graph *tl_graph = nullptr;   // handle of the entry point running
+thread_local bool tl_capturing = false;
+
+// Sets the handle whose buffers the current entry point (re)allocates.
+struct HandleScope {
+    bipart_graph *prev;
+    explicit HandleScope(bipart_graph *g) : prev(tl_graph) { tl_graph = g; }
+    ~HandleScope() { tl_graph = prev; }
+};
+
+void note_realloc() {
+    if (tl_graph) tl_graph->gen++;
+}
+
 void *dev_alloc(size_t bytes, cudaStream_t s) {
+    if (tl_capturing) return nullptr;  // no allocation may happen inside a captured plan
     if (g_alloc) return g_alloc(g_alloc_ctx, bytes, (void *)s);
     void *p = nullptr;
     if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
@@ -51,13 +66,108 @@ void dev_free(void *p, size_t bytes, cudaStream_t s) {
 
 uint32_t *dev_status(bipart_graph *g) { return g->w.status.as<uint32_t>(); }
 
-void sync(bipart_graph *g) { BP_CUDA(cudaStreamSynchronize(g->stream)); }
+void sync(bipart_graph *g) {
+    if (g->ex.capturing) return;
+    BP_CUDA(cudaStreamSynchronize(g->stream));
+}
 
 void check_status(bipart_graph *g) {
+    if (g->ex.capturing) return;
     uint32_t st = 0;
     BP_CUDA(cudaMemcpy(&st, dev_status(g), sizeof(uint32_t), cudaMemcpyDeviceToHost));
     if (st & DEV_TIMEOUT) throw Fail{BIPART_ERR_TIMEOUT, "a bounded device-side wait expired"};
     if (st & DEV_OVERFLOW) throw Fail{BIPART_ERR_OOM, "a device-side size limit was exceeded"};
+}
+
+// ------------------------------------------------------------------------- plans and conditionals
+__global__ void k_expect(const int *d, int v, uint32_t *status) {
+    if (threadIdx.x == 0 && *d != v) atomicOr(status, (uint32_t)DEV_PLAN_MISMATCH);
+}
+
+__global__ void k_cond(cudaGraphConditionalHandle h, const unsigned *flag) {
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, *flag ? 1u : 0u);
+}
+
+int32_t read_i32(bipart_graph *g, const int32_t *d) {
+    Exec &ex = g->ex;
+    if (ex.capturing) {
+        if (ex.pos >= ex.sizes.size()) throw Fail{BIPART_ERR_CUDA, "plan capture ran past its recorded sizes"};
+        int32_t v = ex.sizes[ex.pos++];
+        k_expect<<<1, 32, 0, g->stream>>>(d, v, dev_status(g));
+        BP_LAUNCH();
+        return v;
+    }
+    BP_CUDA(cudaMemcpyAsync(g->w.host_small, d, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+    sync(g);
+    int32_t v = (int32_t)g->w.host_small[0];
+    check_status(g);
+    if (ex.recording) ex.sizes.push_back(v);
+    return v;
+}
+
+unsigned read_flag(bipart_graph *g, const unsigned *d) {
+    BP_CUDA(cudaMemcpyAsync(g->w.host_small, d, sizeof(unsigned), cudaMemcpyDeviceToHost, g->stream));
+    sync(g);
+    if (g->ex.recording) g->ex.loop_launches++;  // one condition kernel per evaluation on replay
+    return g->w.host_small[0];
+}
+
+CondNode cond_begin(bipart_graph *g, const unsigned *d_flag, bool loop) {
+    Exec &ex = g->ex;
+    const int depth = ex.depth + 1;
+    if (depth >= 4) throw Fail{BIPART_ERR_CUDA, "conditional nesting too deep"};
+    if (!ex.body[depth]) BP_CUDA(cudaStreamCreateWithFlags(&ex.body[depth], cudaStreamNonBlocking));
+    cudaStream_t outer = g->stream;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    BP_CUDA(cudaStreamGetCaptureInfo(outer, &cs, nullptr, &graph, &deps, nullptr, &nd));
+    cudaGraphConditionalHandle h;
+    BP_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault));
+    k_cond<<<1, 32, 0, outer>>>(h, d_flag);  // initial value of the condition
+    BP_LAUNCH();
+    BP_CUDA(cudaStreamGetCaptureInfo(outer, &cs, nullptr, &graph, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = loop ? cudaGraphCondTypeWhile : cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    BP_CUDA(cudaGraphAddNode(&node, graph, deps, nullptr, nd, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    BP_CUDA(cudaStreamBeginCaptureToGraph(ex.body[depth], body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed));
+    ex.depth = depth;
+    g->stream = ex.body[depth];
+    return CondNode{h, node, outer};
+}
+
+void cond_end(bipart_graph *g, const CondNode &c, const unsigned *d_flag, bool loop) {
+    Exec &ex = g->ex;
+    if (loop) {
+        k_cond<<<1, 32, 0, g->stream>>>(c.h, d_flag);  // re-evaluated after every iteration
+        BP_LAUNCH();
+    }
+    cudaGraph_t body = nullptr;
+    BP_CUDA(cudaStreamEndCapture(g->stream, &body));
+    ex.depth--;
+    g->stream = c.outer;
+    cudaGraphNode_t n = c.node;
+    BP_CUDA(cudaStreamUpdateCaptureDependencies(c.outer, &n, nullptr, 1, cudaStreamSetCaptureDependencies));
+}
+
+void Plan::reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (Probe &p : probes) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    probes.clear();
+    exec = nullptr;
+    graph = nullptr;
+    valid = false;
 }
 
 // ------------------------------------------------------------------------- validation kernels
@@ -288,8 +398,9 @@ void extract_subgraph(bipart_graph *g, const int *d_part, int j) {
 }
 
 // Sec. 3.4: coarsen until `levels` levels exist or the node count stops changing (reading C11),
-// then initial partition + refinement back to level 0.  Coarse levels live in g->lev.
-int bisect(bipart_graph *g, Level &L0, const Params &p, int64_t W, uint8_t *d_side, int *nlev) {
+// then initial partition + refinement back to level 0.  Coarse levels live in g->lev; the side
+// of level 0 goes to d_side and the status word (level-0 rebalance imbalanced) stays on device.
+void bisect_body(bipart_graph *g, Level &L0, const Params &p, int64_t W, uint8_t *d_side, int *nlev) {
     std::vector<Level *> levels{&L0};
     while ((int)levels.size() - 1 < p.levels) {
         Level &f = *levels.back();
@@ -302,8 +413,122 @@ int bisect(bipart_graph *g, Level &L0, const Params &p, int64_t W, uint8_t *d_si
         levels.push_back(&c);
     }
     if (nlev) *nlev = (int)levels.size();
-    const int64_t limit = balance_limit(W, p.eps);
-    return uncoarsen(g, levels, limit, p.iters, d_side);
+    uncoarsen(g, levels, balance_limit(W, p.eps), p.iters, d_side);
+}
+
+int read_bisect_status(bipart_graph *g) {
+    BP_CUDA(cudaMemcpyAsync(g->w.host_small, bisect_status_word(g), sizeof(unsigned),
+                            cudaMemcpyDeviceToHost, g->stream));
+    sync(g);
+    return g->w.host_small[0] ? BIPART_WARN_IMBALANCED : BIPART_OK;
+}
+
+// Captures the bisection just run eagerly (its sizes recorded) into a CUDA graph with WHILE / IF
+// nodes for the device-driven loops.  Best effort: on any failure the plan stays invalid and the
+// next call runs eagerly again.
+void capture_plan(bipart_graph *g, const Params &p, uint8_t *d_side, int nlev, int64_t kernels) {
+    Plan &pl = g->plan;
+    pl.reset();
+    Exec &ex = g->ex;
+    const uint64_t gen0 = g->gen;
+    ex.capturing = true;
+    ex.pos = 0;
+    ex.depth = 0;
+    tl_capturing = true;
+    cudaStream_t main = g->stream;
+    cudaGraph_t graph = nullptr;
+    bool ok = true;
+    if (cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) ok = false;
+    if (ok) {
+        try {
+            int n2 = 0;
+            bisect_body(g, g->L0, p, g->total_node_weight, d_side, &n2);
+            if (n2 != nlev) ok = false;
+        } catch (...) {
+            ok = false;
+        }
+        // close any open body captures, then the main one
+        while (ex.depth > 0) {
+            cudaGraph_t b = nullptr;
+            cudaStreamEndCapture(ex.body[ex.depth], &b);
+            ex.depth--;
+        }
+        g->stream = main;
+        if (cudaStreamEndCapture(main, &graph) != cudaSuccess) ok = false;
+    }
+    ex.capturing = false;
+    tl_capturing = false;
+    cudaGetLastError();
+    if (ok && ex.pos != ex.sizes.size()) ok = false;
+    if (ok && g->gen != gen0) ok = false;
+    if (ok && cudaGraphInstantiate(&pl.exec, graph, 0) != cudaSuccess) ok = false;
+    cudaGetLastError();
+    pl.graph = graph;
+    if (!ok) {
+        pl.reset();
+        return;
+    }
+    pl.valid = true;
+    pl.params = p;
+    pl.nlev = nlev;
+    pl.gen = g->gen;
+    pl.prof_epoch = prof_epoch();
+    pl.launches = kernels + ex.loop_launches + (int64_t)ex.sizes.size();
+}
+
+bool same_params(const Params &a, const Params &b) {
+    return a.policy == b.policy && a.levels == b.levels && a.iters == b.iters && a.eps == b.eps;
+}
+
+// Bisection of the handle's level 0.  First call with given parameters: eager, recording the
+// level sizes.  Second call: captures those launches into a CUDA graph and launches it.  Later
+// calls: launch the graph.  A replay whose device-side size checks fail (or a change of buffers
+// or of profiling) drops the plan and runs eagerly again.
+int bisect_top(bipart_graph *g, const Params &p, uint8_t *d_side, int *nlev) {
+    Plan &pl = g->plan;
+    Exec &ex = g->ex;
+    if (!(pl.valid && same_params(pl.params, p) && pl.gen == g->gen && pl.prof_epoch == prof_epoch())) {
+        pl.reset();
+        if (ex.rec_valid && same_params(ex.rec_params, p) && ex.rec_gen == g->gen)
+            capture_plan(g, p, d_side, ex.rec_nlev, ex.rec_kernels);
+    }
+    if (pl.valid) {
+        BP_CUDA(cudaGraphLaunch(pl.exec, g->stream));
+        for (int64_t i = 0; i < pl.launches; ++i) note_launch();
+        sync(g);
+        uint32_t st = 0;
+        BP_CUDA(cudaMemcpy(&st, dev_status(g), sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        if (!(st & DEV_PLAN_MISMATCH)) {
+            check_status(g);
+            prof_collect(pl.probes);
+            *nlev = pl.nlev;
+            return read_bisect_status(g);
+        }
+        // the replayed control flow did not match this run: discard the plan, run eagerly
+        BP_CUDA(cudaMemsetAsync(dev_status(g), 0, sizeof(uint32_t), g->stream));
+        pl.reset();
+        ex.rec_valid = false;
+    }
+    ex.recording = true;
+    ex.sizes.clear();
+    ex.loop_launches = 0;
+    const int64_t k0 = bipart_kernel_launches();
+    try {
+        bisect_body(g, g->L0, p, g->total_node_weight, d_side, nlev);
+    } catch (...) {
+        ex.recording = false;
+        throw;
+    }
+    ex.recording = false;
+    const int64_t kernels = bipart_kernel_launches() - k0;
+    int st = read_bisect_status(g);
+    check_status(g);
+    ex.rec_valid = true;
+    ex.rec_params = p;
+    ex.rec_gen = g->gen;
+    ex.rec_nlev = *nlev;
+    ex.rec_kernels = kernels;
+    return st;
 }
 
 int partition_device(bipart_graph *g, const Params &p, int *d_parts) {
@@ -315,11 +540,11 @@ int partition_device(bipart_graph *g, const Params &p, int *d_parts) {
         BP_CUDA(cudaMemsetAsync(d_parts, 0, sizeof(int) * (size_t)L.N, s));
         return BIPART_OK;
     }
-    Buf side_out;
-    uint8_t *d_side = (uint8_t *)side_out.ensure((size_t)L.N, s);
+    uint8_t *d_side = (uint8_t *)g->side_out.ensure((size_t)L.N, s);
+    BP_CUDA(cudaMemsetAsync(dev_status(g), 0, sizeof(uint32_t), s));
     int status = BIPART_OK;
     int nlev = 0;
-    int st = bisect(g, L, p, g->total_node_weight, d_side, &nlev);
+    int st = bisect_top(g, p, d_side, &nlev);
     if (st != BIPART_OK) status = st;
     k_side_to_part<<<grid_for(L.N), kBlock, 0, s>>>(L.N, d_side, nullptr, 0, d_parts);
     BP_LAUNCH();
@@ -338,8 +563,9 @@ int partition_device(bipart_graph *g, const Params &p, int *d_parts) {
             Level &S = g->sub0;
             if (S.N == 0) continue;
             int64_t Wj = node_weight_sum(g, S);
-            uint8_t *ds = (uint8_t *)side_out.ensure((size_t)S.N, s);
-            st = bisect(g, S, p, Wj, ds, nullptr);
+            uint8_t *ds = (uint8_t *)g->side_out.ensure((size_t)S.N, s);
+            bisect_body(g, S, p, Wj, ds, nullptr);
+            st = read_bisect_status(g);
             if (st != BIPART_OK) status = st;
             k_side_to_part<<<grid_for(S.N), kBlock, 0, s>>>(S.N, ds, g->l2g.as<int>(), 2 * j, d_parts);
             BP_LAUNCH();
@@ -388,6 +614,20 @@ void validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t 
         throw Fail{BIPART_ERR_INVALID_CSR, "weight sum must stay below 2^31"};
 }
 
+}  // namespace
+}  // namespace bp
+
+bipart_graph::~bipart_graph() {
+    plan.reset();
+    for (cudaStream_t &b : ex.body)
+        if (b) cudaStreamDestroy(b);
+    if (w.host_small) cudaFreeHost(w.host_small);
+    w.host_small = nullptr;
+}
+
+namespace bp {
+namespace {
+
 bipart_graph *new_graph(cudaStream_t s) {
     std::unique_ptr<bipart_graph> g(new bipart_graph);
     BP_CUDA(cudaGetDevice(&g->device));
@@ -396,6 +636,7 @@ bipart_graph *new_graph(cudaStream_t s) {
     g->w.small.ensure(kSmallBytes, s);
     BP_CUDA(cudaMemsetAsync(g->w.status.p, 0, 64, s));
     BP_CUDA(cudaMallocHost(&g->w.host_small, 4096));
+    refine_init();
     return g.release();
 }
 
@@ -523,6 +764,7 @@ int bipart_set_stream(bipart_handle h, void *stream) {
 int bipart_partition_device(bipart_handle h, int32_t k, double epsilon, int32_t policy,
                             int32_t levels, int32_t refine_iters, int32_t *d_out_parts) {
     if (!h) { set_error("handle is NULL"); return BIPART_ERR_INVALID_ARG; }
+    HandleScope hs(h);
     return guard([&]() {
         validate_params(k, epsilon, policy, levels, refine_iters);
         if (!d_out_parts && h->L0.N > 0) throw Fail{BIPART_ERR_INVALID_ARG, "out_parts is NULL"};
@@ -536,6 +778,7 @@ int bipart_partition_device(bipart_handle h, int32_t k, double epsilon, int32_t 
 int bipart_partition(bipart_handle h, int32_t k, double epsilon, int32_t policy, int32_t levels,
                      int32_t refine_iters, int32_t *out_parts) {
     if (!h) { set_error("handle is NULL"); return BIPART_ERR_INVALID_ARG; }
+    HandleScope hs(h);
     return guard([&]() {
         validate_params(k, epsilon, policy, levels, refine_iters);
         const int32_t N = h->L0.N;
@@ -605,8 +848,6 @@ int bipart_sizes(bipart_handle h, int32_t *N, int32_t *E, int32_t *P) {
 void bipart_destroy(bipart_handle h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
-    if (h->w.host_small) cudaFreeHost(h->w.host_small);
-    h->w.host_small = nullptr;
     delete h;
 }
 
@@ -628,6 +869,7 @@ __global__ void k_cut_sum(int E, const int *__restrict__ cnt, const int *__restr
 
 extern "C" int bipart_cut(bipart_handle h, const int32_t *parts, int64_t *cut) {
     if (!h || !cut || (!parts && h->L0.N > 0)) { set_error("NULL argument"); return BIPART_ERR_INVALID_ARG; }
+    HandleScope hs(h);
     return guard([&]() {
         Level &L = h->L0;
         cudaStream_t s = h->stream;
@@ -670,6 +912,7 @@ struct ProfTot {
 };
 std::mutex g_prof_mu;
 bool g_prof_on = false;
+int g_prof_epoch = 0;
 std::vector<ProfRec> g_prof_pending;
 std::vector<cudaEvent_t> g_prof_pool;
 std::map<std::string, ProfTot> g_prof_tot;
@@ -701,10 +944,43 @@ void prof_drain() {
 }
 }  // namespace
 
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launch() {
+    if (tl_capturing) return;  // captured launches run when the graph is launched
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+int prof_epoch() { return g_prof_epoch; }
+
+void prof_collect(const std::vector<Probe> &probes) {
+    if (probes.empty()) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (const Probe &p : probes) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            ProfTot &t = g_prof_tot[p.name];
+            t.launches++;
+            t.ms += ms;
+            t.bytes += p.bytes;
+        }
+    }
+    cudaGetLastError();
+}
 
 ProfScope::ProfScope(const char *name, double bytes, cudaStream_t s) {
     if (!g_prof_on) return;
+    if (tl_capturing) {
+        // inside a captured plan: event nodes at the top level of the graph only (conditional
+        // bodies may not hold event nodes); read back after every replay
+        bipart_graph *g = tl_graph;
+        if (!g || g->ex.depth > 0) return;
+        Probe p{name, bytes, nullptr, nullptr};
+        cudaEventCreate(&p.a);
+        cudaEventCreate(&p.b);
+        cudaEventRecord(p.a, s);
+        g->plan.probes.push_back(p);
+        slot = -2 - (int)(g->plan.probes.size() - 1);
+        return;
+    }
     std::lock_guard<std::mutex> lk(g_prof_mu);
     ProfRec r{name, bytes, prof_event(), prof_event(), s};
     cudaEventRecord(r.a, s);
@@ -713,6 +989,12 @@ ProfScope::ProfScope(const char *name, double bytes, cudaStream_t s) {
 }
 
 ProfScope::~ProfScope() {
+    if (slot <= -2) {
+        bipart_graph *g = tl_graph;
+        size_t i = (size_t)(-2 - slot);
+        if (g && i < g->plan.probes.size()) cudaEventRecord(g->plan.probes[i].b, g->stream);
+        return;
+    }
     if (slot < 0) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (slot < (int)g_prof_pending.size()) cudaEventRecord(g_prof_pending[slot].b, g_prof_pending[slot].s);
@@ -726,6 +1008,7 @@ extern "C" int bipart_profile_enable(int on) {
     std::lock_guard<std::mutex> lk(bp::g_prof_mu);
     bp::prof_drain();
     bp::g_prof_tot.clear();
+    if (bp::g_prof_on != (on != 0)) bp::g_prof_epoch++;  // plans are recaptured with/without probes
     bp::g_prof_on = on != 0;
     return BIPART_OK;
 }

@@ -537,11 +537,8 @@ void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int 
     } else {
         BP_CUDA(cudaMemsetAsync(c.hoff(), 0, sizeof(int), s));
     }
-    BP_CUDA(cudaMemcpyAsync(w.host_small, small, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    sync(g);
-    check_status(g);
-    c.E = E > 0 ? (int)w.host_small[2] : 0;
-    c.P = E > 0 ? (int)w.host_small[3] : 0;
+    c.E = E > 0 ? read_i32(g, small + 2) : 0;
+    c.P = E > 0 ? read_i32(g, small + 3) : 0;
 }
 
 }  // namespace
@@ -655,11 +652,8 @@ void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy) {
             scan(N, RenumIn{grp, rep}, RenumOut{N, grp, f.cmap(), gcid, small + 4},
                  w.scan.ensure(scan_state_bytes(N), s), dev_status(g), s);
         }
-        BP_CUDA(cudaMemcpyAsync(w.host_small, small + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
-        sync(g);
-        check_status(g);
     }
-    const int Nc = N > 0 ? (int)w.host_small[0] : 0;
+    const int Nc = N > 0 ? read_i32(g, small + 4) : 0;
     c.N = Nc;
     c.b_nw.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);
     if (N > 0) {

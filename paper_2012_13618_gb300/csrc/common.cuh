@@ -13,7 +13,7 @@
 namespace bp {
 
 // Status word shared by kernels that can fail at run time (bounded waits, size overflows).
-enum DevErr : uint32_t { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_OVERFLOW = 2 };
+enum DevErr : uint32_t { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_OVERFLOW = 2, DEV_PLAN_MISMATCH = 4 };
 
 // Spin limit of every device-side wait: after this many polls the waiting thread records
 // DEV_TIMEOUT in the status word and carries on with a defined (wrong) value, so the kernel

@@ -17,6 +17,9 @@ namespace bp {
 // ---------------------------------------------------------------------------------- memory
 void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, size_t bytes, cudaStream_t s);
+// Bumped whenever a buffer is (re)allocated: a captured graph is only valid while the buffers
+// it points to are the ones it was captured with.
+void note_realloc();
 
 // A growable device buffer (capacity only grows; contents are not preserved on growth).
 struct Buf {
@@ -41,6 +44,7 @@ struct Buf {
             p = dev_alloc(c, stream);
             if (!p) throw Fail{BIPART_ERR_OOM, "device allocation of " + std::to_string(c) + " bytes failed"};
             cap = c;
+            note_realloc();
         }
         return p;
     }
@@ -99,17 +103,55 @@ struct Work {
 };
 
 struct Params {
-    int32_t k;
-    double eps;
-    int32_t policy;
-    int32_t levels;
-    int32_t iters;
+    int32_t k = 2;
+    double eps = 0;
+    int32_t policy = 0;
+    int32_t levels = 0;
+    int32_t iters = 0;
 };
 
 // Result of one bisection kept for parity queries.
 struct Hierarchy {
     int32_t nlev = 0;
     bool valid = false;
+};
+
+// How the host driver executes: eagerly (reading sizes back, optionally recording them), or
+// while capturing a CUDA graph (replaying the recorded sizes, which a device check verifies).
+struct Exec {
+    bool capturing = false;
+    bool recording = false;
+    std::vector<int32_t> sizes;
+    size_t pos = 0;
+    cudaStream_t body[4] = {};   // capture streams of nested conditional bodies
+    int depth = 0;
+    int64_t loop_launches = 0;   // helper kernels run per replay (conditions, size checks)
+    // the last eager top-level bisection, ready to be captured
+    bool rec_valid = false;
+    Params rec_params;
+    uint64_t rec_gen = 0;
+    int rec_nlev = 0;
+    int64_t rec_kernels = 0;
+};
+
+struct Probe {
+    std::string name;
+    double bytes;
+    cudaEvent_t a, b;
+};
+
+// A captured bisection of level 0 for fixed parameters.
+struct Plan {
+    bool valid = false;
+    Params params;
+    int nlev = 0;
+    uint64_t gen = 0;
+    int prof_epoch = -1;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;
+    std::vector<Probe> probes;
+    void reset();
 };
 
 }  // namespace bp
@@ -123,8 +165,12 @@ struct bipart_graph {
     bp::Work w;
     // k-way workspace: subgraph level 0 and its node map
     bp::Level sub0;
-    bp::Buf part_a, part_b, l2g;
+    bp::Buf part_a, part_b, l2g, side_out;
     int64_t total_node_weight = 0;
+    bp::Exec ex;
+    bp::Plan plan;
+    uint64_t gen = 0;            // buffer (re)allocation count of this handle
+    ~bipart_graph();
 };
 
 namespace bp {
@@ -139,14 +185,20 @@ void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy);
 void build_incidence(bipart_graph *g, Level &L);
 
 // -------------------------------------------------------------------- refinement (refine.cu)
-// Runs Algorithms 3, 5 (+ rebalance) over the hierarchy; writes side of level 0.
-int uncoarsen(bipart_graph *g, std::vector<Level *> &levels, int64_t limit, int32_t iters,
-              uint8_t *d_side0);
+// Runs Algorithms 3, 5 (+ rebalance) over the hierarchy; writes side of level 0.  The status
+// (1 = the level-0 rebalance ran out of candidates) is left in *bisect_status_word(g).
+void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, int64_t limit, int32_t iters,
+               uint8_t *d_side0);
+const unsigned *bisect_status_word(bipart_graph *g);
+void refine_init();  // once per process: kernel attributes (never during a capture)
 int64_t balance_limit(int64_t W, double eps);
 
 // ------------------------------------------------------------------------- diagnostics
 // Brackets one kernel launch with CUDA events on `s` when profiling is on (see
 // bipart_profile_enable); `bytes` is the launch's algorithmic traffic.
+int prof_epoch();
+void prof_collect(const std::vector<Probe> &probes);
+
 struct ProfScope {
     int slot = -1;
     ProfScope(const char *name, double bytes, cudaStream_t s);
@@ -157,5 +209,50 @@ struct ProfScope {
 uint32_t *dev_status(bipart_graph *g);
 void check_status(bipart_graph *g);
 void sync(bipart_graph *g);
+
+// Scalar produced on the device that the host needs (a level size).  Eager: copied back (and
+// recorded when recording).  Capturing: the recorded value is returned and a device check
+// against the live value is added to the graph (a mismatch invalidates the plan).
+int32_t read_i32(bipart_graph *g, const int32_t *d);
+// Reads a device flag in eager mode.
+unsigned read_flag(bipart_graph *g, const unsigned *d);
+
+// Conditional-node helpers used while capturing (api.cu).
+struct CondNode {
+    cudaGraphConditionalHandle h;
+    cudaGraphNode_t node;
+    cudaStream_t outer;
+};
+CondNode cond_begin(bipart_graph *g, const unsigned *d_flag, bool loop);
+void cond_end(bipart_graph *g, const CondNode &c, const unsigned *d_flag, bool loop);
+
+// Runs body() while *d_flag != 0 (the body must update the flag).  Eager: the host reads the flag
+// before every iteration; capturing: a WHILE conditional node.
+template <class Body>
+void device_while(bipart_graph *g, const unsigned *d_flag, int64_t max_iter, Body body) {
+    if (!g->ex.capturing) {
+        for (int64_t it = 0;; ++it) {
+            if (!read_flag(g, d_flag)) break;
+            if (it > max_iter) throw Fail{BIPART_ERR_TIMEOUT, "device loop made no progress"};
+            body();
+        }
+        return;
+    }
+    CondNode c = cond_begin(g, d_flag, true);
+    body();
+    cond_end(g, c, d_flag, true);
+}
+
+// Runs body() once if *d_flag != 0.  Eager: host check; capturing: an IF conditional node.
+template <class Body>
+void device_if(bipart_graph *g, const unsigned *d_flag, Body body) {
+    if (!g->ex.capturing) {
+        if (read_flag(g, d_flag)) body();
+        return;
+    }
+    CondNode c = cond_begin(g, d_flag, false);
+    body();
+    cond_end(g, c, d_flag, false);
+}
 
 }  // namespace bp

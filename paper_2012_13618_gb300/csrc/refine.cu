@@ -2,12 +2,14 @@
 // per-hyperedge side counts, Algorithm 3 growth of P0 by the top ceil(sqrt n) gains, Algorithm 5
 // swaps of the gain >= 0 lists and the rebalancing pass.
 //
-// Ordering of nodes is always (gain descending, node id ascending).  The top-K of a candidate set
-// is found without sorting: a radix select over the order-preserving 32-bit key
-// key = gain ^ 0x80000000 (up to three 11-bit histogram passes) fixes the threshold key and how
-// many nodes with exactly that key are taken; a scan over node ids then takes the lowest ids
-// among the ties.  Only the rebalancing pass needs the selected nodes in order; it sorts at most
-// ceil(sqrt n) of them in shared memory.
+// Node order is always (gain descending, node id ascending).  A top-K is found without sorting:
+// one histogram pass over gains clamped to [-1024, 1023] fixes the threshold gain exactly unless
+// it falls in one of the two clamped end buckets, in which case an exact radix select (up to
+// three 11-bit passes over the order-preserving key gain ^ 0x80000000) narrows it down; a scan
+// over node ids then takes the lowest ids among nodes whose gain equals the threshold.  Only the
+// rebalancing pass needs the chosen nodes in order; it sorts at most ceil(sqrt n) of them in one
+// block.  The two data-dependent loops (Algorithm 3's rounds and the rebalancing rounds) are
+// driven by a device-side flag, so they run unchanged inside a CUDA graph (WHILE nodes).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,8 +27,8 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int kHistBits = 11;
 constexpr int kHistBins = 1 << kHistBits;
-constexpr int kWarpDeg = 32;          // hyperedges above this degree: one warp each
-constexpr int kRebalMax = 16384;      // largest ceil(sqrt n) handled by the ordered rebalance
+constexpr int kClampLo = -1024;          // fast-path buckets: gains -1023 .. 1022 are exact
+constexpr int kRebalMax = 16384;         // largest ceil(sqrt n) handled by the ordered rebalance
 
 inline int grid_for(int64_t n, int per_block = kBlock, int cap = 152 * 16) {
     int64_t b = (n + per_block - 1) / per_block;
@@ -36,88 +38,66 @@ inline int grid_for(int64_t n, int per_block = kBlock, int cap = 152 * 16) {
 
 }  // namespace
 
-// Candidate predicate of a selection.
 enum SelKind : int { SEL_REFINE = 0, SEL_INITIAL = 1, SEL_REBAL = 2 };
 
-// Selection state of one group (one side).  mode: 0 none, 1 all candidates, 2 threshold final,
-// 3 threshold in progress.
+// Selection state of one group (one side).  mode: 0 select none, 1 select all candidates,
+// 2 threshold known (thr, take_eq), 3 exact radix select in progress over keys in [base, top).
 struct SelGroup {
-    unsigned kmin, kmax, cnt, K;
-    unsigned base, shift, need, thr, take_eq, mode;
-    unsigned long long top;  // exclusive upper bound of the keys still in play
-    unsigned pad[4];
-};
-struct SelState {
-    SelGroup g[2];
-    unsigned hist[2][kHistBins];
-    unsigned long long W[2];      // side weights
-    unsigned list_count;
+    unsigned cnt, K, thr, take_eq, mode;
+    unsigned base, shift, need;
+    unsigned long long top;
 };
 
-struct SelArgs {
-    int kind;
-    int heavy;        // SEL_REBAL: heavy side
-    long long room;   // SEL_REBAL: weight room on the light side
-    long long s;      // ceil(sqrt n) for SEL_INITIAL / SEL_REBAL
+// All device-side state of refinement, resident in the handle's small scratch.
+struct RState {
+    SelGroup g[2];
+    unsigned hist[2][kHistBins];
+    unsigned long long W[2];   // side weights
+    long long limit, room, need;
+    int heavy;                 // rebalance: heavy side or -1
+    unsigned list_count;       // rebalance: selected nodes
+    unsigned flag;             // loop-continue flag
+    unsigned slow;             // exact radix path needed by the current selection
+    unsigned warn;             // rebalance ran out of candidates
+    unsigned rounds;           // loop guard
+    unsigned status0;          // warn of the level-0 rebalance
 };
 
 __device__ __forceinline__ unsigned gkey(int gain) { return (unsigned)gain ^ 0x80000000u; }
 
-__device__ __forceinline__ int sel_group(const SelArgs &a, int gain, uint8_t side, int w) {
-    if (a.kind == SEL_REFINE) return gain >= 0 ? (int)side : -1;
-    if (a.kind == SEL_INITIAL) return side == 1 ? 1 : -1;
-    return (side == a.heavy && (long long)w <= a.room) ? a.heavy : -1;
+// Candidate group of node v for a selection (-1: not a candidate).
+__device__ __forceinline__ int sel_group(int kind, const RState *st, int gain, uint8_t side, int w) {
+    if (kind == SEL_REFINE) return gain >= 0 ? (int)side : -1;
+    if (kind == SEL_INITIAL) return side == 1 ? 1 : -1;
+    return (side == st->heavy && (long long)w <= st->room) ? st->heavy : -1;
 }
 
 // ------------------------------------------------------------------------ Algorithm 4
-// Per hyperedge: n1 = pins on side 1; contribution to a pin on side i:
-// +w if n_i == 1 (moving it uncuts e), -w if n_i == |e| (moving it cuts e), else 0.
-__device__ __forceinline__ int2 contrib(int n1, int d, int w) {
-    int n0 = d - n1;
-    int c0 = n0 == 1 ? w : (n0 == d ? -w : 0);
-    int c1 = n1 == 1 ? w : (n1 == d ? -w : 0);
-    return make_int2(c0, c1);
+// n1[e] = number of pins of e on side 1 (load-balanced over pins, integer atomics).
+__global__ void __launch_bounds__(kLbBlock)
+k_hedge_n1(int E, int P, const int *__restrict__ hoff, const int *__restrict__ pins,
+           const uint8_t *__restrict__ side, int *__restrict__ n1) {
+    lb_for_each<int>(
+        hoff, E, P, 0,
+        [&](int, int i, int acc) { return acc + __ldg(side + __ldg(pins + i)); },
+        [&](int e, int acc) {
+            if (acc) atomicAdd(n1 + e, acc);
+        });
 }
 
-__global__ void __launch_bounds__(kBlock)
-k_hedge_side_small(int E, const int *__restrict__ hoff, const int *__restrict__ pins,
-                   const int *__restrict__ hw, const uint8_t *__restrict__ side,
-                   int2 *__restrict__ hc) {
+// Contribution of e to a pin on side i: +w if n_i == 1 (moving it uncuts e), -w if n_i == |e|
+// (moving it cuts e), else 0.
+__global__ void k_hedge_contrib(int E, const int *__restrict__ hoff, const int *__restrict__ hw,
+                                const int *__restrict__ n1, int2 *__restrict__ hc) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
-        int a = hoff[e], d = hoff[e + 1] - a;
-        if (d > kWarpDeg) continue;
-        int n1 = 0;
-        for (int i = 0; i < d; ++i) n1 += side[pins[a + i]];
-        hc[e] = contrib(n1, d, hw ? hw[e] : 1);
+        int d = hoff[e + 1] - hoff[e], a1 = n1[e], a0 = d - a1, w = hw ? hw[e] : 1;
+        int c0 = a0 == 1 ? w : (a0 == d ? -w : 0);
+        int c1 = a1 == 1 ? w : (a1 == d ? -w : 0);
+        hc[e] = make_int2(c0, c1);
     }
 }
 
-__global__ void __launch_bounds__(kBlock)
-k_hedge_side_big(const int *__restrict__ hoff, const int *__restrict__ pins,
-                 const int *__restrict__ hw, const uint8_t *__restrict__ side,
-                 const int *__restrict__ list, const int *__restrict__ count,
-                 int2 *__restrict__ hc) {
-    const int n = *count;
-    const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += warps) {
-        int e = list[w];
-        int a = hoff[e], d = hoff[e + 1] - a;
-        int n1 = 0;
-        for (int i = lane; i < d; i += 32) n1 += side[pins[a + i]];
-        n1 = warp_sum(n1);
-        if (lane == 0) hc[e] = contrib(n1, d, hw ? hw[e] : 1);
-    }
-}
-
-__global__ void k_big_list(int E, const int *__restrict__ hoff, int *__restrict__ list,
-                           int *__restrict__ count) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
-        if (hoff[e + 1] - hoff[e] > kWarpDeg) list[atomicAdd(count, 1)] = e;
-}
-
-// gain[v] = sum over v's hyperedges of the contribution for v's side; load-balanced over the
-// incidence array, per-node partial sums combined with integer atomicAdd (gain zeroed first).
+// gain[v] = sum over v's hyperedges of the contribution for v's side (gain zeroed first).
 __global__ void __launch_bounds__(kLbBlock)
 k_node_gain(int N, int P, const int *__restrict__ noff, const int *__restrict__ nadj,
             const int2 *__restrict__ hc, const uint8_t *__restrict__ side, int *__restrict__ gain) {
@@ -133,79 +113,119 @@ k_node_gain(int N, int P, const int *__restrict__ noff, const int *__restrict__ 
 }
 
 // ------------------------------------------------------------------------ selection
-__global__ void k_sel_reset(SelState *st) {
-    for (int i = threadIdx.x; i < 2; i += blockDim.x) {
-        st->g[i].kmin = 0xffffffffu;
-        st->g[i].kmax = 0;
-        st->g[i].cnt = 0;
-        st->g[i].K = 0;
-        st->g[i].mode = 0;
-    }
-    if (threadIdx.x == 0) st->list_count = 0;
-}
-
+// Fast pass: histogram of clamped gains per group.
 __global__ void __launch_bounds__(kBlock)
-k_sel_count(int N, SelArgs a, const int *__restrict__ gain, const uint8_t *__restrict__ side,
-            const int *__restrict__ nw, SelState *st) {
-    unsigned mn[2] = {0xffffffffu, 0xffffffffu}, mx[2] = {0, 0}, c[2] = {0, 0};
+k_sel_hist(int N, int kind, const int *__restrict__ gain, const uint8_t *__restrict__ side,
+           const int *__restrict__ nw, RState *st) {
+    __shared__ unsigned h[2][kHistBins];
+    for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
         int g = gain[v];
-        int grp = sel_group(a, g, side[v], nw[v]);
+        int grp = sel_group(kind, st, g, side[v], nw[v]);
         if (grp < 0) continue;
-        unsigned k = gkey(g);
-        mn[grp] = min(mn[grp], k);
-        mx[grp] = max(mx[grp], k);
-        c[grp]++;
+        int b = g - kClampLo;
+        b = b < 0 ? 0 : (b > kHistBins - 1 ? kHistBins - 1 : b);
+        atomicAdd(&h[grp][b], 1u);
     }
-#pragma unroll
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) {
+        unsigned c = (&h[0][0])[i];
+        if (c) atomicAdd(&(&st->hist[0][0])[i], c);
+    }
+}
+
+// Suffix scan of one group's histogram (descending buckets) by a block of 1024 threads: returns
+// the bucket holding the need-th largest key (-1 if need is 0 or exceeds the total), with
+// *above = keys in buckets above it and *total_out = all keys of the group.
+__device__ int hist_find(const unsigned *hist, unsigned need, unsigned *above, unsigned *total_out) {
+    __shared__ unsigned red[33];
+    __shared__ int s_b;
+    __shared__ unsigned s_above;
+    constexpr int per = kHistBins / 1024;
+    unsigned loc[per], tsum = 0;
+    for (int q = 0; q < per; ++q) {
+        int b = kHistBins - 1 - (threadIdx.x * per + q);
+        loc[q] = hist[b];
+        tsum += loc[q];
+    }
+    unsigned total;
+    unsigned run = block_exclusive_scan<unsigned>(tsum, red, &total);
+    if (threadIdx.x == 0) { s_b = -1; s_above = 0; }
+    __syncthreads();
+    for (int q = 0; q < per; ++q) {
+        int b = kHistBins - 1 - (threadIdx.x * per + q);
+        if (need > 0 && run < need && run + loc[q] >= need) {
+            s_b = b;
+            s_above = run;
+        }
+        run += loc[q];
+    }
+    __syncthreads();
+    int b = s_b;
+    *above = s_above;
+    *total_out = total;
+    __syncthreads();
+    return b;
+}
+
+// Decides K per group from the fast histogram and fixes the threshold, or starts the exact path.
+__global__ void __launch_bounds__(1024) k_sel_find(int kind, long long s, RState *st) {
+    unsigned cnt[2];
     for (int i = 0; i < 2; ++i) {
-        mn[i] = warp_min(mn[i]);
-        mx[i] = warp_max(mx[i]);
-        c[i] = warp_sum(c[i]);
-        if ((threadIdx.x & 31) == 0 && c[i]) {
-            atomicMin(&st->g[i].kmin, mn[i]);
-            atomicMax(&st->g[i].kmax, mx[i]);
-            atomicAdd(&st->g[i].cnt, c[i]);
+        unsigned above, total;
+        hist_find(st->hist[i], 0, &above, &total);
+        cnt[i] = total;
+    }
+    unsigned K[2] = {0, 0};
+    if (kind == SEL_REFINE) {
+        K[0] = K[1] = min(cnt[0], cnt[1]);
+    } else {
+        int grp = kind == SEL_INITIAL ? 1 : st->heavy;
+        if (grp >= 0) K[grp] = (unsigned)min((long long)cnt[grp], s);
+    }
+    unsigned slow = 0;
+    for (int i = 0; i < 2; ++i) {
+        SelGroup &G = st->g[i];
+        unsigned above = 0, total = 0;
+        int b = -1;
+        if (K[i] > 0 && K[i] < cnt[i]) b = hist_find(st->hist[i], K[i], &above, &total);
+        if (threadIdx.x == 0) {
+            G.cnt = cnt[i];
+            G.K = K[i];
+            if (K[i] == 0) {
+                G.mode = 0;
+            } else if (K[i] >= cnt[i]) {
+                G.mode = 1;
+            } else if (b > 0 && b < kHistBins - 1) {
+                G.mode = 2;
+                G.thr = gkey(b + kClampLo);
+                G.take_eq = K[i] - above;
+            } else {
+                // the threshold lies in a clamped end bucket: exact radix select over its keys
+                G.mode = 3;
+                G.need = K[i] - above;
+                if (b == kHistBins - 1) {
+                    G.base = gkey(kHistBins - 1 + kClampLo);
+                    G.top = 1ull << 32;
+                } else {
+                    G.base = 0;
+                    G.top = (unsigned long long)gkey(kClampLo) + 1ull;
+                }
+                unsigned long long range = G.top - G.base;  // >= 1
+                unsigned bits = range > 1 ? 64 - __clzll(range - 1ull) : 0;
+                G.shift = bits > kHistBits ? bits - kHistBits : 0;
+                slow = 1;
+            }
         }
     }
+    if (threadIdx.x == 0) st->slow = slow;
 }
 
-__device__ __forceinline__ unsigned bitlen(unsigned x) { return x ? 32u - __clz(x) : 0u; }
-
-// Decides K per group and prepares the first histogram pass.
-__global__ void k_sel_plan(SelArgs a, SelState *st) {
-    if (threadIdx.x != 0) return;
-    unsigned K[2];
-    if (a.kind == SEL_REFINE) {
-        unsigned l = min(st->g[0].cnt, st->g[1].cnt);
-        K[0] = K[1] = l;
-    } else {
-        int grp = a.kind == SEL_INITIAL ? 1 : a.heavy;
-        K[grp] = (unsigned)min((long long)st->g[grp].cnt, a.s);
-        K[1 - grp] = 0;
-    }
-    for (int i = 0; i < 2; ++i) {
-        SelGroup &g = st->g[i];
-        g.K = K[i];
-        if (K[i] == 0) { g.mode = 0; continue; }
-        if (K[i] >= g.cnt) { g.mode = 1; continue; }
-        unsigned range = g.kmax - g.kmin;  // keys span [kmin, kmax]
-        unsigned b = bitlen(range);
-        g.base = g.kmin;
-        g.top = (unsigned long long)g.kmax + 1ull;
-        g.shift = b > kHistBits ? b - kHistBits : 0;
-        g.need = K[i];
-        g.mode = 3;
-    }
-}
-
-__global__ void k_sel_clear_hist(SelState *st) {
-    for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) (&st->hist[0][0])[i] = 0;
-}
-
+// Exact path: histogram of keys in [base, top) by (key - base) >> shift.
 __global__ void __launch_bounds__(kBlock)
-k_sel_hist(int N, SelArgs a, const int *__restrict__ gain, const uint8_t *__restrict__ side,
-           const int *__restrict__ nw, SelState *st) {
+k_sel_hist_exact(int N, int kind, const int *__restrict__ gain, const uint8_t *__restrict__ side,
+                 const int *__restrict__ nw, RState *st) {
     __shared__ unsigned h[2][kHistBins];
     __shared__ unsigned s_base[2], s_shift[2], s_on[2];
     __shared__ unsigned long long s_top[2];
@@ -220,13 +240,11 @@ k_sel_hist(int N, SelArgs a, const int *__restrict__ gain, const uint8_t *__rest
     if (!s_on[0] && !s_on[1]) return;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
         int g = gain[v];
-        int grp = sel_group(a, g, side[v], nw[v]);
+        int grp = sel_group(kind, st, g, side[v], nw[v]);
         if (grp < 0 || !s_on[grp]) continue;
         unsigned k = gkey(g);
         if (k < s_base[grp] || (unsigned long long)k >= s_top[grp]) continue;
-        unsigned long long off = (unsigned long long)(k - s_base[grp]) >> s_shift[grp];
-        if (off >= kHistBins) continue;
-        atomicAdd(&h[grp][off], 1u);
+        atomicAdd(&h[grp][(k - s_base[grp]) >> s_shift[grp]], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) {
@@ -235,52 +253,32 @@ k_sel_hist(int N, SelArgs a, const int *__restrict__ gain, const uint8_t *__rest
     }
 }
 
-// One block of 1024 threads: for each group in progress, find the bucket holding the need-th
-// largest key; either finish (bucket width 1) or narrow to that bucket for the next pass.
-__global__ void __launch_bounds__(1024) k_sel_find(SelState *st, uint32_t *status) {
-    __shared__ unsigned suf[kHistBins];
-    __shared__ unsigned red[33];
-    __shared__ int s_bucket;
+__global__ void __launch_bounds__(1024) k_sel_find_exact(RState *st, uint32_t *status) {
     for (int i = 0; i < 2; ++i) {
-        SelGroup &g = st->g[i];
-        if (g.mode != 3) continue;  // uniform across the block
-        // suffix sums: suf[b] = count of keys in buckets > b
-        const int per = kHistBins / 1024;
-        unsigned loc[kHistBins / 1024];
-        unsigned tsum = 0;
-        for (int q = 0; q < per; ++q) {
-            int b = kHistBins - 1 - (threadIdx.x * per + q);  // descending bucket order
-            loc[q] = st->hist[i][b];
-            tsum += loc[q];
-        }
-        unsigned total;
-        unsigned ex = block_exclusive_scan<unsigned>(tsum, red, &total);
-        if (threadIdx.x == 0) s_bucket = -1;
+        SelGroup &G = st->g[i];
+        const unsigned mode = G.mode;
         __syncthreads();
-        unsigned run = ex;
-        for (int q = 0; q < per; ++q) {
-            int b = kHistBins - 1 - (threadIdx.x * per + q);
-            suf[b] = run;  // keys strictly above bucket b
-            if (run < g.need && run + loc[q] >= g.need) s_bucket = b;
-            run += loc[q];
-        }
-        __syncthreads();
+        if (mode != 3) continue;  // block-uniform
+        unsigned above = 0, total = 0;
+        int b = hist_find(st->hist[i], G.need, &above, &total);
         if (threadIdx.x == 0) {
-            int b = s_bucket;
-            if (b < 0) {  // inconsistent counts: select nothing and report it
-                g.mode = 0;
+            if (b < 0) {
+                G.mode = 0;
                 record_error(status, DEV_OVERFLOW);
             } else {
-                unsigned need = g.need - suf[b];
-                g.base = g.base + ((unsigned)b << g.shift);
-                g.top = (unsigned long long)g.base + (1ull << g.shift);
-                if (g.shift == 0) {
-                    g.thr = g.base;
-                    g.take_eq = need;
-                    g.mode = 2;
+                unsigned need = G.need - above;
+                G.base = G.base + ((unsigned)b << G.shift);
+                // the chosen bucket, clipped to the keys still in play (the first range is not
+                // a power of two wide, so a bucket may reach past it)
+                const unsigned long long end = (unsigned long long)G.base + (1ull << G.shift);
+                G.top = end < G.top ? end : G.top;
+                if (G.shift == 0) {
+                    G.thr = G.base;
+                    G.take_eq = need;
+                    G.mode = 2;
                 } else {
-                    g.need = need;
-                    g.shift = g.shift > kHistBits ? g.shift - kHistBits : 0;
+                    G.need = need;
+                    G.shift = G.shift > kHistBits ? G.shift - kHistBits : 0;
                 }
             }
         }
@@ -288,32 +286,34 @@ __global__ void __launch_bounds__(1024) k_sel_find(SelState *st, uint32_t *statu
     }
 }
 
-// Tie ranks: value = (ties of group 1) << 31 | ties of group 0, ties = candidates with key == thr.
+// Tie ranks: value = (ties of group 1) << 31 | ties of group 0; a tie is a candidate whose key
+// equals its group's threshold.
 struct TieIn {
-    SelArgs a;
+    int kind;
     const int *gain;
     const uint8_t *side;
     const int *nw;
-    const SelState *st;
+    const RState *st;
     __device__ uint64_t operator()(int64_t v) const {
         int g = gain[v];
-        int grp = sel_group(a, g, side[v], nw[v]);
+        int grp = sel_group(kind, st, g, side[v], nw[v]);
         if (grp < 0 || st->g[grp].mode != 2 || gkey(g) != st->g[grp].thr) return 0;
         return grp ? (1ull << 31) : 1ull;
     }
 };
 
-// Applies the selection: flips the side (refine / initial) or appends to the ordered-rebalance list.
+// Applies the selection: refine flips both sides' chosen nodes; the initial partition moves its
+// chosen nodes to P0 and keeps the side weights current; the rebalance collects its chosen nodes.
 struct ApplyOut {
-    SelArgs a;
+    int kind;
     const int *gain;
     uint8_t *side;
     const int *nw;
-    SelState *st;
+    RState *st;
     int *list;
-    __device__ void operator()(int64_t v, uint64_t pre, uint64_t val) const {
+    __device__ void operator()(int64_t v, uint64_t pre, uint64_t) const {
         int g = gain[v];
-        int grp = sel_group(a, g, side[v], nw[v]);
+        int grp = sel_group(kind, st, g, side[v], nw[v]);
         if (grp < 0) return;
         const SelGroup &G = st->g[grp];
         bool sel;
@@ -322,15 +322,24 @@ struct ApplyOut {
             unsigned k = gkey(g);
             unsigned rank = grp ? (unsigned)(pre >> 31) : (unsigned)(pre & 0x7fffffffu);
             sel = k > G.thr || (k == G.thr && rank < G.take_eq);
-        } else sel = false;
+        } else {
+            sel = false;
+        }
         if (!sel) return;
-        if (a.kind == SEL_REBAL) list[atomicAdd(&st->list_count, 1u)] = (int)v;
-        else side[v] ^= 1;
+        if (kind == SEL_REBAL) {
+            list[atomicAdd(&st->list_count, 1u)] = (int)v;
+        } else {
+            side[v] ^= 1;
+            if (kind == SEL_INITIAL) {
+                atomicAdd(&st->W[0], (unsigned long long)nw[v]);
+                atomicAdd(&st->W[1], (unsigned long long)(-(long long)nw[v]));
+            }
+        }
     }
 };
 
 __global__ void __launch_bounds__(kBlock)
-k_side_weights(int N, const uint8_t *__restrict__ side, const int *__restrict__ nw, SelState *st) {
+k_side_weights(int N, const uint8_t *__restrict__ side, const int *__restrict__ nw, RState *st) {
     unsigned long long w0 = 0, w1 = 0;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
         if (side[v]) w1 += nw[v];
@@ -344,16 +353,53 @@ k_side_weights(int N, const uint8_t *__restrict__ side, const int *__restrict__ 
     }
 }
 
-// Ordered rebalance move (one block): sort the selected nodes by (gain desc, id asc), then move
-// the shortest prefix whose weight reaches `need`, stopping at s nodes or before exceeding room.
+// Algorithm 3 loop condition: continue while P0 is lighter than P1 (guarded).
+__global__ void k_initial_cond(RState *st, long long max_rounds, uint32_t *status) {
+    if (threadIdx.x != 0) return;
+    unsigned f = (long long)st->W[0] < (long long)st->W[1];
+    if (f && (long long)(st->rounds++) >= max_rounds) {
+        record_error(status, DEV_TIMEOUT);
+        f = 0;
+    }
+    st->flag = f;
+}
+
+// Rebalance loop condition (reading C13): heavy side above the limit and candidates left.
+__global__ void k_rebal_cond(RState *st, long long limit, long long max_rounds, uint32_t *status) {
+    if (threadIdx.x != 0) return;
+    st->limit = limit;
+    long long W0 = (long long)st->W[0], W1 = (long long)st->W[1];
+    int H = W0 > limit ? 0 : (W1 > limit ? 1 : -1);
+    st->heavy = H;
+    unsigned f = H >= 0 && !st->warn;
+    if (H >= 0) {
+        long long Wh = H ? W1 : W0, Wo = H ? W0 : W1;
+        st->room = limit - Wo;
+        st->need = Wh - limit;
+    }
+    if (f && (long long)(st->rounds++) >= max_rounds) {
+        record_error(status, DEV_TIMEOUT);
+        f = 0;
+    }
+    st->flag = f;
+}
+
+// Ordered rebalance move (one block): sort the selected nodes by (gain desc, id asc), move the
+// shortest prefix whose weight reaches `need`, stopping at s nodes or before exceeding `room`.
+// With nothing selected, marks the level imbalanced.
 __global__ void __launch_bounds__(1024)
 k_rebal_move(const int *__restrict__ gain, uint8_t *__restrict__ side, const int *__restrict__ nw,
-             const int *__restrict__ list, SelState *st, int heavy, long long need, long long room,
-             long long s) {
+             const int *__restrict__ list, RState *st, long long s) {
     extern __shared__ unsigned long long keys[];
     __shared__ long long red[33];
     __shared__ int s_cut;
     const int n = (int)st->list_count;
+    if (n == 0) {
+        if (threadIdx.x == 0) st->warn = 1;
+        return;
+    }
+    const int heavy = st->heavy;
+    const long long room = st->room, need = st->need;
     int S = 1;
     while (S < n) S <<= 1;
     for (int i = threadIdx.x; i < S; i += blockDim.x) {
@@ -379,7 +425,6 @@ k_rebal_move(const int *__restrict__ gain, uint8_t *__restrict__ side, const int
             __syncthreads();
         }
     }
-    // prefix weights in sorted order: each thread owns a contiguous chunk
     const int per = (n + blockDim.x - 1) / blockDim.x;
     const int i0 = threadIdx.x * per;
     long long loc = 0;
@@ -397,13 +442,27 @@ k_rebal_move(const int *__restrict__ gain, uint8_t *__restrict__ side, const int
     }
     __syncthreads();
     const int cut = s_cut;
-    for (int i = threadIdx.x; i < cut; i += blockDim.x) side[(int)(keys[i] & 0xffffffffu)] = (uint8_t)(1 - heavy);
+    long long moved = 0;
+    for (int i = threadIdx.x; i < cut; i += blockDim.x) {
+        int v = (int)(keys[i] & 0xffffffffu);
+        side[v] = (uint8_t)(1 - heavy);
+        moved += nw[v];
+    }
+    moved = block_sum(moved, red);
+    if (threadIdx.x == 0) {
+        atomicAdd(&st->W[1 - heavy], (unsigned long long)moved);
+        atomicAdd(&st->W[heavy], (unsigned long long)(-moved));
+    }
 }
 
 __global__ void k_project(int N, const int *__restrict__ cmap, const uint8_t *__restrict__ coarse,
                           uint8_t *__restrict__ fine) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x)
         fine[v] = coarse[cmap[v]];
+}
+
+__global__ void k_keep_status(RState *st) {
+    if (threadIdx.x == 0) st->status0 = st->warn;
 }
 
 // ------------------------------------------------------------------------ host side
@@ -424,24 +483,27 @@ static int64_t ceil_sqrt64(int64_t n) {
 
 namespace {
 
-struct LevelCtx {
-    Level *L;
-    int *big_list;
-    int *big_count;
-};
+RState *rstate(bipart_graph *g) {
+    return reinterpret_cast<RState *>(g->w.small.as<char>() + 256);
+}
 
-void compute_gains(bipart_graph *g, const LevelCtx &lc, const uint8_t *side, int *gain) {
+void compute_gains(bipart_graph *g, Level &L, const uint8_t *side, int *gain) {
     cudaStream_t s = g->stream;
-    Level &L = *lc.L;
-    int2 *hc = (int2 *)g->w.hc.as<int2>();
+    int *n1 = g->w.e_d.as<int>();
+    int2 *hc = g->w.hc.as<int2>();
     if (L.E > 0) {
-        // hoff, pins, one side byte per pin, weights; writes two contributions per hyperedge
-        ProfScope ps("hedge_side", 12.0 * L.E + 5.0 * L.P + (L.hw() ? 4.0 * L.E : 0.0), s);
-        k_hedge_side_small<<<grid_for(L.E), kBlock, 0, s>>>(L.E, L.hoff(), L.pins(), L.hw(), side, hc);
-        BP_LAUNCH();
-        k_hedge_side_big<<<grid_for((int64_t)L.P / (kWarpDeg + 1) * 32 + 32), kBlock, 0, s>>>(
-            L.hoff(), L.pins(), L.hw(), side, lc.big_list, lc.big_count, hc);
-        BP_LAUNCH();
+        BP_CUDA(cudaMemsetAsync(n1, 0, sizeof(int) * (size_t)L.E, s));
+        {
+            // hoff, pins, one side byte per pin, one atomic per hyperedge run
+            ProfScope ps("hedge_n1", 8.0 * L.E + 5.0 * L.P, s);
+            k_hedge_n1<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.E, L.P, L.hoff(), L.pins(), side, n1);
+            BP_LAUNCH();
+        }
+        {
+            ProfScope ps("hedge_contrib", 16.0 * L.E + (L.hw() ? 4.0 * L.E : 0.0), s);
+            k_hedge_contrib<<<grid_for(L.E), kBlock, 0, s>>>(L.E, L.hoff(), L.hw(), n1, hc);
+            BP_LAUNCH();
+        }
     }
     if (L.N > 0) BP_CUDA(cudaMemsetAsync(gain, 0, sizeof(int) * (size_t)L.N, s));
     if (L.P > 0) {
@@ -452,122 +514,99 @@ void compute_gains(bipart_graph *g, const LevelCtx &lc, const uint8_t *side, int
     }
 }
 
-SelState *sel_state(bipart_graph *g) {
-    return reinterpret_cast<SelState *>(g->w.small.as<char>() + 256);
-}
-
-// Selects per SelArgs and applies (flip or list).  Returns nothing; state stays on the device.
-void select_apply(bipart_graph *g, Level &L, const SelArgs &a, const int *gain, uint8_t *side,
-                  int *list) {
+// Top-K selection per `kind` and its application (flip, or collect for the ordered rebalance).
+void select_apply(bipart_graph *g, Level &L, int kind, long long sq, const int *gain,
+                  uint8_t *side, int *list) {
     cudaStream_t s = g->stream;
-    SelState *st = sel_state(g);
-    k_sel_reset<<<1, 32, 0, s>>>(st);
-    BP_LAUNCH();
+    RState *st = rstate(g);
+    BP_CUDA(cudaMemsetAsync(&st->hist[0][0], 0, sizeof(st->hist), s));
+    if (kind == SEL_REBAL) BP_CUDA(cudaMemsetAsync(&st->list_count, 0, sizeof(unsigned), s));
     {
-        ProfScope ps("select_count", 9.0 * L.N, s);
-        k_sel_count<<<grid_for(L.N), kBlock, 0, s>>>(L.N, a, gain, side, L.nw(), st);
+        ProfScope ps("select_hist", 9.0 * L.N, s);
+        k_sel_hist<<<grid_for(L.N), kBlock, 0, s>>>(L.N, kind, gain, side, L.nw(), st);
         BP_LAUNCH();
     }
-    k_sel_plan<<<1, 32, 0, s>>>(a, st);
+    k_sel_find<<<1, 1024, 0, s>>>(kind, sq, st);
     BP_LAUNCH();
-    for (int pass = 0; pass < 3; ++pass) {
-        k_sel_clear_hist<<<1, 1024, 0, s>>>(st);
-        BP_LAUNCH();
-        {
-            ProfScope ps("select_hist", 9.0 * L.N, s);
-            k_sel_hist<<<grid_for(L.N), kBlock, 0, s>>>(L.N, a, gain, side, L.nw(), st);
+    device_if(g, &st->slow, [&]() {
+        for (int pass = 0; pass < 3; ++pass) {
+            BP_CUDA(cudaMemsetAsync(&st->hist[0][0], 0, sizeof(st->hist), g->stream));
+            k_sel_hist_exact<<<grid_for(L.N), kBlock, 0, g->stream>>>(L.N, kind, gain, side, L.nw(), st);
+            BP_LAUNCH();
+            k_sel_find_exact<<<1, 1024, 0, g->stream>>>(st, dev_status(g));
             BP_LAUNCH();
         }
-        k_sel_find<<<1, 1024, 0, s>>>(st, dev_status(g));
-        BP_LAUNCH();
-    }
+    });
+    s = g->stream;
     ProfScope ps("select_apply", 10.0 * L.N, s);
-    scan(L.N, TieIn{a, gain, side, L.nw(), st}, ApplyOut{a, gain, side, L.nw(), st, list},
+    scan(L.N, TieIn{kind, gain, side, L.nw(), st}, ApplyOut{kind, gain, side, L.nw(), st, list},
          g->w.scan.ensure(scan_state_bytes(L.N), s), dev_status(g), s);
 }
 
-void side_weights(bipart_graph *g, Level &L, const uint8_t *side, int64_t W[2]) {
+void side_weights(bipart_graph *g, Level &L, const uint8_t *side) {
     cudaStream_t s = g->stream;
-    SelState *st = sel_state(g);
+    RState *st = rstate(g);
     BP_CUDA(cudaMemsetAsync(&st->W[0], 0, 2 * sizeof(unsigned long long), s));
     if (L.N > 0) {
         k_side_weights<<<grid_for(L.N), kBlock, 0, s>>>(L.N, side, L.nw(), st);
         BP_LAUNCH();
     }
-    BP_CUDA(cudaMemcpyAsync(g->w.host_small, &st->W[0], 2 * sizeof(unsigned long long),
-                            cudaMemcpyDeviceToHost, s));
-    sync(g);
-    check_status(g);
-    const unsigned long long *hw = reinterpret_cast<const unsigned long long *>(g->w.host_small);
-    W[0] = (int64_t)hw[0];
-    W[1] = (int64_t)hw[1];
 }
 
 // Algorithm 3 on the coarsest level.
-void initial_partition(bipart_graph *g, const LevelCtx &lc, uint8_t *side, int *gain) {
+void initial_partition(bipart_graph *g, Level &L, uint8_t *side, int *gain) {
     cudaStream_t s = g->stream;
-    Level &L = *lc.L;
     if (L.N == 0) return;
+    RState *st = rstate(g);
+    const long long sq = ceil_sqrt64(L.N);
     BP_CUDA(cudaMemsetAsync(side, 1, (size_t)L.N, s));
-    SelArgs a{SEL_INITIAL, 1, 0, ceil_sqrt64(L.N)};
-    int64_t W[2];
-    side_weights(g, L, side, W);
-    int64_t rounds = 0;
-    while (W[0] < W[1]) {
-        if (++rounds > (int64_t)L.N + 1) throw Fail{BIPART_ERR_TIMEOUT, "initial partition made no progress"};
-        compute_gains(g, lc, side, gain);
-        select_apply(g, L, a, gain, side, nullptr);
-        side_weights(g, L, side, W);
-    }
+    BP_CUDA(cudaMemsetAsync(&st->rounds, 0, sizeof(unsigned), s));
+    side_weights(g, L, side);
+    k_initial_cond<<<1, 32, 0, s>>>(st, (long long)L.N + 1, dev_status(g));
+    BP_LAUNCH();
+    device_while(g, &st->flag, (int64_t)L.N + 2, [&]() {
+        compute_gains(g, L, side, gain);
+        select_apply(g, L, SEL_INITIAL, sq, gain, side, nullptr);
+        k_initial_cond<<<1, 32, 0, g->stream>>>(st, (long long)L.N + 1, dev_status(g));
+        BP_LAUNCH();
+    });
 }
 
-void refine_iter(bipart_graph *g, const LevelCtx &lc, uint8_t *side, int *gain) {
-    Level &L = *lc.L;
+void refine_iter(bipart_graph *g, Level &L, uint8_t *side, int *gain) {
     if (L.N == 0) return;
-    compute_gains(g, lc, side, gain);
-    SelArgs a{SEL_REFINE, 0, 0, 0};
-    select_apply(g, L, a, gain, side, nullptr);
+    compute_gains(g, L, side, gain);
+    select_apply(g, L, SEL_REFINE, 0, gain, side, nullptr);
 }
 
-int rebalance(bipart_graph *g, const LevelCtx &lc, uint8_t *side, int *gain, int64_t limit) {
+// Rebalance of reading C13; leaves warn = 1 when it ran out of candidates.
+void rebalance(bipart_graph *g, Level &L, uint8_t *side, int *gain, int64_t limit) {
     cudaStream_t s = g->stream;
-    Level &L = *lc.L;
+    RState *st = rstate(g);
     const int64_t sq = ceil_sqrt64(L.N);
     if (sq > kRebalMax) throw Fail{BIPART_ERR_OOM, "level too large for the ordered rebalance"};
     int *list = (int *)g->w.list.ensure(sizeof(int) * (size_t)std::max<int64_t>(sq, 1), s);
-    for (int64_t rounds = 0;; ++rounds) {
-        if (rounds > (int64_t)L.N + 1) throw Fail{BIPART_ERR_TIMEOUT, "rebalance made no progress"};
-        int64_t W[2];
-        side_weights(g, L, side, W);
-        int H;
-        if (W[0] > limit) H = 0;
-        else if (W[1] > limit) H = 1;
-        else return BIPART_OK;
-        const int64_t room = limit - W[1 - H], need = W[H] - limit;
-        compute_gains(g, lc, side, gain);
-        SelArgs a{SEL_REBAL, H, (long long)room, (long long)sq};
-        select_apply(g, L, a, gain, side, list);
-        SelState *st = sel_state(g);
-        BP_CUDA(cudaMemcpyAsync(g->w.host_small, &st->list_count, sizeof(unsigned),
-                                cudaMemcpyDeviceToHost, s));
-        sync(g);
-        const unsigned n = g->w.host_small[0];
-        if (n == 0) return BIPART_WARN_IMBALANCED;
-        int S = 1;
-        while (S < (int)n) S <<= 1;
-        size_t smem = sizeof(unsigned long long) * (size_t)S;
-        if (smem > 48 * 1024)
-            BP_CUDA(cudaFuncSetAttribute(k_rebal_move, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_rebal_move<<<1, 1024, smem, s>>>(gain, side, L.nw(), list, st, H, (long long)need,
-                                          (long long)room, (long long)sq);
+    int S = 1;
+    while (S < sq) S <<= 1;
+    const size_t smem = sizeof(unsigned long long) * (size_t)S;
+    BP_CUDA(cudaMemsetAsync(&st->warn, 0, sizeof(unsigned), s));
+    BP_CUDA(cudaMemsetAsync(&st->rounds, 0, sizeof(unsigned), s));
+    side_weights(g, L, side);
+    k_rebal_cond<<<1, 32, 0, s>>>(st, (long long)limit, (long long)L.N + 1, dev_status(g));
+    BP_LAUNCH();
+    device_while(g, &st->flag, (int64_t)L.N + 2, [&]() {
+        compute_gains(g, L, side, gain);
+        select_apply(g, L, SEL_REBAL, sq, gain, side, list);
+        k_rebal_move<<<1, 1024, smem, g->stream>>>(gain, side, L.nw(), list, st, sq);
         BP_LAUNCH();
-    }
+        k_rebal_cond<<<1, 32, 0, g->stream>>>(st, (long long)limit, (long long)L.N + 1, dev_status(g));
+        BP_LAUNCH();
+    });
 }
 
 }  // namespace
 
-int uncoarsen(bipart_graph *g, std::vector<Level *> &levels, int64_t limit, int32_t iters,
-              uint8_t *d_side0) {
+void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, int64_t limit, int32_t iters,
+               uint8_t *d_side0) {
     cudaStream_t s = g->stream;
     const int Lc = (int)levels.size() - 1;
     int64_t nmax = 1, emax = 1;
@@ -579,26 +618,14 @@ int uncoarsen(bipart_graph *g, std::vector<Level *> &levels, int64_t limit, int3
     uint8_t *sb = (uint8_t *)g->w.side_b.ensure((size_t)nmax, s);
     int *gain = (int *)g->w.gain.ensure(sizeof(int) * (size_t)nmax, s);
     g->w.hc.ensure(sizeof(int2) * (size_t)emax, s);
-    int *big_list = (int *)g->w.e_c.ensure(sizeof(int) * (size_t)emax, s);
-    int *big_count = g->w.small.as<int>() + 8;
-
-    auto level_ctx = [&](Level *L) {
-        BP_CUDA(cudaMemsetAsync(big_count, 0, sizeof(int), s));
-        if (L->E > 0) {
-            k_big_list<<<grid_for(L->E), kBlock, 0, s>>>(L->E, L->hoff(), big_list, big_count);
-            BP_LAUNCH();
-        }
-        return LevelCtx{L, big_list, big_count};
-    };
+    g->w.e_d.ensure(sizeof(int) * (size_t)emax, s);
 
     uint8_t *cur = sa, *other = sb;
-    LevelCtx lc = level_ctx(levels[Lc]);
-    initial_partition(g, lc, cur, gain);
-    int status = BIPART_OK;
+    initial_partition(g, *levels[Lc], cur, gain);
     for (int l = Lc; l >= 0; --l) {
         Level *L = levels[l];
+        s = g->stream;
         if (l < Lc) {
-            lc = level_ctx(L);
             if (L->N > 0) {
                 ProfScope ps("project", 6.0 * L->N, s);
                 k_project<<<grid_for(L->N), kBlock, 0, s>>>(L->N, L->cmap(), cur, other);
@@ -606,12 +633,25 @@ int uncoarsen(bipart_graph *g, std::vector<Level *> &levels, int64_t limit, int3
             }
             std::swap(cur, other);
         }
-        for (int it = 0; it < iters; ++it) refine_iter(g, lc, cur, gain);
-        status = rebalance(g, lc, cur, gain, limit);
+        for (int it = 0; it < iters; ++it) refine_iter(g, *L, cur, gain);
+        if (L->N > 0) rebalance(g, *L, cur, gain, limit);
+        else BP_CUDA(cudaMemsetAsync(&rstate(g)->warn, 0, sizeof(unsigned), g->stream));
     }
+    s = g->stream;
+    k_keep_status<<<1, 32, 0, s>>>(rstate(g));
+    BP_LAUNCH();
     if (levels[0]->N > 0)
         BP_CUDA(cudaMemcpyAsync(d_side0, cur, (size_t)levels[0]->N, cudaMemcpyDeviceToDevice, s));
-    return status;
+}
+
+const unsigned *bisect_status_word(bipart_graph *g) { return &rstate(g)->status0; }
+
+void refine_init() {
+    static bool done = false;
+    if (done) return;
+    BP_CUDA(cudaFuncSetAttribute(k_rebal_move, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(unsigned long long) * kRebalMax)));
+    done = true;
 }
 
 }  // namespace bp

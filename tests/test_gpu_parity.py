@@ -173,3 +173,48 @@ def test_c2_rownet_reduced_k8():
     with bp.create_from(g) as h:
         parts, st = h.partition(8, 0.05, "LDH", 25, 2)
         assert np.array_equal(parts, ref) and st == rst
+
+
+@pytest.mark.parametrize("gen", ["c0", "netlist"])
+def test_graph_replay_matches_oracle(gen):
+    # call 1 runs eagerly and records the level sizes, call 2 captures a CUDA graph (WHILE / IF
+    # nodes for the device-driven loops) and launches it, call 3 replays it: all bit-exact
+    bp = _bp()
+    g = synth.c0_uniform() if gen == "c0" else synth.c1_netlist(N=120_000)
+    eps = 0.1 if gen == "c0" else 0.05
+    hr = oracle.Hypergraph.from_dict(g)
+    ref = oracle.bisect(hr, eps, "LDH", 25, 2)
+    with bp.create_from(g) as h:
+        for call in range(3):
+            parts, st = h.partition(2, eps, "LDH", 25, 2)
+            assert np.array_equal(parts, ref["side"].astype(np.int32)), call
+            assert st == ref["status"]
+        compare_levels(h, ref)
+        # a different parameter set on the same handle, then back again
+        ref_h = oracle.bisect(hr, eps, "HDH", 7, 1, keep_levels=False)
+        for call in range(3):
+            parts, _ = h.partition(2, eps, "HDH", 7, 1)
+            assert np.array_equal(parts, ref_h["side"].astype(np.int32)), ("HDH", call)
+        parts, _ = h.partition(2, eps, "LDH", 25, 2)
+        assert np.array_equal(parts, ref["side"].astype(np.int32))
+
+
+def test_large_weighted_gains_take_exact_select():
+    # hyperedge weights in the thousands push gains beyond the clamped histogram range, so the
+    # threshold comes from the exact radix path
+    rng = np.random.default_rng(11)
+    N, E = 4000, 6000
+    deg = rng.integers(2, 7, size=E)
+    hoff = np.zeros(E + 1, np.int32)
+    hoff[1:] = np.cumsum(deg)
+    pins = np.concatenate([rng.choice(N, size=d, replace=False) for d in deg]).astype(np.int32)
+    hw = rng.integers(500, 3000, size=E).astype(np.int32)
+    g = dict(N=N, E=E, hoff=hoff, pins=pins, nw=rng.integers(1, 4, size=N).astype(np.int32), hw=hw)
+    for pol in ("LDH", "HWD"):
+        check_bisection(g, 0.05, pol)
+    bp = _bp()
+    with bp.create_from(g) as h:
+        ref = oracle.bisect(oracle.Hypergraph.from_dict(g), 0.05, "LWD", 25, 2, keep_levels=False)
+        for _ in range(3):
+            parts, _ = h.partition(2, 0.05, "LWD", 25, 2)
+            assert np.array_equal(parts, ref["side"].astype(np.int32))
