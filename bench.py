@@ -329,6 +329,145 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------------------- batched form (C3)
+def c3_graphs(n, big_nodes):
+    import synth
+    graphs = [synth.c3_instance(i) for i in range(n)]
+    params = [dict(k=2, eps=0.05, policy="LDH", levels=25, iters=2) for _ in range(n)]
+    if big_nodes:
+        graphs.append(synth.c3_instance(n, N=big_nodes))
+        params.append(dict(k=64, eps=0.05, policy="LDH", levels=25, iters=2))
+    return graphs, params
+
+
+def run_plain(bp, graphs, params):
+    """One instance at a time through the public API (create, partition, destroy)."""
+    outs = []
+    t0 = time.perf_counter()
+    for g, p in zip(graphs, params):
+        with bp.create_from(g, stream=0) as h:
+            parts, _ = h.partition(p["k"], p["eps"], p["policy"], p["levels"], p["iters"])
+        outs.append(parts)
+    return outs, time.perf_counter() - t0
+
+
+def run_batch(args):
+    import torch
+    import oracle
+    import paper_2012_13618_gb300 as bp
+    torch.cuda.set_device(0)
+    graphs, params = c3_graphs(args.batch_n, args.big_nodes)
+    pins = sum(int(g["hoff"][-1]) for g in graphs)
+    bp.partition_batch(graphs[:8], params[:8], workers=args.workers)  # warm-up
+    t0 = time.perf_counter()
+    bparts, bst = bp.partition_batch(graphs, params, workers=args.workers)
+    t_batch = time.perf_counter() - t0
+    plain_n = min(len(graphs), args.plain_n)
+    pparts, t_plain = run_plain(bp, graphs[:plain_n], params[:plain_n])
+    same = all(np.array_equal(a, b) for a, b in zip(bparts[:plain_n], pparts))
+    rng = np.random.default_rng(0)
+    sample = sorted(rng.choice(len(graphs) - (1 if args.big_nodes else 0),
+                               size=min(args.oracle_n, len(graphs)), replace=False).tolist())
+    oracle_ok = all(np.array_equal(bparts[i], oracle.partition(oracle.Hypergraph.from_dict(graphs[i]),
+                                                               params[i]["k"], 0.05, "LDH", 25, 2)[0])
+                    for i in sample)
+    line = {"metric": "batched solves/s", "value": len(graphs) / t_batch, "unit": "solves/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"{args.batch_n} netlist-like instances, N log-uniform 1k-200k, "
+                                   f"k=2, eps=0.05" + (f", plus one {args.big_nodes}-node instance at k=64"
+                                                       if args.big_nodes else ""),
+                       "instances": len(graphs), "pins": pins, "workers": args.workers},
+            "batch_seconds": t_batch, "pins_per_s": pins / t_batch,
+            "plain": {"solves_per_s": plain_n / t_plain, "instances": plain_n,
+                      "seconds": t_plain},
+            "speedup_vs_plain": (len(graphs) / t_batch) / (plain_n / t_plain),
+            "bit_exact_vs_plain": bool(same), "oracle_checked": len(sample),
+            "bit_exact_vs_oracle": bool(oracle_ok),
+            "warn_imbalanced": int((bst == 1).sum())}
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------- served form (C4)
+def c4_requests(n, seed=4):
+    import math
+    import synth
+    u = synth.uniform01(seed, 7, 4 * n)
+    reqs = []
+    for i in range(n):
+        target = math.exp(math.log(1e4) + u[4 * i] * (math.log(2e6) - math.log(1e4)))
+        k = [2, 4, 16][min(2, int(u[4 * i + 1] * 3))]
+        if u[4 * i + 2] < 0.5:
+            N = max(1000, int(target / 9.7))
+            g = synth.c3_instance(4_000_000 + i, N=N)
+        else:
+            rows = max(1000, int(target / 11.46))
+            g = synth.rownet(rows, rows, seed=4_000_000 + i)
+        reqs.append((g, dict(k=k, eps=0.05, policy="LDH", levels=25, iters=2)))
+    return reqs, u
+
+
+def run_serve(args):
+    import torch
+    import synth
+    import paper_2012_13618_gb300 as bp
+    torch.cuda.set_device(0)
+    reqs, _ = c4_requests(args.serve_n)
+    # plain path rate: one request at a time
+    _, t_plain_all = run_plain(bp, [g for g, _ in reqs], [p for _, p in reqs])
+    plain_rate = len(reqs) / t_plain_all
+    alone = run_plain(bp, [g for g, _ in reqs], [p for _, p in reqs])[0]
+    results = []
+    for mult in args.rates:
+        rate = mult * plain_rate
+        gaps = -np.log(1.0 - synth.uniform01(44, int(mult * 1000), len(reqs))) / rate
+        arrivals = np.cumsum(gaps)
+        # served: continuous batching
+        lat = []
+        with bp.Server(hbm_budget_bytes=args.budget_gb << 30, workers=args.workers) as srv:
+            t0 = time.perf_counter()
+            tickets = []
+            for (g, p), ta in zip(reqs, arrivals):
+                now = time.perf_counter() - t0
+                if ta > now:
+                    time.sleep(ta - now)
+                tickets.append((srv.submit(g, **p), time.perf_counter()))
+            exact = True
+            lat, done_t = [], []
+            for i, (t, ts) in enumerate(tickets):
+                parts, st, qms, rms = srv.wait(t)
+                lat.append(qms + rms)                 # submit -> completion, timed by the server
+                done_t.append(ts + (qms + rms) / 1000.0)
+                exact &= bool(np.array_equal(parts, alone[i]))
+            span = max(done_t) - t0
+        # plain path on the same trace: one at a time in arrival order
+        t0 = time.perf_counter()
+        plat = []
+        for (g, p), ta in zip(reqs, arrivals):
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            with bp.create_from(g, stream=0) as h:
+                h.partition(p["k"], p["eps"], p["policy"], p["levels"], p["iters"])
+            plat.append(1000 * (time.perf_counter() - t0 - ta))
+        pspan = time.perf_counter() - t0
+        results.append({"rate_x_plain": mult, "offered_per_s": rate,
+                        "served": {"solves_per_s": len(reqs) / span,
+                                   "p50_ms": float(np.percentile(lat, 50)),
+                                   "p99_ms": float(np.percentile(lat, 99))},
+                        "plain": {"solves_per_s": len(reqs) / pspan,
+                                  "p50_ms": float(np.percentile(plat, 50)),
+                                  "p99_ms": float(np.percentile(plat, 99))},
+                        "bit_exact_vs_alone": exact})
+    best = max(results, key=lambda r: r["served"]["solves_per_s"])
+    line = {"metric": "serving p50/p99 ms", "value": best["served"]["p99_ms"], "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"{len(reqs)} Poisson-arrival requests, netlist or row-net, "
+                                   "10k-2M pins log-uniform, k in {2,4,16}, eps=0.05",
+                       "workers": args.workers, "hbm_budget_gb": args.budget_gb},
+            "plain_solves_per_s": plain_rate, "sweep": results}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -336,7 +475,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "serve"])
+    ap.add_argument("--workers", type=int, default=16)
+    ap.add_argument("--batch-n", type=int, default=4096)
+    ap.add_argument("--big-nodes", type=int, default=2_000_000)
+    ap.add_argument("--plain-n", type=int, default=256)
+    ap.add_argument("--oracle-n", type=int, default=16)
+    ap.add_argument("--serve-n", type=int, default=120)
+    ap.add_argument("--rates", type=float, nargs="+", default=[0.25, 0.5, 1, 2, 4])
+    ap.add_argument("--budget-gb", type=int, default=64)
     args = ap.parse_args()
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3
     if args.impl == "reference":

@@ -111,6 +111,47 @@ void bipart_destroy(bipart_handle h);
 /* Text of the last error on the calling thread ("" if none). */
 const char *bipart_last_error(void);
 
+/* ---- Many independent hypergraphs on one GPU -------------------------------------------- */
+/* One hypergraph in HOST memory (same conventions as bipart_create); the caller keeps the arrays
+ * alive until the call that uses them has returned (batch) or been waited for (server). */
+typedef struct {
+    int32_t num_nodes, num_hedges;
+    const int32_t *hedge_offsets, *hedge_pins, *node_weights, *hedge_weights;
+} bipart_instance;
+
+/* Parameters of one partition request (as in bipart_partition). */
+typedef struct {
+    int32_t k;
+    double epsilon;
+    int32_t policy, levels, refine_iters;
+} bipart_params;
+
+/* Partitions n independent hypergraphs concurrently on the current GPU (each as bipart_partition
+ * would, Sec. 3 / Algorithm 6): `workers` host threads (<= 0: min(16, n)) each own a private
+ * workspace and CUDA stream and take instances largest first.  out_parts[i] (HOST, num_nodes
+ * entries) receives instance i's parts, statuses[i] (may be NULL) its return code.  The result of
+ * every instance equals what bipart_partition returns for it alone.  Returns OK when no instance
+ * failed, else the first failing instance's error (see bipart_last_error). */
+int bipart_partition_batch(int32_t n, const bipart_instance *instances, const bipart_params *params,
+                           int32_t *const *out_parts, int32_t *statuses, int32_t workers);
+
+/* Serving: a pool of `workers` threads (<= 0: 8) that partitions requests as they arrive.  A
+ * request is admitted once its estimated device working set fits, next to the running requests,
+ * in hbm_budget_bytes (0 = unlimited); requests larger than the whole budget complete at once with
+ * BIPART_ERR_OOM.  Results are identical to bipart_partition on the same input. */
+typedef struct bipart_server_s *bipart_server;
+int bipart_server_create(size_t hbm_budget_bytes, int32_t workers, bipart_server *out);
+/* Queues a request; the caller keeps instance arrays and out_parts (HOST) alive until waited. */
+int bipart_server_submit(bipart_server server, const bipart_instance *instance,
+                         const bipart_params *params, int32_t *out_parts, int64_t *ticket);
+/* Waits for a request (timeout_ms < 0: forever; BIPART_ERR_TIMEOUT when it expires, the request
+ * stays queued).  *status = the request's return code; queue_ms / run_ms = time from submit to
+ * start and from start to completion (any may be NULL).  Each ticket can be waited for once. */
+int bipart_server_wait(bipart_server server, int64_t ticket, int32_t timeout_ms, int32_t *status,
+                       double *queue_ms, double *run_ms);
+/* Finishes all queued requests, then stops the workers. */
+void bipart_server_destroy(bipart_server server);
+
 /* Cut of a k-way partition computed without allocating any device memory.  The paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc when they need
  * the cut -- a host application that gives all of HBM to its own memory pool up front (so an

@@ -38,6 +38,17 @@ _free_cb = None
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
 _p32 = ctypes.POINTER(ctypes.c_int32)
+class Instance(ctypes.Structure):
+    _fields_ = [("num_nodes", ctypes.c_int32), ("num_hedges", ctypes.c_int32),
+                ("hedge_offsets", ctypes.c_void_p), ("hedge_pins", ctypes.c_void_p),
+                ("node_weights", ctypes.c_void_p), ("hedge_weights", ctypes.c_void_p)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("epsilon", ctypes.c_double), ("policy", ctypes.c_int32),
+                ("levels", ctypes.c_int32), ("refine_iters", ctypes.c_int32)]
+
+
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 
@@ -55,6 +66,13 @@ SYMBOLS = {
     "bipart_destroy": (None, [_vp]),
     "bipart_last_error": (ctypes.c_char_p, []),
     "bipart_cut_noalloc": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp, _vp, _i32, _vp, _vp]),
+    "bipart_partition_batch": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _i32]),
+    "bipart_server_create": (ctypes.c_int, [ctypes.c_size_t, _i32, ctypes.POINTER(_vp)]),
+    "bipart_server_submit": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64)]),
+    "bipart_server_wait": (ctypes.c_int, [_vp, ctypes.c_int64, _i32, _p32,
+                                          ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]),
+    "bipart_server_destroy": (None, [_vp]),
     "bipart_kernel_launches": (ctypes.c_int64, []),
     "bipart_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "bipart_profile_read": (ctypes.c_int, [_i32, ctypes.c_char_p, ctypes.c_size_t,
@@ -273,6 +291,79 @@ def cut_noalloc(N, hoff, pins, hw, parts, k, out, stream=None) -> int:
 
 def create_from(g: dict, stream=None) -> Handle:
     return create(g["N"], g["hoff"], g["pins"], g.get("nw"), g.get("hw"), stream=stream)
+
+
+def _instance(g):
+    """Instance struct + the arrays it points to (kept alive by the caller)."""
+    arrs = [_np32(g["hoff"]), _np32(g["pins"]), _np32(g.get("nw")), _np32(g.get("hw"))]
+    inst = Instance(int(g["N"]), int(arrs[0].size - 1), *[_ptr(a) for a in arrs])
+    return inst, arrs
+
+
+def _params(k=2, eps=0.1, policy="LDH", levels=25, iters=2):
+    return Params(int(k), float(eps), _policy(policy), int(levels), int(iters))
+
+
+def partition_batch(graphs, params, workers=0):
+    """bipart_partition_batch: graphs = list of dicts (N, hoff, pins, nw, hw), params = list of
+    dicts (k, eps, policy, levels, iters) or one dict for all.  Returns (parts list, statuses)."""
+    n = len(graphs)
+    if isinstance(params, dict):
+        params = [params] * n
+    keep, insts, outs = [], (Instance * max(n, 1))(), []
+    pars = (Params * max(n, 1))()
+    for i, g in enumerate(graphs):
+        inst, arrs = _instance(g)
+        keep.append(arrs)
+        insts[i] = inst
+        pars[i] = _params(**params[i])
+        outs.append(np.empty(max(int(g["N"]), 1), np.int32))
+    out_ptrs = (ctypes.c_void_p * max(n, 1))(*[o.ctypes.data for o in outs])
+    st = np.zeros(max(n, 1), np.int32)
+    _check(load().bipart_partition_batch(n, ctypes.cast(insts, ctypes.c_void_p),
+                                         ctypes.cast(pars, ctypes.c_void_p),
+                                         ctypes.cast(out_ptrs, ctypes.c_void_p), _ptr(st), int(workers)))
+    return [o[: int(g["N"])] for o, g in zip(outs, graphs)], st[:n]
+
+
+class Server:
+    """bipart_server_*: submit(graph, params) -> ticket; wait(ticket) -> (parts, status, queue_ms,
+    run_ms).  Input arrays and the output buffer are kept alive here until waited for."""
+
+    def __init__(self, hbm_budget_bytes=0, workers=8):
+        h = ctypes.c_void_p()
+        _check(load().bipart_server_create(int(hbm_budget_bytes), int(workers), ctypes.byref(h)))
+        self._h = h
+        self._live = {}
+
+    def submit(self, g, **params):
+        inst, arrs = _instance(g)
+        par = _params(**params)
+        out = np.empty(max(int(g["N"]), 1), np.int32)
+        t = ctypes.c_int64()
+        _check(load().bipart_server_submit(self._h, ctypes.byref(inst), ctypes.byref(par),
+                                           _ptr(out), ctypes.byref(t)))
+        self._live[t.value] = (inst, arrs, par, out, int(g["N"]))
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        st = _i32()
+        qms, rms = ctypes.c_double(), ctypes.c_double()
+        _check(load().bipart_server_wait(self._h, int(ticket), int(timeout_ms), ctypes.byref(st),
+                                         ctypes.byref(qms), ctypes.byref(rms)))
+        inst, arrs, par, out, n = self._live.pop(ticket)
+        return out[:n], st.value, qms.value, rms.value
+
+    def close(self):
+        if self._h:
+            load().bipart_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 @atexit.register

@@ -648,6 +648,48 @@ void finish_create(bipart_graph *g, int32_t N, int32_t E, const int *d_hoff, con
     check_status(g);
 }
 
+}  // namespace
+
+// Workspace for the executor: a handle on its own stream with no hypergraph loaded yet.
+bipart_graph *graph_new(cudaStream_t s) { return new_graph(s); }
+
+// Loads a host CSR into an existing handle, reusing its buffers (validated first).
+void graph_load_host(bipart_graph *g, int32_t N, int32_t E, const int32_t *hoff, const int32_t *pins,
+                     const int32_t *nw, const int32_t *hw) {
+    HandleScope hs(g);
+    validate_host_csr(N, E, hoff, pins, nw, hw);
+    cudaStream_t s = g->stream;
+    const int32_t P = E > 0 ? hoff[E] : 0;
+    int *d_hoff = (int *)g->in_hoff.ensure(sizeof(int) * ((size_t)E + 1), s);
+    int *d_pins = (int *)g->in_pins.ensure(sizeof(int) * (size_t)std::max(P, 1), s);
+    int *d_nw = nw ? (int *)g->in_nw.ensure(sizeof(int) * (size_t)std::max(N, 1), s) : nullptr;
+    int *d_hw = hw ? (int *)g->in_hw.ensure(sizeof(int) * (size_t)std::max(E, 1), s) : nullptr;
+    if (E > 0) BP_CUDA(cudaMemcpyAsync(d_hoff, hoff, sizeof(int) * ((size_t)E + 1), cudaMemcpyHostToDevice, s));
+    if (P > 0) BP_CUDA(cudaMemcpyAsync(d_pins, pins, sizeof(int) * (size_t)P, cudaMemcpyHostToDevice, s));
+    if (d_nw && N > 0) BP_CUDA(cudaMemcpyAsync(d_nw, nw, sizeof(int) * (size_t)N, cudaMemcpyHostToDevice, s));
+    if (d_hw && E > 0) BP_CUDA(cudaMemcpyAsync(d_hw, hw, sizeof(int) * (size_t)E, cudaMemcpyHostToDevice, s));
+    g->plan.reset();
+    g->ex.rec_valid = false;
+    g->hier.valid = false;
+    g->gen++;
+    finish_create(g, N, E, E > 0 ? d_hoff : nullptr, d_pins, d_nw, d_hw);
+}
+
+// Partitions the loaded hypergraph into host memory (blocking on the handle's stream).
+int graph_partition_host(bipart_graph *g, const Params &p, int32_t *out) {
+    HandleScope hs(g);
+    validate_params(p.k, p.eps, p.policy, p.levels, p.iters);
+    const int32_t N = g->L0.N;
+    int *d = (int *)g->part_b.ensure(sizeof(int) * (size_t)std::max(N, 1), g->stream);
+    int st = partition_device(g, p, d);
+    if (N > 0) BP_CUDA(cudaMemcpyAsync(out, d, sizeof(int) * (size_t)N, cudaMemcpyDeviceToHost, g->stream));
+    sync(g);
+    check_status(g);
+    return st;
+}
+
+namespace {
+
 template <class F>
 int guard(F &&f) {
     try {

@@ -1,0 +1,310 @@
+// Batched and served partitioning: a native worker pool on one GPU.
+//
+// Every worker thread owns a private workspace (a handle with its own non-blocking CUDA stream
+// and its own level store and scratch, grown to the largest instance it has seen), so any number
+// of independent hypergraphs are partitioned concurrently: while one worker waits on its stream,
+// the others keep the GPU busy.  A job's result depends only on its own input (the workspaces
+// share nothing), so the output of an instance is the same alone, in a batch, or in any mix of
+// served requests.
+//
+// Batch (bipart_partition_batch): all instances queued largest first (longest-processing-time
+// order keeps the tail short), then waited for.
+// Serving (bipart_server_*): requests arrive at any time; a request is admitted when its
+// estimated working set fits the HBM budget next to the requests already running (continuous
+// batching: new requests start as soon as memory and a worker are free, smaller ones may pass a
+// large one that does not fit yet); each request records its queueing and running time.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace bp {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+    bipart_instance inst;
+    bipart_params params;
+    int32_t *out = nullptr;
+    int64_t ticket = 0;
+    size_t bytes = 0;
+    int status = 0;
+    bool done = false;
+    std::string error;
+    Clock::time_point t_submit, t_start, t_end;
+};
+
+// Estimated device working set of one job: level store over all levels (bounded by a few times
+// level 0 for the shapes of interest), scratch and the input copy.
+size_t estimate_bytes(const bipart_instance &in) {
+    const size_t N = (size_t)std::max(in.num_nodes, 0), E = (size_t)std::max(in.num_hedges, 0);
+    const size_t P = (in.num_hedges > 0 && in.hedge_offsets) ? (size_t)std::max(in.hedge_offsets[in.num_hedges], 0) : 0;
+    return 64 * P + 96 * E + 96 * N + (8u << 20);
+}
+
+class Pool {
+   public:
+    Pool(int workers, size_t budget) : budget_(budget) {
+        BP_CUDA(cudaGetDevice(&device_));
+        if (workers < 1) workers = 1;
+        for (int i = 0; i < workers; ++i) threads_.emplace_back([this]() { run(); });
+    }
+
+    ~Pool() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (std::thread &t : threads_) t.join();
+    }
+
+    // Queues a job; returns its ticket.  Jobs larger than the whole budget are rejected.
+    int64_t submit(const bipart_instance &inst, const bipart_params &p, int32_t *out, bool front_by_size) {
+        auto j = std::make_shared<Job>();
+        j->inst = inst;
+        j->params = p;
+        j->out = out;
+        j->bytes = estimate_bytes(inst);
+        j->t_submit = Clock::now();
+        std::lock_guard<std::mutex> lk(mu_);
+        j->ticket = ++next_ticket_;
+        if (budget_ && j->bytes > budget_) {
+            j->status = BIPART_ERR_OOM;
+            j->error = "request exceeds the whole HBM budget";
+            j->done = true;
+            j->t_start = j->t_end = j->t_submit;
+            jobs_[j->ticket] = j;
+            done_cv_.notify_all();
+            return j->ticket;
+        }
+        jobs_[j->ticket] = j;
+        if (front_by_size) {
+            auto it = std::find_if(queue_.begin(), queue_.end(),
+                                   [&](const std::shared_ptr<Job> &q) { return q->bytes < j->bytes; });
+            queue_.insert(it, j);
+        } else {
+            queue_.push_back(j);
+        }
+        cv_.notify_one();
+        return j->ticket;
+    }
+
+    // Waits for a ticket; timeout_ms < 0 waits forever.  Returns false on timeout.
+    bool wait(int64_t ticket, int timeout_ms, std::shared_ptr<Job> *out) {
+        std::unique_lock<std::mutex> lk(mu_);
+        auto pred = [&]() {
+            auto it = jobs_.find(ticket);
+            return it == jobs_.end() || it->second->done;
+        };
+        if (timeout_ms < 0) done_cv_.wait(lk, pred);
+        else if (!done_cv_.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred)) return false;
+        auto it = jobs_.find(ticket);
+        if (it == jobs_.end()) {
+            out->reset();
+            return true;
+        }
+        *out = it->second;
+        jobs_.erase(it);
+        return true;
+    }
+
+   private:
+    void run() {
+        cudaSetDevice(device_);
+        cudaStream_t s = nullptr;
+        std::unique_ptr<bipart_graph> ws;
+        try {
+            BP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            ws.reset(graph_new(s));
+        } catch (const Fail &) {
+            ws.reset();
+        }
+        for (;;) {
+            std::shared_ptr<Job> j;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&]() { return (stop_ && queue_.empty()) || admissible() != queue_.end(); });
+                if (stop_ && queue_.empty()) break;
+                auto it = admissible();
+                j = *it;
+                queue_.erase(it);
+                in_flight_ += j->bytes;
+            }
+            j->t_start = Clock::now();
+            if (!ws) {
+                j->status = BIPART_ERR_CUDA;
+                j->error = "worker could not create its workspace";
+            } else {
+                try {
+                    const bipart_instance &in = j->inst;
+                    graph_load_host(ws.get(), in.num_nodes, in.num_hedges, in.hedge_offsets,
+                                    in.hedge_pins, in.node_weights, in.hedge_weights);
+                    Params p;
+                    p.k = j->params.k;
+                    p.eps = j->params.epsilon;
+                    p.policy = j->params.policy;
+                    p.levels = j->params.levels;
+                    p.iters = j->params.refine_iters;
+                    j->status = graph_partition_host(ws.get(), p, j->out);
+                } catch (const Fail &e) {
+                    j->status = e.code;
+                    j->error = e.msg;
+                } catch (...) {
+                    j->status = BIPART_ERR_CUDA;
+                    j->error = "unexpected exception";
+                }
+            }
+            j->t_end = Clock::now();
+            {
+                std::lock_guard<std::mutex> lk(mu_);
+                in_flight_ -= j->bytes;
+                j->done = true;
+            }
+            done_cv_.notify_all();
+            cv_.notify_all();  // memory was released: more requests may fit now
+        }
+        ws.reset();
+        if (s) cudaStreamDestroy(s);
+    }
+
+    // First queued job that fits next to the running ones (always the head when nothing runs).
+    std::deque<std::shared_ptr<Job>>::iterator admissible() {
+        if (queue_.empty()) return queue_.end();
+        if (!budget_ || in_flight_ == 0) return queue_.begin();
+        for (auto it = queue_.begin(); it != queue_.end(); ++it)
+            if (in_flight_ + (*it)->bytes <= budget_) return it;
+        return queue_.end();
+    }
+
+    int device_ = 0;
+    size_t budget_ = 0;
+    size_t in_flight_ = 0;
+    bool stop_ = false;
+    int64_t next_ticket_ = 0;
+    std::mutex mu_;
+    std::condition_variable cv_, done_cv_;
+    std::deque<std::shared_ptr<Job>> queue_;
+    std::unordered_map<int64_t, std::shared_ptr<Job>> jobs_;
+    std::vector<std::thread> threads_;
+};
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+}  // namespace
+}  // namespace bp
+
+struct bipart_server_s {
+    std::unique_ptr<bp::Pool> pool;
+};
+
+using namespace bp;
+
+extern "C" int bipart_partition_batch(int32_t n, const bipart_instance *instances,
+                                      const bipart_params *params, int32_t *const *out_parts,
+                                      int32_t *statuses, int32_t workers) {
+    if (n < 0 || (n > 0 && (!instances || !params || !out_parts))) {
+        set_error("bipart_partition_batch: bad arguments");
+        return BIPART_ERR_INVALID_ARG;
+    }
+    if (n == 0) return BIPART_OK;
+    try {
+        if (workers <= 0) workers = std::min<int32_t>(16, std::max<int32_t>(n, 1));
+        Pool pool(workers, 0);
+        std::vector<int64_t> tickets(n);
+        // largest first: queue order by estimated size
+        std::vector<int32_t> order(n);
+        for (int32_t i = 0; i < n; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+            return estimate_bytes(instances[a]) > estimate_bytes(instances[b]);
+        });
+        for (int32_t i : order) tickets[i] = pool.submit(instances[i], params[i], out_parts[i], false);
+        int rc = BIPART_OK;
+        for (int32_t i = 0; i < n; ++i) {
+            std::shared_ptr<Job> j;
+            pool.wait(tickets[i], -1, &j);
+            int st = j ? j->status : BIPART_ERR_CUDA;
+            if (statuses) statuses[i] = st;
+            if (st < 0 && rc == BIPART_OK) {
+                rc = st;
+                set_error("instance " + std::to_string(i) + ": " + (j ? j->error : std::string("lost")));
+            }
+        }
+        return rc;
+    } catch (const Fail &e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (...) {
+        set_error("bipart_partition_batch: unexpected exception");
+        return BIPART_ERR_CUDA;
+    }
+}
+
+extern "C" int bipart_server_create(size_t hbm_budget_bytes, int32_t workers, bipart_server *out) {
+    if (!out) {
+        set_error("out is NULL");
+        return BIPART_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    try {
+        std::unique_ptr<bipart_server_s> s(new bipart_server_s);
+        s->pool.reset(new Pool(workers > 0 ? workers : 8, hbm_budget_bytes));
+        *out = s.release();
+        return BIPART_OK;
+    } catch (const Fail &e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (...) {
+        set_error("bipart_server_create: unexpected exception");
+        return BIPART_ERR_CUDA;
+    }
+}
+
+extern "C" int bipart_server_submit(bipart_server server, const bipart_instance *instance,
+                                    const bipart_params *params, int32_t *out_parts,
+                                    int64_t *ticket) {
+    if (!server || !instance || !params || !ticket || (!out_parts && instance->num_nodes > 0)) {
+        set_error("bipart_server_submit: NULL argument");
+        return BIPART_ERR_INVALID_ARG;
+    }
+    *ticket = server->pool->submit(*instance, *params, out_parts, false);
+    return BIPART_OK;
+}
+
+extern "C" int bipart_server_wait(bipart_server server, int64_t ticket, int32_t timeout_ms,
+                                  int32_t *status, double *queue_ms, double *run_ms) {
+    if (!server) {
+        set_error("server is NULL");
+        return BIPART_ERR_INVALID_ARG;
+    }
+    std::shared_ptr<Job> j;
+    if (!server->pool->wait(ticket, timeout_ms, &j)) {
+        set_error("bipart_server_wait: timed out");
+        return BIPART_ERR_TIMEOUT;
+    }
+    if (!j) {
+        set_error("bipart_server_wait: unknown ticket");
+        return BIPART_ERR_INVALID_ARG;
+    }
+    if (status) *status = j->status;
+    if (queue_ms) *queue_ms = ms_between(j->t_submit, j->t_start);
+    if (run_ms) *run_ms = ms_between(j->t_start, j->t_end);
+    if (j->status < 0) set_error(j->error);
+    return BIPART_OK;
+}
+
+extern "C" void bipart_server_destroy(bipart_server server) { delete server; }

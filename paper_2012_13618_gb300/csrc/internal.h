@@ -166,6 +166,7 @@ struct bipart_graph {
     // k-way workspace: subgraph level 0 and its node map
     bp::Level sub0;
     bp::Buf part_a, part_b, l2g, side_out;
+    bp::Buf in_hoff, in_pins, in_nw, in_hw;   // uploaded input (executor workspaces)
     int64_t total_node_weight = 0;
     bp::Exec ex;
     bp::Plan plan;
@@ -204,6 +205,12 @@ struct ProfScope {
     ProfScope(const char *name, double bytes, cudaStream_t s);
     ~ProfScope();
 };
+
+// ------------------------------------------------------------------------- executor (api.cu)
+bipart_graph *graph_new(cudaStream_t s);
+void graph_load_host(bipart_graph *g, int32_t N, int32_t E, const int32_t *hoff,
+                     const int32_t *pins, const int32_t *nw, const int32_t *hw);
+int graph_partition_host(bipart_graph *g, const Params &p, int32_t *out);
 
 // ------------------------------------------------------------------------- misc (api.cu)
 uint32_t *dev_status(bipart_graph *g);

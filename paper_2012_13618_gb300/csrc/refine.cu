@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -647,11 +648,13 @@ void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, int64_t limit, int
 const unsigned *bisect_status_word(bipart_graph *g) { return &rstate(g)->status0; }
 
 void refine_init() {
-    static bool done = false;
-    if (done) return;
-    BP_CUDA(cudaFuncSetAttribute(k_rebal_move, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(unsigned long long) * kRebalMax)));
-    done = true;
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, []() {
+        err = cudaFuncSetAttribute(k_rebal_move, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(unsigned long long) * kRebalMax));
+    });
+    BP_CUDA(err);
 }
 
 }  // namespace bp

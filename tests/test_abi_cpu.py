@@ -73,3 +73,14 @@ def test_valid_input_without_gpu_reports_cuda_error():
         pytest.skip("a GPU is present")
     rc, out = _create_raw(3, [0, 2, 3], [0, 1, 2])
     assert rc == bp.ERR_CUDA and not out.value
+
+
+def test_batch_and_server_argument_checks():
+    lib = bp.load()
+    assert lib.bipart_partition_batch(-1, None, None, None, None, 0) == bp.ERR_INVALID_ARG
+    assert lib.bipart_partition_batch(2, None, None, None, None, 0) == bp.ERR_INVALID_ARG
+    assert lib.bipart_partition_batch(0, None, None, None, None, 0) == bp.OK
+    assert lib.bipart_server_create(0, 2, None) == bp.ERR_INVALID_ARG
+    assert lib.bipart_server_submit(None, None, None, None, None) == bp.ERR_INVALID_ARG
+    assert lib.bipart_server_wait(None, 1, 0, None, None, None) == bp.ERR_INVALID_ARG
+    lib.bipart_server_destroy(None)
