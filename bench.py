@@ -217,9 +217,22 @@ def run_gpu(args):
     out = torch.empty(N, dtype=torch.int32, device="cuda")
 
     h = bp.create_from(g)
-    for _ in range(args.warmup):
+    # warm-up: the first call runs eagerly and records the level sizes, the second captures the
+    # CUDA graph; a profiled pass then picks the kernel with the largest device time, and the
+    # graph is recaptured with event probes around that kernel only
+    bp.profile_select(None)
+    bp.profile_enable(True)
+    for _ in range(max(args.warmup, 3)):
         h.partition_device(out, k, eps, pol, lev, it)
     torch.cuda.synchronize()
+    prof_all = bp.profile_read()
+    top_name = max(prof_all.items(), key=lambda kv: kv[1][1])[0] if prof_all else None
+    bp.profile_select(top_name)
+    for _ in range(2):
+        h.partition_device(out, k, eps, pol, lev, it)
+    torch.cuda.synchronize()
+    bp.profile_select(top_name)  # reset the totals; the plan keeps its probes
+    warmups = max(args.warmup, 3) + 2
 
     def barrier():
         if ws > 1:
@@ -227,7 +240,6 @@ def run_gpu(args):
             dist.barrier()
 
     # ---------------- device-resident timed region
-    bp.profile_enable(True)
     launches0 = bp.kernel_launches()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -292,7 +304,7 @@ def run_gpu(args):
 
     # ---------------- roofline of the dominant kernel (live CUDA-event timing)
     hbm, src = peaks()
-    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    top = (top_name, prof[top_name]) if top_name in prof else None
     roof = None
     if top:
         name, (cnt, tms, tbytes) = top
@@ -307,7 +319,7 @@ def run_gpu(args):
     if rank == 0:
         cpu = cpu_baseline(g) if (ws == 1 and not args.no_cpu_baseline) else None
         line = {"metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": ws,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+                "steps": args.steps, "warmup": warmups, "ms_per_step": ms_max,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "int32", "data": "synthetic",
                 "config": dict(WORKLOAD, nodes=N, hyperedges=E, pins=P,
@@ -320,8 +332,9 @@ def run_gpu(args):
                 "gpu_launches": int(launches),
                 "roofline": roof,
                 "cpu_baseline": cpu,
-                "kernels": {k2: {"launches": v[0], "ms": v[1], "GBps": (v[2] / (v[1] / 1000) / 1e9) if v[1] else None}
-                            for k2, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
+                "warmup_profile": {k2: {"launches": v[0], "ms": v[1],
+                                        "GBps": (v[2] / (v[1] / 1000) / 1e9) if v[1] else None}
+                                   for k2, v in sorted(prof_all.items(), key=lambda kv: -kv[1][1])}}
         print(json.dumps(line))
     h.close()
     if ws > 1:

@@ -182,6 +182,10 @@ int64_t bipart_kernel_launches(void);
  * each array streamed once, gathers at element size).  Enabling or disabling resets the totals. */
 int bipart_profile_enable(int on);
 
+/* Restricts per-kernel timing to the kernel named `kernel_name` (NULL or "" = all kernels), so
+ * that timing one kernel perturbs the rest as little as possible.  Resets the totals. */
+int bipart_profile_select(const char *kernel_name);
+
 /* Reads entry `idx` of the per-kernel totals (finishes pending timing first).  Returns the number
  * of entries, or INVALID_ARG for an index out of range (idx = -1 only returns the count).
  * `name` receives at most name_len bytes including the terminating zero. */

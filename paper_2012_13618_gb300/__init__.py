@@ -75,6 +75,7 @@ SYMBOLS = {
     "bipart_server_destroy": (None, [_vp]),
     "bipart_kernel_launches": (ctypes.c_int64, []),
     "bipart_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "bipart_profile_select": (ctypes.c_int, [ctypes.c_char_p]),
     "bipart_profile_read": (ctypes.c_int, [_i32, ctypes.c_char_p, ctypes.c_size_t,
                                            ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_double),
@@ -143,6 +144,11 @@ def kernel_launches() -> int:
 
 def profile_enable(on: bool = True):
     _check(load().bipart_profile_enable(1 if on else 0))
+
+
+def profile_select(name=None):
+    """Time only the kernel `name` (None: all)."""
+    _check(load().bipart_profile_select(name.encode() if name else None))
 
 
 def profile_read() -> dict:

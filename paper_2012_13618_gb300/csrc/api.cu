@@ -71,10 +71,18 @@ void sync(bipart_graph *g) {
     BP_CUDA(cudaStreamSynchronize(g->stream));
 }
 
+// Reads the device status word on the handle's own stream (pinned staging), so concurrent
+// handles on other streams are never serialised by it.
+uint32_t read_status_word(bipart_graph *g) {
+    BP_CUDA(cudaMemcpyAsync(g->w.host_small + 1023, dev_status(g), sizeof(uint32_t),
+                            cudaMemcpyDeviceToHost, g->stream));
+    BP_CUDA(cudaStreamSynchronize(g->stream));
+    return g->w.host_small[1023];
+}
+
 void check_status(bipart_graph *g) {
     if (g->ex.capturing) return;
-    uint32_t st = 0;
-    BP_CUDA(cudaMemcpy(&st, dev_status(g), sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    uint32_t st = read_status_word(g);
     if (st & DEV_TIMEOUT) throw Fail{BIPART_ERR_TIMEOUT, "a bounded device-side wait expired"};
     if (st & DEV_OVERFLOW) throw Fail{BIPART_ERR_OOM, "a device-side size limit was exceeded"};
 }
@@ -306,7 +314,7 @@ struct SubEdgeOut {
 __global__ void __launch_bounds__(kBlock)
 k_sub_copy(int E, const int *__restrict__ hoff, const int *__restrict__ pins,
            const int *__restrict__ loc, const int *__restrict__ emap,
-           const int *__restrict__ hoff_out, int *__restrict__ pins_out) {
+           const int *__restrict__ hoff_out, int *__restrict__ pins_out, int *__restrict__ deg) {
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int e0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; e0 < E; e0 += warps * 32) {
@@ -318,7 +326,10 @@ k_sub_copy(int E, const int *__restrict__ hoff, const int *__restrict__ pins,
             int o = hoff_out[ee];
             for (int i = 0; i < d; ++i) {
                 int x = loc[pins[a + i]];
-                if (x >= 0) pins_out[o++] = x;
+                if (x >= 0) {
+                    pins_out[o++] = x;
+                    atomicAdd(deg + x, 1);
+                }
             }
         }
         unsigned bigmask = __ballot_sync(0xffffffffu, ee >= 0 && d > 32);
@@ -332,7 +343,10 @@ k_sub_copy(int E, const int *__restrict__ hoff, const int *__restrict__ pins,
                 int i = i0 + lane;
                 int x = i < db ? loc[pins[ab + i]] : -1;
                 unsigned m = __ballot_sync(0xffffffffu, x >= 0);
-                if (x >= 0) pins_out[o + __popc(m & ((1u << lane) - 1))] = x;
+                if (x >= 0) {
+                    pins_out[o + __popc(m & ((1u << lane) - 1))] = x;
+                    atomicAdd(deg + x, 1);
+                }
                 o += __popc(m);
             }
         }
@@ -375,13 +389,14 @@ void extract_subgraph(bipart_graph *g, const int *d_part, int j) {
     S.b_hoff.ensure(sizeof(int) * ((size_t)L.E + 1), s);
     S.b_pins.ensure(sizeof(int) * (size_t)std::max(L.P, 1), s);
     if (!S.unit_hw) S.b_hw.ensure(sizeof(int) * (size_t)std::max(L.E, 1), s);
+    int *deg = degree_counters(g, L.N);  // subgraph degrees, counted while its pins are written
     if (L.E > 0) {
         int gw = grid_for((int64_t)(L.E + 31) / 32 * 32);
         k_sub_count<<<gw, kBlock, 0, s>>>(L.E, L.hoff(), L.pins(), loc, cnt);
         BP_LAUNCH();
         scan(L.E, SubEdgeIn{cnt}, SubEdgeOut{L.E, L.hw(), S.hoff(), S.unit_hw ? nullptr : S.b_hw.as<int>(), emap, small + 2},
              w.scan.ensure(scan_state_bytes(L.E), s), dev_status(g), s);
-        k_sub_copy<<<gw, kBlock, 0, s>>>(L.E, L.hoff(), L.pins(), loc, emap, S.hoff(), S.pins());
+        k_sub_copy<<<gw, kBlock, 0, s>>>(L.E, L.hoff(), L.pins(), loc, emap, S.hoff(), S.pins(), deg);
         BP_LAUNCH();
     } else {
         BP_CUDA(cudaMemsetAsync(S.hoff(), 0, sizeof(int), s));
@@ -496,8 +511,7 @@ int bisect_top(bipart_graph *g, const Params &p, uint8_t *d_side, int *nlev) {
         BP_CUDA(cudaGraphLaunch(pl.exec, g->stream));
         for (int64_t i = 0; i < pl.launches; ++i) note_launch();
         sync(g);
-        uint32_t st = 0;
-        BP_CUDA(cudaMemcpy(&st, dev_status(g), sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        const uint32_t st = read_status_word(g);
         if (!(st & DEV_PLAN_MISMATCH)) {
             check_status(g);
             prof_collect(pl.probes);
@@ -955,6 +969,7 @@ struct ProfTot {
 std::mutex g_prof_mu;
 bool g_prof_on = false;
 int g_prof_epoch = 0;
+std::string g_prof_only;
 std::vector<ProfRec> g_prof_pending;
 std::vector<cudaEvent_t> g_prof_pool;
 std::map<std::string, ProfTot> g_prof_tot;
@@ -1010,6 +1025,7 @@ void prof_collect(const std::vector<Probe> &probes) {
 
 ProfScope::ProfScope(const char *name, double bytes, cudaStream_t s) {
     if (!g_prof_on) return;
+    if (!g_prof_only.empty() && g_prof_only != name) return;
     if (tl_capturing) {
         // inside a captured plan: event nodes at the top level of the graph only (conditional
         // bodies may not hold event nodes); read back after every replay
@@ -1052,6 +1068,16 @@ extern "C" int bipart_profile_enable(int on) {
     bp::g_prof_tot.clear();
     if (bp::g_prof_on != (on != 0)) bp::g_prof_epoch++;  // plans are recaptured with/without probes
     bp::g_prof_on = on != 0;
+    return BIPART_OK;
+}
+
+extern "C" int bipart_profile_select(const char *kernel_name) {
+    std::lock_guard<std::mutex> lk(bp::g_prof_mu);
+    bp::prof_drain();
+    bp::g_prof_tot.clear();
+    std::string only = kernel_name ? kernel_name : "";
+    if (only != bp::g_prof_only) bp::g_prof_epoch++;
+    bp::g_prof_only = only;
     return BIPART_OK;
 }
 

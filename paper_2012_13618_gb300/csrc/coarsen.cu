@@ -298,36 +298,31 @@ __device__ __forceinline__ void block_seg_range(const int *hoff, int E, int b0, 
     __syncthreads();
 }
 
-// Copies the distinct pins of kept hyperedges from scratch (at fine offsets) to the coarse CSR.
-__global__ void __launch_bounds__(kBlock)
+// Copies the distinct pins of kept hyperedges from scratch (at fine offsets) to the coarse CSR
+// and counts the coarse node degrees (integer atomics) for the incidence build.  Load-balanced
+// over fine pin slots: per-hyperedge values are loaded once per run of slots.
+__global__ void __launch_bounds__(kLbBlock)
 k_seg_copy(int E, int P, const int *__restrict__ hoff, const int *__restrict__ scratch,
            const int *__restrict__ cnt, const int *__restrict__ emap,
-           const int *__restrict__ hoff_out, int *__restrict__ pins_out) {
-    __shared__ int rng[2];
-    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < P; b0 += (int64_t)gridDim.x * blockDim.x) {
-        int b1 = (int)(b0 + blockDim.x < P ? b0 + blockDim.x : P);
-        __syncthreads();
-        block_seg_range(hoff, E, (int)b0, b1, rng);
-        int i = (int)b0 + threadIdx.x;
-        if (i < b1) {
-            int e = seg_of(hoff, i, rng[0], rng[1]);
-            int k = i - hoff[e];
-            int ee = emap[e];
-            if (ee >= 0 && k < cnt[e]) pins_out[hoff_out[ee] + k] = scratch[i];
+           const int *__restrict__ hoff_out, int *__restrict__ pins_out, int *__restrict__ deg) {
+    lb_runs(hoff, E, P, [&](int e, int a, int b) {
+        const int ee = __ldg(emap + e);
+        if (ee < 0) return;
+        const int base = __ldg(hoff + e), c = __ldg(cnt + e), o = __ldg(hoff_out + ee);
+        const int stop = base + c < b ? base + c : b;
+        for (int i = a; i < stop; ++i) {
+            const int v = __ldg(scratch + i);
+            pins_out[o + (i - base)] = v;
+            atomicAdd(deg + v, 1);
         }
-    }
+    });
 }
 
 __global__ void k_fill(int n, int val, int *__restrict__ a) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = val;
 }
 
-// ------------------------------------------------------------------ incidence (transpose)
-__global__ void k_count_deg(int P, const int *__restrict__ pins, int *__restrict__ deg) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x)
-        atomicAdd(&deg[pins[i]], 1);
-}
-
+// ------------------------------------------------------------------------------- incidence
 struct DegIn {
     const int *deg;
     __device__ uint64_t operator()(int64_t v) const { return (uint64_t)deg[v]; }
@@ -342,20 +337,42 @@ struct DegOut {
     }
 };
 
-__global__ void __launch_bounds__(kBlock)
+// Fills the node -> hyperedge incidence: every pin slot takes the next free position of its node
+// (cursor starts at the node's offset).  Each thread owns kLbItems consecutive slots: it finds
+// their hyperedges with one search, then issues all its atomics before any store, so the
+// atomics' round trips overlap.  The order inside a node's list depends on the atomics' order;
+// every consumer is order-independent.
+__global__ void __launch_bounds__(kLbBlock)
 k_fill_adj(int E, int P, const int *__restrict__ hoff, const int *__restrict__ pins,
            int *__restrict__ cursor, int *__restrict__ nadj) {
-    __shared__ int rng[2];
-    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < P; b0 += (int64_t)gridDim.x * blockDim.x) {
-        int b1 = (int)(b0 + blockDim.x < P ? b0 + blockDim.x : P);
+    __shared__ int s_rng[2];
+    for (int64_t t0 = (int64_t)blockIdx.x * kLbTile; t0 < P; t0 += (int64_t)gridDim.x * kLbTile) {
+        const int j0 = (int)t0;
+        const int j1 = (int)(t0 + kLbTile < P ? t0 + kLbTile : P);
         __syncthreads();
-        block_seg_range(hoff, E, (int)b0, b1, rng);
-        int i = (int)b0 + threadIdx.x;
-        if (i < b1) {
-            int e = seg_of(hoff, i, rng[0], rng[1]);
-            int pos = atomicAdd(&cursor[pins[i]], 1);
-            nadj[pos] = e;
+        if (threadIdx.x == 0) s_rng[0] = lb_seg(hoff, j0, 0, E - 1);
+        if (threadIdx.x == 32) s_rng[1] = lb_seg(hoff, j1 - 1, 0, E - 1);
+        __syncthreads();
+        const int j = j0 + threadIdx.x * kLbItems;
+        if (j >= j1) continue;
+        const int n = j1 - j < kLbItems ? j1 - j : kLbItems;
+        int s = lb_seg(hoff, j, s_rng[0], s_rng[1]);
+        int send = __ldg(hoff + s + 1);
+        int v[kLbItems], e[kLbItems], pos[kLbItems];
+#pragma unroll
+        for (int k = 0; k < kLbItems; ++k) {
+            if (k < n) {
+                while (j + k >= send) { ++s; send = __ldg(hoff + s + 1); }
+                e[k] = s;
+                v[k] = __ldg(pins + j + k);
+            }
         }
+#pragma unroll
+        for (int k = 0; k < kLbItems; ++k)
+            if (k < n) pos[k] = atomicAdd(cursor + v[k], 1);
+#pragma unroll
+        for (int k = 0; k < kLbItems; ++k)
+            if (k < n) nadj[pos[k]] = e[k];
     }
 }
 
@@ -509,7 +526,7 @@ void seg_unique(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const in
 // Sorted-unique of every hyperedge's (mapped) pins into the coarse CSR of `c`.
 // Sets c.E and c.P.  `map` null means identity (level-0 normalisation).
 void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int *pins,
-              const int *hw, const int *map, Level &c) {
+              const int *hw, const int *map, Level &c, int *deg) {
     cudaStream_t s = g->stream;
     Work &w = g->w;
     int *scratch = (int *)w.p_a.ensure(sizeof(int) * (size_t)std::max(P, 1), s);
@@ -530,8 +547,9 @@ void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int 
             scan(E, CompactIn{cnt}, out, w.scan.ensure(scan_state_bytes(E), s), dev_status(g), s);
         }
         {
-            ProfScope ps("contract_copy", 8.0 * P + 12.0 * E, s);
-            k_seg_copy<<<grid_for(P), kBlock, 0, s>>>(E, P, hoff, scratch, cnt, emap, c.hoff(), c.pins());
+            // scratch, coarse pins, degree atomics, per-hyperedge offsets
+            ProfScope ps("contract_copy", 12.0 * P + 12.0 * E, s);
+            k_seg_copy<<<lb_grid(P), kLbBlock, 0, s>>>(E, P, hoff, scratch, cnt, emap, c.hoff(), c.pins(), deg);
             BP_LAUNCH();
         }
     } else {
@@ -548,6 +566,8 @@ void distinct_counts(bipart_graph *g, Level &L, const int *d_map, int *cnt) {
     seg_unique(g, L.E, L.P, L.hoff(), L.pins(), d_map, scratch, cnt);
 }
 
+// Node -> hyperedge incidence of a level whose degrees were counted by its contraction
+// (deg[N], in the per-node scratch n_a).
 void build_incidence(bipart_graph *g, Level &L) {
     cudaStream_t s = g->stream;
     Work &w = g->w;
@@ -557,14 +577,8 @@ void build_incidence(bipart_graph *g, Level &L) {
         BP_CUDA(cudaMemsetAsync(L.noff(), 0, sizeof(int), s));
         return;
     }
-    int *deg = (int *)w.n_a.ensure(sizeof(int) * (size_t)L.N, s);
+    int *deg = w.n_a.as<int>();
     int *cursor = (int *)w.n_b.ensure(sizeof(int) * (size_t)L.N, s);
-    BP_CUDA(cudaMemsetAsync(deg, 0, sizeof(int) * (size_t)L.N, s));
-    if (L.P > 0) {
-        ProfScope ps("incidence_count", 8.0 * L.P, s);
-        k_count_deg<<<grid_for(L.P), kBlock, 0, s>>>(L.P, L.pins(), deg);
-        BP_LAUNCH();
-    }
     {
         ProfScope ps("incidence_offsets", 12.0 * L.N, s);
         scan(L.N, DegIn{deg}, DegOut{L.N, L.noff(), cursor}, w.scan.ensure(scan_state_bytes(L.N), s),
@@ -572,9 +586,16 @@ void build_incidence(bipart_graph *g, Level &L) {
     }
     if (L.P > 0) {
         ProfScope ps("incidence_fill", 12.0 * L.P + 4.0 * L.E, s);
-        k_fill_adj<<<grid_for(L.P), kBlock, 0, s>>>(L.E, L.P, L.hoff(), L.pins(), cursor, L.nadj());
+        k_fill_adj<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.E, L.P, L.hoff(), L.pins(), cursor, L.nadj());
         BP_LAUNCH();
     }
+}
+
+// Zeroed degree counters for a level of N nodes (filled by the contraction's copy).
+int *degree_counters(bipart_graph *g, int32_t N) {
+    int *deg = (int *)g->w.n_a.ensure(sizeof(int) * (size_t)std::max(N, 1), g->stream);
+    if (N > 0) BP_CUDA(cudaMemsetAsync(deg, 0, sizeof(int) * (size_t)N, g->stream));
+    return deg;
 }
 
 void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t *d_hoff,
@@ -587,7 +608,7 @@ void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t
         P = (int32_t)g->w.host_small[0];
     }
     L.N = N;
-    contract(g, E, P, d_hoff, d_pins, d_hw, nullptr, L);
+    contract(g, E, P, d_hoff, d_pins, d_hw, nullptr, L, degree_counters(g, N));
     L.b_nw.ensure(sizeof(int) * (size_t)std::max(N, 1), s);
     if (d_nw) {
         BP_CUDA(cudaMemcpyAsync(L.nw(), d_nw, sizeof(int) * (size_t)N, cudaMemcpyDeviceToDevice, s));
@@ -662,7 +683,7 @@ void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy) {
         k_cmap<<<grid_for(N), kBlock, 0, s>>>(N, grp, gcid, f.nw(), f.cmap(), c.nw());
         BP_LAUNCH();
     }
-    contract(g, E, f.P, f.hoff(), f.pins(), f.hw(), f.cmap(), c);
+    contract(g, E, f.P, f.hoff(), f.pins(), f.hw(), f.cmap(), c, degree_counters(g, Nc));
     build_incidence(g, c);
     c.b_cmap.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);
     c.b_match.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);

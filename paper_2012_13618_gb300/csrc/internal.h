@@ -182,8 +182,10 @@ void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t
                   const int32_t *d_pins, const int32_t *d_nw, const int32_t *d_hw);
 // Algorithm 1 + 2 on `f`, producing `c` (sizes read back to the host).
 void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy);
-// Node -> hyperedge incidence of a level whose hyperedge CSR is complete.
+// Node -> hyperedge incidence of a level whose hyperedge CSR is complete and whose node degrees
+// were counted into degree_counters(g, N) while its pins were written.
 void build_incidence(bipart_graph *g, Level &L);
+int *degree_counters(bipart_graph *g, int32_t N);
 
 // -------------------------------------------------------------------- refinement (refine.cu)
 // Runs Algorithms 3, 5 (+ rebalance) over the hierarchy; writes side of level 0.  The status

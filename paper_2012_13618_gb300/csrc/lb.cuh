@@ -58,6 +58,32 @@ __device__ __forceinline__ void lb_for_each(const int *__restrict__ off, int nse
     }
 }
 
+// Calls fn(s, a, b) for every maximal run [a, b) of this thread's items that lies in segment s,
+// in item order (per-segment values can then be loaded once per run).
+template <class Fn>
+__device__ __forceinline__ void lb_runs(const int *__restrict__ off, int nseg, int total, Fn fn) {
+    __shared__ int s_rng[2];
+    for (int64_t t0 = (int64_t)blockIdx.x * kLbTile; t0 < total; t0 += (int64_t)gridDim.x * kLbTile) {
+        const int j0 = (int)t0;
+        const int j1 = (int)(t0 + kLbTile < total ? t0 + kLbTile : total);
+        __syncthreads();
+        if (threadIdx.x == 0) s_rng[0] = lb_seg(off, j0, 0, nseg - 1);
+        if (threadIdx.x == 32) s_rng[1] = lb_seg(off, j1 - 1, 0, nseg - 1);
+        __syncthreads();
+        int j = j0 + threadIdx.x * kLbItems;
+        if (j >= j1) continue;
+        const int je = j + kLbItems < j1 ? j + kLbItems : j1;
+        int s = lb_seg(off, j, s_rng[0], s_rng[1]);
+        while (j < je) {
+            const int send = __ldg(off + s + 1);
+            const int b = send < je ? send : je;
+            if (b > j) fn(s, j, b);
+            j = b > j ? b : j;
+            ++s;
+        }
+    }
+}
+
 inline int lb_grid(int64_t total, int cap = 152 * 8) {
     int64_t b = (total + kLbTile - 1) / kLbTile;
     if (b < 1) b = 1;
