@@ -590,6 +590,8 @@ int partition_device(bipart_graph *g, const Params &p, int *d_parts) {
     return status;
 }
 
+}  // namespace
+
 void validate_params(int32_t k, double eps, int32_t policy, int32_t levels, int32_t iters) {
     if (k < 1 || (k & (k - 1)) != 0) throw Fail{BIPART_ERR_INVALID_ARG, "k must be a power of two >= 1"};
     if (!(eps >= 0.0 && eps <= 1000.0)) throw Fail{BIPART_ERR_INVALID_ARG, "epsilon must be in [0, 1000]"};
@@ -627,6 +629,9 @@ void validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t 
     if (sn >= (int64_t(1) << 31) || se >= (int64_t(1) << 31))
         throw Fail{BIPART_ERR_INVALID_CSR, "weight sum must stay below 2^31"};
 }
+
+namespace {
+
 
 }  // namespace
 }  // namespace bp

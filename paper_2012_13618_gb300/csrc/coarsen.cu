@@ -19,6 +19,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "coarsen_dev.cuh"
 #include "lb.cuh"
 #include "scan.cuh"
 
@@ -27,10 +28,7 @@ namespace bp {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kSmallDeg = 8;      // hyperedges up to this degree: one thread each
-constexpr int kMidDeg = 1024;     // up to this degree: one warp each (register bitonic sort)
-constexpr int kBigThreads = 512;  // above: one block each (shared-memory bitmap windows)
-constexpr int kBigWords = 8192;   // 32 KB bitmap = 262,144 ids per window
+constexpr int kBigThreads = 512;  // block tier: one block per hyperedge
 
 inline int grid_for(int64_t n, int per_block = kBlock, int cap = 152 * 16) {
     int64_t b = (n + per_block - 1) / per_block;
@@ -38,460 +36,85 @@ inline int grid_for(int64_t n, int per_block = kBlock, int cap = 152 * 16) {
     return (int)std::min<int64_t>(b, cap);
 }
 
-// ------------------------------------------------------------------ small fixed sorting network
-template <int n>
-__device__ __forceinline__ void sort_net(int (&v)[n]) {
-    // odd-even transposition sort: n rounds of compare-exchange on alternating pairs
-#pragma unroll
-    for (int r = 0; r < n; ++r) {
-#pragma unroll
-        for (int i = (r & 1); i + 1 < n; i += 2) {
-            int a = v[i], b = v[i + 1];
-            v[i] = min(a, b);
-            v[i + 1] = max(a, b);
-        }
-    }
-}
-
-// ------------------------------------------------------------------ warp bitonic sort, R per lane
-// Blocked layout: element index = lane * R + r.  Sorts 32 * R ints ascending.
-template <int R>
-__device__ __forceinline__ void warp_bitonic(int (&v)[R]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 2; k <= 32 * R; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j >= R) {
-                const int lj = j / R;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int idx = lane * R + r;
-                    int p = __shfl_xor_sync(0xffffffffu, v[r], lj);
-                    bool up = (idx & k) == 0;
-                    bool lower = (idx & j) == 0;
-                    v[r] = (lower == up) ? min(v[r], p) : max(v[r], p);
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int r2 = r ^ j;
-                    if (r2 > r) {
-                        const int idx = lane * R + r;
-                        bool up = (idx & k) == 0;
-                        int a = v[r], b = v[r2];
-                        int lo = min(a, b), hi = max(a, b);
-                        v[r] = up ? lo : hi;
-                        v[r2] = up ? hi : lo;
-                    }
-                }
-            }
-        }
-    }
-}
-
-template <bool MAP>
-__device__ __forceinline__ int mapped(const int *__restrict__ pins, const int *__restrict__ cmap,
-                                      int i) {
-    int p = __ldg(pins + i);
-    return MAP ? __ldg(cmap + p) : p;
-}
-
-// Warp-cooperative sorted-unique of one hyperedge of degree d <= 32 * R.
-template <int R, bool MAP>
-__device__ __forceinline__ int warp_unique(const int *pins, const int *cmap, int a, int d,
-                                           int *out) {
-    const int lane = threadIdx.x & 31;
-    int v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        int idx = lane * R + r;
-        v[r] = idx < d ? mapped<MAP>(pins, cmap, a + idx) : INT_MAX;
-    }
-    warp_bitonic<R>(v);
-    int prev_last = __shfl_up_sync(0xffffffffu, v[R - 1], 1);
-    int keep_cnt = 0;
-    bool keep[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        int idx = lane * R + r;
-        int prev = r == 0 ? prev_last : v[r - 1];
-        keep[r] = idx < d && (idx == 0 || v[r] != prev);
-        keep_cnt += keep[r];
-    }
-    int incl = warp_inclusive_scan(keep_cnt);
-    int pos = incl - keep_cnt;
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-        if (keep[r]) out[pos++] = v[r];
-    return __shfl_sync(0xffffffffu, incl, 31);
-}
-
 }  // namespace
 
-// Small tier: one thread per hyperedge of degree <= 8 (the vast majority); larger hyperedges are
-// appended to the mid / big work lists (list order is irrelevant: every hyperedge writes only
-// its own slots).
+// Grid kernels: one launch per phase (device code in coarsen_dev.cuh).
 template <bool MAP>
 __global__ void __launch_bounds__(kBlock)
 k_seg_small(int E, const int *__restrict__ hoff, const int *__restrict__ pins,
             const int *__restrict__ cmap, int *__restrict__ scratch, int *__restrict__ cnt,
             int *__restrict__ mid_list, int *__restrict__ big_list, int *__restrict__ counters) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
-        int a = hoff[e], d = hoff[e + 1] - a;
-        if (d > kSmallDeg) {
-            if (d > kMidDeg) big_list[atomicAdd(&counters[1], 1)] = e;
-            else mid_list[atomicAdd(&counters[0], 1)] = e;
-            continue;
-        }
-        int v[kSmallDeg];
-#pragma unroll
-        for (int k = 0; k < kSmallDeg; ++k) v[k] = k < d ? mapped<MAP>(pins, cmap, a + k) : INT_MAX;
-        sort_net<kSmallDeg>(v);
-        int m = 0;
-#pragma unroll
-        for (int k = 0; k < kSmallDeg; ++k) {
-            bool keep = k < d && (k == 0 || v[k] != v[k - 1]);
-            if (keep) scratch[a + m] = v[k];
-            m += keep;
-        }
-        cnt[e] = m;
-    }
+    d_seg_small<MAP>(GridTeam(), E, hoff, pins, cmap, scratch, cnt, mid_list, big_list, counters);
 }
 
-// Mid tier: one warp per listed hyperedge (8 < d <= 1024), register bitonic sort.
 template <bool MAP>
 __global__ void __launch_bounds__(kBlock)
 k_seg_mid(const int *__restrict__ hoff, const int *__restrict__ pins, const int *__restrict__ cmap,
           int *__restrict__ scratch, int *__restrict__ cnt, const int *__restrict__ list,
           const int *__restrict__ counters) {
-    const int n = counters[0];
-    const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += warps) {
-        int e = list[w];
-        int a = hoff[e], d = hoff[e + 1] - a;
-        int *out = scratch + a;
-        int m;
-        if (d <= 32) m = warp_unique<1, MAP>(pins, cmap, a, d, out);
-        else if (d <= 64) m = warp_unique<2, MAP>(pins, cmap, a, d, out);
-        else if (d <= 128) m = warp_unique<4, MAP>(pins, cmap, a, d, out);
-        else if (d <= 256) m = warp_unique<8, MAP>(pins, cmap, a, d, out);
-        else if (d <= 512) m = warp_unique<16, MAP>(pins, cmap, a, d, out);
-        else m = warp_unique<32, MAP>(pins, cmap, a, d, out);
-        if (lane == 0) cnt[e] = m;
-    }
+    d_seg_mid<MAP>(GridTeam(), hoff, pins, cmap, scratch, cnt, list, counters);
 }
 
-// Big tier: one block per listed hyperedge (d > 1024).  Distinct values are found with a
-// shared-memory bitmap over a window of ids [lo, lo + 32 * kBigWords); windows sweep the range
-// [min, max] of the mapped pins, so the output comes out ascending without a sort.
 template <bool MAP>
 __global__ void __launch_bounds__(kBigThreads)
 k_seg_big(const int *__restrict__ hoff, const int *__restrict__ pins, const int *__restrict__ cmap,
           int *__restrict__ scratch, int *__restrict__ cnt, const int *__restrict__ list,
           const int *__restrict__ counters) {
     __shared__ uint32_t bits[kBigWords];
-    __shared__ int red[33];
-    __shared__ int s_minmax[2];
-    const int n = counters[1];
-    for (int w = blockIdx.x; w < n; w += gridDim.x) {
-        const int e = list[w];
-        const int a = hoff[e], d = hoff[e + 1] - a;
-        int lo = INT_MAX, hi = INT_MIN;
-        for (int i = threadIdx.x; i < d; i += blockDim.x) {
-            int x = mapped<MAP>(pins, cmap, a + i);
-            lo = min(lo, x);
-            hi = max(hi, x);
-        }
-        lo = warp_min(lo);
-        hi = warp_max(hi);
-        if (threadIdx.x == 0) { s_minmax[0] = INT_MAX; s_minmax[1] = INT_MIN; }
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) { atomicMin(&s_minmax[0], lo); atomicMax(&s_minmax[1], hi); }
-        __syncthreads();
-        lo = s_minmax[0];
-        hi = s_minmax[1];
-        int written = 0;
-        for (int64_t wlo = lo; wlo <= hi; wlo += 32 * kBigWords) {
-            const int64_t rest = (int64_t)hi - wlo + 1;
-            const int64_t span = rest < 32 * (int64_t)kBigWords ? rest : 32 * (int64_t)kBigWords;
-            const int words = (int)((span + 31) >> 5);
-            for (int i = threadIdx.x; i < words; i += blockDim.x) bits[i] = 0;
-            __syncthreads();
-            for (int i = threadIdx.x; i < d; i += blockDim.x) {
-                int64_t x = (int64_t)mapped<MAP>(pins, cmap, a + i) - wlo;
-                if (x >= 0 && x < span) atomicOr(&bits[x >> 5], 1u << (x & 31));
-            }
-            __syncthreads();
-            // each thread owns a contiguous run of words; block scan of their popcounts
-            const int per = (words + blockDim.x - 1) / blockDim.x;
-            const int w0 = threadIdx.x * per;
-            int c = 0;
-            for (int q = 0; q < per; ++q)
-                if (w0 + q < words) c += __popc(bits[w0 + q]);
-            int tot;
-            int pos = block_exclusive_scan<int>(c, red, &tot);
-            int *out = scratch + a + written;
-            for (int q = 0; q < per; ++q) {
-                if (w0 + q >= words) break;
-                uint32_t b = bits[w0 + q];
-                while (b) {
-                    int t = __ffs(b) - 1;
-                    b &= b - 1;
-                    out[pos++] = (int)(wlo + 32 * (int64_t)(w0 + q) + t);
-                }
-            }
-            written += tot;
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) cnt[e] = written;
-        __syncthreads();
-    }
+    d_seg_big<MAP>(GridTeam(), hoff, pins, cmap, scratch, cnt, list, counters, bits);
 }
 
-// Compaction offsets: value = (kept << 31) | distinct pins for hyperedges with >= 2 distinct pins.
-struct CompactIn {
-    const int *cnt;
-    __device__ uint64_t operator()(int64_t e) const {
-        int c = cnt[e];
-        return c >= 2 ? ((1ull << 31) | (uint64_t)c) : 0ull;
-    }
-};
-struct CompactOut {
-    int64_t n;
-    const int *hw_in;
-    int *hoff_out, *hw_out, *emap, *sizes;  // sizes[0] = E', sizes[1] = P'
-    __device__ void operator()(int64_t e, uint64_t pre, uint64_t val) const {
-        int ei = (int)(pre >> 31), pi = (int)(pre & 0x7fffffffu);
-        if (val) {
-            hoff_out[ei] = pi;
-            if (hw_out) hw_out[ei] = hw_in ? hw_in[e] : 1;
-            emap[e] = ei;
-        } else {
-            emap[e] = -1;
-        }
-        if (e == n - 1) {
-            uint64_t t = pre + val;
-            int Et = (int)(t >> 31), Pt = (int)(t & 0x7fffffffu);
-            hoff_out[Et] = Pt;
-            sizes[0] = Et;
-            sizes[1] = Pt;
-        }
-    }
-};
-
-// Segment of pin slot i: largest e with hoff[e] <= i, searched within [e_lo, e_hi].
-__device__ __forceinline__ int seg_of(const int *hoff, int i, int e_lo, int e_hi) {
-    while (e_lo < e_hi) {
-        int m = (e_lo + e_hi + 1) >> 1;
-        if (hoff[m] <= i) e_lo = m;
-        else e_hi = m - 1;
-    }
-    return e_lo;
-}
-
-// Block-level search bounds for pin slots [b0, b1): first and last segment touched.
-__device__ __forceinline__ void block_seg_range(const int *hoff, int E, int b0, int b1, int *s_rng) {
-    if (threadIdx.x == 0) s_rng[0] = seg_of(hoff, b0, 0, E - 1);
-    if (threadIdx.x == 1) s_rng[1] = seg_of(hoff, b1 - 1, 0, E - 1);
-    __syncthreads();
-}
-
-// Copies the distinct pins of kept hyperedges from scratch (at fine offsets) to the coarse CSR
-// and counts the coarse node degrees (integer atomics) for the incidence build.  Load-balanced
-// over fine pin slots: per-hyperedge values are loaded once per run of slots.
 __global__ void __launch_bounds__(kLbBlock)
 k_seg_copy(int E, int P, const int *__restrict__ hoff, const int *__restrict__ scratch,
            const int *__restrict__ cnt, const int *__restrict__ emap,
            const int *__restrict__ hoff_out, int *__restrict__ pins_out, int *__restrict__ deg) {
-    lb_runs(hoff, E, P, [&](int e, int a, int b) {
-        const int ee = __ldg(emap + e);
-        if (ee < 0) return;
-        const int base = __ldg(hoff + e), c = __ldg(cnt + e), o = __ldg(hoff_out + ee);
-        const int stop = base + c < b ? base + c : b;
-        for (int i = a; i < stop; ++i) {
-            const int v = __ldg(scratch + i);
-            pins_out[o + (i - base)] = v;
-            atomicAdd(deg + v, 1);
-        }
-    });
+    d_seg_copy(GridTeam(), E, P, hoff, scratch, cnt, emap, hoff_out, pins_out, deg);
 }
 
 __global__ void k_fill(int n, int val, int *__restrict__ a) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = val;
 }
 
-// ------------------------------------------------------------------------------- incidence
-struct DegIn {
-    const int *deg;
-    __device__ uint64_t operator()(int64_t v) const { return (uint64_t)deg[v]; }
-};
-struct DegOut {
-    int64_t n;
-    int *noff, *cursor;
-    __device__ void operator()(int64_t v, uint64_t pre, uint64_t val) const {
-        noff[v] = (int)pre;
-        cursor[v] = (int)pre;
-        if (v == n - 1) noff[n] = (int)(pre + val);
-    }
-};
-
-// Fills the node -> hyperedge incidence: every pin slot takes the next free position of its node
-// (cursor starts at the node's offset).  Each thread owns kLbItems consecutive slots: it finds
-// their hyperedges with one search, then issues all its atomics before any store, so the
-// atomics' round trips overlap.  The order inside a node's list depends on the atomics' order;
-// every consumer is order-independent.
 __global__ void __launch_bounds__(kLbBlock)
 k_fill_adj(int E, int P, const int *__restrict__ hoff, const int *__restrict__ pins,
            int *__restrict__ cursor, int *__restrict__ nadj) {
-    __shared__ int s_rng[2];
-    for (int64_t t0 = (int64_t)blockIdx.x * kLbTile; t0 < P; t0 += (int64_t)gridDim.x * kLbTile) {
-        const int j0 = (int)t0;
-        const int j1 = (int)(t0 + kLbTile < P ? t0 + kLbTile : P);
-        __syncthreads();
-        if (threadIdx.x == 0) s_rng[0] = lb_seg(hoff, j0, 0, E - 1);
-        if (threadIdx.x == 32) s_rng[1] = lb_seg(hoff, j1 - 1, 0, E - 1);
-        __syncthreads();
-        const int j = j0 + threadIdx.x * kLbItems;
-        if (j >= j1) continue;
-        const int n = j1 - j < kLbItems ? j1 - j : kLbItems;
-        int s = lb_seg(hoff, j, s_rng[0], s_rng[1]);
-        int send = __ldg(hoff + s + 1);
-        int v[kLbItems], e[kLbItems], pos[kLbItems];
-#pragma unroll
-        for (int k = 0; k < kLbItems; ++k) {
-            if (k < n) {
-                while (j + k >= send) { ++s; send = __ldg(hoff + s + 1); }
-                e[k] = s;
-                v[k] = __ldg(pins + j + k);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < kLbItems; ++k)
-            if (k < n) pos[k] = atomicAdd(cursor + v[k], 1);
-#pragma unroll
-        for (int k = 0; k < kLbItems; ++k)
-            if (k < n) nadj[pos[k]] = e[k];
-    }
+    d_fill_adj(GridTeam(), E, P, hoff, pins, cursor, nadj);
 }
 
-// ------------------------------------------------------------------ Algorithm 1
 __global__ void k_hedge_key(int E, int policy, const int *__restrict__ hoff,
                             const int *__restrict__ hw, unsigned long long *__restrict__ hkey) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
-        uint32_t deg = (uint32_t)(hoff[e + 1] - hoff[e]);
-        uint32_t w = hw ? (uint32_t)hw[e] : 1u;
-        uint32_t h = mix32((uint32_t)e);
-        uint32_t pr = policy_priority(policy, deg, w, h);
-        hkey[e] = ((unsigned long long)pr << 32) | h;
-    }
+    d_hedge_key(GridTeam(), E, policy, hoff, hw, hkey);
 }
 
-// Every node takes the incident hyperedge with the smallest key (lexicographic (priority, hash);
-// the hash is a bijection so the key also identifies the hyperedge).  Load-balanced over the
-// incidence array: per-node partial minima are combined with 64-bit atomicMin, whose result does
-// not depend on the order of the atomics.
 __global__ void __launch_bounds__(kLbBlock)
 k_match_min(int N, int P, const int *__restrict__ noff, const int *__restrict__ nadj,
             const unsigned long long *__restrict__ hkey, unsigned long long *__restrict__ nkey) {
-    lb_for_each<unsigned long long>(
-        noff, N, P, ~0ull,
-        [&](int, int j, unsigned long long acc) {
-            unsigned long long k = __ldg(hkey + __ldg(nadj + j));
-            return k < acc ? k : acc;
-        },
-        [&](int v, unsigned long long acc) {
-            if (acc != ~0ull) atomicMin(nkey + v, acc);
-        });
+    d_match_min(GridTeam(), N, P, noff, nadj, hkey, nkey);
 }
 
-// match[v] from the winning key; sizes and weights of the matched sets S(e) (integer atomics).
 __global__ void __launch_bounds__(kBlock)
 k_match_set(int N, const unsigned long long *__restrict__ nkey, const int *__restrict__ nw,
             int *__restrict__ match, int *__restrict__ ssize, int *__restrict__ sweight) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
-        unsigned long long k = nkey[v];
-        int m = k == ~0ull ? -1 : (int)unmix32((uint32_t)k);
-        match[v] = m;
-        if (m >= 0) {
-            atomicAdd(&ssize[m], 1);
-            atomicAdd(&sweight[m], nw[v]);
-        }
-    }
+    d_match_set(GridTeam(), N, nkey, nw, match, ssize, sweight);
 }
 
-// Algorithm 2, second loop, for every singleton set S(e) = {u}: the lightest step-1 merged node
-// among e's pins, as the key (merged weight << 32 | group id), minimum over e's pins.
-// Load-balanced over all pins; hyperedges that are not singleton sets are skipped.
 __global__ void __launch_bounds__(kLbBlock)
 k_single_best(int E, int P, const int *__restrict__ hoff, const int *__restrict__ pins,
               const int *__restrict__ match, const int *__restrict__ ssize,
               const int *__restrict__ sweight, unsigned long long *__restrict__ best) {
-    lb_for_each<unsigned long long>(
-        hoff, E, P, ~0ull,
-        [&](int e, int i, unsigned long long acc) {
-            if (__ldg(ssize + e) != 1) return acc;
-            int mv = __ldg(match + __ldg(pins + i));
-            if (mv >= 0 && __ldg(ssize + mv) >= 2) {
-                unsigned long long k = ((unsigned long long)(unsigned)__ldg(sweight + mv) << 32) | (unsigned)mv;
-                acc = k < acc ? k : acc;
-            }
-            return acc;
-        },
-        [&](int e, unsigned long long acc) {
-            if (acc != ~0ull) atomicMin(best + e, acc);
-        });
+    d_single_best(GridTeam(), E, P, hoff, pins, match, ssize, sweight, best);
 }
 
-// grp[v] = matched hyperedge of v's final group, or -1 when v stays alone; rep[g] receives the
-// smallest member of group g.
 __global__ void __launch_bounds__(kBlock)
 k_group(int N, const int *__restrict__ match, const int *__restrict__ ssize,
         const unsigned long long *__restrict__ best, int *__restrict__ grp,
         unsigned *__restrict__ rep) {
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < N; u += gridDim.x * blockDim.x) {
-        int m = match[u];
-        int g = -1;
-        if (m >= 0) {
-            if (ssize[m] >= 2) g = m;
-            else if (best[m] != ~0ull) g = (int)(best[m] & 0xffffffffu);
-        }
-        grp[u] = g;
-        if (g >= 0) atomicMin(&rep[g], (unsigned)u);
-    }
+    d_group(GridTeam(), N, match, ssize, best, grp, rep);
 }
-
-struct RenumIn {
-    const int *grp;
-    const unsigned *rep;
-    __device__ uint64_t operator()(int64_t v) const {
-        int g = grp[v];
-        return (g < 0 || rep[g] == (unsigned)v) ? 1ull : 0ull;
-    }
-};
-struct RenumOut {
-    int64_t n;
-    const int *grp;
-    int *cmap, *gcid, *nc_out;  // *nc_out = N'
-    __device__ void operator()(int64_t v, uint64_t pre, uint64_t val) const {
-        if (val) {
-            cmap[v] = (int)pre;
-            int g = grp[v];
-            if (g >= 0) gcid[g] = (int)pre;
-        }
-        if (v == n - 1) *nc_out = (int)(pre + val);
-    }
-};
 
 __global__ void k_cmap(int N, const int *__restrict__ grp, const int *__restrict__ gcid,
                        const int *__restrict__ nw, int *__restrict__ cmap, int *__restrict__ cw) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
-        int g = grp[v];
-        int c = g >= 0 ? gcid[g] : cmap[v];
-        cmap[v] = c;
-        atomicAdd(&cw[c], nw[v]);
-    }
+    d_cmap(GridTeam(), N, grp, gcid, nw, cmap, cw);
 }
 
 // ------------------------------------------------------------------ host side

@@ -175,4 +175,30 @@ __device__ __forceinline__ void record_error(uint32_t *status, uint32_t code) {
 
 inline int ceil_div_i(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Teams: the threads that share one phase of the algorithm.  GridTeam = every thread of a kernel
+// launch (phases are separate launches); CtaTeam = one thread block that runs a whole instance
+// (phases separated by __syncthreads).  ld() is the load used for data written by an earlier
+// phase: the read-only path within a kernel launch, a coherent load inside a persistent block.
+struct GridTeam {
+    __device__ __forceinline__ int rank() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+    __device__ __forceinline__ int size() const { return gridDim.x * blockDim.x; }
+    __device__ __forceinline__ int block() const { return blockIdx.x; }
+    __device__ __forceinline__ int blocks() const { return gridDim.x; }
+    __device__ __forceinline__ int warp() const { return rank() >> 5; }
+    __device__ __forceinline__ int warps() const { return size() >> 5; }
+    template <class T>
+    __device__ __forceinline__ static T ld(const T *p) { return __ldg(p); }
+};
+
+struct CtaTeam {
+    __device__ __forceinline__ int rank() const { return threadIdx.x; }
+    __device__ __forceinline__ int size() const { return blockDim.x; }
+    __device__ __forceinline__ int block() const { return 0; }
+    __device__ __forceinline__ int blocks() const { return 1; }
+    __device__ __forceinline__ int warp() const { return threadIdx.x >> 5; }
+    __device__ __forceinline__ int warps() const { return blockDim.x >> 5; }
+    template <class T>
+    __device__ __forceinline__ static T ld(const T *p) { return *p; }
+};
+
 }  // namespace bp

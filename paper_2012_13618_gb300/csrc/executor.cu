@@ -30,6 +30,7 @@
 #include "internal.h"
 
 namespace bp {
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -214,6 +215,9 @@ struct bipart_server_s {
 
 using namespace bp;
 
+// Batch: k = 2 instances of up to 2^18 nodes run in the persistent block kernel on this thread;
+// the others (and any instance the block path defers) go to the worker pool, which runs
+// concurrently.
 extern "C" int bipart_partition_batch(int32_t n, const bipart_instance *instances,
                                       const bipart_params *params, int32_t *const *out_parts,
                                       int32_t *statuses, int32_t workers) {
@@ -224,24 +228,95 @@ extern "C" int bipart_partition_batch(int32_t n, const bipart_instance *instance
     if (n == 0) return BIPART_OK;
     try {
         if (workers <= 0) workers = std::min<int32_t>(16, std::max<int32_t>(n, 1));
-        Pool pool(workers, 0);
-        std::vector<int64_t> tickets(n);
-        // largest first: queue order by estimated size
-        std::vector<int32_t> order(n);
-        for (int32_t i = 0; i < n; ++i) order[i] = i;
-        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-            return estimate_bytes(instances[a]) > estimate_bytes(instances[b]);
-        });
-        for (int32_t i : order) tickets[i] = pool.submit(instances[i], params[i], out_parts[i], false);
-        int rc = BIPART_OK;
+        std::vector<int32_t> st(n, BIPART_OK);
+        std::vector<std::string> err(n);
+        std::vector<int32_t> blk, rest;
         for (int32_t i = 0; i < n; ++i) {
+            const bipart_instance &in = instances[i];
+            const bipart_params &p = params[i];
+            try {
+                validate_params(p.k, p.epsilon, p.policy, p.levels, p.refine_iters);
+                validate_host_csr(in.num_nodes, in.num_hedges, in.hedge_offsets, in.hedge_pins,
+                                  in.node_weights, in.hedge_weights);
+            } catch (const Fail &e) {
+                st[i] = e.code;
+                err[i] = e.msg;
+                continue;
+            }
+            const int64_t P = in.num_hedges > 0 ? in.hedge_offsets[in.num_hedges] : 0;
+            if (block_eligible(in.num_nodes, in.num_hedges, P, p.k) && in.num_nodes > 0) blk.push_back(i);
+            else rest.push_back(i);
+        }
+        auto by_size = [&](std::vector<int32_t> &v) {
+            std::stable_sort(v.begin(), v.end(), [&](int32_t a, int32_t b) {
+                return estimate_bytes(instances[a]) > estimate_bytes(instances[b]);
+            });
+        };
+        by_size(blk);
+        by_size(rest);
+        Pool pool(workers, 0);
+        std::vector<int64_t> tickets(n, 0);
+        for (int32_t i : rest)
+            if (st[i] == BIPART_OK) tickets[i] = pool.submit(instances[i], params[i], out_parts[i], false);
+        if (!blk.empty()) {
+            std::vector<BInst> bi(blk.size());
+            std::vector<const int32_t *> ho(blk.size()), pi(blk.size()), nw(blk.size()), hw(blk.size());
+            for (size_t j = 0; j < blk.size(); ++j) {
+                const bipart_instance &in = instances[blk[j]];
+                const bipart_params &p = params[blk[j]];
+                BInst &b = bi[j];
+                b.N = in.num_nodes;
+                b.E = in.num_hedges;
+                b.P = in.num_hedges > 0 ? in.hedge_offsets[in.num_hedges] : 0;
+                b.policy = p.policy;
+                b.levels = p.levels;
+                b.iters = p.refine_iters;
+                int64_t W = 0;
+                for (int32_t v = 0; v < in.num_nodes; ++v) W += in.node_weights ? in.node_weights[v] : 1;
+                b.limit = balance_limit(W, p.epsilon);
+                b.status = 0;
+                ho[j] = in.num_hedges > 0 ? in.hedge_offsets : nullptr;
+                pi[j] = in.hedge_pins;
+                nw[j] = in.node_weights;
+                hw[j] = in.hedge_weights;
+            }
+            // instances without hyperedges still need an offsets array of one zero
+            static const int32_t zero = 0;
+            for (size_t j = 0; j < blk.size(); ++j)
+                if (!ho[j]) ho[j] = &zero;
+            cudaStream_t s = nullptr;
+            BP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            std::vector<std::vector<uint8_t>> sides;
+            try {
+                run_block_batch(bi, ho, pi, nw, hw, sides, s);
+            } catch (...) {
+                cudaStreamDestroy(s);
+                throw;
+            }
+            cudaStreamDestroy(s);
+            for (size_t j = 0; j < blk.size(); ++j) {
+                const int32_t i = blk[j];
+                if (bi[j].status == 2) {  // did not fit the block arena: single-instance path
+                    tickets[i] = pool.submit(instances[i], params[i], out_parts[i], false);
+                    continue;
+                }
+                st[i] = bi[j].status ? BIPART_WARN_IMBALANCED : BIPART_OK;
+                for (int32_t v = 0; v < instances[i].num_nodes; ++v) out_parts[i][v] = sides[j][v];
+            }
+        }
+        for (int32_t i = 0; i < n; ++i) {
+            if (!tickets[i]) continue;
             std::shared_ptr<Job> j;
             pool.wait(tickets[i], -1, &j);
-            int st = j ? j->status : BIPART_ERR_CUDA;
-            if (statuses) statuses[i] = st;
-            if (st < 0 && rc == BIPART_OK) {
-                rc = st;
-                set_error("instance " + std::to_string(i) + ": " + (j ? j->error : std::string("lost")));
+            st[i] = j ? j->status : BIPART_ERR_CUDA;
+            if (j && st[i] < 0) err[i] = j->error;
+        }
+        int rc = BIPART_OK;
+        for (int32_t i = 0; i < n; ++i) {
+            if (statuses) statuses[i] = st[i];
+            if (st[i] < 0 && rc == BIPART_OK) {
+                rc = st[i];
+                set_error("instance " + std::to_string(i) + ": " + err[i]);
             }
         }
         return rc;

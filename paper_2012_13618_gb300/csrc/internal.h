@@ -208,6 +208,26 @@ struct ProfScope {
     ~ProfScope();
 };
 
+// ------------------------------------------------------------------------- block path (block.cu)
+// One instance of a batch run by the persistent block kernel (device-side descriptor).
+struct BInst {
+    int N, E, P;
+    int policy, levels, iters;
+    long long limit;
+    long long hoff, pins, nw, hw, out;  // offsets into the concatenated arrays (hw < 0: unit)
+    int status;                          // 0 ok, 1 imbalanced, 2 deferred (did not fit)
+};
+bool block_eligible(int64_t N, int64_t E, int64_t P, int k);
+void run_block_batch(std::vector<BInst> &inst, const std::vector<const int32_t *> &hoff,
+                     const std::vector<const int32_t *> &pins, const std::vector<const int32_t *> &nw,
+                     const std::vector<const int32_t *> &hw, std::vector<std::vector<uint8_t>> &sides,
+                     cudaStream_t s);
+
+// ------------------------------------------------------------------------- validation (api.cu)
+void validate_params(int32_t k, double eps, int32_t policy, int32_t levels, int32_t iters);
+void validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t *pins,
+                       const int32_t *nw, const int32_t *hw);
+
 // ------------------------------------------------------------------------- executor (api.cu)
 bipart_graph *graph_new(cudaStream_t s);
 void graph_load_host(bipart_graph *g, int32_t N, int32_t E, const int32_t *hoff,

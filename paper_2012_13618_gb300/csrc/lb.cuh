@@ -16,10 +16,11 @@ constexpr int kLbItems = 8;
 constexpr int kLbTile = kLbBlock * kLbItems;
 
 // Largest s in [lo, hi] with off[s] <= j (the non-empty segment holding item j).
-__device__ __forceinline__ int lb_seg(const int *__restrict__ off, int j, int lo, int hi) {
+template <class Team = GridTeam>
+__device__ __forceinline__ int lb_seg(const int *off, int j, int lo, int hi) {
     while (lo < hi) {
         int m = (lo + hi + 1) >> 1;
-        if (__ldg(off + m) <= j) lo = m;
+        if (Team::ld(off + m) <= j) lo = m;
         else hi = m - 1;
     }
     return lo;
@@ -27,30 +28,32 @@ __device__ __forceinline__ int lb_seg(const int *__restrict__ off, int j, int lo
 
 // Visits the items of this thread in order as (segment, item index) and calls
 // flush(segment, acc) whenever the segment changes and at the end.  `init` is the identity of
-// the combine operation; visit(seg, item, acc) folds one item into acc.
-template <class Acc, class Visit, class Flush>
-__device__ __forceinline__ void lb_for_each(const int *__restrict__ off, int nseg, int total,
-                                            Acc init, Visit visit, Flush flush) {
+// the combine operation; visit(seg, item, acc) folds one item into acc.  A tile is
+// blockDim.x * kLbItems items; the team's blocks take tiles in turn.
+template <class Acc, class Visit, class Flush, class Team = GridTeam>
+__device__ __forceinline__ void lb_for_each(const int *off, int nseg, int total, Acc init,
+                                            Visit visit, Flush flush, Team t = Team()) {
     __shared__ int s_rng[2];
-    for (int64_t t0 = (int64_t)blockIdx.x * kLbTile; t0 < total; t0 += (int64_t)gridDim.x * kLbTile) {
+    const int tile = blockDim.x * kLbItems;
+    for (int64_t t0 = (int64_t)t.block() * tile; t0 < total; t0 += (int64_t)t.blocks() * tile) {
         const int j0 = (int)t0;
-        const int j1 = (int)(t0 + kLbTile < total ? t0 + kLbTile : total);
+        const int j1 = (int)(t0 + tile < total ? t0 + tile : total);
         __syncthreads();
-        if (threadIdx.x == 0) s_rng[0] = lb_seg(off, j0, 0, nseg - 1);
-        if (threadIdx.x == 32) s_rng[1] = lb_seg(off, j1 - 1, 0, nseg - 1);
+        if (threadIdx.x == 0) s_rng[0] = lb_seg<Team>(off, j0, 0, nseg - 1);
+        if (threadIdx.x == 32) s_rng[1] = lb_seg<Team>(off, j1 - 1, 0, nseg - 1);
         __syncthreads();
         int j = j0 + threadIdx.x * kLbItems;
         if (j >= j1) continue;
         const int je = j + kLbItems < j1 ? j + kLbItems : j1;
-        int s = lb_seg(off, j, s_rng[0], s_rng[1]);
-        int send = __ldg(off + s + 1);
+        int s = lb_seg<Team>(off, j, s_rng[0], s_rng[1]);
+        int send = Team::ld(off + s + 1);
         Acc acc = init;
         for (; j < je; ++j) {
             while (j >= send) {  // next non-empty segment
                 flush(s, acc);
                 acc = init;
                 ++s;
-                send = __ldg(off + s + 1);
+                send = Team::ld(off + s + 1);
             }
             acc = visit(s, j, acc);
         }
@@ -60,22 +63,23 @@ __device__ __forceinline__ void lb_for_each(const int *__restrict__ off, int nse
 
 // Calls fn(s, a, b) for every maximal run [a, b) of this thread's items that lies in segment s,
 // in item order (per-segment values can then be loaded once per run).
-template <class Fn>
-__device__ __forceinline__ void lb_runs(const int *__restrict__ off, int nseg, int total, Fn fn) {
+template <class Fn, class Team = GridTeam>
+__device__ __forceinline__ void lb_runs(const int *off, int nseg, int total, Fn fn, Team t = Team()) {
     __shared__ int s_rng[2];
-    for (int64_t t0 = (int64_t)blockIdx.x * kLbTile; t0 < total; t0 += (int64_t)gridDim.x * kLbTile) {
+    const int tile = blockDim.x * kLbItems;
+    for (int64_t t0 = (int64_t)t.block() * tile; t0 < total; t0 += (int64_t)t.blocks() * tile) {
         const int j0 = (int)t0;
-        const int j1 = (int)(t0 + kLbTile < total ? t0 + kLbTile : total);
+        const int j1 = (int)(t0 + tile < total ? t0 + tile : total);
         __syncthreads();
-        if (threadIdx.x == 0) s_rng[0] = lb_seg(off, j0, 0, nseg - 1);
-        if (threadIdx.x == 32) s_rng[1] = lb_seg(off, j1 - 1, 0, nseg - 1);
+        if (threadIdx.x == 0) s_rng[0] = lb_seg<Team>(off, j0, 0, nseg - 1);
+        if (threadIdx.x == 32) s_rng[1] = lb_seg<Team>(off, j1 - 1, 0, nseg - 1);
         __syncthreads();
         int j = j0 + threadIdx.x * kLbItems;
         if (j >= j1) continue;
         const int je = j + kLbItems < j1 ? j + kLbItems : j1;
-        int s = lb_seg(off, j, s_rng[0], s_rng[1]);
+        int s = lb_seg<Team>(off, j, s_rng[0], s_rng[1]);
         while (j < je) {
-            const int send = __ldg(off + s + 1);
+            const int send = Team::ld(off + s + 1);
             const int b = send < je ? send : je;
             if (b > j) fn(s, j, b);
             j = b > j ? b : j;

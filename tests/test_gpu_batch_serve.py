@@ -88,3 +88,57 @@ def test_server_rejects_request_above_budget():
         t = srv.submit(g, k=2, eps=0.05)
         parts, st, _, _ = srv.wait(t)
         assert st == bp.ERR_OOM
+
+
+def _block_cases():
+    rng = np.random.default_rng(9)
+    out = []
+    for i in range(40):
+        kind = i % 5
+        if kind == 0:
+            out.append(synth.uniform(int(rng.integers(50, 3000)), int(rng.integers(50, 3000)), 2, 7, seed=100 + i))
+        elif kind == 1:
+            out.append(synth.c3_instance(500 + i, N=int(rng.integers(1000, 30000))))
+        elif kind == 2:
+            r = int(rng.integers(500, 8000))
+            out.append(synth.rownet(r, r, seed=200 + i))
+        elif kind == 3:  # weighted hyperedges, duplicate and single pins
+            N, E = int(rng.integers(100, 2000)), int(rng.integers(100, 3000))
+            deg = rng.integers(0, 9, size=E)
+            hoff = np.zeros(E + 1, np.int32)
+            hoff[1:] = np.cumsum(deg)
+            out.append(dict(N=N, E=E, hoff=hoff, pins=rng.integers(0, N, size=int(hoff[-1])).astype(np.int32),
+                            nw=rng.integers(1, 6, size=N).astype(np.int32),
+                            hw=rng.integers(1, 2000, size=E).astype(np.int32)))
+        else:  # degenerate: no hyperedges, or a handful of nodes
+            N = int(rng.integers(1, 40))
+            out.append(dict(N=N, E=0, hoff=np.zeros(1, np.int32), pins=np.zeros(0, np.int32), nw=None, hw=None))
+    return out
+
+
+def test_block_path_many_instances_match_oracle():
+    import paper_2012_13618_gb300 as bp
+    graphs = _block_cases()
+    pols = ["LDH", "HDH", "LWD", "HWD", "RAND"]
+    params = [dict(k=2, eps=[0.0, 0.05, 0.1, 0.3][i % 4], policy=pols[i % 5], levels=[25, 3, 0, 25][i % 4],
+                   iters=[2, 1, 2, 0][i % 4]) for i in range(len(graphs))]
+    parts, st = bp.partition_batch(graphs, params, workers=4)
+    for i, g in enumerate(graphs):
+        p = params[i]
+        r = oracle.bisect(oracle.Hypergraph.from_dict(g), p["eps"], p["policy"], p["levels"], p["iters"],
+                          keep_levels=False)
+        assert np.array_equal(parts[i], r["side"].astype(np.int32)), i
+        assert st[i] == r["status"], i
+
+
+def test_block_path_deferral_falls_back(monkeypatch):
+    # an arena too small for the larger instances defers them to the single-instance path
+    import paper_2012_13618_gb300 as bp
+    graphs = [synth.c3_instance(700 + i, N=n) for i, n in enumerate([2000, 40000, 3000, 60000])]
+    p = dict(k=2, eps=0.05, policy="LDH", levels=25, iters=2)
+    want = [oracle.bisect(oracle.Hypergraph.from_dict(g), 0.05, "LDH", 25, 2, keep_levels=False)["side"]
+            for g in graphs]
+    monkeypatch.setenv("BIPART_BLOCK_ARENA_MB", "8")
+    parts, st = bp.partition_batch(graphs, p, workers=2)
+    for a, b in zip(parts, want):
+        assert np.array_equal(a, b.astype(np.int32))
