@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
 #include <cmath>
 #include <cstdlib>
 #include <vector>
@@ -409,6 +411,8 @@ void run_block_batch(std::vector<BInst> &inst, const std::vector<const int32_t *
                      cudaStream_t s) {
     const int n = (int)inst.size();
     if (n == 0) return;
+    const bool timing = std::getenv("BIPART_TIMING") != nullptr;
+    auto t_host0 = std::chrono::steady_clock::now();
     int dev = 0, sms = 0;
     BP_CUDA(cudaGetDevice(&dev));
     BP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -471,14 +475,30 @@ void run_block_batch(std::vector<BInst> &inst, const std::vector<const int32_t *
     BP_CUDA(cudaMemsetAsync(d_misc, 0, 64, s));
     BArgs a{d_inst, n, d_misc, d_hoff, d_pins, d_nw, d_hw, d_side, d_arena, arena,
             reinterpret_cast<uint32_t *>(d_misc + 8)};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (timing) {
+        cudaEventCreate(&ev0);
+        cudaEventCreate(&ev1);
+        cudaEventRecord(ev0, s);
+    }
     k_batch_bisect<<<blocks, kBT, kSmemBytes, s>>>(a);
     BP_LAUNCH();
+    if (timing) cudaEventRecord(ev1, s);
     std::vector<uint8_t> h_side((size_t)std::max<int64_t>(sn, 1));
     BP_CUDA(cudaMemcpyAsync(inst.data(), d_inst, sizeof(BInst) * (size_t)n, cudaMemcpyDeviceToHost, s));
     BP_CUDA(cudaMemcpyAsync(h_side.data(), d_side, (size_t)std::max<int64_t>(sn, 1), cudaMemcpyDeviceToHost, s));
     uint32_t dst = 0;
     BP_CUDA(cudaMemcpyAsync(&dst, d_misc + 8, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     BP_CUDA(cudaStreamSynchronize(s));
+    if (timing) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        const double host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count();
+        std::fprintf(stderr, "[bipart] block batch: %d instances, %d blocks x %d threads, arena %.1f MiB/block, kernel %.2f ms, total %.2f ms\n",
+                     n, blocks, kBT, arena / 1048576.0, ms, host_ms);
+    }
     if (dst & DEV_TIMEOUT) throw Fail{BIPART_ERR_TIMEOUT, "a bounded device loop expired in the batch kernel"};
     sides.resize(n);
     for (int i = 0; i < n; ++i)

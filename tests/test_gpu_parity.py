@@ -218,3 +218,34 @@ def test_large_weighted_gains_take_exact_select():
         for _ in range(3):
             parts, _ = h.partition(2, 0.05, "LWD", 25, 2)
             assert np.array_equal(parts, ref["side"].astype(np.int32))
+
+
+def test_c2_rownet_5m_full_k2():
+    # Full-size power-law row-net (5M x 5M, ~57M pins).  The oracle's full bisection takes minutes
+    # (its rebalance rounds move at most ceil(sqrt n) nodes each), so at this size the coarse
+    # hierarchy is compared level by level with the oracle's Algorithm 2 chain, and the final
+    # partition by properties that hold at any size: balance against the limit, the cut two ways,
+    # and identical results on a second run.
+    bp = _bp()
+    g = synth.c2_rownet()
+    with bp.create_from(g) as h:
+        parts, st = h.partition(2, 0.05, "LDH", 25, 2)
+        nlev = h.num_levels()
+        cur = oracle.Hypergraph.from_dict(g)
+        for l in range(nlev):
+            a, b = h.get_level(l), cur.arrays()
+            for key in ("hoff", "pins", "nw"):
+                assert np.array_equal(a[key], b[key]), (l, key)
+            if l < nlev - 1:
+                nxt, cmap, m = oracle.coarsen(cur, "LDH")
+                assert np.array_equal(a["cmap"], cmap) and np.array_equal(a["match"], m), l
+                cur = nxt
+        assert cur.E == 0 or nlev == 26
+        W = g["N"]
+        lim = oracle.limit(W, 0.05)
+        w1 = int(parts.sum())
+        assert st == 1 or max(w1, W - w1) <= lim
+        hr = oracle.Hypergraph.from_dict(g)
+        assert h.cut(parts) == oracle.cut_bisection(hr, parts.astype(np.uint8))
+        again, st2 = h.partition(2, 0.05, "LDH", 25, 2)
+        assert np.array_equal(parts, again) and st2 == st
