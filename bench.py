@@ -368,13 +368,31 @@ def run_batch(args):
     import torch
     import oracle
     import paper_2012_13618_gb300 as bp
-    torch.cuda.set_device(0)
+    from paper_2012_13618_gb300 import shard
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     graphs, params = c3_graphs(args.batch_n, args.big_nodes)
+    total_instances = len(graphs)
+    total_pins = sum(int(g["hoff"][-1]) for g in graphs)
+    if ws > 1:
+        # independent instances: every rank takes its own longest-processing-time share
+        mine = shard.my_share([int(g["hoff"][-1]) for g in graphs], rank, ws)
+        graphs = [graphs[i] for i in mine]
+        params = [params[i] for i in mine]
     pins = sum(int(g["hoff"][-1]) for g in graphs)
     bp.partition_batch(graphs[:8], params[:8], workers=args.workers)  # warm-up
+    if ws > 1:
+        dist.barrier()
     t0 = time.perf_counter()
     bparts, bst = bp.partition_batch(graphs, params, workers=args.workers)
-    t_batch = time.perf_counter() - t0
+    t_batch = shard.max_over_ranks(time.perf_counter() - t0)
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
     plain_n = min(len(graphs), args.plain_n)
     pparts, t_plain = run_plain(bp, graphs[:plain_n], params[:plain_n])
     same = all(np.array_equal(a, b) for a, b in zip(bparts[:plain_n], pparts))
@@ -384,20 +402,25 @@ def run_batch(args):
     oracle_ok = all(np.array_equal(bparts[i], oracle.partition(oracle.Hypergraph.from_dict(graphs[i]),
                                                                params[i]["k"], 0.05, "LDH", 25, 2)[0])
                     for i in sample)
-    line = {"metric": "batched solves/s", "value": len(graphs) / t_batch, "unit": "solves/s",
-            "n_gpus": 1, "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+    line = {"metric": "batched solves/s", "value": total_instances / t_batch, "unit": "solves/s",
+            "n_gpus": ws, "scaling": "strong", "higher_is_better": True, "dtype": "int32",
+            "data": "synthetic",
             "config": {"workload": f"{args.batch_n} netlist-like instances, N log-uniform 1k-200k, "
                                    f"k=2, eps=0.05" + (f", plus one {args.big_nodes}-node instance at k=64"
                                                        if args.big_nodes else ""),
-                       "instances": len(graphs), "pins": pins, "workers": args.workers},
-            "batch_seconds": t_batch, "pins_per_s": pins / t_batch,
+                       "instances": total_instances, "pins": total_pins, "workers": args.workers,
+                       "parallelism": f"{ws} rank(s), instances sharded longest-first"},
+            "batch_seconds": t_batch, "pins_per_s": total_pins / t_batch,
             "plain": {"solves_per_s": plain_n / t_plain, "instances": plain_n,
                       "seconds": t_plain},
-            "speedup_vs_plain": (len(graphs) / t_batch) / (plain_n / t_plain),
+            "speedup_vs_plain": (total_instances / t_batch) / (plain_n / t_plain),
             "bit_exact_vs_plain": bool(same), "oracle_checked": len(sample),
             "bit_exact_vs_oracle": bool(oracle_ok),
             "warn_imbalanced": int((bst == 1).sum())}
     print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 # --------------------------------------------------------------------------- served form (C4)
@@ -423,6 +446,9 @@ def run_serve(args):
     import torch
     import synth
     import paper_2012_13618_gb300 as bp
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return  # the serving sweep runs on one GPU (rank 0)
     torch.cuda.set_device(0)
     reqs, _ = c4_requests(args.serve_n)
     # plain path rate: one request at a time

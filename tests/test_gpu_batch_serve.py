@@ -142,3 +142,23 @@ def test_block_path_deferral_falls_back(monkeypatch):
     parts, st = bp.partition_batch(graphs, p, workers=2)
     for a, b in zip(parts, want):
         assert np.array_equal(a, b.astype(np.int32))
+
+
+def test_design_space_sweep_matches_oracle_and_frontier():
+    from paper_2012_13618_gb300 import sweep
+    g = synth.uniform(2500, 2600, 2, 6, seed=31)
+    res, front = sweep.sweep(g, levels=(3, 25), iters=(0, 2), policies=("LDH", "RAND"), eps=0.1,
+                             repeats=1)
+    hr = oracle.Hypergraph.from_dict(g)
+    for r in res:
+        ref = oracle.bisect(hr, 0.1, r["policy"], r["levels"], r["iters"], keep_levels=False)
+        assert np.array_equal(r["parts"], ref["side"].astype(np.int32))
+        assert r["cut"] == oracle.cut_bisection(hr, ref["side"])
+    pts = [(r["ms"], r["cut"]) for r in res]
+    assert front and all(not any(pts[j][0] <= pts[i][0] and pts[j][1] <= pts[i][1] and pts[j] != pts[i]
+                                 for j in range(len(pts))) for i in front)
+
+
+def test_pareto_helper():
+    from paper_2012_13618_gb300.sweep import pareto
+    assert pareto([(1, 5), (2, 3), (3, 4), (2, 3), (0.5, 9)]) == [0, 1, 3, 4]
