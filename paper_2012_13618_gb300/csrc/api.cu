@@ -64,6 +64,8 @@ void dev_free(void *p, size_t bytes, cudaStream_t s) {
     else cudaFreeAsync(p, s);
 }
 
+void zero_fill(void *p, size_t bytes, cudaStream_t s) { BP_CUDA(cudaMemsetAsync(p, 0, bytes, s)); }
+
 uint32_t *dev_status(bipart_graph *g) { return g->w.status.as<uint32_t>(); }
 
 void sync(bipart_graph *g) {
@@ -382,7 +384,7 @@ void extract_subgraph(bipart_graph *g, const int *d_part, int j) {
     int *small = w.small.as<int>();
     BP_CUDA(cudaMemsetAsync(small, 0, 8 * sizeof(int), s));
     scan(L.N, SubNodeIn{d_part, j}, SubNodeOut{L.N, L.nw(), loc, l2g, S.nw(), small + 4},
-         w.scan.ensure(scan_state_bytes(L.N), s), dev_status(g), s);
+         w.scan.ensure_zero(scan_state_bytes(L.N), s), dev_status(g), s);
     int *cnt = (int *)w.e_a.ensure(sizeof(int) * (size_t)std::max(L.E, 1), s);
     int *emap = (int *)w.e_b.ensure(sizeof(int) * (size_t)std::max(L.E, 1), s);
     S.unit_hw = L.unit_hw;
@@ -395,7 +397,7 @@ void extract_subgraph(bipart_graph *g, const int *d_part, int j) {
         k_sub_count<<<gw, kBlock, 0, s>>>(L.E, L.hoff(), L.pins(), loc, cnt);
         BP_LAUNCH();
         scan(L.E, SubEdgeIn{cnt}, SubEdgeOut{L.E, L.hw(), S.hoff(), S.unit_hw ? nullptr : S.b_hw.as<int>(), emap, small + 2},
-             w.scan.ensure(scan_state_bytes(L.E), s), dev_status(g), s);
+             w.scan.ensure_zero(scan_state_bytes(L.E), s), dev_status(g), s);
         k_sub_copy<<<gw, kBlock, 0, s>>>(L.E, L.hoff(), L.pins(), loc, emap, S.hoff(), S.pins(), deg);
         BP_LAUNCH();
     } else {
@@ -656,6 +658,7 @@ bipart_graph *new_graph(cudaStream_t s) {
     BP_CUDA(cudaMemsetAsync(g->w.status.p, 0, 64, s));
     BP_CUDA(cudaMallocHost(&g->w.host_small, 4096));
     refine_init();
+    coarsen_init();
     return g.release();
 }
 

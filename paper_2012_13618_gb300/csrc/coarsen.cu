@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -69,6 +70,71 @@ k_seg_copy(int E, int P, const int *__restrict__ hoff, const int *__restrict__ s
            const int *__restrict__ cnt, const int *__restrict__ emap,
            const int *__restrict__ hoff_out, int *__restrict__ pins_out, int *__restrict__ deg) {
     d_seg_copy(GridTeam(), E, P, hoff, scratch, cnt, emap, hoff_out, pins_out, deg);
+}
+
+// Coarse levels with at most kPrivNodes nodes count degrees and claim incidence positions in
+// block-private shared-memory counters: few nodes means many pins per node, and one global
+// atomic per pin would serialise on the heaviest nodes.  Each block merges its counts with one
+// global atomic per node it touched.
+constexpr int kPrivNodes = 24576;
+
+__global__ void __launch_bounds__(kLbBlock)
+k_seg_copy_priv(int E, int P, int N, const int *__restrict__ hoff, const int *__restrict__ scratch,
+                const int *__restrict__ cnt, const int *__restrict__ emap,
+                const int *__restrict__ hoff_out, int *__restrict__ pins_out, int *__restrict__ deg) {
+    extern __shared__ int s_cnt[];
+    for (int v = threadIdx.x; v < N; v += blockDim.x) s_cnt[v] = 0;
+    __syncthreads();
+    lb_runs(
+        hoff, E, P,
+        [&](int e, int a, int b) {
+            const int ee = emap[e];
+            if (ee < 0) return;
+            const int base = hoff[e], c = cnt[e], o = hoff_out[ee];
+            const int stop = base + c < b ? base + c : b;
+            for (int i = a; i < stop; ++i) {
+                const int v = scratch[i];
+                pins_out[o + (i - base)] = v;
+                atomicAdd(s_cnt + v, 1);
+            }
+        },
+        GridTeam());
+    __syncthreads();
+    for (int v = threadIdx.x; v < N; v += blockDim.x) {
+        const int c = s_cnt[v];
+        if (c) atomicAdd(deg + v, c);
+    }
+}
+
+// Pass 1 counts this block's pins per node, one global atomic per touched node reserves the
+// block's range, pass 2 hands out positions inside the range by shared-memory atomics.  Both
+// passes visit the same tiles.
+__global__ void __launch_bounds__(kLbBlock)
+k_fill_adj_priv(int E, int P, int N, const int *__restrict__ hoff, const int *__restrict__ pins,
+                int *__restrict__ cursor, int *__restrict__ nadj) {
+    extern __shared__ int s_cnt[];
+    for (int v = threadIdx.x; v < N; v += blockDim.x) s_cnt[v] = 0;
+    __syncthreads();
+    const int tile = blockDim.x * kLbItems;
+    for (int64_t t0 = (int64_t)blockIdx.x * tile; t0 < P; t0 += (int64_t)gridDim.x * tile) {
+        const int j1 = (int)(t0 + tile < P ? t0 + tile : P);
+        for (int j = (int)t0 + threadIdx.x; j < j1; j += blockDim.x) atomicAdd(s_cnt + pins[j], 1);
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < N; v += blockDim.x) {
+        const int c = s_cnt[v];
+        if (c) s_cnt[v] = atomicAdd(cursor + v, c);
+    }
+    __syncthreads();
+    d_fill_adj_with(GridTeam(), E, P, hoff, pins, nadj, [&](int v) { return atomicAdd(s_cnt + v, 1); });
+}
+
+// Blocks for the private-counter kernels: enough pins per block to amortise clearing and
+// merging N counters, at least one block per SM.
+inline int priv_grid(int P, int N) {
+    int64_t b = (int64_t)P / std::max(N, 1);
+    if (b < 152) b = 152;
+    return (int)std::min<int64_t>(b, lb_grid(P));
 }
 
 __global__ void k_fill(int n, int val, int *__restrict__ a) {
@@ -167,12 +233,16 @@ void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int 
         CompactOut out{E, hw, c.hoff(), unit ? nullptr : c.b_hw.as<int>(), emap, small + 2};
         {
             ProfScope ps("contract_offsets", 16.0 * E, s);
-            scan(E, CompactIn{cnt}, out, w.scan.ensure(scan_state_bytes(E), s), dev_status(g), s);
+            scan(E, CompactIn{cnt}, out, w.scan.ensure_zero(scan_state_bytes(E), s), dev_status(g), s);
         }
         {
             // scratch, coarse pins, degree atomics, per-hyperedge offsets
             ProfScope ps("contract_copy", 12.0 * P + 12.0 * E, s);
-            k_seg_copy<<<lb_grid(P), kLbBlock, 0, s>>>(E, P, hoff, scratch, cnt, emap, c.hoff(), c.pins(), deg);
+            if (c.N <= kPrivNodes)
+                k_seg_copy_priv<<<priv_grid(P, c.N), kLbBlock, sizeof(int) * (size_t)std::max(c.N, 1), s>>>(
+                    E, P, c.N, hoff, scratch, cnt, emap, c.hoff(), c.pins(), deg);
+            else
+                k_seg_copy<<<lb_grid(P), kLbBlock, 0, s>>>(E, P, hoff, scratch, cnt, emap, c.hoff(), c.pins(), deg);
             BP_LAUNCH();
         }
     } else {
@@ -204,12 +274,16 @@ void build_incidence(bipart_graph *g, Level &L) {
     int *cursor = (int *)w.n_b.ensure(sizeof(int) * (size_t)L.N, s);
     {
         ProfScope ps("incidence_offsets", 12.0 * L.N, s);
-        scan(L.N, DegIn{deg}, DegOut{L.N, L.noff(), cursor}, w.scan.ensure(scan_state_bytes(L.N), s),
+        scan(L.N, DegIn{deg}, DegOut{L.N, L.noff(), cursor}, w.scan.ensure_zero(scan_state_bytes(L.N), s),
              dev_status(g), s);
     }
     if (L.P > 0) {
         ProfScope ps("incidence_fill", 12.0 * L.P + 4.0 * L.E, s);
-        k_fill_adj<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.E, L.P, L.hoff(), L.pins(), cursor, L.nadj());
+        if (L.N <= kPrivNodes)
+            k_fill_adj_priv<<<priv_grid(L.P, L.N), kLbBlock, sizeof(int) * (size_t)L.N, s>>>(
+                L.E, L.P, L.N, L.hoff(), L.pins(), cursor, L.nadj());
+        else
+            k_fill_adj<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.E, L.P, L.hoff(), L.pins(), cursor, L.nadj());
         BP_LAUNCH();
     }
 }
@@ -294,7 +368,7 @@ void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy) {
         {
             ProfScope ps("renumber", 12.0 * N, s);
             scan(N, RenumIn{grp, rep}, RenumOut{N, grp, f.cmap(), gcid, small + 4},
-                 w.scan.ensure(scan_state_bytes(N), s), dev_status(g), s);
+                 w.scan.ensure_zero(scan_state_bytes(N), s), dev_status(g), s);
         }
     }
     const int Nc = N > 0 ? read_i32(g, small + 4) : 0;
@@ -310,6 +384,18 @@ void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy) {
     build_incidence(g, c);
     c.b_cmap.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);
     c.b_match.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);
+}
+
+void coarsen_init() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, []() {
+        const int bytes = (int)(sizeof(int) * kPrivNodes);
+        err = cudaFuncSetAttribute(k_seg_copy_priv, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(k_fill_adj_priv, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    });
+    BP_CUDA(err);
 }
 
 }  // namespace bp

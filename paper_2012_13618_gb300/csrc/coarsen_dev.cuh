@@ -287,13 +287,12 @@ struct DegOut {
 };
 
 // Fills the node -> hyperedge incidence: every pin slot takes the next free position of its node
-// (cursor starts at the node's offset).  Each thread owns kLbItems consecutive slots: it finds
-// their hyperedges with one search, then issues all its atomics before any store, so the
-// atomics' round trips overlap.  The order inside a node's list depends on the atomics' order;
-// every consumer is order-independent.
-template <class Team>
-__device__ void d_fill_adj(Team t, int E, int P, const int *hoff, const int *pins, int *cursor,
-                           int *nadj) {
+// from claim(v).  Each thread owns kLbItems consecutive slots: it finds their hyperedges with one
+// search, then issues all its claims before any store, so the atomics' round trips overlap.  The
+// order inside a node's list depends on the atomics' order; every consumer is order-independent.
+template <class Team, class Claim>
+__device__ void d_fill_adj_with(Team t, int E, int P, const int *hoff, const int *pins, int *nadj,
+                                Claim claim) {
     __shared__ int s_rng[2];
     const int tile = blockDim.x * kLbItems;
     for (int64_t t0 = (int64_t)t.block() * tile; t0 < P; t0 += (int64_t)t.blocks() * tile) {
@@ -319,11 +318,19 @@ __device__ void d_fill_adj(Team t, int E, int P, const int *hoff, const int *pin
         }
 #pragma unroll
         for (int k = 0; k < kLbItems; ++k)
-            if (k < n) pos[k] = atomicAdd(cursor + v[k], 1);
+            if (k < n) pos[k] = claim(v[k]);
 #pragma unroll
         for (int k = 0; k < kLbItems; ++k)
             if (k < n) nadj[pos[k]] = e[k];
     }
+}
+
+// Incidence fill claiming positions from the global per-node cursor (cursor starts at the node's
+// offset).
+template <class Team>
+__device__ void d_fill_adj(Team t, int E, int P, const int *hoff, const int *pins, int *cursor,
+                           int *nadj) {
+    d_fill_adj_with(t, E, P, hoff, pins, nadj, [&](int v) { return atomicAdd(cursor + v, 1); });
 }
 
 // ------------------------------------------------------------------ Algorithm 1

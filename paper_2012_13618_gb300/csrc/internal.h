@@ -17,6 +17,7 @@ namespace bp {
 // ---------------------------------------------------------------------------------- memory
 void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, size_t bytes, cudaStream_t s);
+void zero_fill(void *p, size_t bytes, cudaStream_t s);
 // Bumped whenever a buffer is (re)allocated: a captured graph is only valid while the buffers
 // it points to are the ones it was captured with.
 void note_realloc();
@@ -47,6 +48,13 @@ struct Buf {
             note_realloc();
         }
         return p;
+    }
+    // As ensure(), and a new allocation is zero-filled (for state that its users leave zero).
+    void *ensure_zero(size_t bytes, cudaStream_t stream) {
+        const void *old = p;
+        void *q = ensure(bytes, stream);
+        if (q != old) zero_fill(q, cap, stream);
+        return q;
     }
     template <class T>
     T *as() const { return reinterpret_cast<T *>(p); }
@@ -194,6 +202,7 @@ void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, int64_t limit, int
                uint8_t *d_side0);
 const unsigned *bisect_status_word(bipart_graph *g);
 void refine_init();  // once per process: kernel attributes (never during a capture)
+void coarsen_init();  // same, for the coarsening kernels
 int64_t balance_limit(int64_t W, double eps);
 
 // ------------------------------------------------------------------------- diagnostics

@@ -20,7 +20,10 @@ constexpr uint64_t kScanValMask = (1ull << 62) - 1;
 constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagPre = 2ull << 62;
 
-// `state` points at [tile counter (64-bit slot), tile status words ...], zeroed before launch.
+// `state` points at [tile counter, finished-block counter, tile status words ...], all zero at
+// launch.  Every block counts itself finished after its last read of a tile state; the block
+// that finishes last clears the state again, so consecutive scans on one stream need no memset
+// (a scan that gave up on a wait still finishes, so the state is cleared then too).
 template <class In, class Out>
 __global__ void __launch_bounds__(kScanBlock)
 k_scan(int64_t n, In in, Out out, unsigned long long *state, uint32_t *status) {
@@ -29,8 +32,10 @@ k_scan(int64_t n, In in, Out out, unsigned long long *state, uint32_t *status) {
     __shared__ uint64_t red[33];
     __shared__ uint32_t s_tile;
     __shared__ uint64_t s_prefix;
+    __shared__ int s_last;
     unsigned long long *counter = state;
-    unsigned long long *tiles = state + 1;
+    unsigned long long *finished = state + 1;
+    unsigned long long *tiles = state + 2;
 
     if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(counter, 1ull);
     __syncthreads();
@@ -80,8 +85,18 @@ k_scan(int64_t n, In in, Out out, unsigned long long *state, uint32_t *status) {
             atomicExch(&tiles[tile], (unsigned long long)(kFlagPre | ((prefix + total) & kScanValMask)));
         }
         s_prefix = prefix;
+        __threadfence();
+        s_last = atomicAdd(finished, 1ull) == (unsigned long long)gridDim.x - 1;
+        if (s_last) __threadfence();
     }
     __syncthreads();
+    if (s_last) {
+        for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) tiles[i] = 0ull;
+        if (threadIdx.x == 0) {
+            *counter = 0ull;
+            *finished = 0ull;
+        }
+    }
     uint64_t run = s_prefix + excl;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
@@ -100,12 +115,12 @@ inline size_t scan_state_bytes(int64_t n) {
     return sizeof(unsigned long long) * (size_t)(2 + (n + kScanTile - 1) / kScanTile);
 }
 
-// Launches the scan on `s`; `state` must hold scan_state_bytes(n).
+// Launches the scan on `s`; `state` must hold scan_state_bytes(n) zero bytes (as every scan
+// leaves it).
 template <class In, class Out>
 void scan(int64_t n, In in, Out out, void *state, uint32_t *status, cudaStream_t s) {
     if (n <= 0) return;
     int64_t tiles = (n + kScanTile - 1) / kScanTile;
-    BP_CUDA(cudaMemsetAsync(state, 0, scan_state_bytes(n), s));
     k_scan<In, Out><<<(unsigned)tiles, kScanBlock, 0, s>>>(n, in, out,
                                                              (unsigned long long *)state, status);
     BP_LAUNCH();
