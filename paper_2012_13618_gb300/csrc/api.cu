@@ -418,6 +418,10 @@ void extract_subgraph(bipart_graph *g, const int *d_part, int j) {
 // then initial partition + refinement back to level 0.  Coarse levels live in g->lev; the side
 // of level 0 goes to d_side and the status word (level-0 rebalance imbalanced) stays on device.
 void bisect_body(bipart_graph *g, Level &L0, const Params &p, int64_t W, uint8_t *d_side, int *nlev) {
+    // Counters, histograms and scan tile states are zero at rest (each phase clears what it
+    // used); they are cleared once here in case an earlier run stopped midway.
+    BP_CUDA(cudaMemsetAsync(g->w.small.p, 0, small_state_bytes(), g->stream));
+    if (g->w.scan.p) BP_CUDA(cudaMemsetAsync(g->w.scan.p, 0, g->w.scan.cap, g->stream));
     std::vector<Level *> levels{&L0};
     while ((int)levels.size() - 1 < p.levels) {
         Level &f = *levels.back();

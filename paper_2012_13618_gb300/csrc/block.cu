@@ -227,7 +227,7 @@ __device__ void blk_select_apply(Ctx &x, const DLevel &L, int kind, long long sq
     __syncthreads();
     d_sel_hist(x.t, L.N, kind, x.gain, side, L.nw, st, h);
     __syncthreads();
-    d_sel_find(kind, sq, st);
+    d_sel_find(kind, sq, st, st->hist);
     __syncthreads();
     if (st->slow) {
         for (int pass = 0; pass < 3; ++pass) {
@@ -235,7 +235,7 @@ __device__ void blk_select_apply(Ctx &x, const DLevel &L, int kind, long long sq
             __syncthreads();
             d_sel_hist_exact(x.t, L.N, kind, x.gain, side, L.nw, st, h);
             __syncthreads();
-            d_sel_find_exact(st, x.status);
+            d_sel_find_exact(st, x.status, st->hist);
             __syncthreads();
         }
     }
@@ -246,7 +246,7 @@ __device__ void blk_select_apply(Ctx &x, const DLevel &L, int kind, long long sq
 __device__ void blk_side_weights(Ctx &x, const DLevel &L, const uint8_t *side) {
     if (threadIdx.x == 0) { x.st->W[0] = 0; x.st->W[1] = 0; }
     __syncthreads();
-    d_side_weights(x.t, L.N, side, L.nw, x.st);
+    d_side_weights(x.t, L.N, side, L.nw, x.st->W);
     __syncthreads();
 }
 

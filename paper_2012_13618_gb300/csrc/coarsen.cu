@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(kBlock)
 k_seg_small(int E, const int *__restrict__ hoff, const int *__restrict__ pins,
             const int *__restrict__ cmap, int *__restrict__ scratch, int *__restrict__ cnt,
             int *__restrict__ mid_list, int *__restrict__ big_list, int *__restrict__ counters) {
-    d_seg_small<MAP>(GridTeam(), E, hoff, pins, cmap, scratch, cnt, mid_list, big_list, counters);
+    d_seg_small<MAP>(GridTeam(), E, hoff, pins, cmap, scratch, cnt, mid_list, big_list, counters,
+                     kGridMidDeg);
 }
 
 template <bool MAP>
@@ -77,8 +78,9 @@ k_seg_copy(int E, int P, const int *__restrict__ hoff, const int *__restrict__ s
 // atomic per pin would serialise on the heaviest nodes.  Each block merges its counts with one
 // global atomic per node it touched.
 constexpr int kPrivNodes = 24576;
+constexpr int kPrivBlock = 1024;  // large blocks: clearing and merging N counters is per block
 
-__global__ void __launch_bounds__(kLbBlock)
+__global__ void __launch_bounds__(kPrivBlock)
 k_seg_copy_priv(int E, int P, int N, const int *__restrict__ hoff, const int *__restrict__ scratch,
                 const int *__restrict__ cnt, const int *__restrict__ emap,
                 const int *__restrict__ hoff_out, int *__restrict__ pins_out, int *__restrict__ deg) {
@@ -109,7 +111,7 @@ k_seg_copy_priv(int E, int P, int N, const int *__restrict__ hoff, const int *__
 // Pass 1 counts this block's pins per node, one global atomic per touched node reserves the
 // block's range, pass 2 hands out positions inside the range by shared-memory atomics.  Both
 // passes visit the same tiles.
-__global__ void __launch_bounds__(kLbBlock)
+__global__ void __launch_bounds__(kPrivBlock)
 k_fill_adj_priv(int E, int P, int N, const int *__restrict__ hoff, const int *__restrict__ pins,
                 int *__restrict__ cursor, int *__restrict__ nadj) {
     extern __shared__ int s_cnt[];
@@ -129,12 +131,11 @@ k_fill_adj_priv(int E, int P, int N, const int *__restrict__ hoff, const int *__
     d_fill_adj_with(GridTeam(), E, P, hoff, pins, nadj, [&](int v) { return atomicAdd(s_cnt + v, 1); });
 }
 
-// Blocks for the private-counter kernels: enough pins per block to amortise clearing and
-// merging N counters, at least one block per SM.
-inline int priv_grid(int P, int N) {
-    int64_t b = (int64_t)P / std::max(N, 1);
-    if (b < 152) b = 152;
-    return (int)std::min<int64_t>(b, lb_grid(P));
+// Blocks for the private-counter kernels: one tile of kPrivBlock * kLbItems pins each, at most
+// two blocks per SM (up to 96 KB of counters each); blocks loop over further tiles.
+inline int priv_grid(int P) {
+    int64_t b = ((int64_t)P + kPrivBlock * kLbItems - 1) / (kPrivBlock * kLbItems);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 2 * 152));
 }
 
 __global__ void k_fill(int n, int val, int *__restrict__ a) {
@@ -147,9 +148,24 @@ k_fill_adj(int E, int P, const int *__restrict__ hoff, const int *__restrict__ p
     d_fill_adj(GridTeam(), E, P, hoff, pins, cursor, nadj);
 }
 
-__global__ void k_hedge_key(int E, int policy, const int *__restrict__ hoff,
-                            const int *__restrict__ hw, unsigned long long *__restrict__ hkey) {
+// Start of a level: hyperedge keys, and every per-hyperedge / per-node accumulator of the
+// matching reset in the same pass (ssize, sweight, rep, best; nkey).
+__global__ void k_level_init(int E, int N, int policy, const int *__restrict__ hoff,
+                             const int *__restrict__ hw, unsigned long long *__restrict__ hkey,
+                             int *__restrict__ ssize, int *__restrict__ sweight,
+                             unsigned *__restrict__ rep, unsigned long long *__restrict__ best,
+                             unsigned long long *__restrict__ nkey) {
     d_hedge_key(GridTeam(), E, policy, hoff, hw, hkey);
+    const int n = E > N ? E : N;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (i < E) {
+            ssize[i] = 0;
+            sweight[i] = 0;
+            rep[i] = ~0u;
+            best[i] = ~0ull;
+        }
+        if (i < N) nkey[i] = ~0ull;
+    }
 }
 
 __global__ void __launch_bounds__(kLbBlock)
@@ -171,11 +187,20 @@ k_single_best(int E, int P, const int *__restrict__ hoff, const int *__restrict_
     d_single_best(GridTeam(), E, P, hoff, pins, match, ssize, sweight, best);
 }
 
+// Groups, plus the coarse level's accumulators cleared for later phases of this level: node
+// weights (k_cmap), degree counters (contraction copy) for up to N coarse nodes, and the two
+// hyperedge list counters of seg_unique.
 __global__ void __launch_bounds__(kBlock)
 k_group(int N, const int *__restrict__ match, const int *__restrict__ ssize,
         const unsigned long long *__restrict__ best, int *__restrict__ grp,
-        unsigned *__restrict__ rep) {
+        unsigned *__restrict__ rep, int *__restrict__ cw, int *__restrict__ deg,
+        int *__restrict__ list_counts) {
     d_group(GridTeam(), N, match, ssize, best, grp, rep);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        cw[i] = 0;
+        deg[i] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 2) list_counts[threadIdx.x] = 0;
 }
 
 __global__ void k_cmap(int N, const int *__restrict__ grp, const int *__restrict__ gcid,
@@ -188,15 +213,16 @@ namespace {
 
 // Per hyperedge: pins mapped through `map` (identity when null), sorted and de-duplicated into
 // scratch at the hyperedge's own offset; cnt[e] = number of distinct values.
+// `counters_zero`: small[0..1] are known to be zero already (else they are cleared here).
 void seg_unique(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int *pins,
-                const int *map, int *scratch, int *cnt) {
+                const int *map, int *scratch, int *cnt, bool counters_zero) {
     cudaStream_t s = g->stream;
     Work &w = g->w;
     int *mid = (int *)w.e_c.ensure(sizeof(int) * (size_t)std::max(E, 1), s);
     int *big = (int *)w.e_d.ensure(sizeof(int) * (size_t)std::max(E, 1), s);
     int *small = w.small.as<int>();  // [0] mid count, [1] big count
-    BP_CUDA(cudaMemsetAsync(small, 0, 2 * sizeof(int), s));
     if (E == 0) return;
+    if (!counters_zero) BP_CUDA(cudaMemsetAsync(small, 0, 2 * sizeof(int), s));
     // reads hoff, pins, map gathers; writes distinct pins (<= P) and counts
     ProfScope ps("contract_unique", 8.0 * E + 4.0 * P * (map ? 3 : 2), s);
     if (map) k_seg_small<true><<<grid_for(E), kBlock, 0, s>>>(E, hoff, pins, map, scratch, cnt, mid, big, small);
@@ -206,7 +232,7 @@ void seg_unique(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const in
     if (map) k_seg_mid<true><<<mid_grid, kBlock, 0, s>>>(hoff, pins, map, scratch, cnt, mid, small);
     else k_seg_mid<false><<<mid_grid, kBlock, 0, s>>>(hoff, pins, map, scratch, cnt, mid, small);
     BP_LAUNCH();
-    int big_grid = std::max(1, std::min(152 * 4, P / (kMidDeg + 1) + 1));
+    int big_grid = std::max(1, std::min(152 * 4, P / (kGridMidDeg + 1) + 1));
     if (map) k_seg_big<true><<<big_grid, kBigThreads, 0, s>>>(hoff, pins, map, scratch, cnt, big, small);
     else k_seg_big<false><<<big_grid, kBigThreads, 0, s>>>(hoff, pins, map, scratch, cnt, big, small);
     BP_LAUNCH();
@@ -215,15 +241,14 @@ void seg_unique(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const in
 // Sorted-unique of every hyperedge's (mapped) pins into the coarse CSR of `c`.
 // Sets c.E and c.P.  `map` null means identity (level-0 normalisation).
 void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int *pins,
-              const int *hw, const int *map, Level &c, int *deg) {
+              const int *hw, const int *map, Level &c, int *deg, bool counters_zero) {
     cudaStream_t s = g->stream;
     Work &w = g->w;
     int *scratch = (int *)w.p_a.ensure(sizeof(int) * (size_t)std::max(P, 1), s);
     int *cnt = (int *)w.e_a.ensure(sizeof(int) * (size_t)std::max(E, 1), s);
     int *emap = (int *)w.e_b.ensure(sizeof(int) * (size_t)std::max(E, 1), s);
     int *small = w.small.as<int>();
-    BP_CUDA(cudaMemsetAsync(small, 0, 8 * sizeof(int), s));
-    seg_unique(g, E, P, hoff, pins, map, scratch, cnt);
+    seg_unique(g, E, P, hoff, pins, map, scratch, cnt, counters_zero);
     c.b_hoff.ensure(sizeof(int) * ((size_t)E + 1), s);
     c.b_pins.ensure(sizeof(int) * (size_t)std::max(P, 1), s);
     bool unit = (hw == nullptr);
@@ -239,7 +264,7 @@ void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int 
             // scratch, coarse pins, degree atomics, per-hyperedge offsets
             ProfScope ps("contract_copy", 12.0 * P + 12.0 * E, s);
             if (c.N <= kPrivNodes)
-                k_seg_copy_priv<<<priv_grid(P, c.N), kLbBlock, sizeof(int) * (size_t)std::max(c.N, 1), s>>>(
+                k_seg_copy_priv<<<priv_grid(P), kPrivBlock, sizeof(int) * (size_t)std::max(c.N, 1), s>>>(
                     E, P, c.N, hoff, scratch, cnt, emap, c.hoff(), c.pins(), deg);
             else
                 k_seg_copy<<<lb_grid(P), kLbBlock, 0, s>>>(E, P, hoff, scratch, cnt, emap, c.hoff(), c.pins(), deg);
@@ -256,7 +281,7 @@ void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int 
 
 void distinct_counts(bipart_graph *g, Level &L, const int *d_map, int *cnt) {
     int *scratch = (int *)g->w.p_a.ensure(sizeof(int) * (size_t)std::max(L.P, 1), g->stream);
-    seg_unique(g, L.E, L.P, L.hoff(), L.pins(), d_map, scratch, cnt);
+    seg_unique(g, L.E, L.P, L.hoff(), L.pins(), d_map, scratch, cnt, false);
 }
 
 // Node -> hyperedge incidence of a level whose degrees were counted by its contraction
@@ -280,7 +305,7 @@ void build_incidence(bipart_graph *g, Level &L) {
     if (L.P > 0) {
         ProfScope ps("incidence_fill", 12.0 * L.P + 4.0 * L.E, s);
         if (L.N <= kPrivNodes)
-            k_fill_adj_priv<<<priv_grid(L.P, L.N), kLbBlock, sizeof(int) * (size_t)L.N, s>>>(
+            k_fill_adj_priv<<<priv_grid(L.P), kPrivBlock, sizeof(int) * (size_t)L.N, s>>>(
                 L.E, L.P, L.N, L.hoff(), L.pins(), cursor, L.nadj());
         else
             k_fill_adj<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.E, L.P, L.hoff(), L.pins(), cursor, L.nadj());
@@ -305,7 +330,7 @@ void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t
         P = (int32_t)g->w.host_small[0];
     }
     L.N = N;
-    contract(g, E, P, d_hoff, d_pins, d_hw, nullptr, L, degree_counters(g, N));
+    contract(g, E, P, d_hoff, d_pins, d_hw, nullptr, L, degree_counters(g, N), false);
     L.b_nw.ensure(sizeof(int) * (size_t)std::max(N, 1), s);
     if (d_nw) {
         BP_CUDA(cudaMemcpyAsync(L.nw(), d_nw, sizeof(int) * (size_t)N, cudaMemcpyDeviceToDevice, s));
@@ -323,25 +348,25 @@ void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy) {
     Work &w = g->w;
     const int N = f.N, E = f.E;
     unsigned long long *hkey = (unsigned long long *)w.e_key.ensure(sizeof(uint64_t) * (size_t)std::max(E, 1), s);
+    unsigned long long *best = (unsigned long long *)w.e_best.ensure(sizeof(uint64_t) * (size_t)std::max(E, 1), s);
+    unsigned long long *nkey = (unsigned long long *)w.n_key.ensure(sizeof(uint64_t) * (size_t)std::max(N, 1), s);
     int *ssize = (int *)w.e_a.ensure(sizeof(int) * (size_t)std::max(E, 1), s);
     int *sweight = (int *)w.e_b.ensure(sizeof(int) * (size_t)std::max(E, 1), s);
     unsigned *rep = (unsigned *)w.e_c.ensure(sizeof(int) * (size_t)std::max(E, 1), s);
     int *gcid = (int *)w.e_d.ensure(sizeof(int) * (size_t)std::max(E, 1), s);
     int *grp = (int *)w.n_c.ensure(sizeof(int) * (size_t)std::max(N, 1), s);
+    // the coarse level has at most N nodes: its weights and degree counters are sized (and
+    // cleared by k_group) for N before N' is known
+    int *deg = (int *)w.n_a.ensure(sizeof(int) * (size_t)std::max(N, 1), s);
+    c.b_nw.ensure(sizeof(int) * (size_t)std::max(N, 1), s);
     int *small = w.small.as<int>();
-    if (E > 0) {
-        {
-            ProfScope ps("hedge_key", 12.0 * E + (f.hw() ? 4.0 * E : 0.0), s);
-            k_hedge_key<<<grid_for(E), kBlock, 0, s>>>(E, policy, f.hoff(), f.hw(), hkey);
-            BP_LAUNCH();
-        }
-        BP_CUDA(cudaMemsetAsync(ssize, 0, sizeof(int) * (size_t)E, s));
-        BP_CUDA(cudaMemsetAsync(sweight, 0, sizeof(int) * (size_t)E, s));
-        BP_CUDA(cudaMemsetAsync(rep, 0xff, sizeof(int) * (size_t)E, s));
+    if (N > 0 || E > 0) {
+        ProfScope ps("hedge_key", 12.0 * E + (f.hw() ? 4.0 * E : 0.0) + 20.0 * E + 8.0 * N, s);
+        k_level_init<<<grid_for(std::max(E, N)), kBlock, 0, s>>>(E, N, policy, f.hoff(), f.hw(), hkey,
+                                                                 ssize, sweight, rep, best, nkey);
+        BP_LAUNCH();
     }
     if (N > 0) {
-        unsigned long long *nkey = (unsigned long long *)w.n_key.ensure(sizeof(uint64_t) * (size_t)N, s);
-        BP_CUDA(cudaMemsetAsync(nkey, 0xff, sizeof(uint64_t) * (size_t)N, s));
         if (f.P > 0) {
             // noff, nadj, 8-byte key gather per incidence, one 8-byte atomic per node run
             ProfScope ps("match_min", 4.0 * N + 12.0 * f.P + 8.0 * N, s);
@@ -353,16 +378,14 @@ void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy) {
             k_match_set<<<grid_for(N), kBlock, 0, s>>>(N, nkey, f.nw(), f.match(), ssize, sweight);
             BP_LAUNCH();
         }
-        unsigned long long *best = hkey;  // the hyperedge keys are no longer needed
-        BP_CUDA(cudaMemsetAsync(best, 0xff, sizeof(uint64_t) * (size_t)E, s));
         if (f.P > 0) {
             ProfScope ps("single_best", 4.0 * E + 4.0 * f.P, s);
             k_single_best<<<lb_grid(f.P), kLbBlock, 0, s>>>(E, f.P, f.hoff(), f.pins(), f.match(), ssize, sweight, best);
             BP_LAUNCH();
         }
         {
-            ProfScope ps("group", 20.0 * N, s);
-            k_group<<<grid_for(N), kBlock, 0, s>>>(N, f.match(), ssize, best, grp, rep);
+            ProfScope ps("group", 20.0 * N + 8.0 * N, s);
+            k_group<<<grid_for(N), kBlock, 0, s>>>(N, f.match(), ssize, best, grp, rep, c.nw(), deg, small);
             BP_LAUNCH();
         }
         {
@@ -373,14 +396,12 @@ void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy) {
     }
     const int Nc = N > 0 ? read_i32(g, small + 4) : 0;
     c.N = Nc;
-    c.b_nw.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);
     if (N > 0) {
-        BP_CUDA(cudaMemsetAsync(c.nw(), 0, sizeof(int) * (size_t)Nc, s));
         ProfScope ps("cmap", 24.0 * N, s);
         k_cmap<<<grid_for(N), kBlock, 0, s>>>(N, grp, gcid, f.nw(), f.cmap(), c.nw());
         BP_LAUNCH();
     }
-    contract(g, E, f.P, f.hoff(), f.pins(), f.hw(), f.cmap(), c, degree_counters(g, Nc));
+    contract(g, E, f.P, f.hoff(), f.pins(), f.hw(), f.cmap(), c, deg, N > 0);
     build_incidence(g, c);
     c.b_cmap.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);
     c.b_match.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);

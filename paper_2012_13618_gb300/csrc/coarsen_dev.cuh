@@ -12,6 +12,8 @@ namespace bp {
 
 constexpr int kSmallDeg = 8;      // hyperedges up to this degree: one thread each
 constexpr int kMidDeg = 1024;     // up to this degree: one warp each (register bitonic sort)
+constexpr int kGridMidDeg = 256;  // the same bound for the grid kernels, where one warp sorting
+                                  // up to 1024 keys would hold up the whole launch
 constexpr int kBigWords = 8192;   // bitmap window of the block tier: 32 KB = 262,144 ids
 
 // ------------------------------------------------------------------ small fixed sorting network
@@ -108,11 +110,12 @@ __device__ __forceinline__ int warp_unique(const int *pins, const int *cmap, int
 // irrelevant: every hyperedge writes only its own slots).
 template <bool MAP, class Team>
 __device__ void d_seg_small(Team t, int E, const int *hoff, const int *pins, const int *cmap,
-                            int *scratch, int *cnt, int *mid_list, int *big_list, int *counters) {
+                            int *scratch, int *cnt, int *mid_list, int *big_list, int *counters,
+                            int mid_max = kMidDeg) {
     for (int e = t.rank(); e < E; e += t.size()) {
         int a = Team::ld(hoff + e), d = Team::ld(hoff + e + 1) - a;
         if (d > kSmallDeg) {
-            if (d > kMidDeg) big_list[atomicAdd(&counters[1], 1)] = e;
+            if (d > mid_max) big_list[atomicAdd(&counters[1], 1)] = e;
             else mid_list[atomicAdd(&counters[0], 1)] = e;
             continue;
         }
@@ -131,7 +134,7 @@ __device__ void d_seg_small(Team t, int E, const int *hoff, const int *pins, con
     }
 }
 
-// Mid tier: one warp per listed hyperedge (8 < d <= 1024), register bitonic sort.
+// Mid tier: one warp per listed hyperedge (8 < d <= mid_max), register bitonic sort.
 template <bool MAP, class Team>
 __device__ void d_seg_mid(Team t, const int *hoff, const int *pins, const int *cmap, int *scratch,
                           int *cnt, const int *list, const int *counters) {
@@ -353,10 +356,10 @@ __device__ void d_hedge_key(Team t, int E, int policy, const int *hoff, const in
 template <class Team>
 __device__ void d_match_min(Team t, int N, int P, const int *noff, const int *nadj,
                             const unsigned long long *hkey, unsigned long long *nkey) {
-    lb_for_each<unsigned long long>(
-        noff, N, P, ~0ull,
-        [&](int, int j, unsigned long long acc) {
-            unsigned long long k = Team::ld(hkey + Team::ld(nadj + j));
+    lb_for_each_items<unsigned long long>(
+        noff, N, P, nadj, ~0ull,
+        [&](int, int e, unsigned long long acc) {
+            unsigned long long k = Team::ld(hkey + e);
             return k < acc ? k : acc;
         },
         [&](int v, unsigned long long acc) {
@@ -388,11 +391,11 @@ template <class Team>
 __device__ void d_single_best(Team t, int E, int P, const int *hoff, const int *pins,
                               const int *match, const int *ssize, const int *sweight,
                               unsigned long long *best) {
-    lb_for_each<unsigned long long>(
-        hoff, E, P, ~0ull,
-        [&](int e, int i, unsigned long long acc) {
+    lb_for_each_items<unsigned long long>(
+        hoff, E, P, pins, ~0ull,
+        [&](int e, int u, unsigned long long acc) {
             if (Team::ld(ssize + e) != 1) return acc;
-            int mv = Team::ld(match + Team::ld(pins + i));
+            int mv = Team::ld(match + u);
             if (mv >= 0 && Team::ld(ssize + mv) >= 2) {
                 unsigned long long k = ((unsigned long long)(unsigned)Team::ld(sweight + mv) << 32) | (unsigned)mv;
                 acc = k < acc ? k : acc;

@@ -173,6 +173,25 @@ __device__ __forceinline__ void record_error(uint32_t *status, uint32_t code) {
     if (status) atomicOr(status, code);
 }
 
+// True in the block of a grid launch that arrives here last, which also puts `counter` back to
+// zero for the next launch.  Every block's global writes before the call are visible to that
+// block (fence, then one counter atomic per block); it should read them through L2 (__ldcg).
+__device__ __forceinline__ bool last_block(unsigned *counter) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(counter, 1u);
+        s_last = t == gridDim.x - 1;
+        if (s_last) {
+            *counter = 0u;
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    return s_last != 0;
+}
+
 inline int ceil_div_i(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // Teams: the threads that share one phase of the algorithm.  GridTeam = every thread of a kernel

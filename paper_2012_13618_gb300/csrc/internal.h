@@ -105,6 +105,8 @@ struct Work {
     Buf side_a, side_b;      // uint8 sides (ping-pong across levels)
     Buf gain;        // int32 gains
     Buf hc;          // int2 per-hyperedge gain contributions
+    Buf n1;          // int32 per-hyperedge side-1 pin counts (zero between gain passes)
+    Buf e_best;      // per-hyperedge uint64 singleton-attach keys
     Buf list;        // node list (rebalance candidates)
     Buf pinned;      // host-pinned mirror of `small`
     uint32_t *host_small = nullptr;
@@ -201,6 +203,9 @@ int *degree_counters(bipart_graph *g, int32_t N);
 void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, int64_t limit, int32_t iters,
                uint8_t *d_side0);
 const unsigned *bisect_status_word(bipart_graph *g);
+// Bytes at the start of the small scratch holding counters and selection state that phases
+// leave zero for the next one (cleared once at the start of every bisection).
+size_t small_state_bytes();
 void refine_init();  // once per process: kernel attributes (never during a capture)
 void coarsen_init();  // same, for the coarsening kernels
 int64_t balance_limit(int64_t W, double eps);

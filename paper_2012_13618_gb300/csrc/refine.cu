@@ -43,9 +43,11 @@ k_hedge_n1(int E, int P, const int *__restrict__ hoff, const int *__restrict__ p
     d_hedge_n1(GridTeam(), E, P, hoff, pins, side, n1);
 }
 
-__global__ void k_hedge_contrib(int E, const int *__restrict__ hoff, const int *__restrict__ hw,
-                                const int *__restrict__ n1, int2 *__restrict__ hc) {
-    d_hedge_contrib(GridTeam(), E, hoff, hw, n1, hc);
+// Contributions, n1 put back to zero, and the gains of the N nodes cleared for k_node_gain.
+__global__ void k_hedge_contrib(int E, int N, const int *__restrict__ hoff, const int *__restrict__ hw,
+                                int *__restrict__ n1, int2 *__restrict__ hc, int *__restrict__ gain) {
+    d_hedge_contrib(GridTeam(), E, hoff, hw, n1, hc, true);
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) gain[v] = 0;
 }
 
 __global__ void __launch_bounds__(kLbBlock)
@@ -54,39 +56,59 @@ k_node_gain(int N, int P, const int *__restrict__ noff, const int *__restrict__ 
     d_node_gain(GridTeam(), N, P, noff, nadj, hc, side, gain);
 }
 
+// Copies the grid's accumulated histogram into shared memory and clears it in global memory
+// (the last block of a selection pass).
+__device__ __forceinline__ void take_hist(RState *st, unsigned (*h)[kHistBins]) {
+    unsigned *g = &st->hist[0][0];
+    for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) {
+        (&h[0][0])[i] = __ldcg(g + i);
+        g[i] = 0u;
+    }
+    __syncthreads();
+}
+
+// Fast selection pass: clamped-gain histogram, then (last block) the per-group threshold.  The
+// rebalancing list is emptied for the application scan that follows.
 __global__ void __launch_bounds__(kBlock)
-k_sel_hist(int N, int kind, const int *__restrict__ gain, const uint8_t *__restrict__ side,
-           const int *__restrict__ nw, RState *st) {
+k_sel(int N, int kind, long long s, const int *__restrict__ gain, const uint8_t *__restrict__ side,
+      const int *__restrict__ nw, RState *st) {
     __shared__ unsigned h[2][kHistBins];
     d_sel_hist(GridTeam(), N, kind, gain, side, nw, st, h);
+    if (!last_block(&st->arrived)) return;
+    take_hist(st, h);
+    d_sel_find(kind, s, st, h);
+    if (threadIdx.x == 0) st->list_count = 0;
 }
 
-__global__ void __launch_bounds__(1024) k_sel_find(int kind, long long s, RState *st) {
-    d_sel_find(kind, s, st);
-}
-
+// One digit of the exact radix select: histogram, then (last block) the narrowed range.
 __global__ void __launch_bounds__(kBlock)
-k_sel_hist_exact(int N, int kind, const int *__restrict__ gain, const uint8_t *__restrict__ side,
-                 const int *__restrict__ nw, RState *st) {
+k_sel_exact(int N, int kind, const int *__restrict__ gain, const uint8_t *__restrict__ side,
+            const int *__restrict__ nw, RState *st, uint32_t *status) {
     __shared__ unsigned h[2][kHistBins];
     d_sel_hist_exact(GridTeam(), N, kind, gain, side, nw, st, h);
+    if (!last_block(&st->arrived)) return;
+    take_hist(st, h);
+    d_sel_find_exact(st, status, h);
 }
 
-__global__ void __launch_bounds__(1024) k_sel_find_exact(RState *st, uint32_t *status) {
-    d_sel_find_exact(st, status);
-}
-
+// W = side weights: partial sums in Wacc, moved to W (and Wacc cleared) by the last block.
 __global__ void __launch_bounds__(kBlock)
 k_side_weights(int N, const uint8_t *__restrict__ side, const int *__restrict__ nw, RState *st) {
-    d_side_weights(GridTeam(), N, side, nw, st);
+    d_side_weights(GridTeam(), N, side, nw, st->Wacc);
+    if (!last_block(&st->arrived)) return;
+    if (threadIdx.x < 2) {
+        st->W[threadIdx.x] = __ldcg(&st->Wacc[threadIdx.x]);
+        st->Wacc[threadIdx.x] = 0ull;
+    }
 }
 
-__global__ void k_initial_cond(RState *st, long long max_rounds, uint32_t *status) {
-    d_initial_cond(st, max_rounds, status);
+__global__ void k_initial_cond(RState *st, long long max_rounds, uint32_t *status, int first) {
+    d_initial_cond(st, max_rounds, status, first != 0);
 }
 
-__global__ void k_rebal_cond(RState *st, long long limit, long long max_rounds, uint32_t *status) {
-    d_rebal_cond(st, limit, max_rounds, status);
+__global__ void k_rebal_cond(RState *st, long long limit, long long max_rounds, uint32_t *status,
+                             int first) {
+    d_rebal_cond(st, limit, max_rounds, status, first != 0);
 }
 
 __global__ void __launch_bounds__(1024)
@@ -127,12 +149,13 @@ RState *rstate(bipart_graph *g) {
     return reinterpret_cast<RState *>(g->w.small.as<char>() + 256);
 }
 
+// n1 (per-hyperedge side-1 counts) is zero at rest: k_hedge_contrib clears what k_hedge_n1
+// counted, and it clears the gains too, so no memset runs per pass.
 void compute_gains(bipart_graph *g, Level &L, const uint8_t *side, int *gain) {
     cudaStream_t s = g->stream;
-    int *n1 = g->w.e_d.as<int>();
+    int *n1 = g->w.n1.as<int>();
     int2 *hc = g->w.hc.as<int2>();
     if (L.E > 0) {
-        BP_CUDA(cudaMemsetAsync(n1, 0, sizeof(int) * (size_t)L.E, s));
         {
             // hoff, pins, one side byte per pin, one atomic per hyperedge run
             ProfScope ps("hedge_n1", 8.0 * L.E + 5.0 * L.P, s);
@@ -141,11 +164,13 @@ void compute_gains(bipart_graph *g, Level &L, const uint8_t *side, int *gain) {
         }
         {
             ProfScope ps("hedge_contrib", 16.0 * L.E + (L.hw() ? 4.0 * L.E : 0.0), s);
-            k_hedge_contrib<<<grid_for(L.E), kBlock, 0, s>>>(L.E, L.hoff(), L.hw(), n1, hc);
+            k_hedge_contrib<<<grid_for(std::max(L.E, L.N)), kBlock, 0, s>>>(L.E, L.N, L.hoff(), L.hw(),
+                                                                            n1, hc, gain);
             BP_LAUNCH();
         }
+    } else if (L.N > 0) {
+        BP_CUDA(cudaMemsetAsync(gain, 0, sizeof(int) * (size_t)L.N, s));
     }
-    if (L.N > 0) BP_CUDA(cudaMemsetAsync(gain, 0, sizeof(int) * (size_t)L.N, s));
     if (L.P > 0) {
         // noff, nadj, 8-byte contribution gather per incidence, side, gain
         ProfScope ps("node_gain", 9.0 * L.N + 12.0 * L.P, s);
@@ -159,21 +184,15 @@ void select_apply(bipart_graph *g, Level &L, int kind, long long sq, const int *
                   uint8_t *side, int *list) {
     cudaStream_t s = g->stream;
     RState *st = rstate(g);
-    BP_CUDA(cudaMemsetAsync(&st->hist[0][0], 0, sizeof(st->hist), s));
-    if (kind == SEL_REBAL) BP_CUDA(cudaMemsetAsync(&st->list_count, 0, sizeof(unsigned), s));
     {
         ProfScope ps("select_hist", 9.0 * L.N, s);
-        k_sel_hist<<<grid_for(L.N), kBlock, 0, s>>>(L.N, kind, gain, side, L.nw(), st);
+        k_sel<<<grid_for(L.N), kBlock, 0, s>>>(L.N, kind, sq, gain, side, L.nw(), st);
         BP_LAUNCH();
     }
-    k_sel_find<<<1, 1024, 0, s>>>(kind, sq, st);
-    BP_LAUNCH();
     device_if(g, &st->slow, [&]() {
         for (int pass = 0; pass < 3; ++pass) {
-            BP_CUDA(cudaMemsetAsync(&st->hist[0][0], 0, sizeof(st->hist), g->stream));
-            k_sel_hist_exact<<<grid_for(L.N), kBlock, 0, g->stream>>>(L.N, kind, gain, side, L.nw(), st);
-            BP_LAUNCH();
-            k_sel_find_exact<<<1, 1024, 0, g->stream>>>(st, dev_status(g));
+            k_sel_exact<<<grid_for(L.N), kBlock, 0, g->stream>>>(L.N, kind, gain, side, L.nw(), st,
+                                                                 dev_status(g));
             BP_LAUNCH();
         }
     });
@@ -186,11 +205,8 @@ void select_apply(bipart_graph *g, Level &L, int kind, long long sq, const int *
 void side_weights(bipart_graph *g, Level &L, const uint8_t *side) {
     cudaStream_t s = g->stream;
     RState *st = rstate(g);
-    BP_CUDA(cudaMemsetAsync(&st->W[0], 0, 2 * sizeof(unsigned long long), s));
-    if (L.N > 0) {
-        k_side_weights<<<grid_for(L.N), kBlock, 0, s>>>(L.N, side, L.nw(), st);
-        BP_LAUNCH();
-    }
+    k_side_weights<<<grid_for(L.N), kBlock, 0, s>>>(L.N, side, L.nw(), st);
+    BP_LAUNCH();
 }
 
 // Algorithm 3 on the coarsest level.
@@ -200,14 +216,13 @@ void initial_partition(bipart_graph *g, Level &L, uint8_t *side, int *gain) {
     RState *st = rstate(g);
     const long long sq = ceil_sqrt64(L.N);
     BP_CUDA(cudaMemsetAsync(side, 1, (size_t)L.N, s));
-    BP_CUDA(cudaMemsetAsync(&st->rounds, 0, sizeof(unsigned), s));
     side_weights(g, L, side);
-    k_initial_cond<<<1, 32, 0, s>>>(st, (long long)L.N + 1, dev_status(g));
+    k_initial_cond<<<1, 32, 0, s>>>(st, (long long)L.N + 1, dev_status(g), 1);
     BP_LAUNCH();
     device_while(g, &st->flag, (int64_t)L.N + 2, [&]() {
         compute_gains(g, L, side, gain);
         select_apply(g, L, SEL_INITIAL, sq, gain, side, nullptr);
-        k_initial_cond<<<1, 32, 0, g->stream>>>(st, (long long)L.N + 1, dev_status(g));
+        k_initial_cond<<<1, 32, 0, g->stream>>>(st, (long long)L.N + 1, dev_status(g), 0);
         BP_LAUNCH();
     });
 }
@@ -228,17 +243,15 @@ void rebalance(bipart_graph *g, Level &L, uint8_t *side, int *gain, int64_t limi
     int S = 1;
     while (S < sq) S <<= 1;
     const size_t smem = sizeof(unsigned long long) * (size_t)S;
-    BP_CUDA(cudaMemsetAsync(&st->warn, 0, sizeof(unsigned), s));
-    BP_CUDA(cudaMemsetAsync(&st->rounds, 0, sizeof(unsigned), s));
     side_weights(g, L, side);
-    k_rebal_cond<<<1, 32, 0, s>>>(st, (long long)limit, (long long)L.N + 1, dev_status(g));
+    k_rebal_cond<<<1, 32, 0, s>>>(st, (long long)limit, (long long)L.N + 1, dev_status(g), 1);
     BP_LAUNCH();
     device_while(g, &st->flag, (int64_t)L.N + 2, [&]() {
         compute_gains(g, L, side, gain);
         select_apply(g, L, SEL_REBAL, sq, gain, side, list);
         k_rebal_move<<<1, 1024, smem, g->stream>>>(gain, side, L.nw(), list, st, sq);
         BP_LAUNCH();
-        k_rebal_cond<<<1, 32, 0, g->stream>>>(st, (long long)limit, (long long)L.N + 1, dev_status(g));
+        k_rebal_cond<<<1, 32, 0, g->stream>>>(st, (long long)limit, (long long)L.N + 1, dev_status(g), 0);
         BP_LAUNCH();
     });
 }
@@ -258,7 +271,9 @@ void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, int64_t limit, int
     uint8_t *sb = (uint8_t *)g->w.side_b.ensure((size_t)nmax, s);
     int *gain = (int *)g->w.gain.ensure(sizeof(int) * (size_t)nmax, s);
     g->w.hc.ensure(sizeof(int2) * (size_t)emax, s);
-    g->w.e_d.ensure(sizeof(int) * (size_t)emax, s);
+    // zero at rest between passes; cleared here once in case an earlier run stopped midway
+    void *n1 = g->w.n1.ensure(sizeof(int) * (size_t)emax, s);
+    BP_CUDA(cudaMemsetAsync(n1, 0, sizeof(int) * (size_t)emax, s));
 
     uint8_t *cur = sa, *other = sb;
     initial_partition(g, *levels[Lc], cur, gain);
@@ -285,6 +300,8 @@ void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, int64_t limit, int
 }
 
 const unsigned *bisect_status_word(bipart_graph *g) { return &rstate(g)->status0; }
+
+size_t small_state_bytes() { return 256 + sizeof(RState); }
 
 void refine_init() {
     static std::once_flag once;

@@ -39,6 +39,8 @@ struct RState {
     unsigned warn;             // rebalance ran out of candidates
     unsigned rounds;           // loop guard
     unsigned status0;          // warn of the level-0 rebalance
+    unsigned arrived;          // blocks that finished a fused grid phase (zero at rest)
+    unsigned long long Wacc[2];  // side-weight partial sums of a grid launch (zero at rest)
 };
 
 __device__ __forceinline__ unsigned gkey(int gain) { return (unsigned)gain ^ 0x80000000u; }
@@ -55,9 +57,9 @@ __device__ __forceinline__ int sel_group(int kind, const RState *st, int gain, u
 template <class Team>
 __device__ void d_hedge_n1(Team t, int E, int P, const int *hoff, const int *pins,
                            const uint8_t *side, int *n1) {
-    lb_for_each<int>(
-        hoff, E, P, 0,
-        [&](int, int i, int acc) { return acc + Team::ld(side + Team::ld(pins + i)); },
+    lb_for_each_items<int>(
+        hoff, E, P, pins, 0,
+        [&](int, int u, int acc) { return acc + Team::ld(side + u); },
         [&](int e, int acc) {
             if (acc) atomicAdd(n1 + e, acc);
         },
@@ -66,11 +68,13 @@ __device__ void d_hedge_n1(Team t, int E, int P, const int *hoff, const int *pin
 
 // Contribution of e to a pin on side i: +w if n_i == 1 (moving it uncuts e), -w if n_i == |e|
 // (moving it cuts e), else 0.
+// With `reset`, n1[e] is put back to zero once read (the grid path keeps n1 zero at rest).
 template <class Team>
-__device__ void d_hedge_contrib(Team t, int E, const int *hoff, const int *hw, const int *n1,
-                                int2 *hc) {
+__device__ void d_hedge_contrib(Team t, int E, const int *hoff, const int *hw, int *n1,
+                                int2 *hc, bool reset = false) {
     for (int e = t.rank(); e < E; e += t.size()) {
         int d = Team::ld(hoff + e + 1) - Team::ld(hoff + e), a1 = Team::ld(n1 + e), a0 = d - a1;
+        if (reset) n1[e] = 0;
         int w = hw ? Team::ld(hw + e) : 1;
         int c0 = a0 == 1 ? w : (a0 == d ? -w : 0);
         int c1 = a1 == 1 ? w : (a1 == d ? -w : 0);
@@ -82,10 +86,10 @@ __device__ void d_hedge_contrib(Team t, int E, const int *hoff, const int *hw, c
 template <class Team>
 __device__ void d_node_gain(Team t, int N, int P, const int *noff, const int *nadj, const int2 *hc,
                             const uint8_t *side, int *gain) {
-    lb_for_each<int>(
-        noff, N, P, 0,
-        [&](int v, int j, int acc) {
-            int2 c = Team::ld(hc + Team::ld(nadj + j));
+    lb_for_each_items<int>(
+        noff, N, P, nadj, 0,
+        [&](int v, int e, int acc) {
+            int2 c = Team::ld(hc + e);
             return acc + (Team::ld(side + v) ? c.y : c.x);
         },
         [&](int v, int acc) {
@@ -153,11 +157,11 @@ __device__ inline int hist_find(const unsigned *hist, unsigned need, unsigned *a
 
 // One block: decides K per group from the fast histogram and fixes the threshold, or starts the
 // exact path (st->slow).
-__device__ inline void d_sel_find(int kind, long long s, RState *st) {
+__device__ inline void d_sel_find(int kind, long long s, RState *st, const unsigned (*hist)[kHistBins]) {
     unsigned cnt[2];
     for (int i = 0; i < 2; ++i) {
         unsigned above, total;
-        hist_find(st->hist[i], 0, &above, &total);
+        hist_find(hist[i], 0, &above, &total);
         cnt[i] = total;
     }
     unsigned K[2] = {0, 0};
@@ -172,7 +176,7 @@ __device__ inline void d_sel_find(int kind, long long s, RState *st) {
         SelGroup &G = st->g[i];
         unsigned above = 0, total = 0;
         int b = -1;
-        if (K[i] > 0 && K[i] < cnt[i]) b = hist_find(st->hist[i], K[i], &above, &total);
+        if (K[i] > 0 && K[i] < cnt[i]) b = hist_find(hist[i], K[i], &above, &total);
         if (threadIdx.x == 0) {
             G.cnt = cnt[i];
             G.K = K[i];
@@ -236,14 +240,14 @@ __device__ void d_sel_hist_exact(Team t, int N, int kind, const int *gain, const
 }
 
 // One block: narrows every group on the exact path to the next digit, or fixes its threshold.
-__device__ inline void d_sel_find_exact(RState *st, uint32_t *status) {
+__device__ inline void d_sel_find_exact(RState *st, uint32_t *status, const unsigned (*hist)[kHistBins]) {
     for (int i = 0; i < 2; ++i) {
         SelGroup &G = st->g[i];
         const unsigned mode = G.mode;
         __syncthreads();
         if (mode != 3) continue;  // block-uniform
         unsigned above = 0, total = 0;
-        int b = hist_find(st->hist[i], G.need, &above, &total);
+        int b = hist_find(hist[i], G.need, &above, &total);
         if (threadIdx.x == 0) {
             if (b < 0) {
                 G.mode = 0;
@@ -321,8 +325,10 @@ struct ApplyOut {
     }
 };
 
+// Adds the weights of sides 0 and 1 into acc[0], acc[1].
 template <class Team>
-__device__ void d_side_weights(Team t, int N, const uint8_t *side, const int *nw, RState *st) {
+__device__ void d_side_weights(Team t, int N, const uint8_t *side, const int *nw,
+                               unsigned long long *acc) {
     unsigned long long w0 = 0, w1 = 0;
     for (int v = t.rank(); v < N; v += t.size()) {
         if (Team::ld(side + v)) w1 += Team::ld(nw + v);
@@ -331,14 +337,16 @@ __device__ void d_side_weights(Team t, int N, const uint8_t *side, const int *nw
     w0 = warp_sum(w0);
     w1 = warp_sum(w1);
     if ((threadIdx.x & 31) == 0) {
-        if (w0) atomicAdd(&st->W[0], w0);
-        if (w1) atomicAdd(&st->W[1], w1);
+        if (w0) atomicAdd(&acc[0], w0);
+        if (w1) atomicAdd(&acc[1], w1);
     }
 }
 
 // Algorithm 3 loop condition: continue while P0 is lighter than P1 (guarded).  One thread acts.
-__device__ inline void d_initial_cond(RState *st, long long max_rounds, uint32_t *status) {
+__device__ inline void d_initial_cond(RState *st, long long max_rounds, uint32_t *status,
+                                      bool first = false) {
     if (threadIdx.x != 0) return;
+    if (first) st->rounds = 0;
     unsigned f = (long long)st->W[0] < (long long)st->W[1];
     if (f && (long long)(st->rounds++) >= max_rounds) {
         record_error(status, DEV_TIMEOUT);
@@ -349,8 +357,13 @@ __device__ inline void d_initial_cond(RState *st, long long max_rounds, uint32_t
 
 // Rebalance loop condition (reading C13): heavy side above the limit and candidates left.  One
 // thread acts.
-__device__ inline void d_rebal_cond(RState *st, long long limit, long long max_rounds, uint32_t *status) {
+__device__ inline void d_rebal_cond(RState *st, long long limit, long long max_rounds, uint32_t *status,
+                                    bool first = false) {
     if (threadIdx.x != 0) return;
+    if (first) {
+        st->rounds = 0;
+        st->warn = 0;
+    }
     st->limit = limit;
     long long W0 = (long long)st->W[0], W1 = (long long)st->W[1];
     int H = W0 > limit ? 0 : (W1 > limit ? 1 : -1);

@@ -37,7 +37,9 @@ k_scan(int64_t n, In in, Out out, unsigned long long *state, uint32_t *status) {
     unsigned long long *finished = state + 1;
     unsigned long long *tiles = state + 2;
 
-    if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(counter, 1ull);
+    // a single-tile scan has no predecessor: it neither takes a ticket nor touches the state
+    const bool solo = gridDim.x == 1;
+    if (threadIdx.x == 0) s_tile = solo ? 0u : (uint32_t)atomicAdd(counter, 1ull);
     __syncthreads();
     const int64_t tile = s_tile;
     const int64_t base = tile * kScanTile;
@@ -58,7 +60,10 @@ k_scan(int64_t n, In in, Out out, unsigned long long *state, uint32_t *status) {
     uint64_t total;
     uint64_t excl = block_exclusive_scan<uint64_t>(sum, red, &total);
 
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && solo) {
+        s_prefix = 0;
+        s_last = 0;
+    } else if (threadIdx.x == 0) {
         uint64_t prefix = 0;
         if (tile == 0) {
             atomicExch(&tiles[0], (unsigned long long)(kFlagPre | (total & kScanValMask)));
