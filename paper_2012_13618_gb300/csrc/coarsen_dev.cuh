@@ -296,25 +296,21 @@ struct DegOut {
 template <class Team, class Claim>
 __device__ void d_fill_adj_with(Team t, int E, int P, const int *hoff, const int *pins, int *nadj,
                                 Claim claim) {
-    __shared__ int s_rng[2];
     const int tile = blockDim.x * kLbItems;
     for (int64_t t0 = (int64_t)t.block() * tile; t0 < P; t0 += (int64_t)t.blocks() * tile) {
         const int j0 = (int)t0;
         const int j1 = (int)(t0 + tile < P ? t0 + tile : P);
-        __syncthreads();
-        if (threadIdx.x == 0) s_rng[0] = lb_seg<Team>(hoff, j0, 0, E - 1);
-        if (threadIdx.x == 32) s_rng[1] = lb_seg<Team>(hoff, j1 - 1, 0, E - 1);
-        __syncthreads();
+        const LbTile T = lb_tile<Team>(hoff, E, j0, j1);
         const int j = j0 + threadIdx.x * kLbItems;
         if (j >= j1) continue;
         const int n = j1 - j < kLbItems ? j1 - j : kLbItems;
-        int s = lb_seg<Team>(hoff, j, s_rng[0], s_rng[1]);
-        int send = Team::ld(hoff + s + 1);
+        int s = lb_tile_seg<Team>(hoff, T, j);
+        int send = lb_tile_end<Team>(hoff, T, s);
         int v[kLbItems], e[kLbItems], pos[kLbItems];
 #pragma unroll
         for (int k = 0; k < kLbItems; ++k) {
             if (k < n) {
-                while (j + k >= send) { ++s; send = Team::ld(hoff + s + 1); }
+                while (j + k >= send) { ++s; send = lb_tile_end<Team>(hoff, T, s); }
                 e[k] = s;
                 v[k] = Team::ld(pins + j + k);
             }

@@ -1,8 +1,8 @@
 // Load-balanced segmented reductions over a CSR (offsets off[0..nseg], items [0, total)).
 //
 // A block owns kLbTile consecutive items; each thread owns kLbItems consecutive items of that
-// tile, finds the segment of its first item by binary search inside the block's segment range
-// and walks forward.  Per-segment partial results are flushed with one atomic per segment run,
+// tile, finds the segment of its first item inside the block's segment range (staged in shared
+// memory) and walks forward.  Per-segment partial results are flushed with one atomic per segment run,
 // so a segment with 100,000 items costs the same per item as one with 2 items, and the result
 // does not depend on the schedule when the combining operation is an integer sum or minimum.
 #pragma once
@@ -15,6 +15,8 @@ constexpr int kLbBlock = 256;
 constexpr int kLbItems = 8;
 constexpr int kLbTile = kLbBlock * kLbItems;
 
+constexpr int kLbStage = 2048;  // segment offsets of one tile staged in shared memory
+
 // Largest s in [lo, hi] with off[s] <= j (the non-empty segment holding item j).
 template <class Team = GridTeam>
 __device__ __forceinline__ int lb_seg(const int *off, int j, int lo, int hi) {
@@ -26,57 +28,96 @@ __device__ __forceinline__ int lb_seg(const int *off, int j, int lo, int hi) {
     return lo;
 }
 
-// Visits the items of this thread in order as (segment, item index) and calls
-// flush(segment, acc) whenever the segment changes and at the end.  `init` is the identity of
-// the combine operation; visit(seg, item, acc) folds one item into acc.  A tile is
-// blockDim.x * kLbItems items; the team's blocks take tiles in turn.
-template <class Acc, class Visit, class Flush, class Team = GridTeam>
-__device__ __forceinline__ void lb_for_each(const int *off, int nseg, int total, Acc init,
-                                            Visit visit, Flush flush, Team t = Team()) {
-    __shared__ int s_rng[2];
-    const int tile = blockDim.x * kLbItems;
-    for (int64_t t0 = (int64_t)t.block() * tile; t0 < total; t0 += (int64_t)t.blocks() * tile) {
-        const int j0 = (int)t0;
-        const int j1 = (int)(t0 + tile < total ? t0 + tile : total);
-        __syncthreads();
-        if (threadIdx.x == 0) s_rng[0] = lb_seg<Team>(off, j0, 0, nseg - 1);
-        if (threadIdx.x == 32) s_rng[1] = lb_seg<Team>(off, j1 - 1, 0, nseg - 1);
-        __syncthreads();
-        int j = j0 + threadIdx.x * kLbItems;
-        if (j >= j1) continue;
-        const int je = j + kLbItems < j1 ? j + kLbItems : j1;
-        int s = lb_seg<Team>(off, j, s_rng[0], s_rng[1]);
-        int send = Team::ld(off + s + 1);
-        Acc acc = init;
-        for (; j < je; ++j) {
-            while (j >= send) {  // next non-empty segment
-                flush(s, acc);
-                acc = init;
-                ++s;
-                send = Team::ld(off + s + 1);
-            }
-            acc = visit(s, j, acc);
-        }
-        flush(s, acc);
+// The same search by the 32 lanes of a warp together (off[lo] <= j): every round probes 32
+// evenly spaced offsets and keeps the stretch between the last probe <= j and the first probe
+// > j, so R candidates take about log32(R) dependent loads instead of log2(R).  All lanes call
+// it with the same arguments and all get the result.
+template <class Team = GridTeam>
+__device__ __forceinline__ int lb_seg_warp(const int *off, int j, int lo, int hi) {
+    const int lane = threadIdx.x & 31;
+    while (hi - lo >= 32) {
+        const int step = (hi - lo + 31) / 32;
+        const int q = min(lo + (lane + 1) * step, hi);
+        const unsigned below = __ballot_sync(0xffffffffu, Team::ld(off + q) <= j);
+        const int k = __popc(below);  // probes are ascending, so the true ones come first
+        const int nlo = k == 0 ? lo : min(lo + k * step, hi);
+        const int nhi = k == 32 ? hi : min(lo + (k + 1) * step, hi) - 1;
+        lo = nlo;
+        hi = nhi;
     }
+    const int q = lo + 1 + lane;
+    const unsigned below = __ballot_sync(0xffffffffu, q <= hi && Team::ld(off + q) <= j);
+    return lo + __popc(below);
 }
 
-// As lb_for_each, for a visit that reads one int per item: items[j] is loaded for all of the
-// thread's slots up front (two 16-byte loads when its kLbItems slots are in range and aligned),
-// and visit(seg, items[j], acc) folds it in.
+// Shared staging buffer of the load-balanced loops (one per kernel).
+__device__ __forceinline__ int *lb_stage() {
+    __shared__ int buf[kLbStage + 2];
+    return buf;
+}
+
+// Segments [s0, s1] of the tile of items [j0, j1): warps 0 and 1 search the segments of the
+// first and the last item; off[s0 .. s1 + 1] is then staged in shared memory when it fits.
+// Called by the whole block (blockDim >= 64).
+struct LbTile {
+    int s0, s1;
+    bool staged;
+};
+
+template <class Team>
+__device__ __forceinline__ LbTile lb_tile(const int *off, int nseg, int j0, int j1) {
+    __shared__ int s_rng[2];
+    int *st = lb_stage();
+    __syncthreads();  // the previous tile is done with the stage
+    const int w = threadIdx.x >> 5;
+    if (w < 2) {
+        const int s = lb_seg_warp<Team>(off, w == 0 ? j0 : j1 - 1, 0, nseg - 1);
+        if ((threadIdx.x & 31) == 0) s_rng[w] = s;
+    }
+    __syncthreads();
+    LbTile T{s_rng[0], s_rng[1], false};
+    const int cnt = T.s1 - T.s0 + 2;
+    T.staged = cnt <= kLbStage + 2;
+    if (T.staged)
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) st[i] = Team::ld(off + T.s0 + i);
+    __syncthreads();
+    return T;
+}
+
+// Segment of item j of the tile.
+template <class Team>
+__device__ __forceinline__ int lb_tile_seg(const int *off, const LbTile &T, int j) {
+    if (!T.staged) return lb_seg<Team>(off, j, T.s0, T.s1);
+    const int *st = lb_stage();
+    int lo = 0, hi = T.s1 - T.s0;
+    while (lo < hi) {
+        int m = (lo + hi + 1) >> 1;
+        if (st[m] <= j) lo = m;
+        else hi = m - 1;
+    }
+    return T.s0 + lo;
+}
+
+// off[s + 1] for a segment s of the tile.
+template <class Team>
+__device__ __forceinline__ int lb_tile_end(const int *off, const LbTile &T, int s) {
+    return T.staged ? lb_stage()[s - T.s0 + 1] : Team::ld(off + s + 1);
+}
+
+// Segmented reduction over a CSR for a visit that reads one int per item: items[j] is loaded
+// for all of the thread's slots up front (two 16-byte loads when its kLbItems slots are in range
+// and aligned); visit(seg, items[j], acc) folds it in and flush(seg, acc) ends every segment run
+// of the thread.  `init` is the identity of the combine operation.  A tile is
+// blockDim.x * kLbItems items; the team's blocks take tiles in turn.
 template <class Acc, class Visit, class Flush, class Team = GridTeam>
 __device__ __forceinline__ void lb_for_each_items(const int *off, int nseg, int total, const int *items,
                                                   Acc init, Visit visit, Flush flush, Team t = Team()) {
     static_assert(kLbItems == 8, "two int4 loads per thread");
-    __shared__ int s_rng[2];
     const int tile = blockDim.x * kLbItems;
     for (int64_t t0 = (int64_t)t.block() * tile; t0 < total; t0 += (int64_t)t.blocks() * tile) {
         const int j0 = (int)t0;
         const int j1 = (int)(t0 + tile < total ? t0 + tile : total);
-        __syncthreads();
-        if (threadIdx.x == 0) s_rng[0] = lb_seg<Team>(off, j0, 0, nseg - 1);
-        if (threadIdx.x == 32) s_rng[1] = lb_seg<Team>(off, j1 - 1, 0, nseg - 1);
-        __syncthreads();
+        const LbTile T = lb_tile<Team>(off, nseg, j0, j1);
         const int j = j0 + threadIdx.x * kLbItems;
         if (j >= j1) continue;
         const int n = j1 - j < kLbItems ? j1 - j : kLbItems;
@@ -90,8 +131,8 @@ __device__ __forceinline__ void lb_for_each_items(const int *off, int nseg, int 
 #pragma unroll
             for (int k = 0; k < kLbItems; ++k) it[k] = k < n ? Team::ld(items + j + k) : 0;
         }
-        int s = lb_seg<Team>(off, j, s_rng[0], s_rng[1]);
-        int send = Team::ld(off + s + 1);
+        int s = lb_tile_seg<Team>(off, T, j);
+        int send = lb_tile_end<Team>(off, T, s);
         Acc acc = init;
 #pragma unroll
         for (int k = 0; k < kLbItems; ++k) {
@@ -100,7 +141,7 @@ __device__ __forceinline__ void lb_for_each_items(const int *off, int nseg, int 
                     flush(s, acc);
                     acc = init;
                     ++s;
-                    send = Team::ld(off + s + 1);
+                    send = lb_tile_end<Team>(off, T, s);
                 }
                 acc = visit(s, it[k], acc);
             }
@@ -113,21 +154,17 @@ __device__ __forceinline__ void lb_for_each_items(const int *off, int nseg, int 
 // in item order (per-segment values can then be loaded once per run).
 template <class Fn, class Team = GridTeam>
 __device__ __forceinline__ void lb_runs(const int *off, int nseg, int total, Fn fn, Team t = Team()) {
-    __shared__ int s_rng[2];
     const int tile = blockDim.x * kLbItems;
     for (int64_t t0 = (int64_t)t.block() * tile; t0 < total; t0 += (int64_t)t.blocks() * tile) {
         const int j0 = (int)t0;
         const int j1 = (int)(t0 + tile < total ? t0 + tile : total);
-        __syncthreads();
-        if (threadIdx.x == 0) s_rng[0] = lb_seg<Team>(off, j0, 0, nseg - 1);
-        if (threadIdx.x == 32) s_rng[1] = lb_seg<Team>(off, j1 - 1, 0, nseg - 1);
-        __syncthreads();
+        const LbTile T = lb_tile<Team>(off, nseg, j0, j1);
         int j = j0 + threadIdx.x * kLbItems;
         if (j >= j1) continue;
         const int je = j + kLbItems < j1 ? j + kLbItems : j1;
-        int s = lb_seg<Team>(off, j, s_rng[0], s_rng[1]);
+        int s = lb_tile_seg<Team>(off, T, j);
         while (j < je) {
-            const int send = Team::ld(off + s + 1);
+            const int send = lb_tile_end<Team>(off, T, s);
             const int b = send < je ? send : je;
             if (b > j) fn(s, j, b);
             j = b > j ? b : j;
