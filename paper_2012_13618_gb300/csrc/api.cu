@@ -94,8 +94,25 @@ __global__ void k_expect(const int *d, int v, uint32_t *status) {
     if (threadIdx.x == 0 && *d != v) atomicOr(status, (uint32_t)DEV_PLAN_MISMATCH);
 }
 
-__global__ void k_cond(cudaGraphConditionalHandle h, const unsigned *flag) {
-    if (threadIdx.x == 0) cudaGraphSetConditional(h, *flag ? 1u : 0u);
+constexpr int kMaxChecks = 96;
+struct Checks {
+    int n;
+    int slot[kMaxChecks];
+    int32_t value[kMaxChecks];
+};
+
+__global__ void k_expect_all(const int32_t *base, Checks c, uint32_t *status) {
+    for (int i = threadIdx.x; i < c.n; i += blockDim.x)
+        if (base[c.slot[i]] != c.value[i]) atomicOr(status, (uint32_t)DEV_PLAN_MISMATCH);
+}
+
+// Per-level size slots in the small scratch, after the selection state.
+constexpr int kSlotBase = 6144;   // int index (24 KB into the 64 KB scratch)
+constexpr int kSlotLevels = 2048;
+
+int32_t *level_sizes(bipart_graph *g, int idx) {
+    int32_t *small = g->w.small.as<int32_t>();
+    return idx < kSlotLevels ? small + kSlotBase + 3 * idx : small + 8;
 }
 
 int32_t read_i32(bipart_graph *g, const int32_t *d) {
@@ -103,8 +120,15 @@ int32_t read_i32(bipart_graph *g, const int32_t *d) {
     if (ex.capturing) {
         if (ex.pos >= ex.sizes.size()) throw Fail{BIPART_ERR_CUDA, "plan capture ran past its recorded sizes"};
         int32_t v = ex.sizes[ex.pos++];
-        k_expect<<<1, 32, 0, g->stream>>>(d, v, dev_status(g));
-        BP_LAUNCH();
+        const int32_t *small = g->w.small.as<int32_t>();
+        const ptrdiff_t off = d - small;
+        if (off >= kSlotBase && off < kSlotBase + 3 * kSlotLevels) {
+            ex.checks.emplace_back((int)off, v);
+        } else {
+            k_expect<<<1, 32, 0, g->stream>>>(d, v, dev_status(g));
+            BP_LAUNCH();
+            ex.check_kernels++;
+        }
         return v;
     }
     BP_CUDA(cudaMemcpyAsync(g->w.host_small, d, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
@@ -115,14 +139,39 @@ int32_t read_i32(bipart_graph *g, const int32_t *d) {
     return v;
 }
 
+void flush_checks(bipart_graph *g) {
+    Exec &ex = g->ex;
+    for (size_t i = 0; i < ex.checks.size(); i += kMaxChecks) {
+        Checks c{};
+        c.n = (int)std::min<size_t>(kMaxChecks, ex.checks.size() - i);
+        for (int k = 0; k < c.n; ++k) {
+            c.slot[k] = ex.checks[i + k].first;
+            c.value[k] = ex.checks[i + k].second;
+        }
+        k_expect_all<<<1, 128, 0, g->stream>>>(g->w.small.as<int32_t>(), c, dev_status(g));
+        BP_LAUNCH();
+        ex.check_kernels++;
+    }
+    ex.checks.clear();
+}
+
 unsigned read_flag(bipart_graph *g, const unsigned *d) {
     BP_CUDA(cudaMemcpyAsync(g->w.host_small, d, sizeof(unsigned), cudaMemcpyDeviceToHost, g->stream));
     sync(g);
-    if (g->ex.recording) g->ex.loop_launches++;  // one condition kernel per evaluation on replay
     return g->w.host_small[0];
 }
 
-CondNode cond_begin(bipart_graph *g, const unsigned *d_flag, bool loop) {
+cudaGraphConditionalHandle cond_handle(bipart_graph *g) {
+    if (!g->ex.capturing) return 0;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph;
+    BP_CUDA(cudaStreamGetCaptureInfo(g->stream, &cs, nullptr, &graph, nullptr, nullptr, nullptr));
+    cudaGraphConditionalHandle h;
+    BP_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault));
+    return h;
+}
+
+CondNode cond_begin(bipart_graph *g, cudaGraphConditionalHandle h, bool loop) {
     Exec &ex = g->ex;
     const int depth = ex.depth + 1;
     if (depth >= 4) throw Fail{BIPART_ERR_CUDA, "conditional nesting too deep"};
@@ -132,11 +181,6 @@ CondNode cond_begin(bipart_graph *g, const unsigned *d_flag, bool loop) {
     cudaGraph_t graph;
     const cudaGraphNode_t *deps = nullptr;
     size_t nd = 0;
-    BP_CUDA(cudaStreamGetCaptureInfo(outer, &cs, nullptr, &graph, &deps, nullptr, &nd));
-    cudaGraphConditionalHandle h;
-    BP_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault));
-    k_cond<<<1, 32, 0, outer>>>(h, d_flag);  // initial value of the condition
-    BP_LAUNCH();
     BP_CUDA(cudaStreamGetCaptureInfo(outer, &cs, nullptr, &graph, &deps, nullptr, &nd));
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
@@ -153,12 +197,8 @@ CondNode cond_begin(bipart_graph *g, const unsigned *d_flag, bool loop) {
     return CondNode{h, node, outer};
 }
 
-void cond_end(bipart_graph *g, const CondNode &c, const unsigned *d_flag, bool loop) {
+void cond_end(bipart_graph *g, const CondNode &c) {
     Exec &ex = g->ex;
-    if (loop) {
-        k_cond<<<1, 32, 0, g->stream>>>(c.h, d_flag);  // re-evaluated after every iteration
-        BP_LAUNCH();
-    }
     cudaGraph_t body = nullptr;
     BP_CUDA(cudaStreamEndCapture(g->stream, &body));
     ex.depth--;
@@ -429,12 +469,13 @@ void bisect_body(bipart_graph *g, Level &L0, const Params &p, int64_t W, uint8_t
         size_t idx = levels.size() - 1;
         if (g->lev.size() <= idx) g->lev.emplace_back(new Level);
         Level &c = *g->lev[idx];
-        coarsen_level(g, f, c, p.policy);
+        coarsen_level(g, f, c, p.policy, level_sizes(g, (int)idx));
         if (c.N == f.N) break;
         levels.push_back(&c);
     }
     if (nlev) *nlev = (int)levels.size();
     uncoarsen(g, levels, balance_limit(W, p.eps), p.iters, d_side);
+    if (g->ex.capturing) flush_checks(g);
 }
 
 int read_bisect_status(bipart_graph *g) {
@@ -455,6 +496,8 @@ void capture_plan(bipart_graph *g, const Params &p, uint8_t *d_side, int nlev, i
     ex.capturing = true;
     ex.pos = 0;
     ex.depth = 0;
+    ex.checks.clear();
+    ex.check_kernels = 0;
     tl_capturing = true;
     cudaStream_t main = g->stream;
     cudaGraph_t graph = nullptr;
@@ -494,7 +537,7 @@ void capture_plan(bipart_graph *g, const Params &p, uint8_t *d_side, int nlev, i
     pl.nlev = nlev;
     pl.gen = g->gen;
     pl.prof_epoch = prof_epoch();
-    pl.launches = kernels + ex.loop_launches + (int64_t)ex.sizes.size();
+    pl.launches = kernels + ex.check_kernels;
 }
 
 bool same_params(const Params &a, const Params &b) {
@@ -531,7 +574,6 @@ int bisect_top(bipart_graph *g, const Params &p, uint8_t *d_side, int *nlev) {
     }
     ex.recording = true;
     ex.sizes.clear();
-    ex.loop_launches = 0;
     const int64_t k0 = bipart_kernel_launches();
     try {
         bisect_body(g, g->L0, p, g->total_node_weight, d_side, nlev);

@@ -240,8 +240,9 @@ void seg_unique(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const in
 
 // Sorted-unique of every hyperedge's (mapped) pins into the coarse CSR of `c`.
 // Sets c.E and c.P.  `map` null means identity (level-0 normalisation).
+// sizes: two device ints receiving {E', P'}.
 void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int *pins,
-              const int *hw, const int *map, Level &c, int *deg, bool counters_zero) {
+              const int *hw, const int *map, Level &c, int *deg, bool counters_zero, int32_t *sizes) {
     cudaStream_t s = g->stream;
     Work &w = g->w;
     int *scratch = (int *)w.p_a.ensure(sizeof(int) * (size_t)std::max(P, 1), s);
@@ -255,7 +256,7 @@ void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int 
     if (!unit) c.b_hw.ensure(sizeof(int) * (size_t)std::max(E, 1), s);
     c.unit_hw = unit;
     if (E > 0) {
-        CompactOut out{E, hw, c.hoff(), unit ? nullptr : c.b_hw.as<int>(), emap, small + 2};
+        CompactOut out{E, hw, c.hoff(), unit ? nullptr : c.b_hw.as<int>(), emap, sizes};
         {
             ProfScope ps("contract_offsets", 16.0 * E, s);
             scan(E, CompactIn{cnt}, out, w.scan.ensure_zero(scan_state_bytes(E), s), dev_status(g), s);
@@ -273,8 +274,8 @@ void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int 
     } else {
         BP_CUDA(cudaMemsetAsync(c.hoff(), 0, sizeof(int), s));
     }
-    c.E = E > 0 ? read_i32(g, small + 2) : 0;
-    c.P = E > 0 ? read_i32(g, small + 3) : 0;
+    c.E = E > 0 ? read_i32(g, sizes) : 0;
+    c.P = E > 0 ? read_i32(g, sizes + 1) : 0;
 }
 
 }  // namespace
@@ -330,7 +331,8 @@ void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t
         P = (int32_t)g->w.host_small[0];
     }
     L.N = N;
-    contract(g, E, P, d_hoff, d_pins, d_hw, nullptr, L, degree_counters(g, N), false);
+    contract(g, E, P, d_hoff, d_pins, d_hw, nullptr, L, degree_counters(g, N), false,
+             g->w.small.as<int32_t>() + 2);
     L.b_nw.ensure(sizeof(int) * (size_t)std::max(N, 1), s);
     if (d_nw) {
         BP_CUDA(cudaMemcpyAsync(L.nw(), d_nw, sizeof(int) * (size_t)N, cudaMemcpyDeviceToDevice, s));
@@ -343,7 +345,7 @@ void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t
     L.b_match.ensure(sizeof(int) * (size_t)std::max(N, 1), s);
 }
 
-void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy) {
+void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *sizes) {
     cudaStream_t s = g->stream;
     Work &w = g->w;
     const int N = f.N, E = f.E;
@@ -390,18 +392,18 @@ void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy) {
         }
         {
             ProfScope ps("renumber", 12.0 * N, s);
-            scan(N, RenumIn{grp, rep}, RenumOut{N, grp, f.cmap(), gcid, small + 4},
+            scan(N, RenumIn{grp, rep}, RenumOut{N, grp, f.cmap(), gcid, sizes},
                  w.scan.ensure_zero(scan_state_bytes(N), s), dev_status(g), s);
         }
     }
-    const int Nc = N > 0 ? read_i32(g, small + 4) : 0;
+    const int Nc = N > 0 ? read_i32(g, sizes) : 0;
     c.N = Nc;
     if (N > 0) {
         ProfScope ps("cmap", 24.0 * N, s);
         k_cmap<<<grid_for(N), kBlock, 0, s>>>(N, grp, gcid, f.nw(), f.cmap(), c.nw());
         BP_LAUNCH();
     }
-    contract(g, E, f.P, f.hoff(), f.pins(), f.hw(), f.cmap(), c, deg, N > 0);
+    contract(g, E, f.P, f.hoff(), f.pins(), f.hw(), f.cmap(), c, deg, N > 0, sizes + 1);
     build_incidence(g, c);
     c.b_cmap.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);
     c.b_match.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);

@@ -135,7 +135,8 @@ struct Exec {
     size_t pos = 0;
     cudaStream_t body[4] = {};   // capture streams of nested conditional bodies
     int depth = 0;
-    int64_t loop_launches = 0;   // helper kernels run per replay (conditions, size checks)
+    int64_t check_kernels = 0;   // size-check kernels per replay
+    std::vector<std::pair<int, int32_t>> checks;  // deferred (slot index, recorded value)
     // the last eager top-level bisection, ready to be captured
     bool rec_valid = false;
     Params rec_params;
@@ -191,7 +192,8 @@ namespace bp {
 void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t *d_hoff,
                   const int32_t *d_pins, const int32_t *d_nw, const int32_t *d_hw);
 // Algorithm 1 + 2 on `f`, producing `c` (sizes read back to the host).
-void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy);
+// sizes: level_sizes() slots receiving {N', E', P'}.
+void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *sizes);
 // Node -> hyperedge incidence of a level whose hyperedge CSR is complete and whose node degrees
 // were counted into degree_counters(g, N) while its pins were written.
 void build_incidence(bipart_graph *g, Level &L);
@@ -255,24 +257,38 @@ void sync(bipart_graph *g);
 
 // Scalar produced on the device that the host needs (a level size).  Eager: copied back (and
 // recorded when recording).  Capturing: the recorded value is returned and a device check
-// against the live value is added to the graph (a mismatch invalidates the plan).
+// against the live value is added to the graph (a mismatch invalidates the plan): values in the
+// per-level size slots are checked together by flush_checks() at the end of the capture, others
+// at once.
 int32_t read_i32(bipart_graph *g, const int32_t *d);
 // Reads a device flag in eager mode.
 unsigned read_flag(bipart_graph *g, const unsigned *d);
 
-// Conditional-node helpers used while capturing (api.cu).
+// Three device ints {N', E', P'} for coarsening step `idx` of a bisection: distinct slots per
+// level (so their checks can wait until the end of a captured bisection), or one shared slot past
+// the slot capacity.
+int32_t *level_sizes(bipart_graph *g, int idx);
+// Adds the deferred size checks of a capture to the graph (one kernel).
+void flush_checks(bipart_graph *g);
+
+// Conditional nodes.  The kernel that computes a condition's flag also sets the node's value on
+// the device (cudaGraphSetConditional), so no helper kernel runs per evaluation: cond_handle()
+// gives the handle to pass to that kernel (0 when not capturing), and the loop body's last
+// kernel sets it again for the next iteration.
+cudaGraphConditionalHandle cond_handle(bipart_graph *g);
 struct CondNode {
     cudaGraphConditionalHandle h;
     cudaGraphNode_t node;
     cudaStream_t outer;
 };
-CondNode cond_begin(bipart_graph *g, const unsigned *d_flag, bool loop);
-void cond_end(bipart_graph *g, const CondNode &c, const unsigned *d_flag, bool loop);
+CondNode cond_begin(bipart_graph *g, cudaGraphConditionalHandle h, bool loop);
+void cond_end(bipart_graph *g, const CondNode &c);
 
-// Runs body() while *d_flag != 0 (the body must update the flag).  Eager: the host reads the flag
-// before every iteration; capturing: a WHILE conditional node.
+// Runs body() while *d_flag != 0 (the body must update the flag, and set h when capturing).
+// Eager: the host reads the flag before every iteration; capturing: a WHILE conditional node.
 template <class Body>
-void device_while(bipart_graph *g, const unsigned *d_flag, int64_t max_iter, Body body) {
+void device_while(bipart_graph *g, cudaGraphConditionalHandle h, const unsigned *d_flag,
+                  int64_t max_iter, Body body) {
     if (!g->ex.capturing) {
         for (int64_t it = 0;; ++it) {
             if (!read_flag(g, d_flag)) break;
@@ -281,21 +297,22 @@ void device_while(bipart_graph *g, const unsigned *d_flag, int64_t max_iter, Bod
         }
         return;
     }
-    CondNode c = cond_begin(g, d_flag, true);
+    CondNode c = cond_begin(g, h, true);
     body();
-    cond_end(g, c, d_flag, true);
+    cond_end(g, c);
 }
 
-// Runs body() once if *d_flag != 0.  Eager: host check; capturing: an IF conditional node.
+// Runs body() once if *d_flag != 0.  Eager: host check; capturing: an IF conditional node whose
+// value the flag's producer set through h.
 template <class Body>
-void device_if(bipart_graph *g, const unsigned *d_flag, Body body) {
+void device_if(bipart_graph *g, cudaGraphConditionalHandle h, const unsigned *d_flag, Body body) {
     if (!g->ex.capturing) {
         if (read_flag(g, d_flag)) body();
         return;
     }
-    CondNode c = cond_begin(g, d_flag, false);
+    CondNode c = cond_begin(g, h, false);
     body();
-    cond_end(g, c, d_flag, false);
+    cond_end(g, c);
 }
 
 }  // namespace bp

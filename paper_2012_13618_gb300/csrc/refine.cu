@@ -34,6 +34,11 @@ inline int grid_for(int64_t n, int per_block = kBlock, int cap = 152 * 16) {
     return (int)std::min<int64_t>(b, cap);
 }
 
+// Selection passes over up to this many nodes run as one block.
+constexpr int kSelOneBlock = 8192;
+
+inline int sel_grid(int N) { return N <= kSelOneBlock ? 1 : grid_for(N); }
+
 }  // namespace
 
 // Grid kernels: one launch per phase (device code in refine_dev.cuh).
@@ -68,16 +73,33 @@ __device__ __forceinline__ void take_hist(RState *st, unsigned (*h)[kHistBins]) 
 }
 
 // Fast selection pass: clamped-gain histogram, then (last block) the per-group threshold.  The
-// rebalancing list is emptied for the application scan that follows.
+// rebalancing list is emptied for the application scan that follows.  One block (small levels)
+// keeps its histogram in shared memory and also runs the exact radix passes when needed, leaving
+// st->slow clear; a grid leaves st->slow for the exact passes and sets the IF node's value `h`.
 __global__ void __launch_bounds__(kBlock)
 k_sel(int N, int kind, long long s, const int *__restrict__ gain, const uint8_t *__restrict__ side,
-      const int *__restrict__ nw, RState *st) {
+      const int *__restrict__ nw, RState *st, cudaGraphConditionalHandle h_slow, uint32_t *status) {
     __shared__ unsigned h[2][kHistBins];
-    d_sel_hist(GridTeam(), N, kind, gain, side, nw, st, h);
-    if (!last_block(&st->arrived)) return;
-    take_hist(st, h);
+    const bool one = gridDim.x == 1;
+    d_sel_hist(GridTeam(), N, kind, gain, side, nw, st, h, !one);
+    if (!one) {
+        if (!last_block(&st->arrived)) return;
+        take_hist(st, h);
+    }
     d_sel_find(kind, s, st, h);
     if (threadIdx.x == 0) st->list_count = 0;
+    __syncthreads();
+    if (one) {
+        if (*(volatile unsigned *)&st->slow) {
+            for (int pass = 0; pass < 3; ++pass) {
+                d_sel_hist_exact(GridTeam(), N, kind, gain, side, nw, st, h, false);
+                d_sel_find_exact(st, status, h);
+            }
+            if (threadIdx.x == 0) st->slow = 0;
+        }
+    } else if (h_slow && threadIdx.x == 0) {
+        cudaGraphSetConditional(h_slow, st->slow ? 1u : 0u);
+    }
 }
 
 // One digit of the exact radix select: histogram, then (last block) the narrowed range.
@@ -85,9 +107,12 @@ __global__ void __launch_bounds__(kBlock)
 k_sel_exact(int N, int kind, const int *__restrict__ gain, const uint8_t *__restrict__ side,
             const int *__restrict__ nw, RState *st, uint32_t *status) {
     __shared__ unsigned h[2][kHistBins];
-    d_sel_hist_exact(GridTeam(), N, kind, gain, side, nw, st, h);
-    if (!last_block(&st->arrived)) return;
-    take_hist(st, h);
+    const bool one = gridDim.x == 1;
+    d_sel_hist_exact(GridTeam(), N, kind, gain, side, nw, st, h, !one);
+    if (!one) {
+        if (!last_block(&st->arrived)) return;
+        take_hist(st, h);
+    }
     d_sel_find_exact(st, status, h);
 }
 
@@ -102,13 +127,17 @@ k_side_weights(int N, const uint8_t *__restrict__ side, const int *__restrict__ 
     }
 }
 
-__global__ void k_initial_cond(RState *st, long long max_rounds, uint32_t *status, int first) {
+// Loop conditions; they also set the WHILE node's value `h` when the loop runs in a graph.
+__global__ void k_initial_cond(RState *st, long long max_rounds, uint32_t *status, int first,
+                               cudaGraphConditionalHandle h) {
     d_initial_cond(st, max_rounds, status, first != 0);
+    if (h && threadIdx.x == 0) cudaGraphSetConditional(h, st->flag ? 1u : 0u);
 }
 
 __global__ void k_rebal_cond(RState *st, long long limit, long long max_rounds, uint32_t *status,
-                             int first) {
+                             int first, cudaGraphConditionalHandle h) {
     d_rebal_cond(st, limit, max_rounds, status, first != 0);
+    if (h && threadIdx.x == 0) cudaGraphSetConditional(h, st->flag ? 1u : 0u);
 }
 
 __global__ void __launch_bounds__(1024)
@@ -184,14 +213,16 @@ void select_apply(bipart_graph *g, Level &L, int kind, long long sq, const int *
                   uint8_t *side, int *list) {
     cudaStream_t s = g->stream;
     RState *st = rstate(g);
+    const bool one = sel_grid(L.N) == 1;  // exact passes, if any, run inside k_sel
+    const cudaGraphConditionalHandle h = one ? 0 : cond_handle(g);
     {
         ProfScope ps("select_hist", 9.0 * L.N, s);
-        k_sel<<<grid_for(L.N), kBlock, 0, s>>>(L.N, kind, sq, gain, side, L.nw(), st);
+        k_sel<<<sel_grid(L.N), kBlock, 0, s>>>(L.N, kind, sq, gain, side, L.nw(), st, h, dev_status(g));
         BP_LAUNCH();
     }
-    device_if(g, &st->slow, [&]() {
+    if (!one) device_if(g, h, &st->slow, [&]() {
         for (int pass = 0; pass < 3; ++pass) {
-            k_sel_exact<<<grid_for(L.N), kBlock, 0, g->stream>>>(L.N, kind, gain, side, L.nw(), st,
+            k_sel_exact<<<sel_grid(L.N), kBlock, 0, g->stream>>>(L.N, kind, gain, side, L.nw(), st,
                                                                  dev_status(g));
             BP_LAUNCH();
         }
@@ -217,12 +248,13 @@ void initial_partition(bipart_graph *g, Level &L, uint8_t *side, int *gain) {
     const long long sq = ceil_sqrt64(L.N);
     BP_CUDA(cudaMemsetAsync(side, 1, (size_t)L.N, s));
     side_weights(g, L, side);
-    k_initial_cond<<<1, 32, 0, s>>>(st, (long long)L.N + 1, dev_status(g), 1);
+    const cudaGraphConditionalHandle h = cond_handle(g);
+    k_initial_cond<<<1, 32, 0, s>>>(st, (long long)L.N + 1, dev_status(g), 1, h);
     BP_LAUNCH();
-    device_while(g, &st->flag, (int64_t)L.N + 2, [&]() {
+    device_while(g, h, &st->flag, (int64_t)L.N + 2, [&]() {
         compute_gains(g, L, side, gain);
         select_apply(g, L, SEL_INITIAL, sq, gain, side, nullptr);
-        k_initial_cond<<<1, 32, 0, g->stream>>>(st, (long long)L.N + 1, dev_status(g), 0);
+        k_initial_cond<<<1, 32, 0, g->stream>>>(st, (long long)L.N + 1, dev_status(g), 0, h);
         BP_LAUNCH();
     });
 }
@@ -244,14 +276,15 @@ void rebalance(bipart_graph *g, Level &L, uint8_t *side, int *gain, int64_t limi
     while (S < sq) S <<= 1;
     const size_t smem = sizeof(unsigned long long) * (size_t)S;
     side_weights(g, L, side);
-    k_rebal_cond<<<1, 32, 0, s>>>(st, (long long)limit, (long long)L.N + 1, dev_status(g), 1);
+    const cudaGraphConditionalHandle h = cond_handle(g);
+    k_rebal_cond<<<1, 32, 0, s>>>(st, (long long)limit, (long long)L.N + 1, dev_status(g), 1, h);
     BP_LAUNCH();
-    device_while(g, &st->flag, (int64_t)L.N + 2, [&]() {
+    device_while(g, h, &st->flag, (int64_t)L.N + 2, [&]() {
         compute_gains(g, L, side, gain);
         select_apply(g, L, SEL_REBAL, sq, gain, side, list);
         k_rebal_move<<<1, 1024, smem, g->stream>>>(gain, side, L.nw(), list, st, sq);
         BP_LAUNCH();
-        k_rebal_cond<<<1, 32, 0, g->stream>>>(st, (long long)limit, (long long)L.N + 1, dev_status(g), 0);
+        k_rebal_cond<<<1, 32, 0, g->stream>>>(st, (long long)limit, (long long)L.N + 1, dev_status(g), 0, h);
         BP_LAUNCH();
     });
 }

@@ -100,9 +100,10 @@ __device__ void d_node_gain(Team t, int N, int P, const int *noff, const int *na
 
 // ------------------------------------------------------------------------ selection
 // Fast pass: histogram of clamped gains per group (h: 2 * kHistBins shared counters).
+// Without `flush` the histogram stays in h (a one-block pass that searches it itself).
 template <class Team>
 __device__ void d_sel_hist(Team t, int N, int kind, const int *gain, const uint8_t *side,
-                           const int *nw, RState *st, unsigned (*h)[kHistBins]) {
+                           const int *nw, RState *st, unsigned (*h)[kHistBins], bool flush = true) {
     for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
     for (int v = t.rank(); v < N; v += t.size()) {
@@ -114,6 +115,7 @@ __device__ void d_sel_hist(Team t, int N, int kind, const int *gain, const uint8
         atomicAdd(&h[grp][b], 1u);
     }
     __syncthreads();
+    if (!flush) return;
     for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) {
         unsigned c = (&h[0][0])[i];
         if (c) atomicAdd(&(&st->hist[0][0])[i], c);
@@ -212,7 +214,8 @@ __device__ inline void d_sel_find(int kind, long long s, RState *st, const unsig
 // Exact path: histogram of keys in [base, top) by (key - base) >> shift.
 template <class Team>
 __device__ void d_sel_hist_exact(Team t, int N, int kind, const int *gain, const uint8_t *side,
-                                 const int *nw, RState *st, unsigned (*h)[kHistBins]) {
+                                 const int *nw, RState *st, unsigned (*h)[kHistBins],
+                                 bool flush = true) {
     __shared__ unsigned s_base[2], s_shift[2], s_on[2];
     __shared__ unsigned long long s_top[2];
     if (threadIdx.x < 2) {
@@ -233,6 +236,7 @@ __device__ void d_sel_hist_exact(Team t, int N, int kind, const int *gain, const
         atomicAdd(&h[grp][(k - s_base[grp]) >> s_shift[grp]], 1u);
     }
     __syncthreads();
+    if (!flush) return;
     for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) {
         unsigned c = (&h[0][0])[i];
         if (c) atomicAdd(&(&st->hist[0][0])[i], c);

@@ -60,39 +60,55 @@ k_scan(int64_t n, In in, Out out, unsigned long long *state, uint32_t *status) {
     uint64_t total;
     uint64_t excl = block_exclusive_scan<uint64_t>(sum, red, &total);
 
-    if (threadIdx.x == 0 && solo) {
-        s_prefix = 0;
-        s_last = 0;
-    } else if (threadIdx.x == 0) {
+    if (solo) {
+        if (threadIdx.x == 0) {
+            s_prefix = 0;
+            s_last = 0;
+        }
+    } else if (threadIdx.x < 32) {
+        // warp 0 looks back over its predecessors 32 at a time (lane l reads tile j - l): it adds
+        // aggregates up to the nearest tile that already holds its inclusive prefix
+        const int lane = threadIdx.x;
         uint64_t prefix = 0;
         if (tile == 0) {
-            atomicExch(&tiles[0], (unsigned long long)(kFlagPre | (total & kScanValMask)));
+            if (lane == 0) atomicExch(&tiles[0], (unsigned long long)(kFlagPre | (total & kScanValMask)));
         } else {
-            atomicExch(&tiles[tile], (unsigned long long)(kFlagAgg | (total & kScanValMask)));
+            if (lane == 0) atomicExch(&tiles[tile], (unsigned long long)(kFlagAgg | (total & kScanValMask)));
             int64_t j = tile - 1;
-            while (j >= 0) {
-                uint64_t s = 0;
-                int spins = 0;
-                for (;;) {
-                    s = *((volatile unsigned long long *)&tiles[j]);
-                    if ((s >> 62) != 0) break;
-                    if (++spins > kSpinLimit) break;
-                    if (spins > 64) __nanosleep(64);
+            for (;;) {
+                const int64_t idx = j - lane;
+                uint64_t st = kFlagPre;  // before tile 0: an inclusive prefix of 0
+                if (idx >= 0) {
+                    int spins = 0;
+                    for (;;) {
+                        st = *((volatile unsigned long long *)&tiles[idx]);
+                        if ((st >> 62) != 0) break;
+                        if (++spins > kSpinLimit) break;
+                        if (spins > 64) __nanosleep(64);
+                    }
                 }
-                if ((s >> 62) == 0) {  // predecessor never published: give up, flag the error
-                    record_error(status, DEV_TIMEOUT);
+                if (__ballot_sync(0xffffffffu, (st >> 62) == 0)) {  // a predecessor never published
+                    if (lane == 0) record_error(status, DEV_TIMEOUT);
                     break;
                 }
-                prefix += s & kScanValMask;
-                if ((s >> 62) == 2) break;
-                --j;
+                const unsigned inc = __ballot_sync(0xffffffffu, (st >> 62) == 2);
+                const int stop = inc ? __ffs(inc) - 1 : 31;  // nearest inclusive prefix
+                uint64_t v = lane <= stop ? (st & kScanValMask) : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                prefix += v;
+                if (inc) break;
+                j -= 32;
             }
-            atomicExch(&tiles[tile], (unsigned long long)(kFlagPre | ((prefix + total) & kScanValMask)));
+            if (lane == 0)
+                atomicExch(&tiles[tile], (unsigned long long)(kFlagPre | ((prefix + total) & kScanValMask)));
         }
-        s_prefix = prefix;
-        __threadfence();
-        s_last = atomicAdd(finished, 1ull) == (unsigned long long)gridDim.x - 1;
-        if (s_last) __threadfence();
+        if (lane == 0) {
+            s_prefix = prefix;
+            __threadfence();
+            s_last = atomicAdd(finished, 1ull) == (unsigned long long)gridDim.x - 1;
+            if (s_last) __threadfence();
+        }
     }
     __syncthreads();
     if (s_last) {
