@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "lb.cuh"
 #include "scan.cuh"
 
 namespace bp {
@@ -334,11 +335,12 @@ struct SubEdgeIn {
 struct SubEdgeOut {
     int64_t n;
     const int *hw;
-    int *hoff_out, *hw_out, *emap, *sizes;
+    int *hoff_out, *hw_out, *emap, *sizes, *ts;
     __device__ void operator()(int64_t e, uint64_t pre, uint64_t val) const {
         if (val) {
             int ei = (int)(pre >> 31);
             hoff_out[ei] = (int)(pre & 0x7fffffffu);
+            lb_mark_tiles(ts, ei, (int64_t)(pre & 0x7fffffffu), (int64_t)(val & 0x7fffffffu));
             if (hw_out) hw_out[ei] = hw[e];
             emap[e] = ei;
         } else {
@@ -430,13 +432,14 @@ void extract_subgraph(bipart_graph *g, const int *d_part, int j) {
     S.unit_hw = L.unit_hw;
     S.b_hoff.ensure(sizeof(int) * ((size_t)L.E + 1), s);
     S.b_pins.ensure(sizeof(int) * (size_t)std::max(L.P, 1), s);
+    S.b_tsh.ensure(sizeof(int) * ((size_t)L.P / kTsGran + 2), s);
     if (!S.unit_hw) S.b_hw.ensure(sizeof(int) * (size_t)std::max(L.E, 1), s);
     int *deg = degree_counters(g, L.N);  // subgraph degrees, counted while its pins are written
     if (L.E > 0) {
         int gw = grid_for((int64_t)(L.E + 31) / 32 * 32);
         k_sub_count<<<gw, kBlock, 0, s>>>(L.E, L.hoff(), L.pins(), loc, cnt);
         BP_LAUNCH();
-        scan(L.E, SubEdgeIn{cnt}, SubEdgeOut{L.E, L.hw(), S.hoff(), S.unit_hw ? nullptr : S.b_hw.as<int>(), emap, small + 2},
+        scan(L.E, SubEdgeIn{cnt}, SubEdgeOut{L.E, L.hw(), S.hoff(), S.unit_hw ? nullptr : S.b_hw.as<int>(), emap, small + 2, S.tsh()},
              w.scan.ensure_zero(scan_state_bytes(L.E), s), dev_status(g), s);
         k_sub_copy<<<gw, kBlock, 0, s>>>(L.E, L.hoff(), L.pins(), loc, emap, S.hoff(), S.pins(), deg);
         BP_LAUNCH();

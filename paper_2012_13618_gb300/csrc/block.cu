@@ -136,7 +136,7 @@ __device__ bool blk_contract(Ctx &x, int E, int P, const int *hoff, const int *p
     c.hw = hw ? x.ar.take<int>((size_t)E) : nullptr;
     if (x.ar.overflow) return false;
     if (E > 0) {
-        blk_scan(E, CompactIn{cnt}, CompactOut{E, hw, c.hoff, c.hw, emap, counters + 2});
+        blk_scan(E, CompactIn{cnt}, CompactOut{E, hw, c.hoff, c.hw, emap, counters + 2, nullptr});
     } else if (threadIdx.x == 0) {
         c.hoff[0] = 0;
         counters[2] = counters[3] = 0;
@@ -160,7 +160,7 @@ __device__ bool blk_incidence(Ctx &x, DLevel &c) {
     c.cmap = x.ar.take<int>((size_t)c.N);
     c.match = x.ar.take<int>((size_t)c.N);
     if (x.ar.overflow) return false;
-    if (c.N > 0) blk_scan(c.N, DegIn{x.n_a}, DegOut{c.N, c.noff, x.n_b});
+    if (c.N > 0) blk_scan(c.N, DegIn{x.n_a}, DegOut{c.N, c.noff, x.n_b, nullptr});
     else if (threadIdx.x == 0) c.noff[0] = 0;
     __syncthreads();
     if (c.P > 0) d_fill_adj(x.t, c.E, c.P, c.hoff, c.pins, x.n_b, c.nadj);

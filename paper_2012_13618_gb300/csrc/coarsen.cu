@@ -69,8 +69,9 @@ k_seg_big(const int *__restrict__ hoff, const int *__restrict__ pins, const int 
 __global__ void __launch_bounds__(kLbBlock)
 k_seg_copy(int E, int P, const int *__restrict__ hoff, const int *__restrict__ scratch,
            const int *__restrict__ cnt, const int *__restrict__ emap,
-           const int *__restrict__ hoff_out, int *__restrict__ pins_out, int *__restrict__ deg) {
-    d_seg_copy(GridTeam(), E, P, hoff, scratch, cnt, emap, hoff_out, pins_out, deg);
+           const int *__restrict__ hoff_out, int *__restrict__ pins_out, int *__restrict__ deg,
+           const int *__restrict__ ts) {
+    d_seg_copy(GridTeam(), E, P, hoff, scratch, cnt, emap, hoff_out, pins_out, deg, ts);
 }
 
 // Coarse levels with at most kPrivNodes nodes count degrees and claim incidence positions in
@@ -83,7 +84,8 @@ constexpr int kPrivBlock = 1024;  // large blocks: clearing and merging N counte
 __global__ void __launch_bounds__(kPrivBlock)
 k_seg_copy_priv(int E, int P, int N, const int *__restrict__ hoff, const int *__restrict__ scratch,
                 const int *__restrict__ cnt, const int *__restrict__ emap,
-                const int *__restrict__ hoff_out, int *__restrict__ pins_out, int *__restrict__ deg) {
+                const int *__restrict__ hoff_out, int *__restrict__ pins_out, int *__restrict__ deg,
+                const int *__restrict__ ts) {
     extern __shared__ int s_cnt[];
     for (int v = threadIdx.x; v < N; v += blockDim.x) s_cnt[v] = 0;
     __syncthreads();
@@ -100,7 +102,7 @@ k_seg_copy_priv(int E, int P, int N, const int *__restrict__ hoff, const int *__
                 atomicAdd(s_cnt + v, 1);
             }
         },
-        GridTeam());
+        GridTeam(), ts);
     __syncthreads();
     for (int v = threadIdx.x; v < N; v += blockDim.x) {
         const int c = s_cnt[v];
@@ -113,7 +115,7 @@ k_seg_copy_priv(int E, int P, int N, const int *__restrict__ hoff, const int *__
 // passes visit the same tiles.
 __global__ void __launch_bounds__(kPrivBlock)
 k_fill_adj_priv(int E, int P, int N, const int *__restrict__ hoff, const int *__restrict__ pins,
-                int *__restrict__ cursor, int *__restrict__ nadj) {
+                int *__restrict__ cursor, int *__restrict__ nadj, const int *__restrict__ ts) {
     extern __shared__ int s_cnt[];
     for (int v = threadIdx.x; v < N; v += blockDim.x) s_cnt[v] = 0;
     __syncthreads();
@@ -128,7 +130,7 @@ k_fill_adj_priv(int E, int P, int N, const int *__restrict__ hoff, const int *__
         if (c) s_cnt[v] = atomicAdd(cursor + v, c);
     }
     __syncthreads();
-    d_fill_adj_with(GridTeam(), E, P, hoff, pins, nadj, [&](int v) { return atomicAdd(s_cnt + v, 1); });
+    d_fill_adj_with(GridTeam(), E, P, hoff, pins, nadj, [&](int v) { return atomicAdd(s_cnt + v, 1); }, ts);
 }
 
 // Blocks for the private-counter kernels: one tile of kPrivBlock * kLbItems pins each, at most
@@ -144,8 +146,8 @@ __global__ void k_fill(int n, int val, int *__restrict__ a) {
 
 __global__ void __launch_bounds__(kLbBlock)
 k_fill_adj(int E, int P, const int *__restrict__ hoff, const int *__restrict__ pins,
-           int *__restrict__ cursor, int *__restrict__ nadj) {
-    d_fill_adj(GridTeam(), E, P, hoff, pins, cursor, nadj);
+           int *__restrict__ cursor, int *__restrict__ nadj, const int *__restrict__ ts) {
+    d_fill_adj(GridTeam(), E, P, hoff, pins, cursor, nadj, ts);
 }
 
 // Start of a level: hyperedge keys, and every per-hyperedge / per-node accumulator of the
@@ -170,8 +172,9 @@ __global__ void k_level_init(int E, int N, int policy, const int *__restrict__ h
 
 __global__ void __launch_bounds__(kLbBlock)
 k_match_min(int N, int P, const int *__restrict__ noff, const int *__restrict__ nadj,
-            const unsigned long long *__restrict__ hkey, unsigned long long *__restrict__ nkey) {
-    d_match_min(GridTeam(), N, P, noff, nadj, hkey, nkey);
+            const unsigned long long *__restrict__ hkey, unsigned long long *__restrict__ nkey,
+            const int *__restrict__ ts) {
+    d_match_min(GridTeam(), N, P, noff, nadj, hkey, nkey, ts);
 }
 
 __global__ void __launch_bounds__(kBlock)
@@ -183,8 +186,9 @@ k_match_set(int N, const unsigned long long *__restrict__ nkey, const int *__res
 __global__ void __launch_bounds__(kLbBlock)
 k_single_best(int E, int P, const int *__restrict__ hoff, const int *__restrict__ pins,
               const int *__restrict__ match, const int *__restrict__ ssize,
-              const int *__restrict__ sweight, unsigned long long *__restrict__ best) {
-    d_single_best(GridTeam(), E, P, hoff, pins, match, ssize, sweight, best);
+              const int *__restrict__ sweight, unsigned long long *__restrict__ best,
+              const int *__restrict__ ts) {
+    d_single_best(GridTeam(), E, P, hoff, pins, match, ssize, sweight, best, ts);
 }
 
 // Groups, plus the coarse level's accumulators cleared for later phases of this level: node
@@ -240,9 +244,10 @@ void seg_unique(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const in
 
 // Sorted-unique of every hyperedge's (mapped) pins into the coarse CSR of `c`.
 // Sets c.E and c.P.  `map` null means identity (level-0 normalisation).
-// sizes: two device ints receiving {E', P'}.
+// sizes: two device ints receiving {E', P'}; ts_in: tile starts of the input CSR (or null).
 void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int *pins,
-              const int *hw, const int *map, Level &c, int *deg, bool counters_zero, int32_t *sizes) {
+              const int *hw, const int *map, Level &c, int *deg, bool counters_zero, int32_t *sizes,
+              const int *ts_in) {
     cudaStream_t s = g->stream;
     Work &w = g->w;
     int *scratch = (int *)w.p_a.ensure(sizeof(int) * (size_t)std::max(P, 1), s);
@@ -252,11 +257,12 @@ void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int 
     seg_unique(g, E, P, hoff, pins, map, scratch, cnt, counters_zero);
     c.b_hoff.ensure(sizeof(int) * ((size_t)E + 1), s);
     c.b_pins.ensure(sizeof(int) * (size_t)std::max(P, 1), s);
+    c.b_tsh.ensure(sizeof(int) * ((size_t)P / kTsGran + 2), s);
     bool unit = (hw == nullptr);
     if (!unit) c.b_hw.ensure(sizeof(int) * (size_t)std::max(E, 1), s);
     c.unit_hw = unit;
     if (E > 0) {
-        CompactOut out{E, hw, c.hoff(), unit ? nullptr : c.b_hw.as<int>(), emap, sizes};
+        CompactOut out{E, hw, c.hoff(), unit ? nullptr : c.b_hw.as<int>(), emap, sizes, c.tsh()};
         {
             ProfScope ps("contract_offsets", 16.0 * E, s);
             scan(E, CompactIn{cnt}, out, w.scan.ensure_zero(scan_state_bytes(E), s), dev_status(g), s);
@@ -266,9 +272,10 @@ void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int 
             ProfScope ps("contract_copy", 12.0 * P + 12.0 * E, s);
             if (c.N <= kPrivNodes)
                 k_seg_copy_priv<<<priv_grid(P), kPrivBlock, sizeof(int) * (size_t)std::max(c.N, 1), s>>>(
-                    E, P, c.N, hoff, scratch, cnt, emap, c.hoff(), c.pins(), deg);
+                    E, P, c.N, hoff, scratch, cnt, emap, c.hoff(), c.pins(), deg, ts_in);
             else
-                k_seg_copy<<<lb_grid(P), kLbBlock, 0, s>>>(E, P, hoff, scratch, cnt, emap, c.hoff(), c.pins(), deg);
+                k_seg_copy<<<lb_grid(P), kLbBlock, 0, s>>>(E, P, hoff, scratch, cnt, emap, c.hoff(), c.pins(), deg,
+                                                           ts_in);
             BP_LAUNCH();
         }
     } else {
@@ -298,18 +305,19 @@ void build_incidence(bipart_graph *g, Level &L) {
     }
     int *deg = w.n_a.as<int>();
     int *cursor = (int *)w.n_b.ensure(sizeof(int) * (size_t)L.N, s);
+    L.b_tsn.ensure(sizeof(int) * ((size_t)L.P / kTsGran + 2), s);
     {
         ProfScope ps("incidence_offsets", 12.0 * L.N, s);
-        scan(L.N, DegIn{deg}, DegOut{L.N, L.noff(), cursor}, w.scan.ensure_zero(scan_state_bytes(L.N), s),
+        scan(L.N, DegIn{deg}, DegOut{L.N, L.noff(), cursor, L.tsn()}, w.scan.ensure_zero(scan_state_bytes(L.N), s),
              dev_status(g), s);
     }
     if (L.P > 0) {
         ProfScope ps("incidence_fill", 12.0 * L.P + 4.0 * L.E, s);
         if (L.N <= kPrivNodes)
             k_fill_adj_priv<<<priv_grid(L.P), kPrivBlock, sizeof(int) * (size_t)L.N, s>>>(
-                L.E, L.P, L.N, L.hoff(), L.pins(), cursor, L.nadj());
+                L.E, L.P, L.N, L.hoff(), L.pins(), cursor, L.nadj(), L.tsh());
         else
-            k_fill_adj<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.E, L.P, L.hoff(), L.pins(), cursor, L.nadj());
+            k_fill_adj<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.E, L.P, L.hoff(), L.pins(), cursor, L.nadj(), L.tsh());
         BP_LAUNCH();
     }
 }
@@ -332,7 +340,7 @@ void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t
     }
     L.N = N;
     contract(g, E, P, d_hoff, d_pins, d_hw, nullptr, L, degree_counters(g, N), false,
-             g->w.small.as<int32_t>() + 2);
+             g->w.small.as<int32_t>() + 2, nullptr);
     L.b_nw.ensure(sizeof(int) * (size_t)std::max(N, 1), s);
     if (d_nw) {
         BP_CUDA(cudaMemcpyAsync(L.nw(), d_nw, sizeof(int) * (size_t)N, cudaMemcpyDeviceToDevice, s));
@@ -372,7 +380,7 @@ void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *siz
         if (f.P > 0) {
             // noff, nadj, 8-byte key gather per incidence, one 8-byte atomic per node run
             ProfScope ps("match_min", 4.0 * N + 12.0 * f.P + 8.0 * N, s);
-            k_match_min<<<lb_grid(f.P), kLbBlock, 0, s>>>(N, f.P, f.noff(), f.nadj(), hkey, nkey);
+            k_match_min<<<lb_grid(f.P), kLbBlock, 0, s>>>(N, f.P, f.noff(), f.nadj(), hkey, nkey, f.tsn());
             BP_LAUNCH();
         }
         {
@@ -382,7 +390,8 @@ void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *siz
         }
         if (f.P > 0) {
             ProfScope ps("single_best", 4.0 * E + 4.0 * f.P, s);
-            k_single_best<<<lb_grid(f.P), kLbBlock, 0, s>>>(E, f.P, f.hoff(), f.pins(), f.match(), ssize, sweight, best);
+            k_single_best<<<lb_grid(f.P), kLbBlock, 0, s>>>(E, f.P, f.hoff(), f.pins(), f.match(), ssize, sweight, best,
+                                                            f.tsh());
             BP_LAUNCH();
         }
         {
@@ -403,7 +412,7 @@ void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *siz
         k_cmap<<<grid_for(N), kBlock, 0, s>>>(N, grp, gcid, f.nw(), f.cmap(), c.nw());
         BP_LAUNCH();
     }
-    contract(g, E, f.P, f.hoff(), f.pins(), f.hw(), f.cmap(), c, deg, N > 0, sizes + 1);
+    contract(g, E, f.P, f.hoff(), f.pins(), f.hw(), f.cmap(), c, deg, N > 0, sizes + 1, f.tsh());
     build_incidence(g, c);
     c.b_cmap.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);
     c.b_match.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);

@@ -232,10 +232,12 @@ struct CompactOut {
     int64_t n;
     const int *hw_in;
     int *hoff_out, *hw_out, *emap, *sizes;  // sizes[0] = E', sizes[1] = P'
+    int *ts;                                // tile starts of the compacted CSR (or null)
     __device__ void operator()(int64_t e, uint64_t pre, uint64_t val) const {
         int ei = (int)(pre >> 31), pi = (int)(pre & 0x7fffffffu);
         if (val) {
             hoff_out[ei] = pi;
+            lb_mark_tiles(ts, ei, pi, (int64_t)(val & 0x7fffffffu));
             if (hw_out) hw_out[ei] = hw_in ? hw_in[e] : 1;
             emap[e] = ei;
         } else {
@@ -257,7 +259,7 @@ struct CompactOut {
 template <class Team>
 __device__ void d_seg_copy(Team t, int E, int P, const int *hoff, const int *scratch,
                            const int *cnt, const int *emap, const int *hoff_out, int *pins_out,
-                           int *deg) {
+                           int *deg, const int *ts = nullptr) {
     lb_runs(
         hoff, E, P,
         [&](int e, int a, int b) {
@@ -271,7 +273,7 @@ __device__ void d_seg_copy(Team t, int E, int P, const int *hoff, const int *scr
                 atomicAdd(deg + v, 1);
             }
         },
-        t);
+        t, ts);
 }
 
 // ------------------------------------------------------------------------------- incidence
@@ -282,9 +284,11 @@ struct DegIn {
 struct DegOut {
     int64_t n;
     int *noff, *cursor;
+    int *ts;  // tile starts of the incidence CSR (or null)
     __device__ void operator()(int64_t v, uint64_t pre, uint64_t val) const {
         noff[v] = (int)pre;
         cursor[v] = (int)pre;
+        lb_mark_tiles(ts, (int)v, (int64_t)pre, (int64_t)val);
         if (v == n - 1) noff[n] = (int)(pre + val);
     }
 };
@@ -295,12 +299,12 @@ struct DegOut {
 // order inside a node's list depends on the atomics' order; every consumer is order-independent.
 template <class Team, class Claim>
 __device__ void d_fill_adj_with(Team t, int E, int P, const int *hoff, const int *pins, int *nadj,
-                                Claim claim) {
+                                Claim claim, const int *ts = nullptr) {
     const int tile = blockDim.x * kLbItems;
     for (int64_t t0 = (int64_t)t.block() * tile; t0 < P; t0 += (int64_t)t.blocks() * tile) {
         const int j0 = (int)t0;
         const int j1 = (int)(t0 + tile < P ? t0 + tile : P);
-        const LbTile T = lb_tile<Team>(hoff, E, j0, j1);
+        const LbTile T = lb_tile<Team>(hoff, E, P, j0, j1, ts);
         const int j = j0 + threadIdx.x * kLbItems;
         if (j >= j1) continue;
         const int n = j1 - j < kLbItems ? j1 - j : kLbItems;
@@ -328,8 +332,8 @@ __device__ void d_fill_adj_with(Team t, int E, int P, const int *hoff, const int
 // offset).
 template <class Team>
 __device__ void d_fill_adj(Team t, int E, int P, const int *hoff, const int *pins, int *cursor,
-                           int *nadj) {
-    d_fill_adj_with(t, E, P, hoff, pins, nadj, [&](int v) { return atomicAdd(cursor + v, 1); });
+                           int *nadj, const int *ts = nullptr) {
+    d_fill_adj_with(t, E, P, hoff, pins, nadj, [&](int v) { return atomicAdd(cursor + v, 1); }, ts);
 }
 
 // ------------------------------------------------------------------ Algorithm 1
@@ -351,7 +355,8 @@ __device__ void d_hedge_key(Team t, int E, int policy, const int *hoff, const in
 // not depend on the order of the atomics.
 template <class Team>
 __device__ void d_match_min(Team t, int N, int P, const int *noff, const int *nadj,
-                            const unsigned long long *hkey, unsigned long long *nkey) {
+                            const unsigned long long *hkey, unsigned long long *nkey,
+                            const int *ts = nullptr) {
     lb_for_each_items<unsigned long long>(
         noff, N, P, nadj, ~0ull,
         [&](int, int e, unsigned long long acc) {
@@ -361,7 +366,7 @@ __device__ void d_match_min(Team t, int N, int P, const int *noff, const int *na
         [&](int v, unsigned long long acc) {
             if (acc != ~0ull) atomicMin(nkey + v, acc);
         },
-        t);
+        t, ts);
 }
 
 // match[v] from the winning key; sizes and weights of the matched sets S(e) (integer atomics).
@@ -386,7 +391,7 @@ __device__ void d_match_set(Team t, int N, const unsigned long long *nkey, const
 template <class Team>
 __device__ void d_single_best(Team t, int E, int P, const int *hoff, const int *pins,
                               const int *match, const int *ssize, const int *sweight,
-                              unsigned long long *best) {
+                              unsigned long long *best, const int *ts = nullptr) {
     lb_for_each_items<unsigned long long>(
         hoff, E, P, pins, ~0ull,
         [&](int e, int u, unsigned long long acc) {
@@ -401,7 +406,7 @@ __device__ void d_single_best(Team t, int E, int P, const int *hoff, const int *
         [&](int e, unsigned long long acc) {
             if (acc != ~0ull) atomicMin(best + e, acc);
         },
-        t);
+        t, ts);
 }
 
 // grp[v] = matched hyperedge of v's final group, or -1 when v stays alone; rep[g] receives the

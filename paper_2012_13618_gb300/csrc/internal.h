@@ -71,6 +71,9 @@ struct Level {
     int32_t N = 0, E = 0, P = 0;
     bool unit_hw = true;
     Buf b_hoff, b_pins, b_hw, b_nw, b_noff, b_nadj, b_cmap, b_match;
+    Buf b_tsh, b_tsn;  // tile-start tables of the hyperedge and incidence CSRs
+    int32_t *tsh() const { return b_tsh.as<int32_t>(); }
+    int32_t *tsn() const { return b_tsn.as<int32_t>(); }
     int32_t *hoff() const { return b_hoff.as<int32_t>(); }
     int32_t *pins() const { return b_pins.as<int32_t>(); }
     int32_t *hw() const { return unit_hw ? nullptr : b_hw.as<int32_t>(); }

@@ -16,6 +16,16 @@ constexpr int kLbItems = 8;
 constexpr int kLbTile = kLbBlock * kLbItems;
 
 constexpr int kLbStage = 2048;  // segment offsets of one tile staged in shared memory
+constexpr int kTsGran = 2048;   // tile-start tables hold the segment of every item j = t * kTsGran
+
+// Tile-start table: ts[t] = the segment holding item t * kTsGran, for every such item < total.
+// Written while the CSR offsets are produced (by the thread that owns segment `seg`, which holds
+// items [a, a + len)); load-balanced loops over that CSR then find their tiles' segment ranges
+// with two loads instead of a search.  Needs blockDim.x * kLbItems to be a multiple of kTsGran.
+__device__ __forceinline__ void lb_mark_tiles(int *ts, int seg, int64_t a, int64_t len) {
+    if (!ts || len <= 0) return;
+    for (int64_t t = (a + kTsGran - 1) / kTsGran; t * kTsGran < a + len; ++t) ts[t] = seg;
+}
 
 // Largest s in [lo, hi] with off[s] <= j (the non-empty segment holding item j).
 template <class Team = GridTeam>
@@ -56,26 +66,36 @@ __device__ __forceinline__ int *lb_stage() {
     return buf;
 }
 
-// Segments [s0, s1] of the tile of items [j0, j1): warps 0 and 1 search the segments of the
-// first and the last item; off[s0 .. s1 + 1] is then staged in shared memory when it fits.
-// Called by the whole block (blockDim >= 64).
+// Segments [s0, s1] of the tile of items [j0, j1) (a superset: s1 may be the segment of item j1):
+// read from the tile-start table ts when there is one, else warps 0 and 1 search the segments
+// of the first and the last item; off[s0 .. s1 + 1] is then staged in shared memory when it
+// fits.  Called by the whole block (blockDim >= 64).
 struct LbTile {
     int s0, s1;
     bool staged;
 };
 
 template <class Team>
-__device__ __forceinline__ LbTile lb_tile(const int *off, int nseg, int j0, int j1) {
+__device__ __forceinline__ LbTile lb_tile(const int *off, int nseg, int total, int j0, int j1,
+                                          const int *ts) {
     __shared__ int s_rng[2];
     int *st = lb_stage();
     __syncthreads();  // the previous tile is done with the stage
-    const int w = threadIdx.x >> 5;
-    if (w < 2) {
-        const int s = lb_seg_warp<Team>(off, w == 0 ? j0 : j1 - 1, 0, nseg - 1);
-        if ((threadIdx.x & 31) == 0) s_rng[w] = s;
+    LbTile T;
+    if (ts) {
+        T.s0 = Team::ld(ts + j0 / kTsGran);
+        T.s1 = j1 < total ? Team::ld(ts + j1 / kTsGran) : nseg - 1;
+    } else {
+        const int w = threadIdx.x >> 5;
+        if (w < 2) {
+            const int s = lb_seg_warp<Team>(off, w == 0 ? j0 : j1 - 1, 0, nseg - 1);
+            if ((threadIdx.x & 31) == 0) s_rng[w] = s;
+        }
+        __syncthreads();
+        T.s0 = s_rng[0];
+        T.s1 = s_rng[1];
     }
-    __syncthreads();
-    LbTile T{s_rng[0], s_rng[1], false};
+    T.staged = false;
     const int cnt = T.s1 - T.s0 + 2;
     T.staged = cnt <= kLbStage + 2;
     if (T.staged)
@@ -111,13 +131,14 @@ __device__ __forceinline__ int lb_tile_end(const int *off, const LbTile &T, int 
 // blockDim.x * kLbItems items; the team's blocks take tiles in turn.
 template <class Acc, class Visit, class Flush, class Team = GridTeam>
 __device__ __forceinline__ void lb_for_each_items(const int *off, int nseg, int total, const int *items,
-                                                  Acc init, Visit visit, Flush flush, Team t = Team()) {
+                                                  Acc init, Visit visit, Flush flush, Team t = Team(),
+                                                  const int *ts = nullptr) {
     static_assert(kLbItems == 8, "two int4 loads per thread");
     const int tile = blockDim.x * kLbItems;
     for (int64_t t0 = (int64_t)t.block() * tile; t0 < total; t0 += (int64_t)t.blocks() * tile) {
         const int j0 = (int)t0;
         const int j1 = (int)(t0 + tile < total ? t0 + tile : total);
-        const LbTile T = lb_tile<Team>(off, nseg, j0, j1);
+        const LbTile T = lb_tile<Team>(off, nseg, total, j0, j1, ts);
         const int j = j0 + threadIdx.x * kLbItems;
         if (j >= j1) continue;
         const int n = j1 - j < kLbItems ? j1 - j : kLbItems;
@@ -153,12 +174,13 @@ __device__ __forceinline__ void lb_for_each_items(const int *off, int nseg, int 
 // Calls fn(s, a, b) for every maximal run [a, b) of this thread's items that lies in segment s,
 // in item order (per-segment values can then be loaded once per run).
 template <class Fn, class Team = GridTeam>
-__device__ __forceinline__ void lb_runs(const int *off, int nseg, int total, Fn fn, Team t = Team()) {
+__device__ __forceinline__ void lb_runs(const int *off, int nseg, int total, Fn fn, Team t = Team(),
+                                        const int *ts = nullptr) {
     const int tile = blockDim.x * kLbItems;
     for (int64_t t0 = (int64_t)t.block() * tile; t0 < total; t0 += (int64_t)t.blocks() * tile) {
         const int j0 = (int)t0;
         const int j1 = (int)(t0 + tile < total ? t0 + tile : total);
-        const LbTile T = lb_tile<Team>(off, nseg, j0, j1);
+        const LbTile T = lb_tile<Team>(off, nseg, total, j0, j1, ts);
         int j = j0 + threadIdx.x * kLbItems;
         if (j >= j1) continue;
         const int je = j + kLbItems < j1 ? j + kLbItems : j1;

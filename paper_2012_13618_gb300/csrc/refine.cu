@@ -44,8 +44,8 @@ inline int sel_grid(int N) { return N <= kSelOneBlock ? 1 : grid_for(N); }
 // Grid kernels: one launch per phase (device code in refine_dev.cuh).
 __global__ void __launch_bounds__(kLbBlock)
 k_hedge_n1(int E, int P, const int *__restrict__ hoff, const int *__restrict__ pins,
-           const uint8_t *__restrict__ side, int *__restrict__ n1) {
-    d_hedge_n1(GridTeam(), E, P, hoff, pins, side, n1);
+           const uint8_t *__restrict__ side, int *__restrict__ n1, const int *__restrict__ ts) {
+    d_hedge_n1(GridTeam(), E, P, hoff, pins, side, n1, ts);
 }
 
 // Contributions, n1 put back to zero, and the gains of the N nodes cleared for k_node_gain.
@@ -57,8 +57,9 @@ __global__ void k_hedge_contrib(int E, int N, const int *__restrict__ hoff, cons
 
 __global__ void __launch_bounds__(kLbBlock)
 k_node_gain(int N, int P, const int *__restrict__ noff, const int *__restrict__ nadj,
-            const int2 *__restrict__ hc, const uint8_t *__restrict__ side, int *__restrict__ gain) {
-    d_node_gain(GridTeam(), N, P, noff, nadj, hc, side, gain);
+            const int2 *__restrict__ hc, const uint8_t *__restrict__ side, int *__restrict__ gain,
+            const int *__restrict__ ts) {
+    d_node_gain(GridTeam(), N, P, noff, nadj, hc, side, gain, ts);
 }
 
 // Copies the grid's accumulated histogram into shared memory and clears it in global memory
@@ -188,7 +189,7 @@ void compute_gains(bipart_graph *g, Level &L, const uint8_t *side, int *gain) {
         {
             // hoff, pins, one side byte per pin, one atomic per hyperedge run
             ProfScope ps("hedge_n1", 8.0 * L.E + 5.0 * L.P, s);
-            k_hedge_n1<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.E, L.P, L.hoff(), L.pins(), side, n1);
+            k_hedge_n1<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.E, L.P, L.hoff(), L.pins(), side, n1, L.tsh());
             BP_LAUNCH();
         }
         {
@@ -203,7 +204,7 @@ void compute_gains(bipart_graph *g, Level &L, const uint8_t *side, int *gain) {
     if (L.P > 0) {
         // noff, nadj, 8-byte contribution gather per incidence, side, gain
         ProfScope ps("node_gain", 9.0 * L.N + 12.0 * L.P, s);
-        k_node_gain<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.N, L.P, L.noff(), L.nadj(), hc, side, gain);
+        k_node_gain<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.N, L.P, L.noff(), L.nadj(), hc, side, gain, L.tsn());
         BP_LAUNCH();
     }
 }

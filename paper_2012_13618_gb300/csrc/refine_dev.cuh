@@ -56,14 +56,14 @@ __device__ __forceinline__ int sel_group(int kind, const RState *st, int gain, u
 // n1[e] = number of pins of e on side 1 (load-balanced over pins, integer atomics).
 template <class Team>
 __device__ void d_hedge_n1(Team t, int E, int P, const int *hoff, const int *pins,
-                           const uint8_t *side, int *n1) {
+                           const uint8_t *side, int *n1, const int *ts = nullptr) {
     lb_for_each_items<int>(
         hoff, E, P, pins, 0,
         [&](int, int u, int acc) { return acc + Team::ld(side + u); },
         [&](int e, int acc) {
             if (acc) atomicAdd(n1 + e, acc);
         },
-        t);
+        t, ts);
 }
 
 // Contribution of e to a pin on side i: +w if n_i == 1 (moving it uncuts e), -w if n_i == |e|
@@ -85,7 +85,7 @@ __device__ void d_hedge_contrib(Team t, int E, const int *hoff, const int *hw, i
 // gain[v] = sum over v's hyperedges of the contribution for v's side (gain zeroed first).
 template <class Team>
 __device__ void d_node_gain(Team t, int N, int P, const int *noff, const int *nadj, const int2 *hc,
-                            const uint8_t *side, int *gain) {
+                            const uint8_t *side, int *gain, const int *ts = nullptr) {
     lb_for_each_items<int>(
         noff, N, P, nadj, 0,
         [&](int v, int e, int acc) {
@@ -95,7 +95,7 @@ __device__ void d_node_gain(Team t, int N, int P, const int *noff, const int *na
         [&](int v, int acc) {
             if (acc) atomicAdd(gain + v, acc);
         },
-        t);
+        t, ts);
 }
 
 // ------------------------------------------------------------------------ selection
