@@ -48,6 +48,46 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# Sources that define each profiled kernel: a DRAM-traffic record taken with ncu is used only
+# while these files are unchanged (else the kernel may have changed since the counters).
+KERNEL_SOURCES = {
+    "node_gain": ["refine_dev.cuh", "refine.cu", "lb.cuh", "common.cuh"],
+    "hedge_n1": ["refine_dev.cuh", "refine.cu", "lb.cuh", "common.cuh"],
+}
+# Algorithmic bytes of one launch on a level of (N, E, P), as the library's probes count them.
+KERNEL_BYTES = {
+    "node_gain": lambda N, E, P: 9.0 * N + 12.0 * P,
+    "hedge_n1": lambda N, E, P: 8.0 * E + 5.0 * P,
+}
+
+
+def source_hash(name):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[name]:
+        with open(os.path.join(ROOT, "paper_2012_13618_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(name, alg_bytes_per_launch, level0_bytes):
+    """DRAM bytes per launch of `name` from its ncu record in profiles/ (one level-0 launch,
+    scaled to the mean launch by algorithmic bytes), or None without a current record."""
+    if name not in KERNEL_SOURCES:
+        return None
+    path = os.path.join(ROOT, "profiles", f"{name}_c1_netlist_1M.md")
+    if not os.path.exists(path):
+        return None
+    rec = None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("traffic-record:"):
+                rec = json.loads(line.split(":", 1)[1])
+    if not rec or rec.get("source_sha256") != source_hash(name) or level0_bytes <= 0:
+        return None
+    return rec["dram_bytes"] * alg_bytes_per_launch / level0_bytes
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -310,11 +350,20 @@ def run_gpu(args):
         name, (cnt, tms, tbytes) = top
         per_launch_s = tms / cnt / 1000.0
         ach = (tbytes / cnt) / per_launch_s / 1e9
+        traffic = None
+        if name in KERNEL_BYTES:
+            n0 = bp._i32(); e0 = bp._i32(); p0 = bp._i32()
+            bp.load().bipart_get_level(h._h, 0, bp.ctypes.byref(n0), bp.ctypes.byref(e0),
+                                       bp.ctypes.byref(p0), None, None, None, None, None, None)
+            traffic = ncu_traffic(name, tbytes / cnt, KERNEL_BYTES[name](n0.value, e0.value, p0.value))
         roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "peak_source": src,
+                "frac": ach / hbm, "traffic": traffic, "peak_source": src,
                 "launches": cnt, "share_of_step": tms / (ms * args.steps),
                 "note": "achieved = algorithmic bytes per launch / mean CUDA-event duration per "
-                        "launch over the timed region; peak is the " + src + " HBM copy bandwidth"}
+                        "launch over the timed region; peak is the " + src + " HBM copy bandwidth; "
+                        "traffic = ncu DRAM read+write bytes of one level-0 launch, scaled to the "
+                        "mean launch by algorithmic bytes (null unless that record matches the "
+                        "kernel's current sources)"}
 
     if rank == 0:
         cpu = cpu_baseline(g) if (ws == 1 and not args.no_cpu_baseline) else None
@@ -507,6 +556,30 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+def run_once(replay=False):
+    """One eager (first-call) bisection of the plain workload, nothing timed: the launch sequence
+    a focused ncu capture selects from (kernel filter + launch skip).  With `replay`, the graph
+    is then captured and one replay runs inside the NVTX range 'replay'."""
+    import torch
+    import paper_2012_13618_gb300 as bp
+    bp.use_torch_allocator()
+    g = load_workload()
+    out = torch.empty(g["N"], dtype=torch.int32, device="cuda")
+    h = bp.create_from(g)
+    args = (out, WORKLOAD["k"], WORKLOAD["epsilon"], WORKLOAD["policy"], WORKLOAD["levels"],
+            WORKLOAD["refine_iters"])
+    st = h.partition_device(*args)
+    if replay:
+        h.partition_device(*args)  # captures the plan
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("replay")
+        st = h.partition_device(*args)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    print(json.dumps({"once": WORKLOAD["workload"], "status": int(st), "levels": h.num_levels()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -523,7 +596,14 @@ def main():
     ap.add_argument("--serve-n", type=int, default=120)
     ap.add_argument("--rates", type=float, nargs="+", default=[0.25, 0.5, 1, 2, 4])
     ap.add_argument("--budget-gb", type=int, default=64)
+    ap.add_argument("--once", action="store_true",
+                    help="one eager bisection of the workload and exit (for focused ncu captures)")
+    ap.add_argument("--replay", action="store_true",
+                    help="with --once: also capture the graph and run one replay inside an NVTX "
+                         "range named 'replay' (for launch lists of exactly one replay)")
     args = ap.parse_args()
+    if args.once:
+        return run_once(args.replay)
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "serve":
