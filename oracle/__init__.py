@@ -8,6 +8,7 @@ with the CUDA path under ``paper_2012_13618_gb300``.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -77,6 +78,13 @@ def _load():
                 "orc_cut_bisection": (_i64, [_vp, _vp]),
                 "orc_subgraph": (_vp, [_vp, _vp, _i32, _vp]),
                 "orc_partition": (ctypes.c_int, [_vp, _i32, _dbl, ctypes.c_int, _i32, _i32, _vp]),
+                "orc_partition_ex": (ctypes.c_int, [_vp, _i32, _i64, ctypes.c_int, ctypes.c_int,
+                                                    _i32, _i32, _vp]),
+                "orc_initial_target": (_i32, [_vp, _vp, _i32, _i32]),
+                "orc_rebalance2": (ctypes.c_int, [_vp, _vp, _i64, _i64, _vp]),
+                "orc_limit_part": (_i64, [_i64, _i32, _i32, _i64]),
+                "orc_adaptive_e6": (_i64, [_i64, _i32]),
+                "orc_bisect_target": (_vp, [_vp, _i64, _i32, _i32, ctypes.c_int, _i32, _i32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -92,6 +100,11 @@ def _ptr(a):
 
 def _i32arr(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _e6(eps: float) -> int:
+    """eps in millionths, rounded half away from zero like C's llround (eps >= 0)."""
+    return int(math.floor(float(eps) * 1e6 + 0.5))
 
 
 def _policy(p) -> int:
@@ -184,9 +197,13 @@ def gains(g: Hypergraph, side) -> np.ndarray:
     return out
 
 
-def initial(g: Hypergraph):
+def initial(g: Hypergraph, m0=1, m=2):
+    """Algorithm 3 with side 0 meant for m0 of m parts (reading G2; 1 of 2 = the paper's)."""
     side = np.empty(max(g.N, 1), np.uint8)
-    rounds = _load().orc_initial(g._h, _ptr(side))
+    if (m0, m) == (1, 2):
+        rounds = _load().orc_initial(g._h, _ptr(side))
+    else:
+        rounds = _load().orc_initial_target(g._h, _ptr(side), int(m0), int(m))
     return side[: g.N], int(rounds)
 
 
@@ -195,17 +212,39 @@ def refine_iter(g: Hypergraph, side: np.ndarray) -> int:
     return int(_load().orc_refine_iter(g._h, _ptr(side)))
 
 
-def rebalance(g: Hypergraph, side: np.ndarray, lim: int):
+def rebalance(g: Hypergraph, side: np.ndarray, lim: int, lim1=None):
+    """Reading C13 (one limit for both sides), or with a limit per side (reading G2)."""
     assert side.dtype == np.uint8 and side.flags.c_contiguous
     rounds = ctypes.c_int32(0)
-    st = _load().orc_rebalance(g._h, _ptr(side), int(lim), ctypes.byref(rounds))
+    if lim1 is None:
+        st = _load().orc_rebalance(g._h, _ptr(side), int(lim), ctypes.byref(rounds))
+    else:
+        st = _load().orc_rebalance2(g._h, _ptr(side), int(lim), int(lim1), ctypes.byref(rounds))
     return int(st), int(rounds.value)
 
 
-def bisect(g: Hypergraph, eps=0.1, policy="LDH", levels=25, iters=2, keep_levels=True):
-    """Multilevel bisection: dict(side, status, nlev, init_rounds, limit, levels, cmaps, matches)."""
+def limit_part(W: int, ms: int, m: int, e6: int) -> int:
+    """Reading G2: limit of a side meant for ms of m parts, imbalance e6 millionths."""
+    return int(_load().orc_limit_part(int(W), int(ms), int(m), int(e6)))
+
+
+def adaptive_e6(e6: int, k: int) -> int:
+    """Reading G3: per-bisection imbalance (millionths) for k parts."""
+    return int(_load().orc_adaptive_e6(int(e6), int(k)))
+
+
+def bisect(g: Hypergraph, eps=0.1, policy="LDH", levels=25, iters=2, keep_levels=True,
+           target=None, e6=None):
+    """Multilevel bisection: dict(side, status, nlev, init_rounds, limit, levels, cmaps, matches).
+    `target` = (m0, m): side 0 meant for m0 of m parts (reading G2); `e6` overrides eps with an
+    imbalance in millionths."""
     L = _load()
-    r = L.orc_bisect(g._h, float(eps), _policy(policy), int(levels), int(iters))
+    if target is None and e6 is None:
+        r = L.orc_bisect(g._h, float(eps), _policy(policy), int(levels), int(iters))
+    else:
+        m0, m = target if target is not None else (1, 2)
+        e = int(e6) if e6 is not None else _e6(eps)
+        r = L.orc_bisect_target(g._h, e, int(m0), int(m), _policy(policy), int(levels), int(iters))
     try:
         nlev = L.orc_run_nlev(r)
         side = np.empty(max(g.N, 1), np.uint8)
@@ -248,9 +287,14 @@ def subgraph(g: Hypergraph, part, j: int):
     return s, l2g[: s.N]
 
 
-def partition(g: Hypergraph, k=2, eps=0.1, policy="LDH", levels=25, iters=2):
-    """Nested k-way (Algorithm 6): returns (parts int32[N], status)."""
+def partition(g: Hypergraph, k=2, eps=0.1, policy="LDH", levels=25, iters=2, adaptive=False):
+    """Nested k-way (Algorithm 6, any k >= 1 by readings G1-G2; `adaptive`: the per-bisection
+    imbalance of reading G3): returns (parts int32[N], status)."""
     part = np.empty(max(g.N, 1), np.int32)
-    st = _load().orc_partition(g._h, int(k), float(eps), _policy(policy), int(levels),
-                               int(iters), _ptr(part))
+    if not adaptive:
+        st = _load().orc_partition(g._h, int(k), float(eps), _policy(policy), int(levels),
+                                   int(iters), _ptr(part))
+    else:
+        st = _load().orc_partition_ex(g._h, int(k), _e6(eps), 1, _policy(policy),
+                                      int(levels), int(iters), _ptr(part))
     return part[: g.N], int(st)

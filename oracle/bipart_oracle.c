@@ -20,7 +20,9 @@
  *   refine         Algorithm 5 (Sec. 3.3): gain >= 0 lists, swap the top l_min (C15)
  *   rebalance      Algorithm 5's final step, a variant of Algorithm 3 (C13)
  *   bisect         Sec. 3.4 multilevel driver: levels / stop rule (C11), balance limit (C12)
- *   partition      Algorithm 6 (Sec. 3.5): nested k-way by recursive bisection (C16)
+ *   partition      Algorithm 6 (Sec. 3.5): nested k-way by recursive bisection (C16), extended
+ *                  to any k with proportional side targets and an optional per-bisection
+ *                  epsilon (readings G1-G3)
  *   cut            Sec. 1.1: sum over hyperedges of w_e (lambda_e - 1) (C17)
  *
  * Pins: every function here is checked by the -m "not gpu" tests against brute force, closed
@@ -40,6 +42,15 @@ enum { POL_LDH = 0, POL_HDH = 1, POL_LWD = 2, POL_HWD = 3, POL_RAND = 4 };
 
 /* Refinement admits nodes whose gain is at least this value (Algorithm 5 filters gain >= 0). */
 #define REFINE_MIN_GAIN 0
+
+struct orc_hg;
+struct orc_run;
+int32_t orc_initial_target(const struct orc_hg *g, uint8_t *side, int32_t m0, int32_t m);
+int orc_rebalance2(const struct orc_hg *g, uint8_t *side, int64_t limit0, int64_t limit1,
+                   int32_t *rounds_out);
+int64_t orc_limit_part(int64_t W, int32_t ms, int32_t m, int64_t e6);
+struct orc_run *orc_bisect_target(const struct orc_hg *g0, int64_t e6, int32_t m0, int32_t m,
+                                  int policy, int32_t levels, int32_t iters);
 
 typedef struct orc_hg {
     int32_t N, E;
@@ -333,16 +344,21 @@ static void side_weights(const orc_hg *g, const uint8_t *side, int64_t W[2]) {
  * s = ceil(sqrt(n)) nodes of P1 with the highest gains (ties to the smaller id) to P0; the last
  * round may overshoot.  Returns the number of rounds.
  * ------------------------------------------------------------------------------------------ */
-int32_t orc_initial(const orc_hg *g, uint8_t *side) {
+int32_t orc_initial(const orc_hg *g, uint8_t *side) { return orc_initial_target(g, side, 1, 2); }
+
+/* Reading G2: with side 0 meant to hold m0 of the m parts of this subgraph, "P0 lighter than P1"
+ * becomes "P0 below its share": m * W0 < m0 * W.  For m0 / m = 1 / 2 this is W0 < W1. */
+int32_t orc_initial_target(const orc_hg *g, uint8_t *side, int32_t m0, int32_t m) {
     int32_t n = g->N;
     int64_t s = orc_ceil_sqrt(n);
     for (int32_t v = 0; v < n; v++) side[v] = 1;
     int64_t W[2];
     side_weights(g, side, W);
-    int32_t *gain = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)n);
-    cand_t *L = (cand_t *)xmalloc(sizeof(cand_t) * (size_t)n);
+    const int64_t Wt = W[0] + W[1];
+    int32_t *gain = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    cand_t *L = (cand_t *)xmalloc(sizeof(cand_t) * (size_t)(n > 0 ? n : 1));
     int32_t rounds = 0;
-    while (W[0] < W[1]) {
+    while ((int64_t)m * W[0] < (int64_t)m0 * Wt) {
         orc_gains(g, side, gain);
         int32_t m = 0;
         for (int32_t v = 0; v < n; v++)
@@ -396,6 +412,65 @@ int64_t orc_limit(int64_t W, double eps) {
     return a > b ? a : b;
 }
 
+/* Reading G2: the limit of a side meant to hold ms of the m parts of a subgraph of weight W, with
+ * imbalance e6 millionths: max(ceil(W ms / m), floor(W ms (10^6 + e6) / (m 10^6))).  For
+ * ms / m = 1 / 2 this is orc_limit.  Exact in 128-bit integers. */
+int64_t orc_limit_part(int64_t W, int32_t ms, int32_t m, int64_t e6) {
+    __int128 num = (__int128)W * ms;
+    int64_t a = (int64_t)((num + m - 1) / m);
+    int64_t b = (int64_t)(num * (1000000 + e6) / ((__int128)m * 1000000));
+    return a > b ? a : b;
+}
+
+/* Reading G3: the per-bisection imbalance when every bisection on the way to k parts may use
+ * the same allowance: the largest x in [0, e6] with (10^6 + x)^L <= (10^6 + e6) (10^6)^(L-1),
+ * L = ceil(log2 k), i.e. floor(10^6 ((1 + eps)^(1/L) - 1)) without floating point.  L <= 1
+ * returns e6.  The powers are compared exactly in base-2^32 integers. */
+#define BIG_LIMBS 40
+typedef struct { uint32_t d[BIG_LIMBS]; } big_t;
+
+static void big_set(big_t *a, uint32_t v) { memset(a, 0, sizeof(*a)); a->d[0] = v; }
+
+static void big_mul(big_t *a, uint32_t v) {
+    uint64_t carry = 0;
+    for (int i = 0; i < BIG_LIMBS; i++) {
+        uint64_t t = (uint64_t)a->d[i] * v + carry;
+        a->d[i] = (uint32_t)t;
+        carry = t >> 32;
+    }
+}
+
+static int big_cmp(const big_t *a, const big_t *b) {
+    for (int i = BIG_LIMBS - 1; i >= 0; i--) {
+        if (a->d[i] != b->d[i]) return a->d[i] < b->d[i] ? -1 : 1;
+    }
+    return 0;
+}
+
+static int32_t ceil_log2(int64_t k) {
+    int32_t L = 0;
+    while (((int64_t)1 << L) < k) L++;
+    return L;
+}
+
+int64_t orc_adaptive_e6(int64_t e6, int32_t k) {
+    int32_t L = ceil_log2(k);
+    if (L <= 1) return e6;
+    big_t rhs;
+    big_set(&rhs, (uint32_t)(1000000 + e6));
+    for (int32_t i = 1; i < L; i++) big_mul(&rhs, 1000000u);
+    int64_t lo = 0, hi = e6;  /* lo satisfies the bound; find the largest that does */
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo + 1) / 2;
+        big_t lhs;
+        big_set(&lhs, 1);
+        for (int32_t i = 0; i < L; i++) big_mul(&lhs, (uint32_t)(1000000 + mid));
+        if (big_cmp(&lhs, &rhs) <= 0) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 /* ------------------------------------------------------------------------------------------
  * Algorithm 5, final step (reading C13, "a variant of Algorithm 3"): while the heavier side H
  * exceeds the limit, recompute the gains; the candidates are the nodes of H whose weight fits in
@@ -405,6 +480,13 @@ int64_t orc_limit(int64_t W, double eps) {
  * is left while H is still too heavy.
  * ------------------------------------------------------------------------------------------ */
 int orc_rebalance(const orc_hg *g, uint8_t *side, int64_t limit, int32_t *rounds_out) {
+    return orc_rebalance2(g, side, limit, limit, rounds_out);
+}
+
+/* Reading G2: the same with a limit per side (side s may hold up to limit_s); room and need are
+ * taken against the limits of the light and the heavy side. */
+int orc_rebalance2(const orc_hg *g, uint8_t *side, int64_t limit0, int64_t limit1, int32_t *rounds_out) {
+    const int64_t lim[2] = {limit0, limit1};
     int32_t n = g->N;
     int64_t s = orc_ceil_sqrt(n);
     int32_t *gain = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
@@ -414,10 +496,10 @@ int orc_rebalance(const orc_hg *g, uint8_t *side, int64_t limit, int32_t *rounds
         int64_t W[2];
         side_weights(g, side, W);
         int H;
-        if (W[0] > limit) H = 0;
-        else if (W[1] > limit) H = 1;
+        if (W[0] > lim[0]) H = 0;
+        else if (W[1] > lim[1]) H = 1;
         else break;
-        int64_t room = limit - W[1 - H], need = W[H] - limit;
+        int64_t room = lim[1 - H] - W[1 - H], need = W[H] - lim[H];
         orc_gains(g, side, gain);
         int32_t m = 0;
         for (int32_t v = 0; v < n; v++)
@@ -458,6 +540,13 @@ typedef struct orc_run {
 } orc_run;
 
 orc_run *orc_bisect(const orc_hg *g0, double eps, int policy, int32_t levels, int32_t iters) {
+    return orc_bisect_target(g0, llround(eps * 1e6), 1, 2, policy, levels, iters);
+}
+
+/* The same bisection with side 0 meant to hold m0 of m parts (reading G2) and the imbalance given
+ * in millionths.  m0 / m = 1 / 2 is orc_bisect. */
+orc_run *orc_bisect_target(const orc_hg *g0, int64_t e6, int32_t m0, int32_t m, int policy,
+                           int32_t levels, int32_t iters) {
     orc_run *r = (orc_run *)xcalloc(1, sizeof(orc_run));
     int32_t cap = levels + 1;
     r->lev = (orc_hg **)xcalloc((size_t)cap, sizeof(orc_hg *));
@@ -477,11 +566,12 @@ orc_run *orc_bisect(const orc_hg *g0, double eps, int policy, int32_t levels, in
     }
     int64_t W = 0;
     for (int32_t v = 0; v < g0->N; v++) W += g0->nwt[v];
-    r->limit = orc_limit(W, eps);
+    r->limit = orc_limit_part(W, m0, m, e6);
+    const int64_t limit1 = orc_limit_part(W, m - m0, m, e6);
 
     int32_t L = r->nlev - 1;
     uint8_t *side = (uint8_t *)xmalloc((size_t)(r->lev[L]->N > 0 ? r->lev[L]->N : 1));
-    r->init_rounds = orc_initial(r->lev[L], side);
+    r->init_rounds = orc_initial_target(r->lev[L], side, m0, m);
     int status = ORC_OK;
     for (int32_t l = L; l >= 0; l--) {
         const orc_hg *g = r->lev[l];
@@ -492,7 +582,7 @@ orc_run *orc_bisect(const orc_hg *g0, double eps, int policy, int32_t levels, in
             side = fine;
         }
         for (int32_t it = 0; it < iters; it++) orc_refine_iter(g, side);
-        status = orc_rebalance(g, side, r->limit, NULL);
+        status = orc_rebalance2(g, side, r->limit, limit1, NULL);
     }
     r->side = side;
     r->status = status;
@@ -585,29 +675,54 @@ orc_hg *orc_subgraph(const orc_hg *g, const int32_t *part, int32_t j, int32_t *l
 }
 
 /* ------------------------------------------------------------------------------------------
- * Algorithm 6 (nested k-way), sequentially: for tree level l = 1..log2 k, every current part j
- * is bisected as its own subgraph (reading C16) with the same eps, policy, levels and iters, and
- * its side-0 / side-1 nodes become parts 2j / 2j+1.  k must be a power of two; k = 1 gives all
- * zeros.  Returns ORC_WARN_IMBALANCED if any bisection ended above its limit.
+ * Algorithm 6 (nested k-way), sequentially, for any k >= 1 (readings C16, G1-G3).  A subgraph
+ * that owns the m parts [lo, lo + m) is bisected with side 0 meant for m0 = ceil(m / 2) of them
+ * (targets and limits in proportion, G2); its side-0 nodes own [lo, lo + m0), its side-1 nodes
+ * [lo + m0, lo + m); a range of one part is final.  Subgraphs are built as in C16 and bisected
+ * with the same policy, levels and iters, and with e6 millionths of imbalance (or, with
+ * `adaptive`, the per-bisection e6 of reading G3).  For k a power of two this is the paper's
+ * scheme: every split is in halves and the parts of a tree level are 2j, 2j + 1.  Returns
+ * ORC_WARN_IMBALANCED if any bisection ended above its limit.
  * ------------------------------------------------------------------------------------------ */
-int orc_partition(const orc_hg *g, int32_t k, double eps, int policy, int32_t levels,
-                  int32_t iters, int32_t *part) {
-    if (k < 1 || (k & (k - 1)) != 0) return ORC_ERR_INVALID_ARG;
-    for (int32_t v = 0; v < g->N; v++) part[v] = 0;
+int orc_partition_ex(const orc_hg *g, int32_t k, int64_t e6, int adaptive, int policy,
+                     int32_t levels, int32_t iters, int32_t *part) {
+    if (k < 1) return ORC_ERR_INVALID_ARG;
+    const int64_t eb = adaptive ? orc_adaptive_e6(e6, k) : e6;
+    for (int32_t v = 0; v < g->N; v++) part[v] = 0;  /* every node in the range starting at 0 */
     int status = ORC_OK;
     int32_t *l2g = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(g->N > 0 ? g->N : 1));
-    int32_t *next = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(g->N > 0 ? g->N : 1));
-    for (int32_t parts = 1; parts < k; parts *= 2) {
-        for (int32_t j = 0; j < parts; j++) {
-            orc_hg *s = orc_subgraph(g, part, j, l2g);
-            orc_run *r = orc_bisect(s, eps, policy, levels, iters);
-            if (r->status != ORC_OK) status = r->status;
-            for (int32_t i = 0; i < s->N; i++) next[l2g[i]] = 2 * j + r->side[i];
-            orc_run_free(r);
+    /* ranges of the current tree level: (lo, m); nodes carry the lo of their range */
+    int32_t *rlo = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)k);
+    int32_t *rm = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)k);
+    int32_t *nlo = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)k);
+    int32_t *nm = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)k);
+    int32_t nr = 1;
+    rlo[0] = 0;
+    rm[0] = k;
+    while (nr > 0) {
+        int32_t nn = 0;
+        for (int32_t r = 0; r < nr; r++) {
+            const int32_t lo = rlo[r], m = rm[r];
+            if (m < 2) continue;
+            const int32_t m0 = (m + 1) / 2;
+            orc_hg *s = orc_subgraph(g, part, lo, l2g);
+            orc_run *run = orc_bisect_target(s, eb, m0, m, policy, levels, iters);
+            if (run->status != ORC_OK) status = run->status;
+            for (int32_t i = 0; i < s->N; i++) part[l2g[i]] = run->side[i] ? lo + m0 : lo;
+            orc_run_free(run);
             orc_hg_free(s);
+            nlo[nn] = lo; nm[nn] = m0; nn++;
+            nlo[nn] = lo + m0; nm[nn] = m - m0; nn++;
         }
-        memcpy(part, next, sizeof(int32_t) * (size_t)g->N);
+        memcpy(rlo, nlo, sizeof(int32_t) * (size_t)nn);
+        memcpy(rm, nm, sizeof(int32_t) * (size_t)nn);
+        nr = nn;
     }
-    free(l2g); free(next);
+    free(l2g); free(rlo); free(rm); free(nlo); free(nm);
     return status;
+}
+
+int orc_partition(const orc_hg *g, int32_t k, double eps, int policy, int32_t levels,
+                  int32_t iters, int32_t *part) {
+    return orc_partition_ex(g, k, llround(eps * 1e6), 0, policy, levels, iters, part);
 }

@@ -498,5 +498,5 @@ def test_kway_trivial_and_invalid():
     h = oracle.Hypergraph.from_dict(synth.uniform(100, 100, 2, 4, seed=1))
     part, st = oracle.partition(h, 1)
     assert st == 0 and not part.any()
-    _, st = oracle.partition(h, 3)
-    assert st == oracle.ERR_INVALID_ARG
+    part, st = oracle.partition(h, 3)  # any k >= 1 (readings G1-G2)
+    assert part.min() >= 0 and part.max() < 3
