@@ -72,9 +72,12 @@ int bipart_set_stream(bipart_handle h, void *stream);
 
 /* Partitions the handle's hypergraph into k parts (Sec. 3; k-way by the nested recursive
  * bisection of Algorithm 6), writing part ids in [0, k) to out_parts[num_nodes] (HOST memory).
- *   k        power of two >= 1 (k = 1 gives all zeros)
- *   epsilon  imbalance, 0 <= epsilon <= 1000: each bisection keeps both sides at or below
- *            max(ceil(W/2), floor(W (1 + epsilon) / 2)) of its total node weight W
+ *   k        number of parts, >= 1 (k = 1 gives all zeros).  A (sub)graph owning m parts is
+ *            bisected with ceil(m/2) of them on side 0; for k a power of two every split is
+ *            in halves, as in Algorithm 6 (other k: readings G1-G2, the paper is silent)
+ *   epsilon  imbalance, 0 <= epsilon <= 1000: a side meant for ms of the m parts of a
+ *            bisection of total node weight W stays at or below
+ *            max(ceil(W ms / m), floor(W ms (1 + epsilon) / m)) (ms / m = 1/2 when halving)
  *   policy   BIPART_POLICY_* (Table 1)
  *   levels   maximum number of coarsening levels, >= 0 (the paper's default is 25, Sec. 3.4)
  *   refine_iters  refinement iterations per level, >= 0 (default 2, Sec. 3.4)
@@ -85,6 +88,11 @@ int bipart_partition(bipart_handle h, int32_t k, double epsilon, int32_t policy,
 /* Same as bipart_partition with out_parts in DEVICE memory. */
 int bipart_partition_device(bipart_handle h, int32_t k, double epsilon, int32_t policy,
                             int32_t levels, int32_t refine_iters, int32_t *d_out_parts);
+
+/* Flags of bipart_params.  ADAPTIVE_EPS: every bisection of a k-way partition uses the largest
+ * imbalance e' (in millionths) with (1 + e')^L <= 1 + epsilon, L = ceil(log2 k), so that the
+ * nested allowances multiply to at most 1 + epsilon (reading G3; no effect for k <= 2). */
+#define BIPART_FLAG_ADAPTIVE_EPS 1
 
 /* Levels of the hierarchy kept from the last k = 2 call (level 0 = the normalised input). */
 int bipart_num_levels(bipart_handle h, int32_t *num_levels);
@@ -119,12 +127,18 @@ typedef struct {
     const int32_t *hedge_offsets, *hedge_pins, *node_weights, *hedge_weights;
 } bipart_instance;
 
-/* Parameters of one partition request (as in bipart_partition). */
+/* Parameters of one partition request (as in bipart_partition), plus BIPART_FLAG_* bits in
+ * `flags` (unknown bits are rejected with INVALID_ARG). */
 typedef struct {
     int32_t k;
     double epsilon;
     int32_t policy, levels, refine_iters;
+    int32_t flags;
 } bipart_params;
+
+/* bipart_partition / bipart_partition_device with the parameters (and flags) in a struct. */
+int bipart_partition_ex(bipart_handle h, const bipart_params *params, int32_t *out_parts);
+int bipart_partition_device_ex(bipart_handle h, const bipart_params *params, int32_t *d_out_parts);
 
 /* Partitions n independent hypergraphs concurrently on the current GPU (each as bipart_partition
  * would, Sec. 3 / Algorithm 6): `workers` host threads (<= 0: min(16, n)) each own a private

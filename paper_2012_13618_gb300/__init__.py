@@ -46,7 +46,11 @@ class Instance(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("epsilon", ctypes.c_double), ("policy", ctypes.c_int32),
-                ("levels", ctypes.c_int32), ("refine_iters", ctypes.c_int32)]
+                ("levels", ctypes.c_int32), ("refine_iters", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+FLAG_ADAPTIVE_EPS = 1
 
 
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -59,6 +63,8 @@ SYMBOLS = {
     "bipart_set_stream": (ctypes.c_int, [_vp, _vp]),
     "bipart_partition": (ctypes.c_int, [_vp, _i32, ctypes.c_double, _i32, _i32, _i32, _vp]),
     "bipart_partition_device": (ctypes.c_int, [_vp, _i32, ctypes.c_double, _i32, _i32, _i32, _vp]),
+    "bipart_partition_ex": (ctypes.c_int, [_vp, _vp, _vp]),
+    "bipart_partition_device_ex": (ctypes.c_int, [_vp, _vp, _vp]),
     "bipart_num_levels": (ctypes.c_int, [_vp, _p32]),
     "bipart_get_level": (ctypes.c_int, [_vp, _i32, _p32, _p32, _p32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "bipart_cut": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_int64)]),
@@ -217,16 +223,26 @@ class Handle:
     def set_stream(self, stream):
         _check(load().bipart_set_stream(self._h, _stream_ptr(stream)))
 
-    def partition(self, k=2, eps=0.1, policy="LDH", levels=25, iters=2):
-        """Returns (parts int32[N] on the host, status)."""
+    def partition(self, k=2, eps=0.1, policy="LDH", levels=25, iters=2, adaptive_eps=False):
+        """Returns (parts int32[N] on the host, status).  Any k >= 1; `adaptive_eps` gives every
+        bisection of a k-way partition the per-bisection imbalance (BIPART_FLAG_ADAPTIVE_EPS)."""
         N = self.sizes()[0]
         out = np.empty(max(N, 1), np.int32)
-        st = _check(load().bipart_partition(self._h, int(k), float(eps), _policy(policy),
-                                            int(levels), int(iters), _ptr(out)))
+        if adaptive_eps:
+            p = _params(k, eps, policy, levels, iters, adaptive_eps)
+            st = _check(load().bipart_partition_ex(self._h, ctypes.byref(p), _ptr(out)))
+        else:
+            st = _check(load().bipart_partition(self._h, int(k), float(eps), _policy(policy),
+                                                int(levels), int(iters), _ptr(out)))
         return out[:N], st
 
-    def partition_device(self, out, k=2, eps=0.1, policy="LDH", levels=25, iters=2):
+    def partition_device(self, out, k=2, eps=0.1, policy="LDH", levels=25, iters=2,
+                         adaptive_eps=False):
         """Writes parts into the int32 CUDA tensor `out` (asynchronously on the handle's stream)."""
+        if adaptive_eps:
+            p = _params(k, eps, policy, levels, iters, adaptive_eps)
+            return _check(load().bipart_partition_device_ex(self._h, ctypes.byref(p),
+                                                            ctypes.c_void_p(out.data_ptr())))
         return _check(load().bipart_partition_device(self._h, int(k), float(eps), _policy(policy),
                                                      int(levels), int(iters),
                                                      ctypes.c_void_p(out.data_ptr())))
@@ -306,8 +322,9 @@ def _instance(g):
     return inst, arrs
 
 
-def _params(k=2, eps=0.1, policy="LDH", levels=25, iters=2):
-    return Params(int(k), float(eps), _policy(policy), int(levels), int(iters))
+def _params(k=2, eps=0.1, policy="LDH", levels=25, iters=2, adaptive_eps=False):
+    return Params(int(k), float(eps), _policy(policy), int(levels), int(iters),
+                  FLAG_ADAPTIVE_EPS if adaptive_eps else 0)
 
 
 def partition_batch(graphs, params, workers=0):

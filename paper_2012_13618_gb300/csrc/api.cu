@@ -263,11 +263,12 @@ __global__ void k_weight_sum(int N, const int *__restrict__ nw, unsigned long lo
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
 }
 
+// Side 0 of a subgraph keeps the part range starting at lo, side 1 takes the one starting at hi.
 __global__ void k_side_to_part(int N, const uint8_t *__restrict__ side, const int *__restrict__ l2g,
-                               int base, int *__restrict__ part) {
+                               int lo, int hi, int *__restrict__ part) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         int v = l2g ? l2g[i] : i;
-        part[v] = base + side[i];
+        part[v] = side[i] ? hi : lo;
     }
 }
 
@@ -477,7 +478,8 @@ void bisect_body(bipart_graph *g, Level &L0, const Params &p, int64_t W, uint8_t
         levels.push_back(&c);
     }
     if (nlev) *nlev = (int)levels.size();
-    uncoarsen(g, levels, balance_limit(W, p.eps), p.iters, d_side);
+    const int64_t limit[2] = {balance_limit(W, p.m0, p.m, p.e6), balance_limit(W, p.m - p.m0, p.m, p.e6)};
+    uncoarsen(g, levels, limit, p.m0, p.m, p.iters, d_side);
     if (g->ex.capturing) flush_checks(g);
 }
 
@@ -544,7 +546,8 @@ void capture_plan(bipart_graph *g, const Params &p, uint8_t *d_side, int nlev, i
 }
 
 bool same_params(const Params &a, const Params &b) {
-    return a.policy == b.policy && a.levels == b.levels && a.iters == b.iters && a.eps == b.eps;
+    return a.policy == b.policy && a.levels == b.levels && a.iters == b.iters && a.e6 == b.e6 &&
+           a.m0 == b.m0 && a.m == b.m;
 }
 
 // Bisection of the handle's level 0.  First call with given parameters: eager, recording the
@@ -596,6 +599,10 @@ int bisect_top(bipart_graph *g, const Params &p, uint8_t *d_side, int *nlev) {
     return st;
 }
 
+// Nested k-way (Algorithm 6; readings C16, G1-G2 for any k): the subgraph owning the parts
+// [lo, lo + m) is bisected with side 0 meant for ceil(m / 2) of them; its nodes carry lo as
+// their part until their range holds one part.  Ranges of one tree level are bisected one after
+// another, each as its own subgraph.
 int partition_device(bipart_graph *g, const Params &p, int *d_parts) {
     cudaStream_t s = g->stream;
     Level &L = g->L0;
@@ -609,9 +616,12 @@ int partition_device(bipart_graph *g, const Params &p, int *d_parts) {
     BP_CUDA(cudaMemsetAsync(dev_status(g), 0, sizeof(uint32_t), s));
     int status = BIPART_OK;
     int nlev = 0;
-    int st = bisect_top(g, p, d_side, &nlev);
+    Params top = p;
+    top.m = p.k;
+    top.m0 = (p.k + 1) / 2;
+    int st = bisect_top(g, top, d_side, &nlev);
     if (st != BIPART_OK) status = st;
-    k_side_to_part<<<grid_for(L.N), kBlock, 0, s>>>(L.N, d_side, nullptr, 0, d_parts);
+    k_side_to_part<<<grid_for(L.N), kBlock, 0, s>>>(L.N, d_side, nullptr, 0, top.m0, d_parts);
     BP_LAUNCH();
     if (p.k == 2) {
         g->hier.nlev = nlev;
@@ -619,23 +629,33 @@ int partition_device(bipart_graph *g, const Params &p, int *d_parts) {
         sync(g);
         return status;
     }
-    // nested k-way (Algorithm 6): tree level by tree level, every part bisected as a subgraph
     int *pa = (int *)g->part_a.ensure(sizeof(int) * (size_t)L.N, s);
     BP_CUDA(cudaMemcpyAsync(pa, d_parts, sizeof(int) * (size_t)L.N, cudaMemcpyDeviceToDevice, s));
-    for (int parts = 2; parts < p.k; parts *= 2) {
-        for (int j = 0; j < parts; ++j) {
-            extract_subgraph(g, pa, j);
+    std::vector<std::pair<int32_t, int32_t>> ranges{{0, top.m0}, {top.m0, p.k - top.m0}};
+    while (!ranges.empty()) {
+        std::vector<std::pair<int32_t, int32_t>> next;
+        for (const auto &r : ranges) {
+            const int32_t lo = r.first, m = r.second;
+            if (m < 2) continue;
+            Params q = p;
+            q.m = m;
+            q.m0 = (m + 1) / 2;
+            next.emplace_back(lo, q.m0);
+            next.emplace_back(lo + q.m0, m - q.m0);
+            extract_subgraph(g, pa, lo);
             Level &S = g->sub0;
             if (S.N == 0) continue;
             int64_t Wj = node_weight_sum(g, S);
             uint8_t *ds = (uint8_t *)g->side_out.ensure((size_t)S.N, s);
-            bisect_body(g, S, p, Wj, ds, nullptr);
+            bisect_body(g, S, q, Wj, ds, nullptr);
             st = read_bisect_status(g);
             if (st != BIPART_OK) status = st;
-            k_side_to_part<<<grid_for(S.N), kBlock, 0, s>>>(S.N, ds, g->l2g.as<int>(), 2 * j, d_parts);
+            k_side_to_part<<<grid_for(S.N), kBlock, 0, s>>>(S.N, ds, g->l2g.as<int>(), lo, lo + q.m0, d_parts);
             BP_LAUNCH();
         }
-        BP_CUDA(cudaMemcpyAsync(pa, d_parts, sizeof(int) * (size_t)L.N, cudaMemcpyDeviceToDevice, s));
+        if (!next.empty())
+            BP_CUDA(cudaMemcpyAsync(pa, d_parts, sizeof(int) * (size_t)L.N, cudaMemcpyDeviceToDevice, s));
+        ranges.swap(next);
     }
     sync(g);
     return status;
@@ -644,11 +664,77 @@ int partition_device(bipart_graph *g, const Params &p, int *d_parts) {
 }  // namespace
 
 void validate_params(int32_t k, double eps, int32_t policy, int32_t levels, int32_t iters) {
-    if (k < 1 || (k & (k - 1)) != 0) throw Fail{BIPART_ERR_INVALID_ARG, "k must be a power of two >= 1"};
+    if (k < 1) throw Fail{BIPART_ERR_INVALID_ARG, "k must be >= 1"};
     if (!(eps >= 0.0 && eps <= 1000.0)) throw Fail{BIPART_ERR_INVALID_ARG, "epsilon must be in [0, 1000]"};
     if (policy < BIPART_POLICY_LDH || policy > BIPART_POLICY_RAND) throw Fail{BIPART_ERR_INVALID_ARG, "unknown policy"};
     if (levels < 0) throw Fail{BIPART_ERR_INVALID_ARG, "levels must be >= 0"};
     if (iters < 0) throw Fail{BIPART_ERR_INVALID_ARG, "refine_iters must be >= 0"};
+}
+
+namespace {
+
+// Base-10^9 digits, least significant first: enough for the powers compared below.
+using Digits = std::vector<uint64_t>;
+
+void mul_small(Digits &a, uint64_t f) {
+    uint64_t carry = 0;
+    for (uint64_t &d : a) {
+        const unsigned __int128 t = (unsigned __int128)d * f + carry;
+        d = (uint64_t)(t % 1000000000u);
+        carry = (uint64_t)(t / 1000000000u);
+    }
+    while (carry) {
+        a.push_back(carry % 1000000000u);
+        carry /= 1000000000u;
+    }
+}
+
+bool less_equal(const Digits &a, const Digits &b) {
+    if (a.size() != b.size()) return a.size() < b.size();
+    for (size_t i = a.size(); i-- > 0;)
+        if (a[i] != b[i]) return a[i] < b[i];
+    return true;
+}
+
+}  // namespace
+
+// Reading G3: the imbalance every bisection of a k-way partition may use so that the L =
+// ceil(log2 k) nested allowances multiply to at most 1 + e: the largest x <= e6 (millionths)
+// with (10^6 + x)^L <= (10^6 + e6) * 10^(6 (L - 1)), compared exactly.
+int64_t adaptive_e6(int64_t e6, int32_t k) {
+    int L = 0;
+    while ((int64_t(1) << L) < k) ++L;
+    if (L <= 1) return e6;
+    Digits bound{1};
+    mul_small(bound, (uint64_t)(1000000 + e6));
+    for (int i = 1; i < L; ++i) mul_small(bound, 1000000u);
+    int64_t lo = 0, hi = e6;
+    while (lo < hi) {
+        const int64_t x = hi - (hi - lo) / 2;
+        Digits pw{1};
+        for (int i = 0; i < L; ++i) mul_small(pw, (uint64_t)(1000000 + x));
+        if (less_equal(pw, bound)) lo = x;
+        else hi = x - 1;
+    }
+    return lo;
+}
+
+Params make_params(int32_t k, double eps, int32_t policy, int32_t levels, int32_t iters,
+                   int32_t flags) {
+    validate_params(k, eps, policy, levels, iters);
+    if (flags & ~BIPART_FLAG_ADAPTIVE_EPS) throw Fail{BIPART_ERR_INVALID_ARG, "unknown flags"};
+    Params p;
+    p.k = k;
+    p.eps = eps;
+    p.policy = policy;
+    p.levels = levels;
+    p.iters = iters;
+    p.flags = flags;
+    const int64_t e6 = llround(eps * 1e6);
+    p.e6 = (flags & BIPART_FLAG_ADAPTIVE_EPS) ? adaptive_e6(e6, k) : e6;
+    p.m0 = 1;
+    p.m = 2;
+    return p;
 }
 
 void validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t *pins,
@@ -749,7 +835,6 @@ void graph_load_host(bipart_graph *g, int32_t N, int32_t E, const int32_t *hoff,
 // Partitions the loaded hypergraph into host memory (blocking on the handle's stream).
 int graph_partition_host(bipart_graph *g, const Params &p, int32_t *out) {
     HandleScope hs(g);
-    validate_params(p.k, p.eps, p.policy, p.levels, p.iters);
     const int32_t N = g->L0.N;
     int *d = (int *)g->part_b.ensure(sizeof(int) * (size_t)std::max(N, 1), g->stream);
     int st = partition_device(g, p, d);
@@ -874,17 +959,34 @@ int bipart_set_stream(bipart_handle h, void *stream) {
     });
 }
 
+namespace {
+
+int partition_to_device(bipart_handle h, const Params &p, int32_t *d_out_parts) {
+    if (!d_out_parts && h->L0.N > 0) throw Fail{BIPART_ERR_INVALID_ARG, "out_parts is NULL"};
+    int st = partition_device(h, p, d_out_parts);
+    check_status(h);
+    return st;
+}
+
+int partition_to_host(bipart_handle h, const Params &p, int32_t *out_parts) {
+    const int32_t N = h->L0.N;
+    if (!out_parts && N > 0) throw Fail{BIPART_ERR_INVALID_ARG, "out_parts is NULL"};
+    int *d = (int *)h->part_b.ensure(sizeof(int) * (size_t)std::max(N, 1), h->stream);
+    int st = partition_device(h, p, d);
+    if (N > 0) BP_CUDA(cudaMemcpyAsync(out_parts, d, sizeof(int) * (size_t)N, cudaMemcpyDeviceToHost, h->stream));
+    sync(h);
+    check_status(h);
+    return st;
+}
+
+}  // namespace
+
 int bipart_partition_device(bipart_handle h, int32_t k, double epsilon, int32_t policy,
                             int32_t levels, int32_t refine_iters, int32_t *d_out_parts) {
     if (!h) { set_error("handle is NULL"); return BIPART_ERR_INVALID_ARG; }
     HandleScope hs(h);
     return guard([&]() {
-        validate_params(k, epsilon, policy, levels, refine_iters);
-        if (!d_out_parts && h->L0.N > 0) throw Fail{BIPART_ERR_INVALID_ARG, "out_parts is NULL"};
-        Params p{k, epsilon, policy, levels, refine_iters};
-        int st = partition_device(h, p, d_out_parts);
-        check_status(h);
-        return st;
+        return partition_to_device(h, make_params(k, epsilon, policy, levels, refine_iters, 0), d_out_parts);
     });
 }
 
@@ -893,16 +995,27 @@ int bipart_partition(bipart_handle h, int32_t k, double epsilon, int32_t policy,
     if (!h) { set_error("handle is NULL"); return BIPART_ERR_INVALID_ARG; }
     HandleScope hs(h);
     return guard([&]() {
-        validate_params(k, epsilon, policy, levels, refine_iters);
-        const int32_t N = h->L0.N;
-        if (!out_parts && N > 0) throw Fail{BIPART_ERR_INVALID_ARG, "out_parts is NULL"};
-        Params p{k, epsilon, policy, levels, refine_iters};
-        int *d = (int *)h->part_b.ensure(sizeof(int) * (size_t)std::max(N, 1), h->stream);
-        int st = partition_device(h, p, d);
-        if (N > 0) BP_CUDA(cudaMemcpyAsync(out_parts, d, sizeof(int) * (size_t)N, cudaMemcpyDeviceToHost, h->stream));
-        sync(h);
-        check_status(h);
-        return st;
+        return partition_to_host(h, make_params(k, epsilon, policy, levels, refine_iters, 0), out_parts);
+    });
+}
+
+int bipart_partition_ex(bipart_handle h, const bipart_params *params, int32_t *out_parts) {
+    if (!h || !params) { set_error("NULL argument"); return BIPART_ERR_INVALID_ARG; }
+    HandleScope hs(h);
+    return guard([&]() {
+        const bipart_params &q = *params;
+        return partition_to_host(h, make_params(q.k, q.epsilon, q.policy, q.levels, q.refine_iters, q.flags),
+                                 out_parts);
+    });
+}
+
+int bipart_partition_device_ex(bipart_handle h, const bipart_params *params, int32_t *d_out_parts) {
+    if (!h || !params) { set_error("NULL argument"); return BIPART_ERR_INVALID_ARG; }
+    HandleScope hs(h);
+    return guard([&]() {
+        const bipart_params &q = *params;
+        return partition_to_device(h, make_params(q.k, q.epsilon, q.policy, q.levels, q.refine_iters, q.flags),
+                                   d_out_parts);
     });
 }
 

@@ -279,14 +279,14 @@ __device__ void blk_rebalance(Ctx &x, const DLevel &L, uint8_t *side, long long 
     if (threadIdx.x == 0) { st->warn = 0; st->rounds = 0; }
     __syncthreads();
     blk_side_weights(x, L, side);
-    if (threadIdx.x == 0) d_rebal_cond(st, limit, (long long)L.N + 1, x.status);
+    if (threadIdx.x == 0) d_rebal_cond(st, limit, limit, (long long)L.N + 1, x.status);
     __syncthreads();
     while (st->flag) {
         blk_gains(x, L, side);
         blk_select_apply(x, L, SEL_REBAL, s, side);
         d_rebal_move(x.gain, side, L.nw, x.list, st, s, reinterpret_cast<unsigned long long *>(x.smem));
         __syncthreads();
-        if (threadIdx.x == 0) d_rebal_cond(st, limit, (long long)L.N + 1, x.status);
+        if (threadIdx.x == 0) d_rebal_cond(st, limit, limit, (long long)L.N + 1, x.status);
         __syncthreads();
     }
 }

@@ -153,12 +153,8 @@ class Pool {
                     const bipart_instance &in = j->inst;
                     graph_load_host(ws.get(), in.num_nodes, in.num_hedges, in.hedge_offsets,
                                     in.hedge_pins, in.node_weights, in.hedge_weights);
-                    Params p;
-                    p.k = j->params.k;
-                    p.eps = j->params.epsilon;
-                    p.policy = j->params.policy;
-                    p.levels = j->params.levels;
-                    p.iters = j->params.refine_iters;
+                    const bipart_params &q = j->params;
+                    const Params p = make_params(q.k, q.epsilon, q.policy, q.levels, q.refine_iters, q.flags);
                     j->status = graph_partition_host(ws.get(), p, j->out);
                 } catch (const Fail &e) {
                     j->status = e.code;
@@ -235,7 +231,7 @@ extern "C" int bipart_partition_batch(int32_t n, const bipart_instance *instance
             const bipart_instance &in = instances[i];
             const bipart_params &p = params[i];
             try {
-                validate_params(p.k, p.epsilon, p.policy, p.levels, p.refine_iters);
+                make_params(p.k, p.epsilon, p.policy, p.levels, p.refine_iters, p.flags);  // validates
                 validate_host_csr(in.num_nodes, in.num_hedges, in.hedge_offsets, in.hedge_pins,
                                   in.node_weights, in.hedge_weights);
             } catch (const Fail &e) {
@@ -254,10 +250,16 @@ extern "C" int bipart_partition_batch(int32_t n, const bipart_instance *instance
         };
         by_size(blk);
         by_size(rest);
-        Pool pool(workers, 0);
+        // the worker pool exists only if some valid instance needs it (an all-invalid batch
+        // reports its validation errors without touching the GPU)
+        std::unique_ptr<Pool> pool_owner;
+        auto pool_ref = [&]() -> Pool & {
+            if (!pool_owner) pool_owner.reset(new Pool(workers, 0));
+            return *pool_owner;
+        };
         std::vector<int64_t> tickets(n, 0);
         for (int32_t i : rest)
-            if (st[i] == BIPART_OK) tickets[i] = pool.submit(instances[i], params[i], out_parts[i], false);
+            if (st[i] == BIPART_OK) tickets[i] = pool_ref().submit(instances[i], params[i], out_parts[i], false);
         if (!blk.empty()) {
             std::vector<BInst> bi(blk.size());
             std::vector<const int32_t *> ho(blk.size()), pi(blk.size()), nw(blk.size()), hw(blk.size());
@@ -273,7 +275,8 @@ extern "C" int bipart_partition_batch(int32_t n, const bipart_instance *instance
                 b.iters = p.refine_iters;
                 int64_t W = 0;
                 for (int32_t v = 0; v < in.num_nodes; ++v) W += in.node_weights ? in.node_weights[v] : 1;
-                b.limit = balance_limit(W, p.epsilon);
+                b.limit = balance_limit(W, 1, 2, make_params(p.k, p.epsilon, p.policy, p.levels,
+                                                              p.refine_iters, p.flags).e6);
                 b.status = 0;
                 ho[j] = in.num_hedges > 0 ? in.hedge_offsets : nullptr;
                 pi[j] = in.hedge_pins;
@@ -297,7 +300,7 @@ extern "C" int bipart_partition_batch(int32_t n, const bipart_instance *instance
             for (size_t j = 0; j < blk.size(); ++j) {
                 const int32_t i = blk[j];
                 if (bi[j].status == 2) {  // did not fit the block arena: single-instance path
-                    tickets[i] = pool.submit(instances[i], params[i], out_parts[i], false);
+                    tickets[i] = pool_ref().submit(instances[i], params[i], out_parts[i], false);
                     continue;
                 }
                 st[i] = bi[j].status ? BIPART_WARN_IMBALANCED : BIPART_OK;
@@ -307,7 +310,7 @@ extern "C" int bipart_partition_batch(int32_t n, const bipart_instance *instance
         for (int32_t i = 0; i < n; ++i) {
             if (!tickets[i]) continue;
             std::shared_ptr<Job> j;
-            pool.wait(tickets[i], -1, &j);
+            pool_ref().wait(tickets[i], -1, &j);
             st[i] = j ? j->status : BIPART_ERR_CUDA;
             if (j && st[i] < 0) err[i] = j->error;
         }

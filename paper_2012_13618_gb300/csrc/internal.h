@@ -121,7 +121,15 @@ struct Params {
     int32_t policy = 0;
     int32_t levels = 0;
     int32_t iters = 0;
+    int32_t flags = 0;      // BIPART_FLAG_*
+    // derived: the imbalance every bisection uses (millionths, after the adaptive rule) and the
+    // share of the bisection at hand (side 0 meant for m0 of m parts)
+    int64_t e6 = 0;
+    int32_t m0 = 1, m = 2;
 };
+// Checks the user parameters and fills the derived fields for the top-level bisection.
+Params make_params(int32_t k, double eps, int32_t policy, int32_t levels, int32_t iters,
+                   int32_t flags);
 
 // Result of one bisection kept for parity queries.
 struct Hierarchy {
@@ -205,15 +213,20 @@ int *degree_counters(bipart_graph *g, int32_t N);
 // -------------------------------------------------------------------- refinement (refine.cu)
 // Runs Algorithms 3, 5 (+ rebalance) over the hierarchy; writes side of level 0.  The status
 // (1 = the level-0 rebalance ran out of candidates) is left in *bisect_status_word(g).
-void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, int64_t limit, int32_t iters,
-               uint8_t *d_side0);
+// Side 0 is meant for m0 of m parts: Algorithm 3 grows it to that share and limit[s] bounds
+// side s (halving bisection: m0 / m = 1 / 2, equal limits).
+void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, const int64_t limit[2], int m0,
+               int m, int32_t iters, uint8_t *d_side0);
 const unsigned *bisect_status_word(bipart_graph *g);
 // Bytes at the start of the small scratch holding counters and selection state that phases
 // leave zero for the next one (cleared once at the start of every bisection).
 size_t small_state_bytes();
 void refine_init();  // once per process: kernel attributes (never during a capture)
 void coarsen_init();  // same, for the coarsening kernels
-int64_t balance_limit(int64_t W, double eps);
+// Weight limit of a side meant for ms of m parts of a (sub)graph of weight W, imbalance e6
+// millionths: max(ceil(W ms / m), floor(W ms (10^6 + e6) / (m 10^6))) (reading C12; G2 for
+// m != 2).
+int64_t balance_limit(int64_t W, int32_t ms, int32_t m, int64_t e6);
 
 // ------------------------------------------------------------------------- diagnostics
 // Brackets one kernel launch with CUDA events on `s` when profiling is on (see

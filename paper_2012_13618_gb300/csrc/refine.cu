@@ -130,14 +130,14 @@ k_side_weights(int N, const uint8_t *__restrict__ side, const int *__restrict__ 
 
 // Loop conditions; they also set the WHILE node's value `h` when the loop runs in a graph.
 __global__ void k_initial_cond(RState *st, long long max_rounds, uint32_t *status, int first,
-                               cudaGraphConditionalHandle h) {
-    d_initial_cond(st, max_rounds, status, first != 0);
+                               int m0, int m, cudaGraphConditionalHandle h) {
+    d_initial_cond(st, max_rounds, status, first != 0, m0, m);
     if (h && threadIdx.x == 0) cudaGraphSetConditional(h, st->flag ? 1u : 0u);
 }
 
-__global__ void k_rebal_cond(RState *st, long long limit, long long max_rounds, uint32_t *status,
-                             int first, cudaGraphConditionalHandle h) {
-    d_rebal_cond(st, limit, max_rounds, status, first != 0);
+__global__ void k_rebal_cond(RState *st, long long limit0, long long limit1, long long max_rounds,
+                             uint32_t *status, int first, cudaGraphConditionalHandle h) {
+    d_rebal_cond(st, limit0, limit1, max_rounds, status, first != 0);
     if (h && threadIdx.x == 0) cudaGraphSetConditional(h, st->flag ? 1u : 0u);
 }
 
@@ -158,10 +158,10 @@ __global__ void k_keep_status(RState *st) {
 }
 
 // ------------------------------------------------------------------------ host side
-int64_t balance_limit(int64_t W, double eps) {
-    long long e6 = llround(eps * 1e6);
-    int64_t a = (W + 1) / 2;
-    int64_t b = (W * (1000000 + e6)) / 2000000;
+int64_t balance_limit(int64_t W, int32_t ms, int32_t m, int64_t e6) {
+    const __int128 share = (__int128)W * ms;  // the side's share is share / m
+    const int64_t a = (int64_t)((share + m - 1) / m);
+    const int64_t b = (int64_t)(share * (1000000 + e6) / ((__int128)m * 1000000));
     return a > b ? a : b;
 }
 
@@ -241,8 +241,8 @@ void side_weights(bipart_graph *g, Level &L, const uint8_t *side) {
     BP_LAUNCH();
 }
 
-// Algorithm 3 on the coarsest level.
-void initial_partition(bipart_graph *g, Level &L, uint8_t *side, int *gain) {
+// Algorithm 3 on the coarsest level (side 0 grown to its share m0 / m).
+void initial_partition(bipart_graph *g, Level &L, uint8_t *side, int *gain, int m0, int m) {
     cudaStream_t s = g->stream;
     if (L.N == 0) return;
     RState *st = rstate(g);
@@ -250,12 +250,12 @@ void initial_partition(bipart_graph *g, Level &L, uint8_t *side, int *gain) {
     BP_CUDA(cudaMemsetAsync(side, 1, (size_t)L.N, s));
     side_weights(g, L, side);
     const cudaGraphConditionalHandle h = cond_handle(g);
-    k_initial_cond<<<1, 32, 0, s>>>(st, (long long)L.N + 1, dev_status(g), 1, h);
+    k_initial_cond<<<1, 32, 0, s>>>(st, (long long)L.N + 1, dev_status(g), 1, m0, m, h);
     BP_LAUNCH();
     device_while(g, h, &st->flag, (int64_t)L.N + 2, [&]() {
         compute_gains(g, L, side, gain);
         select_apply(g, L, SEL_INITIAL, sq, gain, side, nullptr);
-        k_initial_cond<<<1, 32, 0, g->stream>>>(st, (long long)L.N + 1, dev_status(g), 0, h);
+        k_initial_cond<<<1, 32, 0, g->stream>>>(st, (long long)L.N + 1, dev_status(g), 0, m0, m, h);
         BP_LAUNCH();
     });
 }
@@ -266,8 +266,8 @@ void refine_iter(bipart_graph *g, Level &L, uint8_t *side, int *gain) {
     select_apply(g, L, SEL_REFINE, 0, gain, side, nullptr);
 }
 
-// Rebalance of reading C13; leaves warn = 1 when it ran out of candidates.
-void rebalance(bipart_graph *g, Level &L, uint8_t *side, int *gain, int64_t limit) {
+// Rebalance of reading C13 with a limit per side; leaves warn = 1 when it ran out of candidates.
+void rebalance(bipart_graph *g, Level &L, uint8_t *side, int *gain, const int64_t limit[2]) {
     cudaStream_t s = g->stream;
     RState *st = rstate(g);
     const int64_t sq = ceil_sqrt64(L.N);
@@ -278,22 +278,24 @@ void rebalance(bipart_graph *g, Level &L, uint8_t *side, int *gain, int64_t limi
     const size_t smem = sizeof(unsigned long long) * (size_t)S;
     side_weights(g, L, side);
     const cudaGraphConditionalHandle h = cond_handle(g);
-    k_rebal_cond<<<1, 32, 0, s>>>(st, (long long)limit, (long long)L.N + 1, dev_status(g), 1, h);
+    k_rebal_cond<<<1, 32, 0, s>>>(st, (long long)limit[0], (long long)limit[1], (long long)L.N + 1,
+                                  dev_status(g), 1, h);
     BP_LAUNCH();
     device_while(g, h, &st->flag, (int64_t)L.N + 2, [&]() {
         compute_gains(g, L, side, gain);
         select_apply(g, L, SEL_REBAL, sq, gain, side, list);
         k_rebal_move<<<1, 1024, smem, g->stream>>>(gain, side, L.nw(), list, st, sq);
         BP_LAUNCH();
-        k_rebal_cond<<<1, 32, 0, g->stream>>>(st, (long long)limit, (long long)L.N + 1, dev_status(g), 0, h);
+        k_rebal_cond<<<1, 32, 0, g->stream>>>(st, (long long)limit[0], (long long)limit[1],
+                                              (long long)L.N + 1, dev_status(g), 0, h);
         BP_LAUNCH();
     });
 }
 
 }  // namespace
 
-void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, int64_t limit, int32_t iters,
-               uint8_t *d_side0) {
+void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, const int64_t limit[2], int m0,
+               int m, int32_t iters, uint8_t *d_side0) {
     cudaStream_t s = g->stream;
     const int Lc = (int)levels.size() - 1;
     int64_t nmax = 1, emax = 1;
@@ -310,7 +312,7 @@ void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, int64_t limit, int
     BP_CUDA(cudaMemsetAsync(n1, 0, sizeof(int) * (size_t)emax, s));
 
     uint8_t *cur = sa, *other = sb;
-    initial_partition(g, *levels[Lc], cur, gain);
+    initial_partition(g, *levels[Lc], cur, gain, m0, m);
     for (int l = Lc; l >= 0; --l) {
         Level *L = levels[l];
         s = g->stream;

@@ -31,7 +31,7 @@ struct RState {
     SelGroup g[2];
     unsigned hist[2][kHistBins];
     unsigned long long W[2];   // side weights
-    long long limit, room, need;
+    long long limit[2], room, need;  // per-side limits of the current rebalance
     int heavy;                 // rebalance: heavy side or -1
     unsigned list_count;       // rebalance: selected nodes
     unsigned flag;             // loop-continue flag
@@ -346,12 +346,15 @@ __device__ void d_side_weights(Team t, int N, const uint8_t *side, const int *nw
     }
 }
 
-// Algorithm 3 loop condition: continue while P0 is lighter than P1 (guarded).  One thread acts.
+// Algorithm 3 loop condition: continue while P0 is below its share, m * W0 < m0 * (W0 + W1)
+// (side 0 meant for m0 of m parts; m0 / m = 1 / 2 is "P0 lighter than P1").  Guarded; one
+// thread acts.
 __device__ inline void d_initial_cond(RState *st, long long max_rounds, uint32_t *status,
-                                      bool first = false) {
+                                      bool first = false, int m0 = 1, int m = 2) {
     if (threadIdx.x != 0) return;
     if (first) st->rounds = 0;
-    unsigned f = (long long)st->W[0] < (long long)st->W[1];
+    const long long W0 = (long long)st->W[0], W1 = (long long)st->W[1];
+    unsigned f = (long long)m * W0 < (long long)m0 * (W0 + W1);
     if (f && (long long)(st->rounds++) >= max_rounds) {
         record_error(status, DEV_TIMEOUT);
         f = 0;
@@ -361,22 +364,24 @@ __device__ inline void d_initial_cond(RState *st, long long max_rounds, uint32_t
 
 // Rebalance loop condition (reading C13): heavy side above the limit and candidates left.  One
 // thread acts.
-__device__ inline void d_rebal_cond(RState *st, long long limit, long long max_rounds, uint32_t *status,
-                                    bool first = false) {
+// Side s may hold up to limit_s (both equal for a halving bisection).
+__device__ inline void d_rebal_cond(RState *st, long long limit0, long long limit1,
+                                    long long max_rounds, uint32_t *status, bool first = false) {
     if (threadIdx.x != 0) return;
     if (first) {
         st->rounds = 0;
         st->warn = 0;
     }
-    st->limit = limit;
+    st->limit[0] = limit0;
+    st->limit[1] = limit1;
     long long W0 = (long long)st->W[0], W1 = (long long)st->W[1];
-    int H = W0 > limit ? 0 : (W1 > limit ? 1 : -1);
+    int H = W0 > limit0 ? 0 : (W1 > limit1 ? 1 : -1);
     st->heavy = H;
     unsigned f = H >= 0 && !st->warn;
     if (H >= 0) {
         long long Wh = H ? W1 : W0, Wo = H ? W0 : W1;
-        st->room = limit - Wo;
-        st->need = Wh - limit;
+        st->room = (H ? limit0 : limit1) - Wo;
+        st->need = Wh - (H ? limit1 : limit0);
     }
     if (f && (long long)(st->rounds++) >= max_rounds) {
         record_error(status, DEV_TIMEOUT);

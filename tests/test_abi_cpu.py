@@ -84,3 +84,19 @@ def test_batch_and_server_argument_checks():
     assert lib.bipart_server_submit(None, None, None, None, None) == bp.ERR_INVALID_ARG
     assert lib.bipart_server_wait(None, 1, 0, None, None, None) == bp.ERR_INVALID_ARG
     lib.bipart_server_destroy(None)
+
+
+def test_params_validation_before_any_device_work():
+    # any k >= 1 is valid (readings G1-G2); k <= 0 and unknown flag bits are rejected on the host
+    lib = bp.load()
+    g = {"N": 4, "hoff": [0, 2, 4], "pins": [0, 1, 2, 3]}
+    for k, flags in [(0, 0), (-3, 0), (2, 2), (3, 1 << 5)]:
+        inst, keep = bp._instance(g)
+        par = bp.Params(k, 0.1, 0, 25, 2, flags)
+        out = np.empty(4, np.int32)
+        outs = (ctypes.c_void_p * 1)(out.ctypes.data)
+        sts = np.zeros(1, np.int32)
+        rc = lib.bipart_partition_batch(1, ctypes.byref(inst), ctypes.byref(par), outs,
+                                        ctypes.c_void_p(sts.ctypes.data), 1)
+        assert rc == bp.ERR_INVALID_ARG, (k, flags, rc)
+    assert lib.bipart_partition_ex(None, None, None) == bp.ERR_INVALID_ARG

@@ -162,3 +162,17 @@ def test_design_space_sweep_matches_oracle_and_frontier():
 def test_pareto_helper():
     from paper_2012_13618_gb300.sweep import pareto
     assert pareto([(1, 5), (2, 3), (3, 4), (2, 3), (0.5, 9)]) == [0, 1, 3, 4]
+
+
+def test_batch_general_k_matches_single():
+    # the worker pool runs k = 3 / 6 (adaptive) requests exactly as bipart_partition does
+    import paper_2012_13618_gb300 as bp
+    graphs = [synth.uniform(2000 + 300 * i, 2100 + 300 * i, 2, 6, seed=60 + i) for i in range(4)]
+    params = [dict(k=3, eps=0.05, policy="LDH", levels=25, iters=2, adaptive_eps=bool(i % 2))
+              for i in range(2)] + [dict(k=6, eps=0.05, policy="LDH", levels=25, iters=2,
+                                         adaptive_eps=bool(i % 2)) for i in range(2)]
+    parts, sts = bp.partition_batch(graphs, params, workers=3)
+    for i, g in enumerate(graphs):
+        ref, rst = oracle.partition(oracle.Hypergraph.from_dict(g), params[i]["k"], 0.05, "LDH", 25, 2,
+                                    adaptive=params[i]["adaptive_eps"])
+        assert np.array_equal(parts[i], ref) and sts[i] == rst

@@ -151,6 +151,39 @@ def test_kway_small(k):
         assert h.cut(parts) == oracle.cut(hr, parts)
 
 
+@pytest.mark.parametrize("k", [3, 5, 6, 7, 12])
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_general_k_small(k, adaptive):
+    # readings G1-G3: any k, proportional targets, optional per-bisection imbalance
+    import torch
+    bp = _bp()
+    g = synth.uniform(3000, 3200, 2, 6, seed=22)
+    g["nw"] = np.random.default_rng(7).integers(1, 4, size=g["N"]).astype(np.int32)
+    hr = oracle.Hypergraph.from_dict(g)
+    ref, rst = oracle.partition(hr, k, 0.1, "LDH", 25, 2, adaptive=adaptive)
+    with bp.create_from(g) as h:
+        parts, st = h.partition(k, 0.1, "LDH", 25, 2, adaptive_eps=adaptive)
+        assert np.array_equal(parts, ref)
+        assert st == rst
+        assert h.cut(parts) == oracle.cut(hr, parts)
+        # the device-output form and a second call (graph replay of the top bisection) agree
+        out = torch.empty(hr.N, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            st2 = h.partition_device(out, k, 0.1, "LDH", 25, 2, adaptive_eps=adaptive)
+            torch.cuda.synchronize()
+            assert st2 == rst and np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_netlist_100k_general_k():
+    bp = _bp()
+    g = synth.c1_netlist(N=100_000)
+    hr = oracle.Hypergraph.from_dict(g)
+    ref, rst = oracle.partition(hr, 10, 0.05, "LDH", 25, 2, adaptive=True)
+    with bp.create_from(g) as h:
+        parts, st = h.partition(10, 0.05, "LDH", 25, 2, adaptive_eps=True)
+        assert np.array_equal(parts, ref) and st == rst
+
+
 def test_netlist_100k_kway16():
     bp = _bp()
     g = synth.c1_netlist(N=100_000)
