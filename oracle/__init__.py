@@ -85,6 +85,9 @@ def _load():
                 "orc_limit_part": (_i64, [_i64, _i32, _i32, _i64]),
                 "orc_adaptive_e6": (_i64, [_i64, _i32]),
                 "orc_bisect_target": (_vp, [_vp, _i64, _i32, _i32, ctypes.c_int, _i32, _i32]),
+                "orc_bisect_ex": (_vp, [_vp, _i64, _i32, _i32, ctypes.c_int, ctypes.c_int, _i32, _i32]),
+                "orc_coarsen_ex": (_vp, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+                "orc_merge_parallel": (None, [_vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -182,6 +185,22 @@ def match(g: Hypergraph, policy) -> np.ndarray:
     return out
 
 
+def coarsen_merge(g: Hypergraph, policy):
+    """Algorithm 2 followed by reading M1 (parallel nets merged): (coarse, cmap, match)."""
+    cm = np.empty(max(g.N, 1), np.int32)
+    mt = np.empty(max(g.N, 1), np.int32)
+    h = _load().orc_coarsen_ex(g._h, _policy(policy), 1, _ptr(cm), _ptr(mt))
+    return Hypergraph(h), cm[: g.N], mt[: g.N]
+
+
+def merge_parallel(g: Hypergraph) -> "Hypergraph":
+    """Reading M1 applied to a copy of g."""
+    a = g.arrays()
+    h = Hypergraph.from_csr(g.N, a["hoff"], a["pins"], a["nw"], a["hw"])
+    _load().orc_merge_parallel(h._h)
+    return h
+
+
 def coarsen(g: Hypergraph, policy):
     """One level of Algorithm 2: returns (coarse Hypergraph, cmap, match)."""
     cmap = np.empty(max(g.N, 1), np.int32)
@@ -234,17 +253,18 @@ def adaptive_e6(e6: int, k: int) -> int:
 
 
 def bisect(g: Hypergraph, eps=0.1, policy="LDH", levels=25, iters=2, keep_levels=True,
-           target=None, e6=None):
+           target=None, e6=None, merge=False):
     """Multilevel bisection: dict(side, status, nlev, init_rounds, limit, levels, cmaps, matches).
     `target` = (m0, m): side 0 meant for m0 of m parts (reading G2); `e6` overrides eps with an
     imbalance in millionths."""
     L = _load()
-    if target is None and e6 is None:
+    if target is None and e6 is None and not merge:
         r = L.orc_bisect(g._h, float(eps), _policy(policy), int(levels), int(iters))
     else:
         m0, m = target if target is not None else (1, 2)
         e = int(e6) if e6 is not None else _e6(eps)
-        r = L.orc_bisect_target(g._h, e, int(m0), int(m), _policy(policy), int(levels), int(iters))
+        r = L.orc_bisect_ex(g._h, e, int(m0), int(m), 1 if merge else 0, _policy(policy),
+                            int(levels), int(iters))
     try:
         nlev = L.orc_run_nlev(r)
         side = np.empty(max(g.N, 1), np.uint8)
@@ -287,14 +307,17 @@ def subgraph(g: Hypergraph, part, j: int):
     return s, l2g[: s.N]
 
 
-def partition(g: Hypergraph, k=2, eps=0.1, policy="LDH", levels=25, iters=2, adaptive=False):
+def partition(g: Hypergraph, k=2, eps=0.1, policy="LDH", levels=25, iters=2, adaptive=False,
+              merge=False):
     """Nested k-way (Algorithm 6, any k >= 1 by readings G1-G2; `adaptive`: the per-bisection
-    imbalance of reading G3): returns (parts int32[N], status)."""
+    imbalance of reading G3; `merge`: parallel nets merged at contraction, reading M1): returns
+    (parts int32[N], status)."""
     part = np.empty(max(g.N, 1), np.int32)
-    if not adaptive:
+    if not adaptive and not merge:
         st = _load().orc_partition(g._h, int(k), float(eps), _policy(policy), int(levels),
                                    int(iters), _ptr(part))
     else:
-        st = _load().orc_partition_ex(g._h, int(k), _e6(eps), 1, _policy(policy),
+        flags = (1 if adaptive else 0) | (2 if merge else 0)
+        st = _load().orc_partition_ex(g._h, int(k), _e6(eps), flags, _policy(policy),
                                       int(levels), int(iters), _ptr(part))
     return part[: g.N], int(st)

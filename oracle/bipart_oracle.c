@@ -13,7 +13,7 @@
  *   normalise      input hyperedges -> sorted unique pins, drop < 2 pins (reading C10)
  *   match          Algorithm 1 (Sec. 3.1.1): three min passes; hash = MurmurHash3 fmix32 (C1-C3)
  *   coarsen        Algorithm 2 (Sec. 3.1.2): merge matched sets, attach singletons, contract
- *                  (C4-C9)
+ *                  (C4-C9); optionally merge parallel nets of the contracted level (M1)
  *   gains          Algorithm 4 (Sec. 3.2): move gains from per-hyperedge side counts, weighted
  *                  by hyperedge weight (weighted cut, Sec. 1.1)
  *   initial        Algorithm 3 (Sec. 3.2): grow P0 by the top ceil(sqrt n) gains (C14)
@@ -43,8 +43,15 @@ enum { POL_LDH = 0, POL_HDH = 1, POL_LWD = 2, POL_HWD = 3, POL_RAND = 4 };
 /* Refinement admits nodes whose gain is at least this value (Algorithm 5 filters gain >= 0). */
 #define REFINE_MIN_GAIN 0
 
+#define ORC_FLAG_ADAPTIVE 1
+#define ORC_FLAG_MERGE 2
+
 struct orc_hg;
 struct orc_run;
+struct orc_hg *orc_coarsen_ex(const struct orc_hg *g, int policy, int merge, int32_t *cmap,
+                              int32_t *match_out);
+struct orc_run *orc_bisect_ex(const struct orc_hg *g0, int64_t e6, int32_t m0, int32_t m,
+                              int merge, int policy, int32_t levels, int32_t iters);
 int32_t orc_initial_target(const struct orc_hg *g, uint8_t *side, int32_t m0, int32_t m);
 int orc_rebalance2(const struct orc_hg *g, uint8_t *side, int64_t limit0, int64_t limit1,
                    int32_t *rounds_out);
@@ -212,7 +219,63 @@ void orc_match(const orc_hg *g, int policy, int32_t *hedgeid) {
  *     coarse hyperedge (ascending fine id) with sorted unique pins and the same weight.
  * cmap[v] receives the coarse node of fine node v.  The matching is returned in match (N).
  * ------------------------------------------------------------------------------------------ */
+/* ------------------------------------------------------------------------------------------
+ * Reading M1 (a switch, off by default; the paper never merges hyperedges): parallel nets of a
+ * contracted level -- coarse hyperedges with the same sorted pin list -- become the one with the
+ * smallest id, which keeps its place and carries the sum of their weights; the others are
+ * dropped.  Every cut is unchanged, since identical nets are cut together.
+ * ------------------------------------------------------------------------------------------ */
+static const orc_hg *g_lists;  /* hyperedges compared by cmp_lists (single-threaded oracle) */
+
+static int cmp_lists(const void *pa, const void *pb) {
+    int32_t a = *(const int32_t *)pa, b = *(const int32_t *)pb;
+    int32_t da = g_lists->off[a + 1] - g_lists->off[a], db = g_lists->off[b + 1] - g_lists->off[b];
+    const int32_t *la = g_lists->pin + g_lists->off[a], *lb = g_lists->pin + g_lists->off[b];
+    for (int32_t i = 0; i < da && i < db; i++)
+        if (la[i] != lb[i]) return la[i] < lb[i] ? -1 : 1;
+    if (da != db) return da < db ? -1 : 1;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+static int same_list(const orc_hg *c, int32_t a, int32_t b) {
+    int32_t da = c->off[a + 1] - c->off[a], db = c->off[b + 1] - c->off[b];
+    if (da != db) return 0;
+    return memcmp(c->pin + c->off[a], c->pin + c->off[b], sizeof(int32_t) * (size_t)da) == 0;
+}
+
+void orc_merge_parallel(orc_hg *c) {
+    int32_t E = c->E;
+    if (E < 2) return;
+    int32_t *idx = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)E);
+    int32_t *rep = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)E);
+    int64_t *w = (int64_t *)xcalloc((size_t)E, sizeof(int64_t));
+    for (int32_t e = 0; e < E; e++) idx[e] = e;
+    g_lists = c;
+    qsort(idx, (size_t)E, sizeof(int32_t), cmp_lists);
+    for (int32_t i = 0; i < E; i++) {
+        /* runs of equal lists are sorted by id: the run's first is the smallest id */
+        rep[idx[i]] = (i > 0 && same_list(c, idx[i], idx[i - 1])) ? rep[idx[i - 1]] : idx[i];
+    }
+    for (int32_t e = 0; e < E; e++) w[rep[e]] += c->hwt[e];
+    int32_t ne = 0, np = 0;
+    for (int32_t e = 0; e < E; e++) {
+        if (rep[e] != e) continue;
+        int32_t a = c->off[e], d = c->off[e + 1] - a;
+        memmove(c->pin + np, c->pin + a, sizeof(int32_t) * (size_t)d);
+        c->hwt[ne] = (int32_t)w[e];
+        np += d;
+        c->off[++ne] = np;
+    }
+    c->E = ne;
+    free(idx); free(rep); free(w);
+}
+
 orc_hg *orc_coarsen(const orc_hg *g, int policy, int32_t *cmap, int32_t *match_out) {
+    return orc_coarsen_ex(g, policy, 0, cmap, match_out);
+}
+
+/* Algorithm 2, then (with `merge`) reading M1 on the contracted level. */
+orc_hg *orc_coarsen_ex(const orc_hg *g, int policy, int merge, int32_t *cmap, int32_t *match_out) {
     int32_t N = g->N, E = g->E;
     int32_t *hedgeid = match_out ? match_out : (int32_t *)xmalloc(sizeof(int32_t) * (size_t)N);
     orc_match(g, policy, hedgeid);
@@ -290,6 +353,7 @@ orc_hg *orc_coarsen(const orc_hg *g, int policy, int32_t *cmap, int32_t *match_o
         c->off[++ne] = np;
     }
     c->E = ne;
+    if (merge) orc_merge_parallel(c);
 
     free(grp_first); free(merged); free(parent); free(mergedw); free(Ssize);
     if (!match_out) free(hedgeid);
@@ -547,6 +611,12 @@ orc_run *orc_bisect(const orc_hg *g0, double eps, int policy, int32_t levels, in
  * in millionths.  m0 / m = 1 / 2 is orc_bisect. */
 orc_run *orc_bisect_target(const orc_hg *g0, int64_t e6, int32_t m0, int32_t m, int policy,
                            int32_t levels, int32_t iters) {
+    return orc_bisect_ex(g0, e6, m0, m, 0, policy, levels, iters);
+}
+
+/* The same with `merge` (reading M1) applied to every contracted level. */
+orc_run *orc_bisect_ex(const orc_hg *g0, int64_t e6, int32_t m0, int32_t m, int merge, int policy,
+                       int32_t levels, int32_t iters) {
     orc_run *r = (orc_run *)xcalloc(1, sizeof(orc_run));
     int32_t cap = levels + 1;
     r->lev = (orc_hg **)xcalloc((size_t)cap, sizeof(orc_hg *));
@@ -558,7 +628,7 @@ orc_run *orc_bisect_target(const orc_hg *g0, int64_t e6, int32_t m0, int32_t m, 
         const orc_hg *f = r->lev[r->nlev - 1];
         int32_t *cm = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(f->N > 0 ? f->N : 1));
         int32_t *mt = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(f->N > 0 ? f->N : 1));
-        orc_hg *c = orc_coarsen(f, policy, cm, mt);
+        orc_hg *c = orc_coarsen_ex(f, policy, merge, cm, mt);
         if (c->N == f->N) { orc_hg_free(c); free(cm); free(mt); break; }
         r->cmap[r->nlev - 1] = cm;
         r->match[r->nlev - 1] = mt;
@@ -680,14 +750,15 @@ orc_hg *orc_subgraph(const orc_hg *g, const int32_t *part, int32_t j, int32_t *l
  * (targets and limits in proportion, G2); its side-0 nodes own [lo, lo + m0), its side-1 nodes
  * [lo + m0, lo + m); a range of one part is final.  Subgraphs are built as in C16 and bisected
  * with the same policy, levels and iters, and with e6 millionths of imbalance (or, with
- * `adaptive`, the per-bisection e6 of reading G3).  For k a power of two this is the paper's
+ * ORC_FLAG_ADAPTIVE, the per-bisection e6 of reading G3; ORC_FLAG_MERGE: reading M1).  For k a power of two this is the paper's
  * scheme: every split is in halves and the parts of a tree level are 2j, 2j + 1.  Returns
  * ORC_WARN_IMBALANCED if any bisection ended above its limit.
  * ------------------------------------------------------------------------------------------ */
-int orc_partition_ex(const orc_hg *g, int32_t k, int64_t e6, int adaptive, int policy,
+int orc_partition_ex(const orc_hg *g, int32_t k, int64_t e6, int flags, int policy,
                      int32_t levels, int32_t iters, int32_t *part) {
     if (k < 1) return ORC_ERR_INVALID_ARG;
-    const int64_t eb = adaptive ? orc_adaptive_e6(e6, k) : e6;
+    const int64_t eb = (flags & ORC_FLAG_ADAPTIVE) ? orc_adaptive_e6(e6, k) : e6;
+    const int merge = (flags & ORC_FLAG_MERGE) != 0;
     for (int32_t v = 0; v < g->N; v++) part[v] = 0;  /* every node in the range starting at 0 */
     int status = ORC_OK;
     int32_t *l2g = (int32_t *)xmalloc(sizeof(int32_t) * (size_t)(g->N > 0 ? g->N : 1));
@@ -706,7 +777,7 @@ int orc_partition_ex(const orc_hg *g, int32_t k, int64_t e6, int adaptive, int p
             if (m < 2) continue;
             const int32_t m0 = (m + 1) / 2;
             orc_hg *s = orc_subgraph(g, part, lo, l2g);
-            orc_run *run = orc_bisect_target(s, eb, m0, m, policy, levels, iters);
+            orc_run *run = orc_bisect_ex(s, eb, m0, m, merge, policy, levels, iters);
             if (run->status != ORC_OK) status = run->status;
             for (int32_t i = 0; i < s->N; i++) part[l2g[i]] = run->side[i] ? lo + m0 : lo;
             orc_run_free(run);
