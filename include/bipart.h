@@ -93,6 +93,12 @@ int bipart_partition_device(bipart_handle h, int32_t k, double epsilon, int32_t 
  * imbalance e' (in millionths) with (1 + e')^L <= 1 + epsilon, L = ceil(log2 k), so that the
  * nested allowances multiply to at most 1 + epsilon (reading G3; no effect for k <= 2). */
 #define BIPART_FLAG_ADAPTIVE_EPS 1
+/* MERGE_PARALLEL: when a level is contracted (Algorithm 2), coarse hyperedges with the same
+ * sorted pin list are merged into the one with the smallest id, which carries the sum of their
+ * weights (reading M1; the paper never merges, so this is off by default).  Every cut is
+ * unchanged; coarse hyperedge weights then differ from 1, which gives the weight-based matching
+ * policies (LWD, HWD, Table 1) something to order by.  The input level is not merged. */
+#define BIPART_FLAG_MERGE_PARALLEL 2
 
 /* Levels of the hierarchy kept from the last k = 2 call (level 0 = the normalised input). */
 int bipart_num_levels(bipart_handle h, int32_t *num_levels);

@@ -51,6 +51,7 @@ class Params(ctypes.Structure):
 
 
 FLAG_ADAPTIVE_EPS = 1
+FLAG_MERGE_PARALLEL = 2
 
 
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -223,13 +224,15 @@ class Handle:
     def set_stream(self, stream):
         _check(load().bipart_set_stream(self._h, _stream_ptr(stream)))
 
-    def partition(self, k=2, eps=0.1, policy="LDH", levels=25, iters=2, adaptive_eps=False):
+    def partition(self, k=2, eps=0.1, policy="LDH", levels=25, iters=2, adaptive_eps=False,
+                  merge_parallel=False):
         """Returns (parts int32[N] on the host, status).  Any k >= 1; `adaptive_eps` gives every
-        bisection of a k-way partition the per-bisection imbalance (BIPART_FLAG_ADAPTIVE_EPS)."""
+        bisection of a k-way partition the per-bisection imbalance (BIPART_FLAG_ADAPTIVE_EPS);
+        `merge_parallel` merges parallel nets at contraction (BIPART_FLAG_MERGE_PARALLEL)."""
         N = self.sizes()[0]
         out = np.empty(max(N, 1), np.int32)
-        if adaptive_eps:
-            p = _params(k, eps, policy, levels, iters, adaptive_eps)
+        if adaptive_eps or merge_parallel:
+            p = _params(k, eps, policy, levels, iters, adaptive_eps, merge_parallel)
             st = _check(load().bipart_partition_ex(self._h, ctypes.byref(p), _ptr(out)))
         else:
             st = _check(load().bipart_partition(self._h, int(k), float(eps), _policy(policy),
@@ -237,10 +240,10 @@ class Handle:
         return out[:N], st
 
     def partition_device(self, out, k=2, eps=0.1, policy="LDH", levels=25, iters=2,
-                         adaptive_eps=False):
+                         adaptive_eps=False, merge_parallel=False):
         """Writes parts into the int32 CUDA tensor `out` (asynchronously on the handle's stream)."""
-        if adaptive_eps:
-            p = _params(k, eps, policy, levels, iters, adaptive_eps)
+        if adaptive_eps or merge_parallel:
+            p = _params(k, eps, policy, levels, iters, adaptive_eps, merge_parallel)
             return _check(load().bipart_partition_device_ex(self._h, ctypes.byref(p),
                                                             ctypes.c_void_p(out.data_ptr())))
         return _check(load().bipart_partition_device(self._h, int(k), float(eps), _policy(policy),
@@ -322,9 +325,11 @@ def _instance(g):
     return inst, arrs
 
 
-def _params(k=2, eps=0.1, policy="LDH", levels=25, iters=2, adaptive_eps=False):
+def _params(k=2, eps=0.1, policy="LDH", levels=25, iters=2, adaptive_eps=False,
+            merge_parallel=False):
     return Params(int(k), float(eps), _policy(policy), int(levels), int(iters),
-                  FLAG_ADAPTIVE_EPS if adaptive_eps else 0)
+                  (FLAG_ADAPTIVE_EPS if adaptive_eps else 0) |
+                  (FLAG_MERGE_PARALLEL if merge_parallel else 0))
 
 
 def partition_batch(graphs, params, workers=0):

@@ -473,7 +473,7 @@ void bisect_body(bipart_graph *g, Level &L0, const Params &p, int64_t W, uint8_t
         size_t idx = levels.size() - 1;
         if (g->lev.size() <= idx) g->lev.emplace_back(new Level);
         Level &c = *g->lev[idx];
-        coarsen_level(g, f, c, p.policy, level_sizes(g, (int)idx));
+        coarsen_level(g, f, c, p.policy, level_sizes(g, (int)idx), (p.flags & BIPART_FLAG_MERGE_PARALLEL) != 0);
         if (c.N == f.N) break;
         levels.push_back(&c);
     }
@@ -547,7 +547,7 @@ void capture_plan(bipart_graph *g, const Params &p, uint8_t *d_side, int nlev, i
 
 bool same_params(const Params &a, const Params &b) {
     return a.policy == b.policy && a.levels == b.levels && a.iters == b.iters && a.e6 == b.e6 &&
-           a.m0 == b.m0 && a.m == b.m;
+           a.m0 == b.m0 && a.m == b.m && a.flags == b.flags;
 }
 
 // Bisection of the handle's level 0.  First call with given parameters: eager, recording the
@@ -722,7 +722,8 @@ int64_t adaptive_e6(int64_t e6, int32_t k) {
 Params make_params(int32_t k, double eps, int32_t policy, int32_t levels, int32_t iters,
                    int32_t flags) {
     validate_params(k, eps, policy, levels, iters);
-    if (flags & ~BIPART_FLAG_ADAPTIVE_EPS) throw Fail{BIPART_ERR_INVALID_ARG, "unknown flags"};
+    if (flags & ~(BIPART_FLAG_ADAPTIVE_EPS | BIPART_FLAG_MERGE_PARALLEL))
+        throw Fail{BIPART_ERR_INVALID_ARG, "unknown flags"};
     Params p;
     p.k = k;
     p.eps = eps;

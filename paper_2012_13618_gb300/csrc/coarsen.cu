@@ -212,6 +212,145 @@ __global__ void k_cmap(int N, const int *__restrict__ grp, const int *__restrict
     d_cmap(GridTeam(), N, grp, gcid, nw, cmap, cw);
 }
 
+// ------------------------------------------------------------------ parallel-net merging
+// Reading M1 (a switch, off by default): after contraction, hyperedges with the same sorted pin
+// list become the smallest-id one with the summed weight.  Groups are found without sorting:
+// a fingerprint per list (sum of SplitMix64-mixed (position, pin) terms, so the partial sums can
+// be combined in any order), an open-addressing table giving the smallest id per fingerprint,
+// an exact list comparison against it, and an exact scan for the (practically never) hyperedges
+// whose fingerprint collided with a different list.
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_merge_clear(int E, int T, unsigned long long *__restrict__ fp,
+                              int *__restrict__ wsum, unsigned long long *__restrict__ tkey,
+                              int *__restrict__ tmin, unsigned *__restrict__ flag) {
+    const int n = E > T ? E : T;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (i < E) {
+            fp[i] = 0ull;
+            wsum[i] = 0;
+        }
+        if (i < T) {
+            tkey[i] = 0ull;
+            tmin[i] = INT_MAX;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *flag = 0u;
+}
+
+__global__ void __launch_bounds__(kLbBlock)
+k_merge_fp(int E, int P, const int *__restrict__ hoff, const int *__restrict__ scratch,
+           const int *__restrict__ cnt, unsigned long long *__restrict__ fp,
+           const int *__restrict__ ts) {
+    lb_runs(
+        hoff, E, P,
+        [&](int e, int a, int b) {
+            const int c = cnt[e];
+            if (c < 2) return;
+            const int base = hoff[e];
+            const int stop = base + c < b ? base + c : b;
+            unsigned long long acc = 0;
+            for (int i = a; i < stop; ++i)
+                acc += splitmix64(((uint64_t)(uint32_t)(i - base) << 32) | (uint32_t)scratch[i]);
+            if (stop > a) atomicAdd(fp + e, acc);
+        },
+        GridTeam(), ts);
+}
+
+// Final key of a kept list (its length mixed in; 0 marks an empty table slot).
+__device__ __forceinline__ unsigned long long merge_key(unsigned long long f, int c) {
+    unsigned long long k = f ^ splitmix64(0xFFFFFFFF00000000ull | (uint32_t)c);
+    return k ? k : 1ull;
+}
+
+__global__ void k_merge_insert(int E, int T, const int *__restrict__ cnt,
+                               unsigned long long *__restrict__ fp,
+                               unsigned long long *__restrict__ tkey, int *__restrict__ tmin) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+        const int c = cnt[e];
+        if (c < 2) continue;
+        const unsigned long long k = merge_key(fp[e], c);
+        fp[e] = k;
+        unsigned slot = (unsigned)(k & (unsigned long long)(T - 1));
+        for (int probe = 0; probe < T; ++probe) {  // the table is at least twice the key count
+            const unsigned long long prev = atomicCAS(tkey + slot, 0ull, k);
+            if (prev == 0ull || prev == k) {
+                atomicMin(tmin + slot, e);
+                break;
+            }
+            slot = (slot + 1) & (unsigned)(T - 1);
+        }
+    }
+}
+
+__device__ __forceinline__ bool same_list(const int *scratch, const int *hoff, int a, int b, int c) {
+    const int *la = scratch + hoff[a], *lb = scratch + hoff[b];
+    for (int i = 0; i < c; ++i)
+        if (la[i] != lb[i]) return false;
+    return true;
+}
+
+// rep[e] = smallest id with e's list; -1 - e when the fingerprint's smallest id has another list
+// (a collision, settled by k_merge_exact).
+__global__ void k_merge_rep(int E, int T, const int *__restrict__ hoff, const int *__restrict__ scratch,
+                            const int *__restrict__ cnt, const unsigned long long *__restrict__ fp,
+                            const unsigned long long *__restrict__ tkey, const int *__restrict__ tmin,
+                            int *__restrict__ rep, unsigned *__restrict__ flag) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+        const int c = cnt[e];
+        if (c < 2) {
+            rep[e] = e;
+            continue;
+        }
+        const unsigned long long k = fp[e];
+        unsigned slot = (unsigned)(k & (unsigned long long)(T - 1));
+        int r = e;
+        for (int probe = 0; probe < T; ++probe) {
+            if (tkey[slot] == k) {
+                r = tmin[slot];
+                break;
+            }
+            slot = (slot + 1) & (unsigned)(T - 1);
+        }
+        if (r == e || (cnt[r] == c && same_list(scratch, hoff, r, e, c))) {
+            rep[e] = r;
+        } else {
+            rep[e] = -1 - e;
+            atomicOr(flag, 1u);
+        }
+    }
+}
+
+__global__ void k_merge_exact(int E, const int *__restrict__ hoff, const int *__restrict__ scratch,
+                              const int *__restrict__ cnt, const unsigned long long *__restrict__ fp,
+                              int *__restrict__ rep, const unsigned *__restrict__ flag) {
+    if (*flag == 0u) return;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+        if (rep[e] >= 0) continue;
+        const int c = cnt[e];
+        int r = e;
+        for (int q = 0; q < e; ++q) {
+            if (cnt[q] == c && fp[q] == fp[e] && same_list(scratch, hoff, q, e, c)) {
+                r = q;
+                break;
+            }
+        }
+        rep[e] = r;
+    }
+}
+
+__global__ void k_merge_weights(int E, const int *__restrict__ cnt, const int *__restrict__ hw,
+                                const int *__restrict__ rep, int *__restrict__ wsum) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
+        if (cnt[e] >= 2) atomicAdd(wsum + rep[e], hw ? hw[e] : 1);
+}
+
 // ------------------------------------------------------------------ host side
 namespace {
 
@@ -247,7 +386,7 @@ void seg_unique(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const in
 // sizes: two device ints receiving {E', P'}; ts_in: tile starts of the input CSR (or null).
 void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int *pins,
               const int *hw, const int *map, Level &c, int *deg, bool counters_zero, int32_t *sizes,
-              const int *ts_in) {
+              const int *ts_in, bool merge) {
     cudaStream_t s = g->stream;
     Work &w = g->w;
     int *scratch = (int *)w.p_a.ensure(sizeof(int) * (size_t)std::max(P, 1), s);
@@ -258,14 +397,39 @@ void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int 
     c.b_hoff.ensure(sizeof(int) * ((size_t)E + 1), s);
     c.b_pins.ensure(sizeof(int) * (size_t)std::max(P, 1), s);
     c.b_tsh.ensure(sizeof(int) * ((size_t)P / kTsGran + 2), s);
-    bool unit = (hw == nullptr);
+    merge = merge && E > 1;
+    bool unit = (hw == nullptr) && !merge;  // merged groups carry summed weights
     if (!unit) c.b_hw.ensure(sizeof(int) * (size_t)std::max(E, 1), s);
     c.unit_hw = unit;
+    int *rep = nullptr, *wsum = nullptr;
+    if (merge) {
+        int T = 1;
+        while (T < 2 * E) T <<= 1;
+        auto *fp = (unsigned long long *)w.m_fp.ensure(sizeof(uint64_t) * (size_t)E, s);
+        auto *tkey = (unsigned long long *)w.m_tkey.ensure(sizeof(uint64_t) * (size_t)T, s);
+        int *tmin = (int *)w.m_tmin.ensure(sizeof(int) * (size_t)T, s);
+        rep = (int *)w.m_rep.ensure(sizeof(int) * (size_t)E, s);
+        wsum = (int *)w.m_wsum.ensure(sizeof(int) * (size_t)E, s);
+        unsigned *flag = reinterpret_cast<unsigned *>(small + 6);
+        ProfScope ps("merge_parallel", 8.0 * P + 48.0 * E + 12.0 * T, s);
+        k_merge_clear<<<grid_for(std::max(E, T)), kBlock, 0, s>>>(E, T, fp, wsum, tkey, tmin, flag);
+        BP_LAUNCH();
+        k_merge_fp<<<lb_grid(P), kLbBlock, 0, s>>>(E, P, hoff, scratch, cnt, fp, ts_in);
+        BP_LAUNCH();
+        k_merge_insert<<<grid_for(E), kBlock, 0, s>>>(E, T, cnt, fp, tkey, tmin);
+        BP_LAUNCH();
+        k_merge_rep<<<grid_for(E), kBlock, 0, s>>>(E, T, hoff, scratch, cnt, fp, tkey, tmin, rep, flag);
+        BP_LAUNCH();
+        k_merge_exact<<<grid_for(E), kBlock, 0, s>>>(E, hoff, scratch, cnt, fp, rep, flag);
+        BP_LAUNCH();
+        k_merge_weights<<<grid_for(E), kBlock, 0, s>>>(E, cnt, hw, rep, wsum);
+        BP_LAUNCH();
+    }
     if (E > 0) {
-        CompactOut out{E, hw, c.hoff(), unit ? nullptr : c.b_hw.as<int>(), emap, sizes, c.tsh()};
+        CompactOut out{E, hw, c.hoff(), unit ? nullptr : c.b_hw.as<int>(), emap, sizes, c.tsh(), wsum};
         {
             ProfScope ps("contract_offsets", 16.0 * E, s);
-            scan(E, CompactIn{cnt}, out, w.scan.ensure_zero(scan_state_bytes(E), s), dev_status(g), s);
+            scan(E, CompactIn{cnt, rep}, out, w.scan.ensure_zero(scan_state_bytes(E), s), dev_status(g), s);
         }
         {
             // scratch, coarse pins, degree atomics, per-hyperedge offsets
@@ -340,7 +504,7 @@ void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t
     }
     L.N = N;
     contract(g, E, P, d_hoff, d_pins, d_hw, nullptr, L, degree_counters(g, N), false,
-             g->w.small.as<int32_t>() + 2, nullptr);
+             g->w.small.as<int32_t>() + 2, nullptr, false);
     L.b_nw.ensure(sizeof(int) * (size_t)std::max(N, 1), s);
     if (d_nw) {
         BP_CUDA(cudaMemcpyAsync(L.nw(), d_nw, sizeof(int) * (size_t)N, cudaMemcpyDeviceToDevice, s));
@@ -353,7 +517,7 @@ void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t
     L.b_match.ensure(sizeof(int) * (size_t)std::max(N, 1), s);
 }
 
-void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *sizes) {
+void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *sizes, bool merge) {
     cudaStream_t s = g->stream;
     Work &w = g->w;
     const int N = f.N, E = f.E;
@@ -412,7 +576,7 @@ void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *siz
         k_cmap<<<grid_for(N), kBlock, 0, s>>>(N, grp, gcid, f.nw(), f.cmap(), c.nw());
         BP_LAUNCH();
     }
-    contract(g, E, f.P, f.hoff(), f.pins(), f.hw(), f.cmap(), c, deg, N > 0, sizes + 1, f.tsh());
+    contract(g, E, f.P, f.hoff(), f.pins(), f.hw(), f.cmap(), c, deg, N > 0, sizes + 1, f.tsh(), merge);
     build_incidence(g, c);
     c.b_cmap.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);
     c.b_match.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);

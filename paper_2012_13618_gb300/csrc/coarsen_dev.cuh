@@ -221,11 +221,14 @@ __device__ void d_seg_big(Team t, const int *hoff, const int *pins, const int *c
 }
 
 // Compaction offsets: value = (kept << 31) | distinct pins for hyperedges with >= 2 distinct pins.
+// With parallel-net merging (rep non-null) only the representative of each group is kept.
 struct CompactIn {
     const int *cnt;
+    const int *rep = nullptr;
     __device__ uint64_t operator()(int64_t e) const {
         int c = cnt[e];
-        return c >= 2 ? ((1ull << 31) | (uint64_t)c) : 0ull;
+        const bool keep = c >= 2 && (!rep || rep[e] == (int)e);
+        return keep ? ((1ull << 31) | (uint64_t)c) : 0ull;
     }
 };
 struct CompactOut {
@@ -233,12 +236,13 @@ struct CompactOut {
     const int *hw_in;
     int *hoff_out, *hw_out, *emap, *sizes;  // sizes[0] = E', sizes[1] = P'
     int *ts;                                // tile starts of the compacted CSR (or null)
+    const int *wsum = nullptr;              // merged group weights (parallel-net merging)
     __device__ void operator()(int64_t e, uint64_t pre, uint64_t val) const {
         int ei = (int)(pre >> 31), pi = (int)(pre & 0x7fffffffu);
         if (val) {
             hoff_out[ei] = pi;
             lb_mark_tiles(ts, ei, pi, (int64_t)(val & 0x7fffffffu));
-            if (hw_out) hw_out[ei] = hw_in ? hw_in[e] : 1;
+            if (hw_out) hw_out[ei] = wsum ? wsum[e] : (hw_in ? hw_in[e] : 1);
             emap[e] = ei;
         } else {
             emap[e] = -1;

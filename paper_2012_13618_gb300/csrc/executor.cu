@@ -240,7 +240,10 @@ extern "C" int bipart_partition_batch(int32_t n, const bipart_instance *instance
                 continue;
             }
             const int64_t P = in.num_hedges > 0 ? in.hedge_offsets[in.num_hedges] : 0;
-            if (block_eligible(in.num_nodes, in.num_hedges, P, p.k) && in.num_nodes > 0) blk.push_back(i);
+            // the persistent block path runs the paper's contraction only (no parallel-net merging)
+            if (block_eligible(in.num_nodes, in.num_hedges, P, p.k) && in.num_nodes > 0 &&
+                !(p.flags & BIPART_FLAG_MERGE_PARALLEL))
+                blk.push_back(i);
             else rest.push_back(i);
         }
         auto by_size = [&](std::vector<int32_t> &v) {

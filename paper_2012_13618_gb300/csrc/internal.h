@@ -110,6 +110,7 @@ struct Work {
     Buf hc;          // int2 per-hyperedge gain contributions
     Buf n1;          // int32 per-hyperedge side-1 pin counts (zero between gain passes)
     Buf e_best;      // per-hyperedge uint64 singleton-attach keys
+    Buf m_fp, m_tkey, m_tmin, m_rep, m_wsum;  // parallel-net merging: fingerprints, table, groups
     Buf list;        // node list (rebalance candidates)
     Buf pinned;      // host-pinned mirror of `small`
     uint32_t *host_small = nullptr;
@@ -204,7 +205,7 @@ void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t
                   const int32_t *d_pins, const int32_t *d_nw, const int32_t *d_hw);
 // Algorithm 1 + 2 on `f`, producing `c` (sizes read back to the host).
 // sizes: level_sizes() slots receiving {N', E', P'}.
-void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *sizes);
+void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *sizes, bool merge);
 // Node -> hyperedge incidence of a level whose hyperedge CSR is complete and whose node degrees
 // were counted into degree_counters(g, N) while its pins were written.
 void build_incidence(bipart_graph *g, Level &L);

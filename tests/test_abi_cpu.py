@@ -90,7 +90,7 @@ def test_params_validation_before_any_device_work():
     # any k >= 1 is valid (readings G1-G2); k <= 0 and unknown flag bits are rejected on the host
     lib = bp.load()
     g = {"N": 4, "hoff": [0, 2, 4], "pins": [0, 1, 2, 3]}
-    for k, flags in [(0, 0), (-3, 0), (2, 2), (3, 1 << 5)]:
+    for k, flags in [(0, 0), (-3, 0), (2, 4), (3, 1 << 5)]:
         inst, keep = bp._instance(g)
         par = bp.Params(k, 0.1, 0, 25, 2, flags)
         out = np.empty(4, np.int32)

@@ -174,6 +174,40 @@ def test_general_k_small(k, adaptive):
             assert st2 == rst and np.array_equal(out.cpu().numpy(), ref)
 
 
+@pytest.mark.parametrize("policy", ["LDH", "LWD", "HWD", "RAND"])
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_merge_parallel_nets(policy, k):
+    # reading M1: parallel nets merged at contraction, weights summed (off by default)
+    bp = _bp()
+    g = synth.c1_netlist(N=30_000)
+    hr = oracle.Hypergraph.from_dict(g)
+    ref, rst = oracle.partition(hr, k, 0.05, policy, 25, 2, merge=True)
+    with bp.create_from(g) as h:
+        for _ in range(3):  # eager, capture, replay
+            parts, st = h.partition(k, 0.05, policy, 25, 2, merge_parallel=True)
+            assert np.array_equal(parts, ref) and st == rst
+        if k == 2:
+            r = oracle.bisect(hr, 0.05, policy, 25, 2, keep_levels=True, merge=True)
+            assert h.num_levels() == r["nlev"]
+            for l in range(r["nlev"]):
+                lv = h.get_level(l)
+                want = r["levels"][l]
+                assert lv["E"] == want["E"] and np.array_equal(lv["hoff"], want["hoff"])
+                assert np.array_equal(lv["pins"], want["pins"])
+                assert np.array_equal(lv["hw"], want["hw"][: want["E"]])
+
+
+def test_merge_parallel_rownet_hubs():
+    # row-net shape: hub columns make many identical short rows at coarse levels
+    bp = _bp()
+    g = synth.rownet(60_000, 60_000, seed=5)
+    hr = oracle.Hypergraph.from_dict(g)
+    ref, rst = oracle.partition(hr, 2, 0.05, "HWD", 25, 2, merge=True)
+    with bp.create_from(g) as h:
+        parts, st = h.partition(2, 0.05, "HWD", 25, 2, merge_parallel=True)
+        assert np.array_equal(parts, ref) and st == rst
+
+
 def test_netlist_100k_general_k():
     bp = _bp()
     g = synth.c1_netlist(N=100_000)
