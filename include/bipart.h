@@ -100,6 +100,11 @@ int bipart_partition_device(bipart_handle h, int32_t k, double epsilon, int32_t 
  * policies (LWD, HWD, Table 1) something to order by.  The input level is not merged. */
 #define BIPART_FLAG_MERGE_PARALLEL 2
 
+/* Diagnostics: *active = 1 when the top-level bisection of the last partition call replayed a
+ * captured CUDA graph (a handle captures one on the second call with the same parameters), 0
+ * when it ran eagerly. */
+int bipart_plan_active(bipart_handle h, int32_t *active);
+
 /* Levels of the hierarchy kept from the last k = 2 call (level 0 = the normalised input). */
 int bipart_num_levels(bipart_handle h, int32_t *num_levels);
 

@@ -65,6 +65,7 @@ SYMBOLS = {
     "bipart_partition": (ctypes.c_int, [_vp, _i32, ctypes.c_double, _i32, _i32, _i32, _vp]),
     "bipart_partition_device": (ctypes.c_int, [_vp, _i32, ctypes.c_double, _i32, _i32, _i32, _vp]),
     "bipart_partition_ex": (ctypes.c_int, [_vp, _vp, _vp]),
+    "bipart_plan_active": (ctypes.c_int, [_vp, _vp]),
     "bipart_partition_device_ex": (ctypes.c_int, [_vp, _vp, _vp]),
     "bipart_num_levels": (ctypes.c_int, [_vp, _p32]),
     "bipart_get_level": (ctypes.c_int, [_vp, _i32, _p32, _p32, _p32, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -249,6 +250,12 @@ class Handle:
         return _check(load().bipart_partition_device(self._h, int(k), float(eps), _policy(policy),
                                                      int(levels), int(iters),
                                                      ctypes.c_void_p(out.data_ptr())))
+
+    def plan_active(self) -> bool:
+        """Whether the last partition call replayed a captured CUDA graph (diagnostics)."""
+        a = _i32()
+        _check(load().bipart_plan_active(self._h, ctypes.byref(a)))
+        return bool(a.value)
 
     def num_levels(self):
         n = _i32()

@@ -4,6 +4,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -162,50 +164,31 @@ unsigned read_flag(bipart_graph *g, const unsigned *d) {
     return g->w.host_small[0];
 }
 
-cudaGraphConditionalHandle cond_handle(bipart_graph *g) {
-    if (!g->ex.capturing) return 0;
-    cudaStreamCaptureStatus cs;
-    cudaGraph_t graph;
-    BP_CUDA(cudaStreamGetCaptureInfo(g->stream, &cs, nullptr, &graph, nullptr, nullptr, nullptr));
-    cudaGraphConditionalHandle h;
-    BP_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault));
-    return h;
+// Flag slots in the small scratch, after the level size slots.
+constexpr int kFlagBase = kSlotBase + 3 * kSlotLevels;  // int index
+constexpr int kFlagSlots = 16384 - kFlagBase;
+
+unsigned *flag_slot(bipart_graph *g) {
+    Exec &ex = g->ex;
+    if (!ex.capturing) return nullptr;
+    if (ex.flag_next >= kFlagSlots) throw Fail{BIPART_ERR_CUDA, "too many control decisions to capture"};
+    ex.flag_pending = ex.flag_next++;
+    return reinterpret_cast<unsigned *>(g->w.small.as<int32_t>() + kFlagBase + ex.flag_pending);
 }
 
-CondNode cond_begin(bipart_graph *g, cudaGraphConditionalHandle h, bool loop) {
+bool device_flag(bipart_graph *g, const unsigned *d_flag) {
     Exec &ex = g->ex;
-    const int depth = ex.depth + 1;
-    if (depth >= 4) throw Fail{BIPART_ERR_CUDA, "conditional nesting too deep"};
-    if (!ex.body[depth]) BP_CUDA(cudaStreamCreateWithFlags(&ex.body[depth], cudaStreamNonBlocking));
-    cudaStream_t outer = g->stream;
-    cudaStreamCaptureStatus cs;
-    cudaGraph_t graph;
-    const cudaGraphNode_t *deps = nullptr;
-    size_t nd = 0;
-    BP_CUDA(cudaStreamGetCaptureInfo(outer, &cs, nullptr, &graph, &deps, nullptr, &nd));
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = loop ? cudaGraphCondTypeWhile : cudaGraphCondTypeIf;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    BP_CUDA(cudaGraphAddNode(&node, graph, deps, nullptr, nd, &cp));
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    BP_CUDA(cudaStreamBeginCaptureToGraph(ex.body[depth], body, nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeRelaxed));
-    ex.depth = depth;
-    g->stream = ex.body[depth];
-    return CondNode{h, node, outer};
-}
-
-void cond_end(bipart_graph *g, const CondNode &c) {
-    Exec &ex = g->ex;
-    cudaGraph_t body = nullptr;
-    BP_CUDA(cudaStreamEndCapture(g->stream, &body));
-    ex.depth--;
-    g->stream = c.outer;
-    cudaGraphNode_t n = c.node;
-    BP_CUDA(cudaStreamUpdateCaptureDependencies(c.outer, &n, nullptr, 1, cudaStreamSetCaptureDependencies));
+    if (ex.capturing) {
+        if (ex.flag_pos >= ex.flags.size()) throw Fail{BIPART_ERR_CUDA, "plan capture ran past its recorded decisions"};
+        if (ex.flag_pending < 0) throw Fail{BIPART_ERR_CUDA, "control decision without a slot"};
+        const bool v = ex.flags[ex.flag_pos++] != 0;
+        ex.checks.emplace_back(kFlagBase + ex.flag_pending, v ? 1 : 0);
+        ex.flag_pending = -1;
+        return v;
+    }
+    const bool v = read_flag(g, d_flag) != 0;
+    if (ex.recording) ex.flags.push_back(v ? 1 : 0);
+    return v;
 }
 
 void Plan::reset() {
@@ -467,13 +450,16 @@ void bisect_body(bipart_graph *g, Level &L0, const Params &p, int64_t W, uint8_t
     BP_CUDA(cudaMemsetAsync(g->w.small.p, 0, small_state_bytes(), g->stream));
     if (g->w.scan.p) BP_CUDA(cudaMemsetAsync(g->w.scan.p, 0, g->w.scan.cap, g->stream));
     std::vector<Level *> levels{&L0};
+    bool init_done = false;  // the next level's key and reset pass already ran
     while ((int)levels.size() - 1 < p.levels) {
         Level &f = *levels.back();
         if (f.E == 0) break;  // with no hyperedge nothing merges: N' == N
         size_t idx = levels.size() - 1;
         if (g->lev.size() <= idx) g->lev.emplace_back(new Level);
         Level &c = *g->lev[idx];
-        coarsen_level(g, f, c, p.policy, level_sizes(g, (int)idx), (p.flags & BIPART_FLAG_MERGE_PARALLEL) != 0);
+        init_done = coarsen_level(g, f, c, p.policy, level_sizes(g, (int)idx),
+                                  (p.flags & BIPART_FLAG_MERGE_PARALLEL) != 0, init_done,
+                                  (int)idx + 1 < p.levels);
         if (c.N == f.N) break;
         levels.push_back(&c);
     }
@@ -500,15 +486,24 @@ void capture_plan(bipart_graph *g, const Params &p, uint8_t *d_side, int nlev, i
     const uint64_t gen0 = g->gen;
     ex.capturing = true;
     ex.pos = 0;
-    ex.depth = 0;
+    ex.flag_pos = 0;
+    ex.flag_next = 0;
+    ex.flag_pending = -1;
     ex.checks.clear();
     ex.check_kernels = 0;
     tl_capturing = true;
+    // the graph is captured on a private stream and launched on the handle's stream, which may
+    // be the legacy default stream (not capturable)
     cudaStream_t main = g->stream;
     cudaGraph_t graph = nullptr;
     bool ok = true;
-    if (cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) ok = false;
+    if (!g->cap_stream && cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        g->cap_stream = nullptr;
+        ok = false;
+    }
+    if (ok && cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) ok = false;
     if (ok) {
+        g->stream = g->cap_stream;
         try {
             int n2 = 0;
             bisect_body(g, g->L0, p, g->total_node_weight, d_side, &n2);
@@ -516,24 +511,19 @@ void capture_plan(bipart_graph *g, const Params &p, uint8_t *d_side, int nlev, i
         } catch (...) {
             ok = false;
         }
-        // close any open body captures, then the main one
-        while (ex.depth > 0) {
-            cudaGraph_t b = nullptr;
-            cudaStreamEndCapture(ex.body[ex.depth], &b);
-            ex.depth--;
-        }
         g->stream = main;
-        if (cudaStreamEndCapture(main, &graph) != cudaSuccess) ok = false;
+        if (cudaStreamEndCapture(g->cap_stream, &graph) != cudaSuccess) ok = false;
     }
     ex.capturing = false;
     tl_capturing = false;
     cudaGetLastError();
-    if (ok && ex.pos != ex.sizes.size()) ok = false;
+    if (ok && (ex.pos != ex.sizes.size() || ex.flag_pos != ex.flags.size())) ok = false;
     if (ok && g->gen != gen0) ok = false;
     if (ok && cudaGraphInstantiate(&pl.exec, graph, 0) != cudaSuccess) ok = false;
     cudaGetLastError();
     pl.graph = graph;
     if (!ok) {
+        if (std::getenv("BIPART_TIMING")) std::fprintf(stderr, "[bipart] plan capture failed; calls stay eager\n");
         pl.reset();
         return;
     }
@@ -557,20 +547,38 @@ bool same_params(const Params &a, const Params &b) {
 int bisect_top(bipart_graph *g, const Params &p, uint8_t *d_side, int *nlev) {
     Plan &pl = g->plan;
     Exec &ex = g->ex;
+    g->last_replayed = false;
     if (!(pl.valid && same_params(pl.params, p) && pl.gen == g->gen && pl.prof_epoch == prof_epoch())) {
         pl.reset();
         if (ex.rec_valid && same_params(ex.rec_params, p) && ex.rec_gen == g->gen)
             capture_plan(g, p, d_side, ex.rec_nlev, ex.rec_kernels);
     }
     if (pl.valid) {
+        // BIPART_TIMING: device time of the replay alone, on stderr (diagnostics)
+        static const bool timing = std::getenv("BIPART_TIMING") != nullptr;
+        cudaEvent_t t0 = nullptr, t1 = nullptr;
+        if (timing) {
+            cudaEventCreate(&t0);
+            cudaEventCreate(&t1);
+            cudaEventRecord(t0, g->stream);
+        }
         BP_CUDA(cudaGraphLaunch(pl.exec, g->stream));
+        if (timing) cudaEventRecord(t1, g->stream);
         for (int64_t i = 0; i < pl.launches; ++i) note_launch();
         sync(g);
+        if (timing) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, t0, t1);
+            std::fprintf(stderr, "[bipart] graph replay %.3f ms (%lld launches)\n", ms, (long long)pl.launches);
+            cudaEventDestroy(t0);
+            cudaEventDestroy(t1);
+        }
         const uint32_t st = read_status_word(g);
         if (!(st & DEV_PLAN_MISMATCH)) {
             check_status(g);
             prof_collect(pl.probes);
             *nlev = pl.nlev;
+            g->last_replayed = true;
             return read_bisect_status(g);
         }
         // the replayed control flow did not match this run: discard the plan, run eagerly
@@ -580,6 +588,7 @@ int bisect_top(bipart_graph *g, const Params &p, uint8_t *d_side, int *nlev) {
     }
     ex.recording = true;
     ex.sizes.clear();
+    ex.flags.clear();
     const int64_t k0 = bipart_kernel_launches();
     try {
         bisect_body(g, g->L0, p, g->total_node_weight, d_side, nlev);
@@ -768,16 +777,11 @@ void validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t 
         throw Fail{BIPART_ERR_INVALID_CSR, "weight sum must stay below 2^31"};
 }
 
-namespace {
-
-
-}  // namespace
 }  // namespace bp
 
 bipart_graph::~bipart_graph() {
     plan.reset();
-    for (cudaStream_t &b : ex.body)
-        if (b) cudaStreamDestroy(b);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     if (w.host_small) cudaFreeHost(w.host_small);
     w.host_small = nullptr;
 }
@@ -1020,6 +1024,12 @@ int bipart_partition_device_ex(bipart_handle h, const bipart_params *params, int
     });
 }
 
+int bipart_plan_active(bipart_handle h, int32_t *active) {
+    if (!h || !active) { set_error("NULL argument"); return BIPART_ERR_INVALID_ARG; }
+    *active = h->last_replayed ? 1 : 0;
+    return BIPART_OK;
+}
+
 int bipart_num_levels(bipart_handle h, int32_t *num_levels) {
     if (!h || !num_levels) { set_error("NULL argument"); return BIPART_ERR_INVALID_ARG; }
     if (!h->hier.valid) { set_error("no k = 2 hierarchy kept"); return BIPART_ERR_INVALID_ARG; }
@@ -1201,7 +1211,7 @@ ProfScope::ProfScope(const char *name, double bytes, cudaStream_t s) {
         // inside a captured plan: event nodes at the top level of the graph only (conditional
         // bodies may not hold event nodes); read back after every replay
         bipart_graph *g = tl_graph;
-        if (!g || g->ex.depth > 0) return;
+        if (!g) return;
         Probe p{name, bytes, nullptr, nullptr};
         cudaEventCreate(&p.a);
         cudaEventCreate(&p.b);

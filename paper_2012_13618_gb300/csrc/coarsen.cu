@@ -49,21 +49,21 @@ k_seg_small(int E, const int *__restrict__ hoff, const int *__restrict__ pins,
                      kGridMidDeg);
 }
 
-template <bool MAP>
-__global__ void __launch_bounds__(kBlock)
-k_seg_mid(const int *__restrict__ hoff, const int *__restrict__ pins, const int *__restrict__ cmap,
-          int *__restrict__ scratch, int *__restrict__ cnt, const int *__restrict__ list,
-          const int *__restrict__ counters) {
-    d_seg_mid<MAP>(GridTeam(), hoff, pins, cmap, scratch, cnt, list, counters);
-}
-
+// Mid and big tiers in one launch: blocks [0, nbig) take the big list (one block per
+// hyperedge, shared-memory bitmap), the others the mid list (one warp per hyperedge).  The two
+// lists are disjoint, so the tiers run side by side.
 template <bool MAP>
 __global__ void __launch_bounds__(kBigThreads)
-k_seg_big(const int *__restrict__ hoff, const int *__restrict__ pins, const int *__restrict__ cmap,
-          int *__restrict__ scratch, int *__restrict__ cnt, const int *__restrict__ list,
-          const int *__restrict__ counters) {
+k_seg_midbig(int nbig, const int *__restrict__ hoff, const int *__restrict__ pins,
+             const int *__restrict__ cmap, int *__restrict__ scratch, int *__restrict__ cnt,
+             const int *__restrict__ mid_list, const int *__restrict__ big_list,
+             const int *__restrict__ counters) {
     __shared__ uint32_t bits[kBigWords];
-    d_seg_big<MAP>(GridTeam(), hoff, pins, cmap, scratch, cnt, list, counters, bits);
+    if ((int)blockIdx.x < nbig)
+        d_seg_big<MAP>(SubGridTeam{0, nbig}, hoff, pins, cmap, scratch, cnt, big_list, counters, bits);
+    else
+        d_seg_mid<MAP>(SubGridTeam{nbig, (int)gridDim.x - nbig}, hoff, pins, cmap, scratch, cnt, mid_list,
+                       counters);
 }
 
 __global__ void __launch_bounds__(kLbBlock)
@@ -72,6 +72,31 @@ k_seg_copy(int E, int P, const int *__restrict__ hoff, const int *__restrict__ s
            const int *__restrict__ hoff_out, int *__restrict__ pins_out, int *__restrict__ deg,
            const int *__restrict__ ts) {
     d_seg_copy(GridTeam(), E, P, hoff, scratch, cnt, emap, hoff_out, pins_out, deg, ts);
+}
+
+// Start of a level's coarsening: hyperedge keys (Algorithm 1, Table 1), and every
+// per-hyperedge / per-node accumulator of the matching reset in the same pass (ssize, sweight,
+// rep, best; nkey).  Runs alone, or as the second job of the previous level's incidence fill.
+struct LevelInit {
+    int E = 0, N = 0, policy = 0;
+    const int *hoff = nullptr, *hw = nullptr;
+    unsigned long long *hkey = nullptr, *best = nullptr, *nkey = nullptr;
+    int *ssize = nullptr, *sweight = nullptr;
+    unsigned *rep = nullptr;
+};
+
+__device__ __forceinline__ void d_level_init(const LevelInit &li) {
+    d_hedge_key(GridTeam(), li.E, li.policy, li.hoff, li.hw, li.hkey);
+    const int n = li.E > li.N ? li.E : li.N;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (i < li.E) {
+            li.ssize[i] = 0;
+            li.sweight[i] = 0;
+            li.rep[i] = ~0u;
+            li.best[i] = ~0ull;
+        }
+        if (i < li.N) li.nkey[i] = ~0ull;
+    }
 }
 
 // Coarse levels with at most kPrivNodes nodes count degrees and claim incidence positions in
@@ -115,7 +140,9 @@ k_seg_copy_priv(int E, int P, int N, const int *__restrict__ hoff, const int *__
 // passes visit the same tiles.
 __global__ void __launch_bounds__(kPrivBlock)
 k_fill_adj_priv(int E, int P, int N, const int *__restrict__ hoff, const int *__restrict__ pins,
-                int *__restrict__ cursor, int *__restrict__ nadj, const int *__restrict__ ts) {
+                int *__restrict__ cursor, int *__restrict__ nadj, const int *__restrict__ ts,
+                LevelInit next) {
+    d_level_init(next);  // the next coarsening's keys and resets (E = N = 0: nothing)
     extern __shared__ int s_cnt[];
     for (int v = threadIdx.x; v < N; v += blockDim.x) s_cnt[v] = 0;
     __syncthreads();
@@ -146,29 +173,13 @@ __global__ void k_fill(int n, int val, int *__restrict__ a) {
 
 __global__ void __launch_bounds__(kLbBlock)
 k_fill_adj(int E, int P, const int *__restrict__ hoff, const int *__restrict__ pins,
-           int *__restrict__ cursor, int *__restrict__ nadj, const int *__restrict__ ts) {
+           int *__restrict__ cursor, int *__restrict__ nadj, const int *__restrict__ ts,
+           LevelInit next) {
     d_fill_adj(GridTeam(), E, P, hoff, pins, cursor, nadj, ts);
+    d_level_init(next);
 }
 
-// Start of a level: hyperedge keys, and every per-hyperedge / per-node accumulator of the
-// matching reset in the same pass (ssize, sweight, rep, best; nkey).
-__global__ void k_level_init(int E, int N, int policy, const int *__restrict__ hoff,
-                             const int *__restrict__ hw, unsigned long long *__restrict__ hkey,
-                             int *__restrict__ ssize, int *__restrict__ sweight,
-                             unsigned *__restrict__ rep, unsigned long long *__restrict__ best,
-                             unsigned long long *__restrict__ nkey) {
-    d_hedge_key(GridTeam(), E, policy, hoff, hw, hkey);
-    const int n = E > N ? E : N;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        if (i < E) {
-            ssize[i] = 0;
-            sweight[i] = 0;
-            rep[i] = ~0u;
-            best[i] = ~0ull;
-        }
-        if (i < N) nkey[i] = ~0ull;
-    }
-}
+__global__ void k_level_init(LevelInit li) { d_level_init(li); }
 
 __global__ void __launch_bounds__(kLbBlock)
 k_match_min(int N, int P, const int *__restrict__ noff, const int *__restrict__ nadj,
@@ -371,13 +382,13 @@ void seg_unique(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const in
     if (map) k_seg_small<true><<<grid_for(E), kBlock, 0, s>>>(E, hoff, pins, map, scratch, cnt, mid, big, small);
     else k_seg_small<false><<<grid_for(E), kBlock, 0, s>>>(E, hoff, pins, map, scratch, cnt, mid, big, small);
     BP_LAUNCH();
-    int mid_grid = std::max(1, std::min(152 * 16, ceil_div_i(P / (kSmallDeg + 1) + 1, kBlock / 32)));
-    if (map) k_seg_mid<true><<<mid_grid, kBlock, 0, s>>>(hoff, pins, map, scratch, cnt, mid, small);
-    else k_seg_mid<false><<<mid_grid, kBlock, 0, s>>>(hoff, pins, map, scratch, cnt, mid, small);
-    BP_LAUNCH();
-    int big_grid = std::max(1, std::min(152 * 4, P / (kGridMidDeg + 1) + 1));
-    if (map) k_seg_big<true><<<big_grid, kBigThreads, 0, s>>>(hoff, pins, map, scratch, cnt, big, small);
-    else k_seg_big<false><<<big_grid, kBigThreads, 0, s>>>(hoff, pins, map, scratch, cnt, big, small);
+    // warps for the mid tier (at most one per 9 pins), blocks for the big tier (at most one per
+    // kGridMidDeg + 1 pins); the list lengths are only known on the device
+    const int mid_warps = std::max(1, std::min(152 * 16 * (kBlock / 32), P / (kSmallDeg + 1) + 1));
+    const int nmid = ceil_div_i(mid_warps, kBigThreads / 32);
+    const int nbig = std::max(1, std::min(152 * 4, P / (kGridMidDeg + 1) + 1));
+    if (map) k_seg_midbig<true><<<nbig + nmid, kBigThreads, 0, s>>>(nbig, hoff, pins, map, scratch, cnt, mid, big, small);
+    else k_seg_midbig<false><<<nbig + nmid, kBigThreads, 0, s>>>(nbig, hoff, pins, map, scratch, cnt, mid, big, small);
     BP_LAUNCH();
 }
 
@@ -458,7 +469,12 @@ void distinct_counts(bipart_graph *g, Level &L, const int *d_map, int *cnt) {
 
 // Node -> hyperedge incidence of a level whose degrees were counted by its contraction
 // (deg[N], in the per-node scratch n_a).
-void build_incidence(bipart_graph *g, Level &L) {
+void build_incidence_and_init(bipart_graph *g, Level &L, const LevelInit &next);
+
+void build_incidence(bipart_graph *g, Level &L) { build_incidence_and_init(g, L, LevelInit()); }
+
+// The incidence fill of L also runs `next` (the keys and resets of L's own coarsening).
+void build_incidence_and_init(bipart_graph *g, Level &L, const LevelInit &next) {
     cudaStream_t s = g->stream;
     Work &w = g->w;
     L.b_noff.ensure(sizeof(int) * ((size_t)L.N + 1), s);
@@ -476,12 +492,16 @@ void build_incidence(bipart_graph *g, Level &L) {
              dev_status(g), s);
     }
     if (L.P > 0) {
-        ProfScope ps("incidence_fill", 12.0 * L.P + 4.0 * L.E, s);
+        ProfScope ps("incidence_fill", 12.0 * L.P + 4.0 * L.E + 32.0 * next.E + 8.0 * next.N, s);
         if (L.N <= kPrivNodes)
             k_fill_adj_priv<<<priv_grid(L.P), kPrivBlock, sizeof(int) * (size_t)L.N, s>>>(
-                L.E, L.P, L.N, L.hoff(), L.pins(), cursor, L.nadj(), L.tsh());
+                L.E, L.P, L.N, L.hoff(), L.pins(), cursor, L.nadj(), L.tsh(), next);
         else
-            k_fill_adj<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.E, L.P, L.hoff(), L.pins(), cursor, L.nadj(), L.tsh());
+            k_fill_adj<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.E, L.P, L.hoff(), L.pins(), cursor, L.nadj(),
+                                                        L.tsh(), next);
+        BP_LAUNCH();
+    } else if (next.E > 0 || next.N > 0) {
+        k_level_init<<<grid_for(std::max(next.E, next.N)), kBlock, 0, s>>>(next);
         BP_LAUNCH();
     }
 }
@@ -517,7 +537,8 @@ void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t
     L.b_match.ensure(sizeof(int) * (size_t)std::max(N, 1), s);
 }
 
-void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *sizes, bool merge) {
+bool coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *sizes, bool merge,
+                   bool init_done, bool more_levels) {
     cudaStream_t s = g->stream;
     Work &w = g->w;
     const int N = f.N, E = f.E;
@@ -534,10 +555,13 @@ void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *siz
     int *deg = (int *)w.n_a.ensure(sizeof(int) * (size_t)std::max(N, 1), s);
     c.b_nw.ensure(sizeof(int) * (size_t)std::max(N, 1), s);
     int *small = w.small.as<int>();
-    if (N > 0 || E > 0) {
+    if ((N > 0 || E > 0) && !init_done) {
         ProfScope ps("hedge_key", 12.0 * E + (f.hw() ? 4.0 * E : 0.0) + 20.0 * E + 8.0 * N, s);
-        k_level_init<<<grid_for(std::max(E, N)), kBlock, 0, s>>>(E, N, policy, f.hoff(), f.hw(), hkey,
-                                                                 ssize, sweight, rep, best, nkey);
+        LevelInit li;
+        li.E = E; li.N = N; li.policy = policy; li.hoff = f.hoff(); li.hw = f.hw();
+        li.hkey = hkey; li.best = best; li.nkey = nkey; li.ssize = ssize; li.sweight = sweight;
+        li.rep = rep;
+        k_level_init<<<grid_for(std::max(E, N)), kBlock, 0, s>>>(li);
         BP_LAUNCH();
     }
     if (N > 0) {
@@ -577,9 +601,19 @@ void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *siz
         BP_LAUNCH();
     }
     contract(g, E, f.P, f.hoff(), f.pins(), f.hw(), f.cmap(), c, deg, N > 0, sizes + 1, f.tsh(), merge);
-    build_incidence(g, c);
+    // when c will be coarsened in turn (the stop rule of reading C11 lets it), its key and reset
+    // pass rides along with its incidence fill
+    const bool prep = more_levels && c.E > 0 && c.N != f.N;
+    LevelInit next;
+    if (prep) {
+        next.E = c.E; next.N = c.N; next.policy = policy; next.hoff = c.hoff(); next.hw = c.hw();
+        next.hkey = hkey; next.best = best; next.nkey = nkey; next.ssize = ssize;
+        next.sweight = sweight; next.rep = rep;
+    }
+    build_incidence_and_init(g, c, next);
     c.b_cmap.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);
     c.b_match.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);
+    return prep;
 }
 
 void coarsen_init() {

@@ -209,6 +209,20 @@ struct GridTeam {
     __device__ __forceinline__ static T ld(const T *p) { return __ldg(p); }
 };
 
+// The blocks [b0, b0 + nb) of a grid launch, as a team of their own (a launch that runs two
+// independent phases on disjoint sets of blocks).
+struct SubGridTeam {
+    int b0, nb;
+    __device__ __forceinline__ int block() const { return blockIdx.x - b0; }
+    __device__ __forceinline__ int blocks() const { return nb; }
+    __device__ __forceinline__ int rank() const { return block() * blockDim.x + threadIdx.x; }
+    __device__ __forceinline__ int size() const { return nb * blockDim.x; }
+    __device__ __forceinline__ int warp() const { return rank() >> 5; }
+    __device__ __forceinline__ int warps() const { return size() >> 5; }
+    template <class T>
+    __device__ __forceinline__ static T ld(const T *p) { return __ldg(p); }
+};
+
 struct CtaTeam {
     __device__ __forceinline__ int rank() const { return threadIdx.x; }
     __device__ __forceinline__ int size() const { return blockDim.x; }

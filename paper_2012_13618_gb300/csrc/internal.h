@@ -145,8 +145,9 @@ struct Exec {
     bool recording = false;
     std::vector<int32_t> sizes;
     size_t pos = 0;
-    cudaStream_t body[4] = {};   // capture streams of nested conditional bodies
-    int depth = 0;
+    std::vector<uint8_t> flags;  // recorded control decisions, in order
+    size_t flag_pos = 0;
+    int flag_next = 0, flag_pending = -1;
     int64_t check_kernels = 0;   // size-check kernels per replay
     std::vector<std::pair<int, int32_t>> checks;  // deferred (slot index, recorded value)
     // the last eager top-level bisection, ready to be captured
@@ -182,6 +183,9 @@ struct Plan {
 struct bipart_graph {
     int device = 0;
     cudaStream_t stream = nullptr;
+    bool last_replayed = false;  // the last top-level bisection ran a captured plan
+    cudaStream_t cap_stream = nullptr;  // private stream a plan is captured on (the legacy
+                                        // default stream cannot be captured)
     bp::Level L0;                                  // normalised input
     std::vector<std::unique_ptr<bp::Level>> lev;   // coarse levels 1.. of the last bisection
     bp::Hierarchy hier;
@@ -204,8 +208,11 @@ namespace bp {
 void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t *d_hoff,
                   const int32_t *d_pins, const int32_t *d_nw, const int32_t *d_hw);
 // Algorithm 1 + 2 on `f`, producing `c` (sizes read back to the host).
-// sizes: level_sizes() slots receiving {N', E', P'}.
-void coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *sizes, bool merge);
+// sizes: level_sizes() slots receiving {N', E', P'}.  init_done: f's key and reset pass already
+// ran (with the previous level's incidence fill); more_levels: the level count allows another
+// contraction after this one.  Returns whether c's own key and reset pass has been run.
+bool coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *sizes, bool merge,
+                   bool init_done, bool more_levels);
 // Node -> hyperedge incidence of a level whose hyperedge CSR is complete and whose node degrees
 // were counted into degree_counters(g, N) while its pins were written.
 void build_incidence(bipart_graph *g, Level &L);
@@ -288,48 +295,13 @@ int32_t *level_sizes(bipart_graph *g, int idx);
 // Adds the deferred size checks of a capture to the graph (one kernel).
 void flush_checks(bipart_graph *g);
 
-// Conditional nodes.  The kernel that computes a condition's flag also sets the node's value on
-// the device (cudaGraphSetConditional), so no helper kernel runs per evaluation: cond_handle()
-// gives the handle to pass to that kernel (0 when not capturing), and the loop body's last
-// kernel sets it again for the next iteration.
-cudaGraphConditionalHandle cond_handle(bipart_graph *g);
-struct CondNode {
-    cudaGraphConditionalHandle h;
-    cudaGraphNode_t node;
-    cudaStream_t outer;
-};
-CondNode cond_begin(bipart_graph *g, cudaGraphConditionalHandle h, bool loop);
-void cond_end(bipart_graph *g, const CondNode &c);
-
-// Runs body() while *d_flag != 0 (the body must update the flag, and set h when capturing).
-// Eager: the host reads the flag before every iteration; capturing: a WHILE conditional node.
-template <class Body>
-void device_while(bipart_graph *g, cudaGraphConditionalHandle h, const unsigned *d_flag,
-                  int64_t max_iter, Body body) {
-    if (!g->ex.capturing) {
-        for (int64_t it = 0;; ++it) {
-            if (!read_flag(g, d_flag)) break;
-            if (it > max_iter) throw Fail{BIPART_ERR_TIMEOUT, "device loop made no progress"};
-            body();
-        }
-        return;
-    }
-    CondNode c = cond_begin(g, h, true);
-    body();
-    cond_end(g, c);
-}
-
-// Runs body() once if *d_flag != 0.  Eager: host check; capturing: an IF conditional node whose
-// value the flag's producer set through h.
-template <class Body>
-void device_if(bipart_graph *g, cudaGraphConditionalHandle h, const unsigned *d_flag, Body body) {
-    if (!g->ex.capturing) {
-        if (read_flag(g, d_flag)) body();
-        return;
-    }
-    CondNode c = cond_begin(g, h, false);
-    body();
-    cond_end(g, c);
-}
+// Device-computed control decisions (loop continuation, the exact-select branch).  The
+// computation is deterministic, so a captured bisection takes every decision the recorded eager
+// run took, as straight-line kernels with no conditional node: flag_slot() gives the kernel that
+// computes the next flag a slot to store it in (null outside a capture), device_flag() returns
+// the flag (eager: read from the device and recorded; capturing: the recorded value) and, while
+// capturing, adds the slot's check to the end-of-bisection verification.
+unsigned *flag_slot(bipart_graph *g);
+bool device_flag(bipart_graph *g, const unsigned *d_flag);
 
 }  // namespace bp

@@ -9,7 +9,8 @@
 // over node ids then takes the lowest ids among nodes whose gain equals the threshold.  Only the
 // rebalancing pass needs the chosen nodes in order; it sorts at most ceil(sqrt n) of them in one
 // block.  The two data-dependent loops (Algorithm 3's rounds and the rebalancing rounds) are
-// driven by a device-side flag, so they run unchanged inside a CUDA graph (WHILE nodes).
+// driven by a device-side flag; a captured bisection replays the recorded decisions as
+// straight-line kernels and verifies every flag on the device.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -76,10 +77,10 @@ __device__ __forceinline__ void take_hist(RState *st, unsigned (*h)[kHistBins]) 
 // Fast selection pass: clamped-gain histogram, then (last block) the per-group threshold.  The
 // rebalancing list is emptied for the application scan that follows.  One block (small levels)
 // keeps its histogram in shared memory and also runs the exact radix passes when needed, leaving
-// st->slow clear; a grid leaves st->slow for the exact passes and sets the IF node's value `h`.
+// st->slow clear; a grid leaves st->slow for the exact passes (and in its check slot).
 __global__ void __launch_bounds__(kBlock)
 k_sel(int N, int kind, long long s, const int *__restrict__ gain, const uint8_t *__restrict__ side,
-      const int *__restrict__ nw, RState *st, cudaGraphConditionalHandle h_slow, uint32_t *status) {
+      const int *__restrict__ nw, RState *st, unsigned *slow_slot, uint32_t *status) {
     __shared__ unsigned h[2][kHistBins];
     const bool one = gridDim.x == 1;
     d_sel_hist(GridTeam(), N, kind, gain, side, nw, st, h, !one);
@@ -98,8 +99,8 @@ k_sel(int N, int kind, long long s, const int *__restrict__ gain, const uint8_t 
             }
             if (threadIdx.x == 0) st->slow = 0;
         }
-    } else if (h_slow && threadIdx.x == 0) {
-        cudaGraphSetConditional(h_slow, st->slow ? 1u : 0u);
+    } else if (slow_slot && threadIdx.x == 0) {
+        *slow_slot = st->slow;
     }
 }
 
@@ -117,35 +118,53 @@ k_sel_exact(int N, int kind, const int *__restrict__ gain, const uint8_t *__rest
     d_sel_find_exact(st, status, h);
 }
 
-// W = side weights: partial sums in Wacc, moved to W (and Wacc cleared) by the last block.
+// A loop condition evaluated by the last thread of the kernel that produced its inputs; in a
+// captured bisection the flag is also stored in its check slot.
+struct CondArgs {
+    int kind;                    // COND_NONE, COND_INITIAL, COND_REBAL
+    int first;                   // first evaluation of the loop (resets its counters)
+    int m0, m;                   // Algorithm 3: side 0 grows to m0 / m of the weight
+    long long limit0, limit1;    // rebalance: per-side limits
+    long long max_rounds;
+    unsigned *slot;              // flag_slot() of this evaluation (null outside a capture)
+};
+enum { COND_NONE = 0, COND_INITIAL = 1, COND_REBAL = 2 };
+
+__device__ __forceinline__ void eval_cond(RState *st, const CondArgs &c, uint32_t *status) {
+    if (c.kind == COND_INITIAL) d_initial_cond(st, c.max_rounds, status, c.first != 0, c.m0, c.m);
+    else if (c.kind == COND_REBAL) d_rebal_cond(st, c.limit0, c.limit1, c.max_rounds, status, c.first != 0);
+    else return;
+    if (c.slot && threadIdx.x == 0) *c.slot = st->flag;
+}
+
+// W = side weights: partial sums in Wacc, moved to W (and Wacc cleared) by the last block, which
+// then evaluates the loop condition that needs W (if any).
 __global__ void __launch_bounds__(kBlock)
-k_side_weights(int N, const uint8_t *__restrict__ side, const int *__restrict__ nw, RState *st) {
+k_side_weights(int N, const uint8_t *__restrict__ side, const int *__restrict__ nw, RState *st,
+               CondArgs cond, uint32_t *status) {
     d_side_weights(GridTeam(), N, side, nw, st->Wacc);
     if (!last_block(&st->arrived)) return;
     if (threadIdx.x < 2) {
         st->W[threadIdx.x] = __ldcg(&st->Wacc[threadIdx.x]);
         st->Wacc[threadIdx.x] = 0ull;
     }
+    __syncthreads();
+    eval_cond(st, cond, status);
 }
 
-// Loop conditions; they also set the WHILE node's value `h` when the loop runs in a graph.
-__global__ void k_initial_cond(RState *st, long long max_rounds, uint32_t *status, int first,
-                               int m0, int m, cudaGraphConditionalHandle h) {
-    d_initial_cond(st, max_rounds, status, first != 0, m0, m);
-    if (h && threadIdx.x == 0) cudaGraphSetConditional(h, st->flag ? 1u : 0u);
+// Loop conditions evaluated alone (the Algorithm 3 loop body ends with one).
+__global__ void k_initial_cond(RState *st, CondArgs cond, uint32_t *status) {
+    eval_cond(st, cond, status);
 }
 
-__global__ void k_rebal_cond(RState *st, long long limit0, long long limit1, long long max_rounds,
-                             uint32_t *status, int first, cudaGraphConditionalHandle h) {
-    d_rebal_cond(st, limit0, limit1, max_rounds, status, first != 0);
-    if (h && threadIdx.x == 0) cudaGraphSetConditional(h, st->flag ? 1u : 0u);
-}
-
+// Ordered rebalance move, then (same block) the rebalance condition for the next round.
 __global__ void __launch_bounds__(1024)
 k_rebal_move(const int *__restrict__ gain, uint8_t *__restrict__ side, const int *__restrict__ nw,
-             const int *__restrict__ list, RState *st, long long s) {
+             const int *__restrict__ list, RState *st, long long s, CondArgs cond, uint32_t *status) {
     extern __shared__ unsigned long long keys[];
     d_rebal_move(gain, side, nw, list, st, s, keys);
+    __syncthreads();
+    eval_cond(st, cond, status);
 }
 
 __global__ void k_project(int N, const int *__restrict__ cmap, const uint8_t *__restrict__ coarse,
@@ -215,29 +234,28 @@ void select_apply(bipart_graph *g, Level &L, int kind, long long sq, const int *
     cudaStream_t s = g->stream;
     RState *st = rstate(g);
     const bool one = sel_grid(L.N) == 1;  // exact passes, if any, run inside k_sel
-    const cudaGraphConditionalHandle h = one ? 0 : cond_handle(g);
+    unsigned *slot = one ? nullptr : flag_slot(g);
     {
         ProfScope ps("select_hist", 9.0 * L.N, s);
-        k_sel<<<sel_grid(L.N), kBlock, 0, s>>>(L.N, kind, sq, gain, side, L.nw(), st, h, dev_status(g));
+        k_sel<<<sel_grid(L.N), kBlock, 0, s>>>(L.N, kind, sq, gain, side, L.nw(), st, slot, dev_status(g));
         BP_LAUNCH();
     }
-    if (!one) device_if(g, h, &st->slow, [&]() {
+    if (!one && device_flag(g, &st->slow)) {
         for (int pass = 0; pass < 3; ++pass) {
-            k_sel_exact<<<sel_grid(L.N), kBlock, 0, g->stream>>>(L.N, kind, gain, side, L.nw(), st,
-                                                                 dev_status(g));
+            k_sel_exact<<<sel_grid(L.N), kBlock, 0, s>>>(L.N, kind, gain, side, L.nw(), st, dev_status(g));
             BP_LAUNCH();
         }
-    });
+    }
     s = g->stream;
     ProfScope ps("select_apply", 10.0 * L.N, s);
     scan(L.N, TieIn{kind, gain, side, L.nw(), st}, ApplyOut{kind, gain, side, L.nw(), st, list},
          g->w.scan.ensure_zero(scan_state_bytes(L.N), s), dev_status(g), s);
 }
 
-void side_weights(bipart_graph *g, Level &L, const uint8_t *side) {
+void side_weights(bipart_graph *g, Level &L, const uint8_t *side, const CondArgs &cond) {
     cudaStream_t s = g->stream;
     RState *st = rstate(g);
-    k_side_weights<<<grid_for(L.N), kBlock, 0, s>>>(L.N, side, L.nw(), st);
+    k_side_weights<<<grid_for(L.N), kBlock, 0, s>>>(L.N, side, L.nw(), st, cond, dev_status(g));
     BP_LAUNCH();
 }
 
@@ -248,16 +266,17 @@ void initial_partition(bipart_graph *g, Level &L, uint8_t *side, int *gain, int 
     RState *st = rstate(g);
     const long long sq = ceil_sqrt64(L.N);
     BP_CUDA(cudaMemsetAsync(side, 1, (size_t)L.N, s));
-    side_weights(g, L, side);
-    const cudaGraphConditionalHandle h = cond_handle(g);
-    k_initial_cond<<<1, 32, 0, s>>>(st, (long long)L.N + 1, dev_status(g), 1, m0, m, h);
-    BP_LAUNCH();
-    device_while(g, h, &st->flag, (int64_t)L.N + 2, [&]() {
+    CondArgs c{COND_INITIAL, 1, m0, m, 0, 0, (long long)L.N + 1, flag_slot(g)};
+    side_weights(g, L, side, c);
+    c.first = 0;
+    for (int64_t it = 0; device_flag(g, &st->flag); ++it) {
+        if (it > (int64_t)L.N + 2) throw Fail{BIPART_ERR_TIMEOUT, "Algorithm 3 made no progress"};
         compute_gains(g, L, side, gain);
         select_apply(g, L, SEL_INITIAL, sq, gain, side, nullptr);
-        k_initial_cond<<<1, 32, 0, g->stream>>>(st, (long long)L.N + 1, dev_status(g), 0, m0, m, h);
+        c.slot = flag_slot(g);
+        k_initial_cond<<<1, 32, 0, s>>>(st, c, dev_status(g));
         BP_LAUNCH();
-    });
+    }
 }
 
 void refine_iter(bipart_graph *g, Level &L, uint8_t *side, int *gain) {
@@ -276,20 +295,18 @@ void rebalance(bipart_graph *g, Level &L, uint8_t *side, int *gain, const int64_
     int S = 1;
     while (S < sq) S <<= 1;
     const size_t smem = sizeof(unsigned long long) * (size_t)S;
-    side_weights(g, L, side);
-    const cudaGraphConditionalHandle h = cond_handle(g);
-    k_rebal_cond<<<1, 32, 0, s>>>(st, (long long)limit[0], (long long)limit[1], (long long)L.N + 1,
-                                  dev_status(g), 1, h);
-    BP_LAUNCH();
-    device_while(g, h, &st->flag, (int64_t)L.N + 2, [&]() {
+    CondArgs c{COND_REBAL, 1, 1, 2, (long long)limit[0], (long long)limit[1], (long long)L.N + 1,
+               flag_slot(g)};
+    side_weights(g, L, side, c);
+    c.first = 0;
+    for (int64_t it = 0; device_flag(g, &st->flag); ++it) {
+        if (it > (int64_t)L.N + 2) throw Fail{BIPART_ERR_TIMEOUT, "rebalance made no progress"};
         compute_gains(g, L, side, gain);
         select_apply(g, L, SEL_REBAL, sq, gain, side, list);
-        k_rebal_move<<<1, 1024, smem, g->stream>>>(gain, side, L.nw(), list, st, sq);
+        c.slot = flag_slot(g);
+        k_rebal_move<<<1, 1024, smem, s>>>(gain, side, L.nw(), list, st, sq, c, dev_status(g));
         BP_LAUNCH();
-        k_rebal_cond<<<1, 32, 0, g->stream>>>(st, (long long)limit[0], (long long)limit[1],
-                                              (long long)L.N + 1, dev_status(g), 0, h);
-        BP_LAUNCH();
-    });
+    }
 }
 
 }  // namespace

@@ -244,8 +244,8 @@ def test_c2_rownet_reduced_k8():
 
 @pytest.mark.parametrize("gen", ["c0", "netlist"])
 def test_graph_replay_matches_oracle(gen):
-    # call 1 runs eagerly and records the level sizes, call 2 captures a CUDA graph (WHILE / IF
-    # nodes for the device-driven loops) and launches it, call 3 replays it: all bit-exact
+    # call 1 runs eagerly and records the level sizes and control decisions, call 2 captures a
+    # CUDA graph and launches it, call 3 replays it: all bit-exact, and 2-3 really replay
     bp = _bp()
     g = synth.c0_uniform() if gen == "c0" else synth.c1_netlist(N=120_000)
     eps = 0.1 if gen == "c0" else 0.05
@@ -256,12 +256,14 @@ def test_graph_replay_matches_oracle(gen):
             parts, st = h.partition(2, eps, "LDH", 25, 2)
             assert np.array_equal(parts, ref["side"].astype(np.int32)), call
             assert st == ref["status"]
+            assert h.plan_active() == (call > 0), call
         compare_levels(h, ref)
         # a different parameter set on the same handle, then back again
         ref_h = oracle.bisect(hr, eps, "HDH", 7, 1, keep_levels=False)
         for call in range(3):
             parts, _ = h.partition(2, eps, "HDH", 7, 1)
             assert np.array_equal(parts, ref_h["side"].astype(np.int32)), ("HDH", call)
+            assert h.plan_active() == (call > 0), ("HDH", call)
         parts, _ = h.partition(2, eps, "LDH", 25, 2)
         assert np.array_equal(parts, ref["side"].astype(np.int32))
 
