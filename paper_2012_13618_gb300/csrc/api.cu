@@ -1208,14 +1208,14 @@ ProfScope::ProfScope(const char *name, double bytes, cudaStream_t s) {
     if (!g_prof_on) return;
     if (!g_prof_only.empty() && g_prof_only != name) return;
     if (tl_capturing) {
-        // inside a captured plan: event nodes at the top level of the graph only (conditional
-        // bodies may not hold event nodes); read back after every replay
+        // inside a captured plan: event record nodes (external records: a plain record during
+        // capture only orders work inside the graph), read back after every replay
         bipart_graph *g = tl_graph;
         if (!g) return;
         Probe p{name, bytes, nullptr, nullptr};
         cudaEventCreate(&p.a);
         cudaEventCreate(&p.b);
-        cudaEventRecord(p.a, s);
+        cudaEventRecordWithFlags(p.a, s, cudaEventRecordExternal);
         g->plan.probes.push_back(p);
         slot = -2 - (int)(g->plan.probes.size() - 1);
         return;
@@ -1231,7 +1231,8 @@ ProfScope::~ProfScope() {
     if (slot <= -2) {
         bipart_graph *g = tl_graph;
         size_t i = (size_t)(-2 - slot);
-        if (g && i < g->plan.probes.size()) cudaEventRecord(g->plan.probes[i].b, g->stream);
+        if (g && i < g->plan.probes.size())
+            cudaEventRecordWithFlags(g->plan.probes[i].b, g->stream, cudaEventRecordExternal);
         return;
     }
     if (slot < 0) return;

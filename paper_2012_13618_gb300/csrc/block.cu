@@ -23,13 +23,13 @@
 #include "common.cuh"
 #include "internal.h"
 #include "refine_dev.cuh"
+#include "scan.cuh"
 
 namespace bp {
 
 namespace {
 
 constexpr int kBT = 512;                  // threads per block
-constexpr int kScanItems = 8;             // items per thread per block-scan chunk
 constexpr int kMaxLev = 64;
 constexpr size_t kSmemBytes = 32 * 1024;  // union: bitmap window / gain histogram / sort keys
 
@@ -77,33 +77,6 @@ __device__ void blk_fill(T *a, size_t n, T v) {
     for (size_t i = threadIdx.x; i < n; i += blockDim.x) a[i] = v;
 }
 
-// Exclusive scan over n items inside the block: chunks of blockDim * kScanItems items, each
-// thread owning kScanItems consecutive ones; out(i, prefix, value) after all in() of a chunk.
-template <class In, class Out>
-__device__ void blk_scan(int64_t n, In in, Out out) {
-    __shared__ uint64_t red[33];
-    uint64_t carry = 0;
-    const int64_t chunk = (int64_t)blockDim.x * kScanItems;
-    for (int64_t base = 0; base < n; base += chunk) {
-        const int64_t i0 = base + (int64_t)threadIdx.x * kScanItems;
-        uint64_t v[kScanItems], sum = 0;
-#pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-            v[k] = i0 + k < n ? (uint64_t)in(i0 + k) : 0ull;
-            sum += v[k];
-        }
-        uint64_t total;
-        uint64_t run = carry + block_exclusive_scan<uint64_t>(sum, red, &total);
-#pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-            if (i0 + k < n) out(i0 + k, run, v[k]);
-            run += v[k];
-        }
-        carry += total;
-        __syncthreads();
-    }
-}
-
 struct Ctx {
     CtaTeam t;
     Arena ar;
@@ -136,7 +109,7 @@ __device__ bool blk_contract(Ctx &x, int E, int P, const int *hoff, const int *p
     c.hw = hw ? x.ar.take<int>((size_t)E) : nullptr;
     if (x.ar.overflow) return false;
     if (E > 0) {
-        blk_scan(E, CompactIn{cnt}, CompactOut{E, hw, c.hoff, c.hw, emap, counters + 2, nullptr});
+        block_scan_items(E, CompactIn{cnt}, CompactOut{E, hw, c.hoff, c.hw, emap, counters + 2, nullptr});
     } else if (threadIdx.x == 0) {
         c.hoff[0] = 0;
         counters[2] = counters[3] = 0;
@@ -160,7 +133,7 @@ __device__ bool blk_incidence(Ctx &x, DLevel &c) {
     c.cmap = x.ar.take<int>((size_t)c.N);
     c.match = x.ar.take<int>((size_t)c.N);
     if (x.ar.overflow) return false;
-    if (c.N > 0) blk_scan(c.N, DegIn{x.n_a}, DegOut{c.N, c.noff, x.n_b, nullptr});
+    if (c.N > 0) block_scan_items(c.N, DegIn{x.n_a}, DegOut{c.N, c.noff, x.n_b, nullptr});
     else if (threadIdx.x == 0) c.noff[0] = 0;
     __syncthreads();
     if (c.P > 0) d_fill_adj(x.t, c.E, c.P, c.hoff, c.pins, x.n_b, c.nadj);
@@ -191,7 +164,7 @@ __device__ bool blk_coarsen(Ctx &x, const DLevel &f, DLevel &c, int policy) {
     __syncthreads();
     d_group(x.t, N, f.match, ssize, best, grp, rep);
     __syncthreads();
-    if (N > 0) blk_scan(N, RenumIn{grp, rep}, RenumOut{N, grp, f.cmap, gcid, x.cnt4 + 2});
+    if (N > 0) block_scan_items(N, RenumIn{grp, rep}, RenumOut{N, grp, f.cmap, gcid, x.cnt4 + 2});
     __syncthreads();
     c.N = N > 0 ? x.cnt4[2] : 0;
     __syncthreads();
@@ -239,7 +212,7 @@ __device__ void blk_select_apply(Ctx &x, const DLevel &L, int kind, long long sq
             __syncthreads();
         }
     }
-    blk_scan(L.N, TieIn{kind, x.gain, side, L.nw, st}, ApplyOut{kind, x.gain, side, L.nw, st, x.list});
+    block_scan_items(L.N, TieIn{kind, x.gain, side, L.nw, st}, ApplyOut{kind, x.gain, side, L.nw, st, x.list});
     __syncthreads();
 }
 

@@ -30,6 +30,7 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kBigThreads = 512;  // block tier: one block per hyperedge
+constexpr int kFuseTiersPins = 2'000'000;  // mid and big tiers share a launch up to this many pins
 
 inline int grid_for(int64_t n, int per_block = kBlock, int cap = 152 * 16) {
     int64_t b = (n + per_block - 1) / per_block;
@@ -49,7 +50,25 @@ k_seg_small(int E, const int *__restrict__ hoff, const int *__restrict__ pins,
                      kGridMidDeg);
 }
 
-// Mid and big tiers in one launch: blocks [0, nbig) take the big list (one block per
+template <bool MAP>
+__global__ void __launch_bounds__(kBlock)
+k_seg_mid(const int *__restrict__ hoff, const int *__restrict__ pins, const int *__restrict__ cmap,
+          int *__restrict__ scratch, int *__restrict__ cnt, const int *__restrict__ list,
+          const int *__restrict__ counters) {
+    d_seg_mid<MAP>(GridTeam(), hoff, pins, cmap, scratch, cnt, list, counters);
+}
+
+template <bool MAP>
+__global__ void __launch_bounds__(kBigThreads)
+k_seg_big(const int *__restrict__ hoff, const int *__restrict__ pins, const int *__restrict__ cmap,
+          int *__restrict__ scratch, int *__restrict__ cnt, const int *__restrict__ list,
+          const int *__restrict__ counters) {
+    __shared__ uint32_t bits[kBigWords];
+    d_seg_big<MAP>(GridTeam(), hoff, pins, cmap, scratch, cnt, list, counters, bits);
+}
+
+// Mid and big tiers in one launch (small levels, where the launch is the larger cost; on large
+// levels the big tier's blocks would hold the GPU while the mid tier waits): blocks [0, nbig) take the big list (one block per
 // hyperedge, shared-memory bitmap), the others the mid list (one warp per hyperedge).  The two
 // lists are disjoint, so the tiers run side by side.
 template <bool MAP>
@@ -385,11 +404,21 @@ void seg_unique(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const in
     // warps for the mid tier (at most one per 9 pins), blocks for the big tier (at most one per
     // kGridMidDeg + 1 pins); the list lengths are only known on the device
     const int mid_warps = std::max(1, std::min(152 * 16 * (kBlock / 32), P / (kSmallDeg + 1) + 1));
-    const int nmid = ceil_div_i(mid_warps, kBigThreads / 32);
     const int nbig = std::max(1, std::min(152 * 4, P / (kGridMidDeg + 1) + 1));
-    if (map) k_seg_midbig<true><<<nbig + nmid, kBigThreads, 0, s>>>(nbig, hoff, pins, map, scratch, cnt, mid, big, small);
-    else k_seg_midbig<false><<<nbig + nmid, kBigThreads, 0, s>>>(nbig, hoff, pins, map, scratch, cnt, mid, big, small);
-    BP_LAUNCH();
+    if (P <= kFuseTiersPins) {
+        const int nmid = ceil_div_i(mid_warps, kBigThreads / 32);
+        if (map) k_seg_midbig<true><<<nbig + nmid, kBigThreads, 0, s>>>(nbig, hoff, pins, map, scratch, cnt, mid, big, small);
+        else k_seg_midbig<false><<<nbig + nmid, kBigThreads, 0, s>>>(nbig, hoff, pins, map, scratch, cnt, mid, big, small);
+        BP_LAUNCH();
+    } else {
+        const int mid_grid = ceil_div_i(mid_warps, kBlock / 32);
+        if (map) k_seg_mid<true><<<mid_grid, kBlock, 0, s>>>(hoff, pins, map, scratch, cnt, mid, small);
+        else k_seg_mid<false><<<mid_grid, kBlock, 0, s>>>(hoff, pins, map, scratch, cnt, mid, small);
+        BP_LAUNCH();
+        if (map) k_seg_big<true><<<nbig, kBigThreads, 0, s>>>(hoff, pins, map, scratch, cnt, big, small);
+        else k_seg_big<false><<<nbig, kBigThreads, 0, s>>>(hoff, pins, map, scratch, cnt, big, small);
+        BP_LAUNCH();
+    }
 }
 
 // Sorted-unique of every hyperedge's (mapped) pins into the coarse CSR of `c`.

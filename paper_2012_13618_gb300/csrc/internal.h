@@ -108,7 +108,10 @@ struct Work {
     Buf side_a, side_b;      // uint8 sides (ping-pong across levels)
     Buf gain;        // int32 gains
     Buf hc;          // int2 per-hyperedge gain contributions
-    Buf n1;          // int32 per-hyperedge side-1 pin counts (zero between gain passes)
+    Buf n1;          // int32 per-hyperedge side-1 pin counts: two halves used by alternate passes
+    int64_t n1_half = 0;
+    int64_t gain_pass = 0;   // gain passes so far in this bisection
+    int32_t n1_prev_E = 0;   // hyperedges counted by the previous pass (its half is dirty there)
     Buf e_best;      // per-hyperedge uint64 singleton-attach keys
     Buf m_fp, m_tkey, m_tmin, m_rep, m_wsum;  // parallel-net merging: fingerprints, table, groups
     Buf list;        // node list (rebalance candidates)

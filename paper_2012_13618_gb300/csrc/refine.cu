@@ -35,25 +35,40 @@ inline int grid_for(int64_t n, int per_block = kBlock, int cap = 152 * 16) {
     return (int)std::min<int64_t>(b, cap);
 }
 
-// Selection passes over up to this many nodes run as one block.
+// Selection passes over up to this many nodes run as one block of kSelOneThreads threads (the
+// histogram, the threshold and the application in one launch).
 constexpr int kSelOneBlock = 8192;
+constexpr int kSelOneThreads = 1024;
 
 inline int sel_grid(int N) { return N <= kSelOneBlock ? 1 : grid_for(N); }
+inline int sel_threads(int N) { return N <= kSelOneBlock ? kSelOneThreads : kBlock; }
+
+// Levels up to this many pins compute gains without the separate contribution pass.
+constexpr int kDirectGainPins = 2'000'000;
 
 }  // namespace
 
 // Grid kernels: one launch per phase (device code in refine_dev.cuh).
+// Side-1 pin counts of this pass into n1, plus two clearing jobs for the pass: the other count
+// buffer over the previous pass's hyperedges (it alternates with n1 from pass to pass), and the
+// gains that k_node_gain accumulates.
 __global__ void __launch_bounds__(kLbBlock)
 k_hedge_n1(int E, int P, const int *__restrict__ hoff, const int *__restrict__ pins,
-           const uint8_t *__restrict__ side, int *__restrict__ n1, const int *__restrict__ ts) {
+           const uint8_t *__restrict__ side, int *__restrict__ n1, const int *__restrict__ ts,
+           int *__restrict__ n1_prev, int E_prev, int *__restrict__ gain, int N) {
     d_hedge_n1(GridTeam(), E, P, hoff, pins, side, n1, ts);
+    const int n = E_prev > N ? E_prev : N;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (i < E_prev) n1_prev[i] = 0;
+        if (i < N) gain[i] = 0;
+    }
 }
 
-// Contributions, n1 put back to zero, and the gains of the N nodes cleared for k_node_gain.
-__global__ void k_hedge_contrib(int E, int N, const int *__restrict__ hoff, const int *__restrict__ hw,
-                                int *__restrict__ n1, int2 *__restrict__ hc, int *__restrict__ gain) {
-    d_hedge_contrib(GridTeam(), E, hoff, hw, n1, hc, true);
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) gain[v] = 0;
+
+// Gains from per-hyperedge contributions (large levels: one 8-byte gather per incidence) ...
+__global__ void k_hedge_contrib(int E, const int *__restrict__ hoff, const int *__restrict__ hw,
+                                int *__restrict__ n1, int2 *__restrict__ hc) {
+    d_hedge_contrib(GridTeam(), E, hoff, hw, n1, hc, false);
 }
 
 __global__ void __launch_bounds__(kLbBlock)
@@ -61,6 +76,15 @@ k_node_gain(int N, int P, const int *__restrict__ noff, const int *__restrict__ 
             const int2 *__restrict__ hc, const uint8_t *__restrict__ side, int *__restrict__ gain,
             const int *__restrict__ ts) {
     d_node_gain(GridTeam(), N, P, noff, nadj, hc, side, gain, ts);
+}
+
+// ... or formed on the spot (small levels, where the contribution pass costs more as a launch
+// than its gathers save).
+__global__ void __launch_bounds__(kLbBlock)
+k_node_gain_direct(int N, int P, const int *__restrict__ noff, const int *__restrict__ nadj,
+                   const int *__restrict__ hoff, const int *__restrict__ hw, const int *__restrict__ n1,
+                   const uint8_t *__restrict__ side, int *__restrict__ gain, const int *__restrict__ ts) {
+    d_node_gain_direct(GridTeam(), N, P, noff, nadj, hoff, hw, n1, side, gain, ts);
 }
 
 // Copies the grid's accumulated histogram into shared memory and clears it in global memory
@@ -76,11 +100,12 @@ __device__ __forceinline__ void take_hist(RState *st, unsigned (*h)[kHistBins]) 
 
 // Fast selection pass: clamped-gain histogram, then (last block) the per-group threshold.  The
 // rebalancing list is emptied for the application scan that follows.  One block (small levels)
-// keeps its histogram in shared memory and also runs the exact radix passes when needed, leaving
-// st->slow clear; a grid leaves st->slow for the exact passes (and in its check slot).
-__global__ void __launch_bounds__(kBlock)
-k_sel(int N, int kind, long long s, const int *__restrict__ gain, const uint8_t *__restrict__ side,
-      const int *__restrict__ nw, RState *st, unsigned *slow_slot, uint32_t *status) {
+// keeps its histogram in shared memory, runs the exact radix passes when needed (leaving
+// st->slow clear) and applies the selection itself; a grid leaves st->slow for the exact passes
+// (and in its check slot) and the application to the scan launched after it.
+__global__ void __launch_bounds__(kSelOneThreads, 1)
+k_sel(int N, int kind, long long s, const int *__restrict__ gain, uint8_t *side,
+      const int *__restrict__ nw, RState *st, unsigned *slow_slot, uint32_t *status, int *list) {
     __shared__ unsigned h[2][kHistBins];
     const bool one = gridDim.x == 1;
     d_sel_hist(GridTeam(), N, kind, gain, side, nw, st, h, !one);
@@ -98,7 +123,10 @@ k_sel(int N, int kind, long long s, const int *__restrict__ gain, const uint8_t 
                 d_sel_find_exact(st, status, h);
             }
             if (threadIdx.x == 0) st->slow = 0;
+            __syncthreads();
         }
+        // the tie ranks and the application, in the same block
+        block_scan_items(N, TieIn{kind, gain, side, nw, st}, ApplyOut{kind, gain, side, nw, st, list});
     } else if (slow_slot && threadIdx.x == 0) {
         *slow_slot = st->slow;
     }
@@ -198,32 +226,42 @@ RState *rstate(bipart_graph *g) {
     return reinterpret_cast<RState *>(g->w.small.as<char>() + 256);
 }
 
-// n1 (per-hyperedge side-1 counts) is zero at rest: k_hedge_contrib clears what k_hedge_n1
-// counted, and it clears the gains too, so no memset runs per pass.
+// Algorithm 4.  The side-1 counts alternate between two buffers from pass to pass: a pass counts
+// into one while its k_hedge_n1 clears the other (dirty over the previous pass's hyperedges) and
+// the gains; k_node_gain forms every hyperedge's contribution from its degree, count and weight.
 void compute_gains(bipart_graph *g, Level &L, const uint8_t *side, int *gain) {
     cudaStream_t s = g->stream;
-    int *n1 = g->w.n1.as<int>();
-    int2 *hc = g->w.hc.as<int2>();
-    if (L.E > 0) {
-        {
-            // hoff, pins, one side byte per pin, one atomic per hyperedge run
-            ProfScope ps("hedge_n1", 8.0 * L.E + 5.0 * L.P, s);
-            k_hedge_n1<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.E, L.P, L.hoff(), L.pins(), side, n1, L.tsh());
-            BP_LAUNCH();
-        }
+    Work &w = g->w;
+    const int cur = w.gain_pass & 1;
+    int *n1 = w.n1.as<int>() + (size_t)cur * w.n1_half;
+    int *n1_prev = w.n1.as<int>() + (size_t)(cur ^ 1) * w.n1_half;
+    {
+        // hoff, pins, one side byte per pin, one atomic per hyperedge run; clearing
+        ProfScope ps("hedge_n1", 8.0 * L.E + 5.0 * L.P + 4.0 * w.n1_prev_E + 4.0 * L.N, s);
+        const int64_t work = std::max<int64_t>({(int64_t)L.P, (int64_t)w.n1_prev_E, (int64_t)L.N});
+        k_hedge_n1<<<lb_grid(work), kLbBlock, 0, s>>>(L.E, L.P, L.hoff(), L.pins(), side, n1, L.tsh(),
+                                                       n1_prev, w.n1_prev_E, gain, L.N);
+        BP_LAUNCH();
+    }
+    w.gain_pass++;
+    w.n1_prev_E = L.E;
+    if (L.P == 0) return;
+    if (L.P > kDirectGainPins) {
+        int2 *hc = w.hc.as<int2>();
         {
             ProfScope ps("hedge_contrib", 16.0 * L.E + (L.hw() ? 4.0 * L.E : 0.0), s);
-            k_hedge_contrib<<<grid_for(std::max(L.E, L.N)), kBlock, 0, s>>>(L.E, L.N, L.hoff(), L.hw(),
-                                                                            n1, hc, gain);
+            k_hedge_contrib<<<grid_for(L.E), kBlock, 0, s>>>(L.E, L.hoff(), L.hw(), n1, hc);
             BP_LAUNCH();
         }
-    } else if (L.N > 0) {
-        BP_CUDA(cudaMemsetAsync(gain, 0, sizeof(int) * (size_t)L.N, s));
-    }
-    if (L.P > 0) {
         // noff, nadj, 8-byte contribution gather per incidence, side, gain
         ProfScope ps("node_gain", 9.0 * L.N + 12.0 * L.P, s);
         k_node_gain<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.N, L.P, L.noff(), L.nadj(), hc, side, gain, L.tsn());
+        BP_LAUNCH();
+    } else {
+        // noff, nadj, gathers of two offsets and a count (and a weight) per incidence, side, gain
+        ProfScope ps("node_gain", 9.0 * L.N + 16.0 * L.P + (L.hw() ? 4.0 * L.P : 0.0), s);
+        k_node_gain_direct<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.N, L.P, L.noff(), L.nadj(), L.hoff(), L.hw(),
+                                                             n1, side, gain, L.tsn());
         BP_LAUNCH();
     }
 }
@@ -237,16 +275,17 @@ void select_apply(bipart_graph *g, Level &L, int kind, long long sq, const int *
     unsigned *slot = one ? nullptr : flag_slot(g);
     {
         ProfScope ps("select_hist", 9.0 * L.N, s);
-        k_sel<<<sel_grid(L.N), kBlock, 0, s>>>(L.N, kind, sq, gain, side, L.nw(), st, slot, dev_status(g));
+        k_sel<<<sel_grid(L.N), sel_threads(L.N), 0, s>>>(L.N, kind, sq, gain, side, L.nw(), st, slot,
+                                                         dev_status(g), list);
         BP_LAUNCH();
     }
-    if (!one && device_flag(g, &st->slow)) {
+    if (one) return;  // applied by k_sel
+    if (device_flag(g, &st->slow)) {
         for (int pass = 0; pass < 3; ++pass) {
             k_sel_exact<<<sel_grid(L.N), kBlock, 0, s>>>(L.N, kind, gain, side, L.nw(), st, dev_status(g));
             BP_LAUNCH();
         }
     }
-    s = g->stream;
     ProfScope ps("select_apply", 10.0 * L.N, s);
     scan(L.N, TieIn{kind, gain, side, L.nw(), st}, ApplyOut{kind, gain, side, L.nw(), st, list},
          g->w.scan.ensure_zero(scan_state_bytes(L.N), s), dev_status(g), s);
@@ -324,9 +363,13 @@ void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, const int64_t limi
     uint8_t *sb = (uint8_t *)g->w.side_b.ensure((size_t)nmax, s);
     int *gain = (int *)g->w.gain.ensure(sizeof(int) * (size_t)nmax, s);
     g->w.hc.ensure(sizeof(int2) * (size_t)emax, s);
-    // zero at rest between passes; cleared here once in case an earlier run stopped midway
-    void *n1 = g->w.n1.ensure(sizeof(int) * (size_t)emax, s);
-    BP_CUDA(cudaMemsetAsync(n1, 0, sizeof(int) * (size_t)emax, s));
+    // two halves of emax counts, both zero at the start of a bisection (cleared here once in case
+    // an earlier run stopped midway)
+    g->w.n1_half = emax;
+    void *n1 = g->w.n1.ensure(sizeof(int) * 2 * (size_t)emax, s);
+    BP_CUDA(cudaMemsetAsync(n1, 0, sizeof(int) * 2 * (size_t)emax, s));
+    g->w.gain_pass = 0;
+    g->w.n1_prev_E = 0;
 
     uint8_t *cur = sa, *other = sb;
     initial_partition(g, *levels[Lc], cur, gain, m0, m);

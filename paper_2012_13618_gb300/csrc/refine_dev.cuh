@@ -98,6 +98,27 @@ __device__ void d_node_gain(Team t, int N, int P, const int *noff, const int *na
         t, ts);
 }
 
+// The same gains with each hyperedge's contribution formed on the spot from its degree, its
+// side-1 count and its weight (no separate contribution pass).
+template <class Team>
+__device__ void d_node_gain_direct(Team t, int N, int P, const int *noff, const int *nadj,
+                                   const int *hoff, const int *hw, const int *n1,
+                                   const uint8_t *side, int *gain, const int *ts = nullptr) {
+    lb_for_each_items<int>(
+        noff, N, P, nadj, 0,
+        [&](int v, int e, int acc) {
+            const int d = Team::ld(hoff + e + 1) - Team::ld(hoff + e);
+            const int a1 = Team::ld(n1 + e);
+            const int w = hw ? Team::ld(hw + e) : 1;
+            const int a = Team::ld(side + v) ? a1 : d - a1;  // pins on v's side
+            return acc + (a == 1 ? w : (a == d ? -w : 0));
+        },
+        [&](int v, int acc) {
+            if (acc) atomicAdd(gain + v, acc);
+        },
+        t, ts);
+}
+
 // ------------------------------------------------------------------------ selection
 // Fast pass: histogram of clamped gains per group (h: 2 * kHistBins shared counters).
 // Without `flush` the histogram stays in h (a one-block pass that searches it itself).

@@ -19,6 +19,7 @@ constexpr int kScanTile = kScanBlock * kScanItems;
 constexpr uint64_t kScanValMask = (1ull << 62) - 1;
 constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagPre = 2ull << 62;
+constexpr int kLookR = 4;  // predecessors per lane in one look-back round
 
 // `state` points at [tile counter, finished-block counter, tile status words ...], all zero at
 // launch.  Every block counts itself finished after its last read of a tile state; the block
@@ -66,39 +67,53 @@ k_scan(int64_t n, In in, Out out, unsigned long long *state, uint32_t *status) {
             s_last = 0;
         }
     } else if (threadIdx.x < 32) {
-        // warp 0 looks back over its predecessors 32 at a time (lane l reads tile j - l): it adds
-        // aggregates up to the nearest tile that already holds its inclusive prefix
+        // warp 0 looks back over its predecessors 32 * kLookR at a time: it adds aggregates up to
+        // the nearest tile that already holds its inclusive prefix
         const int lane = threadIdx.x;
         uint64_t prefix = 0;
         if (tile == 0) {
             if (lane == 0) atomicExch(&tiles[0], (unsigned long long)(kFlagPre | (total & kScanValMask)));
         } else {
             if (lane == 0) atomicExch(&tiles[tile], (unsigned long long)(kFlagAgg | (total & kScanValMask)));
+            // each lane reads kLookR consecutive predecessors: one round covers 32 * kLookR tiles
             int64_t j = tile - 1;
             for (;;) {
-                const int64_t idx = j - lane;
-                uint64_t st = kFlagPre;  // before tile 0: an inclusive prefix of 0
-                if (idx >= 0) {
-                    int spins = 0;
-                    for (;;) {
-                        st = *((volatile unsigned long long *)&tiles[idx]);
-                        if ((st >> 62) != 0) break;
-                        if (++spins > kSpinLimit) break;
-                        if (spins > 64) __nanosleep(64);
+                uint64_t st[kLookR];
+                bool bad = false, inc_here = false;
+#pragma unroll
+                for (int r = 0; r < kLookR; ++r) {
+                    const int64_t idx = j - (int64_t)lane * kLookR - r;
+                    st[r] = kFlagPre;  // before tile 0: an inclusive prefix of 0
+                    if (idx >= 0) {
+                        int spins = 0;
+                        for (;;) {
+                            st[r] = *((volatile unsigned long long *)&tiles[idx]);
+                            if ((st[r] >> 62) != 0) break;
+                            if (++spins > kSpinLimit) break;
+                            if (spins > 64) __nanosleep(64);
+                        }
                     }
+                    bad |= (st[r] >> 62) == 0;
+                    inc_here |= (st[r] >> 62) == 2;
                 }
-                if (__ballot_sync(0xffffffffu, (st >> 62) == 0)) {  // a predecessor never published
+                if (__ballot_sync(0xffffffffu, bad)) {  // a predecessor never published
                     if (lane == 0) record_error(status, DEV_TIMEOUT);
                     break;
                 }
-                const unsigned inc = __ballot_sync(0xffffffffu, (st >> 62) == 2);
-                const int stop = inc ? __ffs(inc) - 1 : 31;  // nearest inclusive prefix
-                uint64_t v = lane <= stop ? (st & kScanValMask) : 0ull;
+                const unsigned inc = __ballot_sync(0xffffffffu, inc_here);
+                const int stop_lane = inc ? __ffs(inc) - 1 : 32;  // lane holding the nearest inclusive
+                uint64_t v = 0;
+                bool stopped = false;
+#pragma unroll
+                for (int r = 0; r < kLookR; ++r) {
+                    if (lane < stop_lane || (lane == stop_lane && !stopped)) v += st[r] & kScanValMask;
+                    if (lane == stop_lane && (st[r] >> 62) == 2) stopped = true;
+                }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 prefix += v;
                 if (inc) break;
-                j -= 32;
+                j -= 32 * kLookR;
             }
             if (lane == 0)
                 atomicExch(&tiles[tile], (unsigned long long)(kFlagPre | ((prefix + total) & kScanValMask)));
@@ -129,6 +144,34 @@ k_scan(int64_t n, In in, Out out, unsigned long long *state, uint32_t *status) {
     for (int k = 0; k < kScanItems; ++k) {
         int64_t i = base + k * kScanBlock + threadIdx.x;
         if (i < n) out(i, s_pre[k * kScanBlock + threadIdx.x], s_val[k * kScanBlock + threadIdx.x]);
+    }
+}
+
+// Exclusive scan over n items by one block: chunks of blockDim * kScanItems items, each thread
+// owning kScanItems consecutive ones; out(i, prefix, value) after all in() of the chunk.  Used
+// where a whole phase runs in one block (small levels; the persistent batch kernel).
+template <class In, class Out>
+__device__ void block_scan_items(int64_t n, In in, Out out) {
+    __shared__ uint64_t red[33];
+    uint64_t carry = 0;
+    const int64_t chunk = (int64_t)blockDim.x * kScanItems;
+    for (int64_t base = 0; base < n; base += chunk) {
+        const int64_t i0 = base + (int64_t)threadIdx.x * kScanItems;
+        uint64_t v[kScanItems], sum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            v[k] = i0 + k < n ? (uint64_t)in(i0 + k) : 0ull;
+            sum += v[k];
+        }
+        uint64_t total;
+        uint64_t run = carry + block_exclusive_scan<uint64_t>(sum, red, &total);
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if (i0 + k < n) out(i0 + k, run, v[k]);
+            run += v[k];
+        }
+        carry += total;
+        __syncthreads();
     }
 }
 
