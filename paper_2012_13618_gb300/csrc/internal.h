@@ -114,6 +114,7 @@ struct Work {
     int32_t n1_prev_E = 0;   // hyperedges counted by the previous pass (its half is dirty there)
     Buf e_best;      // per-hyperedge uint64 singleton-attach keys
     Buf m_fp, m_tkey, m_tmin, m_rep, m_wsum;  // parallel-net merging: fingerprints, table, groups
+    Buf partial;     // per-block partial sums of grid-wide reductions
     Buf list;        // node list (rebalance candidates)
     Buf pinned;      // host-pinned mirror of `small`
     uint32_t *host_small = nullptr;

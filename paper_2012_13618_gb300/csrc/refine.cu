@@ -40,8 +40,11 @@ inline int grid_for(int64_t n, int per_block = kBlock, int cap = 152 * 16) {
 constexpr int kSelOneBlock = 8192;
 constexpr int kSelOneThreads = 1024;
 
-inline int sel_grid(int N) { return N <= kSelOneBlock ? 1 : grid_for(N); }
+inline int sel_grid(int N) { return N <= kSelOneBlock ? 1 : std::min(grid_for(N), 608); }
 inline int sel_threads(int N) { return N <= kSelOneBlock ? kSelOneThreads : kBlock; }
+
+// Blocks of a grid-wide sum (each block stores its partial; the last block adds them).
+constexpr int kReduceBlocks = 608;
 
 // Levels up to this many pins compute gains without the separate contribution pass.
 constexpr int kDirectGainPins = 2'000'000;
@@ -169,12 +172,33 @@ __device__ __forceinline__ void eval_cond(RState *st, const CondArgs &c, uint32_
 // then evaluates the loop condition that needs W (if any).
 __global__ void __launch_bounds__(kBlock)
 k_side_weights(int N, const uint8_t *__restrict__ side, const int *__restrict__ nw, RState *st,
-               CondArgs cond, uint32_t *status) {
-    d_side_weights(GridTeam(), N, side, nw, st->Wacc);
+               CondArgs cond, uint32_t *status, unsigned long long *__restrict__ partial) {
+    __shared__ unsigned long long red[33];
+    // per block: both sums reduced in the block and stored (no contended atomics); the last
+    // block adds the partials in block order
+    unsigned long long w0 = 0, w1 = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
+        const unsigned long long w = (unsigned long long)nw[v];
+        if (side[v]) w1 += w;
+        else w0 += w;
+    }
+    w0 = block_sum(w0, red);
+    w1 = block_sum(w1, red);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = w0;
+        partial[2 * blockIdx.x + 1] = w1;
+    }
     if (!last_block(&st->arrived)) return;
-    if (threadIdx.x < 2) {
-        st->W[threadIdx.x] = __ldcg(&st->Wacc[threadIdx.x]);
-        st->Wacc[threadIdx.x] = 0ull;
+    unsigned long long s0 = 0, s1 = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        s0 += __ldcg(partial + 2 * b);
+        s1 += __ldcg(partial + 2 * b + 1);
+    }
+    s0 = block_sum(s0, red);
+    s1 = block_sum(s1, red);
+    if (threadIdx.x == 0) {
+        st->W[0] = s0;
+        st->W[1] = s1;
     }
     __syncthreads();
     eval_cond(st, cond, status);
@@ -294,7 +318,9 @@ void select_apply(bipart_graph *g, Level &L, int kind, long long sq, const int *
 void side_weights(bipart_graph *g, Level &L, const uint8_t *side, const CondArgs &cond) {
     cudaStream_t s = g->stream;
     RState *st = rstate(g);
-    k_side_weights<<<grid_for(L.N), kBlock, 0, s>>>(L.N, side, L.nw(), st, cond, dev_status(g));
+    const int grid = std::min(grid_for(L.N), kReduceBlocks);
+    auto *partial = (unsigned long long *)g->w.partial.as<void>();
+    k_side_weights<<<grid, kBlock, 0, s>>>(L.N, side, L.nw(), st, cond, dev_status(g), partial);
     BP_LAUNCH();
 }
 
@@ -363,6 +389,7 @@ void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, const int64_t limi
     uint8_t *sb = (uint8_t *)g->w.side_b.ensure((size_t)nmax, s);
     int *gain = (int *)g->w.gain.ensure(sizeof(int) * (size_t)nmax, s);
     g->w.hc.ensure(sizeof(int2) * (size_t)emax, s);
+    g->w.partial.ensure(sizeof(unsigned long long) * 2 * kReduceBlocks, s);
     // two halves of emax counts, both zero at the start of a bisection (cleared here once in case
     // an earlier run stopped midway)
     g->w.n1_half = emax;
