@@ -304,21 +304,13 @@ struct DegOut {
 template <class Team, class Claim>
 __device__ void d_fill_adj_with(Team t, int E, int P, const int *hoff, const int *pins, int *nadj,
                                 Claim claim, const int *ts = nullptr) {
-    const int tile = blockDim.x * kLbItems;
-    for (int64_t t0 = (int64_t)t.block() * tile; t0 < P; t0 += (int64_t)t.blocks() * tile) {
-        const int j0 = (int)t0;
-        const int j1 = (int)(t0 + tile < P ? t0 + tile : P);
-        const LbTile T = lb_tile<Team>(hoff, E, P, j0, j1, ts);
-        const int j = j0 + threadIdx.x * kLbItems;
-        if (j >= j1) continue;
-        const int n = j1 - j < kLbItems ? j1 - j : kLbItems;
-        int s = lb_tile_seg<Team>(hoff, T, j);
-        int send = lb_tile_end<Team>(hoff, T, s);
+    lb_schedule(hoff, E, P, ts, t, [&](int j, int n, int s, auto end) {
+        int send = end(s);
         int v[kLbItems], e[kLbItems], pos[kLbItems];
 #pragma unroll
         for (int k = 0; k < kLbItems; ++k) {
             if (k < n) {
-                while (j + k >= send) { ++s; send = lb_tile_end<Team>(hoff, T, s); }
+                while (j + k >= send) { ++s; send = end(s); }
                 e[k] = s;
                 v[k] = Team::ld(pins + j + k);
             }
@@ -329,7 +321,7 @@ __device__ void d_fill_adj_with(Team t, int E, int P, const int *hoff, const int
 #pragma unroll
         for (int k = 0; k < kLbItems; ++k)
             if (k < n) nadj[pos[k]] = e[k];
-    }
+    });
 }
 
 // Incidence fill claiming positions from the global per-node cursor (cursor starts at the node's

@@ -1,10 +1,16 @@
-// Load-balanced segmented reductions over a CSR (offsets off[0..nseg], items [0, total)).
+// Load-balanced segmented loops over a CSR (offsets off[0..nseg], items [0, total)).
 //
-// A block owns kLbTile consecutive items; each thread owns kLbItems consecutive items of that
-// tile, finds the segment of its first item inside the block's segment range (staged in shared
-// memory) and walks forward.  Per-segment partial results are flushed with one atomic per segment run,
-// so a segment with 100,000 items costs the same per item as one with 2 items, and the result
-// does not depend on the schedule when the combining operation is an integer sum or minimum.
+// Every thread owns kLbItems consecutive items, finds the segment of its first item and walks
+// forward.  Per-segment partial results are flushed with one atomic per segment run, so a
+// segment with 100,000 items costs the same per item as one with 2 items, and the result does
+// not depend on the schedule when the combining operation is an integer sum or minimum.
+//
+// Two schedules.  With a tile-start table (the CSRs of the hierarchy's levels), a warp takes a
+// warp tile of kWarpTile items, reads the tile's segment range with two loads and its lanes
+// search that short range in cached global memory -- no block barriers.  Without one (input
+// CSRs; the one-block batch path), a block takes a tile of blockDim * kLbItems items, warps 0
+// and 1 find its segment range with a 32-way warp search, and the offsets are staged in shared
+// memory for the threads' searches.
 #pragma once
 
 #include "common.cuh"
@@ -14,14 +20,14 @@ namespace bp {
 constexpr int kLbBlock = 256;
 constexpr int kLbItems = 8;
 constexpr int kLbTile = kLbBlock * kLbItems;
+constexpr int kWarpTile = 32 * kLbItems;
 
-constexpr int kLbStage = 2048;  // segment offsets of one tile staged in shared memory
-constexpr int kTsGran = 2048;   // tile-start tables hold the segment of every item j = t * kTsGran
+constexpr int kLbStage = 2048;      // segment offsets of one block tile staged in shared memory
+constexpr int kTsGran = kWarpTile;  // tile-start tables hold the segment of every item t * kTsGran
 
 // Tile-start table: ts[t] = the segment holding item t * kTsGran, for every such item < total.
-// Written while the CSR offsets are produced (by the thread that owns segment `seg`, which holds
-// items [a, a + len)); load-balanced loops over that CSR then find their tiles' segment ranges
-// with two loads instead of a search.  Needs blockDim.x * kLbItems to be a multiple of kTsGran.
+// Written while the CSR offsets are produced, by the thread that owns segment `seg` (items
+// [a, a + len)).
 __device__ __forceinline__ void lb_mark_tiles(int *ts, int seg, int64_t a, int64_t len) {
     if (!ts || len <= 0) return;
     for (int64_t t = (a + kTsGran - 1) / kTsGran; t * kTsGran < a + len; ++t) ts[t] = seg;
@@ -60,88 +66,81 @@ __device__ __forceinline__ int lb_seg_warp(const int *off, int j, int lo, int hi
     return lo + __popc(below);
 }
 
-// Shared staging buffer of the load-balanced loops (one per kernel).
+// Shared staging buffer of the block schedule (one per kernel).
 __device__ __forceinline__ int *lb_stage() {
     __shared__ int buf[kLbStage + 2];
     return buf;
 }
 
-// Segments [s0, s1] of the tile of items [j0, j1) (a superset: s1 may be the segment of item j1):
-// read from the tile-start table ts when there is one, else warps 0 and 1 search the segments
-// of the first and the last item; off[s0 .. s1 + 1] is then staged in shared memory when it
-// fits.  Called by the whole block (blockDim >= 64).
-struct LbTile {
-    int s0, s1;
-    bool staged;
-};
-
-template <class Team>
-__device__ __forceinline__ LbTile lb_tile(const int *off, int nseg, int total, int j0, int j1,
-                                          const int *ts) {
+// Calls fn(j, n, s, end) for every run of n <= kLbItems consecutive items [j, j + n) owned by
+// this thread, s = the segment of item j and end(x) = off[x + 1] for the segments of the run's
+// tile.  fn must not use block-wide barriers or warp-collective operations.
+template <class Fn, class Team = GridTeam>
+__device__ __forceinline__ void lb_schedule(const int *off, int nseg, int total, const int *ts,
+                                            Team t, Fn fn) {
+    if (ts) {
+        const int lane = threadIdx.x & 31;
+        const int64_t tiles = ((int64_t)total + kWarpTile - 1) / kWarpTile;
+        auto end = [&](int x) { return Team::ld(off + x + 1); };
+        for (int64_t w = t.warp(); w < tiles; w += t.warps()) {
+            const int j0 = (int)(w * kWarpTile);
+            const int j1 = (int)(w * kWarpTile + kWarpTile < total ? w * kWarpTile + kWarpTile : total);
+            const int j = j0 + lane * kLbItems;
+            if (j >= j1) continue;
+            const int s0 = Team::ld(ts + w);
+            const int s1 = j1 < total ? Team::ld(ts + w + 1) : nseg - 1;
+            fn(j, j1 - j < kLbItems ? j1 - j : kLbItems, lb_seg<Team>(off, j, s0, s1), end);
+        }
+        return;
+    }
     __shared__ int s_rng[2];
     int *st = lb_stage();
-    __syncthreads();  // the previous tile is done with the stage
-    LbTile T;
-    if (ts) {
-        T.s0 = Team::ld(ts + j0 / kTsGran);
-        T.s1 = j1 < total ? Team::ld(ts + j1 / kTsGran) : nseg - 1;
-    } else {
+    const int tile = blockDim.x * kLbItems;
+    for (int64_t t0 = (int64_t)t.block() * tile; t0 < total; t0 += (int64_t)t.blocks() * tile) {
+        const int j0 = (int)t0;
+        const int j1 = (int)(t0 + tile < total ? t0 + tile : total);
+        __syncthreads();  // the previous tile is done with the stage
         const int w = threadIdx.x >> 5;
         if (w < 2) {
-            const int s = lb_seg_warp<Team>(off, w == 0 ? j0 : j1 - 1, 0, nseg - 1);
-            if ((threadIdx.x & 31) == 0) s_rng[w] = s;
+            const int x = lb_seg_warp<Team>(off, w == 0 ? j0 : j1 - 1, 0, nseg - 1);
+            if ((threadIdx.x & 31) == 0) s_rng[w] = x;
         }
         __syncthreads();
-        T.s0 = s_rng[0];
-        T.s1 = s_rng[1];
+        const int s0 = s_rng[0], s1 = s_rng[1];
+        const int cnt = s1 - s0 + 2;
+        const bool staged = cnt <= kLbStage + 2;
+        if (staged)
+            for (int i = threadIdx.x; i < cnt; i += blockDim.x) st[i] = Team::ld(off + s0 + i);
+        __syncthreads();
+        const int j = j0 + threadIdx.x * kLbItems;
+        if (j >= j1) continue;
+        int s;
+        if (staged) {
+            int lo = 0, hi = s1 - s0;
+            while (lo < hi) {
+                int m = (lo + hi + 1) >> 1;
+                if (st[m] <= j) lo = m;
+                else hi = m - 1;
+            }
+            s = s0 + lo;
+        } else {
+            s = lb_seg<Team>(off, j, s0, s1);
+        }
+        auto end = [&](int x) { return staged ? st[x - s0 + 1] : Team::ld(off + x + 1); };
+        fn(j, j1 - j < kLbItems ? j1 - j : kLbItems, s, end);
     }
-    T.staged = false;
-    const int cnt = T.s1 - T.s0 + 2;
-    T.staged = cnt <= kLbStage + 2;
-    if (T.staged)
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) st[i] = Team::ld(off + T.s0 + i);
-    __syncthreads();
-    return T;
-}
-
-// Segment of item j of the tile.
-template <class Team>
-__device__ __forceinline__ int lb_tile_seg(const int *off, const LbTile &T, int j) {
-    if (!T.staged) return lb_seg<Team>(off, j, T.s0, T.s1);
-    const int *st = lb_stage();
-    int lo = 0, hi = T.s1 - T.s0;
-    while (lo < hi) {
-        int m = (lo + hi + 1) >> 1;
-        if (st[m] <= j) lo = m;
-        else hi = m - 1;
-    }
-    return T.s0 + lo;
-}
-
-// off[s + 1] for a segment s of the tile.
-template <class Team>
-__device__ __forceinline__ int lb_tile_end(const int *off, const LbTile &T, int s) {
-    return T.staged ? lb_stage()[s - T.s0 + 1] : Team::ld(off + s + 1);
 }
 
 // Segmented reduction over a CSR for a visit that reads one int per item: items[j] is loaded
 // for all of the thread's slots up front (two 16-byte loads when its kLbItems slots are in range
 // and aligned); visit(seg, items[j], acc) folds it in and flush(seg, acc) ends every segment run
-// of the thread.  `init` is the identity of the combine operation.  A tile is
-// blockDim.x * kLbItems items; the team's blocks take tiles in turn.
+// of the thread.  `init` is the identity of the combine operation.
 template <class Acc, class Visit, class Flush, class Team = GridTeam>
 __device__ __forceinline__ void lb_for_each_items(const int *off, int nseg, int total, const int *items,
                                                   Acc init, Visit visit, Flush flush, Team t = Team(),
                                                   const int *ts = nullptr) {
     static_assert(kLbItems == 8, "two int4 loads per thread");
-    const int tile = blockDim.x * kLbItems;
-    for (int64_t t0 = (int64_t)t.block() * tile; t0 < total; t0 += (int64_t)t.blocks() * tile) {
-        const int j0 = (int)t0;
-        const int j1 = (int)(t0 + tile < total ? t0 + tile : total);
-        const LbTile T = lb_tile<Team>(off, nseg, total, j0, j1, ts);
-        const int j = j0 + threadIdx.x * kLbItems;
-        if (j >= j1) continue;
-        const int n = j1 - j < kLbItems ? j1 - j : kLbItems;
+    lb_schedule(off, nseg, total, ts, t, [&](int j, int n, int s, auto end) {
         int it[kLbItems];
         if (n == kLbItems && ((reinterpret_cast<uintptr_t>(items + j) & 15) == 0)) {
             const int4 a = Team::ld(reinterpret_cast<const int4 *>(items + j));
@@ -152,8 +151,7 @@ __device__ __forceinline__ void lb_for_each_items(const int *off, int nseg, int 
 #pragma unroll
             for (int k = 0; k < kLbItems; ++k) it[k] = k < n ? Team::ld(items + j + k) : 0;
         }
-        int s = lb_tile_seg<Team>(off, T, j);
-        int send = lb_tile_end<Team>(off, T, s);
+        int send = end(s);
         Acc acc = init;
 #pragma unroll
         for (int k = 0; k < kLbItems; ++k) {
@@ -162,13 +160,13 @@ __device__ __forceinline__ void lb_for_each_items(const int *off, int nseg, int 
                     flush(s, acc);
                     acc = init;
                     ++s;
-                    send = lb_tile_end<Team>(off, T, s);
+                    send = end(s);
                 }
                 acc = visit(s, it[k], acc);
             }
         }
         flush(s, acc);
-    }
+    });
 }
 
 // Calls fn(s, a, b) for every maximal run [a, b) of this thread's items that lies in segment s,
@@ -176,23 +174,16 @@ __device__ __forceinline__ void lb_for_each_items(const int *off, int nseg, int 
 template <class Fn, class Team = GridTeam>
 __device__ __forceinline__ void lb_runs(const int *off, int nseg, int total, Fn fn, Team t = Team(),
                                         const int *ts = nullptr) {
-    const int tile = blockDim.x * kLbItems;
-    for (int64_t t0 = (int64_t)t.block() * tile; t0 < total; t0 += (int64_t)t.blocks() * tile) {
-        const int j0 = (int)t0;
-        const int j1 = (int)(t0 + tile < total ? t0 + tile : total);
-        const LbTile T = lb_tile<Team>(off, nseg, total, j0, j1, ts);
-        int j = j0 + threadIdx.x * kLbItems;
-        if (j >= j1) continue;
-        const int je = j + kLbItems < j1 ? j + kLbItems : j1;
-        int s = lb_tile_seg<Team>(off, T, j);
+    lb_schedule(off, nseg, total, ts, t, [&](int j, int n, int s, auto end) {
+        const int je = j + n;
         while (j < je) {
-            const int send = lb_tile_end<Team>(off, T, s);
+            const int send = end(s);
             const int b = send < je ? send : je;
             if (b > j) fn(s, j, b);
             j = b > j ? b : j;
             ++s;
         }
-    }
+    });
 }
 
 inline int lb_grid(int64_t total, int cap = 152 * 8) {
