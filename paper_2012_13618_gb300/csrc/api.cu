@@ -8,8 +8,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -69,6 +71,32 @@ void dev_free(void *p, size_t bytes, cudaStream_t s) {
 
 void zero_fill(void *p, size_t bytes, cudaStream_t s) { BP_CUDA(cudaMemsetAsync(p, 0, bytes, s)); }
 
+// Pinned 4 KB host blocks for the small device-to-host reads of a handle, kept in a process-wide
+// pool: pinning and unpinning memory costs far more than a short-lived handle's whole run.
+namespace {
+std::mutex g_pinned_mu;
+std::vector<uint32_t *> g_pinned_free;
+}  // namespace
+
+uint32_t *pinned_take() {
+    {
+        std::lock_guard<std::mutex> lk(g_pinned_mu);
+        if (!g_pinned_free.empty()) {
+            uint32_t *p = g_pinned_free.back();
+            g_pinned_free.pop_back();
+            return p;
+        }
+    }
+    void *p = nullptr;
+    BP_CUDA(cudaMallocHost(&p, 4096));
+    return static_cast<uint32_t *>(p);
+}
+
+void pinned_release(uint32_t *p) {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    g_pinned_free.push_back(p);
+}
+
 uint32_t *dev_status(bipart_graph *g) { return g->w.status.as<uint32_t>(); }
 
 void sync(bipart_graph *g) {
@@ -116,6 +144,22 @@ constexpr int kSlotLevels = 2048;
 int32_t *level_sizes(bipart_graph *g, int idx) {
     int32_t *small = g->w.small.as<int32_t>();
     return idx < kSlotLevels ? small + kSlotBase + 3 * idx : small + 8;
+}
+
+void read_i32s(bipart_graph *g, int n, const int32_t *const *d, int32_t *v) {
+    Exec &ex = g->ex;
+    if (ex.capturing) {
+        for (int i = 0; i < n; ++i) v[i] = read_i32(g, d[i]);
+        return;
+    }
+    for (int i = 0; i < n; ++i)
+        BP_CUDA(cudaMemcpyAsync(g->w.host_small + i, d[i], sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+    sync(g);
+    check_status(g);
+    for (int i = 0; i < n; ++i) {
+        v[i] = (int32_t)g->w.host_small[i];
+        if (ex.recording) ex.sizes.push_back(v[i]);
+    }
 }
 
 int32_t read_i32(bipart_graph *g, const int32_t *d) {
@@ -747,17 +791,50 @@ Params make_params(int32_t k, double eps, int32_t policy, int32_t levels, int32_
     return p;
 }
 
+namespace {
+
+// Runs body(lo, hi) over [0, n) in up to 16 host threads (a few large chunks) and returns the
+// smallest index at which a chunk reported a failure (body returns the failing index or -1).
+template <class Body>
+int64_t parallel_first(int64_t n, Body body) {
+    const int64_t kChunk = 1 << 20;
+    int T = (int)std::min<int64_t>((n + kChunk - 1) / kChunk, 16);
+    const int hw = (int)std::thread::hardware_concurrency();
+    if (hw > 0) T = std::min(T, hw);
+    if (T <= 1) return body(0, n);
+    std::vector<int64_t> first(T, -1);
+    std::vector<std::thread> th;
+    for (int i = 0; i < T; ++i)
+        th.emplace_back([&, i]() { first[i] = body(n * i / T, n * (i + 1) / T); });
+    for (auto &t : th) t.join();
+    for (int64_t f : first)
+        if (f >= 0) return f;  // chunks are in index order: the first hit is the smallest index
+    return -1;
+}
+
+}  // namespace
+
+// Host-side validation of a CSR given in host memory; the long loops run in parallel and report
+// the same first offending index as a sequential pass would.
 void validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t *pins,
                        const int32_t *nw, const int32_t *hw) {
     if (N < 0 || E < 0) throw Fail{BIPART_ERR_INVALID_ARG, "negative size"};
     if (E > 0 && !hoff) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_offsets is NULL"};
     if (hoff && hoff[0] != 0) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets[0] != 0"};
-    for (int32_t e = 0; e < E; ++e)
-        if (hoff[e + 1] < hoff[e]) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets not non-decreasing at " + std::to_string(e)};
+    int64_t bad = parallel_first(E, [&](int64_t lo, int64_t hi) -> int64_t {
+        for (int64_t e = lo; e < hi; ++e)
+            if (hoff[e + 1] < hoff[e]) return e;
+        return -1;
+    });
+    if (bad >= 0) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets not non-decreasing at " + std::to_string(bad)};
     const int32_t P = E > 0 ? hoff[E] : 0;
     if (P > 0 && !pins) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_pins is NULL"};
-    for (int32_t i = 0; i < P; ++i)
-        if (pins[i] < 0 || pins[i] >= N) throw Fail{BIPART_ERR_INVALID_CSR, "pin " + std::to_string(i) + " out of range"};
+    bad = parallel_first(P, [&](int64_t lo, int64_t hi) -> int64_t {
+        for (int64_t i = lo; i < hi; ++i)
+            if (pins[i] < 0 || pins[i] >= N) return i;
+        return -1;
+    });
+    if (bad >= 0) throw Fail{BIPART_ERR_INVALID_CSR, "pin " + std::to_string(bad) + " out of range"};
     int64_t sn = 0, se = 0;
     if (nw) {
         for (int32_t v = 0; v < N; ++v) {
@@ -782,7 +859,7 @@ void validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t 
 bipart_graph::~bipart_graph() {
     plan.reset();
     if (cap_stream) cudaStreamDestroy(cap_stream);
-    if (w.host_small) cudaFreeHost(w.host_small);
+    if (w.host_small) bp::pinned_release(w.host_small);
     w.host_small = nullptr;
 }
 
@@ -796,7 +873,7 @@ bipart_graph *new_graph(cudaStream_t s) {
     g->w.status.ensure(64, s);
     g->w.small.ensure(kSmallBytes, s);
     BP_CUDA(cudaMemsetAsync(g->w.status.p, 0, 64, s));
-    BP_CUDA(cudaMallocHost(&g->w.host_small, 4096));
+    g->w.host_small = pinned_take();
     refine_init();
     coarsen_init();
     return g.release();

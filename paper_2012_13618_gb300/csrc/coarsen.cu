@@ -424,9 +424,11 @@ void seg_unique(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const in
 // Sorted-unique of every hyperedge's (mapped) pins into the coarse CSR of `c`.
 // Sets c.E and c.P.  `map` null means identity (level-0 normalisation).
 // sizes: two device ints receiving {E', P'}; ts_in: tile starts of the input CSR (or null).
+// n_slot (or null): the device int holding c.N, read in the same round trip as E' and P'
+// (otherwise c.N must be set by the caller).
 void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int *pins,
               const int *hw, const int *map, Level &c, int *deg, bool counters_zero, int32_t *sizes,
-              const int *ts_in, bool merge) {
+              const int *ts_in, bool merge, const int32_t *n_slot) {
     cudaStream_t s = g->stream;
     Work &w = g->w;
     int *scratch = (int *)w.p_a.ensure(sizeof(int) * (size_t)std::max(P, 1), s);
@@ -471,6 +473,12 @@ void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int 
             ProfScope ps("contract_offsets", 16.0 * E, s);
             scan(E, CompactIn{cnt, rep}, out, w.scan.ensure_zero(scan_state_bytes(E), s), dev_status(g), s);
         }
+        const int32_t *ptr[3] = {sizes, sizes + 1, n_slot};
+        int32_t v[3];
+        read_i32s(g, n_slot ? 3 : 2, ptr, v);
+        c.E = v[0];
+        c.P = v[1];
+        if (n_slot) c.N = v[2];
         {
             // scratch, coarse pins, degree atomics, per-hyperedge offsets
             ProfScope ps("contract_copy", 12.0 * P + 12.0 * E, s);
@@ -484,9 +492,10 @@ void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int 
         }
     } else {
         BP_CUDA(cudaMemsetAsync(c.hoff(), 0, sizeof(int), s));
+        c.E = 0;
+        c.P = 0;
+        if (n_slot) c.N = read_i32(g, n_slot);
     }
-    c.E = E > 0 ? read_i32(g, sizes) : 0;
-    c.P = E > 0 ? read_i32(g, sizes + 1) : 0;
 }
 
 }  // namespace
@@ -553,7 +562,7 @@ void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t
     }
     L.N = N;
     contract(g, E, P, d_hoff, d_pins, d_hw, nullptr, L, degree_counters(g, N), false,
-             g->w.small.as<int32_t>() + 2, nullptr, false);
+             g->w.small.as<int32_t>() + 2, nullptr, false, nullptr);
     L.b_nw.ensure(sizeof(int) * (size_t)std::max(N, 1), s);
     if (d_nw) {
         BP_CUDA(cudaMemcpyAsync(L.nw(), d_nw, sizeof(int) * (size_t)N, cudaMemcpyDeviceToDevice, s));
@@ -622,14 +631,16 @@ bool coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *siz
                  w.scan.ensure_zero(scan_state_bytes(N), s), dev_status(g), s);
         }
     }
-    const int Nc = N > 0 ? read_i32(g, sizes) : 0;
-    c.N = Nc;
+    // N' is read with the contraction's sizes (one host round trip for the three)
+    c.N = 0;
     if (N > 0) {
         ProfScope ps("cmap", 24.0 * N, s);
         k_cmap<<<grid_for(N), kBlock, 0, s>>>(N, grp, gcid, f.nw(), f.cmap(), c.nw());
         BP_LAUNCH();
     }
-    contract(g, E, f.P, f.hoff(), f.pins(), f.hw(), f.cmap(), c, deg, N > 0, sizes + 1, f.tsh(), merge);
+    contract(g, E, f.P, f.hoff(), f.pins(), f.hw(), f.cmap(), c, deg, N > 0, sizes + 1, f.tsh(), merge,
+             N > 0 ? sizes : nullptr);
+    const int Nc = c.N;
     // when c will be coarsened in turn (the stop rule of reading C11 lets it), its key and reset
     // pass rides along with its incidence fill
     const bool prep = more_levels && c.E > 0 && c.N != f.N;

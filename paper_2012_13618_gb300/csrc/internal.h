@@ -18,6 +18,8 @@ namespace bp {
 void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, size_t bytes, cudaStream_t s);
 void zero_fill(void *p, size_t bytes, cudaStream_t s);
+uint32_t *pinned_take();            // a pinned 4 KB host block (pooled)
+void pinned_release(uint32_t *p);
 // Bumped whenever a buffer is (re)allocated: a captured graph is only valid while the buffers
 // it points to are the ones it was captured with.
 void note_realloc();
@@ -289,6 +291,8 @@ void sync(bipart_graph *g);
 // per-level size slots are checked together by flush_checks() at the end of the capture, others
 // at once.
 int32_t read_i32(bipart_graph *g, const int32_t *d);
+// Several such scalars with one host round trip (recorded and checked in order).
+void read_i32s(bipart_graph *g, int n, const int32_t *const *d, int32_t *v);
 // Reads a device flag in eager mode.
 unsigned read_flag(bipart_graph *g, const unsigned *d);
 
