@@ -37,7 +37,7 @@ inline int grid_for(int64_t n, int per_block = kBlock, int cap = 152 * 16) {
 
 // Selection passes over up to this many nodes run as one block of kSelOneThreads threads (the
 // histogram, the threshold and the application in one launch).
-constexpr int kSelOneBlock = 8192;
+constexpr int kSelOneBlock = 16384;
 constexpr int kSelOneThreads = 1024;
 
 inline int sel_grid(int N) { return N <= kSelOneBlock ? 1 : std::min(grid_for(N), 608); }
@@ -47,7 +47,7 @@ inline int sel_threads(int N) { return N <= kSelOneBlock ? kSelOneThreads : kBlo
 constexpr int kReduceBlocks = 608;
 
 // Levels up to this many pins compute gains without the separate contribution pass.
-constexpr int kDirectGainPins = 2'000'000;
+constexpr int kDirectGainPins = 1'000'000;
 
 }  // namespace
 

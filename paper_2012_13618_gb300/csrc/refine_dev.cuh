@@ -179,14 +179,26 @@ __device__ inline int hist_find(const unsigned *hist, unsigned need, unsigned *a
 }
 
 // One block: decides K per group from the fast histogram and fixes the threshold, or starts the
-// exact path (st->slow).
+// exact path (st->slow).  Both groups are searched in one suffix scan over the buckets: the two
+// 32-bit counts travel packed in one 64-bit value (a count never exceeds N < 2^31, so the fields
+// never carry), the scan's total gives both group sizes and so K, and each thread then checks
+// its buckets against both needs.
 __device__ inline void d_sel_find(int kind, long long s, RState *st, const unsigned (*hist)[kHistBins]) {
-    unsigned cnt[2];
-    for (int i = 0; i < 2; ++i) {
-        unsigned above, total;
-        hist_find(hist[i], 0, &above, &total);
-        cnt[i] = total;
+    __shared__ unsigned long long red[33];
+    __shared__ int s_b[2];
+    __shared__ unsigned s_above[2];
+    const int per = kHistBins / blockDim.x;  // 256, 512 or 1024 threads
+    unsigned l0[8], l1[8];
+    unsigned long long tsum = 0;
+    for (int q = 0; q < per; ++q) {
+        const int b = kHistBins - 1 - (threadIdx.x * per + q);
+        l0[q] = hist[0][b];
+        l1[q] = hist[1][b];
+        tsum += (unsigned long long)l1[q] << 32 | l0[q];
     }
+    unsigned long long tot;
+    unsigned long long run = block_exclusive_scan<unsigned long long>(tsum, red, &tot);
+    const unsigned cnt[2] = {(unsigned)tot, (unsigned)(tot >> 32)};
     unsigned K[2] = {0, 0};
     if (kind == SEL_REFINE) {
         K[0] = K[1] = min(cnt[0], cnt[1]);
@@ -194,12 +206,33 @@ __device__ inline void d_sel_find(int kind, long long s, RState *st, const unsig
         int grp = kind == SEL_INITIAL ? 1 : st->heavy;
         if (grp >= 0) K[grp] = (unsigned)min((long long)cnt[grp], s);
     }
+    // bucket search only where 0 < K < cnt (else every candidate or none is taken)
+    const unsigned need0 = K[0] > 0 && K[0] < cnt[0] ? K[0] : 0u;
+    const unsigned need1 = K[1] > 0 && K[1] < cnt[1] ? K[1] : 0u;
+    if (threadIdx.x < 2) {
+        s_b[threadIdx.x] = -1;
+        s_above[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    for (int q = 0; q < per; ++q) {
+        const int b = kHistBins - 1 - (threadIdx.x * per + q);
+        const unsigned r0 = (unsigned)run, r1 = (unsigned)(run >> 32);
+        if (need0 > 0 && r0 < need0 && r0 + l0[q] >= need0) {
+            s_b[0] = b;
+            s_above[0] = r0;
+        }
+        if (need1 > 0 && r1 < need1 && r1 + l1[q] >= need1) {
+            s_b[1] = b;
+            s_above[1] = r1;
+        }
+        run += (unsigned long long)l1[q] << 32 | l0[q];
+    }
+    __syncthreads();
     unsigned slow = 0;
     for (int i = 0; i < 2; ++i) {
         SelGroup &G = st->g[i];
-        unsigned above = 0, total = 0;
-        int b = -1;
-        if (K[i] > 0 && K[i] < cnt[i]) b = hist_find(hist[i], K[i], &above, &total);
+        const int b = s_b[i];
+        const unsigned above = s_above[i];
         if (threadIdx.x == 0) {
             G.cnt = cnt[i];
             G.K = K[i];
