@@ -120,6 +120,31 @@ __device__ void d_node_gain_direct(Team t, int N, int P, const int *noff, const 
 }
 
 // ------------------------------------------------------------------------ selection
+// Grid-stride loop over the team's nodes that loads gain, side and weight of four nodes (one per
+// stride) before visiting any of them: the visits update shared-memory counters, and without the
+// batching every node's loads would wait for the previous node's update.
+template <class Team, class Fn>
+__device__ __forceinline__ void sel_nodes(Team t, int N, const int *gain, const uint8_t *side,
+                                          const int *nw, Fn fn) {
+    const int64_t stride = t.size();
+    for (int64_t v0 = t.rank(); v0 < N; v0 += 4 * stride) {
+        int g[4], w[4];
+        uint8_t sd[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t v = v0 + u * stride;
+            if (v < N) {
+                g[u] = gain[v];
+                sd[u] = side[v];
+                w[u] = nw[v];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (v0 + u * stride < N) fn(g[u], sd[u], w[u]);
+    }
+}
+
 // Fast pass: histogram of clamped gains per group (h: 2 * kHistBins shared counters).
 // Without `flush` the histogram stays in h (a one-block pass that searches it itself).
 template <class Team>
@@ -127,14 +152,13 @@ __device__ void d_sel_hist(Team t, int N, int kind, const int *gain, const uint8
                            const int *nw, RState *st, unsigned (*h)[kHistBins], bool flush = true) {
     for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
-    for (int v = t.rank(); v < N; v += t.size()) {
-        int g = gain[v];
-        int grp = sel_group(kind, st, g, side[v], nw[v]);
-        if (grp < 0) continue;
+    sel_nodes(t, N, gain, side, nw, [&](int g, uint8_t sd, int w) {
+        const int grp = sel_group(kind, st, g, sd, w);
+        if (grp < 0) return;
         int b = g - kClampLo;
         b = b < 0 ? 0 : (b > kHistBins - 1 ? kHistBins - 1 : b);
         atomicAdd(&h[grp][b], 1u);
-    }
+    });
     __syncthreads();
     if (!flush) return;
     for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) {
@@ -281,14 +305,13 @@ __device__ void d_sel_hist_exact(Team t, int N, int kind, const int *gain, const
     for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
     if (!s_on[0] && !s_on[1]) return;
-    for (int v = t.rank(); v < N; v += t.size()) {
-        int g = gain[v];
-        int grp = sel_group(kind, st, g, side[v], nw[v]);
-        if (grp < 0 || !s_on[grp]) continue;
-        unsigned k = gkey(g);
-        if (k < s_base[grp] || (unsigned long long)k >= s_top[grp]) continue;
+    sel_nodes(t, N, gain, side, nw, [&](int g, uint8_t sd, int w) {
+        const int grp = sel_group(kind, st, g, sd, w);
+        if (grp < 0 || !s_on[grp]) return;
+        const unsigned k = gkey(g);
+        if (k < s_base[grp] || (unsigned long long)k >= s_top[grp]) return;
         atomicAdd(&h[grp][(k - s_base[grp]) >> s_shift[grp]], 1u);
-    }
+    });
     __syncthreads();
     if (!flush) return;
     for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) {
