@@ -454,7 +454,7 @@ void extract_subgraph(bipart_graph *g, const int *d_part, int j) {
     int *small = w.small.as<int>();
     BP_CUDA(cudaMemsetAsync(small, 0, 8 * sizeof(int), s));
     scan(L.N, SubNodeIn{d_part, j}, SubNodeOut{L.N, L.nw(), loc, l2g, S.nw(), small + 4},
-         w.scan.ensure_zero(scan_state_bytes(L.N), s), dev_status(g), s);
+         w.scan, dev_status(g), s);
     int *cnt = (int *)w.e_a.ensure(sizeof(int) * (size_t)std::max(L.E, 1), s);
     int *emap = (int *)w.e_b.ensure(sizeof(int) * (size_t)std::max(L.E, 1), s);
     S.unit_hw = L.unit_hw;
@@ -468,7 +468,7 @@ void extract_subgraph(bipart_graph *g, const int *d_part, int j) {
         k_sub_count<<<gw, kBlock, 0, s>>>(L.E, L.hoff(), L.pins(), loc, cnt);
         BP_LAUNCH();
         scan(L.E, SubEdgeIn{cnt}, SubEdgeOut{L.E, L.hw(), S.hoff(), S.unit_hw ? nullptr : S.b_hw.as<int>(), emap, small + 2, S.tsh()},
-             w.scan.ensure_zero(scan_state_bytes(L.E), s), dev_status(g), s);
+             w.scan, dev_status(g), s);
         k_sub_copy<<<gw, kBlock, 0, s>>>(L.E, L.hoff(), L.pins(), loc, emap, S.hoff(), S.pins(), deg);
         BP_LAUNCH();
     } else {
@@ -492,7 +492,7 @@ void bisect_body(bipart_graph *g, Level &L0, const Params &p, int64_t W, uint8_t
     // Counters, histograms and scan tile states are zero at rest (each phase clears what it
     // used); they are cleared once here in case an earlier run stopped midway.
     BP_CUDA(cudaMemsetAsync(g->w.small.p, 0, small_state_bytes(), g->stream));
-    if (g->w.scan.p) BP_CUDA(cudaMemsetAsync(g->w.scan.p, 0, g->w.scan.cap, g->stream));
+    g->w.scan.reset(g->stream);
     std::vector<Level *> levels{&L0};
     bool init_done = false;  // the next level's key and reset pass already ran
     while ((int)levels.size() - 1 < p.levels) {

@@ -471,7 +471,7 @@ void contract(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const int 
         CompactOut out{E, hw, c.hoff(), unit ? nullptr : c.b_hw.as<int>(), emap, sizes, c.tsh(), wsum};
         {
             ProfScope ps("contract_offsets", 16.0 * E, s);
-            scan(E, CompactIn{cnt, rep}, out, w.scan.ensure_zero(scan_state_bytes(E), s), dev_status(g), s);
+            scan(E, CompactIn{cnt, rep}, out, w.scan, dev_status(g), s);
         }
         const int32_t *ptr[3] = {sizes, sizes + 1, n_slot};
         int32_t v[3];
@@ -526,7 +526,7 @@ void build_incidence_and_init(bipart_graph *g, Level &L, const LevelInit &next) 
     L.b_tsn.ensure(sizeof(int) * ((size_t)L.P / kTsGran + 2), s);
     {
         ProfScope ps("incidence_offsets", 12.0 * L.N, s);
-        scan(L.N, DegIn{deg}, DegOut{L.N, L.noff(), cursor, L.tsn()}, w.scan.ensure_zero(scan_state_bytes(L.N), s),
+        scan(L.N, DegIn{deg}, DegOut{L.N, L.noff(), cursor, L.tsn()}, w.scan,
              dev_status(g), s);
     }
     if (L.P > 0) {
@@ -628,7 +628,7 @@ bool coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *siz
         {
             ProfScope ps("renumber", 12.0 * N, s);
             scan(N, RenumIn{grp, rep}, RenumOut{N, grp, f.cmap(), gcid, sizes},
-                 w.scan.ensure_zero(scan_state_bytes(N), s), dev_status(g), s);
+                 w.scan, dev_status(g), s);
         }
     }
     // N' is read with the contraction's sizes (one host round trip for the three)

@@ -62,6 +62,35 @@ struct Buf {
     T *as() const { return reinterpret_cast<T *>(p); }
 };
 
+// Tile states of the decoupled look-back scans issued on one stream, in two halves used in turn:
+// a multi-tile scan runs on the clean half and clears the tile states that the previous
+// multi-tile scan left in the other half, so no scan needs its last block to clean up after it.
+// Each half's tile counter returns to zero by itself (a wrapping increment per tile).
+struct ScanState {
+    Buf buf;
+    size_t half_words = 0;        // 64-bit words per half: [tile counter, unused, tile states...]
+    int clean = 0;                // the half the next multi-tile scan runs on
+    int64_t dirty[2] = {0, 0};    // tile states left set in each half
+    // Both halves, for a scan of `tiles` tiles (a new, zeroed allocation when too small).
+    unsigned long long *halves(int64_t tiles, cudaStream_t stream) {
+        const size_t need = 2 + (size_t)tiles;
+        if (need > half_words) {
+            buf.ensure(16 * need, stream);  // more than the capacity: always a new allocation
+            zero_fill(buf.p, buf.cap, stream);
+            half_words = buf.cap / 16;
+            clean = 0;
+            dirty[0] = dirty[1] = 0;
+        }
+        return buf.as<unsigned long long>();
+    }
+    // Zeroes both halves (the start of a bisection, in case an earlier run stopped midway).
+    void reset(cudaStream_t stream) {
+        if (buf.p) BP_CUDA(cudaMemsetAsync(buf.p, 0, buf.cap, stream));
+        clean = 0;
+        dirty[0] = dirty[1] = 0;
+    }
+};
+
 // One level of the multilevel hierarchy, resident in HBM.
 //   hoff[E+1], pins[P]   hyperedge -> pins CSR, pins ascending within a hyperedge
 //   hw[E]                hyperedge weights (nullptr: all 1)
@@ -99,7 +128,7 @@ struct Level {
 
 // Scratch shared by all levels of one bisection, sized by the largest level seen.
 struct Work {
-    Buf scan;        // decoupled look-back tile states + tile counter
+    ScanState scan;  // decoupled look-back tile states
     Buf status;      // device error word (DevErr bits)
     Buf small;       // small device scalars (counters, totals, selection state)
     Buf e_a, e_b, e_c, e_d;  // per-hyperedge int32 scratch

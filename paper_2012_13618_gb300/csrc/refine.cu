@@ -312,7 +312,7 @@ void select_apply(bipart_graph *g, Level &L, int kind, long long sq, const int *
     }
     ProfScope ps("select_apply", 10.0 * L.N, s);
     scan(L.N, TieIn{kind, gain, side, L.nw(), st}, ApplyOut{kind, gain, side, L.nw(), st, list},
-         g->w.scan.ensure_zero(scan_state_bytes(L.N), s), dev_status(g), s);
+         g->w.scan, dev_status(g), s);
 }
 
 void side_weights(bipart_graph *g, Level &L, const uint8_t *side, const CondArgs &cond) {

@@ -10,6 +10,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "internal.h"
 
 namespace bp {
 
@@ -21,26 +22,28 @@ constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagPre = 2ull << 62;
 constexpr int kLookR = 4;  // predecessors per lane in one look-back round
 
-// `state` points at [tile counter, finished-block counter, tile status words ...], all zero at
-// launch.  Every block counts itself finished after its last read of a tile state; the block
-// that finishes last clears the state again, so consecutive scans on one stream need no memset
-// (a scan that gave up on a wait still finishes, so the state is cleared then too).
+// `state` points at [tile counter, unused, tile status words ...], all zero at launch; the
+// counter wraps back to zero with the last ticket.  `other` is the other half of the stream's
+// scan state: its first `other_dirty` tile states, left by the previous multi-tile scan, are
+// cleared here for the next one.  A single-tile scan touches neither.
 template <class In, class Out>
 __global__ void __launch_bounds__(kScanBlock)
-k_scan(int64_t n, In in, Out out, unsigned long long *state, uint32_t *status) {
+k_scan(int64_t n, In in, Out out, unsigned long long *state, unsigned long long *other,
+       int64_t other_dirty, uint32_t *status) {
     __shared__ uint64_t s_val[kScanTile];
     __shared__ uint64_t s_pre[kScanTile];
     __shared__ uint64_t red[33];
     __shared__ uint32_t s_tile;
     __shared__ uint64_t s_prefix;
-    __shared__ int s_last;
-    unsigned long long *counter = state;
-    unsigned long long *finished = state + 1;
     unsigned long long *tiles = state + 2;
 
     // a single-tile scan has no predecessor: it neither takes a ticket nor touches the state
     const bool solo = gridDim.x == 1;
-    if (threadIdx.x == 0) s_tile = solo ? 0u : (uint32_t)atomicAdd(counter, 1ull);
+    if (threadIdx.x == 0)
+        s_tile = solo ? 0u : atomicInc(reinterpret_cast<unsigned *>(state), gridDim.x - 1u);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < other_dirty;
+         i += (int64_t)gridDim.x * blockDim.x)
+        other[2 + i] = 0ull;
     __syncthreads();
     const int64_t tile = s_tile;
     const int64_t base = tile * kScanTile;
@@ -62,10 +65,7 @@ k_scan(int64_t n, In in, Out out, unsigned long long *state, uint32_t *status) {
     uint64_t excl = block_exclusive_scan<uint64_t>(sum, red, &total);
 
     if (solo) {
-        if (threadIdx.x == 0) {
-            s_prefix = 0;
-            s_last = 0;
-        }
+        if (threadIdx.x == 0) s_prefix = 0;
     } else if (threadIdx.x < 32) {
         // warp 0 looks back over its predecessors 32 * kLookR at a time: it adds aggregates up to
         // the nearest tile that already holds its inclusive prefix
@@ -118,21 +118,9 @@ k_scan(int64_t n, In in, Out out, unsigned long long *state, uint32_t *status) {
             if (lane == 0)
                 atomicExch(&tiles[tile], (unsigned long long)(kFlagPre | ((prefix + total) & kScanValMask)));
         }
-        if (lane == 0) {
-            s_prefix = prefix;
-            __threadfence();
-            s_last = atomicAdd(finished, 1ull) == (unsigned long long)gridDim.x - 1;
-            if (s_last) __threadfence();
-        }
+        if (lane == 0) s_prefix = prefix;
     }
     __syncthreads();
-    if (s_last) {
-        for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) tiles[i] = 0ull;
-        if (threadIdx.x == 0) {
-            *counter = 0ull;
-            *finished = 0ull;
-        }
-    }
     uint64_t run = s_prefix + excl;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
@@ -175,19 +163,24 @@ __device__ void block_scan_items(int64_t n, In in, Out out) {
     }
 }
 
-inline size_t scan_state_bytes(int64_t n) {
-    return sizeof(unsigned long long) * (size_t)(2 + (n + kScanTile - 1) / kScanTile);
-}
-
-// Launches the scan on `s`; `state` must hold scan_state_bytes(n) zero bytes (as every scan
-// leaves it).
+// Launches the scan on `s` with the stream's scan state `ss` (single-tile scans use none).
 template <class In, class Out>
-void scan(int64_t n, In in, Out out, void *state, uint32_t *status, cudaStream_t s) {
+void scan(int64_t n, In in, Out out, ScanState &ss, uint32_t *status, cudaStream_t s) {
     if (n <= 0) return;
-    int64_t tiles = (n + kScanTile - 1) / kScanTile;
-    k_scan<In, Out><<<(unsigned)tiles, kScanBlock, 0, s>>>(n, in, out,
-                                                             (unsigned long long *)state, status);
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 1) {
+        k_scan<In, Out><<<1, kScanBlock, 0, s>>>(n, in, out, nullptr, nullptr, 0, status);
+        BP_LAUNCH();
+        return;
+    }
+    unsigned long long *b = ss.halves(tiles, s);
+    const int c = ss.clean, o = c ^ 1;
+    k_scan<In, Out><<<(unsigned)tiles, kScanBlock, 0, s>>>(n, in, out, b + (size_t)c * ss.half_words,
+                                                             b + (size_t)o * ss.half_words, ss.dirty[o], status);
     BP_LAUNCH();
+    ss.dirty[c] = tiles;
+    ss.dirty[o] = 0;
+    ss.clean = o;
 }
 
 }  // namespace bp
