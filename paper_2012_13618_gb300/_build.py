@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libbipart.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
-         "-Xcompiler", "-O2", "-I", INCLUDE, "-I", CSRC]
+         "-Xcompiler", "-O3", "-I", INCLUDE, "-I", CSRC]
 
 
 def nvcc() -> str:

@@ -3,15 +3,20 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <exception>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <new>
 #include <string>
 #include <thread>
+#include <unistd.h>
 #include <vector>
 
 #include "common.cuh"
@@ -113,11 +118,14 @@ uint32_t read_status_word(bipart_graph *g) {
     return g->w.host_small[1023];
 }
 
-void check_status(bipart_graph *g) {
-    if (g->ex.capturing) return;
-    uint32_t st = read_status_word(g);
+void raise_status(uint32_t st) {
     if (st & DEV_TIMEOUT) throw Fail{BIPART_ERR_TIMEOUT, "a bounded device-side wait expired"};
     if (st & DEV_OVERFLOW) throw Fail{BIPART_ERR_OOM, "a device-side size limit was exceeded"};
+}
+
+void check_status(bipart_graph *g) {
+    if (g->ex.capturing) return;
+    raise_status(read_status_word(g));
 }
 
 // ------------------------------------------------------------------------- plans and conditionals
@@ -152,10 +160,13 @@ void read_i32s(bipart_graph *g, int n, const int32_t *const *d, int32_t *v) {
         for (int i = 0; i < n; ++i) v[i] = read_i32(g, d[i]);
         return;
     }
+    // the values and the status word in one round trip
     for (int i = 0; i < n; ++i)
         BP_CUDA(cudaMemcpyAsync(g->w.host_small + i, d[i], sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+    BP_CUDA(cudaMemcpyAsync(g->w.host_small + 1023, dev_status(g), sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                            g->stream));
     sync(g);
-    check_status(g);
+    raise_status(g->w.host_small[1023]);
     for (int i = 0; i < n; ++i) {
         v[i] = (int32_t)g->w.host_small[i];
         if (ex.recording) ex.sizes.push_back(v[i]);
@@ -178,11 +189,8 @@ int32_t read_i32(bipart_graph *g, const int32_t *d) {
         }
         return v;
     }
-    BP_CUDA(cudaMemcpyAsync(g->w.host_small, d, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
-    sync(g);
-    int32_t v = (int32_t)g->w.host_small[0];
-    check_status(g);
-    if (ex.recording) ex.sizes.push_back(v);
+    int32_t v;
+    read_i32s(g, 1, &d, &v);
     return v;
 }
 
@@ -793,62 +801,158 @@ Params make_params(int32_t k, double eps, int32_t policy, int32_t levels, int32_
 
 namespace {
 
-// Runs body(lo, hi) over [0, n) in up to 16 host threads (a few large chunks) and returns the
-// smallest index at which a chunk reported a failure (body returns the failing index or -1).
+// A fixed set of host worker threads for the long validation loops, started on first use so
+// that creating a handle does not pay for thread starts.  One job runs at a time; the calling
+// thread works on it too.  A forked child (which inherits no threads) starts a pool of its own;
+// pools live until the process exits.
+class HostPool {
+public:
+    static HostPool &get() {
+        static std::mutex m;
+        static HostPool *pool = nullptr;
+        static pid_t owner = 0;
+        std::lock_guard<std::mutex> lk(m);
+        if (!pool || owner != getpid()) {
+            pool = new HostPool();
+            owner = getpid();
+        }
+        return *pool;
+    }
+    // fn(i) for every i in [0, n), shared out to the workers; returns when all have finished.
+    void run(int n, const std::function<void(int)> &fn) {
+        std::lock_guard<std::mutex> one_job(run_m_);
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            job_ = &fn;
+            n_ = n;
+            next_.store(0);
+            pending_ = (int)workers_.size();
+            ++gen_;
+        }
+        cv_.notify_all();
+        work(fn, n);
+        std::unique_lock<std::mutex> lk(m_);
+        done_.wait(lk, [&] { return pending_ == 0; });
+        job_ = nullptr;
+    }
+
+private:
+    std::mutex run_m_, m_;
+    std::condition_variable cv_, done_;
+    const std::function<void(int)> *job_ = nullptr;
+    int n_ = 0, pending_ = 0;
+    uint64_t gen_ = 0;
+    std::atomic<int> next_{0};
+    std::vector<std::thread> workers_;
+
+    HostPool() {
+        const int hw = (int)std::thread::hardware_concurrency();
+        const int T = std::max(1, std::min(hw, 16)) - 1;
+        for (int i = 0; i < T; ++i) workers_.emplace_back([this] { loop(); });
+    }
+    void work(const std::function<void(int)> &fn, int n) {
+        for (int i; (i = next_.fetch_add(1)) < n;) fn(i);
+    }
+    void loop() {
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lk(m_);
+        for (;;) {
+            cv_.wait(lk, [&] { return gen_ != seen; });
+            seen = gen_;
+            const std::function<void(int)> *job = job_;
+            const int n = n_;
+            lk.unlock();
+            work(*job, n);
+            lk.lock();
+            if (--pending_ == 0) done_.notify_one();
+        }
+    }
+};
+
+constexpr int64_t kHostChunk = 1 << 19;
+constexpr int64_t kHostBlock = 4096;
+
+// Runs body(lo, hi) over [0, n) in chunks of kHostChunk on the host pool and returns the
+// smallest index any chunk reported (body returns the first failing index of its range, or -1),
+// which is what a sequential pass would report.
 template <class Body>
 int64_t parallel_first(int64_t n, Body body) {
-    const int64_t kChunk = 1 << 20;
-    int T = (int)std::min<int64_t>((n + kChunk - 1) / kChunk, 16);
-    const int hw = (int)std::thread::hardware_concurrency();
-    if (hw > 0) T = std::min(T, hw);
-    if (T <= 1) return body(0, n);
-    std::vector<int64_t> first(T, -1);
-    std::vector<std::thread> th;
-    for (int i = 0; i < T; ++i)
-        th.emplace_back([&, i]() { first[i] = body(n * i / T, n * (i + 1) / T); });
-    for (auto &t : th) t.join();
+    const int64_t chunks = (n + kHostChunk - 1) / kHostChunk;
+    if (chunks <= 1) return n > 0 ? body(0, n) : -1;
+    std::vector<int64_t> first((size_t)chunks, -1);
+    HostPool::get().run((int)chunks, [&](int c) {
+        first[(size_t)c] = body((int64_t)c * kHostChunk, std::min(n, ((int64_t)c + 1) * kHostChunk));
+    });
     for (int64_t f : first)
-        if (f >= 0) return f;  // chunks are in index order: the first hit is the smallest index
+        if (f >= 0) return f;
     return -1;
+}
+
+// First i in [lo, hi) with bad(i), checked a block at a time with a branch-free OR (a loop the
+// compiler vectorises); the exact index is searched only inside a failing block.
+template <class Bad>
+int64_t first_bad(int64_t lo, int64_t hi, Bad bad) {
+    for (int64_t b0 = lo; b0 < hi; b0 += kHostBlock) {
+        const int64_t b1 = std::min(hi, b0 + kHostBlock);
+        unsigned any = 0;
+        for (int64_t i = b0; i < b1; ++i) any |= bad(i) ? 1u : 0u;
+        if (any)
+            for (int64_t i = b0; i < b1; ++i)
+                if (bad(i)) return i;
+    }
+    return -1;
+}
+
+// Sum of a weight array and the first weight below 1 (or -1), in parallel.
+std::pair<int64_t, int64_t> weight_check(const int32_t *w, int64_t n) {
+    const int64_t chunks = std::max<int64_t>(1, (n + kHostChunk - 1) / kHostChunk);
+    std::vector<int64_t> sum((size_t)chunks, 0), first((size_t)chunks, -1);
+    auto body = [&](int c) {
+        const int64_t lo = (int64_t)c * kHostChunk, hi = std::min(n, lo + kHostChunk);
+        int64_t acc = 0;
+        for (int64_t i = lo; i < hi; ++i) acc += w[i];
+        sum[(size_t)c] = acc;
+        first[(size_t)c] = first_bad(lo, hi, [&](int64_t i) { return (uint32_t)w[i] - 1u >= 0x7fffffffu; });
+    };
+    if (chunks == 1) body(0);
+    else HostPool::get().run((int)chunks, body);
+    int64_t total = 0, bad = -1;
+    for (size_t c = 0; c < (size_t)chunks; ++c) {
+        total += sum[c];
+        if (bad < 0 && first[c] >= 0) bad = first[c];
+    }
+    return {total, bad};
 }
 
 }  // namespace
 
-// Host-side validation of a CSR given in host memory; the long loops run in parallel and report
-// the same first offending index as a sequential pass would.
+// Host-side validation of a CSR given in host memory; the long loops run on the host pool and
+// report the same first offending index as a sequential pass would.
 void validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t *pins,
                        const int32_t *nw, const int32_t *hw) {
     if (N < 0 || E < 0) throw Fail{BIPART_ERR_INVALID_ARG, "negative size"};
     if (E > 0 && !hoff) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_offsets is NULL"};
     if (hoff && hoff[0] != 0) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets[0] != 0"};
-    int64_t bad = parallel_first(E, [&](int64_t lo, int64_t hi) -> int64_t {
-        for (int64_t e = lo; e < hi; ++e)
-            if (hoff[e + 1] < hoff[e]) return e;
-        return -1;
+    int64_t bad = parallel_first(E, [&](int64_t lo, int64_t hi) {
+        return first_bad(lo, hi, [&](int64_t e) { return hoff[e + 1] < hoff[e]; });
     });
     if (bad >= 0) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets not non-decreasing at " + std::to_string(bad)};
     const int32_t P = E > 0 ? hoff[E] : 0;
     if (P > 0 && !pins) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_pins is NULL"};
-    bad = parallel_first(P, [&](int64_t lo, int64_t hi) -> int64_t {
-        for (int64_t i = lo; i < hi; ++i)
-            if (pins[i] < 0 || pins[i] >= N) return i;
-        return -1;
+    bad = parallel_first(P, [&](int64_t lo, int64_t hi) {
+        return first_bad(lo, hi, [&](int64_t i) { return (uint32_t)pins[i] >= (uint32_t)N; });
     });
     if (bad >= 0) throw Fail{BIPART_ERR_INVALID_CSR, "pin " + std::to_string(bad) + " out of range"};
-    int64_t sn = 0, se = 0;
+    int64_t sn = N, se = 0;
     if (nw) {
-        for (int32_t v = 0; v < N; ++v) {
-            if (nw[v] < 1) throw Fail{BIPART_ERR_INVALID_CSR, "node weight < 1"};
-            sn += nw[v];
-        }
-    } else {
-        sn = N;
+        const auto r = weight_check(nw, N);
+        if (r.second >= 0) throw Fail{BIPART_ERR_INVALID_CSR, "node weight < 1"};
+        sn = r.first;
     }
     if (hw) {
-        for (int32_t e = 0; e < E; ++e) {
-            if (hw[e] < 1) throw Fail{BIPART_ERR_INVALID_CSR, "hyperedge weight < 1"};
-            se += hw[e];
-        }
+        const auto r = weight_check(hw, E);
+        if (r.second >= 0) throw Fail{BIPART_ERR_INVALID_CSR, "hyperedge weight < 1"};
+        se = r.first;
     }
     if (sn >= (int64_t(1) << 31) || se >= (int64_t(1) << 31))
         throw Fail{BIPART_ERR_INVALID_CSR, "weight sum must stay below 2^31"};
@@ -971,19 +1075,47 @@ int bipart_create(int32_t num_nodes, int32_t num_hedges, const int32_t *hedge_of
     return guard([&]() {
         if (!out) throw Fail{BIPART_ERR_INVALID_ARG, "out is NULL"};
         *out = nullptr;
-        validate_host_csr(num_nodes, num_hedges, hedge_offsets, hedge_pins, node_weights, hedge_weights);
+        const int32_t E = num_hedges, N = num_nodes;
+        // what the copies depend on is checked first; the full validation then runs on another
+        // thread while the handle is set up and the arrays are copied, and no kernel reads them
+        // before it has passed (its error, if any, is the one reported)
+        if (N < 0 || E < 0) throw Fail{BIPART_ERR_INVALID_ARG, "negative size"};
+        if (E > 0 && !hedge_offsets) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_offsets is NULL"};
+        if (hedge_offsets && hedge_offsets[0] != 0) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets[0] != 0"};
+        const int32_t P = E > 0 ? hedge_offsets[E] : 0;
+        if (P < 0) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets[E] < 0"};
+        if (P > 0 && !hedge_pins) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_pins is NULL"};
+        std::exception_ptr invalid;
+        std::thread checker([&] {
+            try {
+                validate_host_csr(N, E, hedge_offsets, hedge_pins, node_weights, hedge_weights);
+            } catch (...) {
+                invalid = std::current_exception();
+            }
+        });
+        auto checked = [&] {
+            if (checker.joinable()) checker.join();
+            if (invalid) std::rethrow_exception(invalid);
+        };
         cudaStream_t s = (cudaStream_t)stream;
-        std::unique_ptr<bipart_graph> g(new_graph(s));
-        const int32_t E = num_hedges, N = num_nodes, P = E > 0 ? hedge_offsets[E] : 0;
+        std::unique_ptr<bipart_graph> g;
         Buf b_hoff, b_pins, b_nw, b_hw;
-        int *d_hoff = (int *)b_hoff.ensure(sizeof(int) * ((size_t)E + 1), s);
-        int *d_pins = (int *)b_pins.ensure(sizeof(int) * (size_t)std::max(P, 1), s);
-        int *d_nw = node_weights ? (int *)b_nw.ensure(sizeof(int) * (size_t)std::max(N, 1), s) : nullptr;
-        int *d_hw = hedge_weights ? (int *)b_hw.ensure(sizeof(int) * (size_t)std::max(E, 1), s) : nullptr;
-        if (E > 0) BP_CUDA(cudaMemcpyAsync(d_hoff, hedge_offsets, sizeof(int) * ((size_t)E + 1), cudaMemcpyHostToDevice, s));
-        if (P > 0) BP_CUDA(cudaMemcpyAsync(d_pins, hedge_pins, sizeof(int) * (size_t)P, cudaMemcpyHostToDevice, s));
-        if (d_nw && N > 0) BP_CUDA(cudaMemcpyAsync(d_nw, node_weights, sizeof(int) * (size_t)N, cudaMemcpyHostToDevice, s));
-        if (d_hw && E > 0) BP_CUDA(cudaMemcpyAsync(d_hw, hedge_weights, sizeof(int) * (size_t)E, cudaMemcpyHostToDevice, s));
+        int *d_hoff = nullptr, *d_pins = nullptr, *d_nw = nullptr, *d_hw = nullptr;
+        try {
+            g.reset(new_graph(s));
+            d_hoff = (int *)b_hoff.ensure(sizeof(int) * ((size_t)E + 1), s);
+            d_pins = (int *)b_pins.ensure(sizeof(int) * (size_t)std::max(P, 1), s);
+            d_nw = node_weights ? (int *)b_nw.ensure(sizeof(int) * (size_t)std::max(N, 1), s) : nullptr;
+            d_hw = hedge_weights ? (int *)b_hw.ensure(sizeof(int) * (size_t)std::max(E, 1), s) : nullptr;
+            if (E > 0) BP_CUDA(cudaMemcpyAsync(d_hoff, hedge_offsets, sizeof(int) * ((size_t)E + 1), cudaMemcpyHostToDevice, s));
+            if (P > 0) BP_CUDA(cudaMemcpyAsync(d_pins, hedge_pins, sizeof(int) * (size_t)P, cudaMemcpyHostToDevice, s));
+            if (d_nw && N > 0) BP_CUDA(cudaMemcpyAsync(d_nw, node_weights, sizeof(int) * (size_t)N, cudaMemcpyHostToDevice, s));
+            if (d_hw && E > 0) BP_CUDA(cudaMemcpyAsync(d_hw, hedge_weights, sizeof(int) * (size_t)E, cudaMemcpyHostToDevice, s));
+        } catch (...) {
+            checked();  // a CSR error outranks the device error
+            throw;
+        }
+        checked();
         finish_create(g.get(), N, E, E > 0 ? d_hoff : nullptr, d_pins, d_nw, d_hw);
         *out = g.release();
         return BIPART_OK;

@@ -53,6 +53,36 @@ def test_create_rejects_malformed_csr(case):
     assert bp.load().bipart_last_error()
 
 
+@pytest.mark.parametrize("where", ["pins", "offsets", "nw", "hw"])
+def test_large_malformed_csr_reports_first_offender(where):
+    # arrays long enough for the validation to run in parallel chunks: the reported index must
+    # be the first offending one, as a sequential pass would find it
+    N, E = 3_000_000, 1_500_000
+    hoff = np.arange(0, 2 * E + 1, 2, dtype=np.int32)
+    pins = (np.arange(2 * E, dtype=np.int64) % N).astype(np.int32)
+    nw = np.ones(N, np.int32)
+    hw = np.ones(E, np.int32)
+    first = {"pins": 1_345_678, "offsets": 834_567, "nw": 2_222_222, "hw": 811_111}[where]
+    later = first + 600_000  # a later chunk fails too
+    if where == "pins":
+        pins[first] = N
+        pins[later] = -3
+    elif where == "offsets":
+        hoff[first + 1] = hoff[first] - 1
+        hoff[later + 1] = hoff[later] - 1
+    elif where == "nw":
+        nw[first] = 0
+        nw[later] = -1
+    else:
+        hw[first] = 0
+        hw[later] = 0
+    rc, out = _create_raw(N, hoff, pins, nw, hw)
+    assert rc == bp.ERR_INVALID_CSR and not out.value
+    msg = bp.load().bipart_last_error().decode()
+    if where in ("pins", "offsets"):
+        assert str(first) in msg and str(later) not in msg, msg
+
+
 def test_null_arguments():
     lib = bp.load()
     hoff = np.array([0, 2], np.int32)
