@@ -143,6 +143,8 @@ struct Work {
     int64_t n1_half = 0;
     int64_t gain_pass = 0;   // gain passes so far in this bisection
     int32_t n1_prev_E = 0;   // hyperedges counted by the previous pass (its half is dirty there)
+    const void *n1_level = nullptr;  // the level whose counts the current half holds (else null)
+    Buf moved;       // nodes moved since the counts were last brought up to date (int32)
     Buf e_best;      // per-hyperedge uint64 singleton-attach keys
     Buf m_fp, m_tkey, m_tmin, m_rep, m_wsum;  // parallel-net merging: fingerprints, table, groups
     Buf partial;     // per-block partial sums of grid-wide reductions

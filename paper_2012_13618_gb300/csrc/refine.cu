@@ -49,6 +49,11 @@ constexpr int kReduceBlocks = 608;
 // Levels up to this many pins compute gains without the separate contribution pass.
 constexpr int kDirectGainPins = 1'000'000;
 
+// Levels whose nodes have at most this many incidences on average update the side-1 counts after
+// a move (one warp per moved node) instead of recounting them; on coarser levels a moved node
+// can carry a large share of all incidences.
+constexpr int kDeltaMaxDegree = 64;
+
 }  // namespace
 
 // Grid kernels: one launch per phase (device code in refine_dev.cuh).
@@ -90,6 +95,26 @@ k_node_gain_direct(int N, int P, const int *__restrict__ noff, const int *__rest
     d_node_gain_direct(GridTeam(), N, P, noff, nadj, hoff, hw, n1, side, gain, ts);
 }
 
+// Side-1 counts brought up to date after a move instead of recounted (Algorithm 4's n1 is a
+// plain count, so the result is the same): every moved node adds +1 (now on side 1) or -1 (now on
+// side 0) to the count of each of its hyperedges, one warp per moved node over its incidences.
+// The gains are cleared for the pass that follows.
+__global__ void __launch_bounds__(kBlock)
+k_n1_delta(int N, const int *__restrict__ noff, const int *__restrict__ nadj,
+           const uint8_t *__restrict__ side, const int *__restrict__ moved, const RState *st,
+           int *__restrict__ n1, int *__restrict__ gain) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    for (int v = tid; v < N; v += nt) gain[v] = 0;
+    const int m = (int)st->moved_count;
+    const int lane = threadIdx.x & 31;
+    for (int k = tid >> 5; k < m; k += nt >> 5) {
+        const int v = moved[k];
+        const int d = side[v] ? 1 : -1;
+        const int b = noff[v + 1];
+        for (int j = noff[v] + lane; j < b; j += 32) atomicAdd(n1 + nadj[j], d);
+    }
+}
+
 // Copies the grid's accumulated histogram into shared memory and clears it in global memory
 // (the last block of a selection pass).
 __device__ __forceinline__ void take_hist(RState *st, unsigned (*h)[kHistBins]) {
@@ -108,7 +133,8 @@ __device__ __forceinline__ void take_hist(RState *st, unsigned (*h)[kHistBins]) 
 // (and in its check slot) and the application to the scan launched after it.
 __global__ void __launch_bounds__(kSelOneThreads, 1)
 k_sel(int N, int kind, long long s, const int *__restrict__ gain, uint8_t *side,
-      const int *__restrict__ nw, RState *st, unsigned *slow_slot, uint32_t *status, int *list) {
+      const int *__restrict__ nw, RState *st, unsigned *slow_slot, uint32_t *status, int *list,
+      int *moved) {
     __shared__ unsigned h[2][kHistBins];
     const bool one = gridDim.x == 1;
     d_sel_hist(GridTeam(), N, kind, gain, side, nw, st, h, !one);
@@ -117,7 +143,10 @@ k_sel(int N, int kind, long long s, const int *__restrict__ gain, uint8_t *side,
         take_hist(st, h);
     }
     d_sel_find(kind, s, st, h);
-    if (threadIdx.x == 0) st->list_count = 0;
+    if (threadIdx.x == 0) {
+        st->list_count = 0;
+        st->moved_count = 0;
+    }
     __syncthreads();
     if (one) {
         if (*(volatile unsigned *)&st->slow) {
@@ -129,7 +158,7 @@ k_sel(int N, int kind, long long s, const int *__restrict__ gain, uint8_t *side,
             __syncthreads();
         }
         // the tie ranks and the application, in the same block
-        block_scan_items(N, TieIn{kind, gain, side, nw, st}, ApplyOut{kind, gain, side, nw, st, list});
+        block_scan_items(N, TieIn{kind, gain, side, nw, st}, ApplyOut{kind, gain, side, nw, st, list, moved});
     } else if (slow_slot && threadIdx.x == 0) {
         *slow_slot = st->slow;
     }
@@ -212,9 +241,10 @@ __global__ void k_initial_cond(RState *st, CondArgs cond, uint32_t *status) {
 // Ordered rebalance move, then (same block) the rebalance condition for the next round.
 __global__ void __launch_bounds__(1024)
 k_rebal_move(const int *__restrict__ gain, uint8_t *__restrict__ side, const int *__restrict__ nw,
-             const int *__restrict__ list, RState *st, long long s, CondArgs cond, uint32_t *status) {
+             const int *__restrict__ list, RState *st, long long s, CondArgs cond, uint32_t *status,
+             int *__restrict__ moved) {
     extern __shared__ unsigned long long keys[];
-    d_rebal_move(gain, side, nw, list, st, s, keys);
+    d_rebal_move(gain, side, nw, list, st, s, keys, moved);
     __syncthreads();
     eval_cond(st, cond, status);
 }
@@ -250,10 +280,36 @@ RState *rstate(bipart_graph *g) {
     return reinterpret_cast<RState *>(g->w.small.as<char>() + 256);
 }
 
-// Algorithm 4.  The side-1 counts alternate between two buffers from pass to pass: a pass counts
-// into one while its k_hedge_n1 clears the other (dirty over the previous pass's hyperedges) and
-// the gains; k_node_gain forms every hyperedge's contribution from its degree, count and weight.
+int *count_n1(bipart_graph *g, Level &L, const uint8_t *side, int *gain);
+void node_gains(bipart_graph *g, Level &L, const uint8_t *side, int *gain, int *n1);
+
+// Algorithm 4: side-1 counts, then gains.  A level's first pass counts every hyperedge's side-1
+// pins; later passes of the same level (on levels of moderate degree) bring the counts up to
+// date from the nodes the selections moved since, which gives the same counts.
+
 void compute_gains(bipart_graph *g, Level &L, const uint8_t *side, int *gain) {
+    cudaStream_t s = g->stream;
+    Work &w = g->w;
+    int *n1;
+    if (w.n1_level == &L && (int64_t)L.P <= kDeltaMaxDegree * (int64_t)L.N) {
+        // the counts of this level are current up to the nodes moved since: update them
+        n1 = w.n1.as<int>() + (size_t)((w.gain_pass - 1) & 1) * w.n1_half;
+        ProfScope ps("n1_delta", 4.0 * L.N, s);
+        k_n1_delta<<<std::min(grid_for(L.N), kReduceBlocks), kBlock, 0, s>>>(
+            L.N, L.noff(), L.nadj(), side, w.moved.as<int>(), rstate(g), n1, gain);
+        BP_LAUNCH();
+    } else {
+        n1 = count_n1(g, L, side, gain);
+        w.n1_level = &L;
+    }
+    if (L.P == 0) return;
+    node_gains(g, L, side, gain, n1);
+}
+
+// Full count of the side-1 pins of every hyperedge.  The counts alternate between two buffers
+// from count to count: a count fills one while its k_hedge_n1 clears the other (dirty over the
+// previous count's hyperedges) and the gains.
+int *count_n1(bipart_graph *g, Level &L, const uint8_t *side, int *gain) {
     cudaStream_t s = g->stream;
     Work &w = g->w;
     const int cur = w.gain_pass & 1;
@@ -269,7 +325,15 @@ void compute_gains(bipart_graph *g, Level &L, const uint8_t *side, int *gain) {
     }
     w.gain_pass++;
     w.n1_prev_E = L.E;
-    if (L.P == 0) return;
+    return n1;
+}
+
+// gain[v] from the side-1 counts (the gains are zero on entry): on large levels k_node_gain
+// gathers each hyperedge's contribution formed by k_hedge_contrib from its degree, count and
+// weight; on smaller ones k_node_gain_direct forms it per incidence.
+void node_gains(bipart_graph *g, Level &L, const uint8_t *side, int *gain, int *n1) {
+    cudaStream_t s = g->stream;
+    Work &w = g->w;
     if (L.P > kDirectGainPins) {
         int2 *hc = w.hc.as<int2>();
         {
@@ -293,6 +357,7 @@ void compute_gains(bipart_graph *g, Level &L, const uint8_t *side, int *gain) {
 // Top-K selection per `kind` and its application (flip, or collect for the ordered rebalance).
 void select_apply(bipart_graph *g, Level &L, int kind, long long sq, const int *gain,
                   uint8_t *side, int *list) {
+    int *moved = g->w.moved.as<int>();
     cudaStream_t s = g->stream;
     RState *st = rstate(g);
     const bool one = sel_grid(L.N) == 1;  // exact passes, if any, run inside k_sel
@@ -300,7 +365,7 @@ void select_apply(bipart_graph *g, Level &L, int kind, long long sq, const int *
     {
         ProfScope ps("select_hist", 9.0 * L.N, s);
         k_sel<<<sel_grid(L.N), sel_threads(L.N), 0, s>>>(L.N, kind, sq, gain, side, L.nw(), st, slot,
-                                                         dev_status(g), list);
+                                                         dev_status(g), list, moved);
         BP_LAUNCH();
     }
     if (one) return;  // applied by k_sel
@@ -311,7 +376,7 @@ void select_apply(bipart_graph *g, Level &L, int kind, long long sq, const int *
         }
     }
     ProfScope ps("select_apply", 10.0 * L.N, s);
-    scan(L.N, TieIn{kind, gain, side, L.nw(), st}, ApplyOut{kind, gain, side, L.nw(), st, list},
+    scan(L.N, TieIn{kind, gain, side, L.nw(), st}, ApplyOut{kind, gain, side, L.nw(), st, list, moved},
          g->w.scan, dev_status(g), s);
 }
 
@@ -369,7 +434,8 @@ void rebalance(bipart_graph *g, Level &L, uint8_t *side, int *gain, const int64_
         compute_gains(g, L, side, gain);
         select_apply(g, L, SEL_REBAL, sq, gain, side, list);
         c.slot = flag_slot(g);
-        k_rebal_move<<<1, 1024, smem, s>>>(gain, side, L.nw(), list, st, sq, c, dev_status(g));
+        k_rebal_move<<<1, 1024, smem, s>>>(gain, side, L.nw(), list, st, sq, c, dev_status(g),
+                                           g->w.moved.as<int>());
         BP_LAUNCH();
     }
 }
@@ -397,6 +463,8 @@ void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, const int64_t limi
     BP_CUDA(cudaMemsetAsync(n1, 0, sizeof(int) * 2 * (size_t)emax, s));
     g->w.gain_pass = 0;
     g->w.n1_prev_E = 0;
+    g->w.n1_level = nullptr;
+    g->w.moved.ensure(sizeof(int) * (size_t)nmax, s);
 
     uint8_t *cur = sa, *other = sb;
     initial_partition(g, *levels[Lc], cur, gain, m0, m);
@@ -410,6 +478,7 @@ void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, const int64_t limi
                 BP_LAUNCH();
             }
             std::swap(cur, other);
+            g->w.n1_level = nullptr;  // a new level: its counts are recounted
         }
         for (int it = 0; it < iters; ++it) refine_iter(g, *L, cur, gain);
         if (L->N > 0) rebalance(g, *L, cur, gain, limit);

@@ -6,6 +6,8 @@
 
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "lb.cuh"
 
@@ -40,6 +42,7 @@ struct RState {
     unsigned rounds;           // loop guard
     unsigned status0;          // warn of the level-0 rebalance
     unsigned arrived;          // blocks that finished a fused grid phase (zero at rest)
+    unsigned moved_count;      // nodes moved by the current selection (reset by each selection)
     unsigned long long Wacc[2];  // side-weight partial sums of a grid launch (zero at rest)
 };
 
@@ -372,6 +375,8 @@ struct TieIn {
 
 // Applies the selection: refine flips both sides' chosen nodes; the initial partition moves its
 // chosen nodes to P0 and keeps the side weights current; the rebalance collects its chosen nodes.
+// With `moved`, every flipped node is also appended there (st->moved_count; one atomic per group
+// of converged lanes), so the side-1 counts can be updated instead of recounted.
 struct ApplyOut {
     int kind;
     const int *gain;
@@ -379,6 +384,7 @@ struct ApplyOut {
     const int *nw;
     RState *st;
     int *list;
+    int *moved = nullptr;
     __device__ void operator()(int64_t v, uint64_t pre, uint64_t) const {
         int g = gain[v];
         int grp = sel_group(kind, st, g, side[v], nw[v]);
@@ -401,6 +407,14 @@ struct ApplyOut {
             if (kind == SEL_INITIAL) {
                 atomicAdd(&st->W[0], (unsigned long long)nw[v]);
                 atomicAdd(&st->W[1], (unsigned long long)(-(long long)nw[v]));
+            }
+            if (moved) {
+                namespace cg = cooperative_groups;
+                const cg::coalesced_group grp = cg::coalesced_threads();
+                unsigned base = 0;
+                if (grp.thread_rank() == 0) base = atomicAdd(&st->moved_count, grp.size());
+                base = grp.shfl(base, 0);
+                moved[base + grp.thread_rank()] = (int)v;
             }
         }
     }
@@ -472,7 +486,8 @@ __device__ inline void d_rebal_cond(RState *st, long long limit0, long long limi
 // With nothing selected, marks the level imbalanced.  One block; keys: shared memory for the
 // next power of two >= the number selected.
 __device__ inline void d_rebal_move(const int *gain, uint8_t *side, const int *nw, const int *list,
-                                    RState *st, long long s, unsigned long long *keys) {
+                                    RState *st, long long s, unsigned long long *keys,
+                                    int *moved = nullptr) {
     __shared__ long long red[33];
     __shared__ int s_cut;
     const int n = (int)st->list_count;
@@ -524,16 +539,18 @@ __device__ inline void d_rebal_move(const int *gain, uint8_t *side, const int *n
     }
     __syncthreads();
     const int cut = s_cut;
-    long long moved = 0;
+    long long wmoved = 0;
     for (int i = threadIdx.x; i < cut; i += blockDim.x) {
         int v = (int)(keys[i] & 0xffffffffu);
         side[v] = (uint8_t)(1 - heavy);
-        moved += nw[v];
+        wmoved += nw[v];
+        if (moved) moved[i] = v;  // the selection that collected the candidates reset the count
     }
-    moved = block_sum(moved, red);
+    wmoved = block_sum(wmoved, red);
     if (threadIdx.x == 0) {
-        atomicAdd(&st->W[1 - heavy], (unsigned long long)moved);
-        atomicAdd(&st->W[heavy], (unsigned long long)(-moved));
+        atomicAdd(&st->W[1 - heavy], (unsigned long long)wmoved);
+        atomicAdd(&st->W[heavy], (unsigned long long)(-wmoved));
+        if (moved) st->moved_count = (unsigned)cut;
     }
 }
 
