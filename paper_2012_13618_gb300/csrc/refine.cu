@@ -40,8 +40,6 @@ inline int grid_for(int64_t n, int per_block = kBlock, int cap = 152 * 16) {
 constexpr int kSelOneBlock = 16384;
 constexpr int kSelOneThreads = 1024;
 
-inline int sel_grid(int N) { return N <= kSelOneBlock ? 1 : std::min(grid_for(N), 608); }
-inline int sel_threads(int N) { return N <= kSelOneBlock ? kSelOneThreads : kBlock; }
 
 // Blocks of a grid-wide sum (each block stores its partial; the last block adds them).
 constexpr int kReduceBlocks = 608;
@@ -126,41 +124,108 @@ __device__ __forceinline__ void take_hist(RState *st, unsigned (*h)[kHistBins]) 
     __syncthreads();
 }
 
-// Fast selection pass: clamped-gain histogram, then (last block) the per-group threshold.  The
-// rebalancing list is emptied for the application scan that follows.  One block (small levels)
-// keeps its histogram in shared memory, runs the exact radix passes when needed (leaving
-// st->slow clear) and applies the selection itself; a grid leaves st->slow for the exact passes
-// (and in its check slot) and the application to the scan launched after it.
-__global__ void __launch_bounds__(kSelOneThreads, 1)
+// Selection over a grid: clamped-gain histogram, then (last block) the per-group threshold; the
+// rebalancing and moved lists are emptied for the application scan that follows.  st->slow is
+// left for the exact passes (and stored in its check slot).
+__global__ void __launch_bounds__(kBlock)
 k_sel(int N, int kind, long long s, const int *__restrict__ gain, uint8_t *side,
-      const int *__restrict__ nw, RState *st, unsigned *slow_slot, uint32_t *status, int *list,
-      int *moved) {
+      const int *__restrict__ nw, RState *st, unsigned *slow_slot) {
     __shared__ unsigned h[2][kHistBins];
-    const bool one = gridDim.x == 1;
-    d_sel_hist(GridTeam(), N, kind, gain, side, nw, st, h, !one);
-    if (!one) {
-        if (!last_block(&st->arrived)) return;
-        take_hist(st, h);
+    d_sel_hist(GridTeam(), N, kind, gain, side, nw, st, h, true);
+    if (!last_block(&st->arrived)) return;
+    take_hist(st, h);
+    d_sel_find(kind, s, st, h);
+    if (threadIdx.x == 0) {
+        st->list_count = 0;
+        st->moved_count = 0;
+        if (slow_slot) *slow_slot = st->slow;
     }
+}
+
+// Selection of a level of at most kSelOneBlock nodes by one block, every phase after the first
+// on shared memory: the clamped-gain histogram (each node's gain and group cached on the way),
+// the threshold (and the exact radix passes when it falls in a clamped end bucket), the ranks of
+// the threshold's ties by ascending id from a bitmap with per-word prefix counts, and the
+// application.  Dynamic shared memory: 5 bytes per node.
+constexpr int kSelSmallWords = kSelOneBlock / 32;
+
+__global__ void __launch_bounds__(kSelOneThreads, 1)
+k_sel_small(int N, int kind, long long s, const int *__restrict__ gain, uint8_t *side,
+            const int *__restrict__ nw, RState *st, uint32_t *status, int *list, int *moved) {
+    extern __shared__ int s_gain[];                                  // N gains
+    signed char *s_grp = reinterpret_cast<signed char *>(s_gain + N);  // N groups (-1: none)
+    __shared__ unsigned h[2][kHistBins];
+    __shared__ unsigned tie[2][kSelSmallWords];
+    __shared__ unsigned pre[2][kSelSmallWords];
+    __shared__ unsigned long long red[33];
+    __shared__ unsigned s_mode[2], s_thr[2], s_take[2];
+    for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) (&h[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < 2 * kSelSmallWords; i += blockDim.x) (&tie[0][0])[i] = 0;
+    __syncthreads();
+    sel_nodes(GridTeam(), N, gain, side, nw, [&](int64_t v, int g, uint8_t sd, int w) {
+        const int grp = sel_group(kind, st, g, sd, w);
+        s_gain[v] = g;
+        s_grp[v] = (signed char)grp;
+        if (grp < 0) return;
+        int b = g - kClampLo;
+        b = b < 0 ? 0 : (b > kHistBins - 1 ? kHistBins - 1 : b);
+        atomicAdd(&h[grp][b], 1u);
+    });
+    __syncthreads();
     d_sel_find(kind, s, st, h);
     if (threadIdx.x == 0) {
         st->list_count = 0;
         st->moved_count = 0;
     }
     __syncthreads();
-    if (one) {
-        if (*(volatile unsigned *)&st->slow) {
-            for (int pass = 0; pass < 3; ++pass) {
-                d_sel_hist_exact(GridTeam(), N, kind, gain, side, nw, st, h, false);
-                d_sel_find_exact(st, status, h);
-            }
-            if (threadIdx.x == 0) st->slow = 0;
-            __syncthreads();
+    if (*(volatile unsigned *)&st->slow) {
+        for (int pass = 0; pass < 3; ++pass) {
+            d_sel_hist_exact(GridTeam(), N, kind, gain, side, nw, st, h, false);
+            d_sel_find_exact(st, status, h);
         }
-        // the tie ranks and the application, in the same block
-        block_scan_items(N, TieIn{kind, gain, side, nw, st}, ApplyOut{kind, gain, side, nw, st, list, moved});
-    } else if (slow_slot && threadIdx.x == 0) {
-        *slow_slot = st->slow;
+        if (threadIdx.x == 0) st->slow = 0;
+        __syncthreads();
+    }
+    if (threadIdx.x < 2) {
+        s_mode[threadIdx.x] = st->g[threadIdx.x].mode;
+        s_thr[threadIdx.x] = st->g[threadIdx.x].thr;
+        s_take[threadIdx.x] = st->g[threadIdx.x].take_eq;
+    }
+    __syncthreads();
+    // the threshold's ties, one bit per node
+    for (int v = threadIdx.x; v < N; v += blockDim.x) {
+        const int grp = s_grp[v];
+        if (grp >= 0 && s_mode[grp] == 2 && gkey(s_gain[v]) == s_thr[grp])
+            atomicOr(&tie[grp][v >> 5], 1u << (v & 31));
+    }
+    __syncthreads();
+    // ties before each word, both groups in one packed scan (a count stays below 2^31)
+    const int words = (N + 31) >> 5;  // <= kSelSmallWords <= blockDim.x
+    const int t = threadIdx.x;
+    unsigned long long c = 0;
+    if (t < words) c = (unsigned long long)__popc(tie[1][t]) << 32 | (unsigned)__popc(tie[0][t]);
+    unsigned long long total;
+    const unsigned long long ex = block_exclusive_scan<unsigned long long>(c, red, &total);
+    if (t < words) {
+        pre[0][t] = (unsigned)ex;
+        pre[1][t] = (unsigned)(ex >> 32);
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < N; v += blockDim.x) {
+        const int grp = s_grp[v];
+        if (grp < 0) continue;
+        const unsigned mode = s_mode[grp];
+        bool sel = mode == 1;
+        if (mode == 2) {
+            const unsigned k = gkey(s_gain[v]), thr = s_thr[grp];
+            if (k > thr) {
+                sel = true;
+            } else if (k == thr) {
+                const unsigned below = tie[grp][v >> 5] & ((1u << (v & 31)) - 1u);
+                sel = pre[grp][v >> 5] + (unsigned)__popc(below) < s_take[grp];
+            }
+        }
+        if (sel) d_apply_node(kind, v, side, nw, st, list, moved);
     }
 }
 
@@ -360,18 +425,24 @@ void select_apply(bipart_graph *g, Level &L, int kind, long long sq, const int *
     int *moved = g->w.moved.as<int>();
     cudaStream_t s = g->stream;
     RState *st = rstate(g);
-    const bool one = sel_grid(L.N) == 1;  // exact passes, if any, run inside k_sel
-    unsigned *slot = one ? nullptr : flag_slot(g);
+    if (L.N <= kSelOneBlock) {
+        // one block: the selection, its exact passes if any, and its application
+        ProfScope ps("select_hist", 9.0 * L.N, s);
+        k_sel_small<<<1, kSelOneThreads, 5 * (size_t)std::max(L.N, 1), s>>>(L.N, kind, sq, gain, side, L.nw(),
+                                                                            st, dev_status(g), list, moved);
+        BP_LAUNCH();
+        return;
+    }
+    unsigned *slot = flag_slot(g);
     {
         ProfScope ps("select_hist", 9.0 * L.N, s);
-        k_sel<<<sel_grid(L.N), sel_threads(L.N), 0, s>>>(L.N, kind, sq, gain, side, L.nw(), st, slot,
-                                                         dev_status(g), list, moved);
+        k_sel<<<std::min(grid_for(L.N), 608), kBlock, 0, s>>>(L.N, kind, sq, gain, side, L.nw(), st, slot);
         BP_LAUNCH();
     }
-    if (one) return;  // applied by k_sel
     if (device_flag(g, &st->slow)) {
         for (int pass = 0; pass < 3; ++pass) {
-            k_sel_exact<<<sel_grid(L.N), kBlock, 0, s>>>(L.N, kind, gain, side, L.nw(), st, dev_status(g));
+            k_sel_exact<<<std::min(grid_for(L.N), 608), kBlock, 0, s>>>(L.N, kind, gain, side, L.nw(), st,
+                                                                         dev_status(g));
             BP_LAUNCH();
         }
     }
@@ -501,6 +572,9 @@ void refine_init() {
     std::call_once(once, []() {
         err = cudaFuncSetAttribute(k_rebal_move, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(sizeof(unsigned long long) * kRebalMax));
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(k_sel_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       5 * kSelOneBlock);
     });
     BP_CUDA(err);
 }

@@ -124,7 +124,7 @@ __device__ void d_node_gain_direct(Team t, int N, int P, const int *noff, const 
 
 // ------------------------------------------------------------------------ selection
 // Grid-stride loop over the team's nodes that loads gain, side and weight of four nodes (one per
-// stride) before visiting any of them: the visits update shared-memory counters, and without the
+// stride) before visiting any of them (fn(v, gain, side, weight)): the visits update shared-memory counters, and without the
 // batching every node's loads would wait for the previous node's update.
 template <class Team, class Fn>
 __device__ __forceinline__ void sel_nodes(Team t, int N, const int *gain, const uint8_t *side,
@@ -144,7 +144,7 @@ __device__ __forceinline__ void sel_nodes(Team t, int N, const int *gain, const 
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (v0 + u * stride < N) fn(g[u], sd[u], w[u]);
+            if (v0 + u * stride < N) fn(v0 + u * stride, g[u], sd[u], w[u]);
     }
 }
 
@@ -155,7 +155,7 @@ __device__ void d_sel_hist(Team t, int N, int kind, const int *gain, const uint8
                            const int *nw, RState *st, unsigned (*h)[kHistBins], bool flush = true) {
     for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
-    sel_nodes(t, N, gain, side, nw, [&](int g, uint8_t sd, int w) {
+    sel_nodes(t, N, gain, side, nw, [&](int64_t, int g, uint8_t sd, int w) {
         const int grp = sel_group(kind, st, g, sd, w);
         if (grp < 0) return;
         int b = g - kClampLo;
@@ -179,17 +179,20 @@ __device__ inline int hist_find(const unsigned *hist, unsigned need, unsigned *a
     __shared__ int s_b;
     __shared__ unsigned s_above;
     const int per = kHistBins / blockDim.x;
-    unsigned loc[8], tsum = 0;
-    for (int q = 0; q < per; ++q) {
+    unsigned loc[8], tsum = 0;  // per <= 8; fixed indices keep them in registers
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
         int b = kHistBins - 1 - (threadIdx.x * per + q);
-        loc[q] = hist[b];
+        loc[q] = q < per ? hist[b] : 0u;
         tsum += loc[q];
     }
     unsigned total;
     unsigned run = block_exclusive_scan<unsigned>(tsum, red, &total);
     if (threadIdx.x == 0) { s_b = -1; s_above = 0; }
     __syncthreads();
-    for (int q = 0; q < per; ++q) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if (q >= per) break;
         int b = kHistBins - 1 - (threadIdx.x * per + q);
         if (need > 0 && run < need && run + loc[q] >= need) {
             s_b = b;
@@ -215,12 +218,13 @@ __device__ inline void d_sel_find(int kind, long long s, RState *st, const unsig
     __shared__ int s_b[2];
     __shared__ unsigned s_above[2];
     const int per = kHistBins / blockDim.x;  // 256, 512 or 1024 threads
-    unsigned l0[8], l1[8];
+    unsigned l0[8], l1[8];  // per <= 8; fixed indices keep them in registers
     unsigned long long tsum = 0;
-    for (int q = 0; q < per; ++q) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
         const int b = kHistBins - 1 - (threadIdx.x * per + q);
-        l0[q] = hist[0][b];
-        l1[q] = hist[1][b];
+        l0[q] = q < per ? hist[0][b] : 0u;
+        l1[q] = q < per ? hist[1][b] : 0u;
         tsum += (unsigned long long)l1[q] << 32 | l0[q];
     }
     unsigned long long tot;
@@ -241,7 +245,9 @@ __device__ inline void d_sel_find(int kind, long long s, RState *st, const unsig
         s_above[threadIdx.x] = 0;
     }
     __syncthreads();
-    for (int q = 0; q < per; ++q) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if (q >= per) break;
         const int b = kHistBins - 1 - (threadIdx.x * per + q);
         const unsigned r0 = (unsigned)run, r1 = (unsigned)(run >> 32);
         if (need0 > 0 && r0 < need0 && r0 + l0[q] >= need0) {
@@ -308,7 +314,7 @@ __device__ void d_sel_hist_exact(Team t, int N, int kind, const int *gain, const
     for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
     if (!s_on[0] && !s_on[1]) return;
-    sel_nodes(t, N, gain, side, nw, [&](int g, uint8_t sd, int w) {
+    sel_nodes(t, N, gain, side, nw, [&](int64_t, int g, uint8_t sd, int w) {
         const int grp = sel_group(kind, st, g, sd, w);
         if (grp < 0 || !s_on[grp]) return;
         const unsigned k = gkey(g);
@@ -373,10 +379,32 @@ struct TieIn {
     }
 };
 
-// Applies the selection: refine flips both sides' chosen nodes; the initial partition moves its
-// chosen nodes to P0 and keeps the side weights current; the rebalance collects its chosen nodes.
-// With `moved`, every flipped node is also appended there (st->moved_count; one atomic per group
-// of converged lanes), so the side-1 counts can be updated instead of recounted.
+// Applies the selection to a chosen node v: refine flips it; the initial partition moves it to P0
+// and keeps the side weights current; the rebalance collects it.  With `moved`, every flipped node
+// is also appended there (st->moved_count; one atomic per group of converged lanes), so the
+// side-1 counts can be updated instead of recounted.
+__device__ __forceinline__ void d_apply_node(int kind, int64_t v, uint8_t *side, const int *nw,
+                                             RState *st, int *list, int *moved) {
+    if (kind == SEL_REBAL) {
+        list[atomicAdd(&st->list_count, 1u)] = (int)v;
+        return;
+    }
+    side[v] ^= 1;
+    if (kind == SEL_INITIAL) {
+        atomicAdd(&st->W[0], (unsigned long long)nw[v]);
+        atomicAdd(&st->W[1], (unsigned long long)(-(long long)nw[v]));
+    }
+    if (moved) {
+        namespace cg = cooperative_groups;
+        const cg::coalesced_group grp = cg::coalesced_threads();
+        unsigned base = 0;
+        if (grp.thread_rank() == 0) base = atomicAdd(&st->moved_count, grp.size());
+        base = grp.shfl(base, 0);
+        moved[base + grp.thread_rank()] = (int)v;
+    }
+}
+
+// The application pass of a grid selection: the tie ranks come from the scan (TieIn).
 struct ApplyOut {
     int kind;
     const int *gain;
@@ -399,24 +427,7 @@ struct ApplyOut {
         } else {
             sel = false;
         }
-        if (!sel) return;
-        if (kind == SEL_REBAL) {
-            list[atomicAdd(&st->list_count, 1u)] = (int)v;
-        } else {
-            side[v] ^= 1;
-            if (kind == SEL_INITIAL) {
-                atomicAdd(&st->W[0], (unsigned long long)nw[v]);
-                atomicAdd(&st->W[1], (unsigned long long)(-(long long)nw[v]));
-            }
-            if (moved) {
-                namespace cg = cooperative_groups;
-                const cg::coalesced_group grp = cg::coalesced_threads();
-                unsigned base = 0;
-                if (grp.thread_rank() == 0) base = atomicAdd(&st->moved_count, grp.size());
-                base = grp.shfl(base, 0);
-                moved[base + grp.thread_rank()] = (int)v;
-            }
-        }
+        if (sel) d_apply_node(kind, v, side, nw, st, list, moved);
     }
 };
 
