@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kBlock)
 k_seg_mid(const int *__restrict__ hoff, const int *__restrict__ pins, const int *__restrict__ cmap,
           int *__restrict__ scratch, int *__restrict__ cnt, const int *__restrict__ list,
           const int *__restrict__ counters) {
-    d_seg_mid<MAP>(GridTeam(), hoff, pins, cmap, scratch, cnt, list, counters);
+    d_seg_mid<MAP, GridTeam, kGridMidDeg / 32>(GridTeam(), hoff, pins, cmap, scratch, cnt, list, counters);
 }
 
 template <bool MAP>
@@ -81,7 +81,7 @@ k_seg_midbig(int nbig, const int *__restrict__ hoff, const int *__restrict__ pin
     if ((int)blockIdx.x < nbig)
         d_seg_big<MAP>(SubGridTeam{0, nbig}, hoff, pins, cmap, scratch, cnt, big_list, counters, bits);
     else
-        d_seg_mid<MAP>(SubGridTeam{nbig, (int)gridDim.x - nbig}, hoff, pins, cmap, scratch, cnt, mid_list,
+        d_seg_mid<MAP, SubGridTeam, kGridMidDeg / 32>(SubGridTeam{nbig, (int)gridDim.x - nbig}, hoff, pins, cmap, scratch, cnt, mid_list,
                        counters);
 }
 

@@ -15,6 +15,7 @@ constexpr int kMidDeg = 1024;     // up to this degree: one warp each (register 
 constexpr int kGridMidDeg = 256;  // the same bound for the grid kernels, where one warp sorting
                                   // up to 1024 keys would hold up the whole launch
 constexpr int kBigWords = 8192;   // bitmap window of the block tier: 32 KB = 262,144 ids
+constexpr int kBigCache = 20;     // mapped pins a block-tier thread keeps in registers
 
 // ------------------------------------------------------------------ small fixed sorting network
 template <int n>
@@ -134,8 +135,8 @@ __device__ void d_seg_small(Team t, int E, const int *hoff, const int *pins, con
     }
 }
 
-// Mid tier: one warp per listed hyperedge (8 < d <= mid_max), register bitonic sort.
-template <bool MAP, class Team>
+// Mid tier: one warp per listed hyperedge (8 < d <= 32 * kMaxR), register bitonic sort.
+template <bool MAP, class Team, int kMaxR = kMidDeg / 32>
 __device__ void d_seg_mid(Team t, const int *hoff, const int *pins, const int *cmap, int *scratch,
                           int *cnt, const int *list, const int *counters) {
     const int n = Team::ld(counters);
@@ -148,9 +149,11 @@ __device__ void d_seg_mid(Team t, const int *hoff, const int *pins, const int *c
         if (d <= 32) m = warp_unique<1, MAP, Team>(pins, cmap, a, d, out);
         else if (d <= 64) m = warp_unique<2, MAP, Team>(pins, cmap, a, d, out);
         else if (d <= 128) m = warp_unique<4, MAP, Team>(pins, cmap, a, d, out);
-        else if (d <= 256) m = warp_unique<8, MAP, Team>(pins, cmap, a, d, out);
-        else if (d <= 512) m = warp_unique<16, MAP, Team>(pins, cmap, a, d, out);
-        else m = warp_unique<32, MAP, Team>(pins, cmap, a, d, out);
+        else if (kMaxR <= 8 || d <= 256) m = warp_unique<8, MAP, Team>(pins, cmap, a, d, out);
+        else if constexpr (kMaxR > 8) {
+            if (d <= 512) m = warp_unique<16, MAP, Team>(pins, cmap, a, d, out);
+            else m = warp_unique<32, MAP, Team>(pins, cmap, a, d, out);
+        }
         if (lane == 0) cnt[e] = m;
     }
 }
@@ -165,11 +168,27 @@ __device__ void d_seg_big(Team t, const int *hoff, const int *pins, const int *c
     __shared__ int red[33];
     __shared__ int s_minmax[2];
     const int n = Team::ld(counters + 1);
+    const int cached = kBigCache * (int)blockDim.x;
     for (int w = t.block(); w < n; w += t.blocks()) {
         const int e = Team::ld(list + w);
         const int a = Team::ld(hoff + e), d = Team::ld(hoff + e + 1) - a;
+        // the thread's first kBigCache mapped pins (i = threadIdx.x + k * blockDim.x), gathered
+        // together and kept in registers for every pass; pins beyond are gathered per pass
+        int xs[kBigCache];
+#pragma unroll
+        for (int k = 0; k < kBigCache; ++k) {
+            const int i = threadIdx.x + k * (int)blockDim.x;
+            xs[k] = i < d ? mapped<MAP, Team>(pins, cmap, a + i) : 0;
+        }
         int lo = INT_MAX, hi = INT_MIN;
-        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < kBigCache; ++k) {
+            if (threadIdx.x + k * (int)blockDim.x < d) {
+                lo = min(lo, xs[k]);
+                hi = max(hi, xs[k]);
+            }
+        }
+        for (int i = cached + threadIdx.x; i < d; i += blockDim.x) {
             int x = mapped<MAP, Team>(pins, cmap, a + i);
             lo = min(lo, x);
             hi = max(hi, x);
@@ -189,7 +208,13 @@ __device__ void d_seg_big(Team t, const int *hoff, const int *pins, const int *c
             const int words = (int)((span + 31) >> 5);
             for (int i = threadIdx.x; i < words; i += blockDim.x) bits[i] = 0;
             __syncthreads();
-            for (int i = threadIdx.x; i < d; i += blockDim.x) {
+#pragma unroll
+            for (int k = 0; k < kBigCache; ++k) {
+                const int64_t x = (int64_t)xs[k] - wlo;
+                if (threadIdx.x + k * (int)blockDim.x < d && x >= 0 && x < span)
+                    atomicOr(&bits[x >> 5], 1u << (x & 31));
+            }
+            for (int i = cached + threadIdx.x; i < d; i += blockDim.x) {
                 int64_t x = (int64_t)mapped<MAP, Team>(pins, cmap, a + i) - wlo;
                 if (x >= 0 && x < span) atomicOr(&bits[x >> 5], 1u << (x & 31));
             }
