@@ -258,22 +258,12 @@ def run_gpu(args):
 
     h = bp.create_from(g)
     # warm-up: the first call runs eagerly and records the level sizes, the second captures the
-    # CUDA graph; a profiled pass then picks the kernel with the largest device time, and the
-    # graph is recaptured with event probes around that kernel only
-    bp.profile_select(None)
-    bp.profile_enable(True)
-    for _ in range(max(args.warmup, 3)):
-        h.partition_device(out, k, eps, pol, lev, it)
-    torch.cuda.synchronize()
-    prof_all = bp.profile_read()
-    top_name = max(prof_all.items(), key=lambda kv: kv[1][1])[0] if prof_all else None
-    # the timed steps run without probes (event nodes in the graph cost time of their own): the
-    # plan is recaptured without them
+    # CUDA graph, later ones replay it; the timed steps run without event probes
     bp.profile_enable(False)
-    for _ in range(2):
+    warmups = max(args.warmup, 3)
+    for _ in range(warmups):
         h.partition_device(out, k, eps, pol, lev, it)
     torch.cuda.synchronize()
-    warmups = max(args.warmup, 3) + 2
 
     def barrier():
         if ws > 1:
@@ -303,13 +293,14 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
 
     # ---------------- profiled pass: the same steps again, with CUDA-event probes captured into
-    # the graph around every launch of the dominant kernel (on the handle's stream)
+    # the graph around every kernel launch of the bisection (on the handle's stream); the kernel
+    # with the largest device time is the roofline's, its share is its time over all probed time
     bp.profile_enable(True)
-    bp.profile_select(top_name)
+    bp.profile_select(None)
     for _ in range(2):
         h.partition_device(out, k, eps, pol, lev, it)
     torch.cuda.synchronize()
-    bp.profile_select(top_name)  # reset the totals; the plan keeps its probes
+    bp.profile_select(None)  # reset the totals; the plan keeps its probes
     pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     for i in range(args.steps):
@@ -321,6 +312,8 @@ def run_gpu(args):
     prof = bp.profile_read()
     bp.profile_enable(False)
     prof_ms = sum(a.elapsed_time(b) for a, b in pev) / len(pev)
+    probed_ms = sum(v[1] for v in prof.values())
+    top_name = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
     ms = sum(step_ms) / len(step_ms)
     ms_max = ms
     if ws > 1:
@@ -378,12 +371,14 @@ def run_gpu(args):
             traffic = ncu_traffic(name, tbytes / cnt, KERNEL_BYTES[name](n0.value, e0.value, p0.value))
         roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "traffic": traffic, "peak_source": src,
-                "launches": cnt, "share_of_step": tms / (prof_ms * args.steps),
+                "launches": cnt, "share_of_step": tms / probed_ms,
                 "profiled_ms_per_step": prof_ms,
                 "note": "achieved = algorithmic bytes per launch / mean CUDA-event duration per "
                         "launch, from a second pass of the same timed steps with event probes "
-                        "around this kernel's launches (profiled_ms_per_step; the probes are "
-                        "kept out of the pass that gives value); peak is the " + src + " HBM copy bandwidth; "
+                        "around every kernel launch (profiled_ms_per_step; the probes are kept out "
+                        "of the pass that gives value, and their own cost lengthens every probed "
+                        "launch a little); share_of_step = this kernel's probed time over all "
+                        "probed time, as a launch list counts it; peak is the " + src + " HBM copy bandwidth; "
                         "traffic = ncu DRAM read+write bytes of one level-0 launch, scaled to the "
                         "mean launch by algorithmic bytes (null unless that record matches the "
                         "kernel's current sources)"}
@@ -405,9 +400,10 @@ def run_gpu(args):
                 "graph_replay": bool(replayed),
                 "roofline": roof,
                 "cpu_baseline": cpu,
-                "warmup_profile": {k2: {"launches": v[0], "ms": v[1],
-                                        "GBps": (v[2] / (v[1] / 1000) / 1e9) if v[1] else None}
-                                   for k2, v in sorted(prof_all.items(), key=lambda kv: -kv[1][1])}}
+                "profile": {k2: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps,
+                                 "share": v[1] / probed_ms if probed_ms else None,
+                                 "GBps": (v[2] / (v[1] / 1000) / 1e9) if v[1] else None}
+                            for k2, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
         print(json.dumps(line))
     h.close()
     if ws > 1:

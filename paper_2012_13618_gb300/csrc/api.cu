@@ -203,6 +203,7 @@ void flush_checks(bipart_graph *g) {
             c.slot[k] = ex.checks[i + k].first;
             c.value[k] = ex.checks[i + k].second;
         }
+        ProfScope ps("plan_check", 0.0, g->stream);
         k_expect_all<<<1, 128, 0, g->stream>>>(g->w.small.as<int32_t>(), c, dev_status(g));
         BP_LAUNCH();
         ex.check_kernels++;
@@ -682,8 +683,11 @@ int partition_device(bipart_graph *g, const Params &p, int *d_parts) {
     top.m0 = (p.k + 1) / 2;
     int st = bisect_top(g, top, d_side, &nlev);
     if (st != BIPART_OK) status = st;
-    k_side_to_part<<<grid_for(L.N), kBlock, 0, s>>>(L.N, d_side, nullptr, 0, top.m0, d_parts);
-    BP_LAUNCH();
+    {
+        ProfScope ps("side_to_part", 5.0 * L.N, s);
+        k_side_to_part<<<grid_for(L.N), kBlock, 0, s>>>(L.N, d_side, nullptr, 0, top.m0, d_parts);
+        BP_LAUNCH();
+    }
     if (p.k == 2) {
         g->hier.nlev = nlev;
         g->hier.valid = true;

@@ -440,6 +440,7 @@ void select_apply(bipart_graph *g, Level &L, int kind, long long sq, const int *
         BP_LAUNCH();
     }
     if (device_flag(g, &st->slow)) {
+        ProfScope ps("select_exact", 3 * 9.0 * L.N, s);
         for (int pass = 0; pass < 3; ++pass) {
             k_sel_exact<<<std::min(grid_for(L.N), 608), kBlock, 0, s>>>(L.N, kind, gain, side, L.nw(), st,
                                                                          dev_status(g));
@@ -456,6 +457,7 @@ void side_weights(bipart_graph *g, Level &L, const uint8_t *side, const CondArgs
     RState *st = rstate(g);
     const int grid = std::min(grid_for(L.N), kReduceBlocks);
     auto *partial = (unsigned long long *)g->w.partial.as<void>();
+    ProfScope ps("side_weights", 5.0 * L.N, s);
     k_side_weights<<<grid, kBlock, 0, s>>>(L.N, side, L.nw(), st, cond, dev_status(g), partial);
     BP_LAUNCH();
 }
@@ -475,6 +477,7 @@ void initial_partition(bipart_graph *g, Level &L, uint8_t *side, int *gain, int 
         compute_gains(g, L, side, gain);
         select_apply(g, L, SEL_INITIAL, sq, gain, side, nullptr);
         c.slot = flag_slot(g);
+        ProfScope ps("loop_cond", 0.0, s);
         k_initial_cond<<<1, 32, 0, s>>>(st, c, dev_status(g));
         BP_LAUNCH();
     }
@@ -505,6 +508,7 @@ void rebalance(bipart_graph *g, Level &L, uint8_t *side, int *gain, const int64_
         compute_gains(g, L, side, gain);
         select_apply(g, L, SEL_REBAL, sq, gain, side, list);
         c.slot = flag_slot(g);
+        ProfScope ps("rebal_move", 0.0, s);
         k_rebal_move<<<1, 1024, smem, s>>>(gain, side, L.nw(), list, st, sq, c, dev_status(g),
                                            g->w.moved.as<int>());
         BP_LAUNCH();
@@ -556,6 +560,7 @@ void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, const int64_t limi
         else BP_CUDA(cudaMemsetAsync(&rstate(g)->warn, 0, sizeof(unsigned), g->stream));
     }
     s = g->stream;
+    ProfScope ps("loop_cond", 0.0, s);
     k_keep_status<<<1, 32, 0, s>>>(rstate(g));
     BP_LAUNCH();
     if (levels[0]->N > 0)
