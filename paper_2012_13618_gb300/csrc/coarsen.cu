@@ -171,9 +171,20 @@ k_fill_adj_priv(int E, int P, int N, const int *__restrict__ hoff, const int *__
         for (int j = (int)t0 + threadIdx.x; j < j1; j += blockDim.x) atomicAdd(s_cnt + pins[j], 1);
     }
     __syncthreads();
-    for (int v = threadIdx.x; v < N; v += blockDim.x) {
-        const int c = s_cnt[v];
-        if (c) s_cnt[v] = atomicAdd(cursor + v, c);
+    // each touched node's range reserved in the global cursor, eight nodes' atomics in flight at
+    // once (their returns are stored only after all eight are issued)
+    for (int v0 = threadIdx.x; v0 < N; v0 += 8 * blockDim.x) {
+        int c[8], r[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int v = v0 + k * (int)blockDim.x;
+            c[k] = v < N ? s_cnt[v] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r[k] = c[k] ? atomicAdd(cursor + v0 + k * (int)blockDim.x, c[k]) : 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (c[k]) s_cnt[v0 + k * (int)blockDim.x] = r[k];
     }
     __syncthreads();
     d_fill_adj_with(GridTeam(), E, P, hoff, pins, nadj, [&](int v) { return atomicAdd(s_cnt + v, 1); }, ts);

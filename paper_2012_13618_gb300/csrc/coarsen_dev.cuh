@@ -5,6 +5,8 @@
 
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "lb.cuh"
 
@@ -105,6 +107,17 @@ __device__ __forceinline__ int warp_unique(const int *pins, const int *cmap, int
     return __shfl_sync(0xffffffffu, incl, 31);
 }
 
+// Appends x to a work list whose length is *n, with one atomic per group of converged lanes (a
+// single counter shared by a whole grid would otherwise take one atomic per entry).
+__device__ __forceinline__ void append_aggregated(int *list, int *n, int x) {
+    namespace cg = cooperative_groups;
+    const cg::coalesced_group grp = cg::coalesced_threads();
+    int base = 0;
+    if (grp.thread_rank() == 0) base = atomicAdd(n, (int)grp.size());
+    base = grp.shfl(base, 0);
+    list[base + (int)grp.thread_rank()] = x;
+}
+
 // Small tier: one thread per hyperedge of degree <= 8 (the vast majority): mapped pins sorted by
 // a register network, unique values written at the hyperedge's own offset in scratch, cnt[e] =
 // their number.  Larger hyperedges are appended to the mid / big work lists (list order is
@@ -116,8 +129,8 @@ __device__ void d_seg_small(Team t, int E, const int *hoff, const int *pins, con
     for (int e = t.rank(); e < E; e += t.size()) {
         int a = Team::ld(hoff + e), d = Team::ld(hoff + e + 1) - a;
         if (d > kSmallDeg) {
-            if (d > mid_max) big_list[atomicAdd(&counters[1], 1)] = e;
-            else mid_list[atomicAdd(&counters[0], 1)] = e;
+            if (d > mid_max) append_aggregated(big_list, &counters[1], e);
+            else append_aggregated(mid_list, &counters[0], e);
             continue;
         }
         int v[kSmallDeg];
