@@ -157,7 +157,7 @@ k_seg_copy_priv(int E, int P, int N, const int *__restrict__ hoff, const int *__
 // Pass 1 counts this block's pins per node, one global atomic per touched node reserves the
 // block's range, pass 2 hands out positions inside the range by shared-memory atomics.  Both
 // passes visit the same tiles.
-__global__ void __launch_bounds__(kPrivBlock)
+__global__ void __launch_bounds__(kPrivBlock, 2)
 k_fill_adj_priv(int E, int P, int N, const int *__restrict__ hoff, const int *__restrict__ pins,
                 int *__restrict__ cursor, int *__restrict__ nadj, const int *__restrict__ ts,
                 LevelInit next) {
@@ -201,7 +201,7 @@ __global__ void k_fill(int n, int val, int *__restrict__ a) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = val;
 }
 
-__global__ void __launch_bounds__(kLbBlock)
+__global__ void __launch_bounds__(kLbBlock, 6)
 k_fill_adj(int E, int P, const int *__restrict__ hoff, const int *__restrict__ pins,
            int *__restrict__ cursor, int *__restrict__ nadj, const int *__restrict__ ts,
            LevelInit next) {
