@@ -13,6 +13,9 @@
 // memory for the threads' searches.
 #pragma once
 
+#include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
+
 #include "common.cuh"
 
 namespace bp {
@@ -166,6 +169,48 @@ __device__ __forceinline__ void lb_for_each_items(const int *off, int nseg, int 
             }
         }
         flush(s, acc);
+    });
+}
+
+// The same reduction for integer sums (visit returns acc + the item's value, flush adds): the
+// last run of every thread is first summed with the last runs of the lanes that end in the same
+// segment, so a segment spanning many threads (a long incidence list, a long hyperedge) takes one
+// atomic per warp instead of one per thread.
+template <class Visit, class Flush, class Team = GridTeam>
+__device__ __forceinline__ void lb_sum_items(const int *off, int nseg, int total, const int *items,
+                                             Visit visit, Flush flush, Team t = Team(),
+                                             const int *ts = nullptr) {
+    static_assert(kLbItems == 8, "two int4 loads per thread");
+    lb_schedule(off, nseg, total, ts, t, [&](int j, int n, int s, auto end) {
+        int it[kLbItems];
+        if (n == kLbItems && ((reinterpret_cast<uintptr_t>(items + j) & 15) == 0)) {
+            const int4 a = Team::ld(reinterpret_cast<const int4 *>(items + j));
+            const int4 b = Team::ld(reinterpret_cast<const int4 *>(items + j) + 1);
+            it[0] = a.x; it[1] = a.y; it[2] = a.z; it[3] = a.w;
+            it[4] = b.x; it[5] = b.y; it[6] = b.z; it[7] = b.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kLbItems; ++k) it[k] = k < n ? Team::ld(items + j + k) : 0;
+        }
+        int send = end(s);
+        int acc = 0;
+#pragma unroll
+        for (int k = 0; k < kLbItems; ++k) {
+            if (k < n) {
+                while (j + k >= send) {  // next non-empty segment
+                    if (acc) flush(s, acc);
+                    acc = 0;
+                    ++s;
+                    send = end(s);
+                }
+                acc = visit(s, it[k], acc);
+            }
+        }
+        namespace cg = cooperative_groups;
+        const cg::coalesced_group lanes = cg::coalesced_threads();
+        const cg::coalesced_group same = cg::labeled_partition(lanes, s);
+        const int sum = cg::reduce(same, acc, cg::plus<int>());
+        if (same.thread_rank() == 0 && sum) flush(s, sum);
     });
 }
 
