@@ -172,14 +172,14 @@ __device__ __forceinline__ void lb_for_each_items(const int *off, int nseg, int 
     });
 }
 
-// The same reduction for integer sums (visit returns acc + the item's value, flush adds): the
-// last run of every thread is first summed with the last runs of the lanes that end in the same
-// segment, so a segment spanning many threads (a long incidence list, a long hyperedge) takes one
+// The same reduction where the last run of every thread is first combined (op, a cooperative
+// groups operator such as plus or less) with the last runs of the lanes that end in the same
+// segment, so a segment spanning many threads (a coarse node's long incidence list) takes one
 // atomic per warp instead of one per thread.
-template <class Visit, class Flush, class Team = GridTeam>
-__device__ __forceinline__ void lb_sum_items(const int *off, int nseg, int total, const int *items,
-                                             Visit visit, Flush flush, Team t = Team(),
-                                             const int *ts = nullptr) {
+template <class Acc, class Op, class Visit, class Flush, class Team = GridTeam>
+__device__ __forceinline__ void lb_reduce_items(const int *off, int nseg, int total, const int *items,
+                                                Acc init, Op op, Visit visit, Flush flush,
+                                                Team t = Team(), const int *ts = nullptr) {
     static_assert(kLbItems == 8, "two int4 loads per thread");
     lb_schedule(off, nseg, total, ts, t, [&](int j, int n, int s, auto end) {
         int it[kLbItems];
@@ -193,13 +193,13 @@ __device__ __forceinline__ void lb_sum_items(const int *off, int nseg, int total
             for (int k = 0; k < kLbItems; ++k) it[k] = k < n ? Team::ld(items + j + k) : 0;
         }
         int send = end(s);
-        int acc = 0;
+        Acc acc = init;
 #pragma unroll
         for (int k = 0; k < kLbItems; ++k) {
             if (k < n) {
                 while (j + k >= send) {  // next non-empty segment
-                    if (acc) flush(s, acc);
-                    acc = 0;
+                    if (acc != init) flush(s, acc);
+                    acc = init;
                     ++s;
                     send = end(s);
                 }
@@ -209,8 +209,8 @@ __device__ __forceinline__ void lb_sum_items(const int *off, int nseg, int total
         namespace cg = cooperative_groups;
         const cg::coalesced_group lanes = cg::coalesced_threads();
         const cg::coalesced_group same = cg::labeled_partition(lanes, s);
-        const int sum = cg::reduce(same, acc, cg::plus<int>());
-        if (same.thread_rank() == 0 && sum) flush(s, sum);
+        const Acc r = cg::reduce(same, acc, op);
+        if (same.thread_rank() == 0 && r != init) flush(s, r);
     });
 }
 

@@ -89,8 +89,8 @@ __device__ void d_hedge_contrib(Team t, int E, const int *hoff, const int *hw, i
 template <class Team>
 __device__ void d_node_gain(Team t, int N, int P, const int *noff, const int *nadj, const int2 *hc,
                             const uint8_t *side, int *gain, const int *ts = nullptr) {
-    lb_sum_items(
-        noff, N, P, nadj,
+    lb_reduce_items<int>(
+        noff, N, P, nadj, 0, cooperative_groups::plus<int>(),
         [&](int v, int e, int acc) {
             int2 c = Team::ld(hc + e);
             return acc + (Team::ld(side + v) ? c.y : c.x);
@@ -107,8 +107,8 @@ template <class Team>
 __device__ void d_node_gain_direct(Team t, int N, int P, const int *noff, const int *nadj,
                                    const int *hoff, const int *hw, const int *n1,
                                    const uint8_t *side, int *gain, const int *ts = nullptr) {
-    lb_sum_items(
-        noff, N, P, nadj,
+    lb_reduce_items<int>(
+        noff, N, P, nadj, 0, cooperative_groups::plus<int>(),
         [&](int v, int e, int acc) {
             const int d = Team::ld(hoff + e + 1) - Team::ld(hoff + e);
             const int a1 = Team::ld(n1 + e);
