@@ -59,7 +59,7 @@ k_seg_mid(const int *__restrict__ hoff, const int *__restrict__ pins, const int 
 }
 
 template <bool MAP>
-__global__ void __launch_bounds__(kBigThreads)
+__global__ void __launch_bounds__(kBigThreads, 3)
 k_seg_big(const int *__restrict__ hoff, const int *__restrict__ pins, const int *__restrict__ cmap,
           int *__restrict__ scratch, int *__restrict__ cnt, const int *__restrict__ list,
           const int *__restrict__ counters) {
@@ -415,7 +415,7 @@ void seg_unique(bipart_graph *g, int32_t E, int32_t P, const int *hoff, const in
     // warps for the mid tier (at most one per 9 pins), blocks for the big tier (at most one per
     // kGridMidDeg + 1 pins); the list lengths are only known on the device
     const int mid_warps = std::max(1, std::min(152 * 16 * (kBlock / 32), P / (kSmallDeg + 1) + 1));
-    const int nbig = std::max(1, std::min(152 * 4, P / (kGridMidDeg + 1) + 1));
+    const int nbig = std::max(1, std::min(152 * 3, P / (kGridMidDeg + 1) + 1));
     if (P <= kFuseTiersPins) {
         const int nmid = ceil_div_i(mid_warps, kBigThreads / 32);
         if (map) k_seg_midbig<true><<<nbig + nmid, kBigThreads, 0, s>>>(nbig, hoff, pins, map, scratch, cnt, mid, big, small);

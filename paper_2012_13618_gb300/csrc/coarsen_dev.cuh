@@ -17,7 +17,7 @@ constexpr int kMidDeg = 1024;     // up to this degree: one warp each (register 
 constexpr int kGridMidDeg = 256;  // the same bound for the grid kernels, where one warp sorting
                                   // up to 1024 keys would hold up the whole launch
 constexpr int kBigWords = 8192;   // bitmap window of the block tier: 32 KB = 262,144 ids
-constexpr int kBigCache = 20;     // mapped pins a block-tier thread keeps in registers
+constexpr int kBigCache = 12;     // mapped pins a block-tier thread keeps in registers
 
 // ------------------------------------------------------------------ small fixed sorting network
 template <int n>
