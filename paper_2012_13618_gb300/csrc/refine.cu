@@ -52,6 +52,10 @@ constexpr int kDirectGainPins = 1'000'000;
 // can carry a large share of all incidences.
 constexpr int kDeltaMaxDegree = 64;
 
+// Levels whose nodes average more incidences than this sum each warp's gain flushes per node
+// before the atomic (many threads end on one node there); on the others it only costs time.
+constexpr int kWarpSumDegree = 64;
+
 }  // namespace
 
 // Grid kernels: one launch per phase (device code in refine_dev.cuh).
@@ -80,8 +84,8 @@ __global__ void k_hedge_contrib(int E, const int *__restrict__ hoff, const int *
 __global__ void __launch_bounds__(kLbBlock)
 k_node_gain(int N, int P, const int *__restrict__ noff, const int *__restrict__ nadj,
             const int2 *__restrict__ hc, const uint8_t *__restrict__ side, int *__restrict__ gain,
-            const int *__restrict__ ts) {
-    d_node_gain(GridTeam(), N, P, noff, nadj, hc, side, gain, ts);
+            const int *__restrict__ ts, bool warp_sum) {
+    d_node_gain(GridTeam(), N, P, noff, nadj, hc, side, gain, ts, warp_sum);
 }
 
 // ... or formed on the spot (small levels, where the contribution pass costs more as a launch
@@ -89,8 +93,9 @@ k_node_gain(int N, int P, const int *__restrict__ noff, const int *__restrict__ 
 __global__ void __launch_bounds__(kLbBlock)
 k_node_gain_direct(int N, int P, const int *__restrict__ noff, const int *__restrict__ nadj,
                    const int *__restrict__ hoff, const int *__restrict__ hw, const int *__restrict__ n1,
-                   const uint8_t *__restrict__ side, int *__restrict__ gain, const int *__restrict__ ts) {
-    d_node_gain_direct(GridTeam(), N, P, noff, nadj, hoff, hw, n1, side, gain, ts);
+                   const uint8_t *__restrict__ side, int *__restrict__ gain, const int *__restrict__ ts,
+                   bool warp_sum) {
+    d_node_gain_direct(GridTeam(), N, P, noff, nadj, hoff, hw, n1, side, gain, ts, warp_sum);
 }
 
 // Side-1 counts brought up to date after a move instead of recounted (Algorithm 4's n1 is a
@@ -399,6 +404,7 @@ int *count_n1(bipart_graph *g, Level &L, const uint8_t *side, int *gain) {
 void node_gains(bipart_graph *g, Level &L, const uint8_t *side, int *gain, int *n1) {
     cudaStream_t s = g->stream;
     Work &w = g->w;
+    const bool warp_sum = (int64_t)L.P > kWarpSumDegree * (int64_t)L.N;
     if (L.P > kDirectGainPins) {
         int2 *hc = w.hc.as<int2>();
         {
@@ -408,13 +414,14 @@ void node_gains(bipart_graph *g, Level &L, const uint8_t *side, int *gain, int *
         }
         // noff, nadj, 8-byte contribution gather per incidence, side, gain
         ProfScope ps("node_gain", 9.0 * L.N + 12.0 * L.P, s);
-        k_node_gain<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.N, L.P, L.noff(), L.nadj(), hc, side, gain, L.tsn());
+        k_node_gain<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.N, L.P, L.noff(), L.nadj(), hc, side, gain, L.tsn(),
+                                                       warp_sum);
         BP_LAUNCH();
     } else {
         // noff, nadj, gathers of two offsets and a count (and a weight) per incidence, side, gain
         ProfScope ps("node_gain", 9.0 * L.N + 16.0 * L.P + (L.hw() ? 4.0 * L.P : 0.0), s);
         k_node_gain_direct<<<lb_grid(L.P), kLbBlock, 0, s>>>(L.N, L.P, L.noff(), L.nadj(), L.hoff(), L.hw(),
-                                                             n1, side, gain, L.tsn());
+                                                             n1, side, gain, L.tsn(), warp_sum);
         BP_LAUNCH();
     }
 }

@@ -87,18 +87,22 @@ __device__ void d_hedge_contrib(Team t, int E, const int *hoff, const int *hw, i
 
 // gain[v] = sum over v's hyperedges of the contribution for v's side (gain zeroed first).
 template <class Team>
+// With `warp_sum` the last runs of a warp's lanes are summed per node before the atomic (levels
+// whose nodes have long incidence lists, where many threads would hit one node).
 __device__ void d_node_gain(Team t, int N, int P, const int *noff, const int *nadj, const int2 *hc,
-                            const uint8_t *side, int *gain, const int *ts = nullptr) {
-    lb_reduce_items<int>(
-        noff, N, P, nadj, 0, cooperative_groups::plus<int>(),
-        [&](int v, int e, int acc) {
-            int2 c = Team::ld(hc + e);
-            return acc + (Team::ld(side + v) ? c.y : c.x);
-        },
-        [&](int v, int acc) {
-            if (acc) atomicAdd(gain + v, acc);
-        },
-        t, ts);
+                            const uint8_t *side, int *gain, const int *ts = nullptr,
+                            bool warp_sum = true) {
+    auto visit = [&](int v, int e, int acc) {
+        int2 c = Team::ld(hc + e);
+        return acc + (Team::ld(side + v) ? c.y : c.x);
+    };
+    auto flush = [&](int v, int acc) {
+        if (acc) atomicAdd(gain + v, acc);
+    };
+    if (warp_sum)
+        lb_reduce_items<int>(noff, N, P, nadj, 0, cooperative_groups::plus<int>(), visit, flush, t, ts);
+    else
+        lb_for_each_items<int>(noff, N, P, nadj, 0, visit, flush, t, ts);
 }
 
 // The same gains with each hyperedge's contribution formed on the spot from its degree, its
@@ -106,26 +110,29 @@ __device__ void d_node_gain(Team t, int N, int P, const int *noff, const int *na
 template <class Team>
 __device__ void d_node_gain_direct(Team t, int N, int P, const int *noff, const int *nadj,
                                    const int *hoff, const int *hw, const int *n1,
-                                   const uint8_t *side, int *gain, const int *ts = nullptr) {
-    lb_reduce_items<int>(
-        noff, N, P, nadj, 0, cooperative_groups::plus<int>(),
-        [&](int v, int e, int acc) {
-            const int d = Team::ld(hoff + e + 1) - Team::ld(hoff + e);
-            const int a1 = Team::ld(n1 + e);
-            const int w = hw ? Team::ld(hw + e) : 1;
-            const int a = Team::ld(side + v) ? a1 : d - a1;  // pins on v's side
-            return acc + (a == 1 ? w : (a == d ? -w : 0));
-        },
-        [&](int v, int acc) {
-            if (acc) atomicAdd(gain + v, acc);
-        },
-        t, ts);
+                                   const uint8_t *side, int *gain, const int *ts = nullptr,
+                                   bool warp_sum = true) {
+    auto visit = [&](int v, int e, int acc) {
+        const int d = Team::ld(hoff + e + 1) - Team::ld(hoff + e);
+        const int a1 = Team::ld(n1 + e);
+        const int w = hw ? Team::ld(hw + e) : 1;
+        const int a = Team::ld(side + v) ? a1 : d - a1;  // pins on v's side
+        return acc + (a == 1 ? w : (a == d ? -w : 0));
+    };
+    auto flush = [&](int v, int acc) {
+        if (acc) atomicAdd(gain + v, acc);
+    };
+    if (warp_sum)
+        lb_reduce_items<int>(noff, N, P, nadj, 0, cooperative_groups::plus<int>(), visit, flush, t, ts);
+    else
+        lb_for_each_items<int>(noff, N, P, nadj, 0, visit, flush, t, ts);
 }
 
 // ------------------------------------------------------------------------ selection
 // Grid-stride loop over the team's nodes that loads gain, side and weight of four nodes (one per
-// stride) before visiting any of them (fn(v, gain, side, weight)): the visits update shared-memory counters, and without the
-// batching every node's loads would wait for the previous node's update.
+// stride) before visiting any of them (fn(v, gain, side, weight)): the visits update
+// shared-memory counters, and without the batching every node's loads would wait for the
+// previous node's update.
 template <class Team, class Fn>
 __device__ __forceinline__ void sel_nodes(Team t, int N, const int *gain, const uint8_t *side,
                                           const int *nw, Fn fn) {
