@@ -129,6 +129,25 @@ __device__ __forceinline__ void take_hist(RState *st, unsigned (*h)[kHistBins]) 
     __syncthreads();
 }
 
+// A loop condition evaluated by the last thread of the kernel that produced its inputs; in a
+// captured bisection the flag is also stored in its check slot.
+struct CondArgs {
+    int kind;                    // COND_NONE, COND_INITIAL, COND_REBAL
+    int first;                   // first evaluation of the loop (resets its counters)
+    int m0, m;                   // Algorithm 3: side 0 grows to m0 / m of the weight
+    long long limit0, limit1;    // rebalance: per-side limits
+    long long max_rounds;
+    unsigned *slot;              // flag_slot() of this evaluation (null outside a capture)
+};
+enum { COND_NONE = 0, COND_INITIAL = 1, COND_REBAL = 2 };
+
+__device__ __forceinline__ void eval_cond(RState *st, const CondArgs &c, uint32_t *status) {
+    if (c.kind == COND_INITIAL) d_initial_cond(st, c.max_rounds, status, c.first != 0, c.m0, c.m);
+    else if (c.kind == COND_REBAL) d_rebal_cond(st, c.limit0, c.limit1, c.max_rounds, status, c.first != 0);
+    else return;
+    if (c.slot && threadIdx.x == 0) *c.slot = st->flag;
+}
+
 // Selection over a grid: clamped-gain histogram, then (last block) the per-group threshold; the
 // rebalancing and moved lists are emptied for the application scan that follows.  st->slow is
 // left for the exact passes (and stored in its check slot).
@@ -136,7 +155,7 @@ __global__ void __launch_bounds__(kBlock)
 k_sel(int N, int kind, long long s, const int *__restrict__ gain, uint8_t *side,
       const int *__restrict__ nw, RState *st, unsigned *slow_slot) {
     __shared__ unsigned h[2][kHistBins];
-    d_sel_hist(GridTeam(), N, kind, gain, side, nw, st, h, true);
+    d_sel_hist(GridTeam(), N, kind, gain, side, nw, st, h);
     if (!last_block(&st->arrived)) return;
     take_hist(st, h);
     d_sel_find(kind, s, st, h);
@@ -156,7 +175,8 @@ constexpr int kSelSmallWords = kSelOneBlock / 32;
 
 __global__ void __launch_bounds__(kSelOneThreads, 1)
 k_sel_small(int N, int kind, long long s, const int *__restrict__ gain, uint8_t *side,
-            const int *__restrict__ nw, RState *st, uint32_t *status, int *list, int *moved) {
+            const int *__restrict__ nw, RState *st, uint32_t *status, int *list, int *moved,
+            CondArgs cond, bool weights) {
     extern __shared__ int s_gain[];                                  // N gains
     signed char *s_grp = reinterpret_cast<signed char *>(s_gain + N);  // N groups (-1: none)
     __shared__ unsigned h[2][kHistBins];
@@ -232,6 +252,27 @@ k_sel_small(int N, int kind, long long s, const int *__restrict__ gain, uint8_t 
         }
         if (sel) d_apply_node(kind, v, side, nw, st, list, moved);
     }
+    if (cond.kind == COND_NONE) return;
+    // the loop condition that follows the selection, evaluated here instead of by a launch of
+    // its own; with `weights` the side weights are summed afresh first (the initial partition
+    // keeps them current as it moves nodes)
+    __syncthreads();
+    if (weights) {
+        unsigned long long w0 = 0, w1 = 0;
+        for (int v = threadIdx.x; v < N; v += blockDim.x) {
+            const unsigned long long w = (unsigned long long)nw[v];
+            if (side[v]) w1 += w;
+            else w0 += w;
+        }
+        w0 = block_sum(w0, red);
+        w1 = block_sum(w1, red);
+        if (threadIdx.x == 0) {
+            st->W[0] = w0;
+            st->W[1] = w1;
+        }
+        __syncthreads();
+    }
+    eval_cond(st, cond, status);
 }
 
 // One digit of the exact radix select: histogram, then (last block) the narrowed range.
@@ -248,26 +289,7 @@ k_sel_exact(int N, int kind, const int *__restrict__ gain, const uint8_t *__rest
     d_sel_find_exact(st, status, h);
 }
 
-// A loop condition evaluated by the last thread of the kernel that produced its inputs; in a
-// captured bisection the flag is also stored in its check slot.
-struct CondArgs {
-    int kind;                    // COND_NONE, COND_INITIAL, COND_REBAL
-    int first;                   // first evaluation of the loop (resets its counters)
-    int m0, m;                   // Algorithm 3: side 0 grows to m0 / m of the weight
-    long long limit0, limit1;    // rebalance: per-side limits
-    long long max_rounds;
-    unsigned *slot;              // flag_slot() of this evaluation (null outside a capture)
-};
-enum { COND_NONE = 0, COND_INITIAL = 1, COND_REBAL = 2 };
-
-__device__ __forceinline__ void eval_cond(RState *st, const CondArgs &c, uint32_t *status) {
-    if (c.kind == COND_INITIAL) d_initial_cond(st, c.max_rounds, status, c.first != 0, c.m0, c.m);
-    else if (c.kind == COND_REBAL) d_rebal_cond(st, c.limit0, c.limit1, c.max_rounds, status, c.first != 0);
-    else return;
-    if (c.slot && threadIdx.x == 0) *c.slot = st->flag;
-}
-
-// W = side weights: partial sums in Wacc, moved to W (and Wacc cleared) by the last block, which
+// W = side weights: one partial sum per block, added in block order by the last block, which
 // then evaluates the loop condition that needs W (if any).
 __global__ void __launch_bounds__(kBlock)
 k_side_weights(int N, const uint8_t *__restrict__ side, const int *__restrict__ nw, RState *st,
@@ -427,18 +449,25 @@ void node_gains(bipart_graph *g, Level &L, const uint8_t *side, int *gain, int *
 }
 
 // Top-K selection per `kind` and its application (flip, or collect for the ordered rebalance).
-void select_apply(bipart_graph *g, Level &L, int kind, long long sq, const int *gain,
-                  uint8_t *side, int *list) {
+// With `cond`, a one-block selection also evaluates that loop condition (taking its check slot)
+// and returns true; otherwise the caller launches the condition itself.
+bool select_apply(bipart_graph *g, Level &L, int kind, long long sq, const int *gain,
+                  uint8_t *side, int *list, CondArgs *cond = nullptr, bool weights = false) {
     int *moved = g->w.moved.as<int>();
     cudaStream_t s = g->stream;
     RState *st = rstate(g);
     if (L.N <= kSelOneBlock) {
-        // one block: the selection, its exact passes if any, and its application
+        // one block: the selection, its exact passes if any, its application (and the condition)
+        CondArgs c{COND_NONE, 0, 1, 2, 0, 0, 0, nullptr};
+        if (cond) {
+            cond->slot = flag_slot(g);
+            c = *cond;
+        }
         ProfScope ps("select_hist", 9.0 * L.N, s);
-        k_sel_small<<<1, kSelOneThreads, 5 * (size_t)std::max(L.N, 1), s>>>(L.N, kind, sq, gain, side, L.nw(),
-                                                                            st, dev_status(g), list, moved);
+        k_sel_small<<<1, kSelOneThreads, 5 * (size_t)std::max(L.N, 1), s>>>(
+            L.N, kind, sq, gain, side, L.nw(), st, dev_status(g), list, moved, c, weights);
         BP_LAUNCH();
-        return;
+        return cond != nullptr;
     }
     unsigned *slot = flag_slot(g);
     {
@@ -457,6 +486,7 @@ void select_apply(bipart_graph *g, Level &L, int kind, long long sq, const int *
     ProfScope ps("select_apply", 10.0 * L.N, s);
     scan(L.N, TieIn{kind, gain, side, L.nw(), st}, ApplyOut{kind, gain, side, L.nw(), st, list, moved},
          g->w.scan, dev_status(g), s);
+    return false;
 }
 
 void side_weights(bipart_graph *g, Level &L, const uint8_t *side, const CondArgs &cond) {
@@ -482,7 +512,7 @@ void initial_partition(bipart_graph *g, Level &L, uint8_t *side, int *gain, int 
     for (int64_t it = 0; device_flag(g, &st->flag); ++it) {
         if (it > (int64_t)L.N + 2) throw Fail{BIPART_ERR_TIMEOUT, "Algorithm 3 made no progress"};
         compute_gains(g, L, side, gain);
-        select_apply(g, L, SEL_INITIAL, sq, gain, side, nullptr);
+        if (select_apply(g, L, SEL_INITIAL, sq, gain, side, nullptr, &c)) continue;
         c.slot = flag_slot(g);
         ProfScope ps("loop_cond", 0.0, s);
         k_initial_cond<<<1, 32, 0, s>>>(st, c, dev_status(g));
@@ -490,14 +520,23 @@ void initial_partition(bipart_graph *g, Level &L, uint8_t *side, int *gain, int 
     }
 }
 
-void refine_iter(bipart_graph *g, Level &L, uint8_t *side, int *gain) {
-    if (L.N == 0) return;
+// One refinement iteration; with `cond` (the rebalance's first condition, after the last
+// iteration) returns whether the selection kernel evaluated it.
+bool refine_iter(bipart_graph *g, Level &L, uint8_t *side, int *gain, CondArgs *cond = nullptr) {
+    if (L.N == 0) return false;
     compute_gains(g, L, side, gain);
-    select_apply(g, L, SEL_REFINE, 0, gain, side, nullptr);
+    return select_apply(g, L, SEL_REFINE, 0, gain, side, nullptr, cond, true);
+}
+
+CondArgs rebal_cond_args(Level &L, const int64_t limit[2], int first) {
+    return CondArgs{COND_REBAL, first, 1, 2, (long long)limit[0], (long long)limit[1], (long long)L.N + 1,
+                    nullptr};
 }
 
 // Rebalance of reading C13 with a limit per side; leaves warn = 1 when it ran out of candidates.
-void rebalance(bipart_graph *g, Level &L, uint8_t *side, int *gain, const int64_t limit[2]) {
+// `cond_done`: the first condition was evaluated by the last refinement iteration's selection.
+void rebalance(bipart_graph *g, Level &L, uint8_t *side, int *gain, const int64_t limit[2],
+               bool cond_done) {
     cudaStream_t s = g->stream;
     RState *st = rstate(g);
     const int64_t sq = ceil_sqrt64(L.N);
@@ -506,9 +545,11 @@ void rebalance(bipart_graph *g, Level &L, uint8_t *side, int *gain, const int64_
     int S = 1;
     while (S < sq) S <<= 1;
     const size_t smem = sizeof(unsigned long long) * (size_t)S;
-    CondArgs c{COND_REBAL, 1, 1, 2, (long long)limit[0], (long long)limit[1], (long long)L.N + 1,
-               flag_slot(g)};
-    side_weights(g, L, side, c);
+    CondArgs c = rebal_cond_args(L, limit, 1);
+    if (!cond_done) {
+        c.slot = flag_slot(g);
+        side_weights(g, L, side, c);
+    }
     c.first = 0;
     for (int64_t it = 0; device_flag(g, &st->flag); ++it) {
         if (it > (int64_t)L.N + 2) throw Fail{BIPART_ERR_TIMEOUT, "rebalance made no progress"};
@@ -562,8 +603,12 @@ void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, const int64_t limi
             std::swap(cur, other);
             g->w.n1_level = nullptr;  // a new level: its counts are recounted
         }
-        for (int it = 0; it < iters; ++it) refine_iter(g, *L, cur, gain);
-        if (L->N > 0) rebalance(g, *L, cur, gain, limit);
+        bool cond_done = false;
+        for (int it = 0; it < iters; ++it) {
+            CondArgs first = rebal_cond_args(*L, limit, 1);
+            cond_done = refine_iter(g, *L, cur, gain, it + 1 == iters ? &first : nullptr);
+        }
+        if (L->N > 0) rebalance(g, *L, cur, gain, limit, cond_done);
         else BP_CUDA(cudaMemsetAsync(&rstate(g)->warn, 0, sizeof(unsigned), g->stream));
     }
     s = g->stream;

@@ -155,11 +155,11 @@ __device__ __forceinline__ void sel_nodes(Team t, int N, const int *gain, const 
     }
 }
 
-// Fast pass: histogram of clamped gains per group (h: 2 * kHistBins shared counters).
-// Without `flush` the histogram stays in h (a one-block pass that searches it itself).
+// Fast pass: histogram of clamped gains per group (h: 2 * kHistBins shared counters), added into
+// the grid's histogram st->hist.
 template <class Team>
 __device__ void d_sel_hist(Team t, int N, int kind, const int *gain, const uint8_t *side,
-                           const int *nw, RState *st, unsigned (*h)[kHistBins], bool flush = true) {
+                           const int *nw, RState *st, unsigned (*h)[kHistBins]) {
     for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
     sel_nodes(t, N, gain, side, nw, [&](int64_t, int g, uint8_t sd, int w) {
@@ -170,7 +170,6 @@ __device__ void d_sel_hist(Team t, int N, int kind, const int *gain, const uint8
         atomicAdd(&h[grp][b], 1u);
     });
     __syncthreads();
-    if (!flush) return;
     for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) {
         unsigned c = (&h[0][0])[i];
         if (c) atomicAdd(&(&st->hist[0][0])[i], c);
