@@ -8,8 +8,11 @@ call is inside the timed region (CUDA events on the handle's stream).
 Extra keys:
   e2e          the same metric through bipart_create + bipart_partition + destroy with HOST
                buffers (pinned), host<->device copies inside the timed region
-  roofline     the dominant kernel: algorithmic bytes / CUDA-event duration per launch, against
-               the measured HBM copy bandwidth
+  roofline     the dominant kernel (largest device time in a second pass of the timed steps with
+               CUDA-event probes around every launch): algorithmic bytes / probed duration per
+               launch against the measured HBM copy bandwidth, its share of all probed time, and
+               the DRAM traffic of its ncu record in profiles/ (null once its sources changed)
+  profile      every probed kernel group of that pass: launches and ms per step, share, GB/s
   cpu_baseline the CPU oracle (single thread) on one full bisection of the same workload
   gpu_launches kernels the library launched inside the timed region
 
