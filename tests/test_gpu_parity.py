@@ -70,6 +70,12 @@ def test_smoke_small():
     check_bisection(synth.uniform(500, 500, 2, 6, seed=1))
 
 
+def test_entry_point_smoke():
+    # the smoke() a runner calls after build(): one small bisection on cuda:0 against the oracle
+    import __graft_entry__
+    __graft_entry__.smoke()
+
+
 @pytest.mark.parametrize("policy", ["LDH", "HDH", "LWD", "HWD", "RAND"])
 def test_c0_uniform_10k_all_policies(policy):
     check_bisection(synth.c0_uniform(), 0.1, policy)
