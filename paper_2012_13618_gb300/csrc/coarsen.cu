@@ -2,16 +2,19 @@
 // contraction) of Sec. 3.1, plus the level-0 normalisation and the node -> hyperedge incidence.
 //
 // Per level, with N nodes, E hyperedges and P pins:
-//   k_hedge_key      hkey[e] = priority(e) << 32 | mix32(e)                  (Alg. 1, Table 1)
-//   k_match          match[v] = argmin of hkey over v's hyperedges, and the size / weight of
-//                    every matched set S(e) by integer atomics (order-independent)   (Alg. 1)
-//   k_group          singleton sets join the lightest merged node of their hyperedge
-//                    (step-1 snapshot), smallest member id of every group          (Alg. 2)
+//   k_level_init     hkey[e] = priority(e) << 32 | mix32(e), matching accumulators reset
+//                    (Alg. 1, Table 1; runs inside the previous level's incidence fill)
+//   k_match_min      per node, the smallest hkey over its hyperedges (64-bit atomicMin)  (Alg. 1)
+//   k_match_set      match[v], and the size / weight of every matched set S(e) by integer
+//                    atomics (order-independent)                                      (Alg. 1)
+//   k_single_best    per singleton set, the lightest step-1 merged node among its pins  (Alg. 2)
+//   k_group          the final groups, smallest member id of every group              (Alg. 2)
 //   scan             coarse ids in ascending order of the smallest member          (reading C8)
 //   k_cmap           cmap[v] and coarse node weights
-//   seg_unique       per hyperedge: pins mapped through cmap, sorted, de-duplicated   (Alg. 2)
-//   scan + k_seg_copy   compaction of the hyperedges with >= 2 distinct pins
-//   incidence        node -> hyperedge CSR of the coarse level (counting + fill)
+//   seg_unique       per hyperedge: pins mapped through cmap, sorted, de-duplicated in three
+//                    tiers (thread, warp, block)                                      (Alg. 2)
+//   scan + k_seg_copy   compaction of the hyperedges with >= 2 distinct pins, coarse degrees
+//   incidence        node -> hyperedge CSR of the coarse level (offsets scan + fill)
 #include <cuda_runtime.h>
 
 #include <algorithm>
