@@ -5,8 +5,9 @@
 // Node order is always (gain descending, node id ascending).  A top-K is found without sorting:
 // one histogram pass over gains clamped to [-1024, 1023] fixes the threshold gain exactly unless
 // it falls in one of the two clamped end buckets, in which case an exact radix select (up to
-// three 11-bit passes over the order-preserving key gain ^ 0x80000000) narrows it down; a scan
-// over node ids then takes the lowest ids among nodes whose gain equals the threshold.  Only the
+// three 11-bit passes over the order-preserving key gain ^ 0x80000000) narrows it down; the lowest
+// ids among nodes whose gain equals the threshold are then taken by a scan over node ids (grid
+// levels) or from a shared-memory bitmap of those nodes (one-block levels).  Only the
 // rebalancing pass needs the chosen nodes in order; it sorts at most ceil(sqrt n) of them in one
 // block.  The two data-dependent loops (Algorithm 3's rounds and the rebalancing rounds) are
 // driven by a device-side flag; a captured bisection replays the recorded decisions as
@@ -59,9 +60,9 @@ constexpr int kWarpSumDegree = 64;
 }  // namespace
 
 // Grid kernels: one launch per phase (device code in refine_dev.cuh).
-// Side-1 pin counts of this pass into n1, plus two clearing jobs for the pass: the other count
-// buffer over the previous pass's hyperedges (it alternates with n1 from pass to pass), and the
-// gains that k_node_gain accumulates.
+// Side-1 pin counts of a level's first pass into n1, plus two clearing jobs: the other count
+// buffer over the previous count's hyperedges (the two alternate from count to count), and the
+// gains that the node-gain pass accumulates.
 __global__ void __launch_bounds__(kLbBlock)
 k_hedge_n1(int E, int P, const int *__restrict__ hoff, const int *__restrict__ pins,
            const uint8_t *__restrict__ side, int *__restrict__ n1, const int *__restrict__ ts,
