@@ -561,6 +561,9 @@ void capture_plan(bipart_graph *g, const Params &p, uint8_t *d_side, int nlev, i
             int n2 = 0;
             bisect_body(g, g->L0, p, g->total_node_weight, d_side, &n2);
             if (n2 != nlev) ok = false;
+            pl.scan_clean = g->w.scan.clean;
+            pl.scan_dirty[0] = g->w.scan.dirty[0];
+            pl.scan_dirty[1] = g->w.scan.dirty[1];
         } catch (...) {
             ok = false;
         }
@@ -616,6 +619,9 @@ int bisect_top(bipart_graph *g, const Params &p, uint8_t *d_side, int *nlev) {
             cudaEventRecord(t0, g->stream);
         }
         BP_CUDA(cudaGraphLaunch(pl.exec, g->stream));
+        g->w.scan.clean = pl.scan_clean;  // the device's scan state after the graph
+        g->w.scan.dirty[0] = pl.scan_dirty[0];
+        g->w.scan.dirty[1] = pl.scan_dirty[1];
         if (timing) cudaEventRecord(t1, g->stream);
         for (int64_t i = 0; i < pl.launches; ++i) note_launch();
         sync(g);

@@ -212,6 +212,11 @@ struct Plan {
     cudaGraphExec_t exec = nullptr;
     int64_t launches = 0;
     std::vector<Probe> probes;
+    // the stream's scan state as the captured bisection leaves it: a replay runs no host code,
+    // so the host copy is set to this after every launch (later scans on the stream, such as a
+    // k-way split's, must see which half is clean)
+    int scan_clean = 0;
+    int64_t scan_dirty[2] = {0, 0};
     void reset();
 };
 

@@ -134,16 +134,27 @@ def test_mid_and_big_degree_tiers():
     check_bisection(g, 0.05, "HDH", levels=4)
 
 
-def test_deterministic_ten_runs():
+@pytest.mark.parametrize("cfg", ["c0", "c1_50k", "c1_full", "c2_full", "c2_k8"])
+def test_deterministic_ten_runs(cfg):
+    # ten calls on one handle (eager, capture, then eight graph replays) and one on a fresh
+    # handle give the same parts, status and cut
     bp = _bp()
-    g = synth.c1_netlist(N=50_000)
+    g, k, eps = {
+        "c0": lambda: (synth.c0_uniform(), 2, 0.1),
+        "c1_50k": lambda: (synth.c1_netlist(N=50_000), 2, 0.05),
+        "c1_full": lambda: (synth.c1_netlist(), 2, 0.05),
+        "c2_full": lambda: (synth.c2_rownet(), 2, 0.05),
+        "c2_k8": lambda: (synth.c2_rownet(rows=300_000), 8, 0.05),
+    }[cfg]()
     with bp.create_from(g) as h:
-        first, _ = h.partition(2, 0.05, "LDH", 25, 2)
+        first, st = h.partition(k, eps, "LDH", 25, 2)
+        cut = h.cut(first)
         for _ in range(9):
-            again, _ = h.partition(2, 0.05, "LDH", 25, 2)
-            assert np.array_equal(first, again)
+            again, st2 = h.partition(k, eps, "LDH", 25, 2)
+            assert np.array_equal(first, again) and st2 == st
+            assert h.cut(again) == cut
     with bp.create_from(g) as h2:
-        assert np.array_equal(first, h2.partition(2, 0.05, "LDH", 25, 2)[0])
+        assert np.array_equal(first, h2.partition(k, eps, "LDH", 25, 2)[0])
 
 
 @pytest.mark.parametrize("k", [4, 8])
