@@ -157,6 +157,30 @@ def test_deterministic_ten_runs(cfg):
         assert np.array_equal(first, h2.partition(k, eps, "LDH", 25, 2)[0])
 
 
+def test_call_sequences_on_one_handle():
+    # a seeded mix of calls on one handle -- k, policy, epsilon, levels, iterations and flags
+    # changing and repeating, so that plans are captured, replayed, dropped and recaptured, and
+    # k-way splits follow replays -- each equal to the oracle's result for its parameters
+    bp = _bp()
+    g = synth.uniform(3000, 3200, 2, 6, seed=33)
+    g["nw"] = np.random.default_rng(4).integers(1, 4, size=g["N"]).astype(np.int32)
+    hr = oracle.Hypergraph.from_dict(g)
+    rng = np.random.default_rng(77)
+    menu = [(2, 0.1, "LDH", 25, 2, False, False), (8, 0.1, "LDH", 25, 2, False, False),
+            (3, 0.05, "HDH", 25, 1, False, False), (4, 0.1, "RAND", 4, 2, True, False),
+            (2, 0.05, "LWD", 25, 2, False, True), (6, 0.1, "HWD", 25, 3, True, True)]
+    expect = {}
+    with bp.create_from(g) as h:
+        for _ in range(24):
+            i = int(rng.integers(0, len(menu)))
+            k, eps, pol, lev, it, ad, mg = menu[i]
+            if i not in expect:
+                expect[i] = oracle.partition(hr, k, eps, pol, lev, it, adaptive=ad, merge=mg)
+            parts, st = h.partition(k, eps, pol, lev, it, adaptive_eps=ad, merge_parallel=mg)
+            ref, rst = expect[i]
+            assert np.array_equal(parts, ref) and st == rst, menu[i]
+
+
 @pytest.mark.parametrize("k", [4, 8])
 def test_kway_small(k):
     bp = _bp()
