@@ -159,11 +159,6 @@ def test_design_space_sweep_matches_oracle_and_frontier():
                                  for j in range(len(pts))) for i in front)
 
 
-def test_pareto_helper():
-    from paper_2012_13618_gb300.sweep import pareto
-    assert pareto([(1, 5), (2, 3), (3, 4), (2, 3), (0.5, 9)]) == [0, 1, 3, 4]
-
-
 def test_batch_general_k_matches_single():
     # the worker pool runs k = 3 / 6 (adaptive) requests exactly as bipart_partition does
     import paper_2012_13618_gb300 as bp
