@@ -365,6 +365,37 @@ def test_refine_path9():
     assert oracle.cut_bisection(h, side) == g["cut_after"]
 
 
+def test_refine_iteration_properties(rng):
+    # Algorithm 5 on random hypergraphs, checked against brute-force cut deltas: the same number
+    # of nodes leaves each side (l_min), every mover had a non-negative single-move gain, and
+    # on each side no staying node with gain >= 0 ranks before a mover in (gain desc, id asc)
+    for _ in range(30):
+        N, hoff, pins, nw, hw = random_hg(rng, 50, 60, dmax=6, weights=True, hweights=True)
+        h = oracle.Hypergraph.from_csr(N, hoff, pins, nw, hw)
+        before = rng.integers(0, 2, size=N).astype(np.uint8)
+        base = oracle.cut_bisection(h, before)
+        delta = np.empty(N, np.int64)
+        for u in range(N):
+            s2 = before.copy()
+            s2[u] ^= 1
+            delta[u] = base - oracle.cut_bisection(h, s2)
+        side = before.copy()
+        lmin = oracle.refine_iter(h, side)
+        moved = np.nonzero(side != before)[0]
+        assert len(moved) == 2 * lmin
+        for s in (0, 1):
+            movers = [u for u in moved if before[u] == s]
+            assert len(movers) == lmin
+            assert all(delta[u] >= 0 for u in movers)
+            stayers = [u for u in range(N) if before[u] == s and side[u] == s and delta[u] >= 0]
+            if movers:
+                worst = max(movers, key=lambda u: (-delta[u], u))
+                assert all((-delta[v], v) > (-delta[worst], worst) for v in stayers)
+            cand = sum(1 for u in range(N) if before[u] == s and delta[u] >= 0)
+            assert lmin <= cand
+        assert lmin == min(sum(1 for u in range(N) if before[u] == t and delta[u] >= 0) for t in (0, 1))
+
+
 def test_rebalance_path9():
     g = gold("path9_rebalance.json")
     hoff, pins = path_graph(9)
