@@ -353,6 +353,32 @@ def test_initial_without_hyperedges():
         assert side.tolist() == [0] * moved + [1] * (n - moved)
 
 
+def test_initial_against_bruteforce_gains(rng):
+    # Algorithm 3 on random weighted hypergraphs, replayed with brute-force single-move gains:
+    # while side 0 holds less than half the weight, the ceil(sqrt n) nodes of side 1 with the
+    # largest gain (smaller id first) move to side 0 (reading C14)
+    for _ in range(25):
+        N, hoff, pins, nw, hw = random_hg(rng, 36, 40, dmax=5, weights=True, hweights=True)
+        h = oracle.Hypergraph.from_csr(N, hoff, pins, nw, hw)
+        w = np.asarray(h.arrays()["nw"], np.int64)
+        W = int(w.sum())
+        s = oracle.ceil_sqrt(N)
+        side = np.ones(N, np.uint8)
+        rounds = 0
+        while 2 * int(w[side == 0].sum()) < W:
+            rounds += 1
+            base = oracle.cut_bisection(h, side)
+            gain = {}
+            for u in np.nonzero(side == 1)[0]:
+                s2 = side.copy()
+                s2[u] = 0
+                gain[int(u)] = base - oracle.cut_bisection(h, s2)
+            for u in sorted(gain, key=lambda u: (-gain[u], u))[:s]:
+                side[u] = 0
+        got, got_rounds = oracle.initial(h)
+        assert got_rounds == rounds and np.array_equal(got, side)
+
+
 def test_refine_path9():
     g = gold("path9_refine.json")
     hoff, pins = path_graph(9)
