@@ -450,6 +450,50 @@ def test_rebalance_outcome_properties(rng):
             assert not np.any(w[side == H] <= lim - W[1 - H])
 
 
+def test_rebalance_against_bruteforce_gains(rng):
+    # reading C13 replayed with brute-force single-move gains: while a side is above the limit,
+    # its nodes that fit the other side's room, ordered (gain desc, id asc), move as the shortest
+    # prefix reaching the excess, at most ceil(sqrt n) nodes and never past the room
+    for _ in range(40):
+        N, hoff, pins, nw, hw = random_hg(rng, 36, 40, dmax=5, weights=True, hweights=True)
+        h = oracle.Hypergraph.from_csr(N, hoff, pins, nw, hw)
+        w = np.asarray(h.arrays()["nw"], np.int64)
+        lim = oracle.limit(int(w.sum()), float(rng.choice([0.0, 0.05, 0.2])))
+        start = (rng.random(N) < rng.random()).astype(np.uint8)
+        side = start.copy()
+        s = oracle.ceil_sqrt(N)
+        status, rounds = oracle.OK, 0
+        while True:
+            W = [int(w[side == 0].sum()), int(w[side == 1].sum())]
+            H = 0 if W[0] > lim else (1 if W[1] > lim else -1)
+            if H < 0:
+                break
+            room, need = lim - W[1 - H], W[H] - lim
+            cand = [int(u) for u in np.nonzero(side == H)[0] if w[u] <= room]
+            if not cand:
+                status = oracle.WARN_IMBALANCED
+                break
+            rounds += 1
+            base = oracle.cut_bisection(h, side)
+            gain = {}
+            for u in cand:
+                s2 = side.copy()
+                s2[u] ^= 1
+                gain[u] = base - oracle.cut_bisection(h, s2)
+            take, acc = [], 0
+            for u in sorted(cand, key=lambda u: (-gain[u], u)):
+                if len(take) == s or acc + w[u] > room:
+                    break
+                take.append(u)
+                acc += int(w[u])
+                if acc >= need:
+                    break
+            side[take] = 1 - H
+        got = start.copy()
+        st, got_rounds = oracle.rebalance(h, got, lim)
+        assert (st, got_rounds) == (status, rounds) and np.array_equal(got, side)
+
+
 # ----------------------------------------------------------------------------- multilevel driver
 def test_bisect_levels_zero_runs_on_input():
     h = oracle.Hypergraph.from_dict(synth.uniform(300, 300, 2, 4, seed=5))
