@@ -32,3 +32,16 @@ def test_params_marshalling():
     assert bp._params().flags == 0
     # the struct matches the header's layout: int32 k; double epsilon; 4 x int32
     assert ctypes.sizeof(bp.Params) == 32
+
+
+def test_roofline_traffic_record_tracks_the_sources(monkeypatch):
+    # the DRAM traffic bench.py reports comes from the ncu record in profiles/ only while the
+    # record's source hash matches the kernel's current sources; it scales with the launch
+    import bench
+    level0 = 125_651_088
+    t = bench.ncu_traffic("node_gain", level0, level0)
+    assert t is not None and t > 0
+    assert abs(bench.ncu_traffic("node_gain", level0 / 4, level0) - t / 4) < 1e-6 * t
+    monkeypatch.setattr(bench, "source_hash", lambda name: "0000000000000000")
+    assert bench.ncu_traffic("node_gain", level0, level0) is None
+    assert bench.ncu_traffic("no_such_kernel", level0, level0) is None
