@@ -34,14 +34,18 @@ def test_params_marshalling():
     assert ctypes.sizeof(bp.Params) == 32
 
 
-def test_roofline_traffic_record_tracks_the_sources(monkeypatch):
-    # the DRAM traffic bench.py reports comes from the ncu record in profiles/ only while the
+def test_roofline_traffic_record_tracks_the_sources(monkeypatch, tmp_path):
+    # the DRAM traffic bench.py reports comes from an ncu record in profiles/ only while the
     # record's source hash matches the kernel's current sources; it scales with the launch
+    import json
     import bench
-    level0 = 125_651_088
-    t = bench.ncu_traffic("node_gain", level0, level0)
-    assert t is not None and t > 0
-    assert abs(bench.ncu_traffic("node_gain", level0 / 4, level0) - t / 4) < 1e-6 * t
-    monkeypatch.setattr(bench, "source_hash", lambda name: "0000000000000000")
-    assert bench.ncu_traffic("node_gain", level0, level0) is None
-    assert bench.ncu_traffic("no_such_kernel", level0, level0) is None
+    (tmp_path / "profiles").mkdir()
+    rec = {"kernel": "node_gain", "dram_bytes": 1000, "source_sha256": "abc"}
+    (tmp_path / "profiles" / "node_gain_c1_netlist_1M.md").write_text(
+        "# summary\n\ntraffic-record: " + json.dumps(rec) + "\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "source_hash", lambda name: "abc")
+    assert bench.ncu_traffic("node_gain", 50, 100) == 500
+    monkeypatch.setattr(bench, "source_hash", lambda name: "def")
+    assert bench.ncu_traffic("node_gain", 50, 100) is None
+    assert bench.ncu_traffic("no_such_kernel", 50, 100) is None
