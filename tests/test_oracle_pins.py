@@ -510,6 +510,68 @@ def test_bisect_stops_when_no_hyperedges():
     assert r["nlev"] == 26 or sizes[-1][1] == 0
 
 
+def test_bisect_path9_golden():
+    # Sec. 3.4 on the 9-node path, derived by hand step by step (tests/golden/path9_bisect.json):
+    # the driver's order -- Algorithm 3 on the coarsest level, then at every level from the
+    # coarsest down: projection (below the coarsest), `iters` Algorithm 5 iterations, rebalance
+    g = gold("path9_bisect.json")
+    hoff, pins = path_graph(9)
+    for c in g["cases"]:
+        h = oracle.Hypergraph.from_csr(9, hoff, pins, np.array(c["nw"], np.int32))
+        r = oracle.bisect(h, 0.1, "LDH", c["levels"], c["iters"])
+        assert r["nlev"] == c["nlev"], c["name"]
+        if "cmap0" in c:
+            assert r["cmaps"][0].tolist() == c["cmap0"], c["name"]
+        assert r["side"].tolist() == c["side"], c["name"]
+        assert r["status"] == c["status"], c["name"]
+        assert oracle.cut_bisection(h, r["side"]) == c["cut"], c["name"]
+
+
+def _replay_bisect(h, eps, policy, levels, iters):
+    """Sec. 3.4 rebuilt from the oracle's single-step functions in the paper's order: coarsen
+    (Algorithm 2) until `levels` contractions or until N stops changing (reading C11); Algorithm 3
+    on the coarsest level; then from the coarsest level to the input: project through cmap,
+    `iters` Algorithm 5 iterations, the rebalance of reading C13."""
+    levs, cmaps = [h], []
+    while len(levs) - 1 < levels:
+        c, cmap, _ = oracle.coarsen(levs[-1], policy)
+        if c.N == levs[-1].N:
+            break
+        levs.append(c)
+        cmaps.append(cmap)
+    W = int(np.asarray(h.arrays()["nw"], np.int64).sum())
+    lim = oracle.limit(W, eps)
+    side, _ = oracle.initial(levs[-1])
+    side = np.ascontiguousarray(side, np.uint8)
+    status = oracle.OK
+    for l in range(len(levs) - 1, -1, -1):
+        if l < len(levs) - 1:
+            side = np.ascontiguousarray(side[cmaps[l]], np.uint8)
+        for _ in range(iters):
+            oracle.refine_iter(levs[l], side)
+        status, _ = oracle.rebalance(levs[l], side, lim)
+    return side, status, len(levs)
+
+
+def test_bisect_schedule_replayed_from_steps(rng):
+    # the driver against its own schedule written out from the single steps, on random weighted
+    # hypergraphs, several level counts and iteration counts (a coarsest level left unrefined,
+    # a rebalance skipped above level 0, or a projection through the wrong map changes results)
+    for trial in range(24):
+        N = int(rng.integers(20, 120))
+        _, hoff, pins, nw, hw = random_hg(rng, N, int(rng.integers(N // 2, 2 * N)), dmax=5,
+                                         weights=True, hweights=bool(trial % 2))
+        h = oracle.Hypergraph.from_csr(N, hoff, pins, nw, hw)
+        levels = [0, 1, 2, 25][trial % 4]
+        iters = [1, 2, 3][trial % 3]
+        eps = [0.0, 0.05, 0.1][trial % 3]
+        policy = ["LDH", "HDH", "RAND"][trial % 3]
+        side, status, nlev = _replay_bisect(h, eps, policy, levels, iters)
+        r = oracle.bisect(h, eps, policy, levels, iters, keep_levels=False)
+        assert r["nlev"] == nlev and r["status"] == status
+        assert np.array_equal(r["side"], side), trial
+
+
 def _brute_min_cut(a, lim):
     N = a["N"]
     best = None
@@ -593,6 +655,59 @@ def test_kway_children_equal_solo_bisections():
         s, l2g = oracle.subgraph(h, top, j)
         rj = oracle.bisect(s, 0.1, "RAND", 25, 2, keep_levels=False)
         assert np.array_equal(part[l2g] & 1, rj["side"].astype(np.int32))
+
+
+def _subgraph_restated(a, part, j):
+    """Reading C16 written out: the nodes of part j in ascending id, renumbered 0..n-1; every
+    hyperedge restricted to them, kept when at least 2 pins remain, in ascending hyperedge id;
+    node and hyperedge weights carried."""
+    l2g = [v for v in range(a["N"]) if part[v] == j]
+    loc = {v: i for i, v in enumerate(l2g)}
+    hoff, pins, hw = [0], [], []
+    for e in range(a["E"]):
+        kept = [loc[v] for v in a["pins"][a["hoff"][e]:a["hoff"][e + 1]] if v in loc]
+        if len(kept) < 2:
+            continue
+        pins += kept
+        hoff.append(len(pins))
+        hw.append(int(a["hw"][e]))
+    nw = [int(a["nw"][v]) for v in l2g]
+    return l2g, hoff, pins, nw, hw
+
+
+def test_subgraph_restated(rng):
+    # net splitting (reading C16) against its definition, on random weighted hypergraphs and
+    # parts, plus a hyperedge left with exactly one pin in the part (dropped) and one left with
+    # two (kept)
+    cases = []
+    for _ in range(20):
+        N = int(rng.integers(5, 60))
+        _, hoff, pins, nw, hw = random_hg(rng, N, int(rng.integers(1, 2 * N)), dmax=6,
+                                         weights=True, hweights=True)
+        part = rng.integers(0, 3, size=N).astype(np.int32)
+        cases.append((N, hoff, pins, nw, hw, part))
+    # e0 = {0,1,2}: one pin (2) in part 1; e1 = {2,3}: both in part 1; e2 = {0,3,4}: pins 3, 4
+    cases.append((5, np.array([0, 3, 5, 8], np.int32), np.array([0, 1, 2, 2, 3, 0, 3, 4], np.int32),
+                  np.array([1, 2, 3, 4, 5], np.int32), np.array([7, 8, 9], np.int32),
+                  np.array([0, 0, 1, 1, 1], np.int32)))
+    for N, hoff, pins, nw, hw, part in cases:
+        h = oracle.Hypergraph.from_csr(N, hoff, pins, nw, hw)
+        a = h.arrays()
+        for j in range(int(part.max()) + 1):
+            s, l2g = oracle.subgraph(h, part, j)
+            want_l2g, want_hoff, want_pins, want_nw, want_hw = _subgraph_restated(a, part, j)
+            b = s.arrays()
+            assert l2g.tolist() == want_l2g
+            assert b["hoff"].tolist() == want_hoff and b["pins"].tolist() == want_pins
+            assert b["nw"].tolist() == want_nw and b["hw"].tolist() == want_hw
+    # the constructed case, part 1: nodes 2, 3, 4 -> 0, 1, 2; e0 keeps only node 2 (dropped),
+    # e1 -> {0, 1} weight 8, e2 -> {1, 2} weight 9
+    h = oracle.Hypergraph.from_csr(*cases[-1][:5])
+    s, l2g = oracle.subgraph(h, cases[-1][5], 1)
+    b = s.arrays()
+    assert l2g.tolist() == [2, 3, 4] and b["hoff"].tolist() == [0, 2, 4]
+    assert b["pins"].tolist() == [0, 1, 1, 2] and b["hw"].tolist() == [8, 9]
+    assert b["nw"].tolist() == [3, 4, 5]
 
 
 def test_kway_trivial_and_invalid():
