@@ -29,6 +29,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -112,11 +113,11 @@ class Clocks:
         self.gpu = gpu_index
         self.proc = None
         self.t0 = self.t1 = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="bipart_clocks_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -161,6 +162,10 @@ class Clocks:
                     continue
                 if lo <= ts <= hi:
                     rows.append(parts[1:])
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples in window"]}
         num = lambda x: x.replace(".", "", 1).isdigit()
@@ -180,7 +185,8 @@ def load_workload():
 
 
 def cpu_baseline(g, budget_s=12.0):
-    """Times the oracle (single thread, as it stands) on full bisections of the workload."""
+    """Times the oracle (single thread, as it stands) on full bisections of the workload; also
+    returns its partition (side of every node) and status for the bit-exactness check."""
     import oracle
     h = oracle.Hypergraph.from_dict(g)
     P = int(g["hoff"][-1])
@@ -188,15 +194,16 @@ def cpu_baseline(g, budget_s=12.0):
     t_all = time.perf_counter()
     while True:
         t0 = time.perf_counter()
-        oracle.bisect(h, WORKLOAD["epsilon"], WORKLOAD["policy"], WORKLOAD["levels"],
-                      WORKLOAD["refine_iters"], keep_levels=False)
+        r = oracle.bisect(h, WORKLOAD["epsilon"], WORKLOAD["policy"], WORKLOAD["levels"],
+                          WORKLOAD["refine_iters"], keep_levels=False)
         times.append(time.perf_counter() - t0)
         if time.perf_counter() - t_all > budget_s or len(times) >= 5:
             break
     t = statistics.median(times)
-    return {"value": P / t, "unit": "pins/s", "cores": 1, "kind": "oracle",
-            "sample": f"{len(times)} full k=2 bisection(s) of the 1M-node netlist, single-threaded "
-                      f"sequential C oracle, median {t:.3f} s; host has {os.cpu_count()} cores"}
+    return ({"value": P / t, "unit": "pins/s", "cores": 1, "kind": "oracle",
+             "sample": f"{len(times)} full k=2 bisection(s) of the 1M-node netlist, single-threaded "
+                       f"sequential C oracle, median {t:.3f} s; host has {os.cpu_count()} cores"},
+            r["side"].astype(np.int32), int(r["status"]))
 
 
 def run_reference(args):
@@ -387,7 +394,12 @@ def run_gpu(args):
                         "kernel's current sources)"}
 
     if rank == 0:
-        cpu = cpu_baseline(g) if (ws == 1 and not args.no_cpu_baseline) else None
+        cpu, exact = None, None
+        if ws == 1 and not args.no_cpu_baseline:
+            cpu, ref_side, ref_status = cpu_baseline(g)
+            # the timed steps' partition (device buffer) against the oracle's, node for node
+            exact = bool(np.array_equal(parts_dev, ref_side) and int(st) == ref_status)
+            assert exact, "the timed partition differs from the oracle's"
         line = {"metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": warmups, "ms_per_step": ms_max,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -396,6 +408,7 @@ def run_gpu(args):
                                l2="flushed between steps (512 MB write)",
                                parallelism=f"{ws} independent replica(s)"),
                 "status": int(st),
+                "bit_exact_vs_oracle": exact,
                 "clocks": clk.summary(),
                 "e2e": {"value": ws * P / e2e_s, "unit": "pins/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": e2e_steps},

@@ -81,6 +81,39 @@ def test_server_mixed_requests_same_as_alone():
             assert qms >= 0 and rms > 0
 
 
+def test_batch_deterministic_ten_runs():
+    # the batched call (persistent block kernel for the k = 2 instances, worker pool for k = 4)
+    # gives the same parts on ten calls, equal to the oracle's
+    import paper_2012_13618_gb300 as bp
+    graphs = mixed_instances(10, seed=7)
+    params = [dict(k=[2, 2, 4][i % 3], eps=0.05, policy="LDH", levels=25, iters=2)
+              for i in range(len(graphs))]
+    first, st0 = bp.partition_batch(graphs, params, workers=4)
+    for i, g in enumerate(graphs):
+        ref, rst = oracle.partition(oracle.Hypergraph.from_dict(g), params[i]["k"], 0.05, "LDH", 25, 2)
+        assert np.array_equal(first[i], ref) and st0[i] == rst, i
+    for run in range(9):
+        parts, st = bp.partition_batch(graphs, params, workers=[1, 4, 8][run % 3])
+        assert np.array_equal(st, st0), run
+        for a, b in zip(parts, first):
+            assert np.array_equal(a, b), run
+
+
+def test_server_mix_deterministic_ten_runs():
+    # ten rounds of the same mixed request trace through one server: every result identical
+    import paper_2012_13618_gb300 as bp
+    graphs = mixed_instances(9, seed=8)
+    ks = [2, 4, 16]
+    refs = [oracle.partition(oracle.Hypergraph.from_dict(g), ks[i % 3], 0.05, "LDH", 25, 2)
+            for i, g in enumerate(graphs)]
+    with bp.Server(hbm_budget_bytes=8 << 30, workers=4) as srv:
+        for run in range(10):
+            tickets = [srv.submit(g, k=ks[i % 3], eps=0.05) for i, g in enumerate(graphs)]
+            for i, t in enumerate(tickets):
+                parts, st, _, _ = srv.wait(t)
+                assert np.array_equal(parts, refs[i][0]) and st == refs[i][1], (run, i)
+
+
 def test_server_rejects_request_above_budget():
     import paper_2012_13618_gb300 as bp
     g = synth.c3_instance(0, N=5000)

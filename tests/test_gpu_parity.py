@@ -1,7 +1,6 @@
 """Parity of the sm_103a path (through the C ABI) with the CPU oracle: every coarse level
 (hyperedge CSR, node and hyperedge weights, cmap, matching), the partition vector, the status and
 the cut must be identical -- the arithmetic is integer, so the tolerance is zero."""
-import os
 
 import numpy as np
 import pytest
@@ -273,18 +272,6 @@ def test_netlist_100k_kway16():
 
 def test_c1_netlist_1m_full():
     check_bisection(synth.c1_netlist(), 0.05, "LDH")
-
-
-@pytest.mark.skipif(os.environ.get("BIPART_SLOW") != "1",
-                    reason="the oracle's full 5M-row bisection takes ~90 s; set BIPART_SLOW=1")
-def test_c2_rownet_5m_full_vs_oracle():
-    # the whole C2 bisection against the oracle's, partition for partition
-    bp = _bp()
-    g = synth.c2_rownet()
-    ref = oracle.bisect(oracle.Hypergraph.from_dict(g), 0.05, "LDH", 25, 2, keep_levels=False)
-    with bp.create_from(g) as h:
-        parts, st = h.partition(2, 0.05, "LDH", 25, 2)
-        assert np.array_equal(parts, ref["side"].astype(np.int32)) and st == ref["status"]
 
 
 def test_c2_rownet_reduced_k8():
