@@ -185,11 +185,12 @@ void bipart_server_destroy(bipart_server server);
  * allocation by a library fails or breaks the pool's accounting), or a latency-critical loop that
  * cannot afford the synchronisation an allocation may imply.
  *   All arrays are DEVICE memory owned by the caller: a valid hyperedge -> pin CSR
- *   (d_hedge_offsets[num_hedges + 1], d_hedge_pins), optional d_hedge_weights (NULL = unit),
- *   d_parts[num_nodes] with values in [0, k), and the output d_cut (one int64).  Duplicate pins
- *   and single-pin hyperedges are allowed (they do not change the cut).
+ *   (d_hedge_offsets[num_hedges + 1], d_hedge_pins), optional d_hedge_weights (NULL = unit;
+ *   each weight >= 1, as bipart_create requires), d_parts[num_nodes] with values in [0, k), and
+ *   the output d_cut (one int64).  Duplicate pins and single-pin hyperedges are allowed (they do
+ *   not change the cut).
  *   Result: *d_cut = sum over hyperedges of w_e * (lambda_e - 1), written asynchronously on
- *   `stream`; -1 if a pin or a part is out of range.
+ *   `stream`; -1 if a pin, a part or a hyperedge weight is out of range.
  *   Limits: num_hedges <= 4,194,304 and 1 <= k <= 64, else BIPART_ERR_INVALID_ARG before any GPU
  *   work.  Scratch is a fixed 16 MiB array inside the library's device image on every GPU that
  *   loads it (kept until exit).  The first call on each device looks up that array's address
@@ -206,7 +207,9 @@ int64_t bipart_kernel_launches(void);
 /* Per-kernel timing: while enabled, the library brackets the launches of its main kernels with
  * CUDA events on the launching stream and accumulates, per kernel name, the number of launches,
  * their summed device time and their summed algorithmic bytes (the bytes the algorithm must move:
- * each array streamed once, gathers at element size).  Enabling or disabling resets the totals. */
+ * each array streamed once, gathers at element size).  on = 2 keeps the totals per kernel and
+ * level instead ("name@cL" for the coarsening of level L, "name@rL" for the initial partition and
+ * refinement at level L).  Enabling or disabling resets the totals. */
 int bipart_profile_enable(int on);
 
 /* Restricts per-kernel timing to the kernel named `kernel_name` (NULL or "" = all kernels), so

@@ -38,12 +38,13 @@ std::mutex g_na_mu;
 unsigned long long *g_na_ptr[kMaxDevices] = {};
 
 // lambda_e = number of distinct parts among the pins of e (0 for an empty hyperedge); a pin
-// outside [0, N) or a part outside [0, k) raises the error flag instead of being read.
-// Hyperedges of degree <= 32 take one thread; larger ones are handled by the whole warp with a
-// shuffle OR reduction of the part masks.
+// outside [0, N), a part outside [0, k) or a hyperedge weight below 1 raises the error flag
+// instead of being used.  Hyperedges of degree <= 32 take one thread; larger ones are handled by
+// the whole warp with a shuffle OR reduction of the part masks.
 __global__ void __launch_bounds__(kNaBlock)
 k_na_lambda(int N, int E, const int *__restrict__ hoff, const int *__restrict__ pins,
-            const int *__restrict__ parts, int k, unsigned long long *__restrict__ scratch) {
+            const int *__restrict__ hw, const int *__restrict__ parts, int k,
+            unsigned long long *__restrict__ scratch) {
     int *lambda = reinterpret_cast<int *>(scratch + kNaHeaderWords + kNaMaxBlocks);
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
@@ -51,7 +52,11 @@ k_na_lambda(int N, int E, const int *__restrict__ hoff, const int *__restrict__ 
     for (int e0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; e0 < E; e0 += warps * 32) {
         int e = e0 + lane;
         int a = 0, d = 0;
-        if (e < E) { a = hoff[e]; d = hoff[e + 1] - a; }
+        if (e < E) {
+            a = hoff[e];
+            d = hoff[e + 1] - a;
+            if (hw && hw[e] < 1) bad = true;
+        }
         bool small = e < E && d <= 32;
         if (small) {
             unsigned long long m = 0;
@@ -86,7 +91,7 @@ k_na_lambda(int N, int E, const int *__restrict__ hoff, const int *__restrict__ 
 
 // cut = sum_e w_e * max(lambda_e - 1, 0): per-block partials in the scratch, then the last block
 // to finish adds them in block order (a fixed order, so the sum is reproducible) and writes the
-// caller's output (-1 when a part was out of range).
+// caller's output (-1 when a pin, a part or a weight was out of range).
 __global__ void __launch_bounds__(kNaBlock)
 k_na_reduce(int E, const int *__restrict__ hw, unsigned long long *__restrict__ scratch,
             long long *__restrict__ out) {
@@ -180,7 +185,7 @@ extern "C" int bipart_cut_noalloc(int32_t num_nodes, int32_t num_hedges,
     if (grid > kNaMaxBlocks) grid = kNaMaxBlocks;
     if (num_hedges > 0) {
         k_na_lambda<<<grid, kNaBlock, 0, s>>>(num_nodes, num_hedges, d_hedge_offsets, d_hedge_pins,
-                                              d_parts, k, scratch);
+                                              d_hedge_weights, d_parts, k, scratch);
         note_launch();
     }
     k_na_reduce<<<grid, kNaBlock, 0, s>>>(num_hedges, d_hedge_weights, scratch,
