@@ -150,8 +150,10 @@ def kernel_launches() -> int:
     return int(load().bipart_kernel_launches())
 
 
-def profile_enable(on: bool = True):
-    _check(load().bipart_profile_enable(1 if on else 0))
+def profile_enable(on=True):
+    """Per-kernel timing on (True / 1), per kernel and level ("levels" / 2), or off."""
+    mode = 2 if on in ("levels", 2) else (1 if on else 0)
+    _check(load().bipart_profile_enable(mode))
 
 
 def profile_select(name=None):

@@ -151,7 +151,12 @@ constexpr int kSlotLevels = 2048;
 
 int32_t *level_sizes(bipart_graph *g, int idx) {
     int32_t *small = g->w.small.as<int32_t>();
-    return idx < kSlotLevels ? small + kSlotBase + 3 * idx : small + 8;
+    return idx < kSlotLevels - 1 ? small + kSlotBase + 3 * idx : small + 8;
+}
+
+// The last slot triple is kept for the cluster tail's level count, arena check and bytes.
+int32_t *tail_info_slot(bipart_graph *g) {
+    return g->w.small.as<int32_t>() + kSlotBase + 3 * (kSlotLevels - 1);
 }
 
 void read_i32s(bipart_graph *g, int n, const int32_t *const *d, int32_t *v) {
@@ -503,22 +508,39 @@ void bisect_body(bipart_graph *g, Level &L0, const Params &p, int64_t W, uint8_t
     BP_CUDA(cudaMemsetAsync(g->w.small.p, 0, small_state_bytes(), g->stream));
     g->w.scan.reset(g->stream);
     std::vector<Level *> levels{&L0};
+    const int64_t limit[2] = {balance_limit(W, p.m0, p.m, p.e6), balance_limit(W, p.m - p.m0, p.m, p.e6)};
+    // Levels are coarsened by the grid kernels until one is small enough for the cluster tail,
+    // which then runs the rest of the bisection down to that level in one launch.
+    int tail_from = tail_eligible(L0, p.levels, p.flags) ? 0 : -1;
     bool init_done = false;  // the next level's key and reset pass already ran
-    while ((int)levels.size() - 1 < p.levels) {
+    while (tail_from < 0 && (int)levels.size() - 1 < p.levels) {
         Level &f = *levels.back();
         if (f.E == 0) break;  // with no hyperedge nothing merges: N' == N
         size_t idx = levels.size() - 1;
         if (g->lev.size() <= idx) g->lev.emplace_back(new Level);
         Level &c = *g->lev[idx];
+        c.clear_view();
+        prof_level('c', (int)idx);
+        const int tail_new = p.levels - (int)idx - 1;  // contractions allowed after c
+        bool to_tail = false;  // decided by coarsen_level, which then leaves c's incidence out
         init_done = coarsen_level(g, f, c, p.policy, level_sizes(g, (int)idx),
                                   (p.flags & BIPART_FLAG_MERGE_PARALLEL) != 0, init_done,
-                                  (int)idx + 1 < p.levels);
+                                  (int)idx + 1 < p.levels, tail_new, p.flags, &to_tail);
         if (c.N == f.N) break;
         levels.push_back(&c);
+        if (to_tail) tail_from = (int)levels.size() - 1;
+    }
+    if (tail_from >= 0) {
+        // the tail leaves the side of its starting level in side_a, sized for level 0 here so
+        // that uncoarsen() finds it in place
+        g->w.side_b.ensure((size_t)std::max(L0.N, 1), g->stream);
+        uint8_t *sa = (uint8_t *)g->w.side_a.ensure((size_t)std::max(L0.N, 1), g->stream);
+        prof_level('t', tail_from);
+        run_tail(g, levels, p, limit, sa);
     }
     if (nlev) *nlev = (int)levels.size();
-    const int64_t limit[2] = {balance_limit(W, p.m0, p.m, p.e6), balance_limit(W, p.m - p.m0, p.m, p.e6)};
-    uncoarsen(g, levels, limit, p.m0, p.m, p.iters, d_side);
+    uncoarsen(g, levels, limit, p.m0, p.m, p.iters, d_side, tail_from);
+    prof_level(0, 0);
     if (g->ex.capturing) flush_checks(g);
 }
 
@@ -1286,7 +1308,7 @@ int bipart_get_level(bipart_handle h, int32_t level, int32_t *N, int32_t *E, int
         }
         if (hedge_weights && L.E > 0) {
             if (L.unit_hw) std::fill(hedge_weights, hedge_weights + L.E, 1);
-            else BP_CUDA(cudaMemcpyAsync(hedge_weights, L.b_hw.as<int>(), sizeof(int) * (size_t)L.E, cudaMemcpyDeviceToHost, s));
+            else BP_CUDA(cudaMemcpyAsync(hedge_weights, L.hw(), sizeof(int) * (size_t)L.E, cudaMemcpyDeviceToHost, s));
         }
         sync(h);
         return BIPART_OK;
@@ -1368,6 +1390,7 @@ struct ProfTot {
 };
 std::mutex g_prof_mu;
 bool g_prof_on = false;
+bool g_prof_levels = false;  // totals keyed by kernel and level (profile mode 2)
 int g_prof_epoch = 0;
 std::string g_prof_only;
 std::vector<ProfRec> g_prof_pending;
@@ -1423,9 +1446,22 @@ void prof_collect(const std::vector<Probe> &probes) {
     cudaGetLastError();
 }
 
-ProfScope::ProfScope(const char *name, double bytes, cudaStream_t s) {
+thread_local char tl_prof_phase = 0;
+thread_local int tl_prof_level = 0;
+
+void prof_level(char phase, int level) {
+    tl_prof_phase = phase;
+    tl_prof_level = level;
+}
+
+ProfScope::ProfScope(const char *name_in, double bytes, cudaStream_t s) {
     if (!g_prof_on) return;
-    if (!g_prof_only.empty() && g_prof_only != name) return;
+    if (!g_prof_only.empty() && g_prof_only != name_in) return;
+    std::string tagged;
+    if (g_prof_levels && tl_prof_phase) {
+        tagged = std::string(name_in) + "@" + tl_prof_phase + std::to_string(tl_prof_level);
+    }
+    const char *name = tagged.empty() ? name_in : tagged.c_str();
     if (tl_capturing) {
         // inside a captured plan: event record nodes (external records: a plain record during
         // capture only orders work inside the graph), read back after every replay
@@ -1440,13 +1476,29 @@ ProfScope::ProfScope(const char *name, double bytes, cudaStream_t s) {
         return;
     }
     std::lock_guard<std::mutex> lk(g_prof_mu);
+    // finished records are drained here, never between a scope's end() and its set_bytes()
+    if (g_prof_pending.size() > 4096) prof_drain();
     ProfRec r{name, bytes, prof_event(), prof_event(), s};
     cudaEventRecord(r.a, s);
     g_prof_pending.push_back(r);
     slot = (int)g_prof_pending.size() - 1;
 }
 
-ProfScope::~ProfScope() {
+void ProfScope::set_bytes(double bytes) {
+    if (slot <= -2) {
+        bipart_graph *g = tl_graph;
+        size_t i = (size_t)(-2 - slot);
+        if (g && i < g->plan.probes.size()) g->plan.probes[i].bytes = bytes;
+        return;
+    }
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (slot < (int)g_prof_pending.size()) g_prof_pending[slot].bytes = bytes;
+}
+
+void ProfScope::end() {
+    if (ended) return;
+    ended = true;
     if (slot <= -2) {
         bipart_graph *g = tl_graph;
         size_t i = (size_t)(-2 - slot);
@@ -1457,7 +1509,6 @@ ProfScope::~ProfScope() {
     if (slot < 0) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (slot < (int)g_prof_pending.size()) cudaEventRecord(g_prof_pending[slot].b, g_prof_pending[slot].s);
-    if (g_prof_pending.size() > 4096) prof_drain();
 }
 }  // namespace bp
 
@@ -1467,8 +1518,10 @@ extern "C" int bipart_profile_enable(int on) {
     std::lock_guard<std::mutex> lk(bp::g_prof_mu);
     bp::prof_drain();
     bp::g_prof_tot.clear();
-    if (bp::g_prof_on != (on != 0)) bp::g_prof_epoch++;  // plans are recaptured with/without probes
+    if (bp::g_prof_on != (on != 0) || bp::g_prof_levels != (on == 2))
+        bp::g_prof_epoch++;  // plans are recaptured with/without probes
     bp::g_prof_on = on != 0;
+    bp::g_prof_levels = on == 2;
     return BIPART_OK;
 }
 

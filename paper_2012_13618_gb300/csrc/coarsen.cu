@@ -590,7 +590,8 @@ void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t
 }
 
 bool coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *sizes, bool merge,
-                   bool init_done, bool more_levels) {
+                   bool init_done, bool more_levels, int tail_new, int flags, bool *to_tail) {
+    if (to_tail) *to_tail = false;
     cudaStream_t s = g->stream;
     Work &w = g->w;
     const int N = f.N, E = f.E;
@@ -655,6 +656,13 @@ bool coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *siz
     contract(g, E, f.P, f.hoff(), f.pins(), f.hw(), f.cmap(), c, deg, N > 0, sizes + 1, f.tsh(), merge,
              N > 0 ? sizes : nullptr);
     const int Nc = c.N;
+    if (to_tail && tail_new >= 0 && c.N != f.N && tail_eligible(c, tail_new, flags)) {
+        // the cluster tail takes over from c and reads only its hyperedge CSR
+        c.b_cmap.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);
+        c.b_match.ensure(sizeof(int) * (size_t)std::max(Nc, 1), s);
+        *to_tail = true;
+        return false;
+    }
     // when c will be coarsened in turn (the stop rule of reading C11 lets it), its key and reset
     // pass rides along with its incidence fill
     const bool prep = more_levels && c.E > 0 && c.N != f.N;

@@ -103,17 +103,30 @@ struct Level {
     bool unit_hw = true;
     Buf b_hoff, b_pins, b_hw, b_nw, b_noff, b_nadj, b_cmap, b_match;
     Buf b_tsh, b_tsn;  // tile-start tables of the hyperedge and incidence CSRs
+    // A level built by the cluster tail (tail.cu) is a view into the tail's arena: hoff, pins,
+    // hw, nw, cmap, match (it has no incidence CSR and no tile-start tables).
+    int32_t *view[6] = {};
     int32_t *tsh() const { return b_tsh.as<int32_t>(); }
     int32_t *tsn() const { return b_tsn.as<int32_t>(); }
-    int32_t *hoff() const { return b_hoff.as<int32_t>(); }
-    int32_t *pins() const { return b_pins.as<int32_t>(); }
-    int32_t *hw() const { return unit_hw ? nullptr : b_hw.as<int32_t>(); }
-    int32_t *nw() const { return b_nw.as<int32_t>(); }
+    int32_t *hoff() const { return view[0] ? view[0] : b_hoff.as<int32_t>(); }
+    int32_t *pins() const { return view[0] ? view[1] : b_pins.as<int32_t>(); }
+    int32_t *hw() const { return unit_hw ? nullptr : (view[0] ? view[2] : b_hw.as<int32_t>()); }
+    int32_t *nw() const { return view[0] ? view[3] : b_nw.as<int32_t>(); }
     int32_t *noff() const { return b_noff.as<int32_t>(); }
     int32_t *nadj() const { return b_nadj.as<int32_t>(); }
-    int32_t *cmap() const { return b_cmap.as<int32_t>(); }
-    int32_t *match() const { return b_match.as<int32_t>(); }
+    int32_t *cmap() const { return view[0] ? view[4] : b_cmap.as<int32_t>(); }
+    int32_t *match() const { return view[0] ? view[5] : b_match.as<int32_t>(); }
+    bool is_view() const { return view[0] != nullptr; }
+    void set_view(int32_t n, int32_t e, int32_t p, int32_t *hoff_, int32_t *pins_, int32_t *hw_,
+                  int32_t *nw_, int32_t *cmap_, int32_t *match_) {
+        N = n; E = e; P = p; unit_hw = hw_ == nullptr;
+        view[0] = hoff_; view[1] = pins_; view[2] = hw_; view[3] = nw_; view[4] = cmap_; view[5] = match_;
+    }
+    void clear_view() {
+        for (auto &v : view) v = nullptr;
+    }
     void reserve(int32_t n, int32_t e, int32_t p, bool unit, cudaStream_t s) {
+        clear_view();
         N = n; E = e; P = p; unit_hw = unit;
         b_hoff.ensure(sizeof(int32_t) * ((size_t)e + 1), s);
         b_pins.ensure(sizeof(int32_t) * (size_t)p, s);
@@ -151,6 +164,8 @@ struct Work {
     Buf list;        // node list (rebalance candidates)
     Buf pinned;      // host-pinned mirror of `small`
     uint32_t *host_small = nullptr;
+    // the cluster tail (tail.cu): arena of its coarse levels and its scratch
+    Buf t_arena, t_e0, t_e1, t_e2, t_e3, t_e4, t_p, t_n, t_c, t_x, t_trace;
 };
 
 struct Params {
@@ -253,8 +268,12 @@ void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t
 // sizes: level_sizes() slots receiving {N', E', P'}.  init_done: f's key and reset pass already
 // ran (with the previous level's incidence fill); more_levels: the level count allows another
 // contraction after this one.  Returns whether c's own key and reset pass has been run.
+// tail_new: contractions still allowed after c when the cluster tail may take over from c (-1:
+// it may not).  When it does, *to_tail is set and c's node -> hyperedge incidence is not built:
+// the caller must then run the tail from c (this is the one place that decides).
 bool coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *sizes, bool merge,
-                   bool init_done, bool more_levels);
+                   bool init_done, bool more_levels, int tail_new = -1, int flags = 0,
+                   bool *to_tail = nullptr);
 // Node -> hyperedge incidence of a level whose hyperedge CSR is complete and whose node degrees
 // were counted into degree_counters(g, N) while its pins were written.
 void build_incidence(bipart_graph *g, Level &L);
@@ -265,8 +284,10 @@ int *degree_counters(bipart_graph *g, int32_t N);
 // (1 = the level-0 rebalance ran out of candidates) is left in *bisect_status_word(g).
 // Side 0 is meant for m0 of m parts: Algorithm 3 grows it to that share and limit[s] bounds
 // side s (halving bisection: m0 / m = 1 / 2, equal limits).
+// With tail_from >= 0 the levels from tail_from down were refined by the cluster tail, which left
+// the side of level tail_from in the handle's first side buffer (side_a).
 void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, const int64_t limit[2], int m0,
-               int m, int32_t iters, uint8_t *d_side0);
+               int m, int32_t iters, uint8_t *d_side0, int tail_from = -1);
 const unsigned *bisect_status_word(bipart_graph *g);
 // Bytes at the start of the small scratch holding counters and selection state that phases
 // leave zero for the next one (cleared once at the start of every bisection).
@@ -278,16 +299,41 @@ void coarsen_init();  // same, for the coarsening kernels
 // m != 2).
 int64_t balance_limit(int64_t W, int32_t ms, int32_t m, int64_t e6);
 
+// ------------------------------------------------------------------ cluster tail (tail.cu)
+// Blocks per cluster of the tail kernel on this GPU (0: not available; the grid path runs every
+// level).  BIPART_TAIL_NODES / BIPART_TAIL_PINS override the starting-level limits (0 disables).
+int tail_cluster();
+// Whether the rest of a bisection from level L (max_new more contractions allowed) can run as
+// the cluster tail.
+bool tail_eligible(const Level &L, int max_new, int flags);
+// Runs the tail from levels.back(): appends the coarse levels it builds (arena views in g->lev),
+// writes the bisection of the starting level to d_side and its rebalance status to the handle's
+// refinement state.  Eager: one launch and one size read-back; while capturing: the recorded sizes.
+void run_tail(bipart_graph *g, std::vector<Level *> &levels, const Params &p, const int64_t limit[2],
+              uint8_t *d_side);
+// Two device ints of the handle's size slots for the tail's level count and arena check.
+int32_t *tail_info_slot(bipart_graph *g);
+struct RState;
+RState *refine_state(bipart_graph *g);
+
 // ------------------------------------------------------------------------- diagnostics
 // Brackets one kernel launch with CUDA events on `s` when profiling is on (see
 // bipart_profile_enable); `bytes` is the launch's algorithmic traffic.
 int prof_epoch();
 void prof_collect(const std::vector<Probe> &probes);
+// Tags the launches that follow with a phase ('c' coarsening, 'r' refinement, 0 none) and a level
+// index; in profile mode 2 the totals are kept per kernel and tag.
+void prof_level(char phase, int level);
 
 struct ProfScope {
     int slot = -1;
+    bool ended = false;
     ProfScope(const char *name, double bytes, cudaStream_t s);
-    ~ProfScope();
+    ~ProfScope() { end(); }
+    // Records the end event now (right after the launch) instead of at destruction.
+    void end();
+    // Sets the algorithmic bytes when they are known only after the launch (its own read-back).
+    void set_bytes(double bytes);
 };
 
 // ------------------------------------------------------------------------- block path (block.cu)

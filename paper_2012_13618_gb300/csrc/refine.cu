@@ -36,9 +36,8 @@ inline int grid_for(int64_t n, int per_block = kBlock, int cap = 152 * 16) {
     return (int)std::min<int64_t>(b, cap);
 }
 
-// Selection passes over up to this many nodes run as one block of kSelOneThreads threads (the
+// Selection passes over up to kSelOneBlock nodes run as one block of kSelOneThreads threads (the
 // histogram, the threshold and the application in one launch).
-constexpr int kSelOneBlock = 16384;
 constexpr int kSelOneThreads = 1024;
 
 
@@ -167,13 +166,8 @@ k_sel(int N, int kind, long long s, const int *__restrict__ gain, uint8_t *side,
     }
 }
 
-// Selection of a level of at most kSelOneBlock nodes by one block, every phase after the first
-// on shared memory: the clamped-gain histogram (each node's gain and group cached on the way),
-// the threshold (and the exact radix passes when it falls in a clamped end bucket), the ranks of
-// the threshold's ties by ascending id from a bitmap with per-word prefix counts, and the
-// application.  Dynamic shared memory: 5 bytes per node.
-constexpr int kSelSmallWords = kSelOneBlock / 32;
-
+// Selection of a level of at most kSelOneBlock nodes by one block (d_sel_small), then the loop
+// condition that follows it.  Dynamic shared memory: 5 bytes per node.
 __global__ void __launch_bounds__(kSelOneThreads, 1)
 k_sel_small(int N, int kind, long long s, const int *__restrict__ gain, uint8_t *side,
             const int *__restrict__ nw, RState *st, uint32_t *status, int *list, int *moved,
@@ -181,78 +175,8 @@ k_sel_small(int N, int kind, long long s, const int *__restrict__ gain, uint8_t 
     extern __shared__ int s_gain[];                                  // N gains
     signed char *s_grp = reinterpret_cast<signed char *>(s_gain + N);  // N groups (-1: none)
     __shared__ unsigned h[2][kHistBins];
-    __shared__ unsigned tie[2][kSelSmallWords];
-    __shared__ unsigned pre[2][kSelSmallWords];
     __shared__ unsigned long long red[33];
-    __shared__ unsigned s_mode[2], s_thr[2], s_take[2];
-    for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) (&h[0][0])[i] = 0;
-    for (int i = threadIdx.x; i < 2 * kSelSmallWords; i += blockDim.x) (&tie[0][0])[i] = 0;
-    __syncthreads();
-    sel_nodes(GridTeam(), N, gain, side, nw, [&](int64_t v, int g, uint8_t sd, int w) {
-        const int grp = sel_group(kind, st, g, sd, w);
-        s_gain[v] = g;
-        s_grp[v] = (signed char)grp;
-        if (grp < 0) return;
-        int b = g - kClampLo;
-        b = b < 0 ? 0 : (b > kHistBins - 1 ? kHistBins - 1 : b);
-        atomicAdd(&h[grp][b], 1u);
-    });
-    __syncthreads();
-    d_sel_find(kind, s, st, h);
-    if (threadIdx.x == 0) {
-        st->list_count = 0;
-        st->moved_count = 0;
-    }
-    __syncthreads();
-    if (*(volatile unsigned *)&st->slow) {
-        for (int pass = 0; pass < 3; ++pass) {
-            d_sel_hist_exact(GridTeam(), N, kind, gain, side, nw, st, h, false);
-            d_sel_find_exact(st, status, h);
-        }
-        if (threadIdx.x == 0) st->slow = 0;
-        __syncthreads();
-    }
-    if (threadIdx.x < 2) {
-        s_mode[threadIdx.x] = st->g[threadIdx.x].mode;
-        s_thr[threadIdx.x] = st->g[threadIdx.x].thr;
-        s_take[threadIdx.x] = st->g[threadIdx.x].take_eq;
-    }
-    __syncthreads();
-    // the threshold's ties, one bit per node
-    for (int v = threadIdx.x; v < N; v += blockDim.x) {
-        const int grp = s_grp[v];
-        if (grp >= 0 && s_mode[grp] == 2 && gkey(s_gain[v]) == s_thr[grp])
-            atomicOr(&tie[grp][v >> 5], 1u << (v & 31));
-    }
-    __syncthreads();
-    // ties before each word, both groups in one packed scan (a count stays below 2^31)
-    const int words = (N + 31) >> 5;  // <= kSelSmallWords <= blockDim.x
-    const int t = threadIdx.x;
-    unsigned long long c = 0;
-    if (t < words) c = (unsigned long long)__popc(tie[1][t]) << 32 | (unsigned)__popc(tie[0][t]);
-    unsigned long long total;
-    const unsigned long long ex = block_exclusive_scan<unsigned long long>(c, red, &total);
-    if (t < words) {
-        pre[0][t] = (unsigned)ex;
-        pre[1][t] = (unsigned)(ex >> 32);
-    }
-    __syncthreads();
-    for (int v = threadIdx.x; v < N; v += blockDim.x) {
-        const int grp = s_grp[v];
-        if (grp < 0) continue;
-        const unsigned mode = s_mode[grp];
-        bool sel = mode == 1;
-        if (mode == 2) {
-            const unsigned k = gkey(s_gain[v]), thr = s_thr[grp];
-            if (k > thr) {
-                sel = true;
-            } else if (k == thr) {
-                const unsigned below = tie[grp][v >> 5] & ((1u << (v & 31)) - 1u);
-                sel = pre[grp][v >> 5] + (unsigned)__popc(below) < s_take[grp];
-            }
-        }
-        if (sel) d_apply_node(kind, v, side, nw, st, list, moved);
-    }
+    d_sel_small(N, kind, s, gain, side, nw, st, status, list, moved, s_gain, s_grp, h);
     if (cond.kind == COND_NONE) return;
     // the loop condition that follows the selection, evaluated here instead of by a launch of
     // its own; with `weights` the side weights are summed afresh first (the initial partition
@@ -566,8 +490,10 @@ void rebalance(bipart_graph *g, Level &L, uint8_t *side, int *gain, const int64_
 
 }  // namespace
 
+RState *refine_state(bipart_graph *g) { return rstate(g); }
+
 void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, const int64_t limit[2], int m0,
-               int m, int32_t iters, uint8_t *d_side0) {
+               int m, int32_t iters, uint8_t *d_side0, int tail_from) {
     cudaStream_t s = g->stream;
     const int Lc = (int)levels.size() - 1;
     int64_t nmax = 1, emax = 1;
@@ -591,11 +517,18 @@ void uncoarsen(bipart_graph *g, std::vector<Level *> &levels, const int64_t limi
     g->w.moved.ensure(sizeof(int) * (size_t)nmax, s);
 
     uint8_t *cur = sa, *other = sb;
-    initial_partition(g, *levels[Lc], cur, gain, m0, m);
-    for (int l = Lc; l >= 0; --l) {
+    // with the tail, the levels from tail_from down are done and sa holds level tail_from's side
+    const int top = tail_from >= 0 ? tail_from : Lc;
+    if (tail_from < 0) {
+        prof_level('r', Lc);
+        initial_partition(g, *levels[Lc], cur, gain, m0, m);
+    }
+    for (int l = top; l >= 0; --l) {
+        if (tail_from >= 0 && l == top) continue;
         Level *L = levels[l];
         s = g->stream;
-        if (l < Lc) {
+        prof_level('r', l);
+        if (l < top) {
             if (L->N > 0) {
                 ProfScope ps("project", 6.0 * L->N, s);
                 k_project<<<grid_for(L->N), kBlock, 0, s>>>(L->N, L->cmap(), cur, other);

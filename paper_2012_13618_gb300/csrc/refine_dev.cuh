@@ -571,6 +571,94 @@ __device__ inline void d_rebal_move(const int *gain, uint8_t *side, const int *n
     }
 }
 
+// Selection of a level of at most kSelOneBlock nodes by one block, every phase after the first
+// on shared memory: the clamped-gain histogram (each node's gain and group cached on the way in
+// s_gain, s_grp: N entries each; s_gain may be `gain` itself when that is in shared memory), the
+// threshold (and the exact radix passes when it falls in a clamped end bucket), the ranks of the
+// threshold's ties by ascending id from a bitmap with per-word prefix counts, and the
+// application.  h: 2 x kHistBins counters.  The rebalancing list and the moved list are emptied
+// first.  Deterministic: the same inputs give the same sides in every block that runs it.
+constexpr int kSelOneBlock = 16384;
+constexpr int kSelSmallWords = kSelOneBlock / 32;
+
+__device__ inline void d_sel_small(int N, int kind, long long s, const int *gain, uint8_t *side,
+                                   const int *nw, RState *st, uint32_t *status, int *list,
+                                   int *moved, int *s_gain, signed char *s_grp,
+                                   unsigned (*h)[kHistBins]) {
+    __shared__ unsigned tie[2][kSelSmallWords];
+    __shared__ unsigned pre[2][kSelSmallWords];
+    __shared__ unsigned long long red[33];
+    __shared__ unsigned s_mode[2], s_thr[2], s_take[2];
+    for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) (&h[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < 2 * kSelSmallWords; i += blockDim.x) (&tie[0][0])[i] = 0;
+    __syncthreads();
+    sel_nodes(CtaTeam(), N, gain, side, nw, [&](int64_t v, int g, uint8_t sd, int w) {
+        const int grp = sel_group(kind, st, g, sd, w);
+        s_gain[v] = g;
+        s_grp[v] = (signed char)grp;
+        if (grp < 0) return;
+        int b = g - kClampLo;
+        b = b < 0 ? 0 : (b > kHistBins - 1 ? kHistBins - 1 : b);
+        atomicAdd(&h[grp][b], 1u);
+    });
+    __syncthreads();
+    d_sel_find(kind, s, st, h);
+    if (threadIdx.x == 0) {
+        st->list_count = 0;
+        st->moved_count = 0;
+    }
+    __syncthreads();
+    if (*(volatile unsigned *)&st->slow) {
+        for (int pass = 0; pass < 3; ++pass) {
+            d_sel_hist_exact(CtaTeam(), N, kind, gain, side, nw, st, h, false);
+            d_sel_find_exact(st, status, h);
+        }
+        if (threadIdx.x == 0) st->slow = 0;
+        __syncthreads();
+    }
+    if (threadIdx.x < 2) {
+        s_mode[threadIdx.x] = st->g[threadIdx.x].mode;
+        s_thr[threadIdx.x] = st->g[threadIdx.x].thr;
+        s_take[threadIdx.x] = st->g[threadIdx.x].take_eq;
+    }
+    __syncthreads();
+    // the threshold's ties, one bit per node
+    for (int v = threadIdx.x; v < N; v += blockDim.x) {
+        const int grp = s_grp[v];
+        if (grp >= 0 && s_mode[grp] == 2 && gkey(s_gain[v]) == s_thr[grp])
+            atomicOr(&tie[grp][v >> 5], 1u << (v & 31));
+    }
+    __syncthreads();
+    // ties before each word, both groups in one packed scan (a count stays below 2^31)
+    const int words = (N + 31) >> 5;  // <= kSelSmallWords <= blockDim.x
+    const int t = threadIdx.x;
+    unsigned long long c = 0;
+    if (t < words) c = (unsigned long long)__popc(tie[1][t]) << 32 | (unsigned)__popc(tie[0][t]);
+    unsigned long long total;
+    const unsigned long long ex = block_exclusive_scan<unsigned long long>(c, red, &total);
+    if (t < words) {
+        pre[0][t] = (unsigned)ex;
+        pre[1][t] = (unsigned)(ex >> 32);
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < N; v += blockDim.x) {
+        const int grp = s_grp[v];
+        if (grp < 0) continue;
+        const unsigned mode = s_mode[grp];
+        bool sel = mode == 1;
+        if (mode == 2) {
+            const unsigned k = gkey(s_gain[v]), thr = s_thr[grp];
+            if (k > thr) {
+                sel = true;
+            } else if (k == thr) {
+                const unsigned below = tie[grp][v >> 5] & ((1u << (v & 31)) - 1u);
+                sel = pre[grp][v >> 5] + (unsigned)__popc(below) < s_take[grp];
+            }
+        }
+        if (sel) d_apply_node(kind, v, side, nw, st, list, moved);
+    }
+}
+
 template <class Team>
 __device__ void d_project(Team t, int N, const int *cmap, const uint8_t *coarse, uint8_t *fine) {
     for (int v = t.rank(); v < N; v += t.size()) fine[v] = Team::ld(coarse + Team::ld(cmap + v));
