@@ -34,6 +34,8 @@ void *g_alloc_ctx = nullptr;
 constexpr int kBlock = 256;
 constexpr size_t kSmallBytes = 64 * 1024;
 
+constexpr int kLanes = 8;  // host threads that bisect the subgraphs of a recursion-tree level
+
 inline int grid_for(int64_t n, int per_block = kBlock, int cap = 152 * 16) {
     int64_t b = (n + per_block - 1) / per_block;
     if (b < 1) b = 1;
@@ -304,6 +306,12 @@ __global__ void k_weight_sum(int N, const int *__restrict__ nw, unsigned long lo
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
 }
 
+// Tile-start table of a hyperedge CSR (the segment holding every kTsGran-th pin).
+__global__ void k_mark_tiles(int E, const int *__restrict__ hoff, int *__restrict__ ts) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
+        lb_mark_tiles(ts, e, hoff[e], hoff[e + 1] - hoff[e]);
+}
+
 // Side 0 of a subgraph keeps the part range starting at lo, side 1 takes the one starting at hi.
 __global__ void k_side_to_part(int N, const uint8_t *__restrict__ side, const int *__restrict__ l2g,
                                int lo, int hi, int *__restrict__ part) {
@@ -456,48 +464,154 @@ int64_t node_weight_sum(bipart_graph *g, Level &L) {
     return (int64_t)hres;
 }
 
-// Builds the subgraph of part j of level 0 into g->sub0; node map into g->l2g.
-void extract_subgraph(bipart_graph *g, const int *d_part, int j) {
+// Builds the subgraph of part j of the parent's level 0 as the child's level 0 (node map in the
+// child's l2g, weight total in its total_node_weight).  The extraction runs on the parent's stream
+// with the parent's scratch, reads the subgraph's sizes back once, and copies into child buffers of
+// exactly those sizes (a child keeps its buffers, and so its launch plan, from call to call).
+void extract_subgraph(bipart_graph *g, const int *d_part, int j, bipart_graph *kid) {
     cudaStream_t s = g->stream;
     Level &L = g->L0;
-    Level &S = g->sub0;
+    Level &S = kid->L0;
     Work &w = g->w;
-    int *loc = (int *)w.n_c.ensure(sizeof(int) * (size_t)std::max(L.N, 1), s);
-    int *l2g = (int *)g->l2g.ensure(sizeof(int) * (size_t)std::max(L.N, 1), s);
-    S.b_nw.ensure(sizeof(int) * (size_t)std::max(L.N, 1), s);
+    const size_t n1 = (size_t)std::max(L.N, 1), e1 = (size_t)std::max(L.E, 1);
+    int *loc = (int *)w.n_c.ensure(sizeof(int) * n1, s);
+    int *t_l2g = (int *)g->l2g.ensure(sizeof(int) * n1, s);
+    int *t_nw = (int *)w.n_b.ensure(sizeof(int) * n1, s);
+    int *t_hoff = (int *)w.e_c.ensure(sizeof(int) * (e1 + 1), s);
+    int *t_hw = L.unit_hw ? nullptr : (int *)w.e_d.ensure(sizeof(int) * e1, s);
+    int *cnt = (int *)w.e_a.ensure(sizeof(int) * e1, s);
+    int *emap = (int *)w.e_b.ensure(sizeof(int) * e1, s);
     int *small = w.small.as<int>();
-    BP_CUDA(cudaMemsetAsync(small, 0, 8 * sizeof(int), s));
-    scan(L.N, SubNodeIn{d_part, j}, SubNodeOut{L.N, L.nw(), loc, l2g, S.nw(), small + 4},
-         w.scan, dev_status(g), s);
-    int *cnt = (int *)w.e_a.ensure(sizeof(int) * (size_t)std::max(L.E, 1), s);
-    int *emap = (int *)w.e_b.ensure(sizeof(int) * (size_t)std::max(L.E, 1), s);
-    S.unit_hw = L.unit_hw;
-    S.b_hoff.ensure(sizeof(int) * ((size_t)L.E + 1), s);
-    S.b_pins.ensure(sizeof(int) * (size_t)std::max(L.P, 1), s);
-    S.b_tsh.ensure(sizeof(int) * ((size_t)L.P / kTsGran + 2), s);
-    if (!S.unit_hw) S.b_hw.ensure(sizeof(int) * (size_t)std::max(L.E, 1), s);
-    int *deg = degree_counters(g, L.N);  // subgraph degrees, counted while its pins are written
+    unsigned long long *wsum = reinterpret_cast<unsigned long long *>(small + 8);
+    BP_CUDA(cudaMemsetAsync(small, 0, 12 * sizeof(int), s));
+    scan(L.N, SubNodeIn{d_part, j}, SubNodeOut{L.N, L.nw(), loc, t_l2g, t_nw, small + 4}, w.scan,
+         dev_status(g), s);
     if (L.E > 0) {
         int gw = grid_for((int64_t)(L.E + 31) / 32 * 32);
         k_sub_count<<<gw, kBlock, 0, s>>>(L.E, L.hoff(), L.pins(), loc, cnt);
         BP_LAUNCH();
-        scan(L.E, SubEdgeIn{cnt}, SubEdgeOut{L.E, L.hw(), S.hoff(), S.unit_hw ? nullptr : S.b_hw.as<int>(), emap, small + 2, S.tsh()},
+        scan(L.E, SubEdgeIn{cnt}, SubEdgeOut{L.E, L.hw(), t_hoff, t_hw, emap, small + 2, nullptr},
              w.scan, dev_status(g), s);
+    }
+    BP_CUDA(cudaMemcpyAsync(w.host_small, small, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    BP_CUDA(cudaMemcpyAsync(w.host_small + 4, small + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
+    sync(g);
+    check_status(g);
+    const int N = L.N > 0 ? (int)w.host_small[4] : 0;
+    const int E = L.E > 0 ? (int)w.host_small[2] : 0;
+    const int P = L.E > 0 ? (int)w.host_small[3] : 0;
+    cudaStream_t ks = kid->stream;
+    {
+        HandleScope hs(kid);
+        S.clear_view();
+        S.N = N;
+        S.E = E;
+        S.P = P;
+        S.unit_hw = L.unit_hw;
+        kid->l2g.ensure(sizeof(int) * (size_t)std::max(N, 1), ks);
+        S.b_nw.ensure(sizeof(int) * (size_t)std::max(N, 1), ks);
+        S.b_hoff.ensure(sizeof(int) * ((size_t)E + 1), ks);
+        S.b_pins.ensure(sizeof(int) * (size_t)std::max(P, 1), ks);
+        S.b_tsh.ensure(sizeof(int) * ((size_t)P / kTsGran + 2), ks);
+        if (!S.unit_hw) S.b_hw.ensure(sizeof(int) * (size_t)std::max(E, 1), ks);
+        S.b_cmap.ensure(sizeof(int) * (size_t)std::max(N, 1), ks);
+        S.b_match.ensure(sizeof(int) * (size_t)std::max(N, 1), ks);
+        degree_counters(kid, N);  // sized (the counts come from the parent below)
+    }
+    // the kid's new buffers were allocated on its stream: the parent's copies wait for them
+    cudaEvent_t ev = nullptr;
+    BP_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    BP_CUDA(cudaEventRecord(ev, ks));
+    BP_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    cudaEventDestroy(ev);
+    if (N > 0) {
+        BP_CUDA(cudaMemcpyAsync(kid->l2g.p, t_l2g, sizeof(int) * (size_t)N, cudaMemcpyDeviceToDevice, s));
+        BP_CUDA(cudaMemcpyAsync(S.nw(), t_nw, sizeof(int) * (size_t)N, cudaMemcpyDeviceToDevice, s));
+    }
+    int *deg = degree_counters(g, N);  // subgraph degrees, counted while its pins are written
+    if (E > 0) {
+        BP_CUDA(cudaMemcpyAsync(S.hoff(), t_hoff, sizeof(int) * ((size_t)E + 1), cudaMemcpyDeviceToDevice, s));
+        if (t_hw) BP_CUDA(cudaMemcpyAsync(S.b_hw.p, t_hw, sizeof(int) * (size_t)E, cudaMemcpyDeviceToDevice, s));
+        int gw = grid_for((int64_t)(L.E + 31) / 32 * 32);
         k_sub_copy<<<gw, kBlock, 0, s>>>(L.E, L.hoff(), L.pins(), loc, emap, S.hoff(), S.pins(), deg);
+        BP_LAUNCH();
+        k_mark_tiles<<<grid_for(E), kBlock, 0, s>>>(E, S.hoff(), S.tsh());
         BP_LAUNCH();
     } else {
         BP_CUDA(cudaMemsetAsync(S.hoff(), 0, sizeof(int), s));
     }
-    BP_CUDA(cudaMemcpyAsync(w.host_small, small, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (N > 0) BP_CUDA(cudaMemcpyAsync(kid->w.n_a.p, deg, sizeof(int) * (size_t)N, cudaMemcpyDeviceToDevice, s));
+    if (N > 0) {
+        k_weight_sum<<<grid_for(N), kBlock, 0, s>>>(N, t_nw, wsum);
+        BP_LAUNCH();
+    }
+    BP_CUDA(cudaMemcpyAsync(w.host_small, wsum, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     sync(g);
-    check_status(g);
-    S.N = L.N > 0 ? (int)w.host_small[4] : 0;
-    S.E = L.E > 0 ? (int)w.host_small[2] : 0;
-    S.P = L.E > 0 ? (int)w.host_small[3] : 0;
-    build_incidence(g, S);
-    S.b_cmap.ensure(sizeof(int) * (size_t)std::max(S.N, 1), s);
-    S.b_match.ensure(sizeof(int) * (size_t)std::max(S.N, 1), s);
+    unsigned long long W = 0;
+    std::memcpy(&W, w.host_small, sizeof(W));
+    kid->total_node_weight = (int64_t)W;
 }
+
+}  // namespace
+
+// A few host threads that run the bisections of one recursion-tree level at the same time, each
+// on the child workspace of its subgraph.
+struct Lanes {
+    explicit Lanes(int n) {
+        BP_CUDA(cudaGetDevice(&device_));
+        for (int i = 0; i < n; ++i) threads_.emplace_back([this]() { loop(); });
+    }
+    ~Lanes() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto &t : threads_) t.join();
+    }
+    // fn(i) for i in [0, count), spread over the threads; returns when all are done
+    void run(int count, const std::function<void(int)> &fn) {
+        std::unique_lock<std::mutex> lk(mu_);
+        fn_ = &fn;
+        count_ = count;
+        next_ = 0;
+        done_ = 0;
+        ++epoch_;
+        cv_.notify_all();
+        done_cv_.wait(lk, [&]() { return done_ == count_; });
+        fn_ = nullptr;
+    }
+
+   private:
+    void loop() {
+        cudaSetDevice(device_);
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lk(mu_);
+        for (;;) {
+            cv_.wait(lk, [&]() { return stop_ || (epoch_ != seen && next_ < count_); });
+            if (stop_) return;
+            while (next_ < count_) {
+                const int i = next_++;
+                const std::function<void(int)> *fn = fn_;
+                lk.unlock();
+                (*fn)(i);
+                lk.lock();
+                if (++done_ == count_) done_cv_.notify_all();
+            }
+            seen = epoch_;
+        }
+    }
+    int device_ = 0;
+    std::mutex mu_;
+    std::condition_variable cv_, done_cv_;
+    std::vector<std::thread> threads_;
+    const std::function<void(int)> *fn_ = nullptr;
+    int count_ = 0, next_ = 0, done_ = 0;
+    uint64_t epoch_ = 0;
+    bool stop_ = false;
+};
+
+namespace {
 
 // Sec. 3.4: coarsen until `levels` levels exist or the node count stops changing (reading C11),
 // then initial partition + refinement back to level 0.  Coarse levels live in g->lev; the side
@@ -724,28 +838,73 @@ int partition_device(bipart_graph *g, const Params &p, int *d_parts) {
     }
     int *pa = (int *)g->part_a.ensure(sizeof(int) * (size_t)L.N, s);
     BP_CUDA(cudaMemcpyAsync(pa, d_parts, sizeof(int) * (size_t)L.N, cudaMemcpyDeviceToDevice, s));
+    // the subgraphs of each recursion-tree level: extracted one after another on this stream, then
+    // bisected at the same time, each by the child workspace of its place in the tree (its own
+    // stream, level store and launch plan; a result depends only on its subgraph)
     std::vector<std::pair<int32_t, int32_t>> ranges{{0, top.m0}, {top.m0, p.k - top.m0}};
+    size_t kid_base = 0;
     while (!ranges.empty()) {
-        std::vector<std::pair<int32_t, int32_t>> next;
+        std::vector<std::pair<int32_t, int32_t>> next, jobs;
         for (const auto &r : ranges) {
-            const int32_t lo = r.first, m = r.second;
-            if (m < 2) continue;
-            Params q = p;
-            q.m = m;
-            q.m0 = (m + 1) / 2;
-            next.emplace_back(lo, q.m0);
-            next.emplace_back(lo + q.m0, m - q.m0);
-            extract_subgraph(g, pa, lo);
-            Level &S = g->sub0;
-            if (S.N == 0) continue;
-            int64_t Wj = node_weight_sum(g, S);
-            uint8_t *ds = (uint8_t *)g->side_out.ensure((size_t)S.N, s);
-            bisect_body(g, S, q, Wj, ds, nullptr);
-            st = read_bisect_status(g);
-            if (st != BIPART_OK) status = st;
-            k_side_to_part<<<grid_for(S.N), kBlock, 0, s>>>(S.N, ds, g->l2g.as<int>(), lo, lo + q.m0, d_parts);
-            BP_LAUNCH();
+            if (r.second < 2) continue;
+            jobs.push_back(r);
+            const int32_t m0 = (r.second + 1) / 2;
+            next.emplace_back(r.first, m0);
+            next.emplace_back(r.first + m0, r.second - m0);
         }
+        if (jobs.empty()) break;
+        while (g->kids.size() < kid_base + jobs.size()) {
+            cudaStream_t ks = nullptr;
+            BP_CUDA(cudaStreamCreateWithFlags(&ks, cudaStreamNonBlocking));
+            g->kids.emplace_back(graph_new(ks));
+        }
+        for (size_t i = 0; i < jobs.size(); ++i) {
+            bipart_graph *kid = g->kids[kid_base + i].get();
+            if (!kid->kid_stamp_valid || kid->kid_stamp.k != p.k || !same_params(kid->kid_stamp, p)) {
+                // another tree (or another input): the child's subgraph changes, so its plan goes
+                kid->plan.reset();
+                kid->ex.rec_valid = false;
+                kid->kid_stamp = p;
+                kid->kid_stamp_valid = true;
+            }
+            extract_subgraph(g, pa, jobs[i].first, kid);
+        }
+        // every subgraph is in place once the parent's stream gets here
+        BP_CUDA(cudaEventRecord(g->kid_ready, s));
+        std::vector<int> st(jobs.size(), BIPART_OK);
+        std::vector<Fail> errs(jobs.size(), Fail{BIPART_OK, ""});
+        auto job = [&](int i) {
+            bipart_graph *kid = g->kids[kid_base + (size_t)i].get();
+            try {
+                HandleScope hs(kid);
+                const int32_t lo = jobs[(size_t)i].first, m = jobs[(size_t)i].second;
+                Params q = p;
+                q.m = m;
+                q.m0 = (m + 1) / 2;
+                BP_CUDA(cudaStreamWaitEvent(kid->stream, g->kid_ready, 0));
+                build_incidence(kid, kid->L0);
+                if (kid->L0.N > 0) {
+                    uint8_t *ds = (uint8_t *)kid->side_out.ensure((size_t)kid->L0.N, kid->stream);
+                    int nl = 0;
+                    st[(size_t)i] = bisect_top(kid, q, ds, &nl);
+                    k_side_to_part<<<grid_for(kid->L0.N), kBlock, 0, kid->stream>>>(
+                        kid->L0.N, ds, kid->l2g.as<int>(), lo, lo + q.m0, d_parts);
+                    BP_LAUNCH();
+                }
+                BP_CUDA(cudaEventRecord(kid->kid_done, kid->stream));
+            } catch (const Fail &e) {
+                errs[(size_t)i] = e;
+                cudaEventRecord(kid->kid_done, kid->stream);
+            }
+        };
+        if (!g->lanes) g->lanes.reset(new Lanes(kLanes));
+        g->lanes->run((int)jobs.size(), job);
+        for (size_t i = 0; i < jobs.size(); ++i) {
+            BP_CUDA(cudaStreamWaitEvent(s, g->kids[kid_base + i]->kid_done, 0));
+            if (errs[i].code != BIPART_OK) throw errs[i];
+            if (st[i] != BIPART_OK) status = st[i];
+        }
+        kid_base += jobs.size();
         if (!next.empty())
             BP_CUDA(cudaMemcpyAsync(pa, d_parts, sizeof(int) * (size_t)L.N, cudaMemcpyDeviceToDevice, s));
         ranges.swap(next);
@@ -993,10 +1152,20 @@ void validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t 
 }  // namespace bp
 
 bipart_graph::~bipart_graph() {
+    lanes.reset();
+    kids.clear();
     plan.reset();
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (kid_ready) cudaEventDestroy(kid_ready);
+    if (kid_done) cudaEventDestroy(kid_done);
     if (w.host_small) bp::pinned_release(w.host_small);
     w.host_small = nullptr;
+}
+
+void bp::KidDel::operator()(bipart_graph *g) const {
+    cudaStream_t s = g->stream;
+    delete g;
+    if (s) cudaStreamDestroy(s);
 }
 
 namespace bp {
@@ -1010,6 +1179,8 @@ bipart_graph *new_graph(cudaStream_t s) {
     g->w.small.ensure(kSmallBytes, s);
     BP_CUDA(cudaMemsetAsync(g->w.status.p, 0, 64, s));
     g->w.host_small = pinned_take();
+    BP_CUDA(cudaEventCreateWithFlags(&g->kid_ready, cudaEventDisableTiming));
+    BP_CUDA(cudaEventCreateWithFlags(&g->kid_done, cudaEventDisableTiming));
     refine_init();
     coarsen_init();
     return g.release();
@@ -1047,6 +1218,7 @@ void graph_load_host(bipart_graph *g, int32_t N, int32_t E, const int32_t *hoff,
     g->ex.rec_valid = false;
     g->hier.valid = false;
     g->gen++;
+    for (auto &kid : g->kids) kid->kid_stamp_valid = false;  // new input: new subgraphs
     finish_create(g, N, E, E > 0 ? d_hoff : nullptr, d_pins, d_nw, d_hw);
 }
 

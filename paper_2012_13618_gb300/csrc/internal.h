@@ -237,6 +237,14 @@ struct Plan {
 
 }  // namespace bp
 
+namespace bp {
+struct Lanes;
+// Deletes a child workspace, then its stream (the buffers are freed on that stream).
+struct KidDel {
+    void operator()(bipart_graph *g) const;
+};
+}  // namespace bp
+
 struct bipart_graph {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -247,14 +255,23 @@ struct bipart_graph {
     std::vector<std::unique_ptr<bp::Level>> lev;   // coarse levels 1.. of the last bisection
     bp::Hierarchy hier;
     bp::Work w;
-    // k-way workspace: subgraph level 0 and its node map
-    bp::Level sub0;
+    // k-way: part vectors, node map of a subgraph (in a child: its own), bisection output
     bp::Buf part_a, part_b, l2g, side_out;
     bp::Buf in_hoff, in_pins, in_nw, in_hw;   // uploaded input (executor workspaces)
     int64_t total_node_weight = 0;
     bp::Exec ex;
     bp::Plan plan;
     uint64_t gen = 0;            // buffer (re)allocation count of this handle
+    // k-way: one child workspace per subgraph of the recursion tree (own stream, level store and
+    // launch plan), bisected concurrently by a few host threads; events order the streams
+    std::vector<std::unique_ptr<bipart_graph, bp::KidDel>> kids;
+    std::unique_ptr<bp::Lanes> lanes;
+    cudaEvent_t kid_ready = nullptr, kid_done = nullptr;
+    // in a child: the parent's parameters (k included) its subgraph and launch plan belong to; a
+    // child's subgraph is the same for the same parent input and parameters, and only then may
+    // its plan be replayed
+    bp::Params kid_stamp;
+    bool kid_stamp_valid = false;
     ~bipart_graph();
 };
 
