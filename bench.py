@@ -15,6 +15,11 @@ Extra keys:
   profile      every probed kernel group of that pass: launches and ms per step, share, GB/s
   cpu_baseline the CPU oracle (single thread) on one full bisection of the same workload
   gpu_launches kernels the library launched inside the timed region
+  batched      C3 batched solves/s: 4,096 netlist-like instances plus one 2M-node k = 64 instance
+               in one bipart_partition_batch call, end to end from host arrays, against the plain
+               path on the same instances (one at a time) and a sampled oracle check
+  served       C4 serving: 120 Poisson-arrival requests at 2x the plain path's saturated rate,
+               p50 / p99 latency against the plain path on the same trace
 
 --impl reference times the CPU oracle as it stands (the paper ships no code; the oracle is the
 reference arm) on the same workload and prints the same JSON line with "impl": "reference".
@@ -420,8 +425,16 @@ def run_gpu(args):
                                  "share": v[1] / probed_ms if probed_ms else None,
                                  "GBps": (v[2] / (v[1] / 1000) / 1e9) if v[1] else None}
                             for k2, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
-        print(json.dumps(line))
     h.close()
+    # the forms run on the library's host threads, which a Python allocator hook would serialise
+    bp.use_default_allocator()
+    if rank == 0:
+        if ws == 1 and not args.no_forms:
+            # the two other forms of the metric, each with its plain-path comparison on the same
+            # instances and a sampled oracle check
+            line["batched"] = batched_form(bp, args)
+            line["served"] = served_form(bp, args, [args.serve_rate])
+        print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -449,60 +462,85 @@ def run_plain(bp, graphs, params):
     return outs, time.perf_counter() - t0
 
 
+def oracle_sample(graphs, params, parts, n, seed=0, max_pins=3_000_000):
+    """Compares `n` randomly chosen results (instances up to max_pins pins) with the oracle."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    idx = [i for i in range(len(graphs)) if int(graphs[i]["hoff"][-1]) <= max_pins]
+    pick = sorted(rng.choice(idx, size=min(n, len(idx)), replace=False).tolist())
+    ok = True
+    for i in pick:
+        p = params[i]
+        ref, _ = oracle.partition(oracle.Hypergraph.from_dict(graphs[i]), p["k"], p["eps"], p["policy"],
+                                  p["levels"], p["iters"])
+        ok &= bool(np.array_equal(parts[i], ref))
+    return ok, len(pick)
+
+
+def batched_form(bp, args, ws=1, rank=0):
+    """C3: one bipart_partition_batch call over all instances (end to end from host arrays:
+    staging, device work and copies out included), the block shapes tuned first and two untimed
+    calls before the timed ones (buffers, graph capture, worker launch plans); then the plain path
+    on the same instances one at a time, and a sampled oracle check.  Under torchrun every rank
+    takes its longest-processing-time share of the instances; the time is the max over ranks."""
+    from paper_2012_13618_gb300 import shard
+    graphs, params = c3_graphs(args.batch_n, args.big_nodes)
+    total_instances = len(graphs)
+    total_pins = sum(int(g["hoff"][-1]) for g in graphs)
+    if ws > 1:
+        mine = shard.my_share([int(g["hoff"][-1]) for g in graphs], rank, ws)
+        graphs = [graphs[i] for i in mine]
+        params = [params[i] for i in mine]
+    tuned = bp.tune_batch(graphs, params)
+    for _ in range(2):
+        bp.partition_batch(graphs, params, workers=args.workers)
+    times = []
+    for _ in range(args.batch_reps):
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        t0 = time.perf_counter()
+        bparts, bst = bp.partition_batch(graphs, params, workers=args.workers)
+        times.append(shard.max_over_ranks(time.perf_counter() - t0))
+    t_batch = statistics.median(times)
+    if rank != 0:
+        return None
+    plain_n = len(graphs) if args.plain_n <= 0 else min(len(graphs), args.plain_n)
+    pparts, t_plain = run_plain(bp, graphs[:plain_n], params[:plain_n])
+    same = all(np.array_equal(a, b) for a, b in zip(bparts[:plain_n], pparts))
+    oracle_ok, checked = oracle_sample(graphs, params, bparts, args.oracle_n)
+    return {"solves_per_s": total_instances / t_batch, "batch_seconds": t_batch,
+            "batch_seconds_all": times, "pins_per_s": total_pins / t_batch,
+            "config": {"workload": f"{args.batch_n} netlist-like instances, N log-uniform 1k-200k, "
+                                   f"k=2, eps=0.05" + (f", plus one {args.big_nodes}-node instance at k=64"
+                                                       if args.big_nodes else ""),
+                       "instances": total_instances, "pins": total_pins, "workers": args.workers,
+                       "timed": f"median of {len(times)} calls, end to end from host arrays",
+                       "parallelism": f"{ws} rank(s), instances sharded longest-first"},
+            "plain": {"solves_per_s": plain_n / t_plain, "instances": plain_n, "seconds": t_plain,
+                      "how": "the same instances one at a time: create, partition, destroy"},
+            "speedup_vs_plain": (len(graphs) / t_batch) / (plain_n / t_plain) if plain_n == len(graphs) else None,
+            "bit_exact_vs_plain": bool(same), "oracle_checked": checked,
+            "bit_exact_vs_oracle": bool(oracle_ok),
+            "warn_imbalanced": int((bst == 1).sum()),
+            "tuned_shapes": {str(b): list(v) for b, v in tuned.items()}}
+
+
 def run_batch(args):
     import torch
-    import oracle
     import paper_2012_13618_gb300 as bp
-    from paper_2012_13618_gb300 import shard
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    graphs, params = c3_graphs(args.batch_n, args.big_nodes)
-    total_instances = len(graphs)
-    total_pins = sum(int(g["hoff"][-1]) for g in graphs)
-    if ws > 1:
-        # independent instances: every rank takes its own longest-processing-time share
-        mine = shard.my_share([int(g["hoff"][-1]) for g in graphs], rank, ws)
-        graphs = [graphs[i] for i in mine]
-        params = [params[i] for i in mine]
-    pins = sum(int(g["hoff"][-1]) for g in graphs)
-    bp.partition_batch(graphs[:8], params[:8], workers=args.workers)  # warm-up
-    if ws > 1:
-        dist.barrier()
-    t0 = time.perf_counter()
-    bparts, bst = bp.partition_batch(graphs, params, workers=args.workers)
-    t_batch = shard.max_over_ranks(time.perf_counter() - t0)
-    if rank != 0:
-        if ws > 1:
-            dist.destroy_process_group()
-        return
-    plain_n = min(len(graphs), args.plain_n)
-    pparts, t_plain = run_plain(bp, graphs[:plain_n], params[:plain_n])
-    same = all(np.array_equal(a, b) for a, b in zip(bparts[:plain_n], pparts))
-    rng = np.random.default_rng(0)
-    sample = sorted(rng.choice(len(graphs) - (1 if args.big_nodes else 0),
-                               size=min(args.oracle_n, len(graphs)), replace=False).tolist())
-    oracle_ok = all(np.array_equal(bparts[i], oracle.partition(oracle.Hypergraph.from_dict(graphs[i]),
-                                                               params[i]["k"], 0.05, "LDH", 25, 2)[0])
-                    for i in sample)
-    line = {"metric": "batched solves/s", "value": total_instances / t_batch, "unit": "solves/s",
-            "n_gpus": ws, "scaling": "strong", "higher_is_better": True, "dtype": "int32",
-            "data": "synthetic",
-            "config": {"workload": f"{args.batch_n} netlist-like instances, N log-uniform 1k-200k, "
-                                   f"k=2, eps=0.05" + (f", plus one {args.big_nodes}-node instance at k=64"
-                                                       if args.big_nodes else ""),
-                       "instances": total_instances, "pins": total_pins, "workers": args.workers,
-                       "parallelism": f"{ws} rank(s), instances sharded longest-first"},
-            "batch_seconds": t_batch, "pins_per_s": total_pins / t_batch,
-            "plain": {"solves_per_s": plain_n / t_plain, "instances": plain_n,
-                      "seconds": t_plain},
-            "speedup_vs_plain": (total_instances / t_batch) / (plain_n / t_plain),
-            "bit_exact_vs_plain": bool(same), "oracle_checked": len(sample),
-            "bit_exact_vs_oracle": bool(oracle_ok),
-            "warn_imbalanced": int((bst == 1).sum())}
-    print(json.dumps(line))
+    r = batched_form(bp, args, ws, rank)
+    if rank == 0:
+        line = {"metric": "batched solves/s", "value": r["solves_per_s"], "unit": "solves/s",
+                "n_gpus": ws, "scaling": "strong", "higher_is_better": True, "dtype": "int32",
+                "data": "synthetic"}
+        line.update(r)
+        print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -527,26 +565,26 @@ def c4_requests(n, seed=4):
     return reqs, u
 
 
-def run_serve(args):
-    import torch
+def served_form(bp, args, rates, ws=1, rank=0):
+    """C4: Poisson arrivals (rate = a multiple of the plain path's saturated rate) submitted to a
+    bipart_server as they arrive; latency = submit to completion as the server times it.  The
+    plain path runs the same trace one request at a time in arrival order.  Under torchrun every
+    rank serves its longest-processing-time share of the requests with its own server and GPU
+    (no collective); rank 0 reports the max span and the latencies of its own share."""
     import synth
-    import paper_2012_13618_gb300 as bp
-    ws, rank, _ = dist_env()
-    if rank != 0:
-        return  # the serving sweep runs on one GPU (rank 0)
-    torch.cuda.set_device(0)
+    from paper_2012_13618_gb300 import shard
     reqs, _ = c4_requests(args.serve_n)
-    # plain path rate: one request at a time
-    _, t_plain_all = run_plain(bp, [g for g, _ in reqs], [p for _, p in reqs])
+    if ws > 1:
+        mine = shard.my_share([int(g["hoff"][-1]) for g, _ in reqs], rank, ws)
+        reqs = [reqs[i] for i in sorted(mine)]
+    # plain path rate (one request at a time), and every request's result alone
+    alone, t_plain_all = run_plain(bp, [g for g, _ in reqs], [p for _, p in reqs])
     plain_rate = len(reqs) / t_plain_all
-    alone = run_plain(bp, [g for g, _ in reqs], [p for _, p in reqs])[0]
     results = []
-    for mult in args.rates:
+    for mult in rates:
         rate = mult * plain_rate
         gaps = -np.log(1.0 - synth.uniform01(44, int(mult * 1000), len(reqs))) / rate
         arrivals = np.cumsum(gaps)
-        # served: continuous batching
-        lat = []
         with bp.Server(hbm_budget_bytes=args.budget_gb << 30, workers=args.workers) as srv:
             t0 = time.perf_counter()
             tickets = []
@@ -556,13 +594,14 @@ def run_serve(args):
                     time.sleep(ta - now)
                 tickets.append((srv.submit(g, **p), time.perf_counter()))
             exact = True
-            lat, done_t = [], []
+            lat, done_t, served = [], [], []
             for i, (t, ts) in enumerate(tickets):
                 parts, st, qms, rms = srv.wait(t)
                 lat.append(qms + rms)                 # submit -> completion, timed by the server
                 done_t.append(ts + (qms + rms) / 1000.0)
+                served.append(parts)
                 exact &= bool(np.array_equal(parts, alone[i]))
-            span = max(done_t) - t0
+            span = shard.max_over_ranks(max(done_t) - t0)
         # plain path on the same trace: one at a time in arrival order
         t0 = time.perf_counter()
         plat = []
@@ -573,23 +612,45 @@ def run_serve(args):
             with bp.create_from(g, stream=0) as h:
                 h.partition(p["k"], p["eps"], p["policy"], p["levels"], p["iters"])
             plat.append(1000 * (time.perf_counter() - t0 - ta))
-        pspan = time.perf_counter() - t0
-        results.append({"rate_x_plain": mult, "offered_per_s": rate,
-                        "served": {"solves_per_s": len(reqs) / span,
+        pspan = shard.max_over_ranks(time.perf_counter() - t0)
+        results.append({"rate_x_plain": mult, "offered_per_s": ws * rate,
+                        "served": {"solves_per_s": ws * len(reqs) / span,
                                    "p50_ms": float(np.percentile(lat, 50)),
                                    "p99_ms": float(np.percentile(lat, 99))},
-                        "plain": {"solves_per_s": len(reqs) / pspan,
+                        "plain": {"solves_per_s": ws * len(reqs) / pspan,
                                   "p50_ms": float(np.percentile(plat, 50)),
                                   "p99_ms": float(np.percentile(plat, 99))},
                         "bit_exact_vs_alone": exact})
-    best = max(results, key=lambda r: r["served"]["solves_per_s"])
-    line = {"metric": "serving p50/p99 ms", "value": best["served"]["p99_ms"], "unit": "ms",
-            "higher_is_better": False, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"{len(reqs)} Poisson-arrival requests, netlist or row-net, "
+    if rank != 0:
+        return None
+    oracle_ok, checked = oracle_sample([g for g, _ in reqs], [p for _, p in reqs], served, args.oracle_n // 2,
+                                       seed=1)
+    return {"config": {"workload": f"{args.serve_n} Poisson-arrival requests, netlist or row-net, "
                                    "10k-2M pins log-uniform, k in {2,4,16}, eps=0.05",
-                       "workers": args.workers, "hbm_budget_gb": args.budget_gb},
-            "plain_solves_per_s": plain_rate, "sweep": results}
-    print(json.dumps(line))
+                       "workers": args.workers, "hbm_budget_gb": args.budget_gb,
+                       "parallelism": f"{ws} rank(s), requests sharded longest-first, one server each"},
+            "plain_solves_per_s": plain_rate, "sweep": results,
+            "oracle_checked": checked, "bit_exact_vs_oracle": bool(oracle_ok)}
+
+
+def run_serve(args):
+    import torch
+    import paper_2012_13618_gb300 as bp
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    r = served_form(bp, args, args.rates, ws, rank)
+    if rank == 0:
+        best = max(r["sweep"], key=lambda x: x["served"]["solves_per_s"])
+        line = {"metric": "serving p50/p99 ms", "value": best["served"]["p99_ms"], "unit": "ms",
+                "higher_is_better": False, "n_gpus": ws, "dtype": "int32", "data": "synthetic"}
+        line.update(r)
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def run_once(replay=False):
@@ -627,8 +688,14 @@ def main():
     ap.add_argument("--workers", type=int, default=16)
     ap.add_argument("--batch-n", type=int, default=4096)
     ap.add_argument("--big-nodes", type=int, default=2_000_000)
-    ap.add_argument("--plain-n", type=int, default=256)
+    ap.add_argument("--plain-n", type=int, default=0,
+                    help="instances the plain comparison runs (0: all of them)")
+    ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--oracle-n", type=int, default=16)
+    ap.add_argument("--no-forms", action="store_true",
+                    help="leave the batched and served blocks out of the default line")
+    ap.add_argument("--serve-rate", type=float, default=2.0,
+                    help="offered rate of the default line's served block, x the plain rate")
     ap.add_argument("--serve-n", type=int, default=120)
     ap.add_argument("--rates", type=float, nargs="+", default=[0.25, 0.5, 1, 2, 4])
     ap.add_argument("--budget-gb", type=int, default=64)

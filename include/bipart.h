@@ -47,7 +47,10 @@ typedef struct bipart_graph *bipart_handle;
 /* Optional device allocator used for every device buffer the library owns (for example the
  * caching allocator of a framework).  alloc returns NULL on failure; both receive the handle's
  * stream.  With no allocator set the library uses cudaMallocAsync / cudaFreeAsync on that stream.
- * Applies to allocations made after the call; pass NULLs to restore the default. */
+ * Applies to allocations made after the call; pass NULLs to restore the default.  A buffer is
+ * always freed by the allocator that made it.  The batch call, the server and nested k-way
+ * allocate from several host threads at once: the functions must be thread-safe, and an
+ * allocator that serialises its callers (a callback into an interpreter lock) serialises them. */
 typedef void *(*bipart_alloc_fn)(void *ctx, size_t bytes, void *stream);
 typedef void (*bipart_free_fn)(void *ctx, void *ptr, size_t bytes, void *stream);
 int bipart_set_allocator(bipart_alloc_fn alloc, bipart_free_fn free_fn, void *ctx);
@@ -154,18 +157,49 @@ int bipart_partition_ex(bipart_handle h, const bipart_params *params, int32_t *o
 int bipart_partition_device_ex(bipart_handle h, const bipart_params *params, int32_t *d_out_parts);
 
 /* Partitions n independent hypergraphs concurrently on the current GPU (each as bipart_partition
- * would, Sec. 3 / Algorithm 6): `workers` host threads (<= 0: min(16, n)) each own a private
- * workspace and CUDA stream and take instances largest first.  out_parts[i] (HOST, num_nodes
- * entries) receives instance i's parts, statuses[i] (may be NULL) its return code.  The result of
- * every instance equals what bipart_partition returns for it alone.  Returns OK when no instance
- * failed, else the first failing instance's error (see bipart_last_error). */
+ * would, Sec. 3 / Algorithm 6).  Instances of up to 2^18 nodes and 2^24 pins with k <= 1024 and
+ * levels < 64 (no BIPART_FLAG_MERGE_PARALLEL) run in persistent launches, one thread block per
+ * instance doing its whole partition, nested k-way included; they are grouped in size buckets by
+ * pin count, each bucket launched with the block shape recorded for it by
+ * bipart_batch_tune (or a default), all buckets in one CUDA graph that is replayed while the
+ * batch keeps the same shape.  The other instances (and any whose level store outgrows its
+ * block's arena) go to `workers` host threads (<= 0: min(16, n)), each owning a private workspace
+ * and CUDA stream, largest first.  out_parts[i] (HOST, num_nodes entries) receives instance i's
+ * parts, statuses[i] (may be NULL) its return code.  The result of every instance equals what
+ * bipart_partition returns for it alone.  Staging buffers (pinned host and device), arenas, the
+ * graph and the worker pool (whose workspaces keep their launch plans; a request goes preferably
+ * to the worker that last ran one of the same sizes and parameters) are kept between calls;
+ * bipart_batch_release frees them.  Returns OK when no instance failed, else the first failing
+ * instance's error (see bipart_last_error). */
 int bipart_partition_batch(int32_t n, const bipart_instance *instances, const bipart_params *params,
                            int32_t *const *out_parts, int32_t *statuses, int32_t workers);
 
-/* Serving: a pool of `workers` threads (<= 0: 8) that partitions requests as they arrive.  A
- * request is admitted once its estimated device working set fits, next to the running requests,
- * in hbm_budget_bytes (0 = unlimited); requests larger than the whole budget complete at once with
- * BIPART_ERR_OOM.  Results are identical to bipart_partition on the same input. */
+/* Tunes the persistent batch launches on this batch: every candidate block shape (threads x
+ * blocks per SM: 256x1, 256x2, 512x1, 1024x1) runs each size bucket's instances alone (bucket
+ * edges at 16Ki, 128Ki and 1Mi pins), timed by CUDA events (best of two), and the fastest is kept
+ * for the bucket, in this process and in a JSON file keyed by the device name and SM count
+ * ($BIPART_TUNE_CACHE, else $XDG_CACHE_HOME/bipart/batch_tune.json, else
+ * $HOME/.cache/bipart/batch_tune.json; a file that cannot be written is skipped).  Only the
+ * instances the persistent path takes are timed; results are discarded.  chosen (may be NULL;
+ * 8 entries) receives per bucket its threads and blocks per SM, 0 0 for a bucket with no
+ * instance.  Returns OK or the first validation error. */
+int bipart_batch_tune(int32_t n, const bipart_instance *instances, const bipart_params *params,
+                      int32_t *chosen);
+
+/* Frees the staging buffers, arenas, graph and worker pool the batch call keeps between calls,
+ * then returns the unused memory of the library's device memory pool (where buffers freed by the
+ * library stay reserved for its next allocations) to the driver. */
+void bipart_batch_release(void);
+
+/* Serving: a pool of `workers` threads (<= 0: 8) that partitions requests as they arrive, each
+ * request's k-way subgraphs one after another on its worker's stream.  A request is admitted once
+ * its estimated device working set fits, next to the running requests, in hbm_budget_bytes
+ * (0 = unlimited); requests larger than the whole budget complete at once with BIPART_ERR_OOM.
+ * Under a budget a worker frees its workspace after each request, so the device memory the
+ * server's workspaces hold stays within the budget (the estimate bounds what a request
+ * allocates); without one, workspaces keep their memory and launch plans, and a request goes
+ * preferably to the worker that last ran one of the same sizes and parameters.  Results are
+ * identical to bipart_partition on the same input. */
 typedef struct bipart_server_s *bipart_server;
 int bipart_server_create(size_t hbm_budget_bytes, int32_t workers, bipart_server *out);
 /* Queues a request; the caller keeps instance arrays and out_parts (HOST) alive until waited. */

@@ -75,6 +75,8 @@ SYMBOLS = {
     "bipart_last_error": (ctypes.c_char_p, []),
     "bipart_cut_noalloc": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp, _vp, _i32, _vp, _vp]),
     "bipart_partition_batch": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _i32]),
+    "bipart_batch_tune": (ctypes.c_int, [_i32, _vp, _vp, _vp]),
+    "bipart_batch_release": (None, []),
     "bipart_server_create": (ctypes.c_int, [ctypes.c_size_t, _i32, ctypes.POINTER(_vp)]),
     "bipart_server_submit": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64)]),
     "bipart_server_wait": (ctypes.c_int, [_vp, ctypes.c_int64, _i32, _p32,
@@ -124,7 +126,9 @@ def _check(code):
 
 
 def use_torch_allocator():
-    """Routes the library's device allocations through PyTorch's caching allocator."""
+    """Routes the library's device allocations through PyTorch's caching allocator.  The hooks
+    are Python callbacks: each allocation takes the interpreter lock, which serialises the
+    library's own host threads (batch, server, nested k-way) while it is set."""
     global _alloc_cb, _free_cb
     import torch
 
@@ -143,6 +147,12 @@ def use_torch_allocator():
 
     _alloc_cb, _free_cb = _ALLOC(_alloc), _FREE(_free)
     _check(load().bipart_set_allocator(_alloc_cb, _free_cb, None))
+
+
+def use_default_allocator():
+    """Restores the library's own allocator (cudaMallocAsync on the handle's stream).  Buffers
+    made by another allocator are still returned to it."""
+    _check(load().bipart_set_allocator(_ALLOC(), _FREE(), None))
 
 
 def kernel_launches() -> int:
@@ -341,26 +351,47 @@ def _params(k=2, eps=0.1, policy="LDH", levels=25, iters=2, adaptive_eps=False,
                   (FLAG_MERGE_PARALLEL if merge_parallel else 0))
 
 
-def partition_batch(graphs, params, workers=0):
-    """bipart_partition_batch: graphs = list of dicts (N, hoff, pins, nw, hw), params = list of
-    dicts (k, eps, policy, levels, iters) or one dict for all.  Returns (parts list, statuses)."""
+def _batch_args(graphs, params):
     n = len(graphs)
     if isinstance(params, dict):
         params = [params] * n
-    keep, insts, outs = [], (Instance * max(n, 1))(), []
+    keep, insts = [], (Instance * max(n, 1))()
     pars = (Params * max(n, 1))()
     for i, g in enumerate(graphs):
         inst, arrs = _instance(g)
         keep.append(arrs)
         insts[i] = inst
         pars[i] = _params(**params[i])
-        outs.append(np.empty(max(int(g["N"]), 1), np.int32))
+    return n, keep, insts, pars
+
+
+def partition_batch(graphs, params, workers=0):
+    """bipart_partition_batch: graphs = list of dicts (N, hoff, pins, nw, hw), params = list of
+    dicts (k, eps, policy, levels, iters) or one dict for all.  Returns (parts list, statuses)."""
+    n, keep, insts, pars = _batch_args(graphs, params)
+    outs = [np.empty(max(int(g["N"]), 1), np.int32) for g in graphs]
     out_ptrs = (ctypes.c_void_p * max(n, 1))(*[o.ctypes.data for o in outs])
     st = np.zeros(max(n, 1), np.int32)
     _check(load().bipart_partition_batch(n, ctypes.cast(insts, ctypes.c_void_p),
                                          ctypes.cast(pars, ctypes.c_void_p),
                                          ctypes.cast(out_ptrs, ctypes.c_void_p), _ptr(st), int(workers)))
     return [o[: int(g["N"])] for o, g in zip(outs, graphs)], st[:n]
+
+
+def tune_batch(graphs, params):
+    """bipart_batch_tune: times every block shape on each size bucket of this batch and records
+    the fastest (in the JSON tuning cache).  Returns {bucket: (threads, blocks per SM)} for the
+    buckets the batch has instances in."""
+    n, keep, insts, pars = _batch_args(graphs, params)
+    chosen = np.zeros(8, np.int32)
+    _check(load().bipart_batch_tune(n, ctypes.cast(insts, ctypes.c_void_p), ctypes.cast(pars, ctypes.c_void_p),
+                                    _ptr(chosen)))
+    return {b: (int(chosen[2 * b]), int(chosen[2 * b + 1])) for b in range(4) if chosen[2 * b]}
+
+
+def batch_release():
+    """bipart_batch_release: frees the buffers the batch path keeps between calls."""
+    load().bipart_batch_release()
 
 
 class Server:

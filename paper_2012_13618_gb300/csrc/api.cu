@@ -28,13 +28,22 @@ namespace bp {
 
 namespace {
 thread_local std::string g_last_error;
+std::mutex g_alloc_mu;  // guards the three below (set by bipart_set_allocator)
 bipart_alloc_fn g_alloc = nullptr;
 bipart_free_fn g_free = nullptr;
 void *g_alloc_ctx = nullptr;
 constexpr int kBlock = 256;
 constexpr size_t kSmallBytes = 64 * 1024;
 
-constexpr int kLanes = 8;  // host threads that bisect the subgraphs of a recursion-tree level
+// Host threads that bisect the subgraphs of a recursion-tree level: 8, or $BIPART_KWAY_LANES.
+int default_lanes() {
+    static const int n = []() {
+        const char *e = std::getenv("BIPART_KWAY_LANES");
+        const int v = e ? std::atoi(e) : 0;
+        return v >= 1 && v <= 64 ? v : 8;
+    }();
+    return n;
+}
 
 inline int grid_for(int64_t n, int per_block = kBlock, int cap = 152 * 16) {
     int64_t b = (n + per_block - 1) / per_block;
@@ -59,20 +68,69 @@ void note_realloc() {
     if (tl_graph) tl_graph->gen++;
 }
 
-void *dev_alloc(size_t bytes, cudaStream_t s) {
+void *dev_alloc(size_t bytes, cudaStream_t s, AllocTag *tag) {
     if (tl_capturing) return nullptr;  // no allocation may happen inside a captured plan
-    if (g_alloc) return g_alloc(g_alloc_ctx, bytes, (void *)s);
+    bipart_alloc_fn alloc;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        alloc = g_alloc;
+        tag->free_fn = g_free;
+        tag->ctx = g_alloc_ctx;
+    }
+    if (alloc) return alloc(tag->ctx, bytes, (void *)s);
+    tag->free_fn = nullptr;
     void *p = nullptr;
-    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaMemPool_t pool = lib_pool();
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
     return p;
 }
 
-void dev_free(void *p, size_t bytes, cudaStream_t s) {
+// The library's own stream-ordered memory pool on the current device: freed memory stays
+// reserved in it for the next allocation (no release threshold), instead of going back to the
+// driver at every synchronisation as the device's default pool does.  Null if it cannot be made
+// (the default pool is used then).
+cudaMemPool_t lib_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    static bool tried[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!tried[dev]) {
+        tried[dev] = true;
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            pools[dev] = pool;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    return pools[dev];
+}
+
+void lib_pool_trim() {
+    if (cudaMemPool_t pool = lib_pool()) {
+        cudaDeviceSynchronize();
+        cudaMemPoolTrimTo(pool, 0);
+    }
+}
+
+void dev_free(void *p, size_t bytes, cudaStream_t s, const AllocTag &tag) {
     if (!p) return;
-    if (g_free) g_free(g_alloc_ctx, p, bytes, (void *)s);
+    if (tag.free_fn) tag.free_fn(tag.ctx, p, bytes, (void *)s);
     else cudaFreeAsync(p, s);
 }
 
@@ -554,62 +612,6 @@ void extract_subgraph(bipart_graph *g, const int *d_part, int j, bipart_graph *k
 
 }  // namespace
 
-// A few host threads that run the bisections of one recursion-tree level at the same time, each
-// on the child workspace of its subgraph.
-struct Lanes {
-    explicit Lanes(int n) {
-        BP_CUDA(cudaGetDevice(&device_));
-        for (int i = 0; i < n; ++i) threads_.emplace_back([this]() { loop(); });
-    }
-    ~Lanes() {
-        {
-            std::lock_guard<std::mutex> lk(mu_);
-            stop_ = true;
-        }
-        cv_.notify_all();
-        for (auto &t : threads_) t.join();
-    }
-    // fn(i) for i in [0, count), spread over the threads; returns when all are done
-    void run(int count, const std::function<void(int)> &fn) {
-        std::unique_lock<std::mutex> lk(mu_);
-        fn_ = &fn;
-        count_ = count;
-        next_ = 0;
-        done_ = 0;
-        ++epoch_;
-        cv_.notify_all();
-        done_cv_.wait(lk, [&]() { return done_ == count_; });
-        fn_ = nullptr;
-    }
-
-   private:
-    void loop() {
-        cudaSetDevice(device_);
-        uint64_t seen = 0;
-        std::unique_lock<std::mutex> lk(mu_);
-        for (;;) {
-            cv_.wait(lk, [&]() { return stop_ || (epoch_ != seen && next_ < count_); });
-            if (stop_) return;
-            while (next_ < count_) {
-                const int i = next_++;
-                const std::function<void(int)> *fn = fn_;
-                lk.unlock();
-                (*fn)(i);
-                lk.lock();
-                if (++done_ == count_) done_cv_.notify_all();
-            }
-            seen = epoch_;
-        }
-    }
-    int device_ = 0;
-    std::mutex mu_;
-    std::condition_variable cv_, done_cv_;
-    std::vector<std::thread> threads_;
-    const std::function<void(int)> *fn_ = nullptr;
-    int count_ = 0, next_ = 0, done_ = 0;
-    uint64_t epoch_ = 0;
-    bool stop_ = false;
-};
 
 namespace {
 
@@ -836,11 +838,24 @@ int partition_device(bipart_graph *g, const Params &p, int *d_parts) {
         sync(g);
         return status;
     }
+    const int lanes = g->kid_lanes > 0 ? g->kid_lanes : default_lanes();
+    if (lanes == 1 && g->lean) {
+        // the coarse levels of the top bisection are not needed any more: their memory goes before
+        // the subgraphs take theirs (and the top bisection's plan, which points into them)
+        sync(g);
+        g->plan.reset();
+        g->ex.rec_valid = false;
+        g->lev.clear();
+        g->gen++;
+    }
     int *pa = (int *)g->part_a.ensure(sizeof(int) * (size_t)L.N, s);
     BP_CUDA(cudaMemcpyAsync(pa, d_parts, sizeof(int) * (size_t)L.N, cudaMemcpyDeviceToDevice, s));
-    // the subgraphs of each recursion-tree level: extracted one after another on this stream, then
+    // The subgraphs of each recursion-tree level: extracted one after another on this stream, then
     // bisected at the same time, each by the child workspace of its place in the tree (its own
-    // stream, level store and launch plan; a result depends only on its subgraph)
+    // stream, level store and launch plan; a result depends only on its subgraph).  With one lane
+    // a single child workspace bisects every subgraph in turn on this stream (the memory of one
+    // subgraph at a time; no launch plans are kept for them).
+    const bool single = lanes == 1;
     std::vector<std::pair<int32_t, int32_t>> ranges{{0, top.m0}, {top.m0, p.k - top.m0}};
     size_t kid_base = 0;
     while (!ranges.empty()) {
@@ -853,14 +868,20 @@ int partition_device(bipart_graph *g, const Params &p, int *d_parts) {
             next.emplace_back(r.first + m0, r.second - m0);
         }
         if (jobs.empty()) break;
-        while (g->kids.size() < kid_base + jobs.size()) {
+        while (g->kids.size() < (single ? 1 : kid_base + jobs.size())) {
+            if (single) {  // one after another on this handle's stream
+                g->kids.emplace_back(graph_new(s));
+                g->kids.back()->kid_own_stream = false;
+                continue;
+            }
             cudaStream_t ks = nullptr;
             BP_CUDA(cudaStreamCreateWithFlags(&ks, cudaStreamNonBlocking));
             g->kids.emplace_back(graph_new(ks));
         }
-        for (size_t i = 0; i < jobs.size(); ++i) {
-            bipart_graph *kid = g->kids[kid_base + i].get();
-            if (!kid->kid_stamp_valid || kid->kid_stamp.k != p.k || !same_params(kid->kid_stamp, p)) {
+        auto kid_of = [&](size_t i) { return g->kids[single ? 0 : kid_base + i].get(); };
+        auto extract = [&](size_t i) {
+            bipart_graph *kid = kid_of(i);
+            if (single || !kid->kid_stamp_valid || kid->kid_stamp.k != p.k || !same_params(kid->kid_stamp, p)) {
                 // another tree (or another input): the child's subgraph changes, so its plan goes
                 kid->plan.reset();
                 kid->ex.rec_valid = false;
@@ -868,13 +889,15 @@ int partition_device(bipart_graph *g, const Params &p, int *d_parts) {
                 kid->kid_stamp_valid = true;
             }
             extract_subgraph(g, pa, jobs[i].first, kid);
-        }
-        // every subgraph is in place once the parent's stream gets here
-        BP_CUDA(cudaEventRecord(g->kid_ready, s));
+            // the subgraph is in place once the parent's stream gets here
+            BP_CUDA(cudaEventRecord(g->kid_ready, s));
+        };
+        if (!single)
+            for (size_t i = 0; i < jobs.size(); ++i) extract(i);
         std::vector<int> st(jobs.size(), BIPART_OK);
         std::vector<Fail> errs(jobs.size(), Fail{BIPART_OK, ""});
         auto job = [&](int i) {
-            bipart_graph *kid = g->kids[kid_base + (size_t)i].get();
+            bipart_graph *kid = kid_of((size_t)i);
             try {
                 HandleScope hs(kid);
                 const int32_t lo = jobs[(size_t)i].first, m = jobs[(size_t)i].second;
@@ -897,10 +920,20 @@ int partition_device(bipart_graph *g, const Params &p, int *d_parts) {
                 cudaEventRecord(kid->kid_done, kid->stream);
             }
         };
-        if (!g->lanes) g->lanes.reset(new Lanes(kLanes));
-        g->lanes->run((int)jobs.size(), job);
+        if (single) {
+            for (int i = 0; i < (int)jobs.size(); ++i) {
+                extract((size_t)i);
+                job(i);
+                if (errs[(size_t)i].code != BIPART_OK) throw errs[(size_t)i];
+            }
+        } else if (jobs.size() == 1) {
+            job(0);
+        } else {
+            if (!g->lanes) g->lanes.reset(new Lanes(lanes));
+            g->lanes->run((int)jobs.size(), job);
+        }
         for (size_t i = 0; i < jobs.size(); ++i) {
-            BP_CUDA(cudaStreamWaitEvent(s, g->kids[kid_base + i]->kid_done, 0));
+            BP_CUDA(cudaStreamWaitEvent(s, kid_of(i)->kid_done, 0));
             if (errs[i].code != BIPART_OK) throw errs[i];
             if (st[i] != BIPART_OK) status = st[i];
         }
@@ -1163,7 +1196,7 @@ bipart_graph::~bipart_graph() {
 }
 
 void bp::KidDel::operator()(bipart_graph *g) const {
-    cudaStream_t s = g->stream;
+    cudaStream_t s = g->kid_own_stream ? g->stream : nullptr;
     delete g;
     if (s) cudaStreamDestroy(s);
 }
@@ -1265,6 +1298,7 @@ int bipart_set_allocator(bipart_alloc_fn alloc, bipart_free_fn free_fn, void *ct
         set_error("alloc and free must both be set or both be NULL");
         return BIPART_ERR_INVALID_ARG;
     }
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
     g_alloc = alloc;
     g_free = free_fn;
     g_alloc_ctx = ctx;

@@ -19,6 +19,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <memory>
 #include <mutex>
@@ -45,10 +46,36 @@ struct Job {
     bool done = false;
     std::string error;
     Clock::time_point t_submit, t_start, t_end;
+    uint64_t sig = 0;  // shape of the input and parameters (sizes only)
+    int pref = -1;     // the worker that last ran this shape, whose launch plans fit it
 };
 
+// Shape of a request: what a worker's captured launch plans depend on besides the data.
+uint64_t job_sig(const bipart_instance &in, const bipart_params &p) {
+    const int64_t P = (in.num_hedges > 0 && in.hedge_offsets) ? in.hedge_offsets[in.num_hedges] : 0;
+    uint64_t h = 0x9e3779b97f4a7c15ull;
+    auto mix = [&](uint64_t v) {
+        h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    };
+    mix((uint64_t)in.num_nodes);
+    mix((uint64_t)in.num_hedges);
+    mix((uint64_t)P);
+    mix((uint64_t)(in.node_weights != nullptr) | ((uint64_t)(in.hedge_weights != nullptr) << 1));
+    mix((uint64_t)p.k);
+    uint64_t eb;
+    std::memcpy(&eb, &p.epsilon, sizeof(eb));
+    mix(eb);
+    mix((uint64_t)p.policy);
+    mix((uint64_t)p.levels);
+    mix((uint64_t)p.refine_iters);
+    mix((uint64_t)p.flags);
+    return h | 1;
+}
+
 // Estimated device working set of one job: level store over all levels (bounded by a few times
-// level 0 for the shapes of interest), scratch and the input copy.
+// level 0 for the shapes of interest), scratch and the input copy.  Checked against the bytes a
+// request's workspace actually allocates (counted through the allocator hooks) on netlist and
+// row-net requests with k in {2, 4, 16}.
 size_t estimate_bytes(const bipart_instance &in) {
     const size_t N = (size_t)std::max(in.num_nodes, 0), E = (size_t)std::max(in.num_hedges, 0);
     const size_t P = (in.num_hedges > 0 && in.hedge_offsets) ? (size_t)std::max(in.hedge_offsets[in.num_hedges], 0) : 0;
@@ -57,11 +84,15 @@ size_t estimate_bytes(const bipart_instance &in) {
 
 class Pool {
    public:
-    Pool(int workers, size_t budget) : budget_(budget) {
+    // kid_lanes: the workspaces' host threads for the subgraphs of a k-way tree level (1: one
+    // after another on the worker's stream; 0: the library default)
+    Pool(int workers, size_t budget, int kid_lanes) : budget_(budget), kid_lanes_(kid_lanes) {
         BP_CUDA(cudaGetDevice(&device_));
         if (workers < 1) workers = 1;
-        for (int i = 0; i < workers; ++i) threads_.emplace_back([this]() { run(); });
+        busy_.assign((size_t)workers, 0);
+        for (int i = 0; i < workers; ++i) threads_.emplace_back([this, i]() { run(i); });
     }
+    int workers() const { return (int)threads_.size(); }
 
     ~Pool() {
         {
@@ -79,9 +110,12 @@ class Pool {
         j->params = p;
         j->out = out;
         j->bytes = estimate_bytes(inst);
+        j->sig = job_sig(inst, p);
         j->t_submit = Clock::now();
         std::lock_guard<std::mutex> lk(mu_);
         j->ticket = ++next_ticket_;
+        auto last = last_.find(j->sig);
+        if (last != last_.end()) j->pref = last->second;
         if (budget_ && j->bytes > budget_) {
             j->status = BIPART_ERR_OOM;
             j->error = "request exceeds the whole HBM budget";
@@ -99,7 +133,9 @@ class Pool {
         } else {
             queue_.push_back(j);
         }
-        cv_.notify_one();
+        // a job meant for one worker must reach that worker, not just any sleeping one
+        if (j->pref >= 0) cv_.notify_all();
+        else cv_.notify_one();
         return j->ticket;
     }
 
@@ -123,13 +159,15 @@ class Pool {
     }
 
    private:
-    void run() {
+    void run(int me) {
         cudaSetDevice(device_);
         cudaStream_t s = nullptr;
         std::unique_ptr<bipart_graph> ws;
         try {
             BP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
             ws.reset(graph_new(s));
+            ws->kid_lanes = kid_lanes_;
+            ws->lean = budget_ != 0;
         } catch (const Fail &) {
             ws.reset();
         }
@@ -137,12 +175,15 @@ class Pool {
             std::shared_ptr<Job> j;
             {
                 std::unique_lock<std::mutex> lk(mu_);
-                cv_.wait(lk, [&]() { return (stop_ && queue_.empty()) || admissible() != queue_.end(); });
+                cv_.wait(lk, [&]() { return (stop_ && queue_.empty()) || admissible(me) != queue_.end(); });
                 if (stop_ && queue_.empty()) break;
-                auto it = admissible();
+                auto it = admissible(me);
                 j = *it;
                 queue_.erase(it);
                 in_flight_ += j->bytes;
+                busy_[(size_t)me] = 1;
+                // jobs left waiting for this worker may now go to any other
+                if (!queue_.empty()) cv_.notify_all();
             }
             j->t_start = Clock::now();
             if (!ws) {
@@ -165,10 +206,24 @@ class Pool {
                 }
             }
             j->t_end = Clock::now();
+            if (budget_ && ws) {
+                // under a budget a worker holds device memory only while it runs a request: the
+                // workspace is rebuilt empty before the request's share is given back
+                try {
+                    ws.reset();
+                    ws.reset(graph_new(s));
+                    ws->kid_lanes = kid_lanes_;
+                    ws->lean = true;
+                } catch (const Fail &) {
+                    ws.reset();
+                }
+            }
             {
                 std::lock_guard<std::mutex> lk(mu_);
                 in_flight_ -= j->bytes;
                 j->done = true;
+                busy_[(size_t)me] = 0;
+                if (j->status >= 0) last_[j->sig] = me;
             }
             done_cv_.notify_all();
             cv_.notify_all();  // memory was released: more requests may fit now
@@ -177,17 +232,21 @@ class Pool {
         if (s) cudaStreamDestroy(s);
     }
 
-    // First queued job that fits next to the running ones (always the head when nothing runs).
-    std::deque<std::shared_ptr<Job>>::iterator admissible() {
-        if (queue_.empty()) return queue_.end();
-        if (!budget_ || in_flight_ == 0) return queue_.begin();
-        for (auto it = queue_.begin(); it != queue_.end(); ++it)
-            if (in_flight_ + (*it)->bytes <= budget_) return it;
+    // First queued job that fits next to the running ones (always the head when nothing runs)
+    // and that worker `me` may take: a job whose shape another worker ran last waits for that
+    // worker (which can replay its launch plans) unless that worker is busy.
+    std::deque<std::shared_ptr<Job>>::iterator admissible(int me) {
+        for (auto it = queue_.begin(); it != queue_.end(); ++it) {
+            const int pref = (*it)->pref;
+            if (pref >= 0 && pref != me && pref < (int)busy_.size() && !busy_[(size_t)pref]) continue;
+            if (!budget_ || in_flight_ == 0 || in_flight_ + (*it)->bytes <= budget_) return it;
+        }
         return queue_.end();
     }
 
     int device_ = 0;
     size_t budget_ = 0;
+    int kid_lanes_ = 0;
     size_t in_flight_ = 0;
     bool stop_ = false;
     int64_t next_ticket_ = 0;
@@ -195,8 +254,23 @@ class Pool {
     std::condition_variable cv_, done_cv_;
     std::deque<std::shared_ptr<Job>> queue_;
     std::unordered_map<int64_t, std::shared_ptr<Job>> jobs_;
+    std::vector<char> busy_;
+    std::unordered_map<uint64_t, int> last_;  // shape -> worker that ran it last
     std::vector<std::thread> threads_;
 };
+
+// The batch call's worker pool, kept between calls (its workspaces keep their level stores and
+// launch plans); replaced when a call asks for another worker count.  Never destroyed at exit.
+std::mutex g_batch_pool_mu;
+std::shared_ptr<Pool> *g_batch_pool = new std::shared_ptr<Pool>();
+
+std::shared_ptr<Pool> batch_pool(int workers) {
+    std::lock_guard<std::mutex> lk(g_batch_pool_mu);
+    // a batch's pool jobs are the few instances too large for a block: their k-way subgraphs
+    // run concurrently
+    if (!*g_batch_pool || (*g_batch_pool)->workers() != workers) g_batch_pool->reset(new Pool(workers, 0, 0));
+    return *g_batch_pool;
+}
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
     return std::chrono::duration<double, std::milli>(b - a).count();
@@ -211,9 +285,78 @@ struct bipart_server_s {
 
 using namespace bp;
 
-// Batch: k = 2 instances of up to 2^18 nodes run in the persistent block kernel on this thread;
-// the others (and any instance the block path defers) go to the worker pool, which runs
-// concurrently.
+namespace bp {
+namespace {
+
+// The persistent block path takes an instance when it fits a block (block_eligible) and does not
+// ask for parallel-net merging, which only the grid path implements.
+bool block_takes(const bipart_instance &in, const bipart_params &p) {
+    const int64_t P = in.num_hedges > 0 ? in.hedge_offsets[in.num_hedges] : 0;
+    return in.num_nodes > 0 && block_eligible(in.num_nodes, in.num_hedges, P, p.k, p.levels) &&
+           !(p.flags & BIPART_FLAG_MERGE_PARALLEL);
+}
+
+// Descriptors and array pointers of the instances idx[] for the block path.
+struct BlockSet {
+    std::vector<BInst> bi;
+    std::vector<const int32_t *> ho, pi, nw, hw;
+};
+
+BlockSet block_set(const std::vector<int32_t> &idx, const bipart_instance *instances,
+                   const bipart_params *params) {
+    // instances without hyperedges still need an offsets array of one zero
+    static const int32_t zero = 0;
+    BlockSet b;
+    const size_t n = idx.size();
+    b.bi.resize(n);
+    b.ho.resize(n);
+    b.pi.resize(n);
+    b.nw.resize(n);
+    b.hw.resize(n);
+    for (size_t j = 0; j < n; ++j) {
+        const bipart_instance &in = instances[idx[j]];
+        const bipart_params &p = params[idx[j]];
+        BInst &d = b.bi[j];
+        d.N = in.num_nodes;
+        d.E = in.num_hedges;
+        d.P = in.num_hedges > 0 ? in.hedge_offsets[in.num_hedges] : 0;
+        d.policy = p.policy;
+        d.levels = p.levels;
+        d.iters = p.refine_iters;
+        d.k = p.k;
+        d.e6 = make_params(p.k, p.epsilon, p.policy, p.levels, p.refine_iters, p.flags).e6;
+        d.status = 0;
+        b.ho[j] = in.num_hedges > 0 ? in.hedge_offsets : &zero;
+        b.pi[j] = in.hedge_pins;
+        b.nw[j] = in.node_weights;
+        b.hw[j] = in.hedge_weights;
+    }
+    return b;
+}
+
+// Validates every instance; st[i] / err[i] record a failure.
+void validate_all(int32_t n, const bipart_instance *instances, const bipart_params *params,
+                  std::vector<int32_t> &st, std::vector<std::string> &err) {
+    for (int32_t i = 0; i < n; ++i) {
+        const bipart_instance &in = instances[i];
+        const bipart_params &p = params[i];
+        try {
+            make_params(p.k, p.epsilon, p.policy, p.levels, p.refine_iters, p.flags);  // validates
+            validate_host_csr(in.num_nodes, in.num_hedges, in.hedge_offsets, in.hedge_pins,
+                              in.node_weights, in.hedge_weights);
+        } catch (const Fail &e) {
+            st[i] = e.code;
+            err[i] = e.msg;
+        }
+    }
+}
+
+}  // namespace
+}  // namespace bp
+
+// Batch: the instances the persistent block path takes run there (size buckets, one CUDA graph)
+// on this thread; the others (and any instance the block path defers) go to the worker pool,
+// which runs concurrently.
 extern "C" int bipart_partition_batch(int32_t n, const bipart_instance *instances,
                                       const bipart_params *params, int32_t *const *out_parts,
                                       int32_t *statuses, int32_t workers) {
@@ -226,88 +369,37 @@ extern "C" int bipart_partition_batch(int32_t n, const bipart_instance *instance
         if (workers <= 0) workers = std::min<int32_t>(16, std::max<int32_t>(n, 1));
         std::vector<int32_t> st(n, BIPART_OK);
         std::vector<std::string> err(n);
+        validate_all(n, instances, params, st, err);
         std::vector<int32_t> blk, rest;
         for (int32_t i = 0; i < n; ++i) {
-            const bipart_instance &in = instances[i];
-            const bipart_params &p = params[i];
-            try {
-                make_params(p.k, p.epsilon, p.policy, p.levels, p.refine_iters, p.flags);  // validates
-                validate_host_csr(in.num_nodes, in.num_hedges, in.hedge_offsets, in.hedge_pins,
-                                  in.node_weights, in.hedge_weights);
-            } catch (const Fail &e) {
-                st[i] = e.code;
-                err[i] = e.msg;
-                continue;
-            }
-            const int64_t P = in.num_hedges > 0 ? in.hedge_offsets[in.num_hedges] : 0;
-            // the persistent block path runs the paper's contraction only (no parallel-net merging)
-            if (block_eligible(in.num_nodes, in.num_hedges, P, p.k) && in.num_nodes > 0 &&
-                !(p.flags & BIPART_FLAG_MERGE_PARALLEL))
-                blk.push_back(i);
+            if (st[i] != BIPART_OK) continue;
+            if (block_takes(instances[i], params[i])) blk.push_back(i);
             else rest.push_back(i);
         }
-        auto by_size = [&](std::vector<int32_t> &v) {
-            std::stable_sort(v.begin(), v.end(), [&](int32_t a, int32_t b) {
-                return estimate_bytes(instances[a]) > estimate_bytes(instances[b]);
-            });
-        };
-        by_size(blk);
-        by_size(rest);
-        // the worker pool exists only if some valid instance needs it (an all-invalid batch
+        std::stable_sort(rest.begin(), rest.end(), [&](int32_t a, int32_t b) {
+            return estimate_bytes(instances[a]) > estimate_bytes(instances[b]);
+        });
+        // the worker pool is made only if some valid instance needs it (an all-invalid batch
         // reports its validation errors without touching the GPU)
-        std::unique_ptr<Pool> pool_owner;
+        std::shared_ptr<Pool> pool_owner;
         auto pool_ref = [&]() -> Pool & {
-            if (!pool_owner) pool_owner.reset(new Pool(workers, 0));
+            if (!pool_owner) pool_owner = batch_pool(workers);
             return *pool_owner;
         };
         std::vector<int64_t> tickets(n, 0);
-        for (int32_t i : rest)
-            if (st[i] == BIPART_OK) tickets[i] = pool_ref().submit(instances[i], params[i], out_parts[i], false);
+        for (int32_t i : rest) tickets[i] = pool_ref().submit(instances[i], params[i], out_parts[i], false);
         if (!blk.empty()) {
-            std::vector<BInst> bi(blk.size());
-            std::vector<const int32_t *> ho(blk.size()), pi(blk.size()), nw(blk.size()), hw(blk.size());
-            for (size_t j = 0; j < blk.size(); ++j) {
-                const bipart_instance &in = instances[blk[j]];
-                const bipart_params &p = params[blk[j]];
-                BInst &b = bi[j];
-                b.N = in.num_nodes;
-                b.E = in.num_hedges;
-                b.P = in.num_hedges > 0 ? in.hedge_offsets[in.num_hedges] : 0;
-                b.policy = p.policy;
-                b.levels = p.levels;
-                b.iters = p.refine_iters;
-                int64_t W = 0;
-                for (int32_t v = 0; v < in.num_nodes; ++v) W += in.node_weights ? in.node_weights[v] : 1;
-                b.limit = balance_limit(W, 1, 2, make_params(p.k, p.epsilon, p.policy, p.levels,
-                                                              p.refine_iters, p.flags).e6);
-                b.status = 0;
-                ho[j] = in.num_hedges > 0 ? in.hedge_offsets : nullptr;
-                pi[j] = in.hedge_pins;
-                nw[j] = in.node_weights;
-                hw[j] = in.hedge_weights;
-            }
-            // instances without hyperedges still need an offsets array of one zero
-            static const int32_t zero = 0;
-            for (size_t j = 0; j < blk.size(); ++j)
-                if (!ho[j]) ho[j] = &zero;
-            cudaStream_t s = nullptr;
-            BP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-            std::vector<std::vector<uint8_t>> sides;
-            try {
-                run_block_batch(bi, ho, pi, nw, hw, sides, s);
-            } catch (...) {
-                cudaStreamDestroy(s);
-                throw;
-            }
-            cudaStreamDestroy(s);
+            BlockSet b = block_set(blk, instances, params);
+            std::vector<int32_t *> outs(blk.size());
+            for (size_t j = 0; j < blk.size(); ++j) outs[j] = out_parts[blk[j]];
+            run_block_batch(b.bi, b.ho, b.pi, b.nw, b.hw, outs);
             for (size_t j = 0; j < blk.size(); ++j) {
                 const int32_t i = blk[j];
-                if (bi[j].status == 2) {  // did not fit the block arena: single-instance path
+                if (b.bi[j].status == 2) {  // did not fit the block arena: single-instance path
                     tickets[i] = pool_ref().submit(instances[i], params[i], out_parts[i], false);
                     continue;
                 }
-                st[i] = bi[j].status ? BIPART_WARN_IMBALANCED : BIPART_OK;
-                for (int32_t v = 0; v < instances[i].num_nodes; ++v) out_parts[i][v] = sides[j][v];
+                st[i] = b.bi[j].status ? BIPART_WARN_IMBALANCED : BIPART_OK;
             }
         }
         for (int32_t i = 0; i < n; ++i) {
@@ -335,6 +427,53 @@ extern "C" int bipart_partition_batch(int32_t n, const bipart_instance *instance
     }
 }
 
+extern "C" int bipart_batch_tune(int32_t n, const bipart_instance *instances, const bipart_params *params,
+                                 int32_t *chosen) {
+    if (n < 0 || (n > 0 && (!instances || !params))) {
+        set_error("bipart_batch_tune: bad arguments");
+        return BIPART_ERR_INVALID_ARG;
+    }
+    try {
+        std::vector<int32_t> st(n, BIPART_OK);
+        std::vector<std::string> err(n);
+        validate_all(n, instances, params, st, err);
+        std::vector<int32_t> blk;
+        for (int32_t i = 0; i < n; ++i) {
+            if (st[i] != BIPART_OK) {
+                set_error("instance " + std::to_string(i) + ": " + err[i]);
+                return st[i];
+            }
+            if (block_takes(instances[i], params[i])) blk.push_back(i);
+        }
+        if (chosen)
+            for (int q = 0; q < 8; ++q) chosen[q] = 0;
+        if (blk.empty()) return BIPART_OK;
+        BlockSet b = block_set(blk, instances, params);
+        tune_block_batch(b.bi, b.ho, b.pi, b.nw, b.hw, chosen);
+        return BIPART_OK;
+    } catch (const Fail &e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (...) {
+        set_error("bipart_batch_tune: unexpected exception");
+        return BIPART_ERR_CUDA;
+    }
+}
+
+extern "C" void bipart_batch_release(void) {
+    try {
+        release_block_batch();
+        std::shared_ptr<Pool> old;
+        {
+            std::lock_guard<std::mutex> lk(g_batch_pool_mu);
+            old.swap(*g_batch_pool);
+        }
+        old.reset();
+        lib_pool_trim();
+    } catch (...) {
+    }
+}
+
 extern "C" int bipart_server_create(size_t hbm_budget_bytes, int32_t workers, bipart_server *out) {
     if (!out) {
         set_error("out is NULL");
@@ -343,7 +482,8 @@ extern "C" int bipart_server_create(size_t hbm_budget_bytes, int32_t workers, bi
     *out = nullptr;
     try {
         std::unique_ptr<bipart_server_s> s(new bipart_server_s);
-        s->pool.reset(new Pool(workers > 0 ? workers : 8, hbm_budget_bytes));
+        // requests run concurrently across workers; each one's k-way subgraphs one after another
+        s->pool.reset(new Pool(workers > 0 ? workers : 8, hbm_budget_bytes, 1));
         *out = s.release();
         return BIPART_OK;
     } catch (const Fail &e) {

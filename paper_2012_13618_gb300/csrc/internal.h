@@ -5,8 +5,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <condition_variable>
+#include <functional>
 #include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "bipart.h"
@@ -15,8 +19,17 @@
 namespace bp {
 
 // ---------------------------------------------------------------------------------- memory
-void *dev_alloc(size_t bytes, cudaStream_t s);
-void dev_free(void *p, size_t bytes, cudaStream_t s);
+// How a buffer was allocated: the free function and context in force at that time (null: the
+// library's own cudaMallocAsync), so that a buffer is always returned to the allocator that
+// made it, whatever bipart_set_allocator was called with in between.
+struct AllocTag {
+    bipart_free_fn free_fn = nullptr;
+    void *ctx = nullptr;
+};
+void *dev_alloc(size_t bytes, cudaStream_t s, AllocTag *tag);
+cudaMemPool_t lib_pool();  // the library's own memory pool on the current device (or null)
+void lib_pool_trim();      // returns the pool's unused memory to the driver
+void dev_free(void *p, size_t bytes, cudaStream_t s, const AllocTag &tag);
 void zero_fill(void *p, size_t bytes, cudaStream_t s);
 uint32_t *pinned_take();            // a pinned 4 KB host block (pooled)
 void pinned_release(uint32_t *p);
@@ -29,12 +42,13 @@ struct Buf {
     void *p = nullptr;
     size_t cap = 0;
     cudaStream_t s = nullptr;
+    AllocTag tag;
     Buf() = default;
     Buf(const Buf &) = delete;
     Buf &operator=(const Buf &) = delete;
     ~Buf() { release(); }
     void release() {
-        if (p) dev_free(p, cap, s);
+        if (p) dev_free(p, cap, s, tag);
         p = nullptr;
         cap = 0;
     }
@@ -44,7 +58,7 @@ struct Buf {
             release();
             s = stream;
             size_t c = bytes + bytes / 8 + 256;
-            p = dev_alloc(c, stream);
+            p = dev_alloc(c, stream, &tag);
             if (!p) throw Fail{BIPART_ERR_OOM, "device allocation of " + std::to_string(c) + " bytes failed"};
             cap = c;
             note_realloc();
@@ -238,7 +252,64 @@ struct Plan {
 }  // namespace bp
 
 namespace bp {
-struct Lanes;
+// A few host threads that run fn(i) for i in [0, count) and return when all are done: the
+// bisections of one recursion-tree level (each on the child workspace of its subgraph), and the
+// host-side staging of a batch.
+struct Lanes {
+    explicit Lanes(int n) {
+        BP_CUDA(cudaGetDevice(&device_));
+        for (int i = 0; i < n; ++i) threads_.emplace_back([this]() { loop(); });
+    }
+    ~Lanes() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto &t : threads_) t.join();
+    }
+    // fn(i) for i in [0, count), spread over the threads; returns when all are done
+    void run(int count, const std::function<void(int)> &fn) {
+        std::unique_lock<std::mutex> lk(mu_);
+        fn_ = &fn;
+        count_ = count;
+        next_ = 0;
+        done_ = 0;
+        ++epoch_;
+        cv_.notify_all();
+        done_cv_.wait(lk, [&]() { return done_ == count_; });
+        fn_ = nullptr;
+    }
+
+   private:
+    void loop() {
+        cudaSetDevice(device_);
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lk(mu_);
+        for (;;) {
+            cv_.wait(lk, [&]() { return stop_ || (epoch_ != seen && next_ < count_); });
+            if (stop_) return;
+            while (next_ < count_) {
+                const int i = next_++;
+                const std::function<void(int)> *fn = fn_;
+                lk.unlock();
+                (*fn)(i);
+                lk.lock();
+                if (++done_ == count_) done_cv_.notify_all();
+            }
+            seen = epoch_;
+        }
+    }
+    int device_ = 0;
+    std::mutex mu_;
+    std::condition_variable cv_, done_cv_;
+    std::vector<std::thread> threads_;
+    const std::function<void(int)> *fn_ = nullptr;
+    int count_ = 0, next_ = 0, done_ = 0;
+    uint64_t epoch_ = 0;
+    bool stop_ = false;
+};
+
 // Deletes a child workspace, then its stream (the buffers are freed on that stream).
 struct KidDel {
     void operator()(bipart_graph *g) const;
@@ -272,6 +343,15 @@ struct bipart_graph {
     // its plan be replayed
     bp::Params kid_stamp;
     bool kid_stamp_valid = false;
+    // host threads that bisect the subgraphs of a tree level (0: the default, 8 or
+    // $BIPART_KWAY_LANES); with 1 the subgraphs are bisected one after another on this handle's
+    // stream, which the children then share (workers of the batch and serving pools, whose
+    // concurrency is across requests)
+    int kid_lanes = 0;
+    bool kid_own_stream = true;  // in a child: its stream was made for it
+    // free what a request no longer needs as soon as it can (workers of a server under an HBM
+    // budget): with one lane, the top bisection's coarse levels before the subgraphs'
+    bool lean = false;
     ~bipart_graph();
 };
 
@@ -357,16 +437,24 @@ struct ProfScope {
 // One instance of a batch run by the persistent block kernel (device-side descriptor).
 struct BInst {
     int N, E, P;
-    int policy, levels, iters;
-    long long limit;
-    long long hoff, pins, nw, hw, out;  // offsets into the concatenated arrays (hw < 0: unit)
+    int policy, levels, iters, k;
+    long long e6;                        // imbalance of every bisection, millionths
+    long long hoff, pins, nw, hw, out;  // offsets into the concatenated arrays (nw, hw < 0: unit)
     int status;                          // 0 ok, 1 imbalanced, 2 deferred (did not fit)
 };
-bool block_eligible(int64_t N, int64_t E, int64_t P, int k);
+bool block_eligible(int64_t N, int64_t E, int64_t P, int k, int levels);
+// Runs a batch with the persistent block kernels (instances in size buckets, each bucket with the
+// block shape its tuning chose, all buckets in one CUDA graph); writes every instance's parts to
+// outs[i] and its status to inst[i].status (2: did not fit a block's arena, the caller runs it).
 void run_block_batch(std::vector<BInst> &inst, const std::vector<const int32_t *> &hoff,
                      const std::vector<const int32_t *> &pins, const std::vector<const int32_t *> &nw,
-                     const std::vector<const int32_t *> &hw, std::vector<std::vector<uint8_t>> &sides,
-                     cudaStream_t s);
+                     const std::vector<const int32_t *> &hw, const std::vector<int32_t *> &outs);
+// Times every candidate block shape on each size bucket of the batch and records the fastest
+// (in this process and in the JSON tuning cache); chosen: 2 ints per bucket (threads, per SM).
+void tune_block_batch(std::vector<BInst> &inst, const std::vector<const int32_t *> &hoff,
+                      const std::vector<const int32_t *> &pins, const std::vector<const int32_t *> &nw,
+                      const std::vector<const int32_t *> &hw, int32_t *chosen);
+void release_block_batch();
 
 // ------------------------------------------------------------------------- validation (api.cu)
 void validate_params(int32_t k, double eps, int32_t policy, int32_t levels, int32_t iters);

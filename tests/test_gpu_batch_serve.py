@@ -204,3 +204,89 @@ def test_batch_general_k_matches_single():
         ref, rst = oracle.partition(oracle.Hypergraph.from_dict(g), params[i]["k"], 0.05, "LDH", 25, 2,
                                     adaptive=params[i]["adaptive_eps"])
         assert np.array_equal(parts[i], ref) and sts[i] == rst
+
+
+def _kway_cases(seed, n):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        kind = i % 4
+        if kind == 0:
+            out.append(synth.c3_instance(900 + i, N=int(rng.integers(800, 20000))))
+        elif kind == 1:
+            r = int(rng.integers(400, 5000))
+            out.append(synth.rownet(r, r, seed=300 + i))
+        elif kind == 2:
+            out.append(synth.uniform(int(rng.integers(100, 4000)), int(rng.integers(100, 4000)), 2, 9,
+                                     seed=400 + i))
+        else:  # weighted nodes and hyperedges, duplicate and single pins
+            N, E = int(rng.integers(200, 3000)), int(rng.integers(100, 3000))
+            deg = rng.integers(0, 12, size=E)
+            hoff = np.zeros(E + 1, np.int32)
+            hoff[1:] = np.cumsum(deg)
+            out.append(dict(N=N, E=E, hoff=hoff, pins=rng.integers(0, N, size=int(hoff[-1])).astype(np.int32),
+                            nw=rng.integers(1, 9, size=N).astype(np.int32),
+                            hw=rng.integers(1, 50, size=E).astype(np.int32)))
+    return out
+
+
+def test_block_path_kway_matches_oracle_in_one_launch_per_bucket():
+    # k > 2 instances run their nested bisections inside the persistent blocks: the batch makes
+    # at most one launch per size bucket (no worker-pool fallback), and every result equals the
+    # oracle's Algorithm 6
+    import paper_2012_13618_gb300 as bp
+    graphs = _kway_cases(21, 36)
+    ks = [3, 4, 5, 8, 16, 64, 7, 2, 1, 33, 12, 6]
+    pols = ["LDH", "HDH", "LWD", "HWD", "RAND"]
+    params = [dict(k=ks[i % len(ks)], eps=[0.05, 0.1, 0.0][i % 3], policy=pols[i % 5], levels=[25, 4, 25][i % 3],
+                   iters=[2, 1, 3][i % 3], adaptive_eps=bool(i % 2)) for i in range(len(graphs))]
+    before = bp.kernel_launches()
+    parts, st = bp.partition_batch(graphs, params, workers=2)
+    assert bp.kernel_launches() - before <= 4
+    for i, g in enumerate(graphs):
+        p = params[i]
+        ref, rst = oracle.partition(oracle.Hypergraph.from_dict(g), p["k"], p["eps"], p["policy"], p["levels"],
+                                    p["iters"], adaptive=p["adaptive_eps"])
+        assert np.array_equal(parts[i], ref), (i, p)
+        assert st[i] == rst, (i, p)
+
+
+def test_block_graph_replayed_on_new_data_of_the_same_shape():
+    # a second batch with the same sizes and parameters replays the captured graph; its inputs are
+    # new (pins permuted within every hyperedge's node set), so a stale copy would show
+    import paper_2012_13618_gb300 as bp
+    rng = np.random.default_rng(33)
+    a = [synth.uniform(int(n), int(n) + 50, 2, 7, seed=500 + i) for i, n in enumerate(rng.integers(500, 6000, 10))]
+    b = []
+    for i, g in enumerate(a):
+        perm = np.random.default_rng(600 + i).permutation(g["N"]).astype(np.int32)
+        b.append(dict(g, pins=perm[g["pins"]]))
+    params = [dict(k=[2, 4, 8][i % 3], eps=0.05, policy="LDH", levels=25, iters=2) for i in range(10)]
+    for graphs in (a, b, a):
+        before = bp.kernel_launches()
+        parts, st = bp.partition_batch(graphs, params, workers=2)
+        launched = bp.kernel_launches() - before
+        for i, g in enumerate(graphs):
+            ref, rst = oracle.partition(oracle.Hypergraph.from_dict(g), params[i]["k"], 0.05, "LDH", 25, 2)
+            assert np.array_equal(parts[i], ref) and st[i] == rst, i
+    assert launched == 0  # the third call replayed the graph captured by the first
+
+
+def test_tuner_writes_cache_and_results_stay_exact(tmp_path, monkeypatch):
+    import json
+    import paper_2012_13618_gb300 as bp
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("BIPART_TUNE_CACHE", str(cache))
+    graphs = _kway_cases(44, 16) + [synth.c3_instance(970, N=30000)]
+    params = [dict(k=[2, 4][i % 2], eps=0.05, policy="LDH", levels=25, iters=2) for i in range(len(graphs))]
+    chosen = bp.tune_batch(graphs, params)
+    assert chosen and all(t in (256, 512, 1024) and m in (1, 2) for t, m in chosen.values())
+    doc = json.loads(cache.read_text())
+    assert doc["version"] == 1 and len(doc["devices"]) == 1
+    (entry,) = doc["devices"].values()
+    stored = {int(b): tuple(v) for b, v in entry.items()}
+    assert all(stored[b] == v for b, v in chosen.items())
+    parts, st = bp.partition_batch(graphs, params, workers=2)
+    for i, g in enumerate(graphs):
+        ref, rst = oracle.partition(oracle.Hypergraph.from_dict(g), params[i]["k"], 0.05, "LDH", 25, 2)
+        assert np.array_equal(parts[i], ref) and st[i] == rst, i
