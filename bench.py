@@ -8,6 +8,7 @@ call is inside the timed region (CUDA events on the handle's stream).
 Extra keys:
   e2e          the same metric through bipart_create + bipart_partition + destroy with HOST
                buffers (pinned), host<->device copies inside the timed region
+  whole_bisection  all kernels' algorithmic bytes per step over the step time, against the same peak
   roofline     the dominant kernel (largest device time in a second pass of the timed steps with
                CUDA-event probes around every launch): algorithmic bytes / probed duration per
                launch against the measured HBM copy bandwidth, its share of all probed time, and
@@ -398,6 +399,15 @@ def run_gpu(args):
                         "mean launch by algorithmic bytes (null unless that record matches the "
                         "kernel's current sources)"}
 
+    # whole bisection: every probed kernel's algorithmic bytes of one step over the unprobed step
+    whole = None
+    if prof:
+        alg_step = sum(v[2] for v in prof.values()) / args.steps
+        whole = {"algorithmic_bytes_per_step": alg_step, "achieved": alg_step / (ms_max / 1000.0) / 1e9,
+                 "peak": hbm, "unit": "GB/s", "frac": alg_step / (ms_max / 1000.0) / 1e9 / hbm,
+                 "note": "the sum of every kernel's algorithmic bytes per step (profiled pass) over "
+                         "ms_per_step of the unprobed timed steps"}
+
     if rank == 0:
         cpu, exact = None, None
         if ws == 1 and not args.no_cpu_baseline:
@@ -420,6 +430,7 @@ def run_gpu(args):
                 "gpu_launches": int(launches),
                 "graph_replay": bool(replayed),
                 "roofline": roof,
+                "whole_bisection": whole,
                 "cpu_baseline": cpu,
                 "profile": {k2: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps,
                                  "share": v[1] / probed_ms if probed_ms else None,
@@ -573,18 +584,23 @@ def served_form(bp, args, rates, ws=1, rank=0):
     (no collective); rank 0 reports the max span and the latencies of its own share."""
     import synth
     from paper_2012_13618_gb300 import shard
-    reqs, _ = c4_requests(args.serve_n)
+    all_reqs, _ = c4_requests(args.serve_n)
+    costs = [int(g["hoff"][-1]) for g, _ in all_reqs]
+    reqs = all_reqs
     if ws > 1:
-        mine = shard.my_share([int(g["hoff"][-1]) for g, _ in reqs], rank, ws)
-        reqs = [reqs[i] for i in sorted(mine)]
+        reqs = [all_reqs[i] for i in shard.serve_share(costs, list(range(len(costs))), rank, ws)[0]]
     # plain path rate (one request at a time), and every request's result alone
     alone, t_plain_all = run_plain(bp, [g for g, _ in reqs], [p for _, p in reqs])
-    plain_rate = len(reqs) / t_plain_all
+    plain_rate = shard.min_over_ranks(len(reqs) / t_plain_all)
     results = []
     for mult in rates:
+        # one Poisson trace over all requests at ws x the rate; every rank serves its share of it
         rate = mult * plain_rate
-        gaps = -np.log(1.0 - synth.uniform01(44, int(mult * 1000), len(reqs))) / rate
-        arrivals = np.cumsum(gaps)
+        gaps = -np.log(1.0 - synth.uniform01(44, int(mult * 1000), len(all_reqs))) / (ws * rate)
+        arrivals_all = np.cumsum(gaps)
+        arrivals = arrivals_all
+        if ws > 1:
+            arrivals = np.asarray(shard.serve_share(costs, arrivals_all.tolist(), rank, ws)[1])
         with bp.Server(hbm_budget_bytes=args.budget_gb << 30, workers=args.workers) as srv:
             t0 = time.perf_counter()
             tickets = []

@@ -1099,10 +1099,13 @@ constexpr int64_t kHostBlock = 4096;
 // Runs body(lo, hi) over [0, n) in chunks of kHostChunk on the host pool and returns the
 // smallest index any chunk reported (body returns the first failing index of its range, or -1),
 // which is what a sequential pass would report.
+// Set on a host-pool thread that validates one of many instances: its checks stay on that thread.
+thread_local bool tl_serial_checks = false;
+
 template <class Body>
 int64_t parallel_first(int64_t n, Body body) {
     const int64_t chunks = (n + kHostChunk - 1) / kHostChunk;
-    if (chunks <= 1) return n > 0 ? body(0, n) : -1;
+    if (chunks <= 1 || tl_serial_checks) return n > 0 ? body(0, n) : -1;
     std::vector<int64_t> first((size_t)chunks, -1);
     HostPool::get().run((int)chunks, [&](int c) {
         first[(size_t)c] = body((int64_t)c * kHostChunk, std::min(n, ((int64_t)c + 1) * kHostChunk));
@@ -1139,6 +1142,8 @@ std::pair<int64_t, int64_t> weight_check(const int32_t *w, int64_t n) {
         first[(size_t)c] = first_bad(lo, hi, [&](int64_t i) { return (uint32_t)w[i] - 1u >= 0x7fffffffu; });
     };
     if (chunks == 1) body(0);
+    else if (tl_serial_checks)
+        for (int c = 0; c < (int)chunks; ++c) body(c);
     else HostPool::get().run((int)chunks, body);
     int64_t total = 0, bad = -1;
     for (size_t c = 0; c < (size_t)chunks; ++c) {
@@ -1180,6 +1185,31 @@ void validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t 
     }
     if (sn >= (int64_t(1) << 31) || se >= (int64_t(1) << 31))
         throw Fail{BIPART_ERR_INVALID_CSR, "weight sum must stay below 2^31"};
+}
+
+void validate_host_many(int32_t n, const bipart_instance *in, int32_t *codes, std::string *errs) {
+    auto one = [&](int i) {
+        const bipart_instance &x = in[i];
+        try {
+            validate_host_csr(x.num_nodes, x.num_hedges, x.hedge_offsets, x.hedge_pins, x.node_weights,
+                              x.hedge_weights);
+        } catch (const Fail &e) {
+            codes[i] = e.code;
+            errs[i] = e.msg;
+        }
+    };
+    if (n <= 1) {
+        for (int i = 0; i < n; ++i) one(i);
+        return;
+    }
+    // instances spread over the host pool, each checked on one thread (tasks strided so that
+    // every one gets a similar mix of sizes)
+    const int tasks = std::min<int>(n, 64);
+    HostPool::get().run(tasks, [&](int t) {
+        tl_serial_checks = true;
+        for (int i = t; i < n; i += tasks) one(i);
+        tl_serial_checks = false;
+    });
 }
 
 }  // namespace bp

@@ -337,13 +337,12 @@ BlockSet block_set(const std::vector<int32_t> &idx, const bipart_instance *insta
 // Validates every instance; st[i] / err[i] record a failure.
 void validate_all(int32_t n, const bipart_instance *instances, const bipart_params *params,
                   std::vector<int32_t> &st, std::vector<std::string> &err) {
+    validate_host_many(n, instances, st.data(), err.data());
     for (int32_t i = 0; i < n; ++i) {
-        const bipart_instance &in = instances[i];
+        if (st[i] != BIPART_OK) continue;
         const bipart_params &p = params[i];
         try {
             make_params(p.k, p.epsilon, p.policy, p.levels, p.refine_iters, p.flags);  // validates
-            validate_host_csr(in.num_nodes, in.num_hedges, in.hedge_offsets, in.hedge_pins,
-                              in.node_weights, in.hedge_weights);
         } catch (const Fail &e) {
             st[i] = e.code;
             err[i] = e.msg;

@@ -460,6 +460,9 @@ void release_block_batch();
 void validate_params(int32_t k, double eps, int32_t policy, int32_t levels, int32_t iters);
 void validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t *pins,
                        const int32_t *nw, const int32_t *hw);
+// validate_host_csr on every instance, spread over the host threads; a failure's code and text
+// go to codes[i] / errs[i] (left untouched for a valid instance).
+void validate_host_many(int32_t n, const bipart_instance *in, int32_t *codes, std::string *errs);
 
 // ------------------------------------------------------------------------- executor (api.cu)
 bipart_graph *graph_new(cudaStream_t s);

@@ -30,6 +30,19 @@ def my_share(costs, rank: int, world: int):
     return assign(costs, world)[rank]
 
 
+def serve_share(costs, arrivals, rank: int, world: int):
+    """The served form's share of a request trace: this rank's longest-processing-time share of
+    the requests, in arrival order, with their arrival times.  Every rank serves its share with its
+    own server on its own GPU; nothing is exchanged while serving."""
+    mine = sorted(my_share(costs, rank, world), key=lambda i: (arrivals[i], i))
+    return mine, [arrivals[i] for i in mine]
+
+
+def min_over_ranks(value: float) -> float:
+    """Minimum of a float over the default process group (identity without one)."""
+    return -max_over_ranks(-float(value))
+
+
 def max_over_ranks(value: float) -> float:
     """Maximum of a float over the default process group (identity without one)."""
     import torch
