@@ -175,7 +175,8 @@ int bipart_partition_batch(int32_t n, const bipart_instance *instances, const bi
                            int32_t *const *out_parts, int32_t *statuses, int32_t workers);
 
 /* Tunes the persistent batch launches on this batch: every candidate block shape (threads x
- * blocks per SM: 256x1, 256x2, 512x1, 1024x1) runs each size bucket's instances alone (bucket
+ * blocks per SM: 256x1, 256x2, 256x4, 512x1, 512x2, 1024x1) runs each size bucket's instances
+ * alone (bucket
  * edges at 16Ki, 128Ki and 1Mi pins), timed by CUDA events (best of two), and the fastest is kept
  * for the bucket, in this process and in a JSON file keyed by the device name and SM count
  * ($BIPART_TUNE_CACHE, else $XDG_CACHE_HOME/bipart/batch_tune.json, else
@@ -210,6 +211,13 @@ int bipart_server_submit(bipart_server server, const bipart_instance *instance,
  * start and from start to completion (any may be NULL).  Each ticket can be waited for once. */
 int bipart_server_wait(bipart_server server, int64_t ticket, int32_t timeout_ms, int32_t *status,
                        double *queue_ms, double *run_ms);
+/* Micro-batches: once at least 8 waiting requests fit the persistent block path (see
+ * bipart_partition_batch) and are small (pins x ceil(log2 k) <= 262,144: a batch completes as a
+ * whole, so its longest member sets every member's latency), a free worker takes up to 1024 of
+ * them, in queue order, as one batch (when its device memory fits the budget next to the running
+ * requests); one batch runs at a time.  *batches / *batched_requests (may be NULL) = how many batches ran and the requests they
+ * held so far. */
+int bipart_server_stats(bipart_server server, int64_t *batches, int64_t *batched_requests);
 /* Finishes all queued requests, then stops the workers. */
 void bipart_server_destroy(bipart_server server);
 

@@ -83,6 +83,7 @@ SYMBOLS = {
                                           ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]),
     "bipart_server_destroy": (None, [_vp]),
+    "bipart_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "bipart_kernel_launches": (ctypes.c_int64, []),
     "bipart_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "bipart_profile_select": (ctypes.c_int, [ctypes.c_char_p]),
@@ -421,6 +422,12 @@ class Server:
                                          ctypes.byref(qms), ctypes.byref(rms)))
         inst, arrs, par, out, n = self._live.pop(ticket)
         return out[:n], st.value, qms.value, rms.value
+
+    def stats(self):
+        """(micro-batches run, requests they held) so far."""
+        b, r = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().bipart_server_stats(self._h, ctypes.byref(b), ctypes.byref(r)))
+        return int(b.value), int(r.value)
 
     def close(self):
         if self._h:

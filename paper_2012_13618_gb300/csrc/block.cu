@@ -33,528 +33,17 @@
 #include <string>
 #include <vector>
 
-#include "coarsen_dev.cuh"
-#include "common.cuh"
-#include "internal.h"
-#include "refine_dev.cuh"
-#include "scan.cuh"
+#include "block_dev.cuh"
 
 namespace bp {
 
-namespace {
-
-constexpr int kMaxLev = 64;               // levels a block keeps (instances asking more: grid path)
-constexpr int kMaxStack = 64;             // pending part ranges of the nested k-way recursion
-constexpr int kBlockMaxK = 1024;          // largest k run inside a block
-constexpr size_t kSmemBytes = 32 * 1024;  // union: bitmap window / gain histogram / sort keys
-
-}  // namespace
-
-struct BArgs {
-    BInst *inst;
-    const int *order;  // this bucket's instances, largest first
-    int n;
-    int *next;         // this bucket's queue head
-    const int *hoff, *pins, *nw, *hw;
-    int *parts;
-    char *arena;
-    size_t arena_bytes;
-    uint32_t *status;
-};
-
-struct DLevel {
-    int N, E, P;
-    int *hoff, *pins, *hw, *nw, *noff, *nadj, *cmap, *match;
-};
-
-namespace {
-
-// Bump allocator over the block's arena; every thread computes the same pointers.
-struct Arena {
-    char *base;
-    size_t cap, top;
-    bool overflow;
-    template <class T>
-    __device__ T *take(size_t count) {
-        size_t bytes = (sizeof(T) * (count ? count : 1) + 255) & ~size_t(255);
-        if (top + bytes > cap) {
-            overflow = true;
-            return reinterpret_cast<T *>(base);  // never dereferenced: the instance is abandoned
-        }
-        T *p = reinterpret_cast<T *>(base + top);
-        top += bytes;
-        return p;
-    }
-};
-
-template <class T>
-__device__ void blk_fill(T *a, size_t n, T v) {
-    for (size_t i = threadIdx.x; i < n; i += blockDim.x) a[i] = v;
-}
-
-struct Ctx {
-    CtaTeam t;
-    Arena ar;
-    char *smem;
-    uint32_t *status;
-    // scratch (sized by the input instance)
-    int *e_a, *e_b, *e_c, *e_d, *n_a, *n_b, *n_c, *p_a, *gain, *list, *cnt4;
-    unsigned long long *e_key, *n_key;
-    int2 *hc;
-    uint8_t *side_a, *side_b;
-    signed char *grp;
-    RState *st;
-    // nested k-way: the part vector and the node maps of the current subgraph
-    int *parts, *loc, *l2g, *snw;
-};
-
-// Sorted-unique pins of every hyperedge (mapped through map, or as is) into p_a at the
-// hyperedge's offset, their counts into e_a.
-template <bool MAP>
-__device__ __noinline__ void blk_dedup(Ctx &x, int E, const int *hoff, const int *pins, const int *map) {
-    int *counters = x.cnt4;
-    if (threadIdx.x == 0) { counters[0] = 0; counters[1] = 0; counters[2] = 0; counters[3] = 0; }
-    __syncthreads();
-    d_seg_small<MAP>(x.t, E, hoff, pins, map, x.p_a, x.e_a, x.e_c, x.e_d, counters);
-    __syncthreads();
-    d_seg_mid<MAP>(x.t, hoff, pins, map, x.p_a, x.e_a, x.e_c, counters);
-    __syncthreads();
-    d_seg_big<MAP>(x.t, hoff, pins, map, x.p_a, x.e_a, x.e_d, counters, reinterpret_cast<uint32_t *>(x.smem));
-    __syncthreads();
-}
-
-// The compacted hyperedge CSR of `c` (hyperedges whose e_a count is >= 2, their pins from p_a,
-// weights carried) with the degrees of c's c.N nodes counted into n_a.  False on arena overflow.
-__device__ __noinline__ bool blk_compact(Ctx &x, int E, int P, const int *hoff, const int *hw, DLevel &c) {
-    int *cnt = x.e_a, *emap = x.e_b, *counters = x.cnt4;
-    c.hoff = x.ar.take<int>((size_t)E + 1);
-    c.hw = hw ? x.ar.take<int>((size_t)E) : nullptr;
-    if (x.ar.overflow) return false;
-    if (E > 0) {
-        block_scan_items(E, CompactIn{cnt}, CompactOut{E, hw, c.hoff, c.hw, emap, counters + 2, nullptr});
-    } else if (threadIdx.x == 0) {
-        c.hoff[0] = 0;
-        counters[2] = counters[3] = 0;
-    }
-    __syncthreads();
-    c.E = counters[2];
-    c.P = counters[3];
-    c.pins = x.ar.take<int>((size_t)c.P);
-    if (x.ar.overflow) return false;
-    blk_fill(x.n_a, (size_t)c.N, 0);  // degree counters of the compacted level
-    __syncthreads();
-    if (P > 0) d_seg_copy(x.t, E, P, hoff, x.p_a, cnt, emap, c.hoff, c.pins, x.n_a);
-    __syncthreads();
-    return true;
-}
-
-// Node -> hyperedge incidence of `c` from the degrees in n_a.
-__device__ __noinline__ bool blk_incidence(Ctx &x, DLevel &c) {
-    c.noff = x.ar.take<int>((size_t)c.N + 1);
-    c.nadj = x.ar.take<int>((size_t)c.P);
-    c.cmap = x.ar.take<int>((size_t)c.N);
-    c.match = x.ar.take<int>((size_t)c.N);
-    if (x.ar.overflow) return false;
-    if (c.N > 0) block_scan_items(c.N, DegIn{x.n_a}, DegOut{c.N, c.noff, x.n_b, nullptr});
-    else if (threadIdx.x == 0) c.noff[0] = 0;
-    __syncthreads();
-    if (c.P > 0) d_fill_adj(x.t, c.E, c.P, c.hoff, c.pins, x.n_b, c.nadj);
-    __syncthreads();
-    return true;
-}
-
-// Algorithms 1 and 2 on level f into c.  Returns false on arena overflow.
-__device__ __noinline__ bool blk_coarsen(Ctx &x, const DLevel &f, DLevel &c, int policy) {
-    const int N = f.N, E = f.E;
-    unsigned long long *hkey = x.e_key;
-    int *ssize = x.e_a, *sweight = x.e_b, *gcid = x.e_d, *grp = x.n_c;
-    unsigned *rep = reinterpret_cast<unsigned *>(x.e_c);
-    d_hedge_key(x.t, E, policy, f.hoff, f.hw, hkey);
-    blk_fill(ssize, (size_t)E, 0);
-    blk_fill(sweight, (size_t)E, 0);
-    blk_fill(rep, (size_t)E, 0xffffffffu);
-    blk_fill(x.n_key, (size_t)N, ~0ull);
-    __syncthreads();
-    if (f.P > 0) d_match_min(x.t, N, f.P, f.noff, f.nadj, hkey, x.n_key);
-    __syncthreads();
-    d_match_set(x.t, N, x.n_key, f.nw, f.match, ssize, sweight);
-    __syncthreads();
-    unsigned long long *best = hkey;  // the hyperedge keys are no longer needed
-    blk_fill(best, (size_t)E, ~0ull);
-    __syncthreads();
-    if (f.P > 0) d_single_best(x.t, E, f.P, f.hoff, f.pins, f.match, ssize, sweight, best);
-    __syncthreads();
-    d_group(x.t, N, f.match, ssize, best, grp, rep);
-    __syncthreads();
-    if (N > 0) block_scan_items(N, RenumIn{grp, rep}, RenumOut{N, grp, f.cmap, gcid, x.cnt4 + 2});
-    __syncthreads();
-    c.N = N > 0 ? x.cnt4[2] : 0;
-    __syncthreads();
-    c.nw = x.ar.take<int>((size_t)c.N);
-    if (x.ar.overflow) return false;
-    blk_fill(c.nw, (size_t)c.N, 0);
-    __syncthreads();
-    d_cmap(x.t, N, grp, gcid, f.nw, f.cmap, c.nw);
-    __syncthreads();
-    blk_dedup<true>(x, E, f.hoff, f.pins, f.cmap);
-    if (!blk_compact(x, E, f.P, f.hoff, f.hw, c)) return false;
-    return blk_incidence(x, c);
-}
-
-// ----------------------------------------------------------------- refinement (block versions)
-__device__ __noinline__ void blk_gains(Ctx &x, const DLevel &L, const uint8_t *side) {
-    int *n1 = x.e_d;
-    blk_fill(n1, (size_t)L.E, 0);
-    blk_fill(x.gain, (size_t)L.N, 0);
-    __syncthreads();
-    if (L.P > 0) d_hedge_n1(x.t, L.E, L.P, L.hoff, L.pins, side, n1);
-    __syncthreads();
-    d_hedge_contrib(x.t, L.E, L.hoff, L.hw, n1, x.hc);
-    __syncthreads();
-    if (L.P > 0) d_node_gain(x.t, L.N, L.P, L.noff, L.nadj, x.hc, side, x.gain);
-    __syncthreads();
-}
-
-// Selection and application of one pass of Algorithm 3 / 5 or of the rebalance.  Levels whose
-// nodes fit one tie bitmap word per thread take the shared-memory selection in one sweep.
-__device__ __noinline__ void blk_select_apply(Ctx &x, const DLevel &L, int kind, long long sq, uint8_t *side) {
-    RState *st = x.st;
-    unsigned(*h)[kHistBins] = reinterpret_cast<unsigned(*)[kHistBins]>(x.smem);
-    if (L.N <= kSelOneBlock && L.N <= 32 * (int)blockDim.x) {
-        d_sel_small(L.N, kind, sq, x.gain, side, L.nw, st, x.status, x.list, nullptr, x.gain, x.grp, h);
-        __syncthreads();
-        return;
-    }
-    blk_fill(&st->hist[0][0], (size_t)2 * kHistBins, 0u);
-    if (threadIdx.x == 0) st->list_count = 0;
-    __syncthreads();
-    d_sel_hist(x.t, L.N, kind, x.gain, side, L.nw, st, h);
-    __syncthreads();
-    d_sel_find(kind, sq, st, st->hist);
-    __syncthreads();
-    if (st->slow) {
-        for (int pass = 0; pass < 3; ++pass) {
-            blk_fill(&st->hist[0][0], (size_t)2 * kHistBins, 0u);
-            __syncthreads();
-            d_sel_hist_exact(x.t, L.N, kind, x.gain, side, L.nw, st, h);
-            __syncthreads();
-            d_sel_find_exact(st, x.status, st->hist);
-            __syncthreads();
-        }
-    }
-    block_scan_items(L.N, TieIn{kind, x.gain, side, L.nw, st}, ApplyOut{kind, x.gain, side, L.nw, st, x.list});
-    __syncthreads();
-}
-
-__device__ void blk_side_weights(Ctx &x, const DLevel &L, const uint8_t *side) {
-    if (threadIdx.x == 0) { x.st->W[0] = 0; x.st->W[1] = 0; }
-    __syncthreads();
-    d_side_weights(x.t, L.N, side, L.nw, x.st->W);
-    __syncthreads();
-}
-
-__device__ long long blk_ceil_sqrt(long long n) {
-    long long s = (long long)ceilf(sqrtf((float)n));
-    while (s * s < n) ++s;
-    while (s > 1 && (s - 1) * (s - 1) >= n) --s;
-    return s;
-}
-
-// Algorithm 3 with side 0 grown to its share m0 / m of the weight (reading G2).
-__device__ __noinline__ void blk_initial(Ctx &x, const DLevel &L, uint8_t *side, int m0, int m) {
-    if (L.N == 0) return;
-    RState *st = x.st;
-    const long long s = blk_ceil_sqrt(L.N);
-    blk_fill(side, (size_t)L.N, (uint8_t)1);
-    if (threadIdx.x == 0) st->rounds = 0;
-    __syncthreads();
-    blk_side_weights(x, L, side);
-    if (threadIdx.x == 0) d_initial_cond(st, (long long)L.N + 1, x.status, true, m0, m);
-    __syncthreads();
-    while (st->flag) {
-        blk_gains(x, L, side);
-        blk_select_apply(x, L, SEL_INITIAL, s, side);
-        if (threadIdx.x == 0) d_initial_cond(st, (long long)L.N + 1, x.status, false, m0, m);
-        __syncthreads();
-    }
-}
-
-// Rebalance of reading C13 with a limit per side.
-__device__ __noinline__ void blk_rebalance(Ctx &x, const DLevel &L, uint8_t *side, long long limit0, long long limit1) {
-    RState *st = x.st;
-    const long long s = blk_ceil_sqrt(L.N);
-    blk_side_weights(x, L, side);
-    if (threadIdx.x == 0) d_rebal_cond(st, limit0, limit1, (long long)L.N + 1, x.status, true);
-    __syncthreads();
-    while (st->flag) {
-        blk_gains(x, L, side);
-        blk_select_apply(x, L, SEL_REBAL, s, side);
-        d_rebal_move(x.gain, side, L.nw, x.list, st, s, reinterpret_cast<unsigned long long *>(x.smem));
-        __syncthreads();
-        if (threadIdx.x == 0) d_rebal_cond(st, limit0, limit1, (long long)L.N + 1, x.status, false);
-        __syncthreads();
-    }
-}
-
-// Total node weight of a level.
-__device__ unsigned long long blk_weight(int N, const int *nw) {
-    __shared__ unsigned long long s_w;
-    if (threadIdx.x == 0) s_w = 0;
-    __syncthreads();
-    unsigned long long w = 0;
-    for (int v = threadIdx.x; v < N; v += blockDim.x) w += (unsigned long long)nw[v];
-    w = warp_sum(w);
-    if ((threadIdx.x & 31) == 0 && w) atomicAdd(&s_w, w);
-    __syncthreads();
-    const unsigned long long r = s_w;
-    __syncthreads();
-    return r;
-}
-
-// The most a side meant for ms of m parts may weigh: max(ceil(W ms / m), floor(W ms (1 + e) / m))
-// with e = e6 / 10^6, in exact integer arithmetic.  Within a block W < 2^49 (2^18 nodes of
-// int32 weights), m <= 1024 and e6 <= 10^9, so every product below stays under 2^60.
-__device__ long long blk_limit(unsigned long long W, int ms, int m, long long e6) {
-    const unsigned long long share = W * (unsigned long long)ms;
-    const unsigned long long a = (share + (unsigned long long)m - 1) / (unsigned long long)m;
-    const unsigned long long D = (unsigned long long)m * 1000000ull, F = 1000000ull + (unsigned long long)e6;
-    const unsigned long long b = (share / D) * F + (share % D) * F / D;
-    return (long long)(a > b ? a : b);
-}
-
-// Sec. 3.4 on the level in lev[0] (incidence built): coarsen until `levels` levels exist or the
-// node count stops changing (reading C11), Algorithm 3 on the coarsest level, then refinement and
-// rebalancing back to level 0.  *result points at level 0's sides.  Returns the level-0
-// rebalance's imbalance flag, or 2 on arena overflow.
-__device__ __noinline__ int blk_bisect(Ctx &x, DLevel *lev, const BInst &I, unsigned long long W, int m0, int m,
-                          uint8_t **result) {
-    const long long lim0 = blk_limit(W, m0, m, I.e6), lim1 = blk_limit(W, m - m0, m, I.e6);
-    int nl = 1;
-    while (nl - 1 < I.levels && lev[nl - 1].E > 0) {
-        const size_t mark = x.ar.top;
-        if (!blk_coarsen(x, lev[nl - 1], lev[nl], I.policy)) return 2;
-        if (lev[nl].N == lev[nl - 1].N) {
-            x.ar.top = mark;
-            break;
-        }
-        ++nl;
-    }
-    uint8_t *cur = x.side_a, *other = x.side_b;
-    blk_initial(x, lev[nl - 1], cur, m0, m);
-    for (int l = nl - 1; l >= 0; --l) {
-        const DLevel &L = lev[l];
-        if (l < nl - 1) {
-            d_project(x.t, L.N, L.cmap, cur, other);
-            __syncthreads();
-            uint8_t *tmp = cur;
-            cur = other;
-            other = tmp;
-        }
-        for (int it = 0; it < I.iters; ++it) {
-            if (L.N == 0) break;
-            blk_gains(x, L, cur);
-            blk_select_apply(x, L, SEL_REFINE, 0, cur);
-        }
-        if (L.N > 0) blk_rebalance(x, L, cur, lim0, lim1);
-        else if (threadIdx.x == 0) x.st->warn = 0;
-        __syncthreads();
-    }
-    *result = cur;
-    return x.st->warn ? 1 : 0;
-}
-
-// Nodes of part `lo` renumbered in ascending id (reading C16): loc (global -> local, -1 outside),
-// l2g and the subgraph's node weights; the count goes to *count.
-struct SubIn {
-    const int *part;
-    int lo;
-    __device__ uint64_t operator()(int64_t v) const { return part[v] == lo ? 1ull : 0ull; }
-};
-struct SubOut {
-    int64_t n;
-    const int *nw;
-    int *loc, *l2g, *snw, *count;
-    __device__ void operator()(int64_t v, uint64_t pre, uint64_t val) const {
-        if (val) {
-            loc[v] = (int)pre;
-            l2g[pre] = (int)v;
-            snw[pre] = nw[v];
-        } else {
-            loc[v] = -1;
-        }
-        if (v == n - 1) *count = (int)(pre + val);
-    }
-};
-
-// Net splitting: every hyperedge of G restricted to the subgraph's nodes (local ids, in G's
-// order, which is ascending) into p_a at the hyperedge's offset, the kept counts into e_a.
-// Hyperedges of up to 32 pins take one thread, larger ones a warp.
-__device__ __noinline__ void blk_split_nets(Ctx &x, const DLevel &G) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
-    for (int e0 = warp * 32; e0 < G.E; e0 += warps * 32) {
-        const int e = e0 + lane;
-        int a = 0, d = 0;
-        if (e < G.E) {
-            a = G.hoff[e];
-            d = G.hoff[e + 1] - a;
-        }
-        const bool small = e < G.E && d <= 32;
-        if (small) {
-            int c = 0;
-            for (int i = 0; i < d; ++i) {
-                const int l = x.loc[G.pins[a + i]];
-                if (l >= 0) x.p_a[a + c++] = l;
-            }
-            x.e_a[e] = c;
-        }
-        unsigned big = __ballot_sync(0xffffffffu, e < G.E && !small);
-        while (big) {
-            const int src = __ffs(big) - 1;
-            big &= big - 1;
-            const int eb = e0 + src, ab = G.hoff[eb], db = G.hoff[eb + 1] - ab;
-            int c = 0;
-            for (int i0 = 0; i0 < db; i0 += 32) {
-                const int l = i0 + lane < db ? x.loc[G.pins[ab + i0 + lane]] : -1;
-                const unsigned keep = __ballot_sync(0xffffffffu, l >= 0);
-                if (l >= 0) x.p_a[ab + c + __popc(keep & ((1u << lane) - 1u))] = l;
-                c += __popc(keep);
-            }
-            if (lane == 0) x.e_a[eb] = c;
-        }
-    }
-    __syncthreads();
-}
-
-// One whole instance: its parts go to a.parts + I.out.  Returns its status (0 ok, 1 imbalanced,
-// 2 deferred).
-__device__ int blk_solve(Ctx &x, const BArgs &a, const BInst &I, DLevel *lev, int2 *stack) {
-    const int N = I.N, E = I.E, P = I.P;
-    int *out = a.parts + I.out;
-    // scratch sized by the input (every subgraph is smaller)
-    x.e_a = x.ar.take<int>(E);
-    x.e_b = x.ar.take<int>(E);
-    x.e_c = x.ar.take<int>(E);
-    x.e_d = x.ar.take<int>(E);
-    x.e_key = x.ar.take<unsigned long long>(E);
-    x.hc = x.ar.take<int2>(E);
-    x.n_a = x.ar.take<int>(N);
-    x.n_b = x.ar.take<int>(N);
-    x.n_c = x.ar.take<int>(N);
-    x.n_key = x.ar.take<unsigned long long>(N);
-    x.gain = x.ar.take<int>(N);
-    x.side_a = x.ar.take<uint8_t>(N);
-    x.side_b = x.ar.take<uint8_t>(N);
-    x.grp = x.ar.take<signed char>(N);
-    x.p_a = x.ar.take<int>(P);
-    x.list = x.ar.take<int>((size_t)blk_ceil_sqrt(N > 0 ? N : 1) + 2);
-    x.cnt4 = x.ar.take<int>(8);
-    x.st = x.ar.take<RState>(1);
-    if (I.k > 2) {
-        x.parts = x.ar.take<int>(N);
-        x.loc = x.ar.take<int>(N);
-        x.l2g = x.ar.take<int>(N);
-        x.snw = x.ar.take<int>(N);
-    }
-    if (x.ar.overflow) return 2;
-    blk_fill(reinterpret_cast<unsigned *>(x.st), sizeof(RState) / sizeof(unsigned), 0u);
-    if (I.k == 1) {
-        blk_fill(out, (size_t)N, 0);
-        __syncthreads();
-        return 0;
-    }
-    // level 0: the normalised input
-    const int *hoff = a.hoff + I.hoff, *pins = a.pins + I.pins;
-    const int *hw = I.hw >= 0 ? a.hw + I.hw : nullptr;
-    DLevel G;
-    G.N = N;
-    blk_dedup<false>(x, E, hoff, pins, nullptr);
-    if (!blk_compact(x, E, P, hoff, hw, G)) return 2;
-    G.nw = x.ar.take<int>(N);
-    if (x.ar.overflow) return 2;
-    for (int v = threadIdx.x; v < N; v += blockDim.x) G.nw[v] = I.nw >= 0 ? a.nw[I.nw + v] : 1;
-    __syncthreads();
-    if (!blk_incidence(x, G)) return 2;
-    lev[0] = G;
-    // the top bisection: side 0 meant for ceil(k / 2) of the k parts
-    const int m0 = (I.k + 1) / 2;
-    uint8_t *side = nullptr;
-    int warn = blk_bisect(x, lev, I, blk_weight(N, G.nw), m0, I.k, &side);
-    if (warn == 2) return 2;
-    int *parts = I.k == 2 ? out : x.parts;
-    for (int v = threadIdx.x; v < N; v += blockDim.x) parts[v] = side[v] ? m0 : 0;
-    __syncthreads();
-    if (I.k == 2) return warn;
-    // Algorithm 6: the subgraph holding parts [lo, lo + m) is bisected with side 0 meant for
-    // ceil(m / 2) of them until every range holds one part.  Ranges own disjoint part values, so
-    // they are taken in any order, each extracted from level 0 by the part vector.
-    const size_t mark = x.ar.top;
-    int sp = 2;
-    if (threadIdx.x == 0) {
-        stack[0] = make_int2(m0, I.k - m0);
-        stack[1] = make_int2(0, m0);
-    }
-    __syncthreads();
-    while (sp > 0) {
-        const int2 r = stack[--sp];
-        if (r.y < 2) continue;
-        block_scan_items(N, SubIn{parts, r.x}, SubOut{N, G.nw, x.loc, x.l2g, x.snw, x.cnt4 + 4});
-        __syncthreads();
-        DLevel S;
-        S.N = x.cnt4[4];
-        __syncthreads();
-        if (S.N == 0) continue;
-        S.nw = x.snw;
-        blk_split_nets(x, G);
-        if (!blk_compact(x, G.E, G.P, G.hoff, G.hw, S)) return 2;
-        if (!blk_incidence(x, S)) return 2;
-        lev[0] = S;
-        const int q0 = (r.y + 1) / 2;
-        const int w = blk_bisect(x, lev, I, blk_weight(S.N, S.nw), q0, r.y, &side);
-        if (w == 2) return 2;
-        warn |= w;
-        for (int i = threadIdx.x; i < S.N; i += blockDim.x) parts[x.l2g[i]] = side[i] ? r.x + q0 : r.x;
-        if (threadIdx.x == 0) {
-            stack[sp] = make_int2(r.x + q0, r.y - q0);
-            stack[sp + 1] = make_int2(r.x, q0);
-        }
-        sp += 2;
-        x.ar.top = mark;
-        __syncthreads();
-    }
-    for (int v = threadIdx.x; v < N; v += blockDim.x) out[v] = parts[v];
-    __syncthreads();
-    return warn;
-}
-
-}  // namespace
-
-template <int BT, int MINB>
-__global__ void __launch_bounds__(BT, MINB) k_batch(BArgs a) {
-    extern __shared__ __align__(16) char smem[];
-    __shared__ DLevel lev[kMaxLev];
-    __shared__ int2 stack[kMaxStack];
-    __shared__ int s_inst;
-    for (;;) {
-        if (threadIdx.x == 0) s_inst = atomicAdd(a.next, 1);
-        __syncthreads();
-        const int q = s_inst;
-        __syncthreads();
-        if (q >= a.n) break;
-        const int i = a.order[q];
-        Ctx x;
-        x.ar.base = a.arena + (size_t)blockIdx.x * a.arena_bytes;
-        x.ar.cap = a.arena_bytes;
-        x.ar.top = 0;
-        // a misaligned arena would fault on its 8-byte arrays: defer instead of touching it
-        x.ar.overflow = ((uintptr_t)x.ar.base & 255) != 0;
-        x.smem = smem;
-        x.status = a.status;
-        const BInst I = a.inst[i];
-        const int st = blk_solve(x, a, I, lev, stack);
-        if (threadIdx.x == 0) a.inst[i].status = st;
-        __syncthreads();
-    }
-}
+// The kernel of each block shape (block_shapes_*.cu).
+const void *batch_kernel_256_1();
+const void *batch_kernel_256_2();
+const void *batch_kernel_256_4();
+const void *batch_kernel_512_1();
+const void *batch_kernel_512_2();
+const void *batch_kernel_1024_1();
 
 // ------------------------------------------------------------------ host side
 namespace {
@@ -563,13 +52,11 @@ namespace {
 // selection of Algorithms 3 and 5 needs at least 256 threads.
 struct Shape {
     int threads, per_sm;
-    const void *fn;
+    const void *(*fn)();
 };
 const Shape kShapes[] = {
-    {256, 1, (const void *)k_batch<256, 1>},
-    {256, 2, (const void *)k_batch<256, 2>},
-    {512, 1, (const void *)k_batch<512, 1>},
-    {1024, 1, (const void *)k_batch<1024, 1>},
+    {256, 1, batch_kernel_256_1}, {256, 2, batch_kernel_256_2}, {256, 4, batch_kernel_256_4},
+    {512, 1, batch_kernel_512_1}, {512, 2, batch_kernel_512_2}, {1024, 1, batch_kernel_1024_1},
 };
 constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
 
@@ -577,7 +64,7 @@ constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
 constexpr int kBuckets = 4;
 const int64_t kBucketEdge[kBuckets - 1] = {16 << 10, 128 << 10, 1 << 20};
 // Shapes used before a bucket is tuned on this device.
-const int kDefaultShape[kBuckets] = {1, 2, 2, 2};
+const int kDefaultShape[kBuckets] = {1, 5, 5, 5};
 
 int bucket_of(int64_t P) {
     int b = 0;
@@ -820,9 +307,9 @@ struct BatchCtx {
             BP_CUDA(cudaEventCreateWithFlags(&join[b], cudaEventDisableTiming));
         }
         for (int s = 0; s < kNumShapes; ++s) {
-            BP_CUDA(cudaFuncSetAttribute(kShapes[s].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+            BP_CUDA(cudaFuncSetAttribute(kShapes[s].fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
             int per = 0;
-            BP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kShapes[s].fn, kShapes[s].threads, kSmemBytes));
+            BP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kShapes[s].fn(), kShapes[s].threads, kSmemBytes));
             occ[s] = std::max(1, std::min(per, kShapes[s].per_sm));
         }
         lanes.reset(new Lanes(16));
@@ -1004,7 +491,7 @@ void record(BatchCtx &c, const Prepared &pr, int n) {
         a.arena_bytes = r.arena;
         a.status = status;
         void *args[] = {&a};
-        BP_CUDA(cudaLaunchKernel(kShapes[r.shape].fn, dim3(r.blocks), dim3(kShapes[r.shape].threads), args,
+        BP_CUDA(cudaLaunchKernel(kShapes[r.shape].fn(), dim3(r.blocks), dim3(kShapes[r.shape].threads), args,
                                  kSmemBytes, bs));
         BP_LAUNCH();
         BP_CUDA(cudaEventRecord(c.join[b], bs));
@@ -1189,6 +676,33 @@ void tune_block_batch(std::vector<BInst> &inst, const std::vector<const int32_t 
     }
     c.drop_graph();
     write_table(tune_path(), c.table);
+}
+
+// Device bytes the batch context needs for these instances (staging copy, outputs and arenas).
+size_t block_batch_bytes(std::vector<BInst> inst) {
+    if (inst.empty()) return 0;
+    BatchCtx &c = ctx();
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.init();
+    std::vector<const int32_t *> nw(inst.size(), nullptr), hw(inst.size(), nullptr);
+    for (size_t i = 0; i < inst.size(); ++i) {
+        if (inst[i].nw >= 0) nw[i] = reinterpret_cast<const int32_t *>(1);  // only presence counts here
+        if (inst[i].hw >= 0) hw[i] = reinterpret_cast<const int32_t *>(1);
+    }
+    const Prepared pr = prepare(c, inst, nw, hw, nullptr);
+    return pr.lay.out_end + std::max<size_t>(pr.arena_total, 256) + 256;
+}
+
+// Frees the device buffers and graph of the batch context (the pinned staging stays).
+void trim_block_batch() {
+    BatchCtx &c = ctx();
+    std::lock_guard<std::mutex> lk(c.mu);
+    if (c.device < 0) return;
+    if (c.stream) cudaStreamSynchronize(c.stream);
+    c.drop_graph();
+    c.dev.release();
+    c.arena.release();
+    c.misc.release();
 }
 
 // Frees the batch context's buffers and graph (they are kept between calls otherwise).

@@ -48,6 +48,7 @@ struct Job {
     Clock::time_point t_submit, t_start, t_end;
     uint64_t sig = 0;  // shape of the input and parameters (sizes only)
     int pref = -1;     // the worker that last ran this shape, whose launch plans fit it
+    bool block_ok = false;  // the persistent block path can take it (server micro-batches)
 };
 
 // Shape of a request: what a worker's captured launch plans depend on besides the data.
@@ -82,11 +83,89 @@ size_t estimate_bytes(const bipart_instance &in) {
     return 64 * P + 96 * E + 96 * N + (8u << 20);
 }
 
+
+// The persistent block path takes an instance when it fits a block (block_eligible) and does not
+// ask for parallel-net merging, which only the grid path implements.
+bool block_takes(const bipart_instance &in, const bipart_params &p) {
+    const int64_t P = in.num_hedges > 0 ? in.hedge_offsets[in.num_hedges] : 0;
+    return in.num_nodes > 0 && block_eligible(in.num_nodes, in.num_hedges, P, p.k, p.levels) &&
+           !(p.flags & BIPART_FLAG_MERGE_PARALLEL);
+}
+
+// Descriptors and array pointers of the instances idx[] for the block path.
+struct BlockSet {
+    std::vector<BInst> bi;
+    std::vector<const int32_t *> ho, pi, nw, hw;
+};
+
+BlockSet block_set(const std::vector<const bipart_instance *> &ins, const std::vector<const bipart_params *> &ps) {
+    // instances without hyperedges still need an offsets array of one zero
+    static const int32_t zero = 0;
+    BlockSet b;
+    const size_t n = ins.size();
+    b.bi.resize(n);
+    b.ho.resize(n);
+    b.pi.resize(n);
+    b.nw.resize(n);
+    b.hw.resize(n);
+    for (size_t j = 0; j < n; ++j) {
+        const bipart_instance &in = *ins[j];
+        const bipart_params &p = *ps[j];
+        BInst &d = b.bi[j];
+        d.N = in.num_nodes;
+        d.E = in.num_hedges;
+        d.P = in.num_hedges > 0 ? in.hedge_offsets[in.num_hedges] : 0;
+        d.policy = p.policy;
+        d.levels = p.levels;
+        d.iters = p.refine_iters;
+        d.k = p.k;
+        d.e6 = make_params(p.k, p.epsilon, p.policy, p.levels, p.refine_iters, p.flags).e6;
+        d.status = 0;
+        d.nw = in.node_weights ? 0 : -1;  // presence (offsets are assigned by the batch)
+        d.hw = in.hedge_weights ? 0 : -1;
+        b.ho[j] = in.num_hedges > 0 ? in.hedge_offsets : &zero;
+        b.pi[j] = in.hedge_pins;
+        b.nw[j] = in.node_weights;
+        b.hw[j] = in.hedge_weights;
+    }
+    return b;
+}
+
+BlockSet block_set(const std::vector<int32_t> &idx, const bipart_instance *instances,
+                   const bipart_params *params) {
+    std::vector<const bipart_instance *> ins;
+    std::vector<const bipart_params *> ps;
+    for (int32_t i : idx) {
+        ins.push_back(instances + i);
+        ps.push_back(params + i);
+    }
+    return block_set(ins, ps);
+}
+
+// Validates every instance; st[i] / err[i] record a failure.
+void validate_all(int32_t n, const bipart_instance *instances, const bipart_params *params,
+                  std::vector<int32_t> &st, std::vector<std::string> &err) {
+    validate_host_many(n, instances, st.data(), err.data());
+    for (int32_t i = 0; i < n; ++i) {
+        if (st[i] != BIPART_OK) continue;
+        const bipart_params &p = params[i];
+        try {
+            make_params(p.k, p.epsilon, p.policy, p.levels, p.refine_iters, p.flags);  // validates
+        } catch (const Fail &e) {
+            st[i] = e.code;
+            err[i] = e.msg;
+        }
+    }
+}
+
+
 class Pool {
    public:
     // kid_lanes: the workspaces' host threads for the subgraphs of a k-way tree level (1: one
-    // after another on the worker's stream; 0: the library default)
-    Pool(int workers, size_t budget, int kid_lanes) : budget_(budget), kid_lanes_(kid_lanes) {
+    // after another on the worker's stream; 0: the library default).  batching: waiting requests
+    // the persistent block path takes are run together as one batch once enough of them queue up.
+    Pool(int workers, size_t budget, int kid_lanes, bool batching = false)
+        : budget_(budget), kid_lanes_(kid_lanes), batching_(batching) {
         BP_CUDA(cudaGetDevice(&device_));
         if (workers < 1) workers = 1;
         busy_.assign((size_t)workers, 0);
@@ -111,6 +190,7 @@ class Pool {
         j->out = out;
         j->bytes = estimate_bytes(inst);
         j->sig = job_sig(inst, p);
+        j->block_ok = batching_ && block_takes(inst, p) && batch_cost(inst, p) <= kBatchMaxCost;
         j->t_submit = Clock::now();
         std::lock_guard<std::mutex> lk(mu_);
         j->ticket = ++next_ticket_;
@@ -171,53 +251,78 @@ class Pool {
         } catch (const Fail &) {
             ws.reset();
         }
+        auto fresh_workspace = [&]() {
+            // under a budget a worker holds device memory only while it runs a request: the
+            // workspace is rebuilt empty before the request's share is given back
+            try {
+                ws.reset();
+                ws.reset(graph_new(s));
+                ws->kid_lanes = kid_lanes_;
+                ws->lean = true;
+            } catch (const Fail &) {
+                ws.reset();
+            }
+        };
+        auto run_one = [&](Job &j) {
+            if (!ws) {
+                j.status = BIPART_ERR_CUDA;
+                j.error = "worker could not create its workspace";
+                return;
+            }
+            try {
+                const bipart_instance &in = j.inst;
+                graph_load_host(ws.get(), in.num_nodes, in.num_hedges, in.hedge_offsets, in.hedge_pins,
+                                in.node_weights, in.hedge_weights);
+                const bipart_params &q = j.params;
+                const Params p = make_params(q.k, q.epsilon, q.policy, q.levels, q.refine_iters, q.flags);
+                j.status = graph_partition_host(ws.get(), p, j.out);
+            } catch (const Fail &e) {
+                j.status = e.code;
+                j.error = e.msg;
+            } catch (...) {
+                j.status = BIPART_ERR_CUDA;
+                j.error = "unexpected exception";
+            }
+        };
         for (;;) {
             std::shared_ptr<Job> j;
+            std::vector<std::shared_ptr<Job>> batch;
+            size_t batch_bytes = 0;
             {
                 std::unique_lock<std::mutex> lk(mu_);
                 cv_.wait(lk, [&]() { return (stop_ && queue_.empty()) || admissible(me) != queue_.end(); });
                 if (stop_ && queue_.empty()) break;
-                auto it = admissible(me);
-                j = *it;
-                queue_.erase(it);
-                in_flight_ += j->bytes;
+                if (!take_batch(batch, batch_bytes)) {
+                    auto it = admissible(me);
+                    j = *it;
+                    queue_.erase(it);
+                    in_flight_ += j->bytes;
+                }
                 busy_[(size_t)me] = 1;
                 // jobs left waiting for this worker may now go to any other
                 if (!queue_.empty()) cv_.notify_all();
             }
+            if (!batch.empty()) {
+                run_batch(batch, run_one);
+                if (budget_) {
+                    trim_block_batch();
+                    if (ws) fresh_workspace();
+                }
+                {
+                    std::lock_guard<std::mutex> lk(mu_);
+                    in_flight_ -= batch_bytes;
+                    batch_busy_ = false;
+                    busy_[(size_t)me] = 0;
+                    for (auto &b : batch) b->done = true;
+                }
+                done_cv_.notify_all();
+                cv_.notify_all();
+                continue;
+            }
             j->t_start = Clock::now();
-            if (!ws) {
-                j->status = BIPART_ERR_CUDA;
-                j->error = "worker could not create its workspace";
-            } else {
-                try {
-                    const bipart_instance &in = j->inst;
-                    graph_load_host(ws.get(), in.num_nodes, in.num_hedges, in.hedge_offsets,
-                                    in.hedge_pins, in.node_weights, in.hedge_weights);
-                    const bipart_params &q = j->params;
-                    const Params p = make_params(q.k, q.epsilon, q.policy, q.levels, q.refine_iters, q.flags);
-                    j->status = graph_partition_host(ws.get(), p, j->out);
-                } catch (const Fail &e) {
-                    j->status = e.code;
-                    j->error = e.msg;
-                } catch (...) {
-                    j->status = BIPART_ERR_CUDA;
-                    j->error = "unexpected exception";
-                }
-            }
+            run_one(*j);
             j->t_end = Clock::now();
-            if (budget_ && ws) {
-                // under a budget a worker holds device memory only while it runs a request: the
-                // workspace is rebuilt empty before the request's share is given back
-                try {
-                    ws.reset();
-                    ws.reset(graph_new(s));
-                    ws->kid_lanes = kid_lanes_;
-                    ws->lean = true;
-                } catch (const Fail &) {
-                    ws.reset();
-                }
-            }
+            if (budget_ && ws) fresh_workspace();
             {
                 std::lock_guard<std::mutex> lk(mu_);
                 in_flight_ -= j->bytes;
@@ -230,6 +335,99 @@ class Pool {
         }
         ws.reset();
         if (s) cudaStreamDestroy(s);
+    }
+
+    // Server micro-batching: once at least kBatchMin waiting requests can run in the persistent
+    // block path (a backlog: every worker is busy and requests queue up), a free worker takes up
+    // to kBatchMax of them, in queue order, as one batch -- one thread block per request, all in
+    // a few launches -- if the batch's device memory fits the budget next to the running jobs.
+    // One batch runs at a time.  Called with mu_ held.
+    // Only requests of at most kBatchMaxCost pin-bisections (pins x ceil(log2 k)) go into a
+    // micro-batch: a batch completes as a whole, so its longest block sets every member's latency,
+    // and one block takes about as long on a 256K-pin bisection as the grid path on a 2M-pin one.
+    static constexpr int kBatchMin = 8, kBatchMax = 1024;
+    static constexpr int64_t kBatchMaxCost = 256 << 10;
+    static int64_t batch_cost(const bipart_instance &in, const bipart_params &p) {
+        const int64_t P = in.num_hedges > 0 ? in.hedge_offsets[in.num_hedges] : 0;
+        int depth = 1;
+        while ((int64_t(1) << depth) < p.k) ++depth;
+        return P * depth;
+    }
+    bool take_batch(std::vector<std::shared_ptr<Job>> &out, size_t &bytes) {
+        if (!batching_ || batch_busy_) return false;
+        std::vector<std::shared_ptr<Job>> cand;
+        for (auto &q : queue_)
+            if (q->block_ok && (int)cand.size() < kBatchMax) cand.push_back(q);
+        if ((int)cand.size() < kBatchMin) return false;
+        std::vector<const bipart_instance *> ins;
+        std::vector<const bipart_params *> ps;
+        for (auto &q : cand) {
+            ins.push_back(&q->inst);
+            ps.push_back(&q->params);
+        }
+        size_t need = 0;
+        try {
+            need = block_batch_bytes(block_set(ins, ps).bi);
+        } catch (const Fail &) {
+            return false;
+        }
+        if (budget_ && (need > budget_ || (in_flight_ != 0 && in_flight_ + need > budget_))) return false;
+        std::deque<std::shared_ptr<Job>> rest;
+        for (auto &q : queue_)
+            if (!(q->block_ok && std::find(cand.begin(), cand.end(), q) != cand.end())) rest.push_back(q);
+        queue_.swap(rest);
+        in_flight_ += need;
+        batch_busy_ = true;
+        bytes = need;
+        batches_ += 1;
+        batched_ += (int64_t)cand.size();
+        out.swap(cand);
+        return true;
+    }
+
+   public:
+    void stats(int64_t *batches, int64_t *batched) {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (batches) *batches = batches_;
+        if (batched) *batched = batched_;
+    }
+
+   private:
+
+    // Runs a micro-batch on this thread; a request the block path defers runs alone here.
+    template <class RunOne>
+    void run_batch(std::vector<std::shared_ptr<Job>> &batch, RunOne &run_one) {
+        const Clock::time_point t0 = Clock::now();
+        std::vector<const bipart_instance *> ins;
+        std::vector<const bipart_params *> ps;
+        std::vector<int32_t *> outs;
+        for (auto &b : batch) {
+            b->t_start = t0;
+            ins.push_back(&b->inst);
+            ps.push_back(&b->params);
+            outs.push_back(b->out);
+        }
+        try {
+            BlockSet bs = block_set(ins, ps);
+            run_block_batch(bs.bi, bs.ho, bs.pi, bs.nw, bs.hw, outs);
+            const Clock::time_point t1 = Clock::now();
+            for (size_t i = 0; i < batch.size(); ++i) {
+                Job &j = *batch[i];
+                if (bs.bi[i].status == 2) {
+                    run_one(j);
+                    j.t_end = Clock::now();
+                } else {
+                    j.status = bs.bi[i].status ? BIPART_WARN_IMBALANCED : BIPART_OK;
+                    j.t_end = t1;
+                }
+            }
+        } catch (const Fail &e) {
+            for (auto &b : batch) {
+                b->status = e.code;
+                b->error = e.msg;
+                b->t_end = Clock::now();
+            }
+        }
     }
 
     // First queued job that fits next to the running ones (always the head when nothing runs)
@@ -247,6 +445,9 @@ class Pool {
     int device_ = 0;
     size_t budget_ = 0;
     int kid_lanes_ = 0;
+    bool batching_ = false;
+    bool batch_busy_ = false;
+    int64_t batches_ = 0, batched_ = 0;  // micro-batches run and the requests they held
     size_t in_flight_ = 0;
     bool stop_ = false;
     int64_t next_ticket_ = 0;
@@ -285,73 +486,6 @@ struct bipart_server_s {
 
 using namespace bp;
 
-namespace bp {
-namespace {
-
-// The persistent block path takes an instance when it fits a block (block_eligible) and does not
-// ask for parallel-net merging, which only the grid path implements.
-bool block_takes(const bipart_instance &in, const bipart_params &p) {
-    const int64_t P = in.num_hedges > 0 ? in.hedge_offsets[in.num_hedges] : 0;
-    return in.num_nodes > 0 && block_eligible(in.num_nodes, in.num_hedges, P, p.k, p.levels) &&
-           !(p.flags & BIPART_FLAG_MERGE_PARALLEL);
-}
-
-// Descriptors and array pointers of the instances idx[] for the block path.
-struct BlockSet {
-    std::vector<BInst> bi;
-    std::vector<const int32_t *> ho, pi, nw, hw;
-};
-
-BlockSet block_set(const std::vector<int32_t> &idx, const bipart_instance *instances,
-                   const bipart_params *params) {
-    // instances without hyperedges still need an offsets array of one zero
-    static const int32_t zero = 0;
-    BlockSet b;
-    const size_t n = idx.size();
-    b.bi.resize(n);
-    b.ho.resize(n);
-    b.pi.resize(n);
-    b.nw.resize(n);
-    b.hw.resize(n);
-    for (size_t j = 0; j < n; ++j) {
-        const bipart_instance &in = instances[idx[j]];
-        const bipart_params &p = params[idx[j]];
-        BInst &d = b.bi[j];
-        d.N = in.num_nodes;
-        d.E = in.num_hedges;
-        d.P = in.num_hedges > 0 ? in.hedge_offsets[in.num_hedges] : 0;
-        d.policy = p.policy;
-        d.levels = p.levels;
-        d.iters = p.refine_iters;
-        d.k = p.k;
-        d.e6 = make_params(p.k, p.epsilon, p.policy, p.levels, p.refine_iters, p.flags).e6;
-        d.status = 0;
-        b.ho[j] = in.num_hedges > 0 ? in.hedge_offsets : &zero;
-        b.pi[j] = in.hedge_pins;
-        b.nw[j] = in.node_weights;
-        b.hw[j] = in.hedge_weights;
-    }
-    return b;
-}
-
-// Validates every instance; st[i] / err[i] record a failure.
-void validate_all(int32_t n, const bipart_instance *instances, const bipart_params *params,
-                  std::vector<int32_t> &st, std::vector<std::string> &err) {
-    validate_host_many(n, instances, st.data(), err.data());
-    for (int32_t i = 0; i < n; ++i) {
-        if (st[i] != BIPART_OK) continue;
-        const bipart_params &p = params[i];
-        try {
-            make_params(p.k, p.epsilon, p.policy, p.levels, p.refine_iters, p.flags);  // validates
-        } catch (const Fail &e) {
-            st[i] = e.code;
-            err[i] = e.msg;
-        }
-    }
-}
-
-}  // namespace
-}  // namespace bp
 
 // Batch: the instances the persistent block path takes run there (size buckets, one CUDA graph)
 // on this thread; the others (and any instance the block path defers) go to the worker pool,
@@ -482,7 +616,7 @@ extern "C" int bipart_server_create(size_t hbm_budget_bytes, int32_t workers, bi
     try {
         std::unique_ptr<bipart_server_s> s(new bipart_server_s);
         // requests run concurrently across workers; each one's k-way subgraphs one after another
-        s->pool.reset(new Pool(workers > 0 ? workers : 8, hbm_budget_bytes, 1));
+        s->pool.reset(new Pool(workers > 0 ? workers : 8, hbm_budget_bytes, 1, true));
         *out = s.release();
         return BIPART_OK;
     } catch (const Fail &e) {
@@ -524,6 +658,15 @@ extern "C" int bipart_server_wait(bipart_server server, int64_t ticket, int32_t 
     if (queue_ms) *queue_ms = ms_between(j->t_submit, j->t_start);
     if (run_ms) *run_ms = ms_between(j->t_start, j->t_end);
     if (j->status < 0) set_error(j->error);
+    return BIPART_OK;
+}
+
+extern "C" int bipart_server_stats(bipart_server server, int64_t *batches, int64_t *batched_requests) {
+    if (!server) {
+        set_error("server is NULL");
+        return BIPART_ERR_INVALID_ARG;
+    }
+    server->pool->stats(batches, batched_requests);
     return BIPART_OK;
 }
 

@@ -455,6 +455,10 @@ void tune_block_batch(std::vector<BInst> &inst, const std::vector<const int32_t 
                       const std::vector<const int32_t *> &pins, const std::vector<const int32_t *> &nw,
                       const std::vector<const int32_t *> &hw, int32_t *chosen);
 void release_block_batch();
+// Device bytes the persistent path needs for these instances (nw / hw >= 0 marks weights), and
+// the release of its device buffers (a server under a budget holds them only while a batch runs).
+size_t block_batch_bytes(std::vector<BInst> inst);
+void trim_block_batch();
 
 // ------------------------------------------------------------------------- validation (api.cu)
 void validate_params(int32_t k, double eps, int32_t policy, int32_t levels, int32_t iters);

@@ -280,7 +280,8 @@ def test_tuner_writes_cache_and_results_stay_exact(tmp_path, monkeypatch):
     graphs = _kway_cases(44, 16) + [synth.c3_instance(970, N=30000)]
     params = [dict(k=[2, 4][i % 2], eps=0.05, policy="LDH", levels=25, iters=2) for i in range(len(graphs))]
     chosen = bp.tune_batch(graphs, params)
-    assert chosen and all(t in (256, 512, 1024) and m in (1, 2) for t, m in chosen.values())
+    assert chosen and all((t, m) in ((256, 1), (256, 2), (256, 4), (512, 1), (512, 2), (1024, 1))
+                          for t, m in chosen.values())
     doc = json.loads(cache.read_text())
     assert doc["version"] == 1 and len(doc["devices"]) == 1
     (entry,) = doc["devices"].values()
@@ -290,3 +291,21 @@ def test_tuner_writes_cache_and_results_stay_exact(tmp_path, monkeypatch):
     for i, g in enumerate(graphs):
         ref, rst = oracle.partition(oracle.Hypergraph.from_dict(g), params[i]["k"], 0.05, "LDH", 25, 2)
         assert np.array_equal(parts[i], ref) and st[i] == rst, i
+
+
+def test_server_micro_batches_a_backlog_exactly():
+    # many small requests submitted at once leave a backlog, which free workers take as
+    # micro-batches through the persistent block path; every result equals the oracle's
+    import paper_2012_13618_gb300 as bp
+    graphs = mixed_instances(48, seed=12)
+    ks = [2, 4, 16, 3]
+    refs = [oracle.partition(oracle.Hypergraph.from_dict(g), ks[i % 4], 0.05, "LDH", 25, 2)
+            for i, g in enumerate(graphs)]
+    with bp.Server(hbm_budget_bytes=0, workers=2) as srv:
+        tickets = [srv.submit(g, k=ks[i % 4], eps=0.05) for i, g in enumerate(graphs)]
+        for i, t in enumerate(tickets):
+            parts, st, qms, rms = srv.wait(t)
+            assert np.array_equal(parts, refs[i][0]) and st == refs[i][1], i
+            assert qms >= 0 and rms >= 0
+        batches, batched = srv.stats()
+    assert batches >= 1 and batched >= 8
