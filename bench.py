@@ -537,6 +537,25 @@ def batched_form(bp, args, ws=1, rank=0):
             "tuned_shapes": {str(b): list(v) for b, v in tuned.items()}}
 
 
+def run_batch_once(args):
+    """One untuned batch call, nothing timed: the launch a focused ncu capture of the persistent
+    kernel selects.  --batch-nodes N gives every instance N nodes (0: C3's size mix); the tuning
+    file is a fresh one, so every bucket runs its default block shape."""
+    import synth
+    os.environ["BIPART_TUNE_CACHE"] = os.path.join(tempfile.mkdtemp(), "tune.json")
+    import torch
+    import paper_2012_13618_gb300 as bp
+    torch.cuda.set_device(0)
+    n = args.batch_n
+    graphs = [synth.c3_instance(i, N=args.batch_nodes) if args.batch_nodes else synth.c3_instance(i)
+              for i in range(n)]
+    parts, st = bp.partition_batch(graphs, dict(k=2, eps=0.05, policy="LDH", levels=25, iters=2),
+                                   workers=args.workers)
+    print(json.dumps({"once": f"{n} netlist-like instances" + (f" of {args.batch_nodes} nodes" if args.batch_nodes
+                                                             else ""),
+                      "pins": sum(int(g["hoff"][-1]) for g in graphs), "status": [int(x) for x in st]}))
+
+
 def run_batch(args):
     import torch
     import paper_2012_13618_gb300 as bp
@@ -704,6 +723,8 @@ def main():
     ap.add_argument("--workers", type=int, default=16)
     ap.add_argument("--batch-n", type=int, default=4096)
     ap.add_argument("--big-nodes", type=int, default=2_000_000)
+    ap.add_argument("--batch-nodes", type=int, default=0,
+                    help="with --workload batch --once: nodes of every instance (0: C3's mix)")
     ap.add_argument("--plain-n", type=int, default=0,
                     help="instances the plain comparison runs (0: all of them)")
     ap.add_argument("--batch-reps", type=int, default=3)
@@ -721,6 +742,8 @@ def main():
                     help="with --once: also capture the graph and run one replay inside an NVTX "
                          "range named 'replay' (for launch lists of exactly one replay)")
     args = ap.parse_args()
+    if args.once and args.workload == "batch":
+        return run_batch_once(args)
     if args.once:
         return run_once(args.replay)
     if args.workload == "batch":
