@@ -67,8 +67,8 @@ struct Ctx {
     uint32_t *status;
     // scratch (sized by the input instance)
     int *e_a, *e_b, *e_c, *e_d, *n_a, *n_b, *n_c, *p_a, *gain, *list, *cnt4;
+    int *dw;  // weighted degree of the level being refined
     unsigned long long *e_key, *n_key;
-    int2 *hc;
     uint8_t *side_a, *side_b;
     signed char *grp;
     RState *st;
@@ -170,16 +170,70 @@ __device__ __noinline__ bool blk_coarsen(Ctx &x, const DLevel &f, DLevel &c, int
 }
 
 // ----------------------------------------------------------------- refinement (block versions)
-__device__ __noinline__ void blk_gains(Ctx &x, const DLevel &L, const uint8_t *side) {
-    int *n1 = x.e_d;
-    blk_fill(n1, (size_t)L.E, 0);
-    blk_fill(x.gain, (size_t)L.N, 0);
+// Weighted degree D[v] = sum of w_e over v's hyperedges, once per level (load-balanced over the
+// incidence, one atomic per run).
+__device__ __noinline__ void blk_wdeg(Ctx &x, const DLevel &L) {
+    blk_fill(x.dw, (size_t)L.N, 0);
     __syncthreads();
-    if (L.P > 0) d_hedge_n1(x.t, L.E, L.P, L.hoff, L.pins, side, n1);
+    if (L.P > 0) {
+        const int *hw = L.hw;
+        lb_for_each_items<int>(
+            L.noff, L.N, L.P, L.nadj, 0, [&](int, int e, int acc) { return acc + (hw ? hw[e] : 1); },
+            [&](int v, int acc) {
+                if (acc) atomicAdd(x.dw + v, acc);
+            },
+            x.t);
+    }
     __syncthreads();
-    d_hedge_contrib(x.t, L.E, L.hoff, L.hw, n1, x.hc);
+}
+
+// Algorithm 4's gains regrouped: an uncut hyperedge gives -w_e to each of its pins and a cut one
+// gives +w_e to a pin alone on its side and 0 to the others, so gain[v] = -D[v] + sum over v's
+// cut hyperedges of w_e (1 + [v alone on its side]) -- the same integers, with only the cut
+// hyperedges touching the gains.  Hyperedges of up to 32 pins take one thread (counting, then
+// scattering), larger ones a warp.
+__device__ __noinline__ void blk_gains_cut(Ctx &x, const DLevel &L, const uint8_t *side) {
+    for (int v = threadIdx.x; v < L.N; v += blockDim.x) x.gain[v] = -x.dw[v];
     __syncthreads();
-    if (L.P > 0) d_node_gain(x.t, L.N, L.P, L.noff, L.nadj, x.hc, side, x.gain);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    for (int e0 = warp * 32; e0 < L.E; e0 += warps * 32) {
+        const int e = e0 + lane;
+        int a = 0, d = 0;
+        if (e < L.E) {
+            a = L.hoff[e];
+            d = L.hoff[e + 1] - a;
+        }
+        const bool small = e < L.E && d <= 32;
+        if (small) {
+            int n1 = 0;
+            for (int i = 0; i < d; ++i) n1 += side[L.pins[a + i]];
+            if (n1 > 0 && n1 < d) {
+                const int w = L.hw ? L.hw[e] : 1;
+                for (int i = 0; i < d; ++i) {
+                    const int v = L.pins[a + i];
+                    const int mine = side[v] ? n1 : d - n1;
+                    atomicAdd(x.gain + v, mine == 1 ? 2 * w : w);
+                }
+            }
+        }
+        unsigned big = __ballot_sync(0xffffffffu, e < L.E && !small);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int eb = e0 + src, ab = L.hoff[eb], db = L.hoff[eb + 1] - ab;
+            int n1 = 0;
+            for (int i = lane; i < db; i += 32) n1 += side[L.pins[ab + i]];
+            n1 = __reduce_add_sync(0xffffffffu, n1);
+            if (n1 > 0 && n1 < db) {
+                const int w = L.hw ? L.hw[eb] : 1;
+                for (int i = lane; i < db; i += 32) {
+                    const int v = L.pins[ab + i];
+                    const int mine = side[v] ? n1 : db - n1;
+                    atomicAdd(x.gain + v, mine == 1 ? 2 * w : w);
+                }
+            }
+        }
+    }
     __syncthreads();
 }
 
@@ -240,7 +294,7 @@ __device__ __noinline__ void blk_initial(Ctx &x, const DLevel &L, uint8_t *side,
     if (threadIdx.x == 0) d_initial_cond(st, (long long)L.N + 1, x.status, true, m0, m);
     __syncthreads();
     while (st->flag) {
-        blk_gains(x, L, side);
+        blk_gains_cut(x, L, side);
         blk_select_apply(x, L, SEL_INITIAL, s, side);
         if (threadIdx.x == 0) d_initial_cond(st, (long long)L.N + 1, x.status, false, m0, m);
         __syncthreads();
@@ -255,7 +309,7 @@ __device__ __noinline__ void blk_rebalance(Ctx &x, const DLevel &L, uint8_t *sid
     if (threadIdx.x == 0) d_rebal_cond(st, limit0, limit1, (long long)L.N + 1, x.status, true);
     __syncthreads();
     while (st->flag) {
-        blk_gains(x, L, side);
+        blk_gains_cut(x, L, side);
         blk_select_apply(x, L, SEL_REBAL, s, side);
         d_rebal_move(x.gain, side, L.nw, x.list, st, s, reinterpret_cast<unsigned long long *>(x.smem));
         __syncthreads();
@@ -308,6 +362,7 @@ __device__ __noinline__ int blk_bisect(Ctx &x, DLevel *lev, const BInst &I, unsi
         ++nl;
     }
     uint8_t *cur = x.side_a, *other = x.side_b;
+    if (lev[nl - 1].N > 0) blk_wdeg(x, lev[nl - 1]);
     blk_initial(x, lev[nl - 1], cur, m0, m);
     for (int l = nl - 1; l >= 0; --l) {
         const DLevel &L = lev[l];
@@ -318,9 +373,10 @@ __device__ __noinline__ int blk_bisect(Ctx &x, DLevel *lev, const BInst &I, unsi
             cur = other;
             other = tmp;
         }
+        if (L.N > 0 && l < nl - 1) blk_wdeg(x, L);  // the coarsest level's came with Algorithm 3
         for (int it = 0; it < I.iters; ++it) {
             if (L.N == 0) break;
-            blk_gains(x, L, cur);
+            blk_gains_cut(x, L, cur);
             blk_select_apply(x, L, SEL_REFINE, 0, cur);
         }
         if (L.N > 0) blk_rebalance(x, L, cur, lim0, lim1);
@@ -404,12 +460,12 @@ __device__ int blk_solve(Ctx &x, const BArgs &a, const BInst &I, DLevel *lev, in
     x.e_c = x.ar.take<int>(E);
     x.e_d = x.ar.take<int>(E);
     x.e_key = x.ar.take<unsigned long long>(E);
-    x.hc = x.ar.take<int2>(E);
     x.n_a = x.ar.take<int>(N);
     x.n_b = x.ar.take<int>(N);
     x.n_c = x.ar.take<int>(N);
     x.n_key = x.ar.take<unsigned long long>(N);
     x.gain = x.ar.take<int>(N);
+    x.dw = x.ar.take<int>(N);
     x.side_a = x.ar.take<uint8_t>(N);
     x.side_b = x.ar.take<uint8_t>(N);
     x.grp = x.ar.take<signed char>(N);
