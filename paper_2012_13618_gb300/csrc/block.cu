@@ -76,7 +76,7 @@ int bucket_of(int64_t P) {
 // for k > 2, the part vector, node maps and one subgraph's level store); instances above the
 // arena given to their bucket are deferred by the device.
 size_t arena_estimate(int64_t N, int64_t E, int64_t P, int k) {
-    const int64_t level0 = 4 * (E + 1) + 4 * E + 4 * P + 4 * N + 4 * (N + 1) + 4 * P + 8 * N;
+    const int64_t level0 = 4 * (E + 1) + 4 * E + 4 * P + 4 * N + 4 * (N + 1) + 4 * P + 8 * N + P / 32 + 16;
     const int64_t scratch = E * (4 * 4 + 8) + N * (4 * 3 + 8 + 4 + 4 + 3) + 4 * P + 64 * 1024;
     const int64_t kway = k > 2 ? 16 * N + level0 : 0;
     return (size_t)(scratch + 5 * level0 + kway + (4 << 20));

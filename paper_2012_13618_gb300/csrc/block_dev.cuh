@@ -33,6 +33,7 @@ struct BArgs {
 struct DLevel {
     int N, E, P;
     int *hoff, *pins, *hw, *nw, *noff, *nadj, *cmap, *match;
+    int *tsh, *tsn;  // tile-start tables of the hyperedge and incidence CSRs (lb.cuh)
 };
 
 namespace {
@@ -92,14 +93,18 @@ __device__ __noinline__ void blk_dedup(Ctx &x, int E, const int *hoff, const int
 }
 
 // The compacted hyperedge CSR of `c` (hyperedges whose e_a count is >= 2, their pins from p_a,
-// weights carried) with the degrees of c's c.N nodes counted into n_a.  False on arena overflow.
-__device__ __noinline__ bool blk_compact(Ctx &x, int E, int P, const int *hoff, const int *hw, DLevel &c) {
+// weights carried, its tile-start table written on the way) with the degrees of c's c.N nodes
+// counted into n_a.  ts: the tile starts of the input CSR (null for a raw input).  False on arena
+// overflow.
+__device__ __noinline__ bool blk_compact(Ctx &x, int E, int P, const int *hoff, const int *hw, DLevel &c,
+                                         const int *ts) {
     int *cnt = x.e_a, *emap = x.e_b, *counters = x.cnt4;
     c.hoff = x.ar.take<int>((size_t)E + 1);
     c.hw = hw ? x.ar.take<int>((size_t)E) : nullptr;
+    c.tsh = x.ar.take<int>((size_t)P / kTsGran + 2);  // the compacted level has at most P pins
     if (x.ar.overflow) return false;
     if (E > 0) {
-        block_scan_items(E, CompactIn{cnt}, CompactOut{E, hw, c.hoff, c.hw, emap, counters + 2, nullptr});
+        block_scan_items(E, CompactIn{cnt}, CompactOut{E, hw, c.hoff, c.hw, emap, counters + 2, c.tsh});
     } else if (threadIdx.x == 0) {
         c.hoff[0] = 0;
         counters[2] = counters[3] = 0;
@@ -111,7 +116,7 @@ __device__ __noinline__ bool blk_compact(Ctx &x, int E, int P, const int *hoff, 
     if (x.ar.overflow) return false;
     blk_fill(x.n_a, (size_t)c.N, 0);  // degree counters of the compacted level
     __syncthreads();
-    if (P > 0) d_seg_copy(x.t, E, P, hoff, x.p_a, cnt, emap, c.hoff, c.pins, x.n_a);
+    if (P > 0) d_seg_copy(x.t, E, P, hoff, x.p_a, cnt, emap, c.hoff, c.pins, x.n_a, ts);
     __syncthreads();
     return true;
 }
@@ -122,11 +127,12 @@ __device__ __noinline__ bool blk_incidence(Ctx &x, DLevel &c) {
     c.nadj = x.ar.take<int>((size_t)c.P);
     c.cmap = x.ar.take<int>((size_t)c.N);
     c.match = x.ar.take<int>((size_t)c.N);
+    c.tsn = x.ar.take<int>((size_t)c.P / kTsGran + 2);
     if (x.ar.overflow) return false;
-    if (c.N > 0) block_scan_items(c.N, DegIn{x.n_a}, DegOut{c.N, c.noff, x.n_b, nullptr});
+    if (c.N > 0) block_scan_items(c.N, DegIn{x.n_a}, DegOut{c.N, c.noff, x.n_b, c.tsn});
     else if (threadIdx.x == 0) c.noff[0] = 0;
     __syncthreads();
-    if (c.P > 0) d_fill_adj(x.t, c.E, c.P, c.hoff, c.pins, x.n_b, c.nadj);
+    if (c.P > 0) d_fill_adj(x.t, c.E, c.P, c.hoff, c.pins, x.n_b, c.nadj, c.tsh);
     __syncthreads();
     return true;
 }
@@ -143,14 +149,14 @@ __device__ __noinline__ bool blk_coarsen(Ctx &x, const DLevel &f, DLevel &c, int
     blk_fill(rep, (size_t)E, 0xffffffffu);
     blk_fill(x.n_key, (size_t)N, ~0ull);
     __syncthreads();
-    if (f.P > 0) d_match_min(x.t, N, f.P, f.noff, f.nadj, hkey, x.n_key);
+    if (f.P > 0) d_match_min(x.t, N, f.P, f.noff, f.nadj, hkey, x.n_key, f.tsn);
     __syncthreads();
     d_match_set(x.t, N, x.n_key, f.nw, f.match, ssize, sweight);
     __syncthreads();
     unsigned long long *best = hkey;  // the hyperedge keys are no longer needed
     blk_fill(best, (size_t)E, ~0ull);
     __syncthreads();
-    if (f.P > 0) d_single_best(x.t, E, f.P, f.hoff, f.pins, f.match, ssize, sweight, best);
+    if (f.P > 0) d_single_best(x.t, E, f.P, f.hoff, f.pins, f.match, ssize, sweight, best, f.tsh);
     __syncthreads();
     d_group(x.t, N, f.match, ssize, best, grp, rep);
     __syncthreads();
@@ -165,7 +171,7 @@ __device__ __noinline__ bool blk_coarsen(Ctx &x, const DLevel &f, DLevel &c, int
     d_cmap(x.t, N, grp, gcid, f.nw, f.cmap, c.nw);
     __syncthreads();
     blk_dedup<true>(x, E, f.hoff, f.pins, f.cmap);
-    if (!blk_compact(x, E, f.P, f.hoff, f.hw, c)) return false;
+    if (!blk_compact(x, E, f.P, f.hoff, f.hw, c, f.tsh)) return false;
     return blk_incidence(x, c);
 }
 
@@ -182,7 +188,7 @@ __device__ __noinline__ void blk_wdeg(Ctx &x, const DLevel &L) {
             [&](int v, int acc) {
                 if (acc) atomicAdd(x.dw + v, acc);
             },
-            x.t);
+            x.t, L.tsn);
     }
     __syncthreads();
 }
@@ -492,7 +498,7 @@ __device__ int blk_solve(Ctx &x, const BArgs &a, const BInst &I, DLevel *lev, in
     DLevel G;
     G.N = N;
     blk_dedup<false>(x, E, hoff, pins, nullptr);
-    if (!blk_compact(x, E, P, hoff, hw, G)) return 2;
+    if (!blk_compact(x, E, P, hoff, hw, G, nullptr)) return 2;
     G.nw = x.ar.take<int>(N);
     if (x.ar.overflow) return 2;
     for (int v = threadIdx.x; v < N; v += blockDim.x) G.nw[v] = I.nw >= 0 ? a.nw[I.nw + v] : 1;
@@ -529,7 +535,7 @@ __device__ int blk_solve(Ctx &x, const BArgs &a, const BInst &I, DLevel *lev, in
         if (S.N == 0) continue;
         S.nw = x.snw;
         blk_split_nets(x, G);
-        if (!blk_compact(x, G.E, G.P, G.hoff, G.hw, S)) return 2;
+        if (!blk_compact(x, G.E, G.P, G.hoff, G.hw, S, G.tsh)) return 2;
         if (!blk_incidence(x, S)) return 2;
         lev[0] = S;
         const int q0 = (r.y + 1) / 2;
