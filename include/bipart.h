@@ -135,6 +135,16 @@ void bipart_destroy(bipart_handle h);
 /* Text of the last error on the calling thread ("" if none). */
 const char *bipart_last_error(void);
 
+/* Sec. 3.4 without the coarsening: re-runs the initial bisection (Algorithm 3) of the coarsest
+ * level and the refinement and rebalancing (Algorithms 4-5) back to level 0 on the hierarchy the
+ * handle's last partition built, with a new imbalance `epsilon` and `refine_iters` iterations;
+ * the policy, levels and flags stay those of that call.  Requires that the last partition of the
+ * handle had k = 2 (else BIPART_ERR_INVALID_ARG).  Coarsening depends on neither parameter, so
+ * the result equals bipart_partition with the same k = 2, policy, levels and the new epsilon and
+ * refine_iters.  out_parts: HOST, num_nodes entries.  Runs eagerly (no launch plan); the kept
+ * hierarchy stays valid.  Used by design-space sweeps over refinement settings (Sec. 4.3). */
+int bipart_refine_kept(bipart_handle h, double epsilon, int32_t refine_iters, int32_t *out_parts);
+
 /* ---- Many independent hypergraphs on one GPU -------------------------------------------- */
 /* One hypergraph in HOST memory (same conventions as bipart_create); the caller keeps the arrays
  * alive until the call that uses them has returned (batch) or been waited for (server). */

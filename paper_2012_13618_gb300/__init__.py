@@ -66,6 +66,7 @@ SYMBOLS = {
     "bipart_partition_device": (ctypes.c_int, [_vp, _i32, ctypes.c_double, _i32, _i32, _i32, _vp]),
     "bipart_partition_ex": (ctypes.c_int, [_vp, _vp, _vp]),
     "bipart_plan_active": (ctypes.c_int, [_vp, _vp]),
+    "bipart_refine_kept": (ctypes.c_int, [_vp, ctypes.c_double, _i32, _vp]),
     "bipart_partition_device_ex": (ctypes.c_int, [_vp, _vp, _vp]),
     "bipart_num_levels": (ctypes.c_int, [_vp, _p32]),
     "bipart_get_level": (ctypes.c_int, [_vp, _i32, _p32, _p32, _p32, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -263,6 +264,14 @@ class Handle:
         return _check(load().bipart_partition_device(self._h, int(k), float(eps), _policy(policy),
                                                      int(levels), int(iters),
                                                      ctypes.c_void_p(out.data_ptr())))
+
+    def refine_kept(self, eps=0.1, iters=2):
+        """bipart_refine_kept: Algorithm 3 and the refinement again on the hierarchy of the last
+        k = 2 partition, with a new imbalance and iteration count.  Returns (parts, status)."""
+        N = self.sizes()[0]
+        out = np.empty(max(N, 1), np.int32)
+        st = _check(load().bipart_refine_kept(self._h, float(eps), int(iters), _ptr(out)))
+        return out[:N], st
 
     def plan_active(self) -> bool:
         """Whether the last partition call replayed a captured CUDA graph (diagnostics)."""

@@ -646,6 +646,7 @@ void bisect_body(bipart_graph *g, Level &L0, const Params &p, int64_t W, uint8_t
         levels.push_back(&c);
         if (to_tail) tail_from = (int)levels.size() - 1;
     }
+    g->last_tail_from = tail_from;
     if (tail_from >= 0) {
         // the tail leaves the side of its starting level in side_a, sized for level 0 here so
         // that uncoarsen() finds it in place
@@ -805,6 +806,44 @@ int bisect_top(bipart_graph *g, const Params &p, uint8_t *d_side, int *nlev) {
     return st;
 }
 
+// Sec. 3.4 without the coarsening: Algorithm 3 on the coarsest kept level, then refinement and
+// rebalancing back to level 0 with `iters` iterations and imbalance e6, on the hierarchy the
+// handle's last k = 2 bisection built (its levels are kept).  Coarsening depends on neither
+// quantity, so the result equals a full bisection with them.  Runs eagerly.
+int refine_kept(bipart_graph *g, int64_t e6, int32_t iters, int *d_parts) {
+    if (!g->hier.valid) throw Fail{BIPART_ERR_INVALID_ARG, "no k = 2 hierarchy kept (partition with k = 2 first)"};
+    Params p = g->hier.params;
+    p.e6 = e6;
+    p.iters = iters;
+    Level &L0 = g->L0;
+    if (L0.N == 0) return BIPART_OK;
+    cudaStream_t s = g->stream;
+    BP_CUDA(cudaMemsetAsync(dev_status(g), 0, sizeof(uint32_t), s));
+    BP_CUDA(cudaMemsetAsync(g->w.small.p, 0, small_state_bytes(), s));
+    g->w.scan.reset(s);
+    const int tail_from = g->hier.tail_from;
+    // the grid levels (the tail rebuilds its own from its starting level, identically)
+    const int grid_levels = tail_from >= 0 ? tail_from + 1 : g->hier.nlev;
+    std::vector<Level *> levels{&L0};
+    for (int l = 1; l < grid_levels; ++l) levels.push_back(g->lev[(size_t)l - 1].get());
+    const int64_t W = g->total_node_weight;
+    const int64_t limit[2] = {balance_limit(W, p.m0, p.m, p.e6), balance_limit(W, p.m - p.m0, p.m, p.e6)};
+    uint8_t *d_side = (uint8_t *)g->side_out.ensure((size_t)L0.N, s);
+    if (tail_from >= 0) {
+        g->w.side_b.ensure((size_t)std::max(L0.N, 1), s);
+        uint8_t *sa = (uint8_t *)g->w.side_a.ensure((size_t)std::max(L0.N, 1), s);
+        run_tail(g, levels, p, limit, sa);
+    }
+    if ((int)levels.size() != g->hier.nlev) throw Fail{BIPART_ERR_CUDA, "kept hierarchy changed size"};
+    uncoarsen(g, levels, limit, p.m0, p.m, p.iters, d_side, tail_from);
+    int st = read_bisect_status(g);
+    k_side_to_part<<<grid_for(L0.N), kBlock, 0, s>>>(L0.N, d_side, nullptr, 0, p.m0, d_parts);
+    BP_LAUNCH();
+    sync(g);
+    check_status(g);
+    return st;
+}
+
 // Nested k-way (Algorithm 6; readings C16, G1-G2 for any k): the subgraph owning the parts
 // [lo, lo + m) is bisected with side 0 meant for ceil(m / 2) of them; its nodes carry lo as
 // their part until their range holds one part.  Ranges of one tree level are bisected one after
@@ -835,6 +874,8 @@ int partition_device(bipart_graph *g, const Params &p, int *d_parts) {
     if (p.k == 2) {
         g->hier.nlev = nlev;
         g->hier.valid = true;
+        g->hier.tail_from = g->last_tail_from;
+        g->hier.params = top;
         sync(g);
         return status;
     }
@@ -1498,6 +1539,22 @@ int bipart_partition_device_ex(bipart_handle h, const bipart_params *params, int
         const bipart_params &q = *params;
         return partition_to_device(h, make_params(q.k, q.epsilon, q.policy, q.levels, q.refine_iters, q.flags),
                                    d_out_parts);
+    });
+}
+
+int bipart_refine_kept(bipart_handle h, double epsilon, int32_t refine_iters, int32_t *out_parts) {
+    if (!h || (!out_parts && h->L0.N > 0)) { set_error("NULL argument"); return BIPART_ERR_INVALID_ARG; }
+    HandleScope hs(h);
+    return guard([&]() {
+        if (!h->hier.valid) throw Fail{BIPART_ERR_INVALID_ARG, "no k = 2 hierarchy kept (partition with k = 2 first)"};
+        const Params &q = h->hier.params;
+        const Params p = make_params(2, epsilon, q.policy, q.levels, refine_iters, q.flags);
+        const int32_t N = h->L0.N;
+        int *d = (int *)h->part_b.ensure(sizeof(int) * (size_t)std::max(N, 1), h->stream);
+        const int st = refine_kept(h, p.e6, p.iters, d);
+        if (N > 0) BP_CUDA(cudaMemcpyAsync(out_parts, d, sizeof(int) * (size_t)N, cudaMemcpyDeviceToHost, h->stream));
+        sync(h);
+        return st;
     });
 }
 

@@ -202,6 +202,8 @@ Params make_params(int32_t k, double eps, int32_t policy, int32_t levels, int32_
 struct Hierarchy {
     int32_t nlev = 0;
     bool valid = false;
+    int32_t tail_from = -1;  // first level the cluster tail built (-1: none)
+    Params params;           // the bisection that built it
 };
 
 // How the host driver executes: eagerly (reading sizes back, optionally recording them), or
@@ -352,6 +354,7 @@ struct bipart_graph {
     // free what a request no longer needs as soon as it can (workers of a server under an HBM
     // budget): with one lane, the top bisection's coarse levels before the subgraphs'
     bool lean = false;
+    int32_t last_tail_from = -1;  // tail start of the last bisection run on the host (eager or captured)
     ~bipart_graph();
 };
 

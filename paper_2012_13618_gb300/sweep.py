@@ -2,16 +2,19 @@
 coarsening levels, refinement iterations and matching policy, and the Pareto frontier of
 (run time, cut).  Because every configuration is deterministic, the frontier is reproducible.
 
-The partitions of all configurations are computed together as one batch (they are independent
-instances of the same hypergraph); each configuration's run time is then measured alone on a
-resident handle (warm: the launch plan of that configuration is captured first).
+The hypergraph is uploaded once.  Coarsening depends only on (levels, policy), so the partitions
+of one (levels, policy) group share one hierarchy: its first configuration partitions in full and
+the others re-run only Algorithm 3 and the refinement on the kept levels (bipart_refine_kept),
+which gives the same partitions.  Each configuration's run time is then measured alone on the
+resident handle as a full bisection (warm: the launch plan of that configuration is captured
+first).
 """
 from __future__ import annotations
 
 import itertools
 import time
 
-from . import Handle, create_from, partition_batch
+from . import create_from
 
 
 def pareto(points):
@@ -30,11 +33,24 @@ def sweep(g, levels=(5, 10, 25), iters=(0, 1, 2, 4), policies=("LDH", "HDH", "RA
           k=2, time_each=True, repeats=3, workers=0):
     """Returns (results, frontier): results = list of dicts (levels, iters, policy, cut, status,
     ms), frontier = indices of the Pareto-optimal results."""
+    if k != 2:
+        raise ValueError("the sweep runs bisections (k = 2)")
     configs = [dict(k=k, eps=eps, policy=p, levels=l, iters=i)
                for p, l, i in itertools.product(policies, levels, iters)]
-    parts, st = partition_batch([g] * len(configs), configs, workers=workers)
     results = []
     with create_from(g) as h:
+        # partitions: one coarsening per (levels, policy) group, the other iteration counts on
+        # the kept hierarchy
+        parts, st = [], []
+        for pol, lev in itertools.product(policies, levels):
+            group = [c for c in configs if c["policy"] == pol and c["levels"] == lev]
+            for j, c in enumerate(group):
+                if j == 0:
+                    pp, ss = h.partition(k, eps, pol, lev, c["iters"])
+                else:
+                    pp, ss = h.refine_kept(eps, c["iters"])
+                parts.append(pp)
+                st.append(ss)
         for c, p, s in zip(configs, parts, st):
             r = dict(levels=c["levels"], iters=c["iters"], policy=c["policy"], cut=h.cut(p),
                      status=int(s), parts=p, ms=None)

@@ -309,3 +309,28 @@ def test_server_micro_batches_a_backlog_exactly():
             assert qms >= 0 and rms >= 0
         batches, batched = srv.stats()
     assert batches >= 1 and batched >= 8
+
+
+def test_refine_kept_equals_full_bisections():
+    # Algorithm 3 and the refinement re-run on a kept hierarchy give what a full bisection with
+    # the new imbalance and iteration count gives: with the cluster tail starting partway down
+    # (netlist) and from level 0 (small uniform hypergraph)
+    import paper_2012_13618_gb300 as bp
+    cases = [(synth.c1_netlist(N=100_000), "LDH", 25), (synth.uniform(3000, 3500, 2, 7, seed=71), "RAND", 3)]
+    for g, pol, lev in cases:
+        hr = oracle.Hypergraph.from_dict(g)
+        with bp.create_from(g) as h:
+            h.partition(2, 0.05, pol, lev, 2)
+            for eps, it in ((0.05, 0), (0.05, 4), (0.1, 1), (0.0, 2)):
+                parts, st = h.refine_kept(eps, it)
+                ref = oracle.bisect(hr, eps, pol, lev, it, keep_levels=False)
+                assert np.array_equal(parts, ref["side"].astype(np.int32)), (pol, eps, it)
+                assert st == ref["status"], (pol, eps, it)
+            # the handle's full path is unaffected (its plan is captured and replayed afterwards)
+            for _ in range(3):
+                parts, st = h.partition(2, 0.1, pol, lev, 1)
+            ref = oracle.bisect(hr, 0.1, pol, lev, 1, keep_levels=False)
+            assert np.array_equal(parts, ref["side"].astype(np.int32))
+            h.partition(4, 0.05, pol, lev, 2)
+            with pytest.raises(bp.BipartError):
+                h.refine_kept(0.05, 2)
