@@ -16,7 +16,9 @@ namespace bp {
 constexpr int kMaxLev = 64;               // levels a block keeps (instances asking more: grid path)
 constexpr int kMaxStack = 64;             // pending part ranges of the nested k-way recursion
 constexpr int kBlockMaxK = 1024;          // largest k run inside a block
-constexpr size_t kSmemBytes = 32 * 1024;  // union: bitmap window / gain histogram / sort keys
+constexpr size_t kSmemBytes = 32 * 1024;  // union: bitmap window / gain histogram / sort keys /
+                                          // a small level's degree counters or fill cursors
+constexpr int kPrivNodes = (int)(kSmemBytes / sizeof(int));
 
 struct BArgs {
     BInst *inst;
@@ -114,10 +116,18 @@ __device__ __noinline__ bool blk_compact(Ctx &x, int E, int P, const int *hoff, 
     c.P = counters[3];
     c.pins = x.ar.take<int>((size_t)c.P);
     if (x.ar.overflow) return false;
-    blk_fill(x.n_a, (size_t)c.N, 0);  // degree counters of the compacted level
+    // degree counters of the compacted level: in shared memory when its nodes fit (few nodes
+    // means many pins a node, whose atomics would queue on the same global words)
+    const bool priv = c.N <= kPrivNodes;
+    int *deg = priv ? reinterpret_cast<int *>(x.smem) : x.n_a;
+    blk_fill(deg, (size_t)c.N, 0);
     __syncthreads();
-    if (P > 0) d_seg_copy(x.t, E, P, hoff, x.p_a, cnt, emap, c.hoff, c.pins, x.n_a, ts);
+    if (P > 0) d_seg_copy(x.t, E, P, hoff, x.p_a, cnt, emap, c.hoff, c.pins, deg, ts);
     __syncthreads();
+    if (priv) {
+        for (int v = threadIdx.x; v < c.N; v += blockDim.x) x.n_a[v] = deg[v];
+        __syncthreads();
+    }
     return true;
 }
 
@@ -129,10 +139,12 @@ __device__ __noinline__ bool blk_incidence(Ctx &x, DLevel &c) {
     c.match = x.ar.take<int>((size_t)c.N);
     c.tsn = x.ar.take<int>((size_t)c.P / kTsGran + 2);
     if (x.ar.overflow) return false;
-    if (c.N > 0) block_scan_items(c.N, DegIn{x.n_a}, DegOut{c.N, c.noff, x.n_b, c.tsn});
+    // the fill's cursors in shared memory when the nodes fit (as the degree counters)
+    int *cursor = c.N <= kPrivNodes ? reinterpret_cast<int *>(x.smem) : x.n_b;
+    if (c.N > 0) block_scan_items(c.N, DegIn{x.n_a}, DegOut{c.N, c.noff, cursor, c.tsn});
     else if (threadIdx.x == 0) c.noff[0] = 0;
     __syncthreads();
-    if (c.P > 0) d_fill_adj(x.t, c.E, c.P, c.hoff, c.pins, x.n_b, c.nadj, c.tsh);
+    if (c.P > 0) d_fill_adj(x.t, c.E, c.P, c.hoff, c.pins, cursor, c.nadj, c.tsh);
     __syncthreads();
     return true;
 }
