@@ -409,6 +409,9 @@ class Pool {
         }
         try {
             BlockSet bs = block_set(ins, ps);
+            // under a budget the batch holds only what it was admitted for (buffers a larger
+            // earlier batch of this process left behind go first)
+            if (budget_) trim_block_batch();
             run_block_batch(bs.bi, bs.ho, bs.pi, bs.nw, bs.hw, outs);
             const Clock::time_point t1 = Clock::now();
             for (size_t i = 0; i < batch.size(); ++i) {

@@ -334,3 +334,18 @@ def test_refine_kept_equals_full_bisections():
             h.partition(4, 0.05, pol, lev, 2)
             with pytest.raises(bp.BipartError):
                 h.refine_kept(0.05, 2)
+
+
+def test_batch_release_then_reuse():
+    # the buffers, arenas, graph and pool the batch call keeps are freed, and the next call
+    # builds them again with the same results
+    import paper_2012_13618_gb300 as bp
+    graphs = mixed_instances(8, seed=77)
+    params = [dict(k=[2, 4][i % 2], eps=0.05, policy="LDH", levels=25, iters=2) for i in range(len(graphs))]
+    a, sa = bp.partition_batch(graphs, params, workers=2)
+    bp.batch_release()
+    b, sb = bp.partition_batch(graphs, params, workers=2)
+    assert np.array_equal(sa, sb)
+    for x, y, g, p in zip(a, b, graphs, params):
+        ref, _ = oracle.partition(oracle.Hypergraph.from_dict(g), p["k"], 0.05, "LDH", 25, 2)
+        assert np.array_equal(x, ref) and np.array_equal(y, ref)
