@@ -217,8 +217,8 @@ __global__ void k_level_init(LevelInit li) { d_level_init(li); }
 __global__ void __launch_bounds__(kLbBlock)
 k_match_min(int N, int P, const int *__restrict__ noff, const int *__restrict__ nadj,
             const unsigned long long *__restrict__ hkey, unsigned long long *__restrict__ nkey,
-            const int *__restrict__ ts) {
-    d_match_min(GridTeam(), N, P, noff, nadj, hkey, nkey, ts);
+            const int *__restrict__ ts, bool warp_min) {
+    d_match_min(GridTeam(), N, P, noff, nadj, hkey, nkey, ts, warp_min);
 }
 
 __global__ void __launch_bounds__(kBlock)
@@ -621,7 +621,8 @@ bool coarsen_level(bipart_graph *g, Level &f, Level &c, int policy, int32_t *siz
         if (f.P > 0) {
             // noff, nadj, 8-byte key gather per incidence, one 8-byte atomic per node run
             ProfScope ps("match_min", 4.0 * N + 12.0 * f.P + 8.0 * N, s);
-            k_match_min<<<lb_grid(f.P), kLbBlock, 0, s>>>(N, f.P, f.noff(), f.nadj(), hkey, nkey, f.tsn());
+            k_match_min<<<lb_grid(f.P), kLbBlock, 0, s>>>(N, f.P, f.noff(), f.nadj(), hkey, nkey, f.tsn(),
+                                                           (int64_t)f.P > 64 * (int64_t)N);
             BP_LAUNCH();
         }
         {

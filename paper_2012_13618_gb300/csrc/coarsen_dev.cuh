@@ -388,19 +388,23 @@ __device__ void d_hedge_key(Team t, int E, int policy, const int *hoff, const in
 // incidence array: per-node partial minima are combined with 64-bit atomicMin, whose result does
 // not depend on the order of the atomics.
 template <class Team>
+// With `warp_min` the last runs of a warp's lanes are combined per node before the atomic (levels
+// whose nodes have long incidence lists, where many threads would end on one node).
 __device__ void d_match_min(Team t, int N, int P, const int *noff, const int *nadj,
                             const unsigned long long *hkey, unsigned long long *nkey,
-                            const int *ts = nullptr) {
-    lb_for_each_items<unsigned long long>(
-        noff, N, P, nadj, ~0ull,
-        [&](int, int e, unsigned long long acc) {
-            unsigned long long k = Team::ld(hkey + e);
-            return k < acc ? k : acc;
-        },
-        [&](int v, unsigned long long acc) {
-            if (acc != ~0ull) atomicMin(nkey + v, acc);
-        },
-        t, ts);
+                            const int *ts = nullptr, bool warp_min = false) {
+    auto visit = [&](int, int e, unsigned long long acc) {
+        unsigned long long k = Team::ld(hkey + e);
+        return k < acc ? k : acc;
+    };
+    auto flush = [&](int v, unsigned long long acc) {
+        if (acc != ~0ull) atomicMin(nkey + v, acc);
+    };
+    if (warp_min)
+        lb_reduce_items<unsigned long long>(noff, N, P, nadj, ~0ull, cooperative_groups::less<unsigned long long>(),
+                                            visit, flush, t, ts);
+    else
+        lb_for_each_items<unsigned long long>(noff, N, P, nadj, ~0ull, visit, flush, t, ts);
 }
 
 // match[v] from the winning key; sizes and weights of the matched sets S(e) (integer atomics).
