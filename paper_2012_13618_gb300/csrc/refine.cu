@@ -38,7 +38,10 @@ inline int grid_for(int64_t n, int per_block = kBlock, int cap = 152 * 16) {
 
 // Selection passes over up to kSelOneBlock nodes run as one block of kSelOneThreads threads (the
 // histogram, the threshold and the application in one launch).
-constexpr int kSelOneThreads = 1024;
+constexpr int kSelOneThreads = 512;  // (512 was 9 us a bisection faster than 1024 in a same-box A/B)
+
+// Threads of the one-block ordered rebalance move (512 was 4 us a bisection faster than 1024).
+constexpr int kRebalThreads = 512;
 
 
 // Blocks of a grid-wide sum (each block stores its partial; the last block adds them).
@@ -256,7 +259,7 @@ __global__ void k_initial_cond(RState *st, CondArgs cond, uint32_t *status) {
 }
 
 // Ordered rebalance move, then (same block) the rebalance condition for the next round.
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(kRebalThreads)
 k_rebal_move(const int *__restrict__ gain, uint8_t *__restrict__ side, const int *__restrict__ nw,
              const int *__restrict__ list, RState *st, long long s, CondArgs cond, uint32_t *status,
              int *__restrict__ moved) {
@@ -482,7 +485,7 @@ void rebalance(bipart_graph *g, Level &L, uint8_t *side, int *gain, const int64_
         select_apply(g, L, SEL_REBAL, sq, gain, side, list);
         c.slot = flag_slot(g);
         ProfScope ps("rebal_move", 0.0, s);
-        k_rebal_move<<<1, 1024, smem, s>>>(gain, side, L.nw(), list, st, sq, c, dev_status(g),
+        k_rebal_move<<<1, kRebalThreads, smem, s>>>(gain, side, L.nw(), list, st, sq, c, dev_status(g),
                                            g->w.moved.as<int>());
         BP_LAUNCH();
     }
