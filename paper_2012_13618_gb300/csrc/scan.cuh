@@ -14,9 +14,15 @@
 
 namespace bp {
 
-constexpr int kScanBlock = 256;
-constexpr int kScanItems = 8;
+// Grid scans: tiles of 2048 items, two per thread of a 1024-thread block (a same-box A/B on the
+// 1M-node bisection: 256 x 8 took 2.652 ms, 512 x 4 2.568, 512 x 2 2.555, 1024 x 2 2.548 -- more
+// warps to cover each tile's loads and look-back, shorter per-thread runs).
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 2;
 constexpr int kScanTile = kScanBlock * kScanItems;
+// One-block scans (block_scan_items) keep eight items per thread: there the block's own loop, not
+// the look-back, is the cost.
+constexpr int kBlockScanItems = 8;
 constexpr uint64_t kScanValMask = (1ull << 62) - 1;
 constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagPre = 2ull << 62;
@@ -135,26 +141,26 @@ k_scan(int64_t n, In in, Out out, unsigned long long *state, unsigned long long 
     }
 }
 
-// Exclusive scan over n items by one block: chunks of blockDim * kScanItems items, each thread
-// owning kScanItems consecutive ones; out(i, prefix, value) after all in() of the chunk.  Used
+// Exclusive scan over n items by one block: chunks of blockDim * kBlockScanItems items, each thread
+// owning kBlockScanItems consecutive ones; out(i, prefix, value) after all in() of the chunk.  Used
 // where a whole phase runs in one block (small levels; the persistent batch kernel).
 template <class In, class Out>
 __device__ void block_scan_items(int64_t n, In in, Out out) {
     __shared__ uint64_t red[33];
     uint64_t carry = 0;
-    const int64_t chunk = (int64_t)blockDim.x * kScanItems;
+    const int64_t chunk = (int64_t)blockDim.x * kBlockScanItems;
     for (int64_t base = 0; base < n; base += chunk) {
-        const int64_t i0 = base + (int64_t)threadIdx.x * kScanItems;
-        uint64_t v[kScanItems], sum = 0;
+        const int64_t i0 = base + (int64_t)threadIdx.x * kBlockScanItems;
+        uint64_t v[kBlockScanItems], sum = 0;
 #pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
+        for (int k = 0; k < kBlockScanItems; ++k) {
             v[k] = i0 + k < n ? (uint64_t)in(i0 + k) : 0ull;
             sum += v[k];
         }
         uint64_t total;
         uint64_t run = carry + block_exclusive_scan<uint64_t>(sum, red, &total);
 #pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
+        for (int k = 0; k < kBlockScanItems; ++k) {
             if (i0 + k < n) out(i0 + k, run, v[k]);
             run += v[k];
         }
