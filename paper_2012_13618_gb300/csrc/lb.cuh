@@ -21,7 +21,10 @@
 namespace bp {
 
 constexpr int kLbBlock = 256;
-constexpr int kLbItems = 8;
+// Items per thread: 4 (one 16-byte load).  A same-box A/B on the 1M-node bisection: 8 items took
+// 2.571 ms, 4 items 2.481, 2 items 2.588 -- the gathers of these loops are latency-bound, and a
+// shorter per-thread run puts twice the warps on them.
+constexpr int kLbItems = 4;
 constexpr int kLbTile = kLbBlock * kLbItems;
 constexpr int kWarpTile = 32 * kLbItems;
 
@@ -135,21 +138,19 @@ __device__ __forceinline__ void lb_schedule(const int *off, int nseg, int total,
 }
 
 // Segmented reduction over a CSR for a visit that reads one int per item: items[j] is loaded
-// for all of the thread's slots up front (two 16-byte loads when its kLbItems slots are in range
+// for all of the thread's slots up front (one 16-byte load when its kLbItems slots are in range
 // and aligned); visit(seg, items[j], acc) folds it in and flush(seg, acc) ends every segment run
 // of the thread.  `init` is the identity of the combine operation.
 template <class Acc, class Visit, class Flush, class Team = GridTeam>
 __device__ __forceinline__ void lb_for_each_items(const int *off, int nseg, int total, const int *items,
                                                   Acc init, Visit visit, Flush flush, Team t = Team(),
                                                   const int *ts = nullptr) {
-    static_assert(kLbItems == 8, "two int4 loads per thread");
+    static_assert(kLbItems == 4, "one int4 load per thread");
     lb_schedule(off, nseg, total, ts, t, [&](int j, int n, int s, auto end) {
         int it[kLbItems];
         if (n == kLbItems && ((reinterpret_cast<uintptr_t>(items + j) & 15) == 0)) {
             const int4 a = Team::ld(reinterpret_cast<const int4 *>(items + j));
-            const int4 b = Team::ld(reinterpret_cast<const int4 *>(items + j) + 1);
             it[0] = a.x; it[1] = a.y; it[2] = a.z; it[3] = a.w;
-            it[4] = b.x; it[5] = b.y; it[6] = b.z; it[7] = b.w;
         } else {
 #pragma unroll
             for (int k = 0; k < kLbItems; ++k) it[k] = k < n ? Team::ld(items + j + k) : 0;
@@ -180,14 +181,12 @@ template <class Acc, class Op, class Visit, class Flush, class Team = GridTeam>
 __device__ __forceinline__ void lb_reduce_items(const int *off, int nseg, int total, const int *items,
                                                 Acc init, Op op, Visit visit, Flush flush,
                                                 Team t = Team(), const int *ts = nullptr) {
-    static_assert(kLbItems == 8, "two int4 loads per thread");
+    static_assert(kLbItems == 4, "one int4 load per thread");
     lb_schedule(off, nseg, total, ts, t, [&](int j, int n, int s, auto end) {
         int it[kLbItems];
         if (n == kLbItems && ((reinterpret_cast<uintptr_t>(items + j) & 15) == 0)) {
             const int4 a = Team::ld(reinterpret_cast<const int4 *>(items + j));
-            const int4 b = Team::ld(reinterpret_cast<const int4 *>(items + j) + 1);
             it[0] = a.x; it[1] = a.y; it[2] = a.z; it[3] = a.w;
-            it[4] = b.x; it[5] = b.y; it[6] = b.z; it[7] = b.w;
         } else {
 #pragma unroll
             for (int k = 0; k < kLbItems; ++k) it[k] = k < n ? Team::ld(items + j + k) : 0;
