@@ -627,7 +627,7 @@ void bisect_body(bipart_graph *g, Level &L0, const Params &p, int64_t W, uint8_t
     const int64_t limit[2] = {balance_limit(W, p.m0, p.m, p.e6), balance_limit(W, p.m - p.m0, p.m, p.e6)};
     // Levels are coarsened by the grid kernels until one is small enough for the cluster tail,
     // which then runs the rest of the bisection down to that level in one launch.
-    int tail_from = tail_eligible(L0, p.levels, p.flags) ? 0 : -1;
+    int tail_from = g->allow_tail && tail_eligible(L0, p.levels, p.flags) ? 0 : -1;
     bool init_done = false;  // the next level's key and reset pass already ran
     while (tail_from < 0 && (int)levels.size() - 1 < p.levels) {
         Level &f = *levels.back();
@@ -641,7 +641,8 @@ void bisect_body(bipart_graph *g, Level &L0, const Params &p, int64_t W, uint8_t
         bool to_tail = false;  // decided by coarsen_level, which then leaves c's incidence out
         init_done = coarsen_level(g, f, c, p.policy, level_sizes(g, (int)idx),
                                   (p.flags & BIPART_FLAG_MERGE_PARALLEL) != 0, init_done,
-                                  (int)idx + 1 < p.levels, tail_new, p.flags, &to_tail);
+                                  (int)idx + 1 < p.levels, tail_new, p.flags,
+                                  g->allow_tail ? &to_tail : nullptr);
         if (c.N == f.N) break;
         levels.push_back(&c);
         if (to_tail) tail_from = (int)levels.size() - 1;
@@ -743,10 +744,17 @@ int bisect_top(bipart_graph *g, const Params &p, uint8_t *d_side, int *nlev) {
     Plan &pl = g->plan;
     Exec &ex = g->ex;
     g->last_replayed = false;
+    // The cluster tail shortens an eager run (it replaces the small levels' host round trips),
+    // while a captured plan runs faster with every level on the grid.  So the first eager run of a
+    // parameter set may take the tail; the next one runs every level on the grid and is the
+    // recording a plan is captured from.
+    const bool have_rec = ex.rec_valid && same_params(ex.rec_params, p) && ex.rec_gen == g->gen;
     if (!(pl.valid && same_params(pl.params, p) && pl.gen == g->gen && pl.prof_epoch == prof_epoch())) {
         pl.reset();
-        if (ex.rec_valid && same_params(ex.rec_params, p) && ex.rec_gen == g->gen)
+        if (have_rec && !ex.rec_tail) {
+            g->allow_tail = false;
             capture_plan(g, p, d_side, ex.rec_nlev, ex.rec_kernels);
+        }
     }
     if (pl.valid) {
         // BIPART_TIMING: device time of the replay alone, on stderr (diagnostics)
@@ -784,6 +792,7 @@ int bisect_top(bipart_graph *g, const Params &p, uint8_t *d_side, int *nlev) {
         pl.reset();
         ex.rec_valid = false;
     }
+    g->allow_tail = !have_rec;
     ex.recording = true;
     ex.sizes.clear();
     ex.flags.clear();
@@ -803,6 +812,7 @@ int bisect_top(bipart_graph *g, const Params &p, uint8_t *d_side, int *nlev) {
     ex.rec_gen = g->gen;
     ex.rec_nlev = *nlev;
     ex.rec_kernels = kernels;
+    ex.rec_tail = g->last_tail_from >= 0;
     return st;
 }
 

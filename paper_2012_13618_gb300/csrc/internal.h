@@ -224,6 +224,7 @@ struct Exec {
     uint64_t rec_gen = 0;
     int rec_nlev = 0;
     int64_t rec_kernels = 0;
+    bool rec_tail = false;  // the recorded run used the cluster tail (not captured: see bisect_top)
 };
 
 struct Probe {
@@ -354,7 +355,8 @@ struct bipart_graph {
     // free what a request no longer needs as soon as it can (workers of a server under an HBM
     // budget): with one lane, the top bisection's coarse levels before the subgraphs'
     bool lean = false;
-    int32_t last_tail_from = -1;  // tail start of the last bisection run on the host (eager or captured)
+    int32_t last_tail_from = -1;
+    bool allow_tail = true;  // the next bisection may hand its coarse levels to the cluster tail  // tail start of the last bisection run on the host (eager or captured)
     ~bipart_graph();
 };
 
