@@ -106,7 +106,8 @@ int bipart_partition_device(bipart_handle h, int32_t k, double epsilon, int32_t 
 #define BIPART_FLAG_MERGE_PARALLEL 2
 
 /* Diagnostics: *active = 1 when the top-level bisection of the last partition call replayed a
- * captured CUDA graph (a handle captures one on the second call with the same parameters), 0
+ * captured CUDA graph (a handle captures one on the second call with the same parameters, or
+ * on the third when its first call handed the coarse levels to the cluster tail), 0
  * when it ran eagerly. */
 int bipart_plan_active(bipart_handle h, int32_t *active);
 
