@@ -113,7 +113,17 @@ def test_batch_and_server_argument_checks():
     assert lib.bipart_server_create(0, 2, None) == bp.ERR_INVALID_ARG
     assert lib.bipart_server_submit(None, None, None, None, None) == bp.ERR_INVALID_ARG
     assert lib.bipart_server_wait(None, 1, 0, None, None, None) == bp.ERR_INVALID_ARG
+    assert lib.bipart_server_stats(None, None, None) == bp.ERR_INVALID_ARG
     lib.bipart_server_destroy(None)
+    # tuning: bad sizes are rejected, an empty batch has nothing to tune
+    assert lib.bipart_batch_tune(-1, None, None, None) == bp.ERR_INVALID_ARG
+    assert lib.bipart_batch_tune(2, None, None, None) == bp.ERR_INVALID_ARG
+    chosen = np.full(8, 7, np.int32)
+    assert lib.bipart_batch_tune(0, None, None, ctypes.c_void_p(chosen.ctypes.data)) == bp.OK
+    assert not chosen.any()
+    lib.bipart_batch_release()  # nothing kept yet: a no-op
+    # refinement on a kept hierarchy needs a handle
+    assert lib.bipart_refine_kept(None, 0.1, 2, None) == bp.ERR_INVALID_ARG
 
 
 def test_params_validation_before_any_device_work():
