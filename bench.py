@@ -340,7 +340,9 @@ def run_gpu(args):
     value = ws * P / (ms_max / 1000.0)
     parts_dev = out.cpu().numpy()
 
-    # ---------------- end to end through the C ABI with host buffers
+    # ---------------- end to end through the C ABI with host buffers (the library's own device
+    # allocator, as a C caller gets it by default)
+    bp.use_default_allocator()
     e2e_steps = max(1, min(args.steps, 5))
     hoff_p = torch.from_numpy(g["hoff"]).pin_memory()
     pins_p = torch.from_numpy(g["pins"]).pin_memory()
@@ -437,8 +439,6 @@ def run_gpu(args):
                                  "GBps": (v[2] / (v[1] / 1000) / 1e9) if v[1] else None}
                             for k2, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
     h.close()
-    # the forms run on the library's host threads, which a Python allocator hook would serialise
-    bp.use_default_allocator()
     if rank == 0:
         if ws == 1 and not args.no_forms:
             # the two other forms of the metric, each with its plain-path comparison on the same

@@ -130,7 +130,11 @@ int bipart_cut(bipart_handle h, const int32_t *parts, int64_t *cut);
 /* Number of nodes / hyperedges / pins of the normalised level 0. */
 int bipart_sizes(bipart_handle h, int32_t *N, int32_t *E, int32_t *P);
 
-/* Releases every device buffer of the handle (on its stream). NULL is ignored. */
+/* Waits for the handle's work on its stream, then releases every device buffer of the handle.
+ * When all of them came from the library's own allocator, the release runs on a background
+ * thread of the library (on a stream of its own, so the caller may destroy its stream at once)
+ * and the memory returns to the library's pool shortly after the call returns; with an
+ * allocator hook (bipart_set_allocator) the hook's free is called here.  NULL is ignored. */
 void bipart_destroy(bipart_handle h);
 
 /* Text of the last error on the calling thread ("" if none). */

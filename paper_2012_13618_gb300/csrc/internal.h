@@ -28,6 +28,7 @@ struct AllocTag {
 };
 void *dev_alloc(size_t bytes, cudaStream_t s, AllocTag *tag);
 cudaMemPool_t lib_pool();  // the library's own memory pool on the current device (or null)
+bool release_later(bipart_graph *g);  // hands a finished handle to the background releaser
 void lib_pool_trim();      // returns the pool's unused memory to the driver
 void dev_free(void *p, size_t bytes, cudaStream_t s, const AllocTag &tag);
 void zero_fill(void *p, size_t bytes, cudaStream_t s);
@@ -355,6 +356,7 @@ struct bipart_graph {
     // free what a request no longer needs as soon as it can (workers of a server under an HBM
     // budget): with one lane, the top bisection's coarse levels before the subgraphs'
     bool lean = false;
+    bool ext_alloc = false;  // some buffer of this handle came from a bipart_set_allocator hook
     int32_t last_tail_from = -1;
     bool allow_tail = true;  // the next bisection may hand its coarse levels to the cluster tail  // tail start of the last bisection run on the host (eager or captured)
     ~bipart_graph();
