@@ -516,21 +516,6 @@ k_sub_copy(int E, const int *__restrict__ hoff, const int *__restrict__ pins,
 
 namespace {
 
-int64_t node_weight_sum(bipart_graph *g, Level &L) {
-    cudaStream_t s = g->stream;
-    unsigned long long *d = reinterpret_cast<unsigned long long *>(g->w.small.as<char>() + 48 * 1024 + 256);
-    BP_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long), s));
-    if (L.N > 0) {
-        k_weight_sum<<<grid_for(L.N), kBlock, 0, s>>>(L.N, L.nw(), d);
-        BP_LAUNCH();
-    }
-    unsigned long long hres = 0;
-    BP_CUDA(cudaMemcpyAsync(g->w.host_small, d, sizeof(hres), cudaMemcpyDeviceToHost, s));
-    sync(g);
-    std::memcpy(&hres, g->w.host_small, sizeof(hres));
-    return (int64_t)hres;
-}
-
 // Builds the subgraph of part j of the parent's level 0 as the child's level 0 (node map in the
 // child's l2g, weight total in its total_node_weight).  The extraction runs on the parent's stream
 // with the parent's scratch, reads the subgraph's sizes back once, and copies into child buffers of
@@ -1153,27 +1138,11 @@ private:
     }
 };
 
-constexpr int64_t kHostChunk = 1 << 19;
+constexpr int64_t kHostChunk = 1 << 18;
 constexpr int64_t kHostBlock = 4096;
 
-// Runs body(lo, hi) over [0, n) in chunks of kHostChunk on the host pool and returns the
-// smallest index any chunk reported (body returns the first failing index of its range, or -1),
-// which is what a sequential pass would report.
 // Set on a host-pool thread that validates one of many instances: its checks stay on that thread.
 thread_local bool tl_serial_checks = false;
-
-template <class Body>
-int64_t parallel_first(int64_t n, Body body) {
-    const int64_t chunks = (n + kHostChunk - 1) / kHostChunk;
-    if (chunks <= 1 || tl_serial_checks) return n > 0 ? body(0, n) : -1;
-    std::vector<int64_t> first((size_t)chunks, -1);
-    HostPool::get().run((int)chunks, [&](int c) {
-        first[(size_t)c] = body((int64_t)c * kHostChunk, std::min(n, ((int64_t)c + 1) * kHostChunk));
-    });
-    for (int64_t f : first)
-        if (f >= 0) return f;
-    return -1;
-}
 
 // First i in [lo, hi) with bad(i), checked a block at a time with a branch-free OR (a loop the
 // compiler vectorises); the exact index is searched only inside a failing block.
@@ -1190,61 +1159,70 @@ int64_t first_bad(int64_t lo, int64_t hi, Bad bad) {
     return -1;
 }
 
-// Sum of a weight array and the first weight below 1 (or -1), in parallel.
-std::pair<int64_t, int64_t> weight_check(const int32_t *w, int64_t n) {
-    const int64_t chunks = std::max<int64_t>(1, (n + kHostChunk - 1) / kHostChunk);
-    std::vector<int64_t> sum((size_t)chunks, 0), first((size_t)chunks, -1);
-    auto body = [&](int c) {
-        const int64_t lo = (int64_t)c * kHostChunk, hi = std::min(n, lo + kHostChunk);
-        int64_t acc = 0;
-        for (int64_t i = lo; i < hi; ++i) acc += w[i];
-        sum[(size_t)c] = acc;
-        first[(size_t)c] = first_bad(lo, hi, [&](int64_t i) { return (uint32_t)w[i] - 1u >= 0x7fffffffu; });
-    };
-    if (chunks == 1) body(0);
-    else if (tl_serial_checks)
-        for (int c = 0; c < (int)chunks; ++c) body(c);
-    else HostPool::get().run((int)chunks, body);
-    int64_t total = 0, bad = -1;
-    for (size_t c = 0; c < (size_t)chunks; ++c) {
-        total += sum[c];
-        if (bad < 0 && first[c] >= 0) bad = first[c];
-    }
-    return {total, bad};
-}
-
 }  // namespace
 
-// Host-side validation of a CSR given in host memory; the long loops run on the host pool and
-// report the same first offending index as a sequential pass would.
-void validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t *pins,
-                       const int32_t *nw, const int32_t *hw) {
+// Host-side validation of a CSR given in host memory.  The four arrays (offsets, pins, node and
+// hyperedge weights) are cut into chunks of kHostChunk entries that all run as ONE job on the host
+// pool; each chunk keeps its first offending index (and its weight sum), and the error reported is
+// the one a sequential pass would meet first: offsets, then pins, then node weights, hyperedge
+// weights and the weight sums.  hedge_pins is read up to hoff[E] entries, its documented length.
+// Returns the total node weight.
+int64_t validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t *pins,
+                          const int32_t *nw, const int32_t *hw) {
     if (N < 0 || E < 0) throw Fail{BIPART_ERR_INVALID_ARG, "negative size"};
     if (E > 0 && !hoff) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_offsets is NULL"};
     if (hoff && hoff[0] != 0) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets[0] != 0"};
-    int64_t bad = parallel_first(E, [&](int64_t lo, int64_t hi) {
-        return first_bad(lo, hi, [&](int64_t e) { return hoff[e + 1] < hoff[e]; });
-    });
+    const int32_t P = E > 0 ? hoff[E] : 0;  // a negative total fails the offsets check
+    const bool pins_null = P > 0 && !pins;
+    enum { kOff, kPins, kNw, kHw, kArrays };
+    const int64_t len[kArrays] = {E, pins_null ? 0 : std::max(P, 0), nw ? N : 0, hw ? E : 0};
+    int64_t first_task[kArrays + 1];
+    first_task[0] = 0;
+    for (int a = 0; a < kArrays; ++a) first_task[a + 1] = first_task[a] + (len[a] + kHostChunk - 1) / kHostChunk;
+    const int tasks = (int)first_task[kArrays];
+    std::vector<int64_t> first((size_t)tasks, -1), sum((size_t)tasks, 0);
+    auto body = [&](int t) {
+        int a = 0;
+        while (t >= first_task[a + 1]) ++a;
+        const int64_t lo = (t - first_task[a]) * kHostChunk, hi = std::min(len[a], lo + kHostChunk);
+        if (a == kOff) {
+            first[(size_t)t] = first_bad(lo, hi, [&](int64_t e) { return hoff[e + 1] < hoff[e]; });
+        } else if (a == kPins) {
+            first[(size_t)t] = first_bad(lo, hi, [&](int64_t i) { return (uint32_t)pins[i] >= (uint32_t)N; });
+        } else {
+            const int32_t *w = a == kNw ? nw : hw;
+            int64_t acc = 0;
+            for (int64_t i = lo; i < hi; ++i) acc += w[i];
+            sum[(size_t)t] = acc;
+            first[(size_t)t] = first_bad(lo, hi, [&](int64_t i) { return (uint32_t)w[i] - 1u >= 0x7fffffffu; });
+        }
+    };
+    if (tasks <= 1 || tl_serial_checks) {
+        for (int t = 0; t < tasks; ++t) body(t);
+    } else {
+        HostPool::get().run(tasks, body);
+    }
+    auto first_of = [&](int a) {
+        for (int64_t t = first_task[a]; t < first_task[a + 1]; ++t)
+            if (first[(size_t)t] >= 0) return first[(size_t)t];
+        return int64_t(-1);
+    };
+    auto sum_of = [&](int a) {
+        int64_t acc = 0;
+        for (int64_t t = first_task[a]; t < first_task[a + 1]; ++t) acc += sum[(size_t)t];
+        return acc;
+    };
+    int64_t bad = first_of(kOff);
     if (bad >= 0) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets not non-decreasing at " + std::to_string(bad)};
-    const int32_t P = E > 0 ? hoff[E] : 0;
-    if (P > 0 && !pins) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_pins is NULL"};
-    bad = parallel_first(P, [&](int64_t lo, int64_t hi) {
-        return first_bad(lo, hi, [&](int64_t i) { return (uint32_t)pins[i] >= (uint32_t)N; });
-    });
+    if (pins_null) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_pins is NULL"};
+    bad = first_of(kPins);
     if (bad >= 0) throw Fail{BIPART_ERR_INVALID_CSR, "pin " + std::to_string(bad) + " out of range"};
-    int64_t sn = N, se = 0;
-    if (nw) {
-        const auto r = weight_check(nw, N);
-        if (r.second >= 0) throw Fail{BIPART_ERR_INVALID_CSR, "node weight < 1"};
-        sn = r.first;
-    }
-    if (hw) {
-        const auto r = weight_check(hw, E);
-        if (r.second >= 0) throw Fail{BIPART_ERR_INVALID_CSR, "hyperedge weight < 1"};
-        se = r.first;
-    }
+    if (nw && first_of(kNw) >= 0) throw Fail{BIPART_ERR_INVALID_CSR, "node weight < 1"};
+    if (hw && first_of(kHw) >= 0) throw Fail{BIPART_ERR_INVALID_CSR, "hyperedge weight < 1"};
+    const int64_t sn = nw ? sum_of(kNw) : N, se = hw ? sum_of(kHw) : 0;
     if (sn >= (int64_t(1) << 31) || se >= (int64_t(1) << 31))
         throw Fail{BIPART_ERR_INVALID_CSR, "weight sum must stay below 2^31"};
+    return sn;
 }
 
 void validate_host_many(int32_t n, const bipart_instance *in, int32_t *codes, std::string *errs) {
@@ -1309,10 +1287,11 @@ bipart_graph *new_graph(cudaStream_t s) {
     return g.release();
 }
 
-void finish_create(bipart_graph *g, int32_t N, int32_t E, const int *d_hoff, const int *d_pins,
-                   const int *d_nw, const int *d_hw) {
-    build_level0(g, g->L0, N, E, d_hoff, d_pins, d_nw, d_hw);
-    g->total_node_weight = node_weight_sum(g, g->L0);
+// Level 0 of a validated CSR of P pins and total node weight W (both known from the validation).
+void finish_create(bipart_graph *g, int32_t N, int32_t E, int32_t P, int64_t W, const int *d_hoff,
+                   const int *d_pins, const int *d_nw, const int *d_hw) {
+    build_level0(g, g->L0, N, E, P, d_hoff, d_pins, d_nw, d_hw);
+    g->total_node_weight = W;
     sync(g);
     check_status(g);
 }
@@ -1368,7 +1347,7 @@ bool release_later(bipart_graph *g) {
 void graph_load_host(bipart_graph *g, int32_t N, int32_t E, const int32_t *hoff, const int32_t *pins,
                      const int32_t *nw, const int32_t *hw) {
     HandleScope hs(g);
-    validate_host_csr(N, E, hoff, pins, nw, hw);
+    const int64_t W = validate_host_csr(N, E, hoff, pins, nw, hw);
     cudaStream_t s = g->stream;
     const int32_t P = E > 0 ? hoff[E] : 0;
     int *d_hoff = (int *)g->in_hoff.ensure(sizeof(int) * ((size_t)E + 1), s);
@@ -1384,7 +1363,7 @@ void graph_load_host(bipart_graph *g, int32_t N, int32_t E, const int32_t *hoff,
     g->hier.valid = false;
     g->gen++;
     for (auto &kid : g->kids) kid->kid_stamp_valid = false;  // new input: new subgraphs
-    finish_create(g, N, E, E > 0 ? d_hoff : nullptr, d_pins, d_nw, d_hw);
+    finish_create(g, N, E, P, W, E > 0 ? d_hoff : nullptr, d_pins, d_nw, d_hw);
 }
 
 // Partitions the loaded hypergraph into host memory (blocking on the handle's stream).
@@ -1456,9 +1435,10 @@ int bipart_create(int32_t num_nodes, int32_t num_hedges, const int32_t *hedge_of
         if (P < 0) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets[E] < 0"};
         if (P > 0 && !hedge_pins) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_pins is NULL"};
         std::exception_ptr invalid;
+        int64_t W = 0;
         std::thread checker([&] {
             try {
-                validate_host_csr(N, E, hedge_offsets, hedge_pins, node_weights, hedge_weights);
+                W = validate_host_csr(N, E, hedge_offsets, hedge_pins, node_weights, hedge_weights);
             } catch (...) {
                 invalid = std::current_exception();
             }
@@ -1486,7 +1466,7 @@ int bipart_create(int32_t num_nodes, int32_t num_hedges, const int32_t *hedge_of
             throw;
         }
         checked();
-        finish_create(g.get(), N, E, E > 0 ? d_hoff : nullptr, d_pins, d_nw, d_hw);
+        finish_create(g.get(), N, E, P, W, E > 0 ? d_hoff : nullptr, d_pins, d_nw, d_hw);
         *out = g.release();
         return BIPART_OK;
     });
@@ -1528,7 +1508,7 @@ int bipart_create_device(int32_t num_nodes, int32_t num_hedges, const int32_t *h
         if (b & 2) throw Fail{BIPART_ERR_INVALID_CSR, "pin out of range"};
         if (b & 4) throw Fail{BIPART_ERR_INVALID_CSR, "weight < 1"};
         if (hs[0] >= (1ull << 31) || hs[1] >= (1ull << 31)) throw Fail{BIPART_ERR_INVALID_CSR, "weight sum must stay below 2^31"};
-        finish_create(g.get(), N, E, hedge_offsets, hedge_pins, node_weights, hedge_weights);
+        finish_create(g.get(), N, E, P, (int64_t)hs[0], hedge_offsets, hedge_pins, node_weights, hedge_weights);
         *out = g.release();
         return BIPART_OK;
     });

@@ -565,15 +565,9 @@ int *degree_counters(bipart_graph *g, int32_t N) {
     return deg;
 }
 
-void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t *d_hoff,
+void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, int32_t P, const int32_t *d_hoff,
                   const int32_t *d_pins, const int32_t *d_nw, const int32_t *d_hw) {
     cudaStream_t s = g->stream;
-    int32_t P = 0;
-    if (E > 0) {
-        BP_CUDA(cudaMemcpyAsync(g->w.host_small, d_hoff + E, sizeof(int), cudaMemcpyDeviceToHost, s));
-        sync(g);
-        P = (int32_t)g->w.host_small[0];
-    }
     L.N = N;
     contract(g, E, P, d_hoff, d_pins, d_hw, nullptr, L, degree_counters(g, N), false,
              g->w.small.as<int32_t>() + 2, nullptr, false, nullptr);

@@ -365,8 +365,9 @@ struct bipart_graph {
 namespace bp {
 
 // ------------------------------------------------------------------- coarsening (coarsen.cu)
-// Builds level 0 from a device CSR (already validated): normalisation + incidence.
-void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, const int32_t *d_hoff,
+// Builds level 0 from a device CSR (already validated, P = its pin count): normalisation +
+// incidence.
+void build_level0(bipart_graph *g, Level &L, int32_t N, int32_t E, int32_t P, const int32_t *d_hoff,
                   const int32_t *d_pins, const int32_t *d_nw, const int32_t *d_hw);
 // Algorithm 1 + 2 on `f`, producing `c` (sizes read back to the host).
 // sizes: level_sizes() slots receiving {N', E', P'}.  init_done: f's key and reset pass already
@@ -469,8 +470,9 @@ void trim_block_batch();
 
 // ------------------------------------------------------------------------- validation (api.cu)
 void validate_params(int32_t k, double eps, int32_t policy, int32_t levels, int32_t iters);
-void validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t *pins,
-                       const int32_t *nw, const int32_t *hw);
+// Returns the total node weight (N without node weights).
+int64_t validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t *pins,
+                          const int32_t *nw, const int32_t *hw);
 // validate_host_csr on every instance, spread over the host threads; a failure's code and text
 // go to codes[i] / errs[i] (left untouched for a valid instance).
 void validate_host_many(int32_t n, const bipart_instance *in, int32_t *codes, std::string *errs);
