@@ -56,10 +56,12 @@ typedef void (*bipart_free_fn)(void *ctx, void *ptr, size_t bytes, void *stream)
 int bipart_set_allocator(bipart_alloc_fn alloc, bipart_free_fn free_fn, void *ctx);
 
 /* Creates a handle from host CSR arrays (Sec. 1.1 problem statement: nodes, hyperedges, optional
- * weights).  Validates the CSR on the host (on worker threads, while the arrays are already being
- * copied to the device on `stream`, a cudaStream_t, NULL = the legacy default stream; no kernel
- * reads them before the validation has passed, and a CSR error outranks any device error) and
- * builds level 0 on the device: each hyperedge's pins sorted and
+ * weights).  The arrays are copied to the device on `stream` (a cudaStream_t, NULL = the legacy
+ * default stream; hedge_pins is read up to hedge_offsets[num_hedges] entries) and checked there by
+ * a kernel whose loops are bounded by the sizes; no other kernel reads them before that check has
+ * passed.  When it fails, or when no device work is possible, the CSR is validated on the host,
+ * whose INVALID_CSR error (naming the first offending offset or pin, as a sequential pass would)
+ * outranks any device error.  Then builds level 0 on the device: each hyperedge's pins sorted and
  * de-duplicated, hyperedges with fewer than 2 distinct pins dropped (they can never be cut), and
  * the node -> hyperedge incidence.  Errors: INVALID_ARG (NULL out, negative sizes),
  * INVALID_CSR, OOM, CUDA. */

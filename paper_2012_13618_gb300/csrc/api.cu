@@ -339,7 +339,7 @@ __global__ void k_validate(int N, int E, int P, const int *__restrict__ hoff,
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
     unsigned b = 0;
     unsigned long long sn = 0, se = 0;
-    if (tid == 0 && hoff[0] != 0) b |= 1;
+    if (tid == 0 && hoff && hoff[0] != 0) b |= 1;
     for (int e = tid; e < E; e += nt) {
         if (hoff[e + 1] < hoff[e]) b |= 1;
         if (hw) {
@@ -1296,6 +1296,37 @@ void finish_create(bipart_graph *g, int32_t N, int32_t E, int32_t P, int64_t W, 
     check_status(g);
 }
 
+// Device-side check of a CSR already on the device: bit 0 malformed offsets, bit 1 a pin out of
+// range, bit 2 a weight below 1, bit 3 a weight sum of 2^31 or more; also the node-weight total.
+// Every loop of the check is bounded by N, E and P, so it is safe on any content (hoff may be null
+// when E = 0).
+struct DevCheck {
+    unsigned bad = 0;
+    int64_t node_weight = 0;
+};
+
+DevCheck device_check(bipart_graph *g, int32_t N, int32_t E, int32_t P, const int *hoff, const int *pins,
+                      const int *nw, const int *hw) {
+    cudaStream_t s = g->stream;
+    unsigned *bad = reinterpret_cast<unsigned *>(g->w.small.as<char>() + 48 * 1024);
+    unsigned long long *sums = reinterpret_cast<unsigned long long *>(g->w.small.as<char>() + 48 * 1024 + 16);
+    BP_CUDA(cudaMemsetAsync(bad, 0, 64, s));
+    if (E > 0 || N > 0) {
+        k_validate<<<grid_for(std::max<int64_t>({(int64_t)N, (int64_t)E, (int64_t)P})), kBlock, 0, s>>>(
+            N, E, P, E > 0 ? hoff : nullptr, pins, nw, hw, bad, sums);
+        BP_LAUNCH();
+    }
+    BP_CUDA(cudaMemcpyAsync(g->w.host_small, bad, 64, cudaMemcpyDeviceToHost, s));
+    sync(g);
+    DevCheck r;
+    r.bad = g->w.host_small[0];
+    unsigned long long hs[2];
+    std::memcpy(hs, g->w.host_small + 4, sizeof(hs));
+    if (hs[0] >= (1ull << 31) || hs[1] >= (1ull << 31)) r.bad |= 8;
+    r.node_weight = (int64_t)hs[0];
+    return r;
+}
+
 }  // namespace
 
 // Workspace for the executor: a handle on its own stream with no hypergraph loaded yet.
@@ -1425,32 +1456,23 @@ int bipart_create(int32_t num_nodes, int32_t num_hedges, const int32_t *hedge_of
         if (!out) throw Fail{BIPART_ERR_INVALID_ARG, "out is NULL"};
         *out = nullptr;
         const int32_t E = num_hedges, N = num_nodes;
-        // what the copies depend on is checked first; the full validation then runs on another
-        // thread while the handle is set up and the arrays are copied, and no kernel reads them
-        // before it has passed (its error, if any, is the one reported)
+        // what the copies depend on is checked here; the copied arrays are then checked on the
+        // device by a kernel whose loops are bounded by N, E and P, and no other kernel reads
+        // them before it has passed.  The host pass runs only when that check fails (it names
+        // the first offending entry, as a sequential pass would) or when no device work is
+        // possible (its CSR error outranks the device error).
         if (N < 0 || E < 0) throw Fail{BIPART_ERR_INVALID_ARG, "negative size"};
         if (E > 0 && !hedge_offsets) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_offsets is NULL"};
         if (hedge_offsets && hedge_offsets[0] != 0) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets[0] != 0"};
         const int32_t P = E > 0 ? hedge_offsets[E] : 0;
         if (P < 0) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets[E] < 0"};
         if (P > 0 && !hedge_pins) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_pins is NULL"};
-        std::exception_ptr invalid;
-        int64_t W = 0;
-        std::thread checker([&] {
-            try {
-                W = validate_host_csr(N, E, hedge_offsets, hedge_pins, node_weights, hedge_weights);
-            } catch (...) {
-                invalid = std::current_exception();
-            }
-        });
-        auto checked = [&] {
-            if (checker.joinable()) checker.join();
-            if (invalid) std::rethrow_exception(invalid);
-        };
+        auto host_check = [&] { validate_host_csr(N, E, hedge_offsets, hedge_pins, node_weights, hedge_weights); };
         cudaStream_t s = (cudaStream_t)stream;
         std::unique_ptr<bipart_graph> g;
         Buf b_hoff, b_pins, b_nw, b_hw;
         int *d_hoff = nullptr, *d_pins = nullptr, *d_nw = nullptr, *d_hw = nullptr;
+        DevCheck chk;
         try {
             g.reset(new_graph(s));
             d_hoff = (int *)b_hoff.ensure(sizeof(int) * ((size_t)E + 1), s);
@@ -1461,12 +1483,16 @@ int bipart_create(int32_t num_nodes, int32_t num_hedges, const int32_t *hedge_of
             if (P > 0) BP_CUDA(cudaMemcpyAsync(d_pins, hedge_pins, sizeof(int) * (size_t)P, cudaMemcpyHostToDevice, s));
             if (d_nw && N > 0) BP_CUDA(cudaMemcpyAsync(d_nw, node_weights, sizeof(int) * (size_t)N, cudaMemcpyHostToDevice, s));
             if (d_hw && E > 0) BP_CUDA(cudaMemcpyAsync(d_hw, hedge_weights, sizeof(int) * (size_t)E, cudaMemcpyHostToDevice, s));
+            chk = device_check(g.get(), N, E, P, d_hoff, d_pins, d_nw, d_hw);
         } catch (...) {
-            checked();  // a CSR error outranks the device error
+            host_check();  // a CSR error outranks the device error
             throw;
         }
-        checked();
-        finish_create(g.get(), N, E, P, W, E > 0 ? d_hoff : nullptr, d_pins, d_nw, d_hw);
+        if (chk.bad) {
+            host_check();
+            throw Fail{BIPART_ERR_INVALID_CSR, "malformed CSR (device check)"};
+        }
+        finish_create(g.get(), N, E, P, chk.node_weight, E > 0 ? d_hoff : nullptr, d_pins, d_nw, d_hw);
         *out = g.release();
         return BIPART_OK;
     });
@@ -1491,24 +1517,12 @@ int bipart_create_device(int32_t num_nodes, int32_t num_hedges, const int32_t *h
             if (P < 0) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets[E] < 0"};
             if (P > 0 && !hedge_pins) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_pins is NULL"};
         }
-        unsigned *bad = reinterpret_cast<unsigned *>(g->w.small.as<char>() + 48 * 1024);
-        unsigned long long *sums = reinterpret_cast<unsigned long long *>(g->w.small.as<char>() + 48 * 1024 + 16);
-        BP_CUDA(cudaMemsetAsync(bad, 0, 64, s));
-        if (E > 0 || N > 0) {
-            k_validate<<<grid_for(std::max<int64_t>({(int64_t)N, (int64_t)E, (int64_t)P})), kBlock, 0, s>>>(
-                N, E, P, hedge_offsets, hedge_pins, node_weights, hedge_weights, bad, sums);
-            BP_LAUNCH();
-        }
-        BP_CUDA(cudaMemcpyAsync(g->w.host_small, bad, 64, cudaMemcpyDeviceToHost, s));
-        sync(g.get());
-        unsigned b = g->w.host_small[0];
-        unsigned long long hs[2];
-        std::memcpy(hs, g->w.host_small + 4, sizeof(hs));
-        if (b & 1) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets malformed"};
-        if (b & 2) throw Fail{BIPART_ERR_INVALID_CSR, "pin out of range"};
-        if (b & 4) throw Fail{BIPART_ERR_INVALID_CSR, "weight < 1"};
-        if (hs[0] >= (1ull << 31) || hs[1] >= (1ull << 31)) throw Fail{BIPART_ERR_INVALID_CSR, "weight sum must stay below 2^31"};
-        finish_create(g.get(), N, E, P, (int64_t)hs[0], hedge_offsets, hedge_pins, node_weights, hedge_weights);
+        const DevCheck chk = device_check(g.get(), N, E, P, hedge_offsets, hedge_pins, node_weights, hedge_weights);
+        if (chk.bad & 1) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets malformed"};
+        if (chk.bad & 2) throw Fail{BIPART_ERR_INVALID_CSR, "pin out of range"};
+        if (chk.bad & 4) throw Fail{BIPART_ERR_INVALID_CSR, "weight < 1"};
+        if (chk.bad & 8) throw Fail{BIPART_ERR_INVALID_CSR, "weight sum must stay below 2^31"};
+        finish_create(g.get(), N, E, P, chk.node_weight, hedge_offsets, hedge_pins, node_weights, hedge_weights);
         *out = g.release();
         return BIPART_OK;
     });
