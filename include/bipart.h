@@ -186,8 +186,12 @@ int bipart_partition_device_ex(bipart_handle h, const bipart_params *params, int
  * bipart_partition returns for it alone.  Staging buffers (pinned host and device), arenas, the
  * graph and the worker pool (whose workspaces keep their launch plans; a request goes preferably
  * to the worker that last ran one of the same sizes and parameters) are kept between calls;
- * bipart_batch_release frees them.  Returns OK when no instance failed, else the first failing
- * instance's error (see bipart_last_error). */
+ * bipart_batch_release frees them.  Each instance's sizes, pointers, hedge_offsets[0],
+ * hedge_offsets[E] and parameters are checked on the host first; its CSR content is checked where it
+ * is read: by its block, before the block reads the arrays through an index, or by its worker's
+ * creation step.  A malformed instance gets INVALID_CSR with the host pass's message (the first
+ * offending offset or pin) and leaves its out_parts untouched.  Returns OK when no instance
+ * failed, else the first failing instance's error (see bipart_last_error). */
 int bipart_partition_batch(int32_t n, const bipart_instance *instances, const bipart_params *params,
                            int32_t *const *out_parts, int32_t *statuses, int32_t workers);
 
@@ -220,7 +224,10 @@ void bipart_batch_release(void);
  * identical to bipart_partition on the same input. */
 typedef struct bipart_server_s *bipart_server;
 int bipart_server_create(size_t hbm_budget_bytes, int32_t workers, bipart_server *out);
-/* Queues a request; the caller keeps instance arrays and out_parts (HOST) alive until waited. */
+/* Queues a request; the caller keeps instance arrays and out_parts (HOST) alive until waited.  A
+ * request whose sizes, pointers, hedge_offsets[0], hedge_offsets[E] or parameters fail the host
+ * checks completes at once with that error; its CSR content is checked where it is read (as in
+ * bipart_partition_batch), a malformed one completing with INVALID_CSR. */
 int bipart_server_submit(bipart_server server, const bipart_instance *instance,
                          const bipart_params *params, int32_t *out_parts, int64_t *ticket);
 /* Waits for a request (timeout_ms < 0: forever; BIPART_ERR_TIMEOUT when it expires, the request

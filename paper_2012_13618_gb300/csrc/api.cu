@@ -1141,9 +1141,6 @@ private:
 constexpr int64_t kHostChunk = 1 << 18;
 constexpr int64_t kHostBlock = 4096;
 
-// Set on a host-pool thread that validates one of many instances: its checks stay on that thread.
-thread_local bool tl_serial_checks = false;
-
 // First i in [lo, hi) with bad(i), checked a block at a time with a branch-free OR (a loop the
 // compiler vectorises); the exact index is searched only inside a failing block.
 template <class Bad>
@@ -1197,7 +1194,7 @@ int64_t validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32
             first[(size_t)t] = first_bad(lo, hi, [&](int64_t i) { return (uint32_t)w[i] - 1u >= 0x7fffffffu; });
         }
     };
-    if (tasks <= 1 || tl_serial_checks) {
+    if (tasks <= 1) {
         for (int t = 0; t < tasks; ++t) body(t);
     } else {
         HostPool::get().run(tasks, body);
@@ -1223,31 +1220,6 @@ int64_t validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32
     if (sn >= (int64_t(1) << 31) || se >= (int64_t(1) << 31))
         throw Fail{BIPART_ERR_INVALID_CSR, "weight sum must stay below 2^31"};
     return sn;
-}
-
-void validate_host_many(int32_t n, const bipart_instance *in, int32_t *codes, std::string *errs) {
-    auto one = [&](int i) {
-        const bipart_instance &x = in[i];
-        try {
-            validate_host_csr(x.num_nodes, x.num_hedges, x.hedge_offsets, x.hedge_pins, x.node_weights,
-                              x.hedge_weights);
-        } catch (const Fail &e) {
-            codes[i] = e.code;
-            errs[i] = e.msg;
-        }
-    };
-    if (n <= 1) {
-        for (int i = 0; i < n; ++i) one(i);
-        return;
-    }
-    // instances spread over the host pool, each checked on one thread (tasks strided so that
-    // every one gets a similar mix of sizes)
-    const int tasks = std::min<int>(n, 64);
-    HostPool::get().run(tasks, [&](int t) {
-        tl_serial_checks = true;
-        for (int i = t; i < n; i += tasks) one(i);
-        tl_serial_checks = false;
-    });
 }
 
 }  // namespace bp

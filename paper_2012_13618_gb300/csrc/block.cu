@@ -592,7 +592,7 @@ void run_block_batch(std::vector<BInst> &inst, const std::vector<const int32_t *
     const int tasks = std::min(n, 64);
     c.lanes->run(tasks, [&](int t) {
         for (int i = t; i < n; i += tasks)
-            if (inst[i].status != 2) std::memcpy(outs[i], parts + inst[i].out, sizeof(int32_t) * (size_t)inst[i].N);
+            if (inst[i].status < kBlkDeferred) std::memcpy(outs[i], parts + inst[i].out, sizeof(int32_t) * (size_t)inst[i].N);
     });
     if (timing) {
         auto t4 = std::chrono::steady_clock::now();
@@ -656,7 +656,7 @@ void tune_block_batch(std::vector<BInst> &inst, const std::vector<const int32_t 
             }
             int deferred = 0;
             const BInst *out = reinterpret_cast<const BInst *>((const char *)c.host.p + pr.lay.inst);
-            for (size_t i = 0; i < sub.size(); ++i) deferred += out[i].status == 2;
+            for (size_t i = 0; i < sub.size(); ++i) deferred += out[i].status == kBlkDeferred;
             if (verbose)
                 std::fprintf(stderr, "[bipart] tune bucket %d (%zu instances): %d x %d per SM: %.2f ms%s\n", b,
                              sub.size(), kShapes[s].threads, kShapes[s].per_sm, ms,

@@ -568,6 +568,65 @@ __device__ int blk_solve(Ctx &x, const BArgs &a, const BInst &I, DLevel *lev, in
     return warn;
 }
 
+// Streams v[0, n) through the block, kU independent loads in flight per thread (one load at a time
+// would leave a block at a few GB/s); f(i, v[i]) sees every element once.
+template <class F>
+__device__ __forceinline__ void blk_stream(const int *v, int n, F f) {
+    constexpr int kU = 8;
+    for (int i0 = threadIdx.x; i0 < n; i0 += kU * blockDim.x) {
+        int x[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int i = i0 + u * blockDim.x;
+            x[u] = i < n ? v[i] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < n) f(i, x[u]);
+        }
+    }
+}
+
+// Whether the instance's staged CSR is well formed: offsets non-decreasing from 0 to P, pins in
+// [0, N), weights at least 1 with sums below 2^31 (the handle path's checks).  The whole block runs
+// it before anything reads the arrays through an index; every load is bounded by N, E and P.
+__device__ bool blk_csr_ok(const BArgs &a, const BInst &I, unsigned long long *s_sum, int *s_bad) {
+    if (threadIdx.x == 0) {
+        s_sum[0] = s_sum[1] = 0;
+        *s_bad = 0;
+    }
+    __syncthreads();
+    const int *hoff = a.hoff + I.hoff;
+    bool bad = threadIdx.x == 0 && (hoff[0] != 0 || hoff[I.E] != I.P);
+    // offsets: each element against its successor (hoff[e + 1] read through the same stream)
+    blk_stream(hoff + 1, I.E, [&](int e, int next) { bad |= next < hoff[e]; });
+    const unsigned N = (unsigned)I.N;
+    blk_stream(a.pins + I.pins, I.P, [&](int, int v) { bad |= (unsigned)v >= N; });
+    unsigned long long sn = 0, se = 0;
+    if (I.nw >= 0)
+        blk_stream(a.nw + I.nw, I.N, [&](int, int w) {
+            bad |= w < 1;
+            sn += (unsigned)max(w, 0);
+        });
+    if (I.hw >= 0)
+        blk_stream(a.hw + I.hw, I.E, [&](int, int w) {
+            bad |= w < 1;
+            se += (unsigned)max(w, 0);
+        });
+    sn = warp_sum(sn);
+    se = warp_sum(se);
+    if ((threadIdx.x & 31) == 0) {
+        if (sn) atomicAdd(&s_sum[0], sn);
+        if (se) atomicAdd(&s_sum[1], se);
+    }
+    if (bad) atomicOr(s_bad, 1);
+    __syncthreads();
+    const bool ok = *s_bad == 0 && s_sum[0] < (1ull << 31) && s_sum[1] < (1ull << 31);
+    __syncthreads();
+    return ok;
+}
+
 }  // namespace
 
 template <int BT, int MINB>
@@ -575,7 +634,8 @@ __global__ void __launch_bounds__(BT, MINB) k_batch(BArgs a) {
     extern __shared__ __align__(16) char smem[];
     __shared__ DLevel lev[kMaxLev];
     __shared__ int2 stack[kMaxStack];
-    __shared__ int s_inst;
+    __shared__ int s_inst, s_bad;
+    __shared__ unsigned long long s_sum[2];
     for (;;) {
         if (threadIdx.x == 0) s_inst = atomicAdd(a.next, 1);
         __syncthreads();
@@ -592,7 +652,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch(BArgs a) {
         x.smem = smem;
         x.status = a.status;
         const BInst I = a.inst[i];
-        const int st = blk_solve(x, a, I, lev, stack);
+        const int st = blk_csr_ok(a, I, s_sum, &s_bad) ? blk_solve(x, a, I, lev, stack) : kBlkMalformed;
         if (threadIdx.x == 0) a.inst[i].status = st;
         __syncthreads();
     }

@@ -142,20 +142,43 @@ BlockSet block_set(const std::vector<int32_t> &idx, const bipart_instance *insta
     return block_set(ins, ps);
 }
 
-// Validates every instance; st[i] / err[i] record a failure.
-void validate_all(int32_t n, const bipart_instance *instances, const bipart_params *params,
+// The checks every instance gets on the host before any of its data is touched: sizes, pointers,
+// hedge_offsets[0] and hedge_offsets[E] (the staging and the size buckets rely on them), then its
+// parameters.  The CSR content is checked where it is read: by its block in the persistent batch
+// kernel (kBlkMalformed, see block_error) or by the worker's creation of its workspace level 0.
+// st[i] / err[i] record a failure.
+void precheck(const bipart_instance &x, const bipart_params &p) {
+    if (x.num_nodes < 0 || x.num_hedges < 0) throw Fail{BIPART_ERR_INVALID_ARG, "negative size"};
+    if (x.num_hedges > 0 && !x.hedge_offsets) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_offsets is NULL"};
+    if (x.hedge_offsets && x.hedge_offsets[0] != 0) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets[0] != 0"};
+    const int32_t P = x.num_hedges > 0 ? x.hedge_offsets[x.num_hedges] : 0;
+    if (P < 0) throw Fail{BIPART_ERR_INVALID_CSR, "hedge_offsets[E] < 0"};
+    if (P > 0 && !x.hedge_pins) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_pins is NULL"};
+    make_params(p.k, p.epsilon, p.policy, p.levels, p.refine_iters, p.flags);  // validates
+}
+
+void precheck_all(int32_t n, const bipart_instance *instances, const bipart_params *params,
                   std::vector<int32_t> &st, std::vector<std::string> &err) {
-    validate_host_many(n, instances, st.data(), err.data());
     for (int32_t i = 0; i < n; ++i) {
-        if (st[i] != BIPART_OK) continue;
-        const bipart_params &p = params[i];
         try {
-            make_params(p.k, p.epsilon, p.policy, p.levels, p.refine_iters, p.flags);  // validates
+            precheck(instances[i], params[i]);
         } catch (const Fail &e) {
             st[i] = e.code;
             err[i] = e.msg;
         }
     }
+}
+
+// The error of an instance its block found malformed: the host pass over its CSR names the first
+// offending entry.
+Fail block_error(const bipart_instance &x) {
+    try {
+        validate_host_csr(x.num_nodes, x.num_hedges, x.hedge_offsets, x.hedge_pins, x.node_weights,
+                          x.hedge_weights);
+    } catch (const Fail &e) {
+        return e;
+    }
+    return Fail{BIPART_ERR_INVALID_CSR, "malformed CSR (device check)"};
 }
 
 
@@ -182,12 +205,26 @@ class Pool {
         for (std::thread &t : threads_) t.join();
     }
 
-    // Queues a job; returns its ticket.  Jobs larger than the whole budget are rejected.
+    // Queues a job; returns its ticket.  Jobs that fail the host checks (precheck) or are larger
+    // than the whole budget are rejected: their ticket is done at once with the error.
     int64_t submit(const bipart_instance &inst, const bipart_params &p, int32_t *out, bool front_by_size) {
         auto j = std::make_shared<Job>();
         j->inst = inst;
         j->params = p;
         j->out = out;
+        try {
+            precheck(inst, p);
+        } catch (const Fail &e) {
+            j->status = e.code;
+            j->error = e.msg;
+            j->done = true;
+            j->t_submit = j->t_start = j->t_end = Clock::now();
+            std::lock_guard<std::mutex> lk(mu_);
+            j->ticket = ++next_ticket_;
+            jobs_[j->ticket] = j;
+            done_cv_.notify_all();
+            return j->ticket;
+        }
         j->bytes = estimate_bytes(inst);
         j->sig = job_sig(inst, p);
         j->block_ok = batching_ && block_takes(inst, p) && batch_cost(inst, p) <= kBatchMaxCost;
@@ -416,8 +453,13 @@ class Pool {
             const Clock::time_point t1 = Clock::now();
             for (size_t i = 0; i < batch.size(); ++i) {
                 Job &j = *batch[i];
-                if (bs.bi[i].status == 2) {
+                if (bs.bi[i].status == kBlkDeferred) {
                     run_one(j);
+                    j.t_end = Clock::now();
+                } else if (bs.bi[i].status == kBlkMalformed) {
+                    const Fail e = block_error(j.inst);
+                    j.status = e.code;
+                    j.error = e.msg;
                     j.t_end = Clock::now();
                 } else {
                     j.status = bs.bi[i].status ? BIPART_WARN_IMBALANCED : BIPART_OK;
@@ -505,7 +547,7 @@ extern "C" int bipart_partition_batch(int32_t n, const bipart_instance *instance
         if (workers <= 0) workers = std::min<int32_t>(16, std::max<int32_t>(n, 1));
         std::vector<int32_t> st(n, BIPART_OK);
         std::vector<std::string> err(n);
-        validate_all(n, instances, params, st, err);
+        precheck_all(n, instances, params, st, err);
         std::vector<int32_t> blk, rest;
         for (int32_t i = 0; i < n; ++i) {
             if (st[i] != BIPART_OK) continue;
@@ -531,8 +573,14 @@ extern "C" int bipart_partition_batch(int32_t n, const bipart_instance *instance
             run_block_batch(b.bi, b.ho, b.pi, b.nw, b.hw, outs);
             for (size_t j = 0; j < blk.size(); ++j) {
                 const int32_t i = blk[j];
-                if (b.bi[j].status == 2) {  // did not fit the block arena: single-instance path
+                if (b.bi[j].status == kBlkDeferred) {  // did not fit the block arena: single-instance path
                     tickets[i] = pool_ref().submit(instances[i], params[i], out_parts[i], false);
+                    continue;
+                }
+                if (b.bi[j].status == kBlkMalformed) {
+                    const Fail e = block_error(instances[i]);
+                    st[i] = e.code;
+                    err[i] = e.msg;
                     continue;
                 }
                 st[i] = b.bi[j].status ? BIPART_WARN_IMBALANCED : BIPART_OK;
@@ -572,7 +620,7 @@ extern "C" int bipart_batch_tune(int32_t n, const bipart_instance *instances, co
     try {
         std::vector<int32_t> st(n, BIPART_OK);
         std::vector<std::string> err(n);
-        validate_all(n, instances, params, st, err);
+        precheck_all(n, instances, params, st, err);
         std::vector<int32_t> blk;
         for (int32_t i = 0; i < n; ++i) {
             if (st[i] != BIPART_OK) {

@@ -448,12 +448,14 @@ struct BInst {
     int policy, levels, iters, k;
     long long e6;                        // imbalance of every bisection, millionths
     long long hoff, pins, nw, hw, out;  // offsets into the concatenated arrays (nw, hw < 0: unit)
-    int status;                          // 0 ok, 1 imbalanced, 2 deferred (did not fit)
+    int status;                          // 0 ok, 1 imbalanced, 2 deferred (did not fit), 3 malformed
 };
+constexpr int kBlkDeferred = 2, kBlkMalformed = 3;
 bool block_eligible(int64_t N, int64_t E, int64_t P, int k, int levels);
 // Runs a batch with the persistent block kernels (instances in size buckets, each bucket with the
 // block shape its tuning chose, all buckets in one CUDA graph); writes every instance's parts to
-// outs[i] and its status to inst[i].status (2: did not fit a block's arena, the caller runs it).
+// outs[i] and its status to inst[i].status (2: did not fit a block's arena, the caller runs it;
+// 3: its CSR failed the block's check, nothing was written, the caller reports it).
 void run_block_batch(std::vector<BInst> &inst, const std::vector<const int32_t *> &hoff,
                      const std::vector<const int32_t *> &pins, const std::vector<const int32_t *> &nw,
                      const std::vector<const int32_t *> &hw, const std::vector<int32_t *> &outs);
@@ -473,9 +475,6 @@ void validate_params(int32_t k, double eps, int32_t policy, int32_t levels, int3
 // Returns the total node weight (N without node weights).
 int64_t validate_host_csr(int32_t N, int32_t E, const int32_t *hoff, const int32_t *pins,
                           const int32_t *nw, const int32_t *hw);
-// validate_host_csr on every instance, spread over the host threads; a failure's code and text
-// go to codes[i] / errs[i] (left untouched for a valid instance).
-void validate_host_many(int32_t n, const bipart_instance *in, int32_t *codes, std::string *errs);
 
 // ------------------------------------------------------------------------- executor (api.cu)
 bipart_graph *graph_new(cudaStream_t s);

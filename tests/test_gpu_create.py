@@ -124,3 +124,71 @@ def test_valid_after_malformed_on_same_stream():
     with bp.create_from(g) as h:
         parts, st = h.partition(2, 0.1, "LDH", 25, 2)
         assert np.array_equal(parts, ref["side"].astype(np.int32))
+
+
+def _batch_raw(graphs, params, workers=2):
+    import ctypes
+    bp = _bp()
+    n, keep, insts, pars = bp._batch_args(graphs, params)
+    outs = [np.full(max(int(g["N"]), 1), -7, np.int32) for g in graphs]
+    out_ptrs = (ctypes.c_void_p * n)(*[o.ctypes.data for o in outs])
+    st = np.zeros(n, np.int32)
+    rc = bp.load().bipart_partition_batch(n, ctypes.cast(insts, ctypes.c_void_p), ctypes.cast(pars, ctypes.c_void_p),
+                                          ctypes.cast(out_ptrs, ctypes.c_void_p),
+                                          ctypes.c_void_p(st.ctypes.data), workers)
+    return rc, [o[: int(g["N"])] for o, g in zip(outs, graphs)], st, bp.load().bipart_last_error().decode()
+
+
+def _malformed_like(g, what):
+    # a copy of g with one defect, keeping hoff[E] == len(pins)
+    g = {k: (None if v is None else (np.array(v, copy=True) if isinstance(v, np.ndarray) else v))
+         for k, v in g.items()}
+    if what == "pin":
+        g["pins"][len(g["pins"]) // 2] = g["N"] + 5
+    elif what == "offsets":
+        e = g["E"] // 2
+        g["hoff"][e + 1] = g["hoff"][e] - 1
+    elif what == "nw":
+        g["nw"] = np.ones(g["N"], np.int32)
+        g["nw"][g["N"] // 3] = 0
+    return g
+
+
+def test_batch_malformed_instances_reported_others_exact():
+    # malformed instances among valid ones on the persistent block path: each malformed one gets
+    # INVALID_CSR and keeps its output untouched, every valid one equals the oracle
+    bp = _bp()
+    base = [synth.uniform(1500 + 100 * i, 1400 + 90 * i, 2, 6, seed=40 + i) for i in range(6)]
+    kinds = [None, "pin", None, "offsets", "nw", None]
+    graphs = [g if k is None else _malformed_like(g, k) for g, k in zip(base, kinds)]
+    p = dict(k=2, eps=0.05, policy="LDH", levels=25, iters=2)
+    rc, parts, st, msg = _batch_raw(graphs, p)
+    assert rc == bp.ERR_INVALID_CSR and "instance 1" in msg, msg
+    for i, (g, k) in enumerate(zip(graphs, kinds)):
+        if k is None:
+            ref = oracle.bisect(oracle.Hypergraph.from_dict(g), 0.05, "LDH", 25, 2)
+            assert np.array_equal(parts[i], ref["side"].astype(np.int32)) and st[i] == ref["status"], i
+        else:
+            assert st[i] == bp.ERR_INVALID_CSR and (parts[i] == -7).all(), (i, k)
+
+
+def test_server_rejects_bad_requests_without_touching_others():
+    # a request with bad parameters completes at once; malformed CSRs complete with INVALID_CSR,
+    # whether they ran in a micro-batch or alone; the valid requests equal the oracle
+    bp = _bp()
+    base = [synth.uniform(1200 + 50 * i, 1100 + 40 * i, 2, 6, seed=70 + i) for i in range(16)]
+    kinds = [None] * 16
+    kinds[3], kinds[8], kinds[12] = "pin", "offsets", "nw"
+    graphs = [g if k is None else _malformed_like(g, k) for g, k in zip(base, kinds)]
+    with bp.Server(hbm_budget_bytes=0, workers=1) as srv:
+        tickets = [srv.submit(g, k=2, eps=0.05) for g in graphs]
+        bad_k = srv.submit(base[0], k=0, eps=0.05)
+        for i, t in enumerate(tickets):
+            parts, st, _, _ = srv.wait(t)
+            if kinds[i] is None:
+                ref = oracle.bisect(oracle.Hypergraph.from_dict(graphs[i]), 0.05, "LDH", 25, 2)
+                assert np.array_equal(parts, ref["side"].astype(np.int32)) and st == ref["status"], i
+            else:
+                assert st == bp.ERR_INVALID_CSR, (i, kinds[i], st)
+        _, st, _, _ = srv.wait(bad_k)
+        assert st == bp.ERR_INVALID_ARG
