@@ -192,3 +192,29 @@ def test_server_rejects_bad_requests_without_touching_others():
                 assert st == bp.ERR_INVALID_CSR, (i, kinds[i], st)
         _, st, _, _ = srv.wait(bad_k)
         assert st == bp.ERR_INVALID_ARG
+
+
+def test_batch_staging_mixed_inputs_match_oracle():
+    # staged batch inputs: instances with and without weights, no hyperedges, pin arrays that
+    # start off a 16-byte boundary; the replayed graph takes new source arrays
+    bp = _bp()
+    graphs = []
+    for i in range(8):
+        g = _weighted(100 + i, N=1500 + 200 * i, E=1300 + 150 * i)
+        if i % 2:
+            g["nw"] = g["hw"] = None
+        if i % 3 == 1:
+            # a view one element into a larger array: the source is not 16-byte aligned
+            buf = np.empty(g["pins"].size + 1, np.int32)
+            buf[1:] = g["pins"]
+            g["pins"] = buf[1:]
+        graphs.append(g)
+    graphs.append(dict(N=40, E=0, hoff=np.zeros(1, np.int32), pins=np.zeros(0, np.int32), nw=None, hw=None))
+    p = dict(k=2, eps=0.05, policy="LDH", levels=25, iters=2)
+    for rep in range(2):  # capture, then replay on copies (new source arrays)
+        if rep:
+            graphs = [{k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in g.items()} for g in graphs]
+        parts, st = bp.partition_batch(graphs, p, workers=2)
+        for i, g in enumerate(graphs):
+            ref = oracle.bisect(oracle.Hypergraph.from_dict(g), 0.05, "LDH", 25, 2)
+            assert np.array_equal(parts[i], ref["side"].astype(np.int32)) and st[i] == ref["status"], i
