@@ -9,8 +9,9 @@
 //
 // Instances go into size buckets by pin count; each bucket runs as its own persistent launch with
 // the block shape (threads, blocks per SM) its tuning chose, and the launches of all buckets,
-// with the copies in and out, form one CUDA graph whose branches run at the same time (a bucket
-// that runs out of instances frees its SMs for the others).  The graph is kept and replayed while
+// with the copies out, form one CUDA graph whose branches run at the same time (a bucket that
+// runs out of instances frees its SMs for the others); the inputs go in ahead of it, each chunk
+// as soon as the host has staged it.  The graph is kept and replayed while
 // the batches keep the same shape.  The tuner times every candidate shape on each bucket of a
 // given batch and keeps the winners in a JSON file per device.
 //
@@ -426,16 +427,19 @@ Prepared prepare(BatchCtx &c, std::vector<BInst> &inst, const std::vector<const 
     return pr;
 }
 
-// Copies the batch's inputs into the pinned staging buffer on the context's host threads.
+// Copies the batch's inputs into the pinned staging buffer on the context's host threads and moves
+// them to the device on c.stream: the pieces are staged in chunks of destination offsets, and each
+// chunk's copy to the device is queued as soon as the chunk is staged, so the copies run while the
+// host stages the next chunks.
 void stage_inputs(BatchCtx &c, const Prepared &pr, const std::vector<BInst> &inst,
                   const std::vector<const int32_t *> &hoff, const std::vector<const int32_t *> &pins,
                   const std::vector<const int32_t *> &nw, const std::vector<const int32_t *> &hw) {
-    char *h = (char *)c.host.p;
+    char *h = (char *)c.host.p, *d = (char *)c.dev.p;
     const Layout &L = pr.lay;
     std::memcpy(h + L.inst, inst.data(), sizeof(BInst) * inst.size());
     std::memcpy(h + L.order, pr.order.data(), sizeof(int) * pr.order.size());
     struct Piece {
-        void *dst;
+        size_t off;
         const void *src;
         size_t bytes;
     };
@@ -443,8 +447,7 @@ void stage_inputs(BatchCtx &c, const Prepared &pr, const std::vector<BInst> &ins
     const size_t kPiece = 4 << 20;
     auto add = [&](size_t off, const int32_t *src, int64_t count) {
         const size_t bytes = sizeof(int32_t) * (size_t)count;
-        for (size_t o = 0; o < bytes; o += kPiece)
-            pieces.push_back({h + off + o, (const char *)src + o, std::min(kPiece, bytes - o)});
+        for (size_t o = 0; o < bytes; o += kPiece) pieces.push_back({off + o, (const char *)src + o, std::min(kPiece, bytes - o)});
     };
     for (size_t i = 0; i < inst.size(); ++i) {
         const BInst &I = inst[i];
@@ -453,21 +456,31 @@ void stage_inputs(BatchCtx &c, const Prepared &pr, const std::vector<BInst> &ins
         if (I.nw >= 0) add(L.nw + sizeof(int) * (size_t)I.nw, nw[i], I.N);
         if (I.hw >= 0 && I.E > 0) add(L.hw + sizeof(int) * (size_t)I.hw, hw[i], I.E);
     }
-    // pieces grouped into about 64 tasks of similar size
-    const size_t tasks = std::min<size_t>(pieces.size(), 64);
-    if (tasks == 0) return;
-    c.lanes->run((int)tasks, [&](int t) {
-        for (size_t j = (size_t)t; j < pieces.size(); j += tasks) std::memcpy(pieces[j].dst, pieces[j].src, pieces[j].bytes);
-    });
+    std::sort(pieces.begin(), pieces.end(), [](const Piece &a, const Piece &b) { return a.off < b.off; });
+    const size_t kChunk = 256 << 20;
+    size_t up = 0;  // [0, up) is queued for the device
+    for (size_t j = 0; j < pieces.size();) {
+        size_t j1 = j;
+        while (j1 < pieces.size() && pieces[j1].off < pieces[j].off + kChunk) ++j1;
+        const int tasks = (int)std::min<size_t>(j1 - j, 64);
+        c.lanes->run(tasks, [&](int t) {
+            for (size_t q = j + (size_t)t; q < j1; q += (size_t)tasks)
+                std::memcpy(h + pieces[q].off, pieces[q].src, pieces[q].bytes);
+        });
+        const size_t hi = j1 < pieces.size() ? pieces[j1].off : L.in_end;
+        BP_CUDA(cudaMemcpyAsync(d + up, h + up, hi - up, cudaMemcpyHostToDevice, c.stream));
+        up = hi;
+        j = j1;
+    }
+    if (up < L.in_end) BP_CUDA(cudaMemcpyAsync(d + up, h + up, L.in_end - up, cudaMemcpyHostToDevice, c.stream));
 }
 
-// Records the batch's device work on c.stream: inputs in, one persistent launch per bucket on its
-// own branch, outputs back.  Run eagerly or under capture.
+// Records the batch's device work on c.stream (after the inputs stage_inputs queued): one
+// persistent launch per bucket on its own branch, outputs back.  Run eagerly or under capture.
 void record(BatchCtx &c, const Prepared &pr, int n) {
     char *h = (char *)c.host.p, *d = (char *)c.dev.p;
     const Layout &L = pr.lay;
     cudaStream_t s = c.stream;
-    BP_CUDA(cudaMemcpyAsync(d, h, L.in_end, cudaMemcpyHostToDevice, s));
     int *heads = c.misc.as<int>();
     uint32_t *status = reinterpret_cast<uint32_t *>(heads + 16);
     BP_CUDA(cudaMemsetAsync(heads, 0, 256, s));
