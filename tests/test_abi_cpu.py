@@ -140,3 +140,29 @@ def test_params_validation_before_any_device_work():
                                         ctypes.c_void_p(sts.ctypes.data), 1)
         assert rc == bp.ERR_INVALID_ARG, (k, flags, rc)
     assert lib.bipart_partition_ex(None, None, None) == bp.ERR_INVALID_ARG
+
+
+def test_batch_prechecks_without_gpu():
+    # sizes, pointers, hedge_offsets[0] and hedge_offsets[E] are checked on the host before any
+    # device work: an all-invalid batch reports its first instance's error with no GPU present
+    lib = bp.load()
+    cases = [
+        (dict(N=-1, hoff=[0, 2], pins=[0, 1]), bp.ERR_INVALID_ARG),      # negative size
+        (dict(N=4, hoff=[1, 2], pins=[0, 1]), bp.ERR_INVALID_CSR),       # offsets[0] != 0
+        (dict(N=4, hoff=[0, -2], pins=[0, 1]), bp.ERR_INVALID_CSR),      # offsets[E] < 0
+        (dict(N=4, hoff=[0, 2], pins=None), bp.ERR_INVALID_ARG),         # pins NULL with P > 0
+    ]
+    for case, code in cases:
+        g = dict(case)
+        keep = [np.ascontiguousarray(g["hoff"], np.int32),
+                None if g["pins"] is None else np.ascontiguousarray(g["pins"], np.int32)]
+        inst = bp.Instance(g["N"], keep[0].size - 1, ctypes.c_void_p(keep[0].ctypes.data),
+                           None if keep[1] is None else ctypes.c_void_p(keep[1].ctypes.data), None, None)
+        par = bp.Params(2, 0.1, 0, 25, 2, 0)
+        out = np.empty(4, np.int32)
+        outs = (ctypes.c_void_p * 1)(out.ctypes.data)
+        sts = np.zeros(1, np.int32)
+        rc = lib.bipart_partition_batch(1, ctypes.byref(inst), ctypes.byref(par), outs,
+                                        ctypes.c_void_p(sts.ctypes.data), 1)
+        assert rc == code and sts[0] == code, (case, rc, sts[0])
+        assert lib.bipart_last_error().startswith(b"instance 0: ")
