@@ -204,7 +204,9 @@ int bipart_partition_batch(int32_t n, const bipart_instance *instances, const bi
  * $HOME/.cache/bipart/batch_tune.json; a file that cannot be written is skipped).  Only the
  * instances the persistent path takes are timed; results are discarded.  chosen (may be NULL;
  * 8 entries) receives per bucket its threads and blocks per SM, 0 0 for a bucket with no
- * instance.  Returns OK or the first validation error. */
+ * instance.  Returns OK or the first error of the host checks (sizes, pointers, offsets[0] and
+ * offsets[E], parameters); an instance whose CSR content is malformed is skipped by its block and
+ * not timed. */
 int bipart_batch_tune(int32_t n, const bipart_instance *instances, const bipart_params *params,
                       int32_t *chosen);
 

@@ -146,7 +146,6 @@ BlockSet block_set(const std::vector<int32_t> &idx, const bipart_instance *insta
 // hedge_offsets[0] and hedge_offsets[E] (the staging and the size buckets rely on them), then its
 // parameters.  The CSR content is checked where it is read: by its block in the persistent batch
 // kernel (kBlkMalformed, see block_error) or by the worker's creation of its workspace level 0.
-// st[i] / err[i] record a failure.
 void precheck(const bipart_instance &x, const bipart_params &p) {
     if (x.num_nodes < 0 || x.num_hedges < 0) throw Fail{BIPART_ERR_INVALID_ARG, "negative size"};
     if (x.num_hedges > 0 && !x.hedge_offsets) throw Fail{BIPART_ERR_INVALID_ARG, "hedge_offsets is NULL"};
@@ -157,6 +156,7 @@ void precheck(const bipart_instance &x, const bipart_params &p) {
     make_params(p.k, p.epsilon, p.policy, p.levels, p.refine_iters, p.flags);  // validates
 }
 
+// precheck on every instance; st[i] / err[i] record a failure.
 void precheck_all(int32_t n, const bipart_instance *instances, const bipart_params *params,
                   std::vector<int32_t> &st, std::vector<std::string> &err) {
     for (int32_t i = 0; i < n; ++i) {
